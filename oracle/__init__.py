@@ -1,0 +1,309 @@
+"""FP64 CPU oracle of the NeDF composition render path (arXiv 2308.04669).
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, ``__graft_entry__.smoke()`` and ``bench.py``'s
+cpu_baseline / reference leg may import this package.  It shares no code with the CUDA
+library and never imports it; both sides consume the same seeded inputs from
+``paper_2308_04669_gb300.scenegen``.
+
+The arithmetic lives in ``nedf_oracle.c`` (plain C, double precision); this module compiles it
+with gcc and marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DEPTH_MLP, DEPTH_EXACT, DEPTH_MARCH = 0, 1, 2
+QUANT_NONE, QUANT_BF16 = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable flags: the same source runs on x86_64 and aarch64)."""
+    src = os.path.join(_HERE, "nedf_oracle.c")
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "nedf_oracle.h"))):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-shared", "-fPIC", "-o",
+                               tmp, src, "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OrcType(C.Structure):
+    _fields_ = [("kind", C.c_int), ("params", C.c_double * 8), ("rb", C.c_double),
+                ("albedo", C.c_double * 3), ("nedf_hidden", C.c_int), ("nedf_width", C.c_int),
+                ("nedf_w", C.POINTER(C.c_double)), ("nerf_hidden", C.c_int), ("nerf_width", C.c_int),
+                ("nerf_w", C.POINTER(C.c_double))]
+
+
+class OrcScene(C.Structure):
+    _fields_ = [("W", C.c_int), ("H", C.c_int), ("eye", C.c_double * 3), ("target", C.c_double * 3),
+                ("fov_deg", C.c_double), ("n_lights", C.c_int), ("lights", C.POINTER(C.c_double)),
+                ("n_types", C.c_int), ("types", C.POINTER(OrcType)), ("n_inst", C.c_int),
+                ("inst_type", C.POINTER(C.c_int)), ("inst_R", C.POINTER(C.c_double)),
+                ("inst_T", C.POINTER(C.c_double)), ("inst_s", C.POINTER(C.c_double)),
+                ("n_shade", C.c_int), ("shade_half", C.c_double), ("beta", C.c_double),
+                ("eps", C.c_double), ("sigma_max", C.c_double), ("sdf_width", C.c_double)]
+
+
+class OrcOpts(C.Structure):
+    _fields_ = [("depth_mode", C.c_int), ("march_n", C.c_int), ("march_b", C.c_int),
+                ("quant", C.c_int), ("fallback_conf", C.c_double), ("refine_steps", C.c_int),
+                ("n_threads", C.c_int)]
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            l = C.CDLL(build())
+            d, i, i64, u32 = C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_uint32)
+            sp, op = C.POINTER(OrcScene), C.POINTER(OrcOpts)
+            l.orc_sdf.argtypes = [C.c_int, d, d]; l.orc_sdf.restype = C.c_double
+            l.orc_density.argtypes = [sp, C.c_int, d]; l.orc_density.restype = C.c_double
+            l.orc_camera_ray.argtypes = [sp, C.c_int, C.c_int, d, d]
+            l.orc_to_local.argtypes = [sp, C.c_int, d, d, d, d]
+            l.orc_bound.argtypes = [d, d, C.c_double, d]; l.orc_bound.restype = C.c_int
+            l.orc_posenc.argtypes = [d, C.c_int, C.c_int, d]; l.orc_posenc.restype = C.c_int
+            l.orc_nedf_features.argtypes = [d, d, C.c_double, d, d]; l.orc_nedf_features.restype = C.c_int
+            l.orc_mlp.argtypes = [d, C.c_int, i, d, d, C.c_int]
+            l.orc_round_bf16.argtypes = [C.c_double]; l.orc_round_bf16.restype = C.c_double
+            l.orc_query.argtypes = [sp, op, C.c_int, d, d, d, d]; l.orc_query.restype = C.c_int
+            l.orc_exact_depth.argtypes = [C.c_int, d, d, d, C.c_double, C.c_double, i]
+            l.orc_exact_depth.restype = C.c_double
+            l.orc_march_depth.argtypes = [sp, C.c_int, d, d, C.c_double, C.c_double, C.c_int, C.c_int, i]
+            l.orc_march_depth.restype = C.c_double
+            l.orc_composite_samples.argtypes = [C.c_int, d, d, C.c_double, d]
+            l.orc_render.argtypes = [sp, op, C.c_int64, i64, d, u32, d, d, d, d, d, d]
+            l.orc_volume_render.argtypes = [sp, op, C.c_int, C.c_int64, i64, d]
+            l.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]; l.orc_splitmix64.restype = C.c_uint64
+            l.orc_train_rays.argtypes = [C.c_double, C.c_uint64, C.c_int64, C.c_int, d, d]
+            l.orc_train_labels.argtypes = [sp, C.c_int, C.c_int, d, d, C.c_int, C.c_int, d, i]
+            l.orc_nedf_loss_grad.argtypes = [sp, C.c_int, C.c_int, d, d, d, i, d, C.c_int]
+            l.orc_nedf_loss_grad.restype = C.c_double
+            l.orc_adam.argtypes = [C.c_int64, d, d, d, d, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
+            _lib = l
+    return _lib
+
+
+class OracleScene:
+    """A scenegen.Scene widened to double and laid out for the C oracle (keeps arrays alive)."""
+
+    def __init__(self, scene, nedf_override: dict | None = None):
+        self.scene = scene
+        self._keep = []
+        nt = len(scene.types)
+        self.types = (OrcType * nt)()
+        for k, t in enumerate(scene.types):
+            ct = self.types[k]
+            ct.kind = int(t.kind)
+            for c in range(8):
+                ct.params[c] = float(t.params[c])
+            ct.rb = float(t.rb)
+            for c in range(3):
+                ct.albedo[c] = float(t.albedo[c])
+            w = np.ascontiguousarray(
+                (nedf_override[k] if nedf_override and k in nedf_override else t.nedf_w), np.float64)
+            self._keep.append(w)
+            ct.nedf_hidden, ct.nedf_width, ct.nedf_w = t.nedf_hidden, t.nedf_width, _dp(w)
+            if t.nerf_hidden:
+                wn = np.ascontiguousarray(t.nerf_w, np.float64)
+                self._keep.append(wn)
+                ct.nerf_hidden, ct.nerf_width, ct.nerf_w = t.nerf_hidden, t.nerf_width, _dp(wn)
+            else:
+                ct.nerf_hidden, ct.nerf_width = 0, 0
+                ct.nerf_w = C.POINTER(C.c_double)()
+        self.lights = np.ascontiguousarray(scene.lights, np.float64).reshape(-1)
+        self.itype = np.ascontiguousarray(scene.inst_type, np.int32)
+        self.R = np.ascontiguousarray(scene.inst_R, np.float64).reshape(-1)
+        self.T = np.ascontiguousarray(scene.inst_T, np.float64).reshape(-1)
+        self.s = np.ascontiguousarray(scene.inst_s, np.float64)
+        sc = OrcScene()
+        sc.W, sc.H = scene.W, scene.H
+        for c in range(3):
+            sc.eye[c] = float(scene.eye[c])
+            sc.target[c] = float(scene.target[c])
+        sc.fov_deg = float(scene.fov_deg)
+        sc.n_lights, sc.lights = scene.lights.shape[0], _dp(self.lights)
+        sc.n_types, sc.types = nt, self.types
+        sc.n_inst = scene.n_inst
+        sc.inst_type = self.itype.ctypes.data_as(C.POINTER(C.c_int))
+        sc.inst_R, sc.inst_T, sc.inst_s = _dp(self.R), _dp(self.T), _dp(self.s)
+        sc.n_shade, sc.shade_half = scene.n_shade, float(np.float32(scene.shade_half))
+        sc.beta, sc.eps = float(np.float32(scene.shadow_beta)), float(np.float32(scene.shadow_eps))
+        sc.sigma_max, sc.sdf_width = float(np.float32(scene.sigma_max)), float(np.float32(scene.sdf_width))
+        self.c = sc
+
+    @property
+    def ptr(self):
+        return C.byref(self.c)
+
+
+def opts(depth_mode=DEPTH_MLP, march_n=128, march_b=4, quant=QUANT_NONE, fallback_conf=0.0,
+         refine_steps=0, n_threads=1) -> OrcOpts:
+    return OrcOpts(depth_mode, march_n, march_b, quant, fallback_conf, refine_steps, n_threads)
+
+
+def render(osc: OracleScene, px=None, **kw):
+    """Steps 1-3 for the pixels `px` (default: all).  Returns a dict of arrays."""
+    s = osc.scene
+    if px is None:
+        px = np.arange(s.W * s.H, dtype=np.int64)
+    px = np.ascontiguousarray(px, np.int64)
+    n = px.shape[0]
+    out = dict(depth=np.empty(n), id=np.empty(n, np.uint32), gap=np.empty(n), pmargin=np.empty(n),
+               rgba=np.empty((n, 4)), shadow=np.empty(n), smargin=np.empty(n), out=np.empty((n, 4)))
+    o = opts(**kw)
+    lib().orc_render(osc.ptr, C.byref(o), n, px.ctypes.data_as(C.POINTER(C.c_int64)),
+                     _dp(out["depth"]), out["id"].ctypes.data_as(C.POINTER(C.c_uint32)),
+                     _dp(out["gap"]), _dp(out["pmargin"]), _dp(out["rgba"]), _dp(out["shadow"]),
+                     _dp(out["smargin"]), _dp(out["out"]))
+    out["px"] = px
+    return out
+
+
+def volume_render(osc: OracleScene, n_samples=128, px=None, n_threads=1, quant=QUANT_NONE):
+    s = osc.scene
+    if px is None:
+        px = np.arange(s.W * s.H, dtype=np.int64)
+    px = np.ascontiguousarray(px, np.int64)
+    rgba = np.empty((px.shape[0], 4))
+    o = opts(n_threads=n_threads, quant=quant)
+    lib().orc_volume_render(osc.ptr, C.byref(o), n_samples, px.shape[0],
+                            px.ctypes.data_as(C.POINTER(C.c_int64)), _dp(rgba))
+    return rgba
+
+
+def sdf(kind, params, x):
+    p = np.ascontiguousarray(np.asarray(params, np.float64).reshape(-1)[:8].tolist() + [0.0] * (8 - min(8, len(params))), np.float64)
+    xx = np.ascontiguousarray(x, np.float64)
+    return lib().orc_sdf(int(kind), _dp(p), _dp(xx))
+
+
+def camera_ray(osc: OracleScene, i, j):
+    o, d = np.empty(3), np.empty(3)
+    lib().orc_camera_ray(osc.ptr, i, j, _dp(o), _dp(d))
+    return o, d
+
+
+def to_local(osc: OracleScene, inst, o, d):
+    o = np.ascontiguousarray(o, np.float64); d = np.ascontiguousarray(d, np.float64)
+    ol, dl = np.empty(3), np.empty(3)
+    lib().orc_to_local(osc.ptr, inst, _dp(o), _dp(d), _dp(ol), _dp(dl))
+    return ol, dl
+
+
+def bound(ol, dl, rb):
+    ol = np.ascontiguousarray(ol, np.float64); dl = np.ascontiguousarray(dl, np.float64)
+    out = np.empty(4)
+    kept = lib().orc_bound(_dp(ol), _dp(dl), float(rb), _dp(out))
+    return bool(kept), out
+
+
+def posenc(x, n_freq):
+    x = np.ascontiguousarray(x, np.float64)
+    out = np.empty(x.shape[0] * (1 + 2 * n_freq))
+    lib().orc_posenc(_dp(x), x.shape[0], n_freq, _dp(out))
+    return out
+
+
+def nedf_features(ol, dl, rb):
+    ol = np.ascontiguousarray(ol, np.float64); dl = np.ascontiguousarray(dl, np.float64)
+    f, b = np.empty(78), np.empty(4)
+    kept = lib().orc_nedf_features(_dp(ol), _dp(dl), float(rb), _dp(f), _dp(b))
+    return bool(kept), f, b
+
+
+def mlp(w, dims, x, quant=QUANT_NONE):
+    w = np.ascontiguousarray(w, np.float64)
+    dims_c = (C.c_int * len(dims))(*dims)
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.empty(dims[-1])
+    lib().orc_mlp(_dp(w), len(dims) - 1, dims_c, _dp(x), _dp(y), quant)
+    return y
+
+
+def round_bf16(x):
+    return lib().orc_round_bf16(float(x))
+
+
+def query(osc: OracleScene, inst, o, d, **kw):
+    o = np.ascontiguousarray(o, np.float64); d = np.ascontiguousarray(d, np.float64)
+    out, mg = np.empty(6), C.c_double()
+    op = opts(**kw)
+    hit = lib().orc_query(osc.ptr, C.byref(op), inst, _dp(o), _dp(d), _dp(out), C.byref(mg))
+    return bool(hit), out, mg.value
+
+
+def exact_depth(kind, params, ol, dl, te, tx):
+    p = np.zeros(8); p[: len(params)] = params
+    ol = np.ascontiguousarray(ol, np.float64); dl = np.ascontiguousarray(dl, np.float64)
+    hit = C.c_int()
+    D = lib().orc_exact_depth(int(kind), _dp(p), _dp(ol), _dp(dl), te, tx, C.byref(hit))
+    return bool(hit.value), D
+
+
+def march_depth(osc: OracleScene, type_, ol, dl, te, tx, n, b):
+    ol = np.ascontiguousarray(ol, np.float64); dl = np.ascontiguousarray(dl, np.float64)
+    hit = C.c_int()
+    D = lib().orc_march_depth(osc.ptr, type_, _dp(ol), _dp(dl), te, tx, n, b, C.byref(hit))
+    return bool(hit.value), D
+
+
+def composite_samples(sigma, rgb, world_delta):
+    sigma = np.ascontiguousarray(sigma, np.float64)
+    rgb = np.ascontiguousarray(rgb, np.float64).reshape(-1)
+    out = np.empty(4)
+    lib().orc_composite_samples(sigma.shape[0], _dp(sigma), _dp(rgb), float(world_delta), _dp(out))
+    return out
+
+
+def splitmix64(seed, index):
+    return lib().orc_splitmix64(seed, index)
+
+
+def train_rays(rb, seed, first, n):
+    o, d = np.empty((n, 3)), np.empty((n, 3))
+    lib().orc_train_rays(float(rb), seed, first, n, _dp(o), _dp(d))
+    return o, d
+
+
+def train_labels(osc: OracleScene, type_, o, d, march_n=256, march_b=8):
+    o = np.ascontiguousarray(o, np.float64); d = np.ascontiguousarray(d, np.float64)
+    n = o.shape[0]
+    m, h = np.empty(n), np.empty(n, np.int32)
+    lib().orc_train_labels(osc.ptr, type_, n, _dp(o), _dp(d), march_n, march_b, _dp(m),
+                           h.ctypes.data_as(C.POINTER(C.c_int)))
+    return m, h
+
+
+def nedf_loss_grad(osc: OracleScene, type_, o, d, m_star, hit_star, quant=QUANT_NONE):
+    o = np.ascontiguousarray(o, np.float64); d = np.ascontiguousarray(d, np.float64)
+    m_star = np.ascontiguousarray(m_star, np.float64)
+    hit_star = np.ascontiguousarray(hit_star, np.int32)
+    t = osc.scene.types[type_]
+    g = np.empty(t.nedf_w.shape[0])
+    loss = lib().orc_nedf_loss_grad(osc.ptr, type_, o.shape[0], _dp(o), _dp(d), _dp(m_star),
+                                    hit_star.ctypes.data_as(C.POINTER(C.c_int)), _dp(g), quant)
+    return loss, g
+
+
+def adam(theta, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam step on float64 arrays."""
+    lib().orc_adam(theta.shape[0], _dp(theta), _dp(np.ascontiguousarray(g, np.float64)), _dp(m), _dp(v),
+                   t, lr, b1, b2, eps)

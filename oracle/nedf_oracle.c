@@ -1,0 +1,776 @@
+/* FP64 CPU oracle of the NeDF composition render path (arXiv 2308.04669).
+ *
+ * TEST INFRASTRUCTURE ONLY: only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline /
+ * reference leg may load this.  It is deliberately plain: nested loops in the order of the
+ * paper's Algorithm 1 (Steps 1-2) and Algorithm 2 (Step 3), every quantity in double.
+ *
+ * Readings of points the paper leaves open are stated where they are used; each one is also
+ * listed in the repository's design notes.
+ */
+#include "nedf_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define PI 3.14159265358979323846
+
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static double len3(const double *a) { return sqrt(dot3(a, a)); }
+static double dmin(double a, double b) { return a < b ? a : b; }
+static double dmax(double a, double b) { return a > b ? a : b; }
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+static void cross3(const double *a, const double *b, double *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static void normalize3(double *a)
+{
+    double l = len3(a);
+    a[0] /= l; a[1] /= l; a[2] /= l;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Analytic shapes (object-local).  These stand in for the pre-trained NeRF objects.            */
+/* ------------------------------------------------------------------------------------------ */
+static double sdf_torus_y(double x, double y, double z, double R, double r)
+{
+    double q0 = sqrt(x * x + z * z) - R;
+    return sqrt(q0 * q0 + y * y) - r;
+}
+
+double orc_sdf(int kind, const double *p, const double x[3])
+{
+    switch (kind) {
+    case ORC_SPHERE:
+        return len3(x) - p[0];
+    case ORC_TORUS:
+        return sdf_torus_y(x[0], x[1], x[2], p[0], p[1]);
+    case ORC_BOX: {
+        double q[3], outside = 0.0, inside;
+        for (int c = 0; c < 3; ++c) q[c] = fabs(x[c]) - p[c];
+        for (int c = 0; c < 3; ++c) outside += dmax(q[c], 0.0) * dmax(q[c], 0.0);
+        inside = dmin(dmax(q[0], dmax(q[1], q[2])), 0.0);
+        return sqrt(outside) + inside;
+    }
+    case ORC_CAPSULE: { /* segment on the y axis, |y| <= p0, radius p1 */
+        double y = x[1] - clampd(x[1], -p[0], p[0]);
+        return sqrt(x[0] * x[0] + y * y + x[2] * x[2]) - p[1];
+    }
+    case ORC_ROUNDCONE: {
+        /* Convex hull of sphere (0,y1,0) radius r1 and sphere (0,y2,0) radius r2, reduced to the
+         * half-plane (radial distance, height): distance to the hull of two discs. */
+        double r1 = p[0], y1 = p[1], r2 = p[2], y2 = p[3];
+        double h = y2 - y1;
+        double qr = sqrt(x[0] * x[0] + x[2] * x[2]), qy = x[1] - y1;
+        double sb = (r1 - r2) / h;           /* sine of the side's tilt */
+        double cb = sqrt(1.0 - sb * sb);     /* cosine of the side's tilt */
+        double k = -qr * sb + qy * cb;       /* position along the side's tangent direction */
+        if (k < 0.0) return sqrt(qr * qr + qy * qy) - r1;
+        if (k > cb * h) return sqrt(qr * qr + (qy - h) * (qy - h)) - r2;
+        return qr * cb + qy * sb - r1;
+    }
+    case ORC_TWOSPHERE: {
+        double a[3] = {x[0] - p[0], x[1], x[2]}, b[3] = {x[0] + p[0], x[1], x[2]};
+        return dmin(len3(a), len3(b)) - p[1];
+    }
+    case ORC_TWISTTORUS: { /* ring in the xy plane (axis z), twisted about y by p2 rad per unit y */
+        double th = p[2] * x[1], c = cos(th), s = sin(th);
+        double xr = c * x[0] - s * x[2], zr = s * x[0] + c * x[2];
+        double q0 = sqrt(xr * xr + x[1] * x[1]) - p[0];
+        return sqrt(q0 * q0 + zr * zr) - p[1];
+    }
+    case ORC_OCTA: /* |x|+|y|+|z| = a, scaled to a lower bound of the distance */
+        return (fabs(x[0]) + fabs(x[1]) + fabs(x[2]) - p[0]) / sqrt(3.0);
+    default:
+        return 1e30;
+    }
+}
+
+/* sigma(x) = sigma_max * sigmoid(-sdf / width): the analytic NeRF density of the workloads. */
+double orc_density(const orc_scene *sc, int type, const double x[3])
+{
+    const orc_type *t = &sc->types[type];
+    return sc->sigma_max / (1.0 + exp(orc_sdf(t->kind, t->params, x) / sc->sdf_width));
+}
+
+static int inside_solid(const orc_scene *sc, int type, const double x[3])
+{
+    /* The iso level sigma_max / 2 (reading: surface = half of the peak density). */
+    return orc_density(sc, type, x) >= 0.5 * sc->sigma_max;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Step 1 inputs: camera rays, rigid transform of rays (Eq. 7), bound cull (Fig. 2b)            */
+/* ------------------------------------------------------------------------------------------ */
+void orc_camera_ray(const orc_scene *sc, int i, int j, double o[3], double d[3])
+{
+    double fwd[3] = {sc->target[0] - sc->eye[0], sc->target[1] - sc->eye[1], sc->target[2] - sc->eye[2]};
+    double up0[3] = {0.0, 1.0, 0.0}, right[3], up[3];
+    normalize3(fwd);
+    cross3(fwd, up0, right);
+    normalize3(right);
+    cross3(right, fwd, up);
+    double th = tan(0.5 * sc->fov_deg * PI / 180.0);
+    double u = (2.0 * (i + 0.5) / sc->W - 1.0) * th * ((double)sc->W / sc->H);
+    double v = (1.0 - 2.0 * (j + 0.5) / sc->H) * th;
+    for (int c = 0; c < 3; ++c) {
+        o[c] = sc->eye[c];
+        d[c] = u * right[c] + v * up[c] + fwd[c];
+    }
+    normalize3(d);
+}
+
+/* G^{-1}: local origin R^T (o - T) / s, local direction R^T d / s normalised (the local ray
+ * parameter times s is the world distance). */
+void orc_to_local(const orc_scene *sc, int inst, const double o[3], const double d[3],
+                  double ol[3], double dl[3])
+{
+    const double *R = sc->inst_R + 9 * inst, *T = sc->inst_T + 3 * inst;
+    double s = sc->inst_s[inst];
+    double v[3] = {o[0] - T[0], o[1] - T[1], o[2] - T[2]};
+    for (int c = 0; c < 3; ++c) {
+        ol[c] = (R[0 * 3 + c] * v[0] + R[1 * 3 + c] * v[1] + R[2 * 3 + c] * v[2]) / s;
+        dl[c] = (R[0 * 3 + c] * d[0] + R[1 * 3 + c] * d[1] + R[2 * 3 + c] * d[2]) / s;
+    }
+    normalize3(dl);
+}
+
+/* Ray vs the bound sphere |x| = rb.  Kept iff the ray meets the sphere ahead of its origin.
+ * out4 = {t_entry (clamped at 0), t_exit, t_perp, discriminant}.  t_perp = -o.d is the signed
+ * distance from the origin to the tangency point p_perp of Eq. 2 (Fig. 2a). */
+int orc_bound(const double ol[3], const double dl[3], double rb, double out4[4])
+{
+    double b = dot3(ol, dl);
+    double c = dot3(ol, ol) - rb * rb;
+    double disc = b * b - c;
+    out4[0] = INFINITY;
+    out4[1] = -INFINITY;
+    out4[2] = -b;
+    out4[3] = disc;
+    if (disc < 0.0) return 0;
+    double sq = sqrt(disc);
+    out4[1] = -b + sq;
+    out4[0] = dmax(0.0, -b - sq);
+    return out4[1] >= 0.0;
+}
+
+/* gamma(x) = [x, sin(2^0 x) .. sin(2^{L-1} x), cos(2^0 x) .. cos(2^{L-1} x)], blocks n wide. */
+int orc_posenc(const double *x, int n, int L, double *out)
+{
+    for (int c = 0; c < n; ++c) out[c] = x[c];
+    for (int k = 0; k < L; ++k)
+        for (int c = 0; c < n; ++c) {
+            out[n + k * n + c] = sin(ldexp(x[c], k));
+            out[n + L * n + k * n + c] = cos(ldexp(x[c], k));
+        }
+    return n * (1 + 2 * L);
+}
+
+/* NeDF input: the ray's entry point on the bound plus its direction, encoded with 6
+ * frequencies (78 features). */
+int orc_nedf_features(const double ol[3], const double dl[3], double rb, double *feat, double out4[4])
+{
+    if (!orc_bound(ol, dl, rb, out4)) return 0;
+    double x[6];
+    for (int c = 0; c < 3; ++c) {
+        x[c] = ol[c] + out4[0] * dl[c];
+        x[3 + c] = dl[c];
+    }
+    orc_posenc(x, 6, 6, feat);
+    return 1;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Networks                                                                                    */
+/* ------------------------------------------------------------------------------------------ */
+double orc_round_bf16(double x)
+{
+    /* Round to the nearest value with an 8-bit significand, ties to even. */
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e;
+    frexp(x, &e); /* |x| in [2^(e-1), 2^e) */
+    double q = ldexp(1.0, e - 8);
+    return nearbyint(x / q) * q;
+}
+
+void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant)
+{
+    int maxd = 0;
+    for (int l = 0; l <= n_layers; ++l) maxd = dims[l] > maxd ? dims[l] : maxd;
+    double *a = (double *)malloc(sizeof(double) * maxd), *b = (double *)malloc(sizeof(double) * maxd);
+    memcpy(a, x, sizeof(double) * dims[0]);
+    const double *p = w;
+    for (int l = 0; l < n_layers; ++l) {
+        int fi = dims[l], fo = dims[l + 1];
+        const double *W = p, *bias = p + (size_t)fi * fo;
+        for (int o = 0; o < fo; ++o) {
+            double acc = 0.0;
+            for (int i = 0; i < fi; ++i) {
+                double wv = W[(size_t)o * fi + i], av = a[i];
+                if (quant == ORC_QUANT_BF16) { wv = orc_round_bf16(wv); av = orc_round_bf16(av); }
+                acc += wv * av;
+            }
+            acc += bias[o];
+            b[o] = (l + 1 < n_layers) ? dmax(acc, 0.0) : acc;
+        }
+        memcpy(a, b, sizeof(double) * fo);
+        p += (size_t)fi * fo + fo;
+    }
+    memcpy(y, a, sizeof(double) * dims[n_layers]);
+    free(a);
+    free(b);
+}
+
+static int nedf_dims(const orc_type *t, int *dims)
+{
+    dims[0] = 78;
+    for (int l = 1; l <= t->nedf_hidden; ++l) dims[l] = t->nedf_width;
+    dims[t->nedf_hidden + 1] = 2;
+    return t->nedf_hidden + 1;
+}
+
+static int nerf_dims(const orc_type *t, int *dims)
+{
+    dims[0] = 90;
+    for (int l = 1; l <= t->nerf_hidden; ++l) dims[l] = t->nerf_width;
+    dims[t->nerf_hidden + 1] = 3;
+    return t->nerf_hidden + 1;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Depth queries: EXACT (analytic root), MARCH (plain method), MLP (NeDF, Eq. 1-2)              */
+/* ------------------------------------------------------------------------------------------ */
+static double march_root_sdf(int kind, const double *params, const double ol[3], const double dl[3],
+                             double te, double tx, int n, int b, int *hit)
+{
+    /* Dense scan for the first outside -> inside change of sign of the distance, then bisection. */
+    double prev_t = te, x[3];
+    for (int c = 0; c < 3; ++c) x[c] = ol[c] + te * dl[c];
+    int prev_in = orc_sdf(kind, params, x) <= 0.0;
+    for (int k = 1; k <= n; ++k) {
+        double t = te + (tx - te) * k / n;
+        for (int c = 0; c < 3; ++c) x[c] = ol[c] + t * dl[c];
+        int in = orc_sdf(kind, params, x) <= 0.0;
+        if (in && !prev_in) {
+            double lo = prev_t, hi = t;
+            for (int it = 0; it < b; ++it) {
+                double mid = 0.5 * (lo + hi);
+                for (int c = 0; c < 3; ++c) x[c] = ol[c] + mid * dl[c];
+                if (orc_sdf(kind, params, x) <= 0.0) hi = mid; else lo = mid;
+            }
+            *hit = 1;
+            return 0.5 * (lo + hi);
+        }
+        prev_in = in;
+        prev_t = t;
+    }
+    *hit = 0;
+    return INFINITY;
+}
+
+double orc_exact_depth(int kind, const double *p, const double ol[3], const double dl[3],
+                       double te, double tx, int *hit)
+{
+    *hit = 0;
+    if (kind == ORC_SPHERE) {
+        double b = dot3(ol, dl), c = dot3(ol, ol) - p[0] * p[0], disc = b * b - c;
+        if (disc < 0.0) return INFINITY;
+        double t0 = -b - sqrt(disc);
+        if (t0 >= te && t0 <= tx) { *hit = 1; return t0; }
+        return INFINITY;
+    }
+    if (kind == ORC_BOX) { /* slab method */
+        double tn = -INFINITY, tf = INFINITY;
+        for (int c = 0; c < 3; ++c) {
+            if (dl[c] == 0.0) {
+                if (fabs(ol[c]) > p[c]) return INFINITY;
+                continue;
+            }
+            double t1 = (-p[c] - ol[c]) / dl[c], t2 = (p[c] - ol[c]) / dl[c];
+            tn = dmax(tn, dmin(t1, t2));
+            tf = dmin(tf, dmax(t1, t2));
+        }
+        if (tn <= tf && tn >= te && tn <= tx) { *hit = 1; return tn; }
+        return INFINITY;
+    }
+    /* No closed form in use: converge a fine scan of the distance's sign change. */
+    return march_root_sdf(kind, p, ol, dl, te, tx, 20000, 80, hit);
+}
+
+/* Plain method (our reading of the label depth): N uniform steps over [te, tx], the first step
+ * whose density reaches sigma_max/2 after one below it, then B bisection steps; midpoint. */
+double orc_march_depth(const orc_scene *sc, int type, const double ol[3], const double dl[3],
+                       double te, double tx, int n, int b, int *hit)
+{
+    double x[3], prev_t = te;
+    for (int c = 0; c < 3; ++c) x[c] = ol[c] + te * dl[c];
+    int prev_in = inside_solid(sc, type, x);
+    for (int k = 1; k <= n; ++k) {
+        double t = te + (tx - te) * k / n;
+        for (int c = 0; c < 3; ++c) x[c] = ol[c] + t * dl[c];
+        int in = inside_solid(sc, type, x);
+        if (in && !prev_in) {
+            double lo = prev_t, hi = t;
+            for (int it = 0; it < b; ++it) {
+                double mid = 0.5 * (lo + hi);
+                for (int c = 0; c < 3; ++c) x[c] = ol[c] + mid * dl[c];
+                if (inside_solid(sc, type, x)) hi = mid; else lo = mid;
+            }
+            *hit = 1;
+            return 0.5 * (lo + hi);
+        }
+        prev_in = in;
+        prev_t = t;
+    }
+    *hit = 0;
+    return INFINITY;
+}
+
+/* One (ray, instance) query of Step 1 / Step 3.  World ray (o, d) with |d| = 1.
+ * Returns 1 on hit; out6 = {D_local, m, a, te, tx, tperp}; *margin = distance of this query's
+ * discrete decisions from their thresholds (cull discriminant, hit logit, D > 0, fallback). */
+int orc_query(const orc_scene *sc, const orc_opts *op, int inst, const double o[3], const double d[3],
+              double out6[6], double *margin)
+{
+    const orc_type *t = &sc->types[sc->inst_type[inst]];
+    double ol[3], dl[3], bd[4], feat[78];
+    orc_to_local(sc, inst, o, d, ol, dl);
+    int kept = orc_nedf_features(ol, dl, t->rb, feat, bd);
+    double mg = fabs(bd[3]) / (t->rb * t->rb);
+    if (kept) mg = dmin(mg, fabs(bd[1]) / t->rb);
+    out6[0] = INFINITY; out6[1] = out6[2] = 0.0;
+    out6[3] = bd[0]; out6[4] = bd[1]; out6[5] = bd[2];
+    if (!kept) { *margin = mg; return 0; }
+    int hit = 0;
+    double Dl = INFINITY;
+    if (op->depth_mode == ORC_DEPTH_EXACT) {
+        Dl = orc_exact_depth(t->kind, t->params, ol, dl, bd[0], bd[1], &hit);
+    } else if (op->depth_mode == ORC_DEPTH_MARCH) {
+        Dl = orc_march_depth(sc, sc->inst_type[inst], ol, dl, bd[0], bd[1], op->march_n, op->march_b, &hit);
+    } else {
+        /* Eq. 1: F_Phi(r) -> (mu, alpha); mu = l * m with l = rb (reading: the mu range [-l, l]
+         * is the bound sphere's).  Eq. 2: D = |o - p_perp| - mu with the signed t_perp. */
+        int dims[64], nl = nedf_dims(t, dims);
+        double y[2];
+        orc_mlp(t->nedf_w, nl, dims, feat, y, op->quant);
+        out6[1] = y[0];
+        out6[2] = y[1];
+        Dl = bd[2] - t->rb * y[0];
+        hit = (y[1] > 0.0) && (Dl > 0.0);
+        mg = dmin(mg, dmin(fabs(y[1]), fabs(Dl) / t->rb));
+        if (op->fallback_conf > 0.0) {
+            double pr = 1.0 / (1.0 + exp(-y[1]));
+            double conf = dmax(pr, 1.0 - pr);
+            mg = dmin(mg, fabs(conf - op->fallback_conf));
+            if (conf < op->fallback_conf)
+                Dl = orc_march_depth(sc, sc->inst_type[inst], ol, dl, bd[0], bd[1], op->march_n,
+                                     op->march_b, &hit);
+        }
+        if (hit && op->refine_steps > 0) {
+            /* Bisection of the density level set inside [D - h, D + h] when it brackets it. */
+            double lo = Dl - sc->shade_half, hi = Dl + sc->shade_half, x[3];
+            for (int c = 0; c < 3; ++c) x[c] = ol[c] + lo * dl[c];
+            int in_lo = inside_solid(sc, sc->inst_type[inst], x);
+            for (int c = 0; c < 3; ++c) x[c] = ol[c] + hi * dl[c];
+            int in_hi = inside_solid(sc, sc->inst_type[inst], x);
+            if (!in_lo && in_hi) {
+                for (int it = 0; it < op->refine_steps; ++it) {
+                    double mid = 0.5 * (lo + hi);
+                    for (int c = 0; c < 3; ++c) x[c] = ol[c] + mid * dl[c];
+                    if (inside_solid(sc, sc->inst_type[inst], x)) hi = mid; else lo = mid;
+                }
+                Dl = 0.5 * (lo + hi);
+                hit = Dl > 0.0;
+            }
+        }
+    }
+    out6[0] = Dl;
+    *margin = mg;
+    return hit;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Step 2: deferred shading (Eq. 8 with n samples in a window around the stored depth)          */
+/* ------------------------------------------------------------------------------------------ */
+void orc_composite_samples(int n, const double *sigma, const double *rgb, double world_delta, double rgba[4])
+{
+    double T = 1.0;
+    rgba[0] = rgba[1] = rgba[2] = rgba[3] = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double alpha = 1.0 - exp(-sigma[j] * world_delta);
+        for (int c = 0; c < 3; ++c) rgba[c] += T * alpha * rgb[3 * j + c];
+        rgba[3] += T * alpha;
+        T *= 1.0 - alpha;
+    }
+}
+
+static void sample_colour(const orc_type *t, const double x[3], const double dl[3], int quant, double rgb[3])
+{
+    if (t->nerf_hidden == 0) {
+        for (int c = 0; c < 3; ++c) rgb[c] = t->albedo[c];
+        return;
+    }
+    double feat[90], y[3];
+    int dims[64], nl = nerf_dims(t, dims);
+    orc_posenc(x, 3, 10, feat);
+    orc_posenc(dl, 3, 4, feat + 63);
+    orc_mlp(t->nerf_w, nl, dims, feat, y, quant);
+    for (int c = 0; c < 3; ++c) rgb[c] = 1.0 / (1.0 + exp(-y[c]));
+}
+
+static void shade_pixel(const orc_scene *sc, const orc_opts *op, const double o[3], const double d[3],
+                        int inst, double depth, double rgba[4])
+{
+    const orc_type *t = &sc->types[sc->inst_type[inst]];
+    double ol[3], dl[3], s = sc->inst_s[inst];
+    orc_to_local(sc, inst, o, d, ol, dl);
+    double Dl = depth / s, h = sc->shade_half;
+    int n = sc->n_shade;
+    double delta = 2.0 * h / n;
+    double *sig = (double *)malloc(sizeof(double) * n), *rgb = (double *)malloc(sizeof(double) * 3 * n);
+    for (int j = 0; j < n; ++j) {
+        double tj = Dl - h + (j + 0.5) * delta, x[3];
+        for (int c = 0; c < 3; ++c) x[c] = ol[c] + tj * dl[c];
+        sig[j] = orc_density(sc, sc->inst_type[inst], x);
+        sample_colour(t, x, dl, op->quant, rgb + 3 * j);
+    }
+    orc_composite_samples(n, sig, rgb, s * delta, rgba);
+    free(sig);
+    free(rgb);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Algorithm 1 (Steps 1-2) and Algorithm 2 (Step 3) for one pixel                               */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+    const orc_scene *sc;
+    const orc_opts *op;
+    const int64_t *px;
+    int64_t begin, end;
+    double *depth, *gap, *pmargin, *rgba, *shadow, *smargin, *out;
+    uint32_t *id;
+} render_job;
+
+static void render_one(const render_job *jb, int64_t k)
+{
+    const orc_scene *sc = jb->sc;
+    const orc_opts *op = jb->op;
+    int64_t p = jb->px[k];
+    int i = (int)(p % sc->W), j = (int)(p / sc->W);
+    double o[3], d[3], q[6], mg, best = INFINITY, second = INFINITY, pm = INFINITY;
+    uint32_t bid = 0xFFFFFFFFu;
+    orc_camera_ray(sc, i, j, o, d);
+    /* STEP 1: clear to infinity; visit models in id order; strict '<' keeps the lowest id on ties. */
+    for (int m = 0; m < sc->n_inst; ++m) {
+        int hit = orc_query(sc, op, m, o, d, q, &mg);
+        pm = dmin(pm, mg);
+        if (!hit) continue;
+        double D = sc->inst_s[m] * q[0];
+        if (D < best) { second = best; best = D; bid = (uint32_t)m; }
+        else if (D < second) second = D;
+    }
+    double rgba[4] = {0, 0, 0, 0}, S = 1.0, sm = INFINITY;
+    if (bid != 0xFFFFFFFFu) {
+        /* STEP 2: shade with the winning model's radiance field only. */
+        shade_pixel(sc, op, o, d, (int)bid, best, rgba);
+        /* STEP 3: x on the surface, shadow ray from each light towards x; an occluder hit
+         * closer to the light than x by more than eps darkens by beta; lights averaged. */
+        double x[3];
+        for (int c = 0; c < 3; ++c) x[c] = o[c] + best * d[c];
+        double acc = 0.0;
+        for (int l = 0; l < sc->n_lights; ++l) {
+            const double *L = sc->lights + 3 * l;
+            double v[3] = {x[0] - L[0], x[1] - L[1], x[2] - L[2]};
+            double ell = len3(v), dir[3] = {v[0] / ell, v[1] / ell, v[2] / ell};
+            int occluded = 0;
+            for (int m = 0; m < sc->n_inst; ++m) {
+                int hit = orc_query(sc, op, m, L, dir, q, &mg);
+                double s = sc->inst_s[m];
+                if (!(q[3] <= q[4]) || q[4] < 0.0) { sm = dmin(sm, mg); continue; } /* culled */
+                /* Reading: only bounds the shadow segment enters before x can occlude x. */
+                sm = dmin(sm, fabs(q[3] * s - ell));
+                if (!(q[3] * s < ell)) continue;
+                sm = dmin(sm, mg);
+                if (!hit) continue;
+                double Dk = s * q[0];
+                sm = dmin(sm, fabs(Dk + sc->eps - ell));
+                if (Dk + sc->eps < ell) occluded = 1;
+            }
+            acc += occluded ? sc->beta : 1.0;
+        }
+        S = acc / sc->n_lights;
+    }
+    jb->depth[k] = best;
+    jb->id[k] = bid;
+    if (jb->gap) jb->gap[k] = (bid != 0xFFFFFFFFu) ? second - best : INFINITY;
+    if (jb->pmargin) jb->pmargin[k] = pm;
+    if (jb->rgba) for (int c = 0; c < 4; ++c) jb->rgba[4 * k + c] = rgba[c];
+    if (jb->shadow) jb->shadow[k] = S;
+    if (jb->smargin) jb->smargin[k] = sm;
+    if (jb->out) {
+        for (int c = 0; c < 3; ++c) jb->out[4 * k + c] = rgba[c] * S;
+        jb->out[4 * k + 3] = rgba[3];
+    }
+}
+
+static void *render_worker(void *arg)
+{
+    const render_job *jb = (const render_job *)arg;
+    for (int64_t k = jb->begin; k < jb->end; ++k) render_one(jb, k);
+    return NULL;
+}
+
+int orc_render(const orc_scene *sc, const orc_opts *op, int64_t n_px, const int64_t *px, double *depth,
+               uint32_t *id, double *gap, double *pmargin, double *rgba, double *shadow, double *smargin,
+               double *out)
+{
+    int nt = op->n_threads > 1 ? op->n_threads : 1;
+    if (nt > 256) nt = 256;
+    render_job jobs[256];
+    pthread_t th[256];
+    for (int t = 0; t < nt; ++t) {
+        render_job jb = {sc, op, px, n_px * t / nt, n_px * (t + 1) / nt, depth, gap, pmargin, rgba,
+                         shadow, smargin, out, id};
+        jobs[t] = jb;
+    }
+    if (nt == 1) { render_worker(&jobs[0]); return 0; }
+    for (int t = 0; t < nt; ++t) pthread_create(&th[t], NULL, render_worker, &jobs[t]);
+    for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Plain method colour: every NeRF volume-rendered front to back (ordered by entry distance)    */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct { double te_world; int inst; } vr_pair;
+
+static int cmp_pair(const void *a, const void *b)
+{
+    const vr_pair *x = (const vr_pair *)a, *y = (const vr_pair *)b;
+    if (x->te_world < y->te_world) return -1;
+    if (x->te_world > y->te_world) return 1;
+    return x->inst - y->inst;
+}
+
+typedef struct {
+    const orc_scene *sc; const orc_opts *op; int ns; const int64_t *px; int64_t begin, end; double *rgba;
+} vr_job;
+
+static void *vr_worker(void *arg)
+{
+    const vr_job *jb = (const vr_job *)arg;
+    const orc_scene *sc = jb->sc;
+    vr_pair *pairs = (vr_pair *)malloc(sizeof(vr_pair) * (sc->n_inst > 0 ? sc->n_inst : 1));
+    for (int64_t k = jb->begin; k < jb->end; ++k) {
+        int64_t p = jb->px[k];
+        double o[3], d[3], ol[3], dl[3], bd[4];
+        orc_camera_ray(sc, (int)(p % sc->W), (int)(p / sc->W), o, d);
+        int np = 0;
+        for (int m = 0; m < sc->n_inst; ++m) {
+            orc_to_local(sc, m, o, d, ol, dl);
+            if (!orc_bound(ol, dl, sc->types[sc->inst_type[m]].rb, bd)) continue;
+            pairs[np].te_world = bd[0] * sc->inst_s[m];
+            pairs[np].inst = m;
+            ++np;
+        }
+        qsort(pairs, np, sizeof(vr_pair), cmp_pair);
+        double T = 1.0, C[3] = {0, 0, 0};
+        for (int q = 0; q < np; ++q) {
+            int m = pairs[q].inst;
+            const orc_type *t = &sc->types[sc->inst_type[m]];
+            double s = sc->inst_s[m];
+            orc_to_local(sc, m, o, d, ol, dl);
+            orc_bound(ol, dl, t->rb, bd);
+            double dt = (bd[1] - bd[0]) / jb->ns;
+            for (int j = 0; j < jb->ns; ++j) {
+                double tj = bd[0] + (j + 0.5) * dt, x[3], rgb[3];
+                for (int c = 0; c < 3; ++c) x[c] = ol[c] + tj * dl[c];
+                double alpha = 1.0 - exp(-orc_density(sc, sc->inst_type[m], x) * s * dt);
+                sample_colour(t, x, dl, jb->op->quant, rgb);
+                for (int c = 0; c < 3; ++c) C[c] += T * alpha * rgb[c];
+                T *= 1.0 - alpha;
+            }
+        }
+        for (int c = 0; c < 3; ++c) jb->rgba[4 * k + c] = C[c];
+        jb->rgba[4 * k + 3] = 1.0 - T;
+    }
+    free(pairs);
+    return NULL;
+}
+
+int orc_volume_render(const orc_scene *sc, const orc_opts *op, int n_samples, int64_t n_px,
+                      const int64_t *px, double *rgba)
+{
+    int nt = op->n_threads > 1 ? op->n_threads : 1;
+    if (nt > 256) nt = 256;
+    vr_job jobs[256];
+    pthread_t th[256];
+    for (int t = 0; t < nt; ++t) {
+        vr_job jb = {sc, op, n_samples, px, n_px * t / nt, n_px * (t + 1) / nt, rgba};
+        jobs[t] = jb;
+    }
+    if (nt == 1) { vr_worker(&jobs[0]); return 0; }
+    for (int t = 0; t < nt; ++t) pthread_create(&th[t], NULL, vr_worker, &jobs[t]);
+    for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Learned part: ray sampler, ray-march labels, loss and hand-derived gradient, Adam            */
+/* ------------------------------------------------------------------------------------------ */
+/* SplitMix64 (Steele, Lea & Flood 2014) in counter form: output `index` of the stream `seed`. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t index)
+{
+    uint64_t z = seed + (index + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static double u24(uint64_t seed, uint64_t index)
+{
+    return (double)(orc_splitmix64(seed, index) >> 40) * (1.0 / 16777216.0);
+}
+
+/* Ray r: entry point uniform on the bound sphere, direction cosine-weighted about the inward
+ * normal.  Draws 4r .. 4r+3.  The tangent frame is Duff et al. (JCGT 2017). */
+void orc_train_rays(double rb, uint64_t seed, int64_t first, int n, double *o, double *d)
+{
+    for (int k = 0; k < n; ++k) {
+        uint64_t r = (uint64_t)(first + k);
+        double u0 = u24(seed, 4 * r), u1 = u24(seed, 4 * r + 1), u2 = u24(seed, 4 * r + 2), u3 = u24(seed, 4 * r + 3);
+        double z = 1.0 - 2.0 * u0, phi = 2.0 * PI * u1, rho = sqrt(dmax(0.0, 1.0 - z * z));
+        double nrm[3] = {rho * cos(phi), rho * sin(phi), z};
+        double w[3] = {-nrm[0], -nrm[1], -nrm[2]};
+        double sg = w[2] >= 0.0 ? 1.0 : -1.0;
+        double a = -1.0 / (sg + w[2]), b = w[0] * w[1] * a;
+        double b1[3] = {1.0 + sg * w[0] * w[0] * a, sg * b, -sg * w[0]};
+        double b2[3] = {b, sg + w[1] * w[1] * a, -w[1]};
+        double rr = sqrt(u2), th = 2.0 * PI * u3;
+        double lx = rr * cos(th), ly = rr * sin(th), lz = sqrt(dmax(0.0, 1.0 - u2));
+        for (int c = 0; c < 3; ++c) {
+            o[3 * k + c] = rb * nrm[c];
+            d[3 * k + c] = lx * b1[c] + ly * b2[c] + lz * w[c];
+        }
+    }
+}
+
+/* Labels from the plain method: hit* = a crossing exists, m* = mu* / l, mu* = t_perp - D*
+ * (Eq. 2 inverted, as the paper converts NeRF depth to mu for supervision). */
+void orc_train_labels(const orc_scene *sc, int type, int n, const double *o, const double *d,
+                      int march_n, int march_b, double *m_star, int *hit_star)
+{
+    const orc_type *t = &sc->types[type];
+    for (int k = 0; k < n; ++k) {
+        double ol[3], dl[3], bd[4];
+        for (int c = 0; c < 3; ++c) { ol[c] = o[3 * k + c]; dl[c] = d[3 * k + c]; }
+        normalize3(dl);
+        m_star[k] = 0.0;
+        hit_star[k] = 0;
+        if (!orc_bound(ol, dl, t->rb, bd)) continue;
+        int hit;
+        double D = orc_march_depth(sc, type, ol, dl, bd[0], bd[1], march_n, march_b, &hit);
+        if (!hit) continue;
+        hit_star[k] = 1;
+        m_star[k] = (bd[2] - D) / t->rb;
+    }
+}
+
+/* Loss (regression form of Eq. 6, reading for a "depth + hit logit" network):
+ *   L = mean over labelled hits of (m - m*)^2 + 0.1 * mean over all rays of BCE(a, hit*).
+ * grad receives dL/dtheta in the packed layout.  Returns L. */
+double orc_nedf_loss_grad(const orc_scene *sc, int type, int n, const double *o, const double *d,
+                          const double *m_star, const int *hit_star, double *grad, int quant)
+{
+    const orc_type *t = &sc->types[type];
+    int dims[64], nl = nedf_dims(t, dims), maxd = 0;
+    for (int l = 0; l <= nl; ++l) maxd = dims[l] > maxd ? dims[l] : maxd;
+    size_t np = 0;
+    for (int l = 0; l < nl; ++l) np += (size_t)dims[l] * dims[l + 1] + dims[l + 1];
+    memset(grad, 0, sizeof(double) * np);
+    double *act = (double *)malloc(sizeof(double) * (nl + 1) * maxd);  /* layer inputs */
+    double *pre = (double *)malloc(sizeof(double) * (nl + 1) * maxd);  /* pre-activations */
+    double *dlt = (double *)malloc(sizeof(double) * maxd), *dnx = (double *)malloc(sizeof(double) * maxd);
+    int n_hit = 0;
+    for (int k = 0; k < n; ++k) n_hit += hit_star[k] != 0;
+    double loss = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double ol[3], dl[3], bd[4];
+        for (int c = 0; c < 3; ++c) { ol[c] = o[3 * k + c]; dl[c] = d[3 * k + c]; }
+        normalize3(dl);
+        if (!orc_nedf_features(ol, dl, t->rb, act, bd)) continue;
+        /* forward with saved activations */
+        const double *p = t->nedf_w;
+        for (int l = 0; l < nl; ++l) {
+            int fi = dims[l], fo = dims[l + 1];
+            for (int u = 0; u < fo; ++u) {
+                double acc = 0.0;
+                for (int i = 0; i < fi; ++i) {
+                    double wv = p[(size_t)u * fi + i], av = act[l * maxd + i];
+                    if (quant == ORC_QUANT_BF16) { wv = orc_round_bf16(wv); av = orc_round_bf16(av); }
+                    acc += wv * av;
+                }
+                acc += p[(size_t)fi * fo + u];
+                pre[(l + 1) * maxd + u] = acc;
+                act[(l + 1) * maxd + u] = (l + 1 < nl) ? dmax(acc, 0.0) : acc;
+            }
+            p += (size_t)fi * fo + fo;
+        }
+        double m = act[nl * maxd + 0], a = act[nl * maxd + 1];
+        double al = hit_star[k] ? 1.0 : 0.0;
+        double bce = dmax(a, 0.0) - al * a + log1p(exp(-fabs(a)));
+        loss += 0.1 * bce / n;
+        dlt[0] = 0.0;
+        if (hit_star[k]) {
+            loss += (m - m_star[k]) * (m - m_star[k]) / n_hit;
+            dlt[0] = 2.0 * (m - m_star[k]) / n_hit;
+        }
+        dlt[1] = 0.1 * (1.0 / (1.0 + exp(-a)) - al) / n;
+        /* backward: dW = delta x input^T, db = delta, d input = W^T delta masked by ReLU */
+        size_t off[64];
+        off[0] = 0;
+        for (int l = 0; l < nl; ++l) off[l + 1] = off[l] + (size_t)dims[l] * dims[l + 1] + dims[l + 1];
+        for (int l = nl - 1; l >= 0; --l) {
+            int fi = dims[l], fo = dims[l + 1];
+            const double *W = t->nedf_w + off[l];
+            double *gW = grad + off[l], *gb = grad + off[l] + (size_t)fi * fo;
+            for (int u = 0; u < fo; ++u) {
+                for (int i = 0; i < fi; ++i) {
+                    double av = act[l * maxd + i];
+                    if (quant == ORC_QUANT_BF16) av = orc_round_bf16(av);
+                    gW[(size_t)u * fi + i] += dlt[u] * av;
+                }
+                gb[u] += dlt[u];
+            }
+            if (l == 0) break;
+            for (int i = 0; i < fi; ++i) {
+                double acc = 0.0;
+                for (int u = 0; u < fo; ++u) {
+                    double wv = W[(size_t)u * fi + i];
+                    if (quant == ORC_QUANT_BF16) wv = orc_round_bf16(wv);
+                    acc += wv * dlt[u];
+                }
+                dnx[i] = pre[l * maxd + i] > 0.0 ? acc : 0.0;
+            }
+            memcpy(dlt, dnx, sizeof(double) * fi);
+        }
+    }
+    free(act); free(pre); free(dlt); free(dnx);
+    return loss;
+}
+
+/* Adam (Kingma & Ba 2015) with bias correction; t counts from 1. */
+void orc_adam(int64_t n, double *theta, const double *g, double *m, double *v, int t, double lr,
+              double b1, double b2, double eps)
+{
+    double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+    for (int64_t i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        theta[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+}

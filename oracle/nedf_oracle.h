@@ -1,0 +1,115 @@
+/* FP64 CPU oracle of the NeDF composition render path (arXiv 2308.04669).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA path; it is never part of it.
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference leg may load it.
+ * It shares no code, header, table or helper with the CUDA library.
+ *
+ * Conventions (inputs are produced by the seeded generator, rounded to float32, then widened):
+ *   - An object type is an analytic signed-distance shape inside a bound sphere of radius rb,
+ *     with density sigma(x) = sigma_max / (1 + exp(sdf(x) / sdf_width)).
+ *   - An instance maps local q to world v = s * R * q + T (R row-major 3x3).  Section
+ *     "Manipulating Objects": rays, not sample points, are taken into the local frame.
+ *   - A packed MLP holds, layer after layer, W[out][in] row-major then b[out].  Hidden layers
+ *     use ReLU, the last layer is linear.
+ *   - Pixel p = j * W + i (row j from the top).
+ */
+#ifndef NEDF_ORACLE_H
+#define NEDF_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_SPHERE = 0, ORC_TORUS, ORC_BOX, ORC_CAPSULE, ORC_ROUNDCONE, ORC_TWOSPHERE,
+       ORC_TWISTTORUS, ORC_OCTA };
+enum { ORC_DEPTH_MLP = 0, ORC_DEPTH_EXACT = 1, ORC_DEPTH_MARCH = 2 };
+enum { ORC_QUANT_NONE = 0, ORC_QUANT_BF16 = 1 };
+
+typedef struct {
+    int kind;
+    double params[8];
+    double rb;
+    double albedo[3];
+    int nedf_hidden, nedf_width;
+    const double *nedf_w;
+    int nerf_hidden, nerf_width; /* nerf_hidden == 0: constant albedo colour */
+    const double *nerf_w;
+} orc_type;
+
+typedef struct {
+    int W, H;
+    double eye[3], target[3], fov_deg;
+    int n_lights;
+    const double *lights; /* [n_lights][3] */
+    int n_types;
+    const orc_type *types;
+    int n_inst;
+    const int *inst_type;
+    const double *inst_R; /* [n][9] */
+    const double *inst_T; /* [n][3] */
+    const double *inst_s; /* [n] */
+    int n_shade;
+    double shade_half, beta, eps, sigma_max, sdf_width;
+} orc_scene;
+
+typedef struct {
+    int depth_mode;        /* ORC_DEPTH_* */
+    int march_n, march_b;  /* MARCH mode, and the fallback march */
+    int quant;             /* ORC_QUANT_*: rounding applied to every layer's operands */
+    double fallback_conf;  /* MLP mode: march the pair when max(p,1-p) < this (0 = never) */
+    int refine_steps;      /* MLP mode: density bisection steps around the NeDF depth (0 = off) */
+    int n_threads;
+} orc_opts;
+
+/* Geometry and encoding */
+double orc_sdf(int kind, const double *params, const double x[3]);
+double orc_density(const orc_scene *sc, int type, const double x[3]);
+void orc_camera_ray(const orc_scene *sc, int i, int j, double o[3], double d[3]);
+void orc_to_local(const orc_scene *sc, int inst, const double o[3], const double d[3],
+                  double ol[3], double dl[3]);
+int orc_bound(const double ol[3], const double dl[3], double rb, double out4[4]);
+int orc_posenc(const double *x, int n, int n_freq, double *out);
+int orc_nedf_features(const double ol[3], const double dl[3], double rb, double *feat78,
+                      double out4[4]);
+
+/* Networks */
+void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant);
+double orc_round_bf16(double x);
+
+/* One (ray, instance) query: returns 1 on hit; out6 = {Dl, m, a, te, tx, tperp} */
+int orc_query(const orc_scene *sc, const orc_opts *op, int inst, const double o[3],
+              const double d[3], double out6[6], double *margin);
+double orc_exact_depth(int kind, const double *params, const double ol[3], const double dl[3],
+                       double te, double tx, int *hit);
+double orc_march_depth(const orc_scene *sc, int type, const double ol[3], const double dl[3],
+                       double te, double tx, int n, int b, int *hit);
+
+/* Shading quadrature over n samples (Eq. 8 with the sample window): rgba = (sum T a c, sum T a) */
+void orc_composite_samples(int n, const double *sigma, const double *rgb, double world_delta,
+                           double rgba[4]);
+
+/* Steps 1-3 of Algorithm 1 / Algorithm 2 for a list of pixels. */
+int orc_render(const orc_scene *sc, const orc_opts *op, int64_t n_px, const int64_t *px,
+               double *depth, uint32_t *id, double *gap, double *pmargin, double *rgba,
+               double *shadow, double *smargin, double *out);
+
+/* Plain method: dense front-to-back volume rendering with n samples per (ray, instance). */
+int orc_volume_render(const orc_scene *sc, const orc_opts *op, int n_samples, int64_t n_px,
+                      const int64_t *px, double *rgba);
+
+/* Learned part */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t index);
+void orc_train_rays(double rb, uint64_t seed, int64_t first, int n, double *o, double *d);
+void orc_train_labels(const orc_scene *sc, int type, int n, const double *o, const double *d,
+                      int march_n, int march_b, double *m_star, int *hit_star);
+double orc_nedf_loss_grad(const orc_scene *sc, int type, int n, const double *o, const double *d,
+                          const double *m_star, const int *hit_star, double *grad, int quant);
+void orc_adam(int64_t n, double *theta, const double *g, double *m, double *v, int t, double lr,
+              double b1, double b2, double eps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
