@@ -1,0 +1,280 @@
+/* nedf_compose.h -- C ABI of the GB300 (sm_103a) NeDF composition renderer.
+ *
+ * Method: arXiv 2308.04669, "A General Implicit Framework for Fast NeRF Composition and
+ * Rendering".  One render call runs the paper's three render-time steps on one GPU:
+ *   Step 1, NeDF generation (Algorithm 1, first half; Eq. 1, 2, 7): every pixel ray is taken
+ *     into each instance's local frame, culled against the instance's bound sphere and answered
+ *     by the type's Neural Depth Field network; a per-pixel minimum fills the depth and ID
+ *     buffers.
+ *   Step 2, deferred shading (Algorithm 1, second half; Eq. 8): only the winning instance's
+ *     radiance field is evaluated, at samples bracketing the stored depth, into the colour
+ *     buffer.
+ *   Step 3, shadows (Algorithm 2): shadow rays from each point light towards the surface point
+ *     are answered by NeDF queries into a shadow buffer that multiplies the colour.
+ * The learned part (Section "Intersection network", Eq. 5-6, "Training details") trains each
+ * type's NeDF on depth / hit labels that the plain ray-marching method computes on the device.
+ *
+ * Conventions shared by every call:
+ *   - All calls return NEDF_OK (0) or a negative NEDF_ERR_* code and never throw.  The text of
+ *     the last error is available from nedf_compose_last_error().
+ *   - A handle is bound to one CUDA stream (given at create) and is not thread safe.
+ *   - "host" pointers point to ordinary CPU memory; "device" pointers to memory of the GPU that
+ *     was current at create.  Unless stated otherwise the caller owns every buffer it passes;
+ *     the library copies what it keeps and owns all of its own workspace.
+ *   - Device work is asynchronous on the handle's stream.  Errors found by kernels (a full work
+ *     list, a wait that gave up) are recorded in a device status word and returned by the next
+ *     nedf_compose_sync() (and by any call that synchronises).
+ *   - Images are row-major, pixel p = j * width + i with row j = 0 at the top.
+ *   - Instance i of the last set_instances() call has id i (Algorithm 1's unique model id).
+ *   - Packed MLP weights (float32): for each layer in order, W[out][in] row-major, then b[out].
+ *     Hidden layers use ReLU, the output layer is linear.
+ *       NeDF dims: [78, nedf_width x nedf_hidden, 2]  input = 6-frequency encoding of
+ *                  (entry point on the bound sphere, local direction); outputs (m, a) with
+ *                  mu = rb * m (Eq. 1) and hit logit a.
+ *       NeRF dims: [90, nerf_width x nerf_hidden, 3]  input = [10-frequency encoding of the
+ *                  local position (63), 4-frequency encoding of the local direction (27)];
+ *                  outputs are RGB logits (sigmoid applied).
+ */
+#ifndef NEDF_COMPOSE_H
+#define NEDF_COMPOSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------------------------- */
+#define NEDF_OK 0
+#define NEDF_ERR_ARG (-1)          /* invalid argument (null, out of range, non-finite)          */
+#define NEDF_ERR_CUDA (-2)         /* a CUDA runtime call failed                                 */
+#define NEDF_ERR_OOM (-3)          /* device allocation failed                                   */
+#define NEDF_ERR_UNSUPPORTED (-4)  /* configuration this build does not implement                */
+#define NEDF_ERR_CAPACITY (-5)     /* a device work list overflowed; the frame is incomplete     */
+#define NEDF_ERR_TIMEOUT (-6)      /* a bounded device wait gave up                              */
+#define NEDF_ERR_STATE (-7)        /* call out of order (e.g. render before set_types)           */
+
+#define NEDF_MAX_LIGHTS 32
+#define NEDF_MAX_TYPES 64
+
+/* ---- enums --------------------------------------------------------------------------------- */
+enum nedf_precision {       /* arithmetic of the NeDF and NeRF layers (accumulation is FP32)   */
+    NEDF_PREC_FP32 = 0,
+    NEDF_PREC_BF16 = 1
+};
+enum nedf_depth_source {    /* what answers the (ray, instance) depth queries of Steps 1 and 3 */
+    NEDF_DEPTH_NEDF = 0,    /* the Neural Depth Field (the method)                             */
+    NEDF_DEPTH_MARCH = 1    /* the plain method: density ray-marching plus bisection           */
+};
+enum nedf_sdf_kind {        /* analytic object densities sigma = sigma_max * sigmoid(-sdf/w)   */
+    NEDF_SDF_SPHERE = 0,    /* params: radius                                                  */
+    NEDF_SDF_TORUS = 1,     /* params: R, r (ring in the xz plane)                             */
+    NEDF_SDF_BOX = 2,       /* params: half extents x, y, z                                    */
+    NEDF_SDF_CAPSULE = 3,   /* params: half length (y), radius                                 */
+    NEDF_SDF_ROUNDCONE = 4, /* params: r1, y1, r2, y2                                          */
+    NEDF_SDF_TWOSPHERE = 5, /* params: centre offset along x, radius                           */
+    NEDF_SDF_TWISTTORUS = 6,/* params: R, r (ring in the xy plane), twist rad per unit y       */
+    NEDF_SDF_OCTA = 7       /* params: a in |x|+|y|+|z| = a                                    */
+};
+
+/* ---- records ------------------------------------------------------------------------------- */
+typedef struct nedf_config {
+    int width, height;             /* framebuffer size, 1 .. 16384 each                         */
+    int max_instances;             /* capacity of set_instances()                               */
+    int max_types;                 /* capacity of set_types(), <= NEDF_MAX_TYPES                */
+    int nedf_hidden, nedf_width;   /* NeDF shape shared by all types: hidden layers, width      */
+    int nerf_hidden, nerf_width;   /* NeRF shape shared by all types; nerf_hidden = 0 means a   */
+                                   /* constant albedo per type instead of a colour network      */
+    int precision;                 /* enum nedf_precision                                       */
+    int64_t primary_pair_capacity; /* (ray, instance) pairs of Step 1; 0 = 8 * width * height   */
+    int64_t shadow_pair_capacity;  /* pairs of Step 3; 0 = 4 * width * height * NEDF_MAX_LIGHTS/8 */
+} nedf_config;
+
+typedef struct nedf_options {
+    int n_shade;             /* samples per pixel in Step 2 (1 .. 32); default 8                */
+    float shade_half;        /* half width h of the sample window, object-local; default 0.05   */
+    float shadow_beta;       /* darkening factor beta of Algorithm 2, (0,1); default 0.5        */
+    float shadow_eps;        /* epsilon of Algorithm 2's test D + eps < |L - x|, world; 0.02    */
+    float sigma_max;         /* peak density of the analytic objects; default 50                */
+    float sdf_width;         /* width w of the density's sigmoid; default 0.01                  */
+    int depth_source;        /* enum nedf_depth_source; default NEDF_DEPTH_NEDF                 */
+    int march_steps;         /* plain method: uniform steps over the bound chord; default 128   */
+    int march_bisect;        /* plain method: bisection steps after the crossing; default 4     */
+    float fallback_conf;     /* NeDF pairs with max(p, 1-p) < this (p = sigmoid(a)) are         */
+                             /* re-answered by the plain method; 0 disables; default 0          */
+    int refine_steps;        /* density bisection steps in [D - h, D + h] after a NeDF hit; 0   */
+} nedf_options;
+
+typedef struct nedf_type_desc {
+    int sdf_kind;                  /* enum nedf_sdf_kind                                        */
+    float sdf_params[8];           /* shape parameters, unused entries ignored                  */
+    float rb;                      /* bound-sphere radius l (object-local); mu in [-l, l]        */
+    float albedo[3];               /* colour when nerf_hidden == 0                              */
+    const float *nedf_weights;     /* host, packed NeDF weights (copied)                        */
+    const float *nerf_weights;     /* host, packed NeRF weights (copied); NULL iff nerf_hidden==0 */
+} nedf_type_desc;
+
+typedef struct nedf_instance {
+    uint32_t type;                 /* index into the types of set_types()                       */
+    float R[9];                    /* rotation, row-major: world = s * R * local + T (Eq. 7's G) */
+    float T[3];                    /* translation                                               */
+    float s;                       /* uniform scale, > 0                                        */
+} nedf_instance;
+
+typedef struct nedf_camera {
+    float eye[3];                  /* pinhole position (all primary rays start here)            */
+    float target[3];               /* look-at point; up is +y                                   */
+    float fov_y_deg;               /* vertical field of view, (0, 180)                          */
+} nedf_camera;
+
+typedef struct nedf_light {
+    float pos[3];                  /* point-light position, world                               */
+} nedf_light;
+
+typedef struct nedf_frame_stats {
+    int64_t primary_pairs;         /* (pixel ray, instance) pairs that survived the bound cull  */
+    int64_t shadow_pairs;          /* (shadow ray, instance) pairs queried                      */
+    int64_t hit_pixels;            /* pixels with a valid id                                    */
+    int64_t fallback_pairs;        /* pairs re-answered by the plain method                     */
+    int64_t kernel_launches;       /* kernels this library launched for the frame               */
+    uint32_t status;               /* device status bits (0 = clean)                            */
+} nedf_frame_stats;
+
+typedef struct nedf_handle nedf_handle;
+
+/* ---- lifecycle ----------------------------------------------------------------------------- */
+
+/* Creates a renderer for `cfg` on `cuda_stream` (a cudaStream_t; NULL = the legacy default
+ * stream) on the current device and allocates all workspace.  *out receives the handle.
+ * Errors: NEDF_ERR_ARG (bad sizes, null), NEDF_ERR_UNSUPPORTED (shape or precision this
+ * build lacks), NEDF_ERR_OOM, NEDF_ERR_CUDA. */
+int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle **out);
+
+/* Frees everything the handle owns.  Synchronises its stream first.  NULL is a no-op. */
+void nedf_compose_destroy(nedf_handle *h);
+
+/* Text of the last error on this handle ("" if none); valid until the next call.  With
+ * h == NULL, the last error of a failed nedf_compose_create on this thread. */
+const char *nedf_compose_last_error(const nedf_handle *h);
+
+/* Replaces the rendering options (host struct, copied).  Defaults are set at create. */
+int nedf_compose_set_options(nedf_handle *h, const nedf_options *opt);
+int nedf_compose_get_options(const nedf_handle *h, nedf_options *opt);
+
+/* Waits for the handle's stream and returns the first recorded device status as an error code
+ * (NEDF_ERR_CAPACITY, NEDF_ERR_TIMEOUT), clearing it; NEDF_OK if clean. */
+int nedf_compose_sync(nedf_handle *h);
+
+/* ---- scene --------------------------------------------------------------------------------- */
+
+/* Object types (Section "Manipulating Objects": instances of a type share its NeDF and NeRF
+ * weights).  `types` is a host array of n_types records; every pointed-to weight array is
+ * copied, converted to the configured precision and laid out for the kernels.  Resets the
+ * training state of every type.  Errors: NEDF_ERR_ARG (n_types out of range, unknown kind,
+ * rb <= 0, missing weights), NEDF_ERR_CUDA. */
+int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *types);
+
+/* Instances (Section "Manipulating Objects", Eq. 7: each model is a type placed by a rigid
+ * transform G(R, T, s)).  `inst` is a host array of n records, copied.  The id of instance i
+ * is i.  Errors: NEDF_ERR_ARG for n > max_instances, a type index >= n_types, s <= 0 or any
+ * non-finite number (nothing is changed then). */
+int nedf_compose_set_instances(nedf_handle *h, int n, const nedf_instance *inst);
+
+/* ---- render -------------------------------------------------------------------------------- */
+
+/* One frame: Steps 1-3 and the composite.  cam and lights are host records (n_lights in
+ * 1 .. NEDF_MAX_LIGHTS).  Output buffers are caller-owned DEVICE arrays of width*height
+ * elements (rgba and out: 4 floats per pixel):
+ *   depth   float  Step 1 depth buffer: world distance along the unit pixel ray, +inf if empty
+ *   id      uint32 Step 1 id buffer: winning instance index, 0xFFFFFFFF if empty
+ *   rgba    float4 Step 2 colour buffer (premultiplied RGB, opacity), (0,0,0,0) if empty
+ *   shadow  float  Step 3 shadow buffer: mean over lights of (occluded ? beta : 1); 1 if empty
+ *   out     float4 composite: (rgba.rgb * shadow, rgba.a)
+ * Any of depth / id / rgba / shadow / out may be NULL (the library then keeps its own copy).
+ * stats (host) may be NULL; when given, the call synchronises and fills it.
+ * Ties in depth go to the lowest instance id (Algorithm 1's strict '<' in id order).
+ * Errors: NEDF_ERR_STATE (no types or instances yet), NEDF_ERR_ARG, NEDF_ERR_CUDA, and with
+ * stats given NEDF_ERR_CAPACITY when a pair list overflowed. */
+int nedf_compose_render(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights,
+                        int n_lights, float *depth, uint32_t *id, float *rgba, float *shadow,
+                        float *out, nedf_frame_stats *stats);
+
+/* The same frame written to HOST buffers (any may be NULL): the library renders into its own
+ * device buffers, copies the requested ones to the host and synchronises. */
+int nedf_compose_render_host(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights,
+                             int n_lights, float *depth, uint32_t *id, float *rgba, float *shadow,
+                             float *out, nedf_frame_stats *stats);
+
+/* Plain method colour (the baseline of the paper's speed comparison, Section "Storage and
+ * Speed"): every (pixel ray, instance) pair that survives the bound cull is volume rendered
+ * with n_samples midpoint samples of its NeRF over the bound chord, pairs composited front to
+ * back by entry distance.  rgba: caller-owned device float4[width*height].  With
+ * early_stop != 0, a ray stops once its transmittance is below 1e-4 and colour networks are
+ * skipped where the sample weight is below 1e-6. */
+int nedf_compose_render_march(nedf_handle *h, const nedf_camera *cam, int n_samples,
+                              int early_stop, float *rgba);
+
+/* ---- per-stage timing (the per-step breakdown of the paper's Fig. 5) ----------------------- */
+
+#define NEDF_N_STAGES 8
+/* Stage i of a frame: 0 setup and clear, 1 Step-1 binning, 2 Step-1 NeDF, 3 Step-1 resolve
+ * (z-min to buffers), 4 Step-2 shading, 5 Step-3 binning, 6 Step-3 NeDF, 7 composite. */
+const char *nedf_compose_stage_name(int stage);
+
+/* on != 0: every later render records CUDA events between its stages on the handle's stream.
+ * Costs a few microseconds per frame; off by default. */
+int nedf_compose_set_profiling(nedf_handle *h, int on);
+
+/* Device milliseconds of each stage of the last profiled render (synchronises).  ms is a host
+ * array of n >= NEDF_N_STAGES floats.  Errors: NEDF_ERR_STATE when nothing was profiled. */
+int nedf_compose_get_stage_times(nedf_handle *h, float *ms, int n);
+
+/* ---- kernels in isolation (for tests and tools) ------------------------------------------- */
+
+/* NeDF queries on n arbitrary object-local rays of one type (Eq. 1-2): o, d are device
+ * float[n][3] (d need not be unit).  out is device float[n][4] = (m, a, D_local, hit) with
+ * D_local = t_perp - rb * m and hit = (a > 0 && D_local > 0); culled rays give (0, 0, +inf, 0). */
+int nedf_compose_nedf_query(nedf_handle *h, int type, int n, const float *o, const float *d,
+                            float *out);
+
+/* ---- learned part -------------------------------------------------------------------------- */
+
+/* Builds the training set of one type on the device: n_rays rays with entry points uniform on
+ * the bound sphere and directions cosine-weighted about the inward normal (counter-based
+ * SplitMix64 draws 4r .. 4r+3 of `seed` for ray r), labelled by the plain method
+ * (march_steps uniform steps, march_bisect bisection steps): hit* and m* = (t_perp - D*) / rb
+ * (Eq. 2 inverted, Eq. 5's depth replaced by the half-density crossing).  Optional device
+ * outputs (each may be NULL): o, d float[n][3], m_star float[n], hit_star float[n]. */
+int nedf_compose_make_labels(nedf_handle *h, int type, int64_t n_rays, uint64_t seed,
+                             int march_steps, int march_bisect, float *o, float *d,
+                             float *m_star, float *hit_star);
+
+/* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) of the type's NeDF on `batch`
+ * consecutive rays of its training set (wrapping around), starting where the previous step
+ * ended.  Loss (regression form of Eq. 6): mean over labelled hits of (m - m*)^2 plus
+ * 0.1 * mean BCE(a, hit*).  FP32 master weights and moments; the rendering copy is refreshed.
+ * loss_host (host float, may be NULL) receives the loss of this batch; giving it synchronises.
+ * Errors: NEDF_ERR_STATE (no training set for the type), NEDF_ERR_ARG. */
+int nedf_compose_train_step(nedf_handle *h, int type, int batch, float lr, float *loss_host);
+
+/* Loss and gradient of the type's current NeDF weights on n caller rays / labels (all device:
+ * o, d float[n][3], m_star, hit_star float[n]); grad is device float[n_params] in the packed
+ * layout.  loss_host may be NULL.  Synchronises. */
+int nedf_compose_loss_grad(nedf_handle *h, int type, int n, const float *o, const float *d,
+                           const float *m_star, const float *hit_star, float *grad,
+                           float *loss_host);
+
+/* Copies the type's current FP32 NeDF weights (packed layout) to host memory. */
+int nedf_compose_get_nedf_weights(nedf_handle *h, int type, float *host_out, int64_t n_floats);
+
+/* Training state of every type (weights, Adam moments, step counts) as one little-endian blob.
+ * save: with buf == NULL only *size is set; otherwise *size is the capacity in bytes.
+ * load: the blob must come from a handle with the same config and types. */
+int nedf_compose_save_state(nedf_handle *h, void *buf, size_t *size);
+int nedf_compose_load_state(nedf_handle *h, const void *buf, size_t size);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NEDF_COMPOSE_H */

@@ -1,0 +1,699 @@
+// C-ABI entry points of libnedf_compose (declared in include/nedf_compose.h).
+//
+// Host side of the renderer: argument checks, ownership of device workspace, weight layout
+// conversion, and the launch sequence of each call.  All arithmetic of the method runs in the
+// kernels; this file only moves and validates data.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nedf_compose.h"
+#include "render_launch.h"
+#include "train_launch.h"
+
+using namespace nedf;
+
+struct TrainState {
+    float *o = nullptr, *d = nullptr, *m_star = nullptr, *hit_star = nullptr;  // training set
+    long long n_rays = 0;
+    long long cursor = 0;
+    float *master = nullptr;   // packed FP32 weights (W[out][in], b)
+    float *adam_m = nullptr, *adam_v = nullptr;
+    int step = 0;
+};
+
+struct nedf_handle {
+    nedf_config cfg{};
+    nedf_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    std::string err;
+    int n_types = 0, n_inst = 0;
+    long long nedf_params = 0, nerf_params = 0;
+    // device memory
+    DevFrame *d_frame = nullptr;
+    HostCamera *d_cam = nullptr;
+    DevFrame *h_frame = nullptr;     // pinned staging
+    HostCamera *h_cam = nullptr;     // pinned staging
+    DevType *d_types = nullptr;
+    DevInst *d_inst = nullptr;
+    float *d_nedf_w = nullptr, *d_nerf_w = nullptr;
+    unsigned long long *d_keys = nullptr;
+    float *d_depth = nullptr, *d_shadow = nullptr;
+    uint32_t *d_id = nullptr, *d_occl = nullptr, *d_hlist = nullptr, *d_status = nullptr;
+    float4 *d_rgba = nullptr, *d_out = nullptr;
+    uint2 *d_ppairs = nullptr, *d_spairs = nullptr;
+    Counters *d_cnt = nullptr;
+    float *d_train_scratch = nullptr;
+    size_t train_scratch_bytes = 0;
+    float *d_loss = nullptr;
+    std::vector<TrainState> train;
+    std::vector<DevType> types_host;
+    bool profiling = false, profiled = false;
+    cudaEvent_t ev[kStages + 1] = {};
+    int last_launches = 0;
+};
+
+static thread_local std::string g_create_error;
+
+static int fail(nedf_handle *h, int code, const std::string &msg)
+{
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+static int cuda_fail(nedf_handle *h, cudaError_t e, const char *what)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? NEDF_ERR_OOM : NEDF_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                                   \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);      \
+    } while (0)
+
+static long long mlp_params(int n_in, int hidden, int width, int n_out)
+{
+    if (hidden <= 0) return 0;
+    long long p = (long long)n_in * width + width;
+    p += (long long)(hidden - 1) * ((long long)width * width + width);
+    p += (long long)width * n_out + n_out;
+    return p;
+}
+
+// packed W[out][in], b  ->  per layer Wt[in][out], b (the SIMT kernels' layout)
+static void to_kernel_layout(const float *src, float *dst, int n_in, int hidden, int width, int n_out)
+{
+    std::vector<int> dims;
+    dims.push_back(n_in);
+    for (int l = 0; l < hidden; ++l) dims.push_back(width);
+    dims.push_back(n_out);
+    size_t off = 0;
+    for (size_t l = 0; l + 1 < dims.size(); ++l) {
+        int fi = dims[l], fo = dims[l + 1];
+        for (int o = 0; o < fo; ++o)
+            for (int i = 0; i < fi; ++i) dst[off + (size_t)i * fo + o] = src[off + (size_t)o * fi + i];
+        for (int o = 0; o < fo; ++o) dst[off + (size_t)fi * fo + o] = src[off + (size_t)fi * fo + o];
+        off += (size_t)fi * fo + fo;
+    }
+}
+
+static Workspace make_ws(nedf_handle *h)
+{
+    Workspace ws{};
+    ws.frame = h->d_frame;
+    ws.types = h->d_types;
+    ws.inst = h->d_inst;
+    ws.keys = h->d_keys;
+    ws.depth = h->d_depth;
+    ws.id = h->d_id;
+    ws.rgba = h->d_rgba;
+    ws.shadow = h->d_shadow;
+    ws.out = h->d_out;
+    ws.occl = h->d_occl;
+    ws.ppairs = h->d_ppairs;
+    ws.pcap = h->cfg.primary_pair_capacity;
+    ws.spairs = h->d_spairs;
+    ws.scap = h->cfg.shadow_pair_capacity;
+    ws.hlist = h->d_hlist;
+    ws.cnt = h->d_cnt;
+    ws.status = h->d_status;
+    ws.nedf_w = h->d_nedf_w;
+    ws.nedf_stride = h->nedf_params;
+    ws.nerf_w = h->d_nerf_w;
+    ws.nerf_stride = h->nerf_params;
+    ws.nedf_hidden = h->cfg.nedf_hidden;
+    ws.nedf_width = h->cfg.nedf_width;
+    ws.nerf_hidden = h->cfg.nerf_hidden;
+    ws.nerf_width = h->cfg.nerf_width;
+    return ws;
+}
+
+static bool finite3(const float *v, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+extern "C" {
+
+const char *nedf_compose_last_error(const nedf_handle *h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle **out)
+{
+    if (!cfg || !out) return fail(nullptr, NEDF_ERR_ARG, "null argument");
+    *out = nullptr;
+    const nedf_config &c = *cfg;
+    if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384)
+        return fail(nullptr, NEDF_ERR_ARG, "width/height out of range");
+    if (c.max_instances < 1 || c.max_types < 1 || c.max_types > NEDF_MAX_TYPES)
+        return fail(nullptr, NEDF_ERR_ARG, "max_instances/max_types out of range");
+    if (c.nedf_hidden < 1 || c.nedf_hidden > 16 || (c.nedf_width != 64 && c.nedf_width != 128 && c.nedf_width != 256))
+        return fail(nullptr, NEDF_ERR_UNSUPPORTED, "NeDF shape: hidden 1..16, width 64/128/256");
+    if (c.nerf_hidden < 0 || c.nerf_hidden > 16 ||
+        (c.nerf_hidden > 0 && c.nerf_width != 64 && c.nerf_width != 128 && c.nerf_width != 256))
+        return fail(nullptr, NEDF_ERR_UNSUPPORTED, "NeRF shape: hidden 0..16, width 64/128/256");
+    if (c.precision != NEDF_PREC_FP32 && c.precision != NEDF_PREC_BF16)
+        return fail(nullptr, NEDF_ERR_UNSUPPORTED, "precision");
+    if (c.primary_pair_capacity < 0 || c.shadow_pair_capacity < 0)
+        return fail(nullptr, NEDF_ERR_ARG, "negative capacity");
+
+    nedf_handle *h = new nedf_handle();
+    h->cfg = c;
+    long long npix = (long long)c.width * c.height;
+    if (h->cfg.primary_pair_capacity == 0) h->cfg.primary_pair_capacity = 8 * npix;
+    if (h->cfg.shadow_pair_capacity == 0) h->cfg.shadow_pair_capacity = 4 * npix * NEDF_MAX_LIGHTS / 8;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->opt = nedf_options{8, 0.05f, 0.5f, 0.02f, 50.0f, 0.01f, NEDF_DEPTH_NEDF, 128, 4, 0.0f, 0};
+    h->nedf_params = mlp_params(kNedfIn, c.nedf_hidden, c.nedf_width, 2);
+    h->nerf_params = mlp_params(kNerfIn, c.nerf_hidden, c.nerf_width, 3);
+    auto bail = [&](cudaError_t e, const char *what) {
+        int code = e == cudaErrorMemoryAllocation ? NEDF_ERR_OOM : NEDF_ERR_CUDA;
+        g_create_error = std::string(what) + ": " + cudaGetErrorString(e);
+        nedf_compose_destroy(h);
+        return code;
+    };
+    cudaError_t e;
+#define CA(ptr, bytes)                                                   \
+    do {                                                                 \
+        e = cudaMalloc((void **)&(ptr), (bytes));                        \
+        if (e != cudaSuccess) return bail(e, "cudaMalloc " #ptr);        \
+    } while (0)
+    if ((e = cudaGetDevice(&h->device)) != cudaSuccess) return bail(e, "cudaGetDevice");
+    if ((e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess)
+        return bail(e, "cudaDeviceGetAttribute");
+    CA(h->d_frame, sizeof(DevFrame));
+    CA(h->d_cam, sizeof(HostCamera));
+    if ((e = cudaMallocHost((void **)&h->h_frame, sizeof(DevFrame))) != cudaSuccess) return bail(e, "cudaMallocHost");
+    if ((e = cudaMallocHost((void **)&h->h_cam, sizeof(HostCamera))) != cudaSuccess) return bail(e, "cudaMallocHost");
+    CA(h->d_types, sizeof(DevType) * c.max_types);
+    CA(h->d_inst, sizeof(DevInst) * c.max_instances);
+    CA(h->d_nedf_w, sizeof(float) * h->nedf_params * c.max_types);
+    if (h->nerf_params) CA(h->d_nerf_w, sizeof(float) * h->nerf_params * c.max_types);
+    CA(h->d_keys, sizeof(unsigned long long) * npix);
+    CA(h->d_depth, sizeof(float) * npix);
+    CA(h->d_shadow, sizeof(float) * npix);
+    CA(h->d_id, sizeof(uint32_t) * npix);
+    CA(h->d_occl, sizeof(uint32_t) * npix);
+    CA(h->d_hlist, sizeof(uint32_t) * npix * c.max_types);
+    CA(h->d_rgba, sizeof(float4) * npix);
+    CA(h->d_out, sizeof(float4) * npix);
+    CA(h->d_ppairs, sizeof(uint2) * h->cfg.primary_pair_capacity);
+    CA(h->d_spairs, sizeof(uint2) * h->cfg.shadow_pair_capacity);
+    CA(h->d_cnt, sizeof(Counters));
+    CA(h->d_status, sizeof(uint32_t));
+    CA(h->d_loss, sizeof(float) * 4);
+#undef CA
+    if ((e = cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), h->stream)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemsetAsync(h->d_cnt, 0, sizeof(Counters), h->stream)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(e, "sync");
+    h->train.resize(c.max_types);
+    *out = h;
+    return NEDF_OK;
+}
+
+void nedf_compose_destroy(nedf_handle *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    void *dev[] = {h->d_frame, h->d_cam, h->d_types, h->d_inst, h->d_nedf_w, h->d_nerf_w, h->d_keys,
+                   h->d_depth, h->d_shadow, h->d_id, h->d_occl, h->d_hlist, h->d_rgba, h->d_out,
+                   h->d_ppairs, h->d_spairs, h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    for (TrainState &t : h->train) {
+        void *tp[] = {t.o, t.d, t.m_star, t.hit_star, t.master, t.adam_m, t.adam_v};
+        for (void *p : tp)
+            if (p) cudaFree(p);
+    }
+    if (h->h_frame) cudaFreeHost(h->h_frame);
+    if (h->h_cam) cudaFreeHost(h->h_cam);
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
+    delete h;
+}
+
+int nedf_compose_set_options(nedf_handle *h, const nedf_options *o)
+{
+    if (!h || !o) return fail(h, NEDF_ERR_ARG, "null argument");
+    if (o->n_shade < 1 || o->n_shade > 32) return fail(h, NEDF_ERR_ARG, "n_shade must be 1..32");
+    if (!(o->shade_half > 0.f) || !(o->shadow_beta > 0.f && o->shadow_beta < 1.f) || !(o->shadow_eps >= 0.f) ||
+        !(o->sigma_max > 0.f) || !(o->sdf_width > 0.f) || !std::isfinite(o->shade_half) || !std::isfinite(o->shadow_eps))
+        return fail(h, NEDF_ERR_ARG, "option out of range");
+    if (o->depth_source != NEDF_DEPTH_NEDF && o->depth_source != NEDF_DEPTH_MARCH)
+        return fail(h, NEDF_ERR_ARG, "depth_source");
+    if (o->march_steps < 1 || o->march_steps > 65536 || o->march_bisect < 0 || o->march_bisect > 64)
+        return fail(h, NEDF_ERR_ARG, "march_steps 1..65536, march_bisect 0..64");
+    if (!(o->fallback_conf >= 0.f && o->fallback_conf <= 1.f) || o->refine_steps < 0 || o->refine_steps > 64)
+        return fail(h, NEDF_ERR_ARG, "fallback_conf / refine_steps");
+    h->opt = *o;
+    return NEDF_OK;
+}
+
+int nedf_compose_get_options(const nedf_handle *h, nedf_options *o)
+{
+    if (!h || !o) return NEDF_ERR_ARG;
+    *o = h->opt;
+    return NEDF_OK;
+}
+
+int nedf_compose_sync(nedf_handle *h)
+{
+    if (!h) return NEDF_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    uint32_t st = 0;
+    CK(h, cudaMemcpy(&st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st) {
+        CK(h, cudaMemset(h->d_status, 0, sizeof(uint32_t)));
+        if (st & kStatusTimeout) return fail(h, NEDF_ERR_TIMEOUT, "a bounded device wait gave up");
+        return fail(h, NEDF_ERR_CAPACITY, st & kStatusPrimaryOverflow ? "primary pair list overflowed"
+                                                                      : "shadow pair list overflowed");
+    }
+    return NEDF_OK;
+}
+
+int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *types)
+{
+    if (!h || !types) return fail(h, NEDF_ERR_ARG, "null argument");
+    if (n_types < 1 || n_types > h->cfg.max_types) return fail(h, NEDF_ERR_ARG, "n_types out of range");
+    std::vector<DevType> dt(n_types);
+    std::vector<float> nedf((size_t)h->nedf_params * n_types), nerf((size_t)h->nerf_params * n_types);
+    for (int k = 0; k < n_types; ++k) {
+        const nedf_type_desc &t = types[k];
+        if (t.sdf_kind < 0 || t.sdf_kind > 7) return fail(h, NEDF_ERR_ARG, "unknown sdf_kind");
+        if (!(t.rb > 0.f) || !std::isfinite(t.rb) || !finite3(t.sdf_params, 8) || !finite3(t.albedo, 3))
+            return fail(h, NEDF_ERR_ARG, "type parameters must be finite, rb > 0");
+        if (!t.nedf_weights) return fail(h, NEDF_ERR_ARG, "missing NeDF weights");
+        if (h->cfg.nerf_hidden > 0 && !t.nerf_weights) return fail(h, NEDF_ERR_ARG, "missing NeRF weights");
+        if (!finite3(t.nedf_weights, (int)h->nedf_params)) return fail(h, NEDF_ERR_ARG, "non-finite NeDF weight");
+        if (h->nerf_params && !finite3(t.nerf_weights, (int)h->nerf_params))
+            return fail(h, NEDF_ERR_ARG, "non-finite NeRF weight");
+        dt[k].kind = t.sdf_kind;
+        for (int i = 0; i < 8; ++i) dt[k].p[i] = t.sdf_params[i];
+        dt[k].rb = t.rb;
+        for (int i = 0; i < 3; ++i) dt[k].albedo[i] = t.albedo[i];
+        dt[k].nerf = h->cfg.nerf_hidden > 0;
+        to_kernel_layout(t.nedf_weights, nedf.data() + (size_t)k * h->nedf_params, kNedfIn, h->cfg.nedf_hidden,
+                         h->cfg.nedf_width, 2);
+        if (h->nerf_params)
+            to_kernel_layout(t.nerf_weights, nerf.data() + (size_t)k * h->nerf_params, kNerfIn,
+                             h->cfg.nerf_hidden, h->cfg.nerf_width, 3);
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(h->d_types, dt.data(), sizeof(DevType) * n_types, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->d_nedf_w, nedf.data(), sizeof(float) * nedf.size(), cudaMemcpyHostToDevice));
+    if (h->nerf_params)
+        CK(h, cudaMemcpy(h->d_nerf_w, nerf.data(), sizeof(float) * nerf.size(), cudaMemcpyHostToDevice));
+    h->types_host = dt;
+    h->n_types = n_types;
+    // training state: master weights = the given packed weights, fresh moments
+    for (int k = 0; k < n_types; ++k) {
+        TrainState &ts = h->train[k];
+        size_t bytes = sizeof(float) * h->nedf_params;
+        if (!ts.master) {
+            CK(h, cudaMalloc((void **)&ts.master, bytes));
+            CK(h, cudaMalloc((void **)&ts.adam_m, bytes));
+            CK(h, cudaMalloc((void **)&ts.adam_v, bytes));
+        }
+        CK(h, cudaMemcpy(ts.master, types[k].nedf_weights, bytes, cudaMemcpyHostToDevice));
+        CK(h, cudaMemset(ts.adam_m, 0, bytes));
+        CK(h, cudaMemset(ts.adam_v, 0, bytes));
+        ts.step = 0;
+        ts.cursor = 0;
+    }
+    return NEDF_OK;
+}
+
+int nedf_compose_set_instances(nedf_handle *h, int n, const nedf_instance *inst)
+{
+    if (!h || (!inst && n > 0)) return fail(h, NEDF_ERR_ARG, "null argument");
+    if (h->n_types == 0) return fail(h, NEDF_ERR_STATE, "set_types first");
+    if (n < 0 || n > h->cfg.max_instances) return fail(h, NEDF_ERR_ARG, "instance count out of range");
+    std::vector<DevInst> di(n > 0 ? n : 1);
+    for (int i = 0; i < n; ++i) {
+        const nedf_instance &s = inst[i];
+        if (s.type >= (uint32_t)h->n_types) return fail(h, NEDF_ERR_ARG, "instance type out of range");
+        if (!finite3(s.R, 9) || !finite3(s.T, 3) || !std::isfinite(s.s) || !(s.s > 0.f))
+            return fail(h, NEDF_ERR_ARG, "instance transform must be finite with s > 0");
+        std::memcpy(di[i].R, s.R, sizeof(s.R));
+        std::memcpy(di[i].T, s.T, sizeof(s.T));
+        di[i].s = s.s;
+        di[i].type = s.type;
+        di[i].pad[0] = di[i].pad[1] = 0.f;
+    }
+    if (n > 0)
+        CK(h, cudaMemcpyAsync(h->d_inst, di.data(), sizeof(DevInst) * n, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));   // di is a host temporary
+    h->n_inst = n;
+    return NEDF_OK;
+}
+
+static int check_frame_args(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights)
+{
+    if (!h || !cam || (!lights && n_lights > 0)) return fail(h, NEDF_ERR_ARG, "null argument");
+    if (h->n_types == 0 || h->n_inst == 0) return fail(h, NEDF_ERR_STATE, "set_types and set_instances first");
+    if (n_lights < 1 || n_lights > NEDF_MAX_LIGHTS) return fail(h, NEDF_ERR_ARG, "n_lights must be 1..32");
+    if (!finite3(cam->eye, 3) || !finite3(cam->target, 3) || !(cam->fov_y_deg > 0.f && cam->fov_y_deg < 180.f))
+        return fail(h, NEDF_ERR_ARG, "camera");
+    float dx = cam->target[0] - cam->eye[0], dz = cam->target[2] - cam->eye[2];
+    float dy = cam->target[1] - cam->eye[1];
+    if (dx * dx + dz * dz <= 1e-12f * (dx * dx + dy * dy + dz * dz) || (dx == 0.f && dy == 0.f && dz == 0.f))
+        return fail(h, NEDF_ERR_ARG, "camera must not look along the up axis");
+    for (int l = 0; l < n_lights; ++l)
+        if (!finite3(lights[l].pos, 3)) return fail(h, NEDF_ERR_ARG, "light");
+    return NEDF_OK;
+}
+
+static cudaError_t upload_frame(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights)
+{
+    cudaError_t e = cudaStreamSynchronize(h->stream);   // staging buffers may still be in flight
+    if (e != cudaSuccess) return e;
+    DevFrame &f = *h->h_frame;
+    std::memset(&f, 0, sizeof(f));
+    f.W = h->cfg.width;
+    f.H = h->cfg.height;
+    f.n_lights = n_lights;
+    for (int l = 0; l < n_lights; ++l)
+        for (int c = 0; c < 3; ++c) f.lights[l][c] = lights[l].pos[c];
+    f.n_shade = h->opt.n_shade;
+    f.shade_half = h->opt.shade_half;
+    f.beta = h->opt.shadow_beta;
+    f.eps = h->opt.shadow_eps;
+    f.sigma_max = h->opt.sigma_max;
+    f.sdf_width = h->opt.sdf_width;
+    f.depth_source = h->opt.depth_source;
+    f.march_steps = h->opt.march_steps;
+    f.march_bisect = h->opt.march_bisect;
+    f.fallback_conf = h->opt.fallback_conf;
+    f.refine_steps = h->opt.refine_steps;
+    f.n_inst = h->n_inst;
+    f.n_types = h->n_types;
+    std::memcpy(h->h_cam->eye, cam->eye, sizeof(cam->eye));
+    std::memcpy(h->h_cam->target, cam->target, sizeof(cam->target));
+    h->h_cam->fov_y_deg = cam->fov_y_deg;
+    e = cudaMemcpyAsync(h->d_frame, h->h_frame, sizeof(DevFrame), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(h->d_cam, h->h_cam, sizeof(HostCamera), cudaMemcpyHostToDevice, h->stream);
+}
+
+static int fill_stats(nedf_handle *h, nedf_frame_stats *stats)
+{
+    CK(h, cudaStreamSynchronize(h->stream));
+    Counters c;
+    uint32_t st = 0;
+    CK(h, cudaMemcpy(&c, h->d_cnt, sizeof(c), cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(&st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+    stats->primary_pairs = (int64_t)c.p_off[h->n_types];
+    stats->shadow_pairs = (int64_t)c.s_off[h->n_types];
+    stats->hit_pixels = (int64_t)c.hit_pixels;
+    stats->fallback_pairs = (int64_t)c.fallback;
+    stats->kernel_launches = h->last_launches;
+    stats->status = st;
+    return nedf_compose_sync(h);
+}
+
+static int render_impl(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights)
+{
+    CK(h, upload_frame(h, cam, lights, n_lights));
+    FrameLaunch L;
+    L.ws = make_ws(h);
+    L.stream = h->stream;
+    L.W = h->cfg.width;
+    L.H = h->cfg.height;
+    L.num_sms = h->num_sms;
+    L.n_inst = h->n_inst;
+    L.n_shade = h->opt.n_shade;
+    L.cam = h->d_cam;
+    L.events = h->profiling ? h->ev : nullptr;
+    L.launches = 0;
+    CK(h, launch_frame_f32(L));
+    h->last_launches = L.launches;
+    if (h->profiling) h->profiled = true;
+    return NEDF_OK;
+}
+
+int nedf_compose_render(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights,
+                        float *depth, uint32_t *id, float *rgba, float *shadow, float *out,
+                        nedf_frame_stats *stats)
+{
+    int r = check_frame_args(h, cam, lights, n_lights);
+    if (r != NEDF_OK) return r;
+    r = render_impl(h, cam, lights, n_lights);
+    if (r != NEDF_OK) return r;
+    size_t npix = (size_t)h->cfg.width * h->cfg.height;
+    cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    if (depth) CK(h, cudaMemcpyAsync(depth, h->d_depth, npix * 4, k, h->stream));
+    if (id) CK(h, cudaMemcpyAsync(id, h->d_id, npix * 4, k, h->stream));
+    if (rgba) CK(h, cudaMemcpyAsync(rgba, h->d_rgba, npix * 16, k, h->stream));
+    if (shadow) CK(h, cudaMemcpyAsync(shadow, h->d_shadow, npix * 4, k, h->stream));
+    if (out) CK(h, cudaMemcpyAsync(out, h->d_out, npix * 16, k, h->stream));
+    if (stats) return fill_stats(h, stats);
+    return NEDF_OK;
+}
+
+int nedf_compose_render_host(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights,
+                             float *depth, uint32_t *id, float *rgba, float *shadow, float *out,
+                             nedf_frame_stats *stats)
+{
+    int r = check_frame_args(h, cam, lights, n_lights);
+    if (r != NEDF_OK) return r;
+    r = render_impl(h, cam, lights, n_lights);
+    if (r != NEDF_OK) return r;
+    size_t npix = (size_t)h->cfg.width * h->cfg.height;
+    cudaMemcpyKind k = cudaMemcpyDeviceToHost;
+    if (depth) CK(h, cudaMemcpyAsync(depth, h->d_depth, npix * 4, k, h->stream));
+    if (id) CK(h, cudaMemcpyAsync(id, h->d_id, npix * 4, k, h->stream));
+    if (rgba) CK(h, cudaMemcpyAsync(rgba, h->d_rgba, npix * 16, k, h->stream));
+    if (shadow) CK(h, cudaMemcpyAsync(shadow, h->d_shadow, npix * 4, k, h->stream));
+    if (out) CK(h, cudaMemcpyAsync(out, h->d_out, npix * 16, k, h->stream));
+    if (stats) return fill_stats(h, stats);
+    return nedf_compose_sync(h);
+}
+
+int nedf_compose_render_march(nedf_handle *h, const nedf_camera *cam, int n_samples, int early_stop, float *rgba)
+{
+    nedf_light dummy{{0.f, 10.f, 0.f}};
+    int r = check_frame_args(h, cam, &dummy, 1);
+    if (r != NEDF_OK) return r;
+    if (!rgba || n_samples < 1 || n_samples > 4096) return fail(h, NEDF_ERR_ARG, "rgba / n_samples 1..4096");
+    CK(h, upload_frame(h, cam, &dummy, 1));
+    CK(h, launch_march_frame(make_ws(h), h->d_cam, h->cfg.width, h->cfg.height, h->n_inst, n_samples, early_stop,
+                             reinterpret_cast<float4 *>(rgba), h->num_sms, h->stream));
+    return NEDF_OK;
+}
+
+const char *nedf_compose_stage_name(int stage)
+{
+    static const char *names[kStages] = {"setup", "step1_bin", "step1_nedf", "step1_resolve",
+                                         "step2_shade", "step3_bin", "step3_nedf", "composite"};
+    return (stage >= 0 && stage < kStages) ? names[stage] : "";
+}
+
+int nedf_compose_set_profiling(nedf_handle *h, int on)
+{
+    if (!h) return NEDF_ERR_ARG;
+    if (on && !h->ev[0])
+        for (cudaEvent_t &e : h->ev) CK(h, cudaEventCreate(&e));
+    h->profiling = on != 0;
+    return NEDF_OK;
+}
+
+int nedf_compose_get_stage_times(nedf_handle *h, float *ms, int n)
+{
+    if (!h || !ms || n < kStages) return fail(h, NEDF_ERR_ARG, "ms must hold NEDF_N_STAGES floats");
+    if (!h->profiled) return fail(h, NEDF_ERR_STATE, "no profiled render");
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < kStages; ++i) CK(h, cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
+    return NEDF_OK;
+}
+
+int nedf_compose_nedf_query(nedf_handle *h, int type, int n, const float *o, const float *d, float *out)
+{
+    if (!h || !o || !d || !out) return fail(h, NEDF_ERR_ARG, "null argument");
+    if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
+    if (n < 0) return fail(h, NEDF_ERR_ARG, "n < 0");
+    CK(h, launch_nedf_query_f32(make_ws(h), type, o, d, out, n, h->num_sms, h->stream));
+    return NEDF_OK;
+}
+
+}  // extern "C"
+
+// ---- learned part -------------------------------------------------------------------------------
+extern "C" {
+
+int nedf_compose_make_labels(nedf_handle *h, int type, int64_t n_rays, uint64_t seed, int march_steps,
+                             int march_bisect, float *o, float *d, float *m_star, float *hit_star)
+{
+    if (!h) return NEDF_ERR_ARG;
+    if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
+    if (n_rays < 1 || n_rays > (1ll << 30)) return fail(h, NEDF_ERR_ARG, "n_rays 1..2^30");
+    if (march_steps < 1 || march_steps > 65536 || march_bisect < 0 || march_bisect > 64)
+        return fail(h, NEDF_ERR_ARG, "march parameters");
+    TrainState &ts = h->train[type];
+    if (ts.n_rays != n_rays) {
+        float *p[] = {ts.o, ts.d, ts.m_star, ts.hit_star};
+        for (float *q : p)
+            if (q) cudaFree(q);
+        ts.o = ts.d = ts.m_star = ts.hit_star = nullptr;
+        ts.n_rays = 0;
+        CK(h, cudaMalloc((void **)&ts.o, sizeof(float) * 3 * n_rays));
+        CK(h, cudaMalloc((void **)&ts.d, sizeof(float) * 3 * n_rays));
+        CK(h, cudaMalloc((void **)&ts.m_star, sizeof(float) * n_rays));
+        CK(h, cudaMalloc((void **)&ts.hit_star, sizeof(float) * n_rays));
+        ts.n_rays = n_rays;
+    }
+    ts.cursor = 0;
+    CK(h, launch_make_labels(h->d_types + type, h->types_host[type].rb, n_rays, seed, march_steps, march_bisect,
+                             ts.o, ts.d, ts.m_star, ts.hit_star, h->num_sms, h->stream));
+    size_t b3 = sizeof(float) * 3 * n_rays, b1 = sizeof(float) * n_rays;
+    if (o) CK(h, cudaMemcpyAsync(o, ts.o, b3, cudaMemcpyDeviceToDevice, h->stream));
+    if (d) CK(h, cudaMemcpyAsync(d, ts.d, b3, cudaMemcpyDeviceToDevice, h->stream));
+    if (m_star) CK(h, cudaMemcpyAsync(m_star, ts.m_star, b1, cudaMemcpyDeviceToDevice, h->stream));
+    if (hit_star) CK(h, cudaMemcpyAsync(hit_star, ts.hit_star, b1, cudaMemcpyDeviceToDevice, h->stream));
+    return NEDF_OK;
+}
+
+static int ensure_train_scratch(nedf_handle *h, int batch)
+{
+    size_t need = train_scratch_bytes(batch, h->cfg.nedf_hidden, h->cfg.nedf_width, h->nedf_params);
+    if (need > h->train_scratch_bytes) {
+        if (h->d_train_scratch) cudaFree(h->d_train_scratch);
+        h->d_train_scratch = nullptr;
+        h->train_scratch_bytes = 0;
+        CK(h, cudaMalloc((void **)&h->d_train_scratch, need));
+        h->train_scratch_bytes = need;
+    }
+    return NEDF_OK;
+}
+
+static TrainLaunch make_train_launch(nedf_handle *h, int type)
+{
+    TrainLaunch L{};
+    L.type = h->d_types + type;
+    L.rb = h->types_host[type].rb;
+    L.hidden = h->cfg.nedf_hidden;
+    L.width = h->cfg.nedf_width;
+    L.n_params = h->nedf_params;
+    L.master = h->train[type].master;
+    L.kernel_w = h->d_nedf_w + (size_t)type * h->nedf_params;
+    L.scratch = h->d_train_scratch;
+    L.loss = h->d_loss;
+    L.num_sms = h->num_sms;
+    L.stream = h->stream;
+    return L;
+}
+
+int nedf_compose_loss_grad(nedf_handle *h, int type, int n, const float *o, const float *d, const float *m_star,
+                           const float *hit_star, float *grad, float *loss_host)
+{
+    if (!h || !o || !d || !m_star || !hit_star || !grad) return fail(h, NEDF_ERR_ARG, "null argument");
+    if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
+    if (n < 1 || n > (1 << 24)) return fail(h, NEDF_ERR_ARG, "n out of range");
+    int r = ensure_train_scratch(h, n);
+    if (r != NEDF_OK) return r;
+    TrainLaunch L = make_train_launch(h, type);
+    CK(h, launch_loss_grad(L, o, d, m_star, hit_star, n, grad));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (loss_host) CK(h, cudaMemcpy(loss_host, h->d_loss, sizeof(float), cudaMemcpyDeviceToHost));
+    return nedf_compose_sync(h);
+}
+
+int nedf_compose_train_step(nedf_handle *h, int type, int batch, float lr, float *loss_host)
+{
+    if (!h) return NEDF_ERR_ARG;
+    if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
+    TrainState &ts = h->train[type];
+    if (ts.n_rays == 0) return fail(h, NEDF_ERR_STATE, "make_labels first");
+    if (batch < 1 || batch > (1 << 22) || batch > ts.n_rays) return fail(h, NEDF_ERR_ARG, "batch out of range");
+    if (!(lr > 0.f) || !std::isfinite(lr)) return fail(h, NEDF_ERR_ARG, "lr");
+    int r = ensure_train_scratch(h, batch);
+    if (r != NEDF_OK) return r;
+    TrainLaunch L = make_train_launch(h, type);
+    ts.step += 1;
+    CK(h, launch_train_step(L, ts.o, ts.d, ts.m_star, ts.hit_star, ts.n_rays, ts.cursor, batch, ts.adam_m,
+                            ts.adam_v, ts.step, lr));
+    ts.cursor = (ts.cursor + batch) % ts.n_rays;
+    if (loss_host) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        CK(h, cudaMemcpy(loss_host, h->d_loss, sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    return NEDF_OK;
+}
+
+int nedf_compose_get_nedf_weights(nedf_handle *h, int type, float *host_out, int64_t n_floats)
+{
+    if (!h || !host_out) return fail(h, NEDF_ERR_ARG, "null argument");
+    if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
+    if (n_floats < h->nedf_params) return fail(h, NEDF_ERR_ARG, "buffer too small");
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(host_out, h->train[type].master, sizeof(float) * h->nedf_params, cudaMemcpyDeviceToHost));
+    return NEDF_OK;
+}
+
+// blob: magic, version, n_types, n_params, then per type: step, master, m, v
+int nedf_compose_save_state(nedf_handle *h, void *buf, size_t *size)
+{
+    if (!h || !size) return fail(h, NEDF_ERR_ARG, "null argument");
+    size_t per = sizeof(int32_t) + 3 * sizeof(float) * h->nedf_params;
+    size_t need = 4 * sizeof(int64_t) + per * h->n_types;
+    if (!buf) {
+        *size = need;
+        return NEDF_OK;
+    }
+    if (*size < need) return fail(h, NEDF_ERR_ARG, "buffer too small");
+    CK(h, cudaStreamSynchronize(h->stream));
+    char *p = (char *)buf;
+    int64_t hdr[4] = {0x4e45444653544154ll, 1, h->n_types, h->nedf_params};
+    std::memcpy(p, hdr, sizeof(hdr));
+    p += sizeof(hdr);
+    size_t wb = sizeof(float) * h->nedf_params;
+    for (int k = 0; k < h->n_types; ++k) {
+        int32_t st = h->train[k].step;
+        std::memcpy(p, &st, sizeof(st));
+        p += sizeof(st);
+        CK(h, cudaMemcpy(p, h->train[k].master, wb, cudaMemcpyDeviceToHost)); p += wb;
+        CK(h, cudaMemcpy(p, h->train[k].adam_m, wb, cudaMemcpyDeviceToHost)); p += wb;
+        CK(h, cudaMemcpy(p, h->train[k].adam_v, wb, cudaMemcpyDeviceToHost)); p += wb;
+    }
+    *size = need;
+    return NEDF_OK;
+}
+
+int nedf_compose_load_state(nedf_handle *h, const void *buf, size_t size)
+{
+    if (!h || !buf) return fail(h, NEDF_ERR_ARG, "null argument");
+    int64_t hdr[4];
+    if (size < sizeof(hdr)) return fail(h, NEDF_ERR_ARG, "blob too small");
+    std::memcpy(hdr, buf, sizeof(hdr));
+    size_t per = sizeof(int32_t) + 3 * sizeof(float) * h->nedf_params;
+    if (hdr[0] != 0x4e45444653544154ll || hdr[1] != 1 || hdr[2] != h->n_types || hdr[3] != h->nedf_params ||
+        size < sizeof(hdr) + per * h->n_types)
+        return fail(h, NEDF_ERR_ARG, "blob does not match this handle");
+    CK(h, cudaStreamSynchronize(h->stream));
+    const char *p = (const char *)buf + sizeof(hdr);
+    size_t wb = sizeof(float) * h->nedf_params;
+    for (int k = 0; k < h->n_types; ++k) {
+        int32_t st;
+        std::memcpy(&st, p, sizeof(st));
+        p += sizeof(st);
+        h->train[k].step = st;
+        CK(h, cudaMemcpy(h->train[k].master, p, wb, cudaMemcpyHostToDevice)); p += wb;
+        CK(h, cudaMemcpy(h->train[k].adam_m, p, wb, cudaMemcpyHostToDevice)); p += wb;
+        CK(h, cudaMemcpy(h->train[k].adam_v, p, wb, cudaMemcpyHostToDevice)); p += wb;
+        TrainLaunch L = make_train_launch(h, k);
+        CK(h, launch_refresh_weights(L));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return NEDF_OK;
+}
+
+}  // extern "C"

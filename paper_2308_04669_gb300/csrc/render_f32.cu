@@ -1,0 +1,682 @@
+// FP32 render path on CUDA cores: the reference-precision implementation of Steps 1-3.
+//
+// Method: arXiv 2308.04669, Algorithm 1 and Algorithm 2, Eq. 1-2, 7, 8.
+#include "render_kernels.cuh"
+#include "mlp_f32.cuh"
+#include "render_launch.h"
+
+#include <algorithm>
+
+namespace nedf {
+
+// ---------------------------------------------------------------------------------------------
+// frame setup: camera basis (look-at with world up +y) and counter reset
+// ---------------------------------------------------------------------------------------------
+__global__ void k_setup(Workspace ws, const HostCamera *cam)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        DevFrame &f = *ws.frame;
+        V3 eye = v3(cam->eye[0], cam->eye[1], cam->eye[2]);
+        V3 fwd = normalized(sub(v3(cam->target[0], cam->target[1], cam->target[2]), eye));
+        V3 right = normalized(v3(-fwd.z, 0.0f, fwd.x));          // fwd x (0,1,0)
+        V3 up = v3(right.y * fwd.z - right.z * fwd.y, right.z * fwd.x - right.x * fwd.z,
+                   right.x * fwd.y - right.y * fwd.x);           // right x fwd
+        f.eye[0] = eye.x; f.eye[1] = eye.y; f.eye[2] = eye.z;
+        f.fwd[0] = fwd.x; f.fwd[1] = fwd.y; f.fwd[2] = fwd.z;
+        f.right[0] = right.x; f.right[1] = right.y; f.right[2] = right.z;
+        f.up[0] = up.x; f.up[1] = up.y; f.up[2] = up.z;
+        f.tan_h = tanf(0.5f * cam->fov_y_deg * 0.017453292519943295f);
+        f.aspect = (float)f.W / (float)f.H;
+    }
+    unsigned long long *c = reinterpret_cast<unsigned long long *>(ws.cnt);
+    for (int i = threadIdx.x; i < (int)(sizeof(Counters) / 8); i += blockDim.x) c[i] = 0ull;
+}
+
+__global__ void k_clear(Workspace ws, int npix)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+        ws.keys[p] = ~0ull;
+        ws.occl[p] = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Step 1 binning: conservative screen rectangle of each instance's bound sphere, exact cull of
+// every pixel ray inside it.  pass 0 counts pairs per type, pass 1 writes them.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool screen_rect(const DevFrame &f, V3 c, float r, int &i0, int &i1, int &j0, int &j1)
+{
+    V3 e = sub(c, v3(f.eye[0], f.eye[1], f.eye[2]));
+    float cx = dot(e, v3(f.right[0], f.right[1], f.right[2]));
+    float cy = dot(e, v3(f.up[0], f.up[1], f.up[2]));
+    float cz = dot(e, v3(f.fwd[0], f.fwd[1], f.fwd[2]));
+    if (cz <= r * 1.001f + 1e-6f) {           // bound reaches behind the eye plane: whole image
+        i0 = 0; i1 = f.W - 1; j0 = 0; j1 = f.H - 1;
+        return true;
+    }
+    // Tangent planes through the eye: (c_a - u c_z)^2 = r^2 (1 + u^2).
+    float den = cz * cz - r * r;
+    float sx = r * sqrtf(fmaxf(cx * cx + cz * cz - r * r, 0.f));
+    float sy = r * sqrtf(fmaxf(cy * cy + cz * cz - r * r, 0.f));
+    float u0 = (cx * cz - sx) / den, u1 = (cx * cz + sx) / den;
+    float v0 = (cy * cz - sy) / den, v1 = (cy * cz + sy) / den;
+    float su = f.W * 0.5f / (f.tan_h * f.aspect), sv = f.H * 0.5f / f.tan_h;
+    float fi0 = u0 * su + f.W * 0.5f - 0.5f, fi1 = u1 * su + f.W * 0.5f - 0.5f;
+    float fj0 = -v1 * sv + f.H * 0.5f - 0.5f, fj1 = -v0 * sv + f.H * 0.5f - 0.5f;
+    if (!(fi1 >= -2.f && fi0 <= f.W + 1.f && fj1 >= -2.f && fj0 <= f.H + 1.f)) return false;
+    i0 = max(0, (int)floorf(fi0) - 2); i1 = min(f.W - 1, (int)ceilf(fi1) + 2);
+    j0 = max(0, (int)floorf(fj0) - 2); j1 = min(f.H - 1, (int)ceilf(fj1) + 2);
+    return i0 <= i1 && j0 <= j1;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Appends (a, b) for every lane with keep set to segment `type` of a list; returns false when
+// the segment was full (the pair is dropped and the status word flagged).
+__device__ __forceinline__ void warp_append(bool keep, uint2 val, unsigned long long *cursor,
+                                            const unsigned long long *seg_end, uint2 *list,
+                                            uint32_t *status, uint32_t flag)
+{
+    unsigned mask = __ballot_sync(0xffffffffu, keep);
+    if (!mask) return;
+    int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    unsigned long long start = 0;
+    if (lane == leader) start = atomicAdd(cursor, (unsigned long long)__popc(mask));
+    start = __shfl_sync(0xffffffffu, start, leader);
+    if (keep) {
+        unsigned long long idx = start + __popc(mask & lanemask_lt());
+        if (idx < *seg_end) list[idx] = val;
+        else atomicOr(status, flag);
+    }
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kThreads) k_bin_primary(Workspace ws)
+{
+    const DevFrame &f = *ws.frame;
+    int inst = blockIdx.x;
+    if (inst >= f.n_inst) return;
+    DevInst I = ws.inst[inst];
+    DevType T = ws.types[I.type];
+    int i0, i1, j0, j1;
+    if (!screen_rect(f, v3(I.T[0], I.T[1], I.T[2]), T.rb * I.s, i0, i1, j0, j1)) return;
+    int bw = i1 - i0 + 1, npx = bw * (j1 - j0 + 1);
+    __shared__ unsigned long long blk_count;
+    if (PASS == 0 && threadIdx.x == 0) blk_count = 0;
+    if (PASS == 0) __syncthreads();
+    unsigned local = 0;
+    for (int base = 0; base < npx; base += blockDim.x) {
+        int p = base + threadIdx.x;
+        bool keep = false;
+        int i = 0, j = 0;
+        if (p < npx) {
+            i = i0 + p % bw; j = j0 + p / bw;
+            V3 o, d, ol, dl;
+            camera_ray(f, i, j, o, d);
+            to_local(I, o, d, ol, dl);
+            Chord c;
+            keep = bound_chord(ol, dl, T.rb, c);
+        }
+        if (PASS == 0) {
+            local += keep;
+        } else {
+            warp_append(keep, make_uint2((uint32_t)(j * f.W + i), (uint32_t)inst), &ws.cnt->p_cursor[I.type],
+                        &ws.cnt->p_off[I.type + 1], ws.ppairs, ws.status, kStatusPrimaryOverflow);
+        }
+    }
+    if (PASS == 0) {
+        for (int o = 16; o; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
+        if ((threadIdx.x & 31) == 0 && local) atomicAdd(&blk_count, (unsigned long long)local);
+        __syncthreads();
+        if (threadIdx.x == 0 && blk_count) atomicAdd(&ws.cnt->p_count[I.type], blk_count);
+    }
+}
+
+// Prefix sums of a list's per-type counts (clamped to the capacity) and of its tiles.
+__device__ void scan_list(unsigned long long *count, unsigned long long *cursor, unsigned long long *off,
+                          unsigned long long *tile, int n_types, long long cap, int rows_per_tile,
+                          uint32_t *status, uint32_t flag, unsigned long long *requested)
+{
+    unsigned long long o = 0, t = 0, req = 0;
+    for (int k = 0; k < n_types; ++k) {
+        req += count[k];
+        unsigned long long c = count[k];
+        if (o + c > (unsigned long long)cap) {
+            c = (unsigned long long)cap - o;
+            *status |= flag;
+        }
+        count[k] = c;
+        off[k] = o;
+        cursor[k] = o;
+        tile[k] = t;
+        o += c;
+        t += (c + rows_per_tile - 1) / rows_per_tile;
+    }
+    off[n_types] = o;
+    tile[n_types] = t;
+    if (requested) *requested = req;
+}
+
+__global__ void k_scan_primary(Workspace ws, int rows_per_tile)
+{
+    const DevFrame &f = *ws.frame;
+    scan_list(ws.cnt->p_count, ws.cnt->p_cursor, ws.cnt->p_off, ws.cnt->p_tile, f.n_types, ws.pcap,
+              rows_per_tile, ws.status, kStatusPrimaryOverflow, &ws.cnt->p_total_requested);
+}
+
+__global__ void k_scan_shadow(Workspace ws, int rows_per_tile)
+{
+    const DevFrame &f = *ws.frame;
+    scan_list(ws.cnt->s_count, ws.cnt->s_cursor, ws.cnt->s_off, ws.cnt->s_tile, f.n_types, ws.scap,
+              rows_per_tile, ws.status, kStatusShadowOverflow, &ws.cnt->s_total_requested);
+}
+
+__global__ void k_scan_shade(Workspace ws, int pixels_per_tile)
+{
+    const DevFrame &f = *ws.frame;
+    unsigned long long t = 0;
+    for (int k = 0; k < f.n_types; ++k) {
+        ws.cnt->h_tile[k] = t;
+        t += (ws.cnt->h_count[k] + pixels_per_tile - 1) / pixels_per_tile;
+    }
+    ws.cnt->h_tile[f.n_types] = t;
+}
+
+// ---------------------------------------------------------------------------------------------
+// NeDF tiles (Step 1 primary pairs, Step 3 shadow pairs)
+// ---------------------------------------------------------------------------------------------
+struct RowInfo {
+    float x6[6];     // entry point on the bound, local direction
+    float ol[3], dl[3];
+    float te, tx, tp, s, rb;
+    float ell;       // shadow: distance light -> surface point
+    uint32_t key;    // primary: pixel; shadow: pixel * n_lights + light
+    uint32_t inst;
+    int valid;
+};
+
+template <int W_HID>
+__global__ void __launch_bounds__(kThreads) k_nedf_tiles(Workspace ws, int shadow_pass)
+{
+    extern __shared__ float4 smem4[];
+    float *X = reinterpret_cast<float *>(smem4);
+    __shared__ RowInfo rows[kTileRows];
+    __shared__ float y[kTileRows][4];
+    const DevFrame &f = *ws.frame;
+    const Counters &C = *ws.cnt;
+    const unsigned long long *tile_off = shadow_pass ? C.s_tile : C.p_tile;
+    const unsigned long long *pair_off = shadow_pass ? C.s_off : C.p_off;
+    const uint2 *pairs = shadow_pass ? ws.spairs : ws.ppairs;
+    const int n_types = f.n_types;
+    const unsigned long long n_tiles = tile_off[n_types];
+    const bool use_march = f.depth_source == 1;
+
+    for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        int t = 0;
+        while (t + 1 < n_types && tile_off[t + 1] <= tile) ++t;
+        unsigned long long begin = pair_off[t] + (tile - tile_off[t]) * kTileRows;
+        unsigned long long end = pair_off[t + 1];
+        const DevType T = ws.types[t];
+        // rays of the tile's rows
+        if (threadIdx.x < kTileRows) {
+            RowInfo &ri = rows[threadIdx.x];
+            unsigned long long idx = begin + threadIdx.x;
+            ri.valid = idx < end;
+            for (int c = 0; c < 6; ++c) ri.x6[c] = 0.0f;
+            if (ri.valid) {
+                uint2 pr = pairs[idx];
+                DevInst I = ws.inst[pr.y];
+                V3 o, d;
+                if (!shadow_pass) {
+                    camera_ray(f, pr.x % f.W, pr.x / f.W, o, d);
+                } else {
+                    uint32_t pix = pr.x / f.n_lights, l = pr.x - pix * f.n_lights;
+                    V3 oc, dc;
+                    camera_ray(f, pix % f.W, pix / f.W, oc, dc);
+                    V3 x = madd(oc, ws.depth[pix], dc);
+                    o = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
+                    V3 v = sub(x, o);
+                    ri.ell = sqrtf(dot(v, v));
+                    d = normalized(v);
+                }
+                V3 ol, dl;
+                to_local(I, o, d, ol, dl);
+                Chord ch;
+                bound_chord(ol, dl, T.rb, ch);
+                V3 pe = madd(ol, ch.te, dl);
+                ri.x6[0] = pe.x; ri.x6[1] = pe.y; ri.x6[2] = pe.z;
+                ri.x6[3] = dl.x; ri.x6[4] = dl.y; ri.x6[5] = dl.z;
+                ri.ol[0] = ol.x; ri.ol[1] = ol.y; ri.ol[2] = ol.z;
+                ri.dl[0] = dl.x; ri.dl[1] = dl.y; ri.dl[2] = dl.z;
+                ri.te = ch.te; ri.tx = ch.tx; ri.tp = ch.tp; ri.s = I.s; ri.rb = T.rb;
+                ri.key = pr.x; ri.inst = pr.y;
+            }
+        }
+        __syncthreads();
+        if (!use_march) {
+            // features: identity, 6 sine blocks, 6 cosine blocks of the 6-D input
+            for (int e = threadIdx.x; e < kTileRows * kNedfIn; e += blockDim.x) {
+                int r = e % kTileRows, fi = e / kTileRows;
+                X[fi * kXStride + r] = posenc_feature(rows[r].x6, 6, 6, fi);
+            }
+            __syncthreads();
+            const float *w = ws.nedf_w + (size_t)t * ws.nedf_stride;
+            mlp_hidden_f32<W_HID>(X, kNedfIn, ws.nedf_hidden, w);
+            const float *wo = w + (size_t)kNedfIn * W_HID + W_HID + (size_t)(ws.nedf_hidden - 1) * (W_HID * W_HID + W_HID);
+            out_layer_f32(X, W_HID, wo, wo + W_HID * 2, 2, y);
+        }
+        // decode (Eq. 2, Eq. 7), fallback, refinement, then z-min or occlusion
+        if (threadIdx.x < kTileRows && rows[threadIdx.x].valid) {
+            const RowInfo &ri = rows[threadIdx.x];
+            V3 ol = v3(ri.ol[0], ri.ol[1], ri.ol[2]), dl = v3(ri.dl[0], ri.dl[1], ri.dl[2]);
+            float Dl;
+            bool hit;
+            if (use_march) {
+                Dl = march_crossing(T, ol, dl, ri.te, ri.tx, f.march_steps, f.march_bisect, hit);
+            } else {
+                float m = y[threadIdx.x][0], a = y[threadIdx.x][1];
+                Dl = ri.tp - ri.rb * m;
+                hit = (a > 0.0f) && (Dl > 0.0f);
+                if (f.fallback_conf > 0.0f) {
+                    float p = 1.0f / (1.0f + expf(-a));
+                    if (fmaxf(p, 1.0f - p) < f.fallback_conf) {
+                        Dl = march_crossing(T, ol, dl, ri.te, ri.tx, f.march_steps, f.march_bisect, hit);
+                        atomicAdd(&ws.cnt->fallback, 1ull);
+                    }
+                }
+                if (hit && f.refine_steps > 0) {
+                    Dl = refine_depth(T, ol, dl, Dl, f.shade_half, f.refine_steps);
+                    hit = Dl > 0.0f;
+                }
+            }
+            if (hit) {
+                float D = ri.s * Dl;
+                if (!shadow_pass) {
+                    unsigned long long key = ((unsigned long long)__float_as_uint(D) << 32) | ri.inst;
+                    atomicMin(&ws.keys[ri.key], key);
+                } else if (D + f.eps < ri.ell) {
+                    uint32_t pix = ri.key / f.n_lights, l = ri.key - pix * f.n_lights;
+                    atomicOr(&ws.occl[pix], 1u << l);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Step 1 resolve: packed keys -> depth / id buffers, per-type lists of pixels to shade
+// ---------------------------------------------------------------------------------------------
+__global__ void k_resolve(Workspace ws, int npix)
+{
+    const DevFrame &f = *ws.frame;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+        unsigned long long k = ws.keys[p];
+        float D = __int_as_float(0x7f800000);
+        uint32_t id = kNoId;
+        if (k != ~0ull) {
+            D = __uint_as_float((uint32_t)(k >> 32));
+            id = (uint32_t)(k & 0xffffffffu);
+            uint32_t t = ws.inst[id].type;
+            unsigned long long pos = atomicAdd(&ws.cnt->h_count[t], 1ull);
+            ws.hlist[(size_t)t * npix + pos] = (uint32_t)p;
+            atomicAdd(&ws.cnt->hit_pixels, 1ull);
+        }
+        ws.depth[p] = D;
+        ws.id[p] = id;
+        ws.rgba[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    (void)f;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Step 2: deferred shading.  Tile rows = pixels x n_shade samples of the winning instance.
+// ---------------------------------------------------------------------------------------------
+template <int W_NERF>
+__global__ void __launch_bounds__(kThreads) k_shade_tiles(Workspace ws, int npix)
+{
+    extern __shared__ float4 smem4[];
+    float *X = reinterpret_cast<float *>(smem4);
+    __shared__ float xs[kTileRows][6];     // local sample position, local direction
+    __shared__ float sig[kTileRows];
+    __shared__ float y[kTileRows][4];
+    __shared__ uint32_t tile_pix[kTileRows];
+    __shared__ float tile_ws[kTileRows];    // world length of one sample interval
+    const DevFrame &f = *ws.frame;
+    const Counters &C = *ws.cnt;
+    const int ns = f.n_shade;
+    const int ppt = kTileRows / ns;
+    const int n_types = f.n_types;
+    const unsigned long long n_tiles = C.h_tile[n_types];
+    for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        int t = 0;
+        while (t + 1 < n_types && C.h_tile[t + 1] <= tile) ++t;
+        unsigned long long first = (tile - C.h_tile[t]) * ppt;
+        int n_pix = (int)min((unsigned long long)ppt, C.h_count[t] - first);
+        const DevType T = ws.types[t];
+        if (threadIdx.x < ppt * ns) {
+            int q = threadIdx.x / ns, j = threadIdx.x - q * ns;
+            for (int c = 0; c < 6; ++c) xs[threadIdx.x][c] = 0.0f;
+            sig[threadIdx.x] = 0.0f;
+            if (q < n_pix) {
+                uint32_t p = ws.hlist[(size_t)t * npix + first + q];
+                if (j == 0) tile_pix[q] = p;
+                DevInst I = ws.inst[ws.id[p]];
+                V3 o, d, ol, dl;
+                camera_ray(f, p % f.W, p / f.W, o, d);
+                to_local(I, o, d, ol, dl);
+                float Dl = ws.depth[p] / I.s;
+                float delta = 2.0f * f.shade_half / ns;
+                float tj = Dl - f.shade_half + (j + 0.5f) * delta;
+                V3 x = madd(ol, tj, dl);
+                xs[threadIdx.x][0] = x.x; xs[threadIdx.x][1] = x.y; xs[threadIdx.x][2] = x.z;
+                xs[threadIdx.x][3] = dl.x; xs[threadIdx.x][4] = dl.y; xs[threadIdx.x][5] = dl.z;
+                sig[threadIdx.x] = density(T, x, f.sigma_max, f.sdf_width);
+                if (j == 0) tile_ws[q] = I.s * delta;
+            }
+        }
+        __syncthreads();
+        if (T.nerf) {
+            for (int e = threadIdx.x; e < kTileRows * kNerfIn; e += blockDim.x) {
+                int r = e % kTileRows, fi = e / kTileRows;
+                float v = fi < 63 ? posenc_feature(&xs[r][0], 3, 10, fi) : posenc_feature(&xs[r][3], 3, 4, fi - 63);
+                X[fi * kXStride + r] = v;
+            }
+            __syncthreads();
+            const float *w = ws.nerf_w + (size_t)t * ws.nerf_stride;
+            mlp_hidden_f32<W_NERF>(X, kNerfIn, ws.nerf_hidden, w);
+            const float *wo = w + (size_t)kNerfIn * W_NERF + W_NERF + (size_t)(ws.nerf_hidden - 1) * (W_NERF * W_NERF + W_NERF);
+            out_layer_f32(X, W_NERF, wo, wo + W_NERF * 3, 3, y);
+        }
+        // front-to-back composite of each pixel's samples (Eq. 8 over the window)
+        if (threadIdx.x < n_pix) {
+            int q = threadIdx.x;
+            float Tr = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
+            for (int j = 0; j < ns; ++j) {
+                int r = q * ns + j;
+                float alpha = 1.0f - expf(-sig[r] * tile_ws[q]);
+                float R, G, B;
+                if (T.nerf) {
+                    R = 1.0f / (1.0f + expf(-y[r][0]));
+                    G = 1.0f / (1.0f + expf(-y[r][1]));
+                    B = 1.0f / (1.0f + expf(-y[r][2]));
+                } else {
+                    R = T.albedo[0]; G = T.albedo[1]; B = T.albedo[2];
+                }
+                float wgt = Tr * alpha;
+                cr += wgt * R; cg += wgt * G; cb += wgt * B; A += wgt;
+                Tr *= 1.0f - alpha;
+            }
+            ws.rgba[tile_pix[q]] = make_float4(cr, cg, cb, A);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Step 3 binning: every (valid pixel, light) shadow ray against every instance, exact cull,
+// and only bounds the segment light -> surface point enters before the point.
+// ---------------------------------------------------------------------------------------------
+template <int PASS>
+__global__ void __launch_bounds__(kThreads) k_bin_shadow(Workspace ws, int npix)
+{
+    __shared__ DevInst sI[128];
+    __shared__ float srb[128];
+    __shared__ unsigned long long cnt_t[kMaxTypes];
+    const DevFrame &f = *ws.frame;
+    const int nl = f.n_lights, n_inst = f.n_inst;
+    const long long n_rays = (long long)npix * nl;
+    if (PASS == 0)
+        for (int k = threadIdx.x; k < kMaxTypes; k += blockDim.x) cnt_t[k] = 0;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < n_rays; base += (long long)gridDim.x * blockDim.x) {
+        long long r = base + threadIdx.x;
+        bool valid = r < n_rays;
+        uint32_t pix = 0, l = 0;
+        V3 o = v3(0, 0, 0), d = v3(0, 0, 1);
+        float ell = 0.0f;
+        if (valid) {
+            pix = (uint32_t)(r / nl); l = (uint32_t)(r - (long long)pix * nl);
+            valid = ws.id[pix] != kNoId;
+            if (valid) {
+                V3 oc, dc;
+                camera_ray(f, pix % f.W, pix / f.W, oc, dc);
+                V3 x = madd(oc, ws.depth[pix], dc);
+                o = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
+                V3 v = sub(x, o);
+                ell = sqrtf(dot(v, v));
+                d = normalized(v);
+            }
+        }
+        bool any = __syncthreads_or(valid);
+        if (!any) continue;
+        for (int c0 = 0; c0 < n_inst; c0 += 128) {
+            int nc = min(128, n_inst - c0);
+            __syncthreads();
+            for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+                sI[k] = ws.inst[c0 + k];
+                srb[k] = ws.types[sI[k].type].rb;
+            }
+            __syncthreads();
+            for (int k = 0; k < nc; ++k) {
+                bool keep = false;
+                if (valid) {
+                    V3 ol, dl;
+                    to_local(sI[k], o, d, ol, dl);
+                    Chord ch;
+                    keep = bound_chord(ol, dl, srb[k], ch) && (ch.te * sI[k].s < ell);
+                }
+                uint32_t ty = sI[k].type;
+                if (PASS == 0) {
+                    unsigned m = __ballot_sync(0xffffffffu, keep);
+                    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&cnt_t[ty], (unsigned long long)__popc(m));
+                } else {
+                    warp_append(keep, make_uint2(pix * nl + l, (uint32_t)(c0 + k)), &ws.cnt->s_cursor[ty],
+                                &ws.cnt->s_off[ty + 1], ws.spairs, ws.status, kStatusShadowOverflow);
+                }
+            }
+        }
+    }
+    if (PASS == 0) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < f.n_types; k += blockDim.x)
+            if (cnt_t[k]) atomicAdd(&ws.cnt->s_count[k], cnt_t[k]);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Composite: shadow buffer = mean over lights of (occluded ? beta : 1); out = rgb * shadow
+// ---------------------------------------------------------------------------------------------
+__global__ void k_composite(Workspace ws, int npix)
+{
+    const DevFrame &f = *ws.frame;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+        float S = 1.0f;
+        if (ws.id[p] != kNoId) {
+            uint32_t m = ws.occl[p];
+            int occ = __popc(m);
+            S = ((f.n_lights - occ) * 1.0f + occ * f.beta) / f.n_lights;
+        }
+        ws.shadow[p] = S;
+        float4 c = ws.rgba[p];
+        ws.out[p] = make_float4(c.x * S, c.y * S, c.z * S, c.w);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// host-side launch sequence of one FP32 frame
+// ---------------------------------------------------------------------------------------------
+template <int W>
+static size_t nedf_smem() { return (size_t)(W > kNedfInPad ? W : kNedfInPad) * kXStride * sizeof(float); }
+template <int W>
+static size_t nerf_smem() { return (size_t)(W > kNerfInPad ? W : kNerfInPad) * kXStride * sizeof(float); }
+
+template <int W>
+static cudaError_t launch_nedf(const Workspace &ws, int grid, int shadow_pass, cudaStream_t st)
+{
+    size_t sm = nedf_smem<W>();
+    cudaError_t e = cudaFuncSetAttribute(k_nedf_tiles<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_nedf_tiles<W><<<grid, kThreads, sm, st>>>(ws, shadow_pass);
+    return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t launch_shade(const Workspace &ws, int grid, int npix, cudaStream_t st)
+{
+    size_t sm = nerf_smem<W>();
+    cudaError_t e = cudaFuncSetAttribute(k_shade_tiles<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_shade_tiles<W><<<grid, kThreads, sm, st>>>(ws, npix);
+    return cudaGetLastError();
+}
+
+static cudaError_t nedf_dispatch(const Workspace &ws, int grid, int shadow_pass, cudaStream_t st)
+{
+    switch (ws.nedf_width) {
+    case 64: return launch_nedf<64>(ws, grid, shadow_pass, st);
+    case 128: return launch_nedf<128>(ws, grid, shadow_pass, st);
+    case 256: return launch_nedf<256>(ws, grid, shadow_pass, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+static cudaError_t shade_dispatch(const Workspace &ws, int grid, int npix, cudaStream_t st)
+{
+    switch (ws.nerf_width) {
+    case 0:
+    case 64: return launch_shade<64>(ws, grid, npix, st);
+    case 128: return launch_shade<128>(ws, grid, npix, st);
+    case 256: return launch_shade<256>(ws, grid, npix, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_frame_f32(FrameLaunch &L)
+{
+    const Workspace &ws = L.ws;
+    cudaStream_t st = L.stream;
+    int npix = L.W * L.H;
+    int gsm = L.num_sms;
+    int stage = 0;
+    auto mark = [&]() {
+        if (L.events) cudaEventRecord(L.events[stage], st);
+        ++stage;
+    };
+    mark();
+    k_setup<<<1, 256, 0, st>>>(ws, L.cam);
+    k_clear<<<gsm * 4, 256, 0, st>>>(ws, npix);
+    mark();
+    k_bin_primary<0><<<L.n_inst, kThreads, 0, st>>>(ws);
+    k_scan_primary<<<1, 1, 0, st>>>(ws, kTileRows);
+    k_bin_primary<1><<<L.n_inst, kThreads, 0, st>>>(ws);
+    mark();
+    cudaError_t e = nedf_dispatch(ws, gsm * 4, 0, st);
+    if (e != cudaSuccess) return e;
+    mark();
+    k_resolve<<<gsm * 4, 256, 0, st>>>(ws, npix);
+    k_scan_shade<<<1, 1, 0, st>>>(ws, kTileRows / L.n_shade);
+    mark();
+    e = shade_dispatch(ws, gsm * 4, npix, st);
+    if (e != cudaSuccess) return e;
+    mark();
+    k_bin_shadow<0><<<gsm * 8, kThreads, 0, st>>>(ws, npix);
+    k_scan_shadow<<<1, 1, 0, st>>>(ws, kTileRows);
+    k_bin_shadow<1><<<gsm * 8, kThreads, 0, st>>>(ws, npix);
+    mark();
+    e = nedf_dispatch(ws, gsm * 4, 1, st);
+    if (e != cudaSuccess) return e;
+    mark();
+    k_composite<<<gsm * 4, 256, 0, st>>>(ws, npix);
+    mark();
+    L.launches = 14;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// NeDF queries on caller-given local rays (the network in isolation)
+// ---------------------------------------------------------------------------------------------
+template <int W_HID>
+__global__ void __launch_bounds__(kThreads) k_nedf_query(Workspace ws, int type, const float *o,
+                                                         const float *d, float *out, int n)
+{
+    extern __shared__ float4 smem4[];
+    float *X = reinterpret_cast<float *>(smem4);
+    __shared__ float x6[kTileRows][6];
+    __shared__ float tp[kTileRows];
+    __shared__ int kept[kTileRows];
+    __shared__ float y[kTileRows][4];
+    const DevType T = ws.types[type];
+    const float *w = ws.nedf_w + (size_t)type * ws.nedf_stride;
+    for (long long tile = blockIdx.x; tile * kTileRows < n; tile += gridDim.x) {
+        if (threadIdx.x < kTileRows) {
+            long long idx = tile * kTileRows + threadIdx.x;
+            for (int c = 0; c < 6; ++c) x6[threadIdx.x][c] = 0.0f;
+            kept[threadIdx.x] = 0;
+            if (idx < n) {
+                V3 ol = v3(o[3 * idx], o[3 * idx + 1], o[3 * idx + 2]);
+                V3 dl = normalized(v3(d[3 * idx], d[3 * idx + 1], d[3 * idx + 2]));
+                Chord ch;
+                kept[threadIdx.x] = bound_chord(ol, dl, T.rb, ch);
+                V3 pe = madd(ol, ch.te, dl);
+                if (kept[threadIdx.x]) {
+                    x6[threadIdx.x][0] = pe.x; x6[threadIdx.x][1] = pe.y; x6[threadIdx.x][2] = pe.z;
+                    x6[threadIdx.x][3] = dl.x; x6[threadIdx.x][4] = dl.y; x6[threadIdx.x][5] = dl.z;
+                }
+                tp[threadIdx.x] = ch.tp;
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kTileRows * kNedfIn; e += blockDim.x) {
+            int r = e % kTileRows, fi = e / kTileRows;
+            X[fi * kXStride + r] = posenc_feature(x6[r], 6, 6, fi);
+        }
+        __syncthreads();
+        mlp_hidden_f32<W_HID>(X, kNedfIn, ws.nedf_hidden, w);
+        const float *wo = w + (size_t)kNedfIn * W_HID + W_HID + (size_t)(ws.nedf_hidden - 1) * (W_HID * W_HID + W_HID);
+        out_layer_f32(X, W_HID, wo, wo + W_HID * 2, 2, y);
+        if (threadIdx.x < kTileRows) {
+            long long idx = tile * kTileRows + threadIdx.x;
+            if (idx < n) {
+                float4 r = make_float4(0.f, 0.f, __int_as_float(0x7f800000), 0.f);
+                if (kept[threadIdx.x]) {
+                    float m = y[threadIdx.x][0], a = y[threadIdx.x][1];
+                    float Dl = tp[threadIdx.x] - T.rb * m;
+                    r = make_float4(m, a, Dl, (a > 0.f && Dl > 0.f) ? 1.f : 0.f);
+                }
+                reinterpret_cast<float4 *>(out)[idx] = r;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int W>
+static cudaError_t launch_query(const Workspace &ws, int type, const float *o, const float *d, float *out,
+                                int n, int grid, cudaStream_t st)
+{
+    size_t sm = nedf_smem<W>();
+    cudaError_t e = cudaFuncSetAttribute(k_nedf_query<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_nedf_query<W><<<grid, kThreads, sm, st>>>(ws, type, o, d, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nedf_query_f32(const Workspace &ws, int type, const float *o, const float *d, float *out,
+                                  int n, int num_sms, cudaStream_t st)
+{
+    int grid = (int)std::min<long long>((long long)num_sms * 4, (n + kTileRows - 1) / kTileRows);
+    if (grid < 1) return cudaSuccess;
+    switch (ws.nedf_width) {
+    case 64: return launch_query<64>(ws, type, o, d, out, n, grid, st);
+    case 128: return launch_query<128>(ws, type, o, d, out, n, grid, st);
+    case 256: return launch_query<256>(ws, type, o, d, out, n, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace nedf

@@ -1,0 +1,39 @@
+// Launch sequences of the learned part (NeDF training), called by the C-ABI layer.
+#pragma once
+
+#include "nedf_device.cuh"
+
+namespace nedf {
+
+struct TrainLaunch {
+    const DevType *type;     // device record of the type being trained
+    float rb;
+    int hidden, width;
+    long long n_params;
+    float *master;           // packed FP32 weights, W[out][in] then b per layer
+    float *kernel_w;         // the renderer's copy (per layer Wt[in][out] then b)
+    float *scratch;          // activations, deltas, gradient (train_scratch_bytes)
+    float *loss;             // device float[4]: loss, hit count, row count
+    int num_sms;
+    cudaStream_t stream;
+};
+
+size_t train_scratch_bytes(int batch, int hidden, int width, long long n_params);
+
+cudaError_t launch_make_labels(const DevType *type, float rb, long long n_rays, uint64_t seed, int steps,
+                               int bisect, float *o, float *d, float *m_star, float *hit_star, int num_sms,
+                               cudaStream_t st);
+
+// Loss and gradient on rows [0, n) of (o, d, m_star, hit_star); gradient written to grad (packed).
+cudaError_t launch_loss_grad(const TrainLaunch &L, const float *o, const float *d, const float *m_star,
+                             const float *hit_star, int n, float *grad);
+
+// One Adam step on rows start .. start+batch-1 (mod n_rays) of the training set.
+cudaError_t launch_train_step(const TrainLaunch &L, const float *o, const float *d, const float *m_star,
+                              const float *hit_star, long long n_rays, long long start, int batch,
+                              float *adam_m, float *adam_v, int step, float lr);
+
+// Re-derives the renderer's copy of the weights from the master weights.
+cudaError_t launch_refresh_weights(const TrainLaunch &L);
+
+}  // namespace nedf

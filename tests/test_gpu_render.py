@@ -1,0 +1,181 @@
+"""CUDA render path vs the FP64 oracle (Steps 1-3 of Algorithm 1 / Algorithm 2), through the C ABI."""
+import numpy as np
+import pytest
+
+from paper_2308_04669_gb300 import scenegen as sg
+
+from .gpu_helpers import NOID, close, compare_frame, gpu_frame
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2308_04669_gb300 import build
+    build.build()
+    import torch
+    assert torch.cuda.is_available()
+
+
+def test_tiny_sphere_full_frame_nedf(orc):
+    """64x64, one sphere, NeDF 4x64 (random init): every pixel, every buffer."""
+    sc = sg.tiny_sphere_scene()
+    g = gpu_frame(sc)
+    o = orc.render(orc.OracleScene(sc))
+    rep = compare_frame(g, o, o["px"])
+    assert rep["hit"] > 1000
+    assert g["stats"].status == 0
+
+
+def test_tiny_sphere_full_frame_march(orc):
+    """Same scene answered by the plain method (surface depths, real shading and shadows)."""
+    sc = sg.tiny_sphere_scene()
+    g = gpu_frame(sc, depth_source=1, march_steps=128, march_bisect=4)
+    o = orc.render(orc.OracleScene(sc), depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4)
+    rep = compare_frame(g, o, o["px"])
+    assert rep["hit"] > 500 and rep["shadowed"] > 50
+    assert (o["rgba"][:, 3] > 0.5).sum() > 500
+
+
+@pytest.mark.parametrize("W,H", [(67, 45), (1, 1), (3, 130)])
+def test_ragged_sizes(orc, W, H):
+    sc = sg.three_types_scene(W, H, nerf=False)
+    g = gpu_frame(sc)
+    o = orc.render(orc.OracleScene(sc))
+    compare_frame(g, o, o["px"], max_excluded=0.2 if W * H < 10 else 0.05)
+
+
+def test_three_types_nerf_subset(orc):
+    """3 types x 16 instances, NeDF 6x128, NeRF 8x256, 2 lights at 128x128; oracle on a subset."""
+    sc = sg.three_types_scene(128, 128)
+    px = sg.pixel_subset(128, 128, 600, 5)
+    for mode, kw in [(0, {}), (1, dict(depth_source=1))]:
+        g = gpu_frame(sc, **kw)
+        o = orc.render(orc.OracleScene(sc), px=px, depth_mode=orc.DEPTH_MLP if mode == 0 else orc.DEPTH_MARCH,
+                       march_n=128, march_b=4, n_threads=8)
+        rep = compare_frame(g, o, px)
+        assert rep["hit"] > 30
+
+
+def test_three_types_full_size_sampled(orc):
+    """The 512x512 workload itself, sampled pixels."""
+    sc = sg.three_types_scene()
+    px = sg.pixel_subset(512, 512, 300, 6)
+    g = gpu_frame(sc, depth_source=1)
+    o = orc.render(orc.OracleScene(sc), px=px, depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4, n_threads=8)
+    compare_frame(g, o, px)
+
+
+def test_thousand_instances_sampled(orc):
+    """1024 instances at 1024x1024 with 4 lights: sampled pixels against the oracle."""
+    sc = sg.thousand_scene()
+    px = sg.pixel_subset(1024, 1024, 200, 7)
+    g = gpu_frame(sc)
+    o = orc.render(orc.OracleScene(sc), px=px, n_threads=8)
+    rep = compare_frame(g, o, px)
+    assert g["stats"].status == 0 and g["stats"].primary_pairs > 500000
+
+
+def test_empty_and_out_of_view(orc):
+    sc = sg.tiny_sphere_scene()
+    sc.inst_T = sg.f32([[0, 50, 0]])          # far outside the frustum
+    g = gpu_frame(sc)
+    assert np.all(g["id"] == NOID) and np.all(np.isinf(g["depth"]))
+    assert np.all(g["rgba"] == 0) and np.all(g["shadow"] == 1)
+    assert g["stats"].primary_pairs == 0 and g["stats"].hit_pixels == 0
+
+
+def test_permutation_invariance_gpu(orc):
+    sc = sg.three_types_scene(96, 96, nerf=False)
+    perm = np.random.default_rng(1).permutation(sc.n_inst)
+    a = gpu_frame(sc)
+    b = gpu_frame(sc.permuted(perm))
+    assert np.array_equal(a["depth"], b["depth"])
+    hit = a["id"] != NOID
+    o = orc.render(orc.OracleScene(sc))
+    ok = hit & (o["gap"] > 1e-4)
+    assert np.array_equal(a["id"][ok], perm[b["id"][ok]])
+
+
+def test_nedf_query_isolated(orc):
+    """The network alone on arbitrary local rays, including culled ones."""
+    import torch
+    from paper_2308_04669_gb300 import native
+    sc = sg.three_types_scene(8, 8, nerf=False)
+    r = native.renderer_for(sc)
+    rng = np.random.default_rng(0)
+    n = 1000
+    o = rng.normal(size=(n, 3)) * 1.5
+    d = rng.normal(size=(n, 3))
+    o32, d32 = o.astype(np.float32), d.astype(np.float32)
+    out = torch.empty(n, 4, device="cuda")
+    osc = orc.OracleScene(sc)
+    for t in range(3):
+        r.nedf_query(t, torch.tensor(o32, device="cuda"), torch.tensor(d32, device="cuda"), out)
+        g = out.cpu().numpy().astype(np.float64)
+        for i in range(n):
+            dd = d32[i].astype(np.float64); dd /= np.linalg.norm(dd)
+            kept, f, b = orc.nedf_features(o32[i].astype(np.float64), dd, 1.0)
+            if abs(b[3]) < 1e-4:
+                continue
+            if not kept:
+                assert g[i, 3] == 0 and np.isinf(g[i, 2])
+                continue
+            y = orc.mlp(sc.types[t].nedf_w.astype(np.float64), sc.types[t].nedf_dims, f)
+            assert close([g[i, 0], g[i, 1]], y, 2e-4, 1e-4).all(), (i, g[i], y)
+            assert g[i, 3] == float(y[1] > 0 and b[2] - y[0] > 0) or abs(y[1]) < 1e-4
+    r.close()
+
+
+def test_render_host_matches_device(orc):
+    import torch
+    from paper_2308_04669_gb300 import native
+    sc = sg.tiny_sphere_scene()
+    r = native.renderer_for(sc)
+    cam, li = r.camera(sc.eye, sc.target, sc.fov_deg), r.lights(sc.lights)
+    n = sc.W * sc.H
+    dd = torch.empty(n, device="cuda")
+    r.render(cam, li, depth=dd)
+    hd = np.empty(n, np.float32)
+    hid = np.empty(n, np.uint32)
+    r.render_host(cam, li, depth=hd, id=hid)
+    assert np.array_equal(dd.cpu().numpy(), hd)
+    r.close()
+
+
+def test_invalid_arguments_rejected():
+    from paper_2308_04669_gb300 import native
+    sc = sg.tiny_sphere_scene()
+    r = native.renderer_for(sc)
+    with pytest.raises(native.NedfError) as e:
+        r.set_instances([5], sc.inst_R, sc.inst_T, sc.inst_s)      # type out of range
+    assert e.value.code == native.NEDF_ERR_ARG
+    with pytest.raises(native.NedfError):
+        r.set_instances([0], sc.inst_R, sc.inst_T, [0.0])            # s <= 0
+    with pytest.raises(native.NedfError):
+        r.set_instances([0], sc.inst_R, sc.inst_T, [float("nan")])
+    with pytest.raises(native.NedfError):
+        r.render(r.camera(sc.eye, sc.target, sc.fov_deg), r.lights(np.zeros((33, 3))))
+    with pytest.raises(native.NedfError):
+        r.render(r.camera(sc.eye, sc.target, 0.0), r.lights(sc.lights))
+    o = r.get_options()
+    o.n_shade = 0
+    with pytest.raises(native.NedfError):
+        r.set_options(o)
+    r.close()
+    with pytest.raises(native.NedfError):
+        native.Renderer(0, 10, 1, 1, 4, 64)
+    with pytest.raises(native.NedfError) as e:
+        native.Renderer(10, 10, 1, 1, 4, 96)
+    assert e.value.code == native.NEDF_ERR_UNSUPPORTED
+
+
+def test_pair_capacity_overflow_is_reported(orc):
+    from paper_2308_04669_gb300 import native
+    sc = sg.tiny_sphere_scene()
+    r = native.Renderer(sc.W, sc.H, 1, 1, 4, 64, primary_pair_capacity=100)
+    r.load_scene(sc)
+    with pytest.raises(native.NedfError) as e:
+        r.render(r.camera(sc.eye, sc.target, sc.fov_deg), r.lights(sc.lights), stats=True)
+    assert e.value.code == native.NEDF_ERR_CAPACITY
+    r.close()

@@ -1,0 +1,84 @@
+"""Learned part on the GPU vs the FP64 oracle: training set, loss and gradient, Adam, state."""
+import numpy as np
+import pytest
+
+from paper_2308_04669_gb300 import scenegen as sg
+
+from .gpu_helpers import close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2308_04669_gb300 import build
+    build.build()
+    import torch
+    from paper_2308_04669_gb300 import native
+    assert torch.cuda.is_available()
+    return native
+
+
+def labels_on_gpu(native, sc, t, n, seed):
+    import torch
+    r = native.renderer_for(sc)
+    o = torch.empty(n, 3, device="cuda"); d = torch.empty(n, 3, device="cuda")
+    m = torch.empty(n, device="cuda"); h = torch.empty(n, device="cuda")
+    r.make_labels(t, n, seed, 256, 8, o, d, m, h)
+    torch.cuda.synchronize()
+    return r, o, d, m, h
+
+
+def test_training_rays_and_labels(lib, orc):
+    sc = sg.three_types_scene(8, 8, nerf=False)
+    osc = orc.OracleScene(sc)
+    n = 4000
+    for t in range(3):
+        r, o, d, m, h = labels_on_gpu(lib, sc, t, n, 2)
+        go, gd = o.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.float64)
+        oo, od = orc.train_rays(1.0, 2, 0, n)
+        assert np.abs(go - oo).max() < 1e-5 and np.abs(gd - od).max() < 1e-5   # same counter draws
+        om, oh = orc.train_labels(osc, t, go, gd, 256, 8)
+        gh = h.cpu().numpy() > 0.5
+        agree = gh == (oh == 1)
+        assert agree.mean() > 0.998
+        both = gh & (oh == 1)
+        assert close(m.cpu().numpy()[both], om[both], 1e-4, 1e-4).all()
+        assert 0.05 < gh.mean() < 0.95
+        r.close()
+
+
+def test_loss_and_gradient_match_oracle(lib, orc):
+    import torch
+    sc = sg.three_types_scene(8, 8, nerf=False)
+    osc = orc.OracleScene(sc)
+    n = 300
+    r, o, d, m, h = labels_on_gpu(lib, sc, 1, n, 9)
+    g = torch.zeros(sc.types[1].nedf_w.shape[0], device="cuda")
+    loss = r.loss_grad(1, o, d, m, h, g)
+    ol, og = orc.nedf_loss_grad(osc, 1, o.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.float64),
+                                m.cpu().numpy().astype(np.float64), (h.cpu().numpy() > 0.5).astype(np.int32))
+    assert abs(loss - ol) <= 1e-4 * abs(ol)
+    gg = g.cpu().numpy().astype(np.float64)
+    scale = np.abs(og).max()
+    assert np.all(np.abs(gg - og) <= 1e-4 * scale + 1e-3 * np.abs(og))
+    r.close()
+
+
+def test_training_reduces_loss_and_state_round_trip(lib):
+    sc = sg.three_types_scene(8, 8, nerf=False)
+    r = lib.renderer_for(sc)
+    r.make_labels(0, 1 << 16, 2)
+    first = r.train_step(0, 4096, 1e-3, want_loss=True)
+    for _ in range(150):
+        r.train_step(0, 4096, 1e-3)
+    last = r.train_step(0, 4096, 1e-3, want_loss=True)
+    assert last < 0.5 * first, (first, last)
+    blob = r.save_state()
+    w0 = r.get_nedf_weights(0, sc.types[0].nedf_w.shape[0])
+    for _ in range(5):
+        r.train_step(0, 4096, 1e-3)
+    assert not np.array_equal(w0, r.get_nedf_weights(0, w0.shape[0]))
+    r.load_state(blob)
+    assert np.array_equal(w0, r.get_nedf_weights(0, w0.shape[0]))
+    r.close()
