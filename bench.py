@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Throughput of the NeDF composition render path on GB300.
+
+Workload: 1024 instances of three analytic object types (sphere / torus / box) at random rigid
+transforms in [-20, 20]^3, a 1024x1024 pinhole frame, 4 point lights, NeDF 6x128 per type
+(trained here on ray-march labels), NeRF 8x256 colour network per type.
+
+A step is one composited frame: Step 1 (NeDF generation: binning, NeDF queries with the
+plain-method fallback below confidence 0.9 and 4-step bisection refinement, z-min), Step 2
+(deferred shading with 8 NeRF samples per pixel), Step 3 (shadow rays to 4 lights answered by
+NeDF queries) and the composite.  Beside it: the plain ray-marching frame on the same GPU, the
+depth error of the NeDF frame against a fine ray-march judge, the training throughput, an
+end-to-end number through the public API with host buffers, and the FP64 CPU oracle timed on
+the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "composited rays/s & ms/frame at 1024², NeDF vs ray-march, same GPU, depth err"
+WORKLOAD = ("1024 instances (sphere/torus/box, seed 3, T in [-20,20]^3) at 1024x1024, 4 point lights, "
+            "NeDF 6x128 per type trained on ray-march labels, NeRF 8x256 per type, 8 shading samples, "
+            "fallback below confidence 0.9, 4 refinement steps")
+NEDF_FLOP = 2 * (78 * 128 + 5 * 128 * 128 + 128 * 2)          # per query, unpadded
+NERF_FLOP = 2 * (90 * 256 + 7 * 256 * 256 + 256 * 3)          # per sample, unpadded
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and the reference arm)
+# ------------------------------------------------------------------------------------------------
+def oracle_rate(scene, nedf_weights, target_s, threads, fallback=0.9, refine=4, seed=11):
+    import oracle
+    oracle.build()
+    osc = oracle.OracleScene(scene, nedf_override=nedf_weights)
+    from paper_2308_04669_gb300 import scenegen as sg
+    n = 64
+    t0 = time.perf_counter()
+    oracle.render(osc, px=sg.pixel_subset(scene.W, scene.H, n, seed), fallback_conf=fallback, refine_steps=refine,
+                  march_n=128, march_b=4, n_threads=threads)
+    dt = time.perf_counter() - t0
+    n2 = int(min(scene.W * scene.H, max(64, n * target_s / max(dt, 1e-3))))
+    px = sg.pixel_subset(scene.W, scene.H, n2, seed + 1)
+    t0 = time.perf_counter()
+    oracle.render(osc, px=px, fallback_conf=fallback, refine_steps=refine, march_n=128, march_b=4, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return n2 / dt, n2, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2308_04669_gb300 import scenegen as sg
+    sc = sg.thousand_scene()
+    threads = os.cpu_count() or 1
+    per_step_s = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    import oracle
+    oracle.build()
+    osc = oracle.OracleScene(sc)
+    # calibrate a per-step pixel sample that takes about per_step_s on the host cores
+    t0 = time.perf_counter()
+    oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, 64, 99), fallback_conf=0.9, refine_steps=4, n_threads=threads)
+    n = int(max(64, 64 * per_step_s / max(time.perf_counter() - t0, 1e-3)))
+    for w in range(args.warmup):
+        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 200 + w), fallback_conf=0.9, refine_steps=4,
+                      n_threads=threads)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 300 + k), fallback_conf=0.9, refine_steps=4,
+                      n_threads=threads)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    ms_frame = 1000.0 * sc.W * sc.H / value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_frame, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORLOAD_REF, "sample_px_per_step": n},
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{n} seeded pixels of the 1024x1024 frame per step, all 1024 instances, "
+                                       f"untrained NeDF weights; ms_per_step extrapolates to the full frame"},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+WORLOAD_REF = WORKLOAD.replace("trained on ray-march labels", "(oracle: FP64, same scene)")
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def train_types(r, scene, steps, batch, n_rays, log):
+    import torch
+    t0 = time.perf_counter()
+    for t in range(len(scene.types)):
+        r.make_labels(t, n_rays, 2 + t, 256, 8)
+    torch.cuda.synchronize()
+    t_labels = time.perf_counter() - t0
+    losses = []
+    t0 = time.perf_counter()
+    for t in range(len(scene.types)):
+        first = r.train_step(t, batch, 1e-3, want_loss=True)
+        for s in range(steps - 2):
+            r.train_step(t, batch, 1e-3)
+        last = r.train_step(t, batch, 1e-3, want_loss=True)
+        losses.append((first, last))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    log["train"] = {"types": len(scene.types), "steps_per_type": steps, "batch": batch,
+                    "label_rays_per_type": n_rays, "label_s": round(t_labels, 3),
+                    "train_steps_per_s": round(len(scene.types) * steps / t_train, 2),
+                    "train_rays_per_s": round(len(scene.types) * steps * batch / t_train, 1),
+                    "loss_first_last": [[round(a, 5), round(b, 5)] for a, b in losses]}
+
+
+def run_ours(args):
+    import torch
+    from paper_2308_04669_gb300 import build as nbuild
+    rank, world, local = dist_setup(args.gpus)
+    if rank == 0 or True:
+        nbuild.build()
+    barrier(world)
+    from paper_2308_04669_gb300 import native
+    from paper_2308_04669_gb300 import scenegen as sg
+
+    sc = sg.thousand_scene()
+    stream = torch.cuda.current_stream()
+    prec = native.PREC_BF16 if args.precision == "bf16" else native.PREC_FP32
+    r = native.renderer_for(sc, precision=prec, stream=stream)
+    log = {}
+    train_types(r, sc, args.train_steps, args.train_batch, args.label_rays, log)
+    o = r.get_options()
+    o.fallback_conf, o.refine_steps = 0.9, 4
+    r.set_options(o)
+    cam, lights = r.camera(sc.eye, sc.target, sc.fov_deg), r.lights(sc.lights)
+    n = sc.W * sc.H
+    dev = "cuda"
+    depth = torch.empty(n, device=dev)
+    ids = torch.empty(n, dtype=torch.int32, device=dev)
+    out = torch.empty(n, 4, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # > 129 MB L2
+    r.set_profiling(True)
+    for _ in range(args.warmup):
+        r.render(cam, lights, depth, ids, None, None, out)
+    st = r.render(cam, lights, depth, ids, None, None, out, stats=True)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_sum = {}
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()                                   # L2 flushed between timed frames (untimed)
+            ev[k][0].record(stream)
+            r.render(cam, lights, depth, ids, None, None, out)
+            ev[k][1].record(stream)
+            for name, ms in r.stage_times().items():
+                stage_sum[name] = stage_sum.get(name, 0.0) + ms
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    barrier(world)
+    frame_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    frame_ms_max = allmax(frame_ms, world)
+    stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
+    clocks = clk.summary()
+
+    # ---- depth error against a fine ray-march judge ------------------------------------------
+    o2 = r.get_options()
+    saved = (o2.depth_source, o2.march_steps, o2.march_bisect, o2.fallback_conf, o2.refine_steps)
+    o2.depth_source, o2.march_steps, o2.march_bisect, o2.fallback_conf, o2.refine_steps = 1, 1024, 24, 0.0, 0
+    r.set_options(o2)
+    jdepth = torch.empty(n, device=dev)
+    jids = torch.empty(n, dtype=torch.int32, device=dev)
+    r.render(cam, lights, jdepth, jids, None, None, None)
+    (o2.depth_source, o2.march_steps, o2.march_bisect, o2.fallback_conf, o2.refine_steps) = saved
+    r.set_options(o2)
+    torch.cuda.synchronize()
+    both = (ids != -1) & (jids != -1)
+    err = (depth.double() - jdepth.double()).abs()[both] / 1.0       # r_b = 1, s = 1: world = local
+    derr = {"mean_over_rb": float(err.mean()) if err.numel() else None,
+            "median_over_rb": float(err.median()) if err.numel() else None,
+            "p99_over_rb": float(torch.quantile(err.float(), 0.99)) if err.numel() else None,
+            "pixels_both_hit": int(both.sum()),
+            "id_agreement": float((ids == jids)[both].double().mean()) if err.numel() else None,
+            "hit_mask_agreement": float(((ids != -1) == (jids != -1)).double().mean())}
+
+    # ---- plain ray-march frame on the same GPU ------------------------------------------------
+    march = {}
+    mrgba = torch.empty(n, 4, device=dev)
+    for es, key in [(1, "early_stop"), (0, "dense")]:
+        try:
+            r.render_march(cam, 128, es, mrgba)
+            torch.cuda.synchronize()
+            reps = 3 if es else 1
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                r.render_march(cam, 128, es, mrgba)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            march[key] = {"ms_per_frame": ms, "rays_per_s": n / (ms * 1e-3), "samples_per_pair": 128}
+        except native.NedfError as e:
+            march[key] = {"unavailable": str(e)}
+
+    # ---- end to end through the public API with host buffers ---------------------------------
+    host_out = torch.empty(n, 4, dtype=torch.float32, pin_memory=True)
+    inst_args = (sc.inst_type, sc.inst_R, sc.inst_T, sc.inst_s)
+    r.set_profiling(False)
+    for _ in range(2):
+        r.set_instances(*inst_args)
+        r.render_host(cam, lights, out=host_out.data_ptr())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r.set_instances(*inst_args)                          # H2D: this step's instance records
+        r.render_host(cam, lights, out=host_out.data_ptr())  # D2H: the composited frame
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    h2d = sc.n_inst * 56 + 16 * 0
+    d2h = n * 16
+
+    # ---- roofline of the dominant kernel ------------------------------------------------------
+    pk, pk_kind = peaks()
+    P1, P3, Hv = st.primary_pairs, st.shadow_pairs, st.hit_pixels
+    flops = {"step1_nedf": P1 * NEDF_FLOP, "step2_shade": Hv * sc.n_shade * NERF_FLOP, "step3_nedf": P3 * NEDF_FLOP}
+    dom = max(flops, key=lambda k: stage_ms.get(k, 0.0))
+    achieved = flops[dom] / (stage_ms[dom] * 1e-3) / 1e12
+    if prec == native.PREC_FP32:
+        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dom,
+                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock (CUDA-core path)"}
+    else:
+        peak = pk["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dom, "peak_basis": f"bf16 dense, {pk_kind} (burst)"}
+
+    # ---- CPU baseline: the oracle on the host cores ------------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        w_tr = {t: r.get_nedf_weights(t, sc.types[t].nedf_w.shape[0]).astype(np.float64)
+                for t in range(len(sc.types))}
+        threads = os.cpu_count() or 1
+        rate, npx, secs = oracle_rate(sc, w_tr, args.cpu_seconds, threads)
+        cpu = {"value": rate, "unit": "rays/s", "cores": threads, "kind": "oracle",
+               "sample": f"{npx} seeded pixels of the same 1024x1024 frame (same trained weights, all 1024 "
+                         f"instances, 4 lights), {secs:.1f} s on {threads} threads"}
+    r.close()
+
+    value = world * n / (frame_ms_max * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": frame_ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == native.PREC_FP32 else "bf16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "W": sc.W, "H": sc.H, "instances": sc.n_inst, "lights": 4,
+                       "l2": "flushed between timed frames (256 MiB write, outside the timed events)",
+                       "parallelism": f"replicas x{world} (one frame per GPU)"},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": world * n / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(st.kernel_launches) * args.steps,
+            "clocks": clocks,
+            "frame": {"ms": frame_ms, "total_rays_per_s": n * (1 + 4) / (frame_ms * 1e-3),
+                      "primary_pairs": P1, "shadow_pairs": P3, "hit_pixels": Hv, "fallback_pairs": st.fallback_pairs,
+                      "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "wall_s": t_wall},
+            "march_frame": march,
+            "speedup_vs_march": {k: v["ms_per_frame"] / frame_ms for k, v in march.items() if "ms_per_frame" in v},
+            "depth_err": derr, **log}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--train-steps", type=int, default=600)
+    ap.add_argument("--train-batch", type=int, default=16384)
+    ap.add_argument("--label-rays", type=int, default=1 << 20)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -51,6 +51,10 @@ struct nedf_handle {
     float *d_loss = nullptr;
     std::vector<TrainState> train;
     std::vector<DevType> types_host;
+    uint8_t *d_nedf_tc = nullptr, *d_nerf_tc = nullptr;   // BF16 blobs
+    size_t nedf_tc_stride = 0, nerf_tc_stride = 0;
+    void *d_march_scratch = nullptr;
+    size_t march_scratch_bytes = 0;
     bool profiling = false, profiled = false;
     cudaEvent_t ev[kStages + 1] = {};
     int last_launches = 0;
@@ -131,6 +135,12 @@ static Workspace make_ws(nedf_handle *h)
     ws.nedf_width = h->cfg.nedf_width;
     ws.nerf_hidden = h->cfg.nerf_hidden;
     ws.nerf_width = h->cfg.nerf_width;
+    ws.precision = h->cfg.precision;
+    ws.depth_source = h->opt.depth_source;
+    ws.nedf_tc = h->d_nedf_tc;
+    ws.nedf_tc_stride = h->nedf_tc_stride;
+    ws.nerf_tc = h->d_nerf_tc;
+    ws.nerf_tc_stride = h->nerf_tc_stride;
     return ws;
 }
 
@@ -164,6 +174,9 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
         return fail(nullptr, NEDF_ERR_UNSUPPORTED, "NeRF shape: hidden 0..16, width 64/128/256");
     if (c.precision != NEDF_PREC_FP32 && c.precision != NEDF_PREC_BF16)
         return fail(nullptr, NEDF_ERR_UNSUPPORTED, "precision");
+    if (c.precision == NEDF_PREC_BF16 && (c.nedf_width > 128 || (c.nedf_width == 128 && c.nedf_hidden > 7)))
+        return fail(nullptr, NEDF_ERR_UNSUPPORTED, "BF16 NeDF weights must fit in shared memory (width <= 128, "
+                                                   "at most 7 hidden layers of 128)");
     if (c.primary_pair_capacity < 0 || c.shadow_pair_capacity < 0)
         return fail(nullptr, NEDF_ERR_ARG, "negative capacity");
 
@@ -212,6 +225,14 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
     CA(h->d_cnt, sizeof(Counters));
     CA(h->d_status, sizeof(uint32_t));
     CA(h->d_loss, sizeof(float) * 4);
+    if (c.precision == NEDF_PREC_BF16) {
+        h->nedf_tc_stride = tc_blob_size(kNedfInPad, c.nedf_width, c.nedf_hidden, 2);
+        CA(h->d_nedf_tc, h->nedf_tc_stride * c.max_types);
+        if (c.nerf_hidden > 0) {
+            h->nerf_tc_stride = tc_blob_size(kNerfInPad, c.nerf_width, c.nerf_hidden, 3);
+            CA(h->d_nerf_tc, h->nerf_tc_stride * c.max_types);
+        }
+    }
 #undef CA
     if ((e = cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), h->stream)) != cudaSuccess) return bail(e, "memset");
     if ((e = cudaMemsetAsync(h->d_cnt, 0, sizeof(Counters), h->stream)) != cudaSuccess) return bail(e, "memset");
@@ -227,7 +248,8 @@ void nedf_compose_destroy(nedf_handle *h)
     cudaStreamSynchronize(h->stream);
     void *dev[] = {h->d_frame, h->d_cam, h->d_types, h->d_inst, h->d_nedf_w, h->d_nerf_w, h->d_keys,
                    h->d_depth, h->d_shadow, h->d_id, h->d_occl, h->d_hlist, h->d_rgba, h->d_out,
-                   h->d_ppairs, h->d_spairs, h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch};
+                   h->d_ppairs, h->d_spairs, h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch,
+                   h->d_march_scratch, h->d_nedf_tc, h->d_nerf_tc};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (TrainState &t : h->train) {
@@ -329,7 +351,28 @@ int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *ty
         CK(h, cudaMemset(ts.adam_v, 0, bytes));
         ts.step = 0;
         ts.cursor = 0;
+        if (h->d_nedf_tc)
+            CK(h, launch_pack_tc(ts.master, h->d_nedf_tc + (size_t)k * h->nedf_tc_stride, kNedfIn, kNedfInPad,
+                                 h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->stream));
     }
+    if (h->d_nerf_tc) {
+        float *tmp = nullptr;
+        CK(h, cudaMalloc((void **)&tmp, sizeof(float) * h->nerf_params));
+        for (int k = 0; k < n_types; ++k) {
+            cudaError_t e = cudaMemcpy(tmp, types[k].nerf_weights, sizeof(float) * h->nerf_params,
+                                       cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = launch_pack_tc(tmp, h->d_nerf_tc + (size_t)k * h->nerf_tc_stride, kNerfIn, kNerfInPad,
+                                   h->cfg.nerf_width, h->cfg.nerf_hidden, 3, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) {
+                cudaFree(tmp);
+                return cuda_fail(h, e, "NeRF weight packing");
+            }
+        }
+        cudaFree(tmp);
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
     return NEDF_OK;
 }
 
@@ -435,7 +478,7 @@ static int render_impl(nedf_handle *h, const nedf_camera *cam, const nedf_light 
     L.cam = h->d_cam;
     L.events = h->profiling ? h->ev : nullptr;
     L.launches = 0;
-    CK(h, launch_frame_f32(L));
+    CK(h, launch_frame(L));
     h->last_launches = L.launches;
     if (h->profiling) h->profiled = true;
     return NEDF_OK;
@@ -486,8 +529,30 @@ int nedf_compose_render_march(nedf_handle *h, const nedf_camera *cam, int n_samp
     if (r != NEDF_OK) return r;
     if (!rgba || n_samples < 1 || n_samples > 4096) return fail(h, NEDF_ERR_ARG, "rgba / n_samples 1..4096");
     CK(h, upload_frame(h, cam, &dummy, 1));
-    CK(h, launch_march_frame(make_ws(h), h->d_cam, h->cfg.width, h->cfg.height, h->n_inst, n_samples, early_stop,
-                             reinterpret_cast<float4 *>(rgba), h->num_sms, h->stream));
+    FrameLaunch L{};
+    L.ws = make_ws(h);
+    L.stream = h->stream;
+    L.W = h->cfg.width;
+    L.H = h->cfg.height;
+    L.num_sms = h->num_sms;
+    L.n_inst = h->n_inst;
+    L.n_shade = h->opt.n_shade;
+    L.cam = h->d_cam;
+    CK(h, launch_primary_binning(L));
+    // the pair count sizes the sample-row workspace (this path synchronises once)
+    unsigned long long pairs = 0;
+    CK(h, cudaMemcpyAsync(&pairs, &h->d_cnt->p_off[h->n_types], sizeof(pairs), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    size_t need = march_bytes(h->cfg.width * h->cfg.height, (long long)pairs, n_samples);
+    if (need > h->march_scratch_bytes) {
+        if (h->d_march_scratch) cudaFree(h->d_march_scratch);
+        h->d_march_scratch = nullptr;
+        h->march_scratch_bytes = 0;
+        CK(h, cudaMalloc(&h->d_march_scratch, need));
+        h->march_scratch_bytes = need;
+    }
+    CK(h, launch_march_colour_frame(L, h->d_march_scratch, (long long)pairs, n_samples, early_stop,
+                                    reinterpret_cast<float4 *>(rgba)));
     return NEDF_OK;
 }
 
@@ -521,7 +586,11 @@ int nedf_compose_nedf_query(nedf_handle *h, int type, int n, const float *o, con
     if (!h || !o || !d || !out) return fail(h, NEDF_ERR_ARG, "null argument");
     if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
     if (n < 0) return fail(h, NEDF_ERR_ARG, "n < 0");
-    CK(h, launch_nedf_query_f32(make_ws(h), type, o, d, out, n, h->num_sms, h->stream));
+    if (h->cfg.precision == NEDF_PREC_BF16)
+        CK(h, launch_nedf_tc(make_ws(h), h->d_nedf_tc, h->nedf_tc_stride, 2, type, o, d, out, n, h->num_sms,
+                             h->stream));
+    else
+        CK(h, launch_nedf_query_f32(make_ws(h), type, o, d, out, n, h->num_sms, h->stream));
     return NEDF_OK;
 }
 
@@ -622,6 +691,9 @@ int nedf_compose_train_step(nedf_handle *h, int type, int batch, float lr, float
     CK(h, launch_train_step(L, ts.o, ts.d, ts.m_star, ts.hit_star, ts.n_rays, ts.cursor, batch, ts.adam_m,
                             ts.adam_v, ts.step, lr));
     ts.cursor = (ts.cursor + batch) % ts.n_rays;
+    if (h->d_nedf_tc)
+        CK(h, launch_pack_tc(ts.master, h->d_nedf_tc + (size_t)type * h->nedf_tc_stride, kNedfIn, kNedfInPad,
+                             h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->stream));
     if (loss_host) {
         CK(h, cudaStreamSynchronize(h->stream));
         CK(h, cudaMemcpy(loss_host, h->d_loss, sizeof(float), cudaMemcpyDeviceToHost));
@@ -691,6 +763,9 @@ int nedf_compose_load_state(nedf_handle *h, const void *buf, size_t size)
         CK(h, cudaMemcpy(h->train[k].adam_v, p, wb, cudaMemcpyHostToDevice)); p += wb;
         TrainLaunch L = make_train_launch(h, k);
         CK(h, launch_refresh_weights(L));
+        if (h->d_nedf_tc)
+            CK(h, launch_pack_tc(h->train[k].master, h->d_nedf_tc + (size_t)k * h->nedf_tc_stride, kNedfIn,
+                                 kNedfInPad, h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->stream));
     }
     CK(h, cudaStreamSynchronize(h->stream));
     return NEDF_OK;

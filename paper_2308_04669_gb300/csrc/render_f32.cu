@@ -556,7 +556,20 @@ static cudaError_t shade_dispatch(const Workspace &ws, int grid, int npix, cudaS
     }
 }
 
-cudaError_t launch_frame_f32(FrameLaunch &L)
+cudaError_t launch_primary_binning(FrameLaunch &L)
+{
+    const Workspace &ws = L.ws;
+    cudaStream_t st = L.stream;
+    int npix = L.W * L.H;
+    k_setup<<<1, 256, 0, st>>>(ws, L.cam);
+    k_clear<<<L.num_sms * 4, 256, 0, st>>>(ws, npix);
+    k_bin_primary<0><<<L.n_inst, kThreads, 0, st>>>(ws);
+    k_scan_primary<<<1, 1, 0, st>>>(ws, kTileRows);
+    k_bin_primary<1><<<L.n_inst, kThreads, 0, st>>>(ws);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frame(FrameLaunch &L)
 {
     const Workspace &ws = L.ws;
     cudaStream_t st = L.stream;
@@ -575,20 +588,24 @@ cudaError_t launch_frame_f32(FrameLaunch &L)
     k_scan_primary<<<1, 1, 0, st>>>(ws, kTileRows);
     k_bin_primary<1><<<L.n_inst, kThreads, 0, st>>>(ws);
     mark();
-    cudaError_t e = nedf_dispatch(ws, gsm * 4, 0, st);
+    const bool tc = ws.precision == 1 && ws.depth_source == 0;
+    cudaError_t e = tc ? launch_nedf_tc(ws, ws.nedf_tc, ws.nedf_tc_stride, 0, 0, nullptr, nullptr, nullptr, 0, gsm, st)
+                       : nedf_dispatch(ws, gsm * 4, 0, st);
     if (e != cudaSuccess) return e;
     mark();
     k_resolve<<<gsm * 4, 256, 0, st>>>(ws, npix);
     k_scan_shade<<<1, 1, 0, st>>>(ws, kTileRows / L.n_shade);
     mark();
-    e = shade_dispatch(ws, gsm * 4, npix, st);
+    e = (ws.precision == 1 && ws.nerf_hidden > 0) ? launch_shade_tc(ws, ws.nerf_tc, ws.nerf_tc_stride, npix, gsm, st)
+                                                   : shade_dispatch(ws, gsm * 4, npix, st);
     if (e != cudaSuccess) return e;
     mark();
     k_bin_shadow<0><<<gsm * 8, kThreads, 0, st>>>(ws, npix);
     k_scan_shadow<<<1, 1, 0, st>>>(ws, kTileRows);
     k_bin_shadow<1><<<gsm * 8, kThreads, 0, st>>>(ws, npix);
     mark();
-    e = nedf_dispatch(ws, gsm * 4, 1, st);
+    e = tc ? launch_nedf_tc(ws, ws.nedf_tc, ws.nedf_tc_stride, 1, 0, nullptr, nullptr, nullptr, 0, gsm, st)
+           : nedf_dispatch(ws, gsm * 4, 1, st);
     if (e != cudaSuccess) return e;
     mark();
     k_composite<<<gsm * 4, 256, 0, st>>>(ws, npix);

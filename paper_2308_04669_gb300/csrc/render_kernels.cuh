@@ -55,6 +55,13 @@ struct Workspace {
     const float *nerf_w;
     long long nerf_stride;
     int nedf_hidden, nedf_width, nerf_hidden, nerf_width;
+    // BF16 tensor-core weight blobs (per type, fixed stride); precision 1 selects them
+    int precision;
+    int depth_source;            // host copy of the frame option (selects kernels)
+    const uint8_t *nedf_tc;
+    size_t nedf_tc_stride;
+    const uint8_t *nerf_tc;
+    size_t nerf_tc_stride;
 };
 
 }  // namespace nedf

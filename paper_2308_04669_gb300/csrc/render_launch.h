@@ -19,11 +19,22 @@ struct FrameLaunch {
 
 constexpr int kStages = 8;
 
-cudaError_t launch_frame_f32(FrameLaunch &L);
+cudaError_t launch_frame(FrameLaunch &L);
+
+// BF16 tensor-core path (render_tc.cu)
+size_t tc_blob_size(int K0, int N, int L, int n_out);
+cudaError_t launch_pack_tc(const float *master, void *blob, int K_in, int K0, int N, int L, int n_out,
+                           cudaStream_t st);
+// mode 0: Step-1 pairs, 1: Step-3 pairs, 2: n caller rays (o, d) of `type` -> out float4[n]
+cudaError_t launch_nedf_tc(const Workspace &ws, const void *blobs, size_t stride, int mode, int type,
+                           const float *o, const float *d, float *out, int n, int num_sms, cudaStream_t st);
+cudaError_t launch_shade_tc(const Workspace &ws, const void *blobs, size_t stride, int npix, int num_sms,
+                            cudaStream_t st);
 cudaError_t launch_nedf_query_f32(const Workspace &ws, int type, const float *o, const float *d,
                                   float *out, int n, int num_sms, cudaStream_t st);
-cudaError_t launch_march_frame(const Workspace &ws, const HostCamera *cam, int W, int H, int n_inst,
-                               int n_samples, int early_stop, float4 *rgba, int num_sms,
-                               cudaStream_t st);
+cudaError_t launch_primary_binning(FrameLaunch &L);
+size_t march_bytes(int npix, long long pairs, int n_samples);
+cudaError_t launch_march_colour_frame(const FrameLaunch &L, void *scratch, long long pairs_cap, int n_samples,
+                                      int early_stop, float4 *rgba);
 
 }  // namespace nedf

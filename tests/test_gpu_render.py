@@ -179,3 +179,43 @@ def test_pair_capacity_overflow_is_reported(orc):
         r.render(r.camera(sc.eye, sc.target, sc.fov_deg), r.lights(sc.lights), stats=True)
     assert e.value.code == native.NEDF_ERR_CAPACITY
     r.close()
+
+
+def _march_gpu(sc, n_samples, early_stop):
+    import torch
+    from paper_2308_04669_gb300 import native
+    r = native.renderer_for(sc)
+    rgba = torch.empty(sc.W * sc.H, 4, device="cuda")
+    r.render_march(r.camera(sc.eye, sc.target, sc.fov_deg), n_samples, early_stop, rgba)
+    torch.cuda.synchronize()
+    r.sync()
+    out = rgba.cpu().numpy().astype(np.float64)
+    r.close()
+    return out
+
+
+def test_plain_method_frame_dense_matches_oracle(orc):
+    """Plain method (every NeRF volume rendered front to back), albedo sphere, full frame."""
+    sc = sg.tiny_sphere_scene()
+    g = _march_gpu(sc, 128, 0)
+    o = orc.volume_render(orc.OracleScene(sc), 128)
+    ok = close(g, o)
+    assert ok.mean() > 0.999 and (o[:, 3] > 0.5).sum() > 500
+
+
+def test_plain_method_frame_nerf_subset(orc):
+    """Three types with 8x256 colour networks, overlapping bounds; subset of pixels."""
+    sc = sg.three_types_scene(96, 96)
+    g = _march_gpu(sc, 64, 0)
+    px = sg.pixel_subset(96, 96, 160, 3)
+    o = orc.volume_render(orc.OracleScene(sc), 64, px=px, n_threads=8)
+    ok = close(g[px], o)
+    assert ok.mean() > 0.995 and (o[:, 3] > 0.5).sum() > 10
+
+
+def test_plain_method_early_stop_bound(orc):
+    """Early stop (T < 1e-4, weights < 1e-6 skipped) changes colour by at most ~1e-3."""
+    sc = sg.three_types_scene(96, 96)
+    dense = _march_gpu(sc, 128, 0)
+    es = _march_gpu(sc, 128, 1)
+    assert np.abs(dense - es).max() < 2e-3

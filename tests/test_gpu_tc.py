@@ -1,0 +1,113 @@
+"""BF16 tensor-core path (tcgen05 MMAs, TMEM accumulators) vs the oracle in BF16-operand mode.
+
+The oracle's QUANT_BF16 mode rounds every layer's inputs and weights to BF16 and accumulates in
+FP64; the kernels accumulate in FP32 in TMEM.  Differences come from accumulation order and from
+the rare activation that lands on the other side of a BF16 rounding boundary (one BF16 ulp,
+2^-8 relative, on one of 128-256 inputs of the next layer), so the network outputs are compared
+with a 1e-2 absolute + 1e-2 relative bound and a median error bound of 1e-3.  The error of the
+BF16 path against the unrounded FP64 network is reported alongside.
+"""
+import numpy as np
+import pytest
+
+from paper_2308_04669_gb300 import scenegen as sg
+
+from .gpu_helpers import NOID, close, gpu_frame
+
+pytestmark = pytest.mark.gpu
+
+BF16_ABS, BF16_REL = 1e-2, 1e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2308_04669_gb300 import build
+    build.build()
+
+
+def run_query(sc, t, o32, d32, precision):
+    import torch
+    from paper_2308_04669_gb300 import native
+    r = native.renderer_for(sc, precision=precision)
+    out = torch.empty(o32.shape[0], 4, device="cuda")
+    r.nedf_query(t, torch.tensor(o32, device="cuda"), torch.tensor(d32, device="cuda"), out)
+    torch.cuda.synchronize()
+    r.close()
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("scene_fn", [sg.tiny_sphere_scene, lambda: sg.three_types_scene(8, 8, nerf=False)])
+def test_bf16_nedf_query_matches_bf16_oracle(orc, scene_fn):
+    from paper_2308_04669_gb300 import native
+    sc = scene_fn()
+    rng = np.random.default_rng(4)
+    n = 1000                      # 7 full tiles of 128 rows and a ragged tail
+    o32 = (rng.normal(size=(n, 3)) * 1.2).astype(np.float32)
+    d32 = rng.normal(size=(n, 3)).astype(np.float32)
+    for t in range(len(sc.types)):
+        g = run_query(sc, t, o32, d32, native.PREC_BF16)
+        w = sc.types[t].nedf_w.astype(np.float64)
+        errs, errs_fp = [], []
+        for i in range(n):
+            dd = d32[i].astype(np.float64); dd /= np.linalg.norm(dd)
+            kept, f, b = orc.nedf_features(o32[i].astype(np.float64), dd, float(sc.types[t].rb))
+            if not kept:
+                if abs(b[3]) > 1e-4:
+                    assert g[i, 3] == 0 and np.isinf(g[i, 2])
+                continue
+            yq = orc.mlp(w, sc.types[t].nedf_dims, f, quant=orc.QUANT_BF16)
+            yf = orc.mlp(w, sc.types[t].nedf_dims, f)
+            assert close(g[i, :2], yq, BF16_ABS, BF16_REL).all(), (i, g[i, :2], yq)
+            errs.append(np.abs(g[i, :2] - yq).max())
+            errs_fp.append(np.abs(g[i, :2] - yf).max())
+        assert len(errs) > 300
+        assert np.median(errs) < 1e-3
+        print(f"type {t}: median |bf16 gpu - bf16 oracle| {np.median(errs):.2e}, "
+              f"median |bf16 gpu - fp64 network| {np.median(errs_fp):.2e}")
+
+
+def test_bf16_shading_matches_bf16_oracle(orc):
+    """Step 2 on the tensor cores (NeRF 8x256 streamed layer by layer), surface depths from the
+    plain method so that every shaded pixel has non-trivial opacity and colour."""
+    from paper_2308_04669_gb300 import native
+    sc = sg.three_types_scene(128, 128)
+    px = sg.pixel_subset(128, 128, 500, 8)
+    g = gpu_frame(sc, precision=native.PREC_BF16, depth_source=1)
+    o = orc.render(orc.OracleScene(sc), px=px, depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4,
+                   quant=orc.QUANT_BF16, n_threads=8)
+    same = (g["id"][px] == o["id"]) & (o["id"] != NOID) & (o["pmargin"] > 1e-3) & (o["gap"] > 1e-4)
+    assert same.sum() > 40
+    ok = close(g["rgba"][px][same], o["rgba"][same], 2e-3, 2e-3)
+    assert ok.mean() > 0.995, np.abs(g["rgba"][px][same] - o["rgba"][same]).max()
+    assert (o["rgba"][same][:, 3] > 0.3).mean() > 0.5
+
+
+def test_bf16_full_frame_nedf(orc):
+    """Steps 1-3 with the NeDF on the tensor cores: ids where the BF16 oracle's decisions are
+    clear of the BF16 error, depths within the depth bound that error implies (rb * 1e-2)."""
+    from paper_2308_04669_gb300 import native
+    sc = sg.three_types_scene(128, 128)
+    px = sg.pixel_subset(128, 128, 500, 9)
+    g = gpu_frame(sc, precision=native.PREC_BF16)
+    o = orc.render(orc.OracleScene(sc), px=px, quant=orc.QUANT_BF16, n_threads=8)
+    decided = (o["pmargin"] > 3e-2) & ((o["gap"] > 3e-2) | (o["id"] == NOID))
+    assert decided.mean() > 0.8
+    gid = g["id"][px]
+    assert (gid[decided] == o["id"][decided]).all()
+    both = decided & (o["id"] != NOID)
+    assert close(g["depth"][px][both], o["depth"][both], 2e-2, 1e-2).all()
+    sd = both & (o["smargin"] > 3e-2)
+    assert (g["shadow"][px][sd] == o["shadow"][sd]).mean() > 0.99
+
+
+def test_bf16_thousand_instances_stats(orc):
+    """The 1024-instance workload runs clean on the tensor-core path and agrees with FP32 on the
+    pair counts (binning does not depend on precision)."""
+    from paper_2308_04669_gb300 import native
+    sc = sg.thousand_scene()
+    a = gpu_frame(sc, precision=native.PREC_FP32)
+    b = gpu_frame(sc, precision=native.PREC_BF16)
+    assert a["stats"].primary_pairs == b["stats"].primary_pairs
+    assert b["stats"].status == 0
+    both = (a["id"] != NOID) & (b["id"] != NOID)
+    assert (a["id"][both] == b["id"][both]).mean() > 0.97
