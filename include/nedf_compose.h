@@ -104,6 +104,10 @@ typedef struct nedf_options {
     float fallback_conf;     /* NeDF pairs with max(p, 1-p) < this (p = sigmoid(a)) are         */
                              /* re-answered by the plain method; 0 disables; default 0          */
     int refine_steps;        /* density bisection steps in [D - h, D + h] after a NeDF hit; 0   */
+    int outlier_resample;    /* with refine_steps > 0: a NeDF hit whose window [D - h, D + h] has */
+                             /* no crossing of the half-density level is an outlier (the density */
+                             /* check of Section "Deferred Shading") and is re-answered by the   */
+                             /* plain method; default 0                                          */
 } nedf_options;
 
 typedef struct nedf_type_desc {

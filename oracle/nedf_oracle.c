@@ -362,21 +362,26 @@ int orc_query(const orc_scene *sc, const orc_opts *op, int inst, const double o[
         Dl = bd[2] - t->rb * y[0];
         hit = (y[1] > 0.0) && (Dl > 0.0);
         mg = dmin(mg, dmin(fabs(y[1]), fabs(Dl) / t->rb));
+        /* Low-confidence pairs are re-answered by the plain method. */
+        int march = 0;
         if (op->fallback_conf > 0.0) {
             double pr = 1.0 / (1.0 + exp(-y[1]));
             double conf = dmax(pr, 1.0 - pr);
             mg = dmin(mg, fabs(conf - op->fallback_conf));
-            if (conf < op->fallback_conf)
-                Dl = orc_march_depth(sc, sc->inst_type[inst], ol, dl, bd[0], bd[1], op->march_n,
-                                     op->march_b, &hit);
+            march = conf < op->fallback_conf;
         }
-        if (hit && op->refine_steps > 0) {
-            /* Bisection of the density level set inside [D - h, D + h] when it brackets it. */
+        /* Depth check of a NeDF hit (Section "Deferred Shading": the density at the predicted
+         * depth tells whether it reached the surface): if the half-density level is crossed
+         * inside [D - h, D + h], bisect it; otherwise the hit is an outlier, re-answered by the
+         * plain method when outlier_resample is set. */
+        if (!march && hit && op->refine_steps > 0) {
             double lo = Dl - sc->shade_half, hi = Dl + sc->shade_half, x[3];
             for (int c = 0; c < 3; ++c) x[c] = ol[c] + lo * dl[c];
             int in_lo = inside_solid(sc, sc->inst_type[inst], x);
+            mg = dmin(mg, fabs(orc_sdf(t->kind, t->params, x)));
             for (int c = 0; c < 3; ++c) x[c] = ol[c] + hi * dl[c];
             int in_hi = inside_solid(sc, sc->inst_type[inst], x);
+            mg = dmin(mg, fabs(orc_sdf(t->kind, t->params, x)));
             if (!in_lo && in_hi) {
                 for (int it = 0; it < op->refine_steps; ++it) {
                     double mid = 0.5 * (lo + hi);
@@ -385,8 +390,13 @@ int orc_query(const orc_scene *sc, const orc_opts *op, int inst, const double o[
                 }
                 Dl = 0.5 * (lo + hi);
                 hit = Dl > 0.0;
+                mg = dmin(mg, fabs(Dl) / t->rb);
+            } else if (op->outlier_resample) {
+                march = 1;
             }
         }
+        if (march)
+            Dl = orc_march_depth(sc, sc->inst_type[inst], ol, dl, bd[0], bd[1], op->march_n, op->march_b, &hit);
     }
     out6[0] = Dl;
     *margin = mg;

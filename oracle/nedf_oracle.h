@@ -61,6 +61,8 @@ typedef struct {
     double fallback_conf;  /* MLP mode: march the pair when max(p,1-p) < this (0 = never) */
     int refine_steps;      /* MLP mode: density bisection steps around the NeDF depth (0 = off) */
     int n_threads;
+    int outlier_resample;  /* MLP mode, with refine_steps > 0: a NeDF hit whose window [D-h, D+h]
+                              holds no density crossing is re-answered by the plain method */
 } orc_opts;
 
 /* Geometry and encoding */

@@ -52,6 +52,11 @@ struct nedf_handle {
     std::vector<TrainState> train;
     std::vector<DevType> types_host;
     uint8_t *d_nedf_tc = nullptr, *d_nerf_tc = nullptr;   // BF16 blobs
+    uint32_t *d_fb[2] = {nullptr, nullptr};
+    LightCam *d_lcam = nullptr;
+    uint32_t *d_lg_count = nullptr, *d_lg_off = nullptr, *d_lg_cursor = nullptr, *d_lg_items = nullptr;
+    uint32_t *d_lg_big = nullptr, *d_lg_big_count = nullptr, *d_scan_tmp = nullptr;
+    long long lg_cap = 0;
     size_t nedf_tc_stride = 0, nerf_tc_stride = 0;
     void *d_march_scratch = nullptr;
     size_t march_scratch_bytes = 0;
@@ -141,6 +146,19 @@ static Workspace make_ws(nedf_handle *h)
     ws.nedf_tc_stride = h->nedf_tc_stride;
     ws.nerf_tc = h->d_nerf_tc;
     ws.nerf_tc_stride = h->nerf_tc_stride;
+    ws.fb_list[0] = h->d_fb[0];
+    ws.fb_list[1] = h->d_fb[1];
+    ws.lcam = h->d_lcam;
+    ws.lg_count = h->d_lg_count;
+    ws.lg_off = h->d_lg_off;
+    ws.lg_cursor = h->d_lg_cursor;
+    ws.lg_items = h->d_lg_items;
+    ws.lg_cap = h->lg_cap;
+    ws.lg_big = h->d_lg_big;
+    ws.lg_big_count = h->d_lg_big_count;
+    ws.lg_G = kLightGridSize;
+    ws.max_inst = h->cfg.max_instances;
+    ws.scan_tmp = h->d_scan_tmp;
     return ws;
 }
 
@@ -186,7 +204,7 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
     if (h->cfg.primary_pair_capacity == 0) h->cfg.primary_pair_capacity = 8 * npix;
     if (h->cfg.shadow_pair_capacity == 0) h->cfg.shadow_pair_capacity = 4 * npix * NEDF_MAX_LIGHTS / 8;
     h->stream = (cudaStream_t)cuda_stream;
-    h->opt = nedf_options{8, 0.05f, 0.5f, 0.02f, 50.0f, 0.01f, NEDF_DEPTH_NEDF, 128, 4, 0.0f, 0};
+    h->opt = nedf_options{8, 0.05f, 0.5f, 0.02f, 50.0f, 0.01f, NEDF_DEPTH_NEDF, 128, 4, 0.0f, 0, 0};
     h->nedf_params = mlp_params(kNedfIn, c.nedf_hidden, c.nedf_width, 2);
     h->nerf_params = mlp_params(kNerfIn, c.nerf_hidden, c.nerf_width, 3);
     auto bail = [&](cudaError_t e, const char *what) {
@@ -225,6 +243,20 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
     CA(h->d_cnt, sizeof(Counters));
     CA(h->d_status, sizeof(uint32_t));
     CA(h->d_loss, sizeof(float) * 4);
+    CA(h->d_fb[0], sizeof(uint32_t) * h->cfg.primary_pair_capacity);
+    CA(h->d_fb[1], sizeof(uint32_t) * h->cfg.shadow_pair_capacity);
+    {
+        const size_t cells = (size_t)NEDF_MAX_LIGHTS * kLightGridSize * kLightGridSize;
+        h->lg_cap = (long long)c.max_instances * 64 * 8;
+        CA(h->d_lcam, sizeof(LightCam) * NEDF_MAX_LIGHTS);
+        CA(h->d_lg_count, sizeof(uint32_t) * cells);
+        CA(h->d_lg_off, sizeof(uint32_t) * (cells + 1));
+        CA(h->d_lg_cursor, sizeof(uint32_t) * cells);
+        CA(h->d_lg_items, sizeof(uint32_t) * h->lg_cap);
+        CA(h->d_lg_big, sizeof(uint32_t) * (size_t)NEDF_MAX_LIGHTS * c.max_instances);
+        CA(h->d_lg_big_count, sizeof(uint32_t) * NEDF_MAX_LIGHTS);
+        CA(h->d_scan_tmp, sizeof(uint32_t) * 1024);
+    }
     if (c.precision == NEDF_PREC_BF16) {
         h->nedf_tc_stride = tc_blob_size(kNedfInPad, c.nedf_width, c.nedf_hidden, 2);
         CA(h->d_nedf_tc, h->nedf_tc_stride * c.max_types);
@@ -249,7 +281,9 @@ void nedf_compose_destroy(nedf_handle *h)
     void *dev[] = {h->d_frame, h->d_cam, h->d_types, h->d_inst, h->d_nedf_w, h->d_nerf_w, h->d_keys,
                    h->d_depth, h->d_shadow, h->d_id, h->d_occl, h->d_hlist, h->d_rgba, h->d_out,
                    h->d_ppairs, h->d_spairs, h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch,
-                   h->d_march_scratch, h->d_nedf_tc, h->d_nerf_tc};
+                   h->d_march_scratch, h->d_nedf_tc, h->d_nerf_tc, h->d_fb[0], h->d_fb[1], h->d_lcam,
+                   h->d_lg_count, h->d_lg_off, h->d_lg_cursor, h->d_lg_items, h->d_lg_big,
+                   h->d_lg_big_count, h->d_scan_tmp};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (TrainState &t : h->train) {
@@ -438,6 +472,7 @@ static cudaError_t upload_frame(nedf_handle *h, const nedf_camera *cam, const ne
     f.march_bisect = h->opt.march_bisect;
     f.fallback_conf = h->opt.fallback_conf;
     f.refine_steps = h->opt.refine_steps;
+    f.outlier_resample = h->opt.outlier_resample;
     f.n_inst = h->n_inst;
     f.n_types = h->n_types;
     std::memcpy(h->h_cam->eye, cam->eye, sizeof(cam->eye));
@@ -475,6 +510,7 @@ static int render_impl(nedf_handle *h, const nedf_camera *cam, const nedf_light 
     L.num_sms = h->num_sms;
     L.n_inst = h->n_inst;
     L.n_shade = h->opt.n_shade;
+    L.n_lights = n_lights;
     L.cam = h->d_cam;
     L.events = h->profiling ? h->ev : nullptr;
     L.launches = 0;

@@ -52,6 +52,7 @@ struct DevFrame {
     int march_steps, march_bisect;
     float fallback_conf;
     int refine_steps;
+    int outlier_resample;
     int n_inst, n_types;
 };
 
@@ -210,6 +211,39 @@ __device__ __forceinline__ float refine_depth(const DevType &t, V3 ol, V3 dl, fl
         if (inside_solid(t, madd(ol, mid, dl))) hi = mid; else lo = mid;
     }
     return 0.5f * (lo + hi);
+}
+
+// Decode of one NeDF answer (Eq. 2, Eq. 1's hit indicator) and the checks around it:
+//   D_l = t_perp - rb * m, hit = (a > 0) and (D_l > 0);
+//   a pair whose confidence max(p, 1 - p), p = sigmoid(a), is below fallback_conf goes to the
+//   plain method; a hit whose window [D_l - h, D_l + h] brackets the half-density level is
+//   refined by bisection there; a hit whose window does not is an outlier and, with
+//   outlier_resample, also goes to the plain method.
+// Returns true when the pair must be re-answered by the plain method.
+__device__ __forceinline__ bool nedf_decode(const DevFrame &f, const DevType &T, V3 ol, V3 dl, float tp, float m,
+                                            float a, float &Dl, bool &hit)
+{
+    Dl = tp - T.rb * m;
+    hit = (a > 0.0f) && (Dl > 0.0f);
+    bool march = false;
+    if (f.fallback_conf > 0.0f) {
+        float p = 1.0f / (1.0f + expf(-a));
+        march = fmaxf(p, 1.0f - p) < f.fallback_conf;
+    }
+    if (!march && hit && f.refine_steps > 0) {
+        float lo = Dl - f.shade_half, hi = Dl + f.shade_half;
+        if (!inside_solid(T, madd(ol, lo, dl)) && inside_solid(T, madd(ol, hi, dl))) {
+            for (int it = 0; it < f.refine_steps; ++it) {
+                float mid = 0.5f * (lo + hi);
+                if (inside_solid(T, madd(ol, mid, dl))) hi = mid; else lo = mid;
+            }
+            Dl = 0.5f * (lo + hi);
+            hit = Dl > 0.0f;
+        } else if (f.outlier_resample) {
+            march = true;
+        }
+    }
+    return march;
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -169,13 +169,6 @@ __global__ void k_scan_primary(Workspace ws, int rows_per_tile)
               rows_per_tile, ws.status, kStatusPrimaryOverflow, &ws.cnt->p_total_requested);
 }
 
-__global__ void k_scan_shadow(Workspace ws, int rows_per_tile)
-{
-    const DevFrame &f = *ws.frame;
-    scan_list(ws.cnt->s_count, ws.cnt->s_cursor, ws.cnt->s_off, ws.cnt->s_tile, f.n_types, ws.scap,
-              rows_per_tile, ws.status, kStatusShadowOverflow, &ws.cnt->s_total_requested);
-}
-
 __global__ void k_scan_shade(Workspace ws, int pixels_per_tile)
 {
     const DevFrame &f = *ws.frame;
@@ -279,19 +272,9 @@ __global__ void __launch_bounds__(kThreads) k_nedf_tiles(Workspace ws, int shado
             if (use_march) {
                 Dl = march_crossing(T, ol, dl, ri.te, ri.tx, f.march_steps, f.march_bisect, hit);
             } else {
-                float m = y[threadIdx.x][0], a = y[threadIdx.x][1];
-                Dl = ri.tp - ri.rb * m;
-                hit = (a > 0.0f) && (Dl > 0.0f);
-                if (f.fallback_conf > 0.0f) {
-                    float p = 1.0f / (1.0f + expf(-a));
-                    if (fmaxf(p, 1.0f - p) < f.fallback_conf) {
-                        Dl = march_crossing(T, ol, dl, ri.te, ri.tx, f.march_steps, f.march_bisect, hit);
-                        atomicAdd(&ws.cnt->fallback, 1ull);
-                    }
-                }
-                if (hit && f.refine_steps > 0) {
-                    Dl = refine_depth(T, ol, dl, Dl, f.shade_half, f.refine_steps);
-                    hit = Dl > 0.0f;
+                if (nedf_decode(f, T, ol, dl, ri.tp, y[threadIdx.x][0], y[threadIdx.x][1], Dl, hit)) {
+                    Dl = march_crossing(T, ol, dl, ri.te, ri.tx, f.march_steps, f.march_bisect, hit);
+                    atomicAdd(&ws.cnt->fallback, 1ull);
                 }
             }
             if (hit) {
@@ -357,7 +340,7 @@ __global__ void __launch_bounds__(kThreads) k_shade_tiles(Workspace ws, int npix
         int t = 0;
         while (t + 1 < n_types && C.h_tile[t + 1] <= tile) ++t;
         unsigned long long first = (tile - C.h_tile[t]) * ppt;
-        int n_pix = (int)min((unsigned long long)ppt, C.h_count[t] - first);
+        int n_pix = first < C.h_count[t] ? (int)min((unsigned long long)ppt, C.h_count[t] - first) : 0;
         const DevType T = ws.types[t];
         if (threadIdx.x < ppt * ns) {
             int q = threadIdx.x / ns, j = threadIdx.x - q * ns;
@@ -415,76 +398,6 @@ __global__ void __launch_bounds__(kThreads) k_shade_tiles(Workspace ws, int npix
             ws.rgba[tile_pix[q]] = make_float4(cr, cg, cb, A);
         }
         __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------------------------
-// Step 3 binning: every (valid pixel, light) shadow ray against every instance, exact cull,
-// and only bounds the segment light -> surface point enters before the point.
-// ---------------------------------------------------------------------------------------------
-template <int PASS>
-__global__ void __launch_bounds__(kThreads) k_bin_shadow(Workspace ws, int npix)
-{
-    __shared__ DevInst sI[128];
-    __shared__ float srb[128];
-    __shared__ unsigned long long cnt_t[kMaxTypes];
-    const DevFrame &f = *ws.frame;
-    const int nl = f.n_lights, n_inst = f.n_inst;
-    const long long n_rays = (long long)npix * nl;
-    if (PASS == 0)
-        for (int k = threadIdx.x; k < kMaxTypes; k += blockDim.x) cnt_t[k] = 0;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < n_rays; base += (long long)gridDim.x * blockDim.x) {
-        long long r = base + threadIdx.x;
-        bool valid = r < n_rays;
-        uint32_t pix = 0, l = 0;
-        V3 o = v3(0, 0, 0), d = v3(0, 0, 1);
-        float ell = 0.0f;
-        if (valid) {
-            pix = (uint32_t)(r / nl); l = (uint32_t)(r - (long long)pix * nl);
-            valid = ws.id[pix] != kNoId;
-            if (valid) {
-                V3 oc, dc;
-                camera_ray(f, pix % f.W, pix / f.W, oc, dc);
-                V3 x = madd(oc, ws.depth[pix], dc);
-                o = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
-                V3 v = sub(x, o);
-                ell = sqrtf(dot(v, v));
-                d = normalized(v);
-            }
-        }
-        bool any = __syncthreads_or(valid);
-        if (!any) continue;
-        for (int c0 = 0; c0 < n_inst; c0 += 128) {
-            int nc = min(128, n_inst - c0);
-            __syncthreads();
-            for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-                sI[k] = ws.inst[c0 + k];
-                srb[k] = ws.types[sI[k].type].rb;
-            }
-            __syncthreads();
-            for (int k = 0; k < nc; ++k) {
-                bool keep = false;
-                if (valid) {
-                    V3 ol, dl;
-                    to_local(sI[k], o, d, ol, dl);
-                    Chord ch;
-                    keep = bound_chord(ol, dl, srb[k], ch) && (ch.te * sI[k].s < ell);
-                }
-                uint32_t ty = sI[k].type;
-                if (PASS == 0) {
-                    unsigned m = __ballot_sync(0xffffffffu, keep);
-                    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&cnt_t[ty], (unsigned long long)__popc(m));
-                } else {
-                    warp_append(keep, make_uint2(pix * nl + l, (uint32_t)(c0 + k)), &ws.cnt->s_cursor[ty],
-                                &ws.cnt->s_off[ty + 1], ws.spairs, ws.status, kStatusShadowOverflow);
-                }
-            }
-        }
-    }
-    if (PASS == 0) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < f.n_types; k += blockDim.x)
-            if (cnt_t[k]) atomicAdd(&ws.cnt->s_count[k], cnt_t[k]);
     }
 }
 
@@ -576,6 +489,12 @@ cudaError_t launch_frame(FrameLaunch &L)
     int npix = L.W * L.H;
     int gsm = L.num_sms;
     int stage = 0;
+    // the tensor-core kernels take 128-row tiles, the CUDA-core kernels 64-row tiles; the work
+    // list scans must use the tile size of the kernel that consumes the list
+    const bool tc_nedf = ws.precision == 1 && ws.depth_source == 0;
+    const bool tc_shade = ws.precision == 1 && ws.nerf_hidden > 0;
+    const int nedf_rows = tc_nedf ? kTcTileRows : kTileRows;
+    const int shade_rows = tc_shade ? kTcTileRows : kTileRows;
     auto mark = [&]() {
         if (L.events) cudaEventRecord(L.events[stage], st);
         ++stage;
@@ -585,32 +504,40 @@ cudaError_t launch_frame(FrameLaunch &L)
     k_clear<<<gsm * 4, 256, 0, st>>>(ws, npix);
     mark();
     k_bin_primary<0><<<L.n_inst, kThreads, 0, st>>>(ws);
-    k_scan_primary<<<1, 1, 0, st>>>(ws, kTileRows);
+    k_scan_primary<<<1, 1, 0, st>>>(ws, nedf_rows);
     k_bin_primary<1><<<L.n_inst, kThreads, 0, st>>>(ws);
     mark();
-    const bool tc = ws.precision == 1 && ws.depth_source == 0;
-    cudaError_t e = tc ? launch_nedf_tc(ws, ws.nedf_tc, ws.nedf_tc_stride, 0, 0, nullptr, nullptr, nullptr, 0, gsm, st)
-                       : nedf_dispatch(ws, gsm * 4, 0, st);
+    cudaError_t e = tc_nedf ? launch_nedf_tc(ws, ws.nedf_tc, ws.nedf_tc_stride, 0, 0, nullptr, nullptr, nullptr, 0, gsm, st)
+                            : nedf_dispatch(ws, gsm * 4, 0, st);
     if (e != cudaSuccess) return e;
+    int launches = 6;
+    if (tc_nedf) {                        // pairs the tensor-core kernel deferred to the plain method
+        if ((e = launch_fallback(ws, 0, gsm, st)) != cudaSuccess) return e;
+        ++launches;
+    }
     mark();
     k_resolve<<<gsm * 4, 256, 0, st>>>(ws, npix);
-    k_scan_shade<<<1, 1, 0, st>>>(ws, kTileRows / L.n_shade);
+    k_scan_shade<<<1, 1, 0, st>>>(ws, shade_rows / L.n_shade);
     mark();
-    e = (ws.precision == 1 && ws.nerf_hidden > 0) ? launch_shade_tc(ws, ws.nerf_tc, ws.nerf_tc_stride, npix, gsm, st)
-                                                   : shade_dispatch(ws, gsm * 4, npix, st);
+    e = tc_shade ? launch_shade_tc(ws, ws.nerf_tc, ws.nerf_tc_stride, npix, gsm, st)
+                 : shade_dispatch(ws, gsm * 4, npix, st);
     if (e != cudaSuccess) return e;
     mark();
-    k_bin_shadow<0><<<gsm * 8, kThreads, 0, st>>>(ws, npix);
-    k_scan_shadow<<<1, 1, 0, st>>>(ws, kTileRows);
-    k_bin_shadow<1><<<gsm * 8, kThreads, 0, st>>>(ws, npix);
-    mark();
-    e = tc ? launch_nedf_tc(ws, ws.nedf_tc, ws.nedf_tc_stride, 1, 0, nullptr, nullptr, nullptr, 0, gsm, st)
-           : nedf_dispatch(ws, gsm * 4, 1, st);
+    int nbin = 0;
+    e = launch_shadow_binning(ws, npix, L.n_lights, L.n_inst, nedf_rows, gsm, st, &nbin);
     if (e != cudaSuccess) return e;
+    mark();
+    e = tc_nedf ? launch_nedf_tc(ws, ws.nedf_tc, ws.nedf_tc_stride, 1, 0, nullptr, nullptr, nullptr, 0, gsm, st)
+                : nedf_dispatch(ws, gsm * 4, 1, st);
+    if (e != cudaSuccess) return e;
+    if (tc_nedf) {
+        if ((e = launch_fallback(ws, 1, gsm, st)) != cudaSuccess) return e;
+        ++launches;
+    }
     mark();
     k_composite<<<gsm * 4, 256, 0, st>>>(ws, npix);
     mark();
-    L.launches = 14;
+    L.launches = launches + 4 + nbin;
     return cudaGetLastError();
 }
 

@@ -14,6 +14,10 @@
 
 namespace nedf {
 
+constexpr int kTcTileRows = 128;     // rows per tensor-core MLP tile (M of the MMA)
+
+struct LightCam;
+
 struct Counters {
     unsigned long long p_count[kMaxTypes];
     unsigned long long p_cursor[kMaxTypes];
@@ -29,6 +33,8 @@ struct Counters {
     unsigned long long hit_pixels;
     unsigned long long p_total_requested;
     unsigned long long s_total_requested;
+    unsigned long long fb_count[2];              // deferred plain-method pairs (primary, shadow)
+    unsigned long long lg_total;                 // shadow light-grid entries requested
 };
 
 struct Workspace {
@@ -62,6 +68,79 @@ struct Workspace {
     size_t nedf_tc_stride;
     const uint8_t *nerf_tc;
     size_t nerf_tc_stride;
+    // pairs deferred to the plain method by the tensor-core NeDF kernels (indices into the lists)
+    uint32_t *fb_list[2];
+    // shadow-map cameras: per light a G x G grid of direction cells with instance lists
+    struct LightCam *lcam;       // [kMaxLights]
+    uint32_t *lg_count;          // [n_lights * G * G]
+    uint32_t *lg_off;            // [n_lights * G * G + 1] (exclusive scan), reused as cursors
+    uint32_t *lg_cursor;         // [n_lights * G * G]
+    uint32_t *lg_items;          // instance ids, cell after cell
+    long long lg_cap;
+    uint32_t *lg_big;            // [n_lights][max_instances] instances too large for cell lists
+    uint32_t *lg_big_count;      // [kMaxLights]
+    int lg_G;
+    int max_inst;
+    uint32_t *scan_tmp;          // block sums of the grid scan
 };
+
+struct LightCam {
+    float eye[3], right[3], up[3], fwd[3];
+    float tan_h;
+    int valid;                   // 0: light inside the scene bound or too wide a view -> all instances
+};
+
+// ---------------------------------------------------------------------------------------------
+// (ray, instance) pair set-up shared by the NeDF kernels and the deferred plain-method pass
+// ---------------------------------------------------------------------------------------------
+struct PairRay {
+    V3 ol, dl;
+    float te, tx, tp, s, ell;
+    uint32_t key, inst;
+    bool kept;
+};
+
+__device__ __forceinline__ void setup_pair_ray(const Workspace &ws, const DevFrame &f, bool shadow, uint2 pr,
+                                               float rb, PairRay &R)
+{
+    R.key = pr.x;
+    R.inst = pr.y;
+    DevInst I = ws.inst[pr.y];
+    R.s = I.s;
+    R.ell = 0.0f;
+    V3 o, d;
+    if (!shadow) {
+        camera_ray(f, pr.x % f.W, pr.x / f.W, o, d);
+    } else {
+        uint32_t pix = pr.x / f.n_lights, l = pr.x - pix * f.n_lights;
+        V3 oc, dc;
+        camera_ray(f, pix % f.W, pix / f.W, oc, dc);
+        V3 x = madd(oc, ws.depth[pix], dc);
+        o = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
+        V3 v = sub(x, o);
+        R.ell = sqrtf(dot(v, v));
+        d = normalized(v);
+    }
+    to_local(I, o, d, R.ol, R.dl);
+    Chord ch;
+    R.kept = bound_chord(R.ol, R.dl, rb, ch);
+    R.te = ch.te;
+    R.tx = ch.tx;
+    R.tp = ch.tp;
+}
+
+// Step 1: packed atomic minimum (strict '<' in id order on ties).  Step 3: occlusion bit when
+// the hit lies closer to the light than the surface point by more than eps (Algorithm 2).
+__device__ __forceinline__ void apply_hit(const Workspace &ws, const DevFrame &f, bool shadow, const PairRay &R,
+                                          float Dl)
+{
+    float D = R.s * Dl;
+    if (!shadow) {
+        atomicMin(&ws.keys[R.key], ((unsigned long long)__float_as_uint(D) << 32) | R.inst);
+    } else if (D + f.eps < R.ell) {
+        uint32_t pix = R.key / f.n_lights, l = R.key - pix * f.n_lights;
+        atomicOr(&ws.occl[pix], 1u << l);
+    }
+}
 
 }  // namespace nedf

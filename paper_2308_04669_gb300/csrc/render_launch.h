@@ -12,12 +12,14 @@ struct FrameLaunch {
     int num_sms;
     int n_inst;
     int n_shade;
+    int n_lights;
     const HostCamera *cam;   // device copy of this frame's camera
     cudaEvent_t *events;     // NULL, or kStages + 1 events recorded between the stages
     int launches;            // out: kernels launched
 };
 
 constexpr int kStages = 8;
+constexpr int kLightGridSize = 128;   // shadow-map camera grid (cells per side)
 
 cudaError_t launch_frame(FrameLaunch &L);
 
@@ -30,6 +32,11 @@ cudaError_t launch_nedf_tc(const Workspace &ws, const void *blobs, size_t stride
                            const float *o, const float *d, float *out, int n, int num_sms, cudaStream_t st);
 cudaError_t launch_shade_tc(const Workspace &ws, const void *blobs, size_t stride, int npix, int num_sms,
                             cudaStream_t st);
+cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStream_t st);
+
+// Step-3 binning through per-light shadow-map cameras (shadow_bin.cu)
+cudaError_t launch_shadow_binning(const Workspace &ws, int npix, int n_lights, int n_inst, int rows_per_tile,
+                                  int num_sms, cudaStream_t st, int *launches);
 cudaError_t launch_nedf_query_f32(const Workspace &ws, int type, const float *o, const float *d,
                                   float *out, int n, int num_sms, cudaStream_t st);
 cudaError_t launch_primary_binning(FrameLaunch &L);

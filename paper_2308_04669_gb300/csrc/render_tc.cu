@@ -24,7 +24,7 @@ namespace nedf {
 
 using namespace tc;
 
-constexpr int kTcRows = 128;
+constexpr int kTcRows = kTcTileRows;
 constexpr int kTcThreads = 128;
 
 // ---- per-type BF16 weight blobs -----------------------------------------------------------------
@@ -293,46 +293,29 @@ k_nedf_tc(Workspace ws, const uint8_t *blobs, size_t blob_stride, int mode, int 
         // ---- row set-up: ray, local frame, bound chord, encoding -------------------------------
         const unsigned long long idx = begin + r;
         const bool valid = idx < end;
-        uint32_t key = 0, inst = 0;
-        float tp = 0.f, te = 0.f, tx = 0.f, s = 1.f, ell = 0.f;
-        V3 ol = v3(0, 0, 0), dl = v3(0, 0, 1);
-        bool kept = false;
+        PairRay R;
+        R.kept = false;
+        R.te = R.tx = R.tp = 0.f;
+        R.ol = v3(0, 0, 0);
+        R.dl = v3(0, 0, 1);
         if (valid) {
             if (mode == 2) {
-                ol = v3(qo[3 * idx], qo[3 * idx + 1], qo[3 * idx + 2]);
-                dl = normalized(v3(qd[3 * idx], qd[3 * idx + 1], qd[3 * idx + 2]));
+                R.ol = v3(qo[3 * idx], qo[3 * idx + 1], qo[3 * idx + 2]);
+                R.dl = normalized(v3(qd[3 * idx], qd[3 * idx + 1], qd[3 * idx + 2]));
+                Chord ch;
+                R.kept = bound_chord(R.ol, R.dl, T.rb, ch);
+                R.te = ch.te; R.tx = ch.tx; R.tp = ch.tp;
             } else {
-                uint2 pr = pairs[idx];
-                key = pr.x;
-                inst = pr.y;
-                DevInst I = ws.inst[inst];
-                s = I.s;
-                V3 o, d;
-                if (mode == 0) {
-                    camera_ray(f, pr.x % f.W, pr.x / f.W, o, d);
-                } else {
-                    uint32_t pix = pr.x / f.n_lights, l = pr.x - pix * f.n_lights;
-                    V3 oc, dc;
-                    camera_ray(f, pix % f.W, pix / f.W, oc, dc);
-                    V3 x = madd(oc, ws.depth[pix], dc);
-                    o = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
-                    V3 v = sub(x, o);
-                    ell = sqrtf(dot(v, v));
-                    d = normalized(v);
-                }
-                to_local(I, o, d, ol, dl);
+                setup_pair_ray(ws, f, mode == 1, pairs[idx], T.rb, R);
             }
-            Chord ch;
-            kept = bound_chord(ol, dl, T.rb, ch);
-            tp = ch.tp; te = ch.te; tx = ch.tx;
         }
         float out[2] = {0.f, 0.f};
         {
             float feat[K0];
             float x6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (valid && kept) {
-                V3 pe = madd(ol, te, dl);
-                x6[0] = pe.x; x6[1] = pe.y; x6[2] = pe.z; x6[3] = dl.x; x6[4] = dl.y; x6[5] = dl.z;
+            if (valid && R.kept) {
+                V3 pe = madd(R.ol, R.te, R.dl);
+                x6[0] = pe.x; x6[1] = pe.y; x6[2] = pe.z; x6[3] = R.dl.x; x6[4] = R.dl.y; x6[5] = R.dl.z;
             }
             encode<6, 6>(x6, feat);
             store_row_bf16<K0>(A, r, feat, kNedfIn);
@@ -358,38 +341,32 @@ k_nedf_tc(Workspace ws, const uint8_t *blobs, size_t blob_stride, int mode, int 
             tc_fence_before();
             __syncthreads();
         }
-        // ---- decode (Eq. 2, 7), fallback, refinement, z-min / occlusion / query output --------
+        // ---- decode (Eq. 2, 7) and checks; plain-method pairs are deferred to their own pass ---
+        bool defer = false;
         if (valid) {
             if (mode == 2) {
                 float4 res = make_float4(0.f, 0.f, __int_as_float(0x7f800000), 0.f);
-                if (kept) {
-                    float Dl = tp - T.rb * out[0];
+                if (R.kept) {
+                    float Dl = R.tp - T.rb * out[0];
                     res = make_float4(out[0], out[1], Dl, (out[1] > 0.f && Dl > 0.f) ? 1.f : 0.f);
                 }
                 qout[idx] = res;
             } else {
-                float Dl = tp - T.rb * out[0];
-                bool hit = (out[1] > 0.0f) && (Dl > 0.0f);
-                if (f.fallback_conf > 0.0f) {
-                    float p = 1.0f / (1.0f + expf(-out[1]));
-                    if (fmaxf(p, 1.0f - p) < f.fallback_conf) {
-                        Dl = march_crossing(T, ol, dl, te, tx, f.march_steps, f.march_bisect, hit);
-                        atomicAdd(&ws.cnt->fallback, 1ull);
-                    }
-                }
-                if (hit && f.refine_steps > 0) {
-                    Dl = refine_depth(T, ol, dl, Dl, f.shade_half, f.refine_steps);
-                    hit = Dl > 0.0f;
-                }
-                if (hit) {
-                    float D = s * Dl;
-                    if (mode == 0) {
-                        atomicMin(&ws.keys[key], ((unsigned long long)__float_as_uint(D) << 32) | inst);
-                    } else if (D + f.eps < ell) {
-                        uint32_t pix = key / f.n_lights, l = key - pix * f.n_lights;
-                        atomicOr(&ws.occl[pix], 1u << l);
-                    }
-                }
+                float Dl;
+                bool hit;
+                defer = nedf_decode(f, T, R.ol, R.dl, R.tp, out[0], out[1], Dl, hit);
+                if (!defer && hit) apply_hit(ws, f, mode == 1, R, Dl);
+            }
+        }
+        if (mode != 2) {
+            const int lane = threadIdx.x & 31;
+            unsigned m = __ballot_sync(0xffffffffu, defer);
+            if (m) {
+                int leader = __ffs(m) - 1;
+                unsigned long long start = 0;
+                if (lane == leader) start = atomicAdd(&ws.cnt->fb_count[mode], (unsigned long long)__popc(m));
+                start = __shfl_sync(0xffffffffu, start, leader);
+                if (defer) ws.fb_list[mode][start + __popc(m & ((1u << lane) - 1u))] = (uint32_t)idx;
             }
         }
         if (!__syncthreads_and(y.ok)) break;
@@ -448,7 +425,7 @@ k_shade_tc(Workspace ws, const uint8_t *blobs, size_t blob_stride, int npix)
     for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int t = shade_tile_type<N>(C, f.n_types, tile);
         const unsigned long long first = (tile - C.h_tile[t]) * ppt;
-        const int n_pix = (int)min((unsigned long long)ppt, C.h_count[t] - first);
+        const int n_pix = first < C.h_count[t] ? (int)min((unsigned long long)ppt, C.h_count[t] - first) : 0;
         const DevType T = ws.types[t];
         const uint8_t *blob = blobs + (size_t)t * blob_stride;
         // weights of layer 0 (unless prefetched) and, on a type change, the fp32 block
@@ -554,6 +531,33 @@ k_shade_tc(Workspace ws, const uint8_t *blobs, size_t blob_stride, int npix)
         if (!__syncthreads_and(y.ok)) break;
     }
     tc_teardown(S, y, kCols, ws.status);
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Deferred plain-method pairs (low confidence or outliers), one thread per pair
+// ---------------------------------------------------------------------------------------------------
+__global__ void k_fallback(Workspace ws, int mode)
+{
+    const DevFrame &f = *ws.frame;
+    const unsigned long long n = ws.cnt->fb_count[mode];
+    const uint2 *pairs = mode == 1 ? ws.spairs : ws.ppairs;
+    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < n;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        uint2 pr = pairs[ws.fb_list[mode][e]];
+        const DevType T = ws.types[ws.inst[pr.y].type];
+        PairRay R;
+        setup_pair_ray(ws, f, mode == 1, pr, T.rb, R);
+        bool hit = false;
+        float Dl = march_crossing(T, R.ol, R.dl, R.te, R.tx, f.march_steps, f.march_bisect, hit);
+        if (hit) apply_hit(ws, f, mode == 1, R, Dl);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ws.cnt->fallback, n);
+}
+
+cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStream_t st)
+{
+    k_fallback<<<num_sms * 8, 128, 0, st>>>(ws, mode);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------------------

@@ -1,0 +1,359 @@
+// Step-3 binning: shadow rays grouped with the instances that can occlude them.
+//
+// Method: arXiv 2308.04669, Algorithm 2 (shadow rays from the point light L towards the surface
+// point x, answered "like in STEP 1") and the shadow-mapping idea it builds on (Section "Fast
+// Dynamic shadows Casting").  Every shadow ray of a light starts at L, so each light gets a
+// pinhole "shadow-map camera" at L aimed at the scene bound: a G x G grid of direction cells.
+// An instance's bound sphere, seen from L, covers exactly the directions inside its tangent
+// cone; the cone's section with the image plane has the bounding rectangle given by the two
+// tangent planes per axis, so the instance is listed in every cell of that rectangle (plus one
+// cell of margin).  A shadow ray then looks up the single cell its direction falls in, and the
+// exact bound-sphere test decides.  Instances whose rectangle is too large (close to the
+// light) go to a per-light list every ray checks; a light inside the scene bound uses all
+// instances.  The per-type pair lists are then built exactly as in Step 1 (count, scan, fill).
+#include "render_kernels.cuh"
+#include "render_launch.h"
+
+#include <algorithm>
+
+namespace nedf {
+
+constexpr int kMaxCellsPerInstance = 1024;
+constexpr int kScanBlock = 4096;        // elements per block of the grid scan (1024 threads x 4)
+
+// ---- scene bound of the instance spheres, one shadow-map camera per light --------------------------
+__global__ void __launch_bounds__(256) k_light_setup(Workspace ws)
+{
+    __shared__ float red[6][256];
+    const DevFrame &f = *ws.frame;
+    float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+    for (int i = threadIdx.x; i < f.n_inst; i += blockDim.x) {
+        DevInst I = ws.inst[i];
+        float r = I.s * ws.types[I.type].rb;
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fminf(lo[c], I.T[c] - r);
+            hi[c] = fmaxf(hi[c], I.T[c] + r);
+        }
+    }
+    for (int c = 0; c < 3; ++c) {
+        red[c][threadIdx.x] = lo[c];
+        red[3 + c][threadIdx.x] = hi[c];
+    }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int c = 0; c < 3; ++c) {
+                red[c][threadIdx.x] = fminf(red[c][threadIdx.x], red[c][threadIdx.x + s]);
+                red[3 + c][threadIdx.x] = fmaxf(red[3 + c][threadIdx.x], red[3 + c][threadIdx.x + s]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < kMaxLights) ws.lg_big_count[threadIdx.x] = 0;
+    const int l = threadIdx.x;
+    if (l >= f.n_lights) return;
+    float blo[3] = {red[0][0], red[1][0], red[2][0]}, bhi[3] = {red[3][0], red[4][0], red[5][0]};
+    V3 L = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
+    LightCam cam{};
+    bool inside = L.x >= blo[0] && L.x <= bhi[0] && L.y >= blo[1] && L.y <= bhi[1] && L.z >= blo[2] && L.z <= bhi[2];
+    cam.valid = !inside && f.n_inst > 0;
+    V3 ctr = v3(0.5f * (blo[0] + bhi[0]), 0.5f * (blo[1] + bhi[1]), 0.5f * (blo[2] + bhi[2]));
+    V3 fwd = normalized(sub(ctr, L));
+    V3 up0 = fabsf(fwd.y) < 0.9f ? v3(0.f, 1.f, 0.f) : v3(1.f, 0.f, 0.f);
+    V3 right = normalized(v3(fwd.y * up0.z - fwd.z * up0.y, fwd.z * up0.x - fwd.x * up0.z, fwd.x * up0.y - fwd.y * up0.x));
+    V3 up = v3(right.y * fwd.z - right.z * fwd.y, right.z * fwd.x - right.x * fwd.z, right.x * fwd.y - right.y * fwd.x);
+    float tmax = 0.0f;
+    for (int k = 0; k < 8 && cam.valid; ++k) {
+        V3 corner = v3((k & 1) ? bhi[0] : blo[0], (k & 2) ? bhi[1] : blo[1], (k & 4) ? bhi[2] : blo[2]);
+        V3 e = sub(corner, L);
+        float z = dot(e, fwd);
+        if (z <= 1e-3f * sqrtf(dot(e, e))) { cam.valid = 0; break; }
+        tmax = fmaxf(tmax, fmaxf(fabsf(dot(e, right)), fabsf(dot(e, up))) / z);
+    }
+    cam.tan_h = tmax * 1.05f + 1e-3f;
+    if (cam.tan_h > 4.0f) cam.valid = 0;
+    cam.eye[0] = L.x; cam.eye[1] = L.y; cam.eye[2] = L.z;
+    cam.fwd[0] = fwd.x; cam.fwd[1] = fwd.y; cam.fwd[2] = fwd.z;
+    cam.right[0] = right.x; cam.right[1] = right.y; cam.right[2] = right.z;
+    cam.up[0] = up.x; cam.up[1] = up.y; cam.up[2] = up.z;
+    ws.lcam[l] = cam;
+}
+
+__device__ __forceinline__ int cell_of(float u, float tan_h, int G)
+{
+    int c = (int)floorf((u / tan_h + 1.0f) * 0.5f * G);
+    return min(max(c, 0), G - 1);
+}
+
+// Cell rectangle of a sphere (centre c, radius r) in a light's grid; false when the sphere
+// reaches the light's image plane (then it goes to the per-light list).
+__device__ __forceinline__ bool light_rect(const LightCam &cam, int G, V3 c, float r, int &i0, int &i1, int &j0,
+                                           int &j1)
+{
+    V3 e = sub(c, v3(cam.eye[0], cam.eye[1], cam.eye[2]));
+    float cx = dot(e, v3(cam.right[0], cam.right[1], cam.right[2]));
+    float cy = dot(e, v3(cam.up[0], cam.up[1], cam.up[2]));
+    float cz = dot(e, v3(cam.fwd[0], cam.fwd[1], cam.fwd[2]));
+    if (cz <= r * 1.001f + 1e-6f) return false;
+    // tangent planes through L: (c_a - u c_z)^2 = r^2 (1 + u^2)
+    float den = cz * cz - r * r;
+    float sx = r * sqrtf(fmaxf(cx * cx + cz * cz - r * r, 0.f));
+    float sy = r * sqrtf(fmaxf(cy * cy + cz * cz - r * r, 0.f));
+    i0 = max(cell_of((cx * cz - sx) / den, cam.tan_h, G) - 1, 0);
+    i1 = min(cell_of((cx * cz + sx) / den, cam.tan_h, G) + 1, G - 1);
+    j0 = max(cell_of((cy * cz - sy) / den, cam.tan_h, G) - 1, 0);
+    j1 = min(cell_of((cy * cz + sy) / den, cam.tan_h, G) + 1, G - 1);
+    return true;
+}
+
+__global__ void k_zero_u32(uint32_t *p, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = 0u;
+}
+
+template <int PASS>
+__global__ void k_light_bin(Workspace ws, int n_lights)
+{
+    const DevFrame &f = *ws.frame;
+    const int G = ws.lg_G, n_inst = f.n_inst;
+    const long long total = (long long)n_lights * n_inst;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        int l = (int)(e / n_inst), i = (int)(e - (long long)l * n_inst);
+        const LightCam cam = ws.lcam[l];
+        if (!cam.valid) continue;
+        DevInst I = ws.inst[i];
+        float r = I.s * ws.types[I.type].rb;
+        int i0, i1, j0, j1;
+        bool ok = light_rect(cam, G, v3(I.T[0], I.T[1], I.T[2]), r, i0, i1, j0, j1);
+        if (!ok || (i1 - i0 + 1) * (j1 - j0 + 1) > kMaxCellsPerInstance) {
+            if (PASS == 1) {
+                uint32_t pos = atomicAdd(&ws.lg_big_count[l], 1u);
+                ws.lg_big[(size_t)l * ws.max_inst + pos] = (uint32_t)i;
+            }
+            continue;
+        }
+        for (int j = j0; j <= j1; ++j)
+            for (int ii = i0; ii <= i1; ++ii) {
+                size_t cell = ((size_t)l * G + j) * G + ii;
+                if (PASS == 0) {
+                    atomicAdd(&ws.lg_count[cell], 1u);
+                } else {
+                    uint32_t pos = atomicAdd(&ws.lg_cursor[cell], 1u);
+                    if ((long long)pos < ws.lg_cap) ws.lg_items[pos] = (uint32_t)i;
+                    else atomicOr(ws.status, kStatusShadowOverflow);
+                }
+            }
+    }
+}
+
+// ---- exclusive scan of the grid counts (3 kernels) ----------------------------------------------
+__global__ void __launch_bounds__(1024) k_scan_blocks(const uint32_t *in, uint32_t *out, uint32_t *block_sums, long long n)
+{
+    __shared__ uint32_t wsum[32];
+    const long long base = (long long)blockIdx.x * kScanBlock + threadIdx.x * 4;
+    uint32_t v[4], t = 0;
+    for (int k = 0; k < 4; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0u;
+        t += v[k];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = wsum[lane], wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp] + incl - t;
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == blockDim.x - 1) block_sums[blockIdx.x] = run;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(uint32_t *block_sums, int nb, uint32_t *total_out)
+{
+    __shared__ uint32_t wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t t = threadIdx.x < nb ? block_sums[threadIdx.x] : 0u, incl = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = wsum[lane], wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    uint32_t excl = wsum[warp] + incl - t;
+    if (threadIdx.x < nb) block_sums[threadIdx.x] = excl;
+    if (threadIdx.x == nb - 1) *total_out = excl + t;
+}
+
+__global__ void k_scan_add(uint32_t *out, uint32_t *cursor, const uint32_t *block_sums, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        uint32_t v = out[i] + block_sums[i / kScanBlock];
+        out[i] = v;
+        cursor[i] = v;
+    }
+}
+
+// ---- shadow rays against the instances listed in their cell --------------------------------------
+__device__ __forceinline__ unsigned lane_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(256) k_bin_shadow_grid(Workspace ws, int npix)
+{
+    __shared__ unsigned long long cnt_t[kMaxTypes];
+    const DevFrame &f = *ws.frame;
+    const int nl = f.n_lights, n_inst = f.n_inst, G = ws.lg_G;
+    const long long n_rays = (long long)npix * nl;
+    const int lane = threadIdx.x & 31;
+    if (PASS == 0) {
+        for (int k = threadIdx.x; k < kMaxTypes; k += blockDim.x) cnt_t[k] = 0;
+        __syncthreads();
+    }
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < n_rays; base += (long long)gridDim.x * blockDim.x) {
+        const long long rr = base + threadIdx.x;
+        bool valid = rr < n_rays;
+        uint32_t pix = 0, l = 0;
+        V3 o = v3(0, 0, 0), d = v3(0, 0, 1);
+        float ell = 0.0f;
+        int count = 0, nc = 0;
+        uint32_t c0 = 0;
+        bool grid = false;
+        if (valid) {
+            pix = (uint32_t)(rr / nl);
+            l = (uint32_t)(rr - (long long)pix * nl);
+            valid = ws.id[pix] != kNoId;
+        }
+        if (valid) {
+            V3 oc, dc;
+            camera_ray(f, pix % f.W, pix / f.W, oc, dc);
+            V3 x = madd(oc, ws.depth[pix], dc);
+            o = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
+            V3 v = sub(x, o);
+            ell = sqrtf(dot(v, v));
+            d = normalized(v);
+            const LightCam &cam = ws.lcam[l];
+            grid = cam.valid;
+            if (grid) {
+                float z = dot(d, v3(cam.fwd[0], cam.fwd[1], cam.fwd[2]));
+                float u = dot(d, v3(cam.right[0], cam.right[1], cam.right[2])) / z;
+                float w = dot(d, v3(cam.up[0], cam.up[1], cam.up[2])) / z;
+                size_t cell = ((size_t)l * G + cell_of(w, cam.tan_h, G)) * G + cell_of(u, cam.tan_h, G);
+                c0 = ws.lg_off[cell];
+                long long end = min((long long)ws.lg_off[cell + 1], ws.lg_cap);   // overflow: flagged in the fill
+                nc = (int)max(0ll, end - (long long)c0);
+                count = nc + (int)ws.lg_big_count[l];
+            } else {
+                count = n_inst;
+            }
+        }
+        const int maxc = __reduce_max_sync(0xffffffffu, count);
+        for (int k = 0; k < maxc; ++k) {
+            bool keep = false;
+            uint32_t inst = 0, ty = 0;
+            if (k < count) {
+                inst = grid ? (k < nc ? ws.lg_items[c0 + k] : ws.lg_big[(size_t)l * ws.max_inst + (k - nc)]) : (uint32_t)k;
+                DevInst I = ws.inst[inst];
+                ty = I.type;
+                V3 ol, dl;
+                to_local(I, o, d, ol, dl);
+                Chord ch;
+                keep = bound_chord(ol, dl, ws.types[ty].rb, ch) && (ch.te * I.s < ell);
+            }
+            if (PASS == 0) {
+                if (keep) atomicAdd(&cnt_t[ty], 1ull);
+            } else {
+                unsigned active = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    unsigned peers = __match_any_sync(active, ty);
+                    int leader = __ffs(peers) - 1;
+                    unsigned long long start = 0;
+                    if (lane == leader) start = atomicAdd(&ws.cnt->s_cursor[ty], (unsigned long long)__popc(peers));
+                    start = __shfl_sync(peers, start, leader);
+                    unsigned long long idx = start + __popc(peers & lane_lt());
+                    if (idx < ws.cnt->s_off[ty + 1]) ws.spairs[idx] = make_uint2(pix * nl + l, inst);
+                    else atomicOr(ws.status, kStatusShadowOverflow);
+                }
+            }
+        }
+    }
+    if (PASS == 0) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < f.n_types; k += blockDim.x)
+            if (cnt_t[k]) atomicAdd(&ws.cnt->s_count[k], cnt_t[k]);
+    }
+}
+
+__global__ void k_scan_shadow_pairs(Workspace ws, int rows_per_tile)
+{
+    const DevFrame &f = *ws.frame;
+    Counters &C = *ws.cnt;
+    unsigned long long o = 0, t = 0, req = 0;
+    for (int k = 0; k < f.n_types; ++k) {
+        unsigned long long c = C.s_count[k];
+        req += c;
+        if (o + c > (unsigned long long)ws.scap) {
+            c = (unsigned long long)ws.scap - o;
+            *ws.status |= kStatusShadowOverflow;
+        }
+        C.s_count[k] = c;
+        C.s_off[k] = o;
+        C.s_cursor[k] = o;
+        C.s_tile[k] = t;
+        o += c;
+        t += (c + rows_per_tile - 1) / rows_per_tile;
+    }
+    C.s_off[f.n_types] = o;
+    C.s_tile[f.n_types] = t;
+    C.s_total_requested = req;
+}
+
+cudaError_t launch_shadow_binning(const Workspace &ws, int npix, int n_lights, int n_inst, int rows_per_tile,
+                                  int num_sms, cudaStream_t st, int *launches)
+{
+    const int G = ws.lg_G;
+    const long long cells = (long long)n_lights * G * G;
+    const int nb = (int)((cells + kScanBlock - 1) / kScanBlock);
+    if (nb > 1024) return cudaErrorInvalidValue;
+    const long long pairs = (long long)n_lights * n_inst;
+    const int gb = (int)std::min<long long>((pairs + 255) / 256, (long long)num_sms * 8);
+    k_light_setup<<<1, 256, 0, st>>>(ws);
+    k_zero_u32<<<num_sms * 2, 256, 0, st>>>(ws.lg_count, cells);
+    k_light_bin<0><<<gb, 256, 0, st>>>(ws, n_lights);
+    k_scan_blocks<<<nb, 1024, 0, st>>>(ws.lg_count, ws.lg_off, ws.scan_tmp, cells);
+    k_scan_sums<<<1, 1024, 0, st>>>(ws.scan_tmp, nb, ws.lg_off + cells);
+    k_scan_add<<<num_sms * 2, 256, 0, st>>>(ws.lg_off, ws.lg_cursor, ws.scan_tmp, cells);
+    k_light_bin<1><<<gb, 256, 0, st>>>(ws, n_lights);
+    k_bin_shadow_grid<0><<<num_sms * 8, 256, 0, st>>>(ws, npix);
+    k_scan_shadow_pairs<<<1, 1, 0, st>>>(ws, rows_per_tile);
+    k_bin_shadow_grid<1><<<num_sms * 8, 256, 0, st>>>(ws, npix);
+    *launches = 10;
+    return cudaGetLastError();
+}
+
+}  // namespace nedf

@@ -39,7 +39,7 @@ class Options(C.Structure):
     _fields_ = [("n_shade", C.c_int), ("shade_half", C.c_float), ("shadow_beta", C.c_float),
                 ("shadow_eps", C.c_float), ("sigma_max", C.c_float), ("sdf_width", C.c_float),
                 ("depth_source", C.c_int), ("march_steps", C.c_int), ("march_bisect", C.c_int),
-                ("fallback_conf", C.c_float), ("refine_steps", C.c_int)]
+                ("fallback_conf", C.c_float), ("refine_steps", C.c_int), ("outlier_resample", C.c_int)]
 
 
 class TypeDesc(C.Structure):
@@ -121,7 +121,7 @@ def _fptr(a: np.ndarray):
 
 
 def default_options(**kw) -> Options:
-    o = Options(8, 0.05, 0.5, 0.02, 50.0, 0.01, DEPTH_NEDF, 128, 4, 0.0, 0)
+    o = Options(8, 0.05, 0.5, 0.02, 50.0, 0.01, DEPTH_NEDF, 128, 4, 0.0, 0, 0)
     for k, v in kw.items():
         setattr(o, k, v)
     return o

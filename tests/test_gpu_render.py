@@ -76,6 +76,26 @@ def test_thousand_instances_sampled(orc):
     assert g["stats"].status == 0 and g["stats"].primary_pairs > 500000
 
 
+def test_refine_and_outlier_resample_fp32(orc):
+    """FP32 path with the confidence fallback, window refinement and outlier re-answering."""
+    sc = sg.three_types_scene(96, 96, nerf=False)
+    kw = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1)
+    g = gpu_frame(sc, **kw)
+    o = orc.render(orc.OracleScene(sc), march_n=128, march_b=4, n_threads=8, **kw)
+    rep = compare_frame(g, o, o["px"], max_excluded=0.08)
+    assert g["stats"].fallback_pairs > 0 and rep["hit"] > 500
+
+
+def test_light_inside_scene_bound(orc):
+    """A light inside the scene's bound cannot use a shadow-map camera: every instance is tested."""
+    sc = sg.three_types_scene(96, 96, nerf=False)
+    sc.lights = sg.f32([[0.3, 0.2, -0.1], [1.0, 9.0, 2.0]])
+    g = gpu_frame(sc, depth_source=1)
+    o = orc.render(orc.OracleScene(sc), depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4, n_threads=8)
+    rep = compare_frame(g, o, o["px"])
+    assert rep["shadowed"] > 50
+
+
 def test_empty_and_out_of_view(orc):
     sc = sg.tiny_sphere_scene()
     sc.inst_T = sg.f32([[0, 50, 0]])          # far outside the frustum

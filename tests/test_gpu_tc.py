@@ -12,7 +12,7 @@ import pytest
 
 from paper_2308_04669_gb300 import scenegen as sg
 
-from .gpu_helpers import NOID, close, gpu_frame
+from .gpu_helpers import NOID, close, compare_frame, gpu_frame
 
 pytestmark = pytest.mark.gpu
 
@@ -41,9 +41,10 @@ def test_bf16_nedf_query_matches_bf16_oracle(orc, scene_fn):
     from paper_2308_04669_gb300 import native
     sc = scene_fn()
     rng = np.random.default_rng(4)
-    n = 1000                      # 7 full tiles of 128 rows and a ragged tail
-    o32 = (rng.normal(size=(n, 3)) * 1.2).astype(np.float32)
-    d32 = rng.normal(size=(n, 3)).astype(np.float32)
+    n = 1500                      # 11 full tiles of 128 rows and a ragged tail
+    o32 = rng.normal(size=(n, 3))
+    o32 = (2.5 * o32 / np.linalg.norm(o32, axis=1, keepdims=True)).astype(np.float32)
+    d32 = (-o32 + rng.normal(size=(n, 3)) * 0.8).astype(np.float32)   # mostly towards the bound
     for t in range(len(sc.types)):
         g = run_query(sc, t, o32, d32, native.PREC_BF16)
         w = sc.types[t].nedf_w.astype(np.float64)
@@ -60,7 +61,7 @@ def test_bf16_nedf_query_matches_bf16_oracle(orc, scene_fn):
             assert close(g[i, :2], yq, BF16_ABS, BF16_REL).all(), (i, g[i, :2], yq)
             errs.append(np.abs(g[i, :2] - yq).max())
             errs_fp.append(np.abs(g[i, :2] - yf).max())
-        assert len(errs) > 300
+        assert len(errs) > 600
         assert np.median(errs) < 1e-3
         print(f"type {t}: median |bf16 gpu - bf16 oracle| {np.median(errs):.2e}, "
               f"median |bf16 gpu - fp64 network| {np.median(errs_fp):.2e}")
@@ -83,21 +84,28 @@ def test_bf16_shading_matches_bf16_oracle(orc):
 
 
 def test_bf16_full_frame_nedf(orc):
-    """Steps 1-3 with the NeDF on the tensor cores: ids where the BF16 oracle's decisions are
-    clear of the BF16 error, depths within the depth bound that error implies (rb * 1e-2)."""
+    """Steps 1-3 with the NeDF on the tensor cores against the BF16-operand oracle; the two agree
+    to FP32-accumulation error, so the FP32 path's knife-edge margins and tolerances apply."""
     from paper_2308_04669_gb300 import native
     sc = sg.three_types_scene(128, 128)
     px = sg.pixel_subset(128, 128, 500, 9)
     g = gpu_frame(sc, precision=native.PREC_BF16)
     o = orc.render(orc.OracleScene(sc), px=px, quant=orc.QUANT_BF16, n_threads=8)
-    decided = (o["pmargin"] > 3e-2) & ((o["gap"] > 3e-2) | (o["id"] == NOID))
-    assert decided.mean() > 0.8
-    gid = g["id"][px]
-    assert (gid[decided] == o["id"][decided]).all()
-    both = decided & (o["id"] != NOID)
-    assert close(g["depth"][px][both], o["depth"][both], 2e-2, 1e-2).all()
-    sd = both & (o["smargin"] > 3e-2)
-    assert (g["shadow"][px][sd] == o["shadow"][sd]).mean() > 0.99
+    rep = compare_frame(g, o, px)
+    assert rep["hit"] > 100
+
+
+def test_bf16_refine_and_outlier_resample(orc):
+    """Confidence fallback, window refinement and outlier re-answering on the tensor-core path
+    (fallback pairs run in their own pass) against the oracle with the same options."""
+    from paper_2308_04669_gb300 import native
+    sc = sg.three_types_scene(128, 128, nerf=False)
+    px = sg.pixel_subset(128, 128, 600, 10)
+    kw = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1)
+    g = gpu_frame(sc, precision=native.PREC_BF16, **kw)
+    o = orc.render(orc.OracleScene(sc), px=px, quant=orc.QUANT_BF16, march_n=128, march_b=4, n_threads=8, **kw)
+    rep = compare_frame(g, o, px, max_excluded=0.08)
+    assert g["stats"].fallback_pairs > 0 and rep["hit"] > 100
 
 
 def test_bf16_thousand_instances_stats(orc):
