@@ -34,7 +34,8 @@ sys.path.insert(0, ROOT)
 METRIC = "composited rays/s & ms/frame at 1024², NeDF vs ray-march, same GPU, depth err"
 WORKLOAD = ("1024 instances (sphere/torus/box, seed 3, T in [-20,20]^3) at 1024x1024, 4 point lights, "
             "NeDF 6x128 per type trained on ray-march labels, NeRF 8x256 per type, 8 shading samples, "
-            "fallback below confidence 0.9, 4 refinement steps")
+            "fallback below confidence 0.9, 4 refinement steps with outlier re-answering")
+FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1)
 NEDF_FLOP = 2 * (78 * 128 + 5 * 128 * 128 + 128 * 2)          # per query, unpadded
 NERF_FLOP = 2 * (90 * 256 + 7 * 256 * 256 + 256 * 3)          # per sample, unpadded
 
@@ -131,22 +132,23 @@ def allmax(x, world):
 # ------------------------------------------------------------------------------------------------
 # the oracle on the host cores (cpu_baseline and the reference arm)
 # ------------------------------------------------------------------------------------------------
-def oracle_rate(scene, nedf_weights, target_s, threads, fallback=0.9, refine=4, seed=11):
+def oracle_rate(scene, nedf_weights, target_s, threads, seed=11):
+    """Pixels per second of the FP64 oracle on this host: seeded pixel batches of the same frame
+    until target_s seconds have been spent."""
     import oracle
     oracle.build()
     osc = oracle.OracleScene(scene, nedf_override=nedf_weights)
     from paper_2308_04669_gb300 import scenegen as sg
-    n = 64
-    t0 = time.perf_counter()
-    oracle.render(osc, px=sg.pixel_subset(scene.W, scene.H, n, seed), fallback_conf=fallback, refine_steps=refine,
-                  march_n=128, march_b=4, n_threads=threads)
-    dt = time.perf_counter() - t0
-    n2 = int(min(scene.W * scene.H, max(64, n * target_s / max(dt, 1e-3))))
-    px = sg.pixel_subset(scene.W, scene.H, n2, seed + 1)
-    t0 = time.perf_counter()
-    oracle.render(osc, px=px, fallback_conf=fallback, refine_steps=refine, march_n=128, march_b=4, n_threads=threads)
-    dt = time.perf_counter() - t0
-    return n2 / dt, n2, dt
+    n, done, secs, batch = 0, 0, 0.0, 256
+    while secs < target_s and done < scene.W * scene.H:
+        px = sg.pixel_subset(scene.W, scene.H, batch, seed + n)
+        t0 = time.perf_counter()
+        oracle.render(osc, px=px, march_n=128, march_b=4, n_threads=threads, **FRAME_OPTS)
+        secs += time.perf_counter() - t0
+        done += len(px)
+        n += 1
+        batch = min(batch * 2, 8192)
+    return done / secs, done, secs
 
 
 def run_reference(args):
@@ -162,15 +164,13 @@ def run_reference(args):
     osc = oracle.OracleScene(sc)
     # calibrate a per-step pixel sample that takes about per_step_s on the host cores
     t0 = time.perf_counter()
-    oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, 64, 99), fallback_conf=0.9, refine_steps=4, n_threads=threads)
-    n = int(max(64, 64 * per_step_s / max(time.perf_counter() - t0, 1e-3)))
+    oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, 256, 99), n_threads=threads, **FRAME_OPTS)
+    n = int(max(64, 256 * per_step_s / max(time.perf_counter() - t0, 1e-3)))
     for w in range(args.warmup):
-        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 200 + w), fallback_conf=0.9, refine_steps=4,
-                      n_threads=threads)
+        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 200 + w), n_threads=threads, **FRAME_OPTS)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 300 + k), fallback_conf=0.9, refine_steps=4,
-                      n_threads=threads)
+        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 300 + k), n_threads=threads, **FRAME_OPTS)
     dt = time.perf_counter() - t0
     value = n * args.steps / dt
     ms_frame = 1000.0 * sc.W * sc.H / value
@@ -226,13 +226,16 @@ def run_ours(args):
     from paper_2308_04669_gb300 import scenegen as sg
 
     sc = sg.thousand_scene()
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()            # a non-default stream: frames are CUDA-graph captured
+    torch.cuda.set_stream(stream)
     prec = native.PREC_BF16 if args.precision == "bf16" else native.PREC_FP32
     r = native.renderer_for(sc, precision=prec, stream=stream)
     log = {}
-    train_types(r, sc, args.train_steps, args.train_batch, args.label_rays, log)
+    if args.train_steps > 0:
+        train_types(r, sc, args.train_steps, args.train_batch, args.label_rays, log)
     o = r.get_options()
-    o.fallback_conf, o.refine_steps = 0.9, 4
+    for k, v in FRAME_OPTS.items():
+        setattr(o, k, v)
     r.set_options(o)
     cam, lights = r.camera(sc.eye, sc.target, sc.fov_deg), r.lights(sc.lights)
     n = sc.W * sc.H
@@ -267,15 +270,23 @@ def run_ours(args):
     stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
     clocks = clk.summary()
 
+    if args.frames_only:
+        r.close()
+        if rank == 0:
+            print(json.dumps({"frames_only": True, "ms_per_frame": frame_ms, "rays_per_s": n / (frame_ms * 1e-3),
+                              "stage_ms": stage_ms, "primary_pairs": st.primary_pairs, "shadow_pairs": st.shadow_pairs,
+                              "hit_pixels": st.hit_pixels, "fallback_pairs": st.fallback_pairs}), flush=True)
+        return
+
     # ---- depth error against a fine ray-march judge ------------------------------------------
     o2 = r.get_options()
-    saved = (o2.depth_source, o2.march_steps, o2.march_bisect, o2.fallback_conf, o2.refine_steps)
-    o2.depth_source, o2.march_steps, o2.march_bisect, o2.fallback_conf, o2.refine_steps = 1, 1024, 24, 0.0, 0
+    saved = (o2.depth_source, o2.march_steps, o2.march_bisect)
+    o2.depth_source, o2.march_steps, o2.march_bisect = 1, 1024, 24
     r.set_options(o2)
     jdepth = torch.empty(n, device=dev)
     jids = torch.empty(n, dtype=torch.int32, device=dev)
     r.render(cam, lights, jdepth, jids, None, None, None)
-    (o2.depth_source, o2.march_steps, o2.march_bisect, o2.fallback_conf, o2.refine_steps) = saved
+    (o2.depth_source, o2.march_steps, o2.march_bisect) = saved
     r.set_options(o2)
     torch.cuda.synchronize()
     both = (ids != -1) & (jids != -1)
@@ -291,10 +302,12 @@ def run_ours(args):
     march = {}
     mrgba = torch.empty(n, 4, device=dev)
     for es, key in [(1, "early_stop"), (0, "dense")]:
+        if not es and not args.march_dense:
+            continue
         try:
             r.render_march(cam, 128, es, mrgba)
             torch.cuda.synchronize()
-            reps = 3 if es else 1
+            reps = 1
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(reps):
@@ -305,6 +318,32 @@ def run_ours(args):
             march[key] = {"ms_per_frame": ms, "rays_per_s": n / (ms * 1e-3), "samples_per_pair": 128}
         except native.NedfError as e:
             march[key] = {"unavailable": str(e)}
+
+    # ---- the same frame with the FP32 CUDA-core networks (reference precision) -----------------
+    fp32 = None
+    if prec != native.PREC_FP32 and not args.no_fp32:
+        r32 = native.renderer_for(sc, precision=native.PREC_FP32, stream=stream)
+        w_tr = [r.get_nedf_weights(t, sc.types[t].nedf_w.shape[0]) for t in range(len(sc.types))]
+        import copy
+        sc32 = copy.copy(sc)
+        sc32.types = [copy.copy(t) for t in sc.types]
+        for t, w in zip(sc32.types, w_tr):
+            t.nedf_w = w
+        r32.load_scene(sc32)
+        o32 = r32.get_options()
+        for k, v in FRAME_OPTS.items():
+            setattr(o32, k, v)
+        r32.set_options(o32)
+        r32.render(cam, lights, depth, ids, None, None, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            r32.render(cam, lights, depth, ids, None, None, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp32 = {"ms_per_frame": e0.elapsed_time(e1) / 3, "rays_per_s": n / (e0.elapsed_time(e1) / 3 * 1e-3)}
+        r32.close()
 
     # ---- end to end through the public API with host buffers ---------------------------------
     host_out = torch.empty(n, 4, dtype=torch.float32, pin_memory=True)
@@ -364,6 +403,7 @@ def run_ours(args):
             "frame": {"ms": frame_ms, "total_rays_per_s": n * (1 + 4) / (frame_ms * 1e-3),
                       "primary_pairs": P1, "shadow_pairs": P3, "hit_pixels": Hv, "fallback_pairs": st.fallback_pairs,
                       "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "wall_s": t_wall},
+            "fp32_frame": fp32,
             "march_frame": march,
             "speedup_vs_march": {k: v["ms_per_frame"] / frame_ms for k, v in march.items() if "ms_per_frame" in v},
             "depth_err": derr, **log}
@@ -380,12 +420,16 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
-    ap.add_argument("--train-steps", type=int, default=600)
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--train-batch", type=int, default=16384)
     ap.add_argument("--label-rays", type=int, default=1 << 20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--march-dense", action="store_true", help="also time the dense 128-sample ray-march frame")
+    ap.add_argument("--frames-only", action="store_true",
+                    help="timed frames only: no judge, ray-march, FP32, e2e or CPU legs (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

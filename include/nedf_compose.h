@@ -195,8 +195,12 @@ int nedf_compose_set_instances(nedf_handle *h, int n, const nedf_instance *inst)
  *   rgba    float4 Step 2 colour buffer (premultiplied RGB, opacity), (0,0,0,0) if empty
  *   shadow  float  Step 3 shadow buffer: mean over lights of (occluded ? beta : 1); 1 if empty
  *   out     float4 composite: (rgba.rgb * shadow, rgba.a)
- * Any of depth / id / rgba / shadow / out may be NULL (the library then keeps its own copy).
+ * Any of depth / id / rgba / shadow / out may be NULL (the library then keeps its own copy);
+ * given buffers are written by the kernels directly and must stay valid until the frame is done.
  * stats (host) may be NULL; when given, the call synchronises and fills it.
+ * On a stream other than the legacy default stream the frame (uploads and every kernel) is
+ * captured into a CUDA graph on first use and relaunched while the instance count, the light
+ * count, depth_source, n_shade, profiling and the output buffers stay the same.
  * Ties in depth go to the lowest instance id (Algorithm 1's strict '<' in id order).
  * Errors: NEDF_ERR_STATE (no types or instances yet), NEDF_ERR_ARG, NEDF_ERR_CUDA, and with
  * stats given NEDF_ERR_CAPACITY when a pair list overflowed. */

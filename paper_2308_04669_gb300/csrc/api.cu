@@ -61,6 +61,23 @@ struct nedf_handle {
     void *d_march_scratch = nullptr;
     size_t march_scratch_bytes = 0;
     bool profiling = false, profiled = false;
+    // CUDA graph of one frame, relaunched while its shape key is unchanged
+    struct FrameKey {
+        int n_inst, n_lights, depth_source, n_shade, profiling;
+        const void *out[5];
+        bool operator==(const FrameKey &o) const
+        {
+            if (n_inst != o.n_inst || n_lights != o.n_lights || depth_source != o.depth_source ||
+                n_shade != o.n_shade || profiling != o.profiling)
+                return false;
+            for (int i = 0; i < 5; ++i)
+                if (out[i] != o.out[i]) return false;
+            return true;
+        }
+    } gkey{};
+    cudaGraphExec_t gexec = nullptr;
+    int glaunches = 0;
+    bool graphs = true;
     cudaEvent_t ev[kStages + 1] = {};
     int last_launches = 0;
 };
@@ -295,6 +312,7 @@ void nedf_compose_destroy(nedf_handle *h)
     if (h->h_cam) cudaFreeHost(h->h_cam);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
     delete h;
 }
 
@@ -450,9 +468,11 @@ static int check_frame_args(nedf_handle *h, const nedf_camera *cam, const nedf_l
     return NEDF_OK;
 }
 
-static cudaError_t upload_frame(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights)
+// Writes this frame's camera, lights and options into the pinned staging records (the copies
+// to the device are part of the frame's launch sequence).
+static cudaError_t stage_frame(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights)
 {
-    cudaError_t e = cudaStreamSynchronize(h->stream);   // staging buffers may still be in flight
+    cudaError_t e = cudaStreamSynchronize(h->stream);   // the previous frame may still read the staging
     if (e != cudaSuccess) return e;
     DevFrame &f = *h->h_frame;
     std::memset(&f, 0, sizeof(f));
@@ -478,9 +498,20 @@ static cudaError_t upload_frame(nedf_handle *h, const nedf_camera *cam, const ne
     std::memcpy(h->h_cam->eye, cam->eye, sizeof(cam->eye));
     std::memcpy(h->h_cam->target, cam->target, sizeof(cam->target));
     h->h_cam->fov_y_deg = cam->fov_y_deg;
-    e = cudaMemcpyAsync(h->d_frame, h->h_frame, sizeof(DevFrame), cudaMemcpyHostToDevice, h->stream);
+    return cudaSuccess;
+}
+
+static cudaError_t enqueue_upload(nedf_handle *h)
+{
+    cudaError_t e = cudaMemcpyAsync(h->d_frame, h->h_frame, sizeof(DevFrame), cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(h->d_cam, h->h_cam, sizeof(HostCamera), cudaMemcpyHostToDevice, h->stream);
+}
+
+static cudaError_t upload_frame(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights)
+{
+    cudaError_t e = stage_frame(h, cam, lights, n_lights);
+    return e != cudaSuccess ? e : enqueue_upload(h);
 }
 
 static int fill_stats(nedf_handle *h, nedf_frame_stats *stats)
@@ -499,11 +530,22 @@ static int fill_stats(nedf_handle *h, nedf_frame_stats *stats)
     return nedf_compose_sync(h);
 }
 
-static int render_impl(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights)
+// One frame.  Caller device buffers (any may be NULL) receive the outputs directly.  On a
+// stream other than the legacy default stream the upload and the launch sequence are captured
+// into a CUDA graph, relaunched while the shape key (instance and light counts, depth source,
+// samples per pixel, profiling, output buffers) stays the same.
+static int render_impl(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights,
+                       float *depth = nullptr, uint32_t *id = nullptr, float *rgba = nullptr, float *shadow = nullptr,
+                       float *out = nullptr)
 {
-    CK(h, upload_frame(h, cam, lights, n_lights));
+    CK(h, stage_frame(h, cam, lights, n_lights));
     FrameLaunch L;
     L.ws = make_ws(h);
+    if (depth) L.ws.depth = depth;
+    if (id) L.ws.id = id;
+    if (rgba) L.ws.rgba = reinterpret_cast<float4 *>(rgba);
+    if (shadow) L.ws.shadow = shadow;
+    if (out) L.ws.out = reinterpret_cast<float4 *>(out);
     L.stream = h->stream;
     L.W = h->cfg.width;
     L.H = h->cfg.height;
@@ -514,8 +556,36 @@ static int render_impl(nedf_handle *h, const nedf_camera *cam, const nedf_light 
     L.cam = h->d_cam;
     L.events = h->profiling ? h->ev : nullptr;
     L.launches = 0;
-    CK(h, launch_frame(L));
-    h->last_launches = L.launches;
+    if (!h->graphs || h->stream == nullptr) {
+        CK(h, enqueue_upload(h));
+        CK(h, launch_frame(L));
+        h->last_launches = L.launches;
+    } else {
+        nedf_handle::FrameKey key{h->n_inst, n_lights, h->opt.depth_source, h->opt.n_shade, h->profiling ? 1 : 0,
+                                  {depth, id, rgba, shadow, out}};
+        if (!h->gexec || !(key == h->gkey)) {
+            if (h->gexec) {
+                cudaGraphExecDestroy(h->gexec);
+                h->gexec = nullptr;
+            }
+            CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_upload(h);
+            if (e == cudaSuccess) e = launch_frame(L);
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                h->gexec = nullptr;
+                return cuda_fail(h, e, "frame graph capture");
+            }
+            h->gkey = key;
+            h->glaunches = L.launches;
+        }
+        CK(h, cudaGraphLaunch(h->gexec, h->stream));
+        h->last_launches = h->glaunches;
+    }
     if (h->profiling) h->profiled = true;
     return NEDF_OK;
 }
@@ -526,15 +596,8 @@ int nedf_compose_render(nedf_handle *h, const nedf_camera *cam, const nedf_light
 {
     int r = check_frame_args(h, cam, lights, n_lights);
     if (r != NEDF_OK) return r;
-    r = render_impl(h, cam, lights, n_lights);
+    r = render_impl(h, cam, lights, n_lights, depth, id, rgba, shadow, out);
     if (r != NEDF_OK) return r;
-    size_t npix = (size_t)h->cfg.width * h->cfg.height;
-    cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
-    if (depth) CK(h, cudaMemcpyAsync(depth, h->d_depth, npix * 4, k, h->stream));
-    if (id) CK(h, cudaMemcpyAsync(id, h->d_id, npix * 4, k, h->stream));
-    if (rgba) CK(h, cudaMemcpyAsync(rgba, h->d_rgba, npix * 16, k, h->stream));
-    if (shadow) CK(h, cudaMemcpyAsync(shadow, h->d_shadow, npix * 4, k, h->stream));
-    if (out) CK(h, cudaMemcpyAsync(out, h->d_out, npix * 16, k, h->stream));
     if (stats) return fill_stats(h, stats);
     return NEDF_OK;
 }

@@ -17,21 +17,6 @@ namespace nedf {
 constexpr float kEsWeight = 1e-6f;
 constexpr float kEsTransmittance = 1e-4f;
 
-struct MarchBuffers {
-    int *head;            // [npix] first pair of the pixel's list (-1 = none)
-    int *next;            // [pairs] next pair of the same pixel
-    float *te_world;      // [pairs]
-    float *T_pair;        // [pairs] transmittance through the pair's samples
-    float *T_first;       // [pairs] transmittance before the pair's first sample row
-    int *k_first;         // [pairs]
-    float4 *C;            // [pairs] accumulated weighted colour (xyz)
-    uint2 *rows;          // [pairs * n] (pair, k)
-    unsigned long long *row_cursor;   // [kMaxTypes]
-    unsigned long long *row_off;      // [kMaxTypes + 1]
-    unsigned long long *row_tile;     // [kMaxTypes + 1]
-    long long row_cap;
-};
-
 __device__ __forceinline__ void pair_ray(const DevFrame &f, const DevInst &I, uint32_t pix, V3 &ol, V3 &dl)
 {
     V3 o, d;
@@ -105,14 +90,14 @@ __global__ void k_march_pairs(Workspace ws, MarchBuffers mb, int n_samples)
     }
 }
 
-__global__ void k_march_scan(Workspace ws, MarchBuffers mb)
+__global__ void k_march_scan(Workspace ws, MarchBuffers mb, int rows_per_tile)
 {
     const DevFrame &f = *ws.frame;
     unsigned long long t = 0;
     for (int k = 0; k < f.n_types; ++k) {
         mb.row_tile[k] = t;
         unsigned long long rows = min(mb.row_cursor[k], mb.row_off[k + 1]) - mb.row_off[k];
-        t += (rows + kTileRows - 1) / kTileRows;
+        t += (rows + rows_per_tile - 1) / rows_per_tile;
     }
     mb.row_tile[f.n_types] = t;
 }
@@ -276,9 +261,13 @@ cudaError_t launch_march_colour_frame(const FrameLaunch &L, void *scratch, long 
     k_march_clear<<<g, 256, 0, st>>>(ws, mb, npix, n_samples);
     if (early_stop) k_march_pairs<true><<<g * 2, 128, 0, st>>>(ws, mb, n_samples);
     else k_march_pairs<false><<<g * 2, 128, 0, st>>>(ws, mb, n_samples);
-    k_march_scan<<<1, 1, 0, st>>>(ws, mb);
+    const bool tc = ws.precision == 1 && ws.nerf_hidden > 0;
+    k_march_scan<<<1, 1, 0, st>>>(ws, mb, tc ? kTcTileRows : kTileRows);
     cudaError_t e = cudaSuccess;
-    if (ws.nerf_hidden > 0) {
+    if (tc) {
+        e = launch_march_colour_tc(ws, mb, n_samples, L.num_sms, st);
+        if (e != cudaSuccess) return e;
+    } else if (ws.nerf_hidden > 0) {
         switch (ws.nerf_width) {
         case 64: e = launch_colour<64>(ws, mb, n_samples, g, st); break;
         case 128: e = launch_colour<128>(ws, mb, n_samples, g, st); break;

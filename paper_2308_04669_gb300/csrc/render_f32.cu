@@ -495,8 +495,9 @@ cudaError_t launch_frame(FrameLaunch &L)
     const bool tc_shade = ws.precision == 1 && ws.nerf_hidden > 0;
     const int nedf_rows = tc_nedf ? kTcTileRows : kTileRows;
     const int shade_rows = tc_shade ? kTcTileRows : kTileRows;
+    // external records: inside a captured graph they still mark the stage boundaries for timing
     auto mark = [&]() {
-        if (L.events) cudaEventRecord(L.events[stage], st);
+        if (L.events) cudaEventRecordWithFlags(L.events[stage], st, cudaEventRecordExternal);
         ++stage;
     };
     mark();

@@ -90,6 +90,23 @@ struct LightCam {
     int valid;                   // 0: light inside the scene bound or too wide a view -> all instances
 };
 
+// Plain-method colour frame buffers (march.cu): per pair, its samples' transmittance and the
+// weighted colour accumulated by the colour-network tiles over its run of sample rows.
+struct MarchBuffers {
+    int *head;            // [npix] first pair of the pixel's list (-1 = none)
+    int *next;            // [pairs] next pair of the same pixel
+    float *te_world;      // [pairs]
+    float *T_pair;        // [pairs] transmittance through the pair's samples
+    float *T_first;       // [pairs] transmittance before the pair's first sample row
+    int *k_first;         // [pairs]
+    float4 *C;            // [pairs] accumulated weighted colour (xyz)
+    uint2 *rows;          // [pairs * n] (pair, k)
+    unsigned long long *row_cursor;   // [kMaxTypes]
+    unsigned long long *row_off;      // [kMaxTypes + 1]
+    unsigned long long *row_tile;     // [kMaxTypes + 1]
+    long long row_cap;
+};
+
 // ---------------------------------------------------------------------------------------------
 // (ray, instance) pair set-up shared by the NeDF kernels and the deferred plain-method pass
 // ---------------------------------------------------------------------------------------------

@@ -33,6 +33,9 @@ cudaError_t launch_nedf_tc(const Workspace &ws, const void *blobs, size_t stride
 cudaError_t launch_shade_tc(const Workspace &ws, const void *blobs, size_t stride, int npix, int num_sms,
                             cudaStream_t st);
 cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStream_t st);
+// plain-method colour rows on the tensor cores (march.cu builds the rows)
+cudaError_t launch_march_colour_tc(const Workspace &ws, const MarchBuffers &mb, int n_samples, int num_sms,
+                                   cudaStream_t st);
 
 // Step-3 binning through per-light shadow-map cameras (shadow_bin.cu)
 cudaError_t launch_shadow_binning(const Workspace &ws, int npix, int n_lights, int n_inst, int rows_per_tile,

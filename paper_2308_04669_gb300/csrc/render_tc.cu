@@ -387,9 +387,12 @@ __device__ __forceinline__ int shade_tile_type(const Counters &C, int n_types, u
     return t;
 }
 
-template <int N>
+// MODE 0: rows of Step 2 (pixels x n_shade samples around the stored depth), composited per
+//         pixel.  MODE 1: sample rows of the plain method's colour frame (runs of samples of
+//         one (ray, instance) pair), weighted by T * alpha and summed per pair.
+template <int N, int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_shade_tc(Workspace ws, const uint8_t *blobs, size_t blob_stride, int npix)
+k_shade_tc(Workspace ws, MarchBuffers mb, const uint8_t *blobs, size_t blob_stride, int npix, int n_samples)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ TcSmem S;
@@ -418,14 +421,18 @@ k_shade_tc(Workspace ws, const uint8_t *blobs, size_t blob_stride, int npix)
     const Counters &C = *ws.cnt;
     const int ns = f.n_shade;
     const int ppt = kTcRows / ns;
-    const unsigned long long n_tiles = C.h_tile[f.n_types];
+    const unsigned long long *tile_off = MODE == 0 ? C.h_tile : mb.row_tile;
+    const unsigned long long n_tiles = tile_off[f.n_types];
+    auto tile_type = [&](unsigned long long tile) {
+        int t = 0;
+        while (t + 1 < f.n_types && tile_off[t + 1] <= tile) ++t;
+        return t;
+    };
     auto layer_off = [&](int l) -> size_t { return l == 0 ? 0 : (size_t)K0 * N * 2 + (size_t)(l - 1) * N * N * 2; };
     auto layer_bytes = [&](int l) -> uint32_t { return (uint32_t)((size_t)N * (l == 0 ? K0 : N) * 2); };
 
     for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int t = shade_tile_type<N>(C, f.n_types, tile);
-        const unsigned long long first = (tile - C.h_tile[t]) * ppt;
-        const int n_pix = first < C.h_count[t] ? (int)min((unsigned long long)ppt, C.h_count[t] - first) : 0;
+        const int t = tile_type(tile);
         const DevType T = ws.types[t];
         const uint8_t *blob = blobs + (size_t)t * blob_stride;
         // weights of layer 0 (unless prefetched) and, on a type change, the fp32 block
@@ -445,24 +452,53 @@ k_shade_tc(Workspace ws, const uint8_t *blobs, size_t blob_stride, int npix)
             f32_type = t;
         }
         prefetched = -1;
-        // ---- row set-up: sample position, density, encoding ----------------------------------
-        const int q = r / ns, j = r - q * ns;
-        const bool valid = q < n_pix;
+        // ---- row set-up: sample position and its density / weight ----------------------------
         float x6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float sig = 0.f;
-        if (valid) {
-            uint32_t p = ws.hlist[(size_t)t * npix + first + q];
-            DevInst I = ws.inst[ws.id[p]];
-            V3 o, d, ol, dl;
-            camera_ray(f, p % f.W, p / f.W, o, d);
-            to_local(I, o, d, ol, dl);
-            float Dl = ws.depth[p] / I.s;
-            float delta = 2.0f * f.shade_half / ns;
-            float tj = Dl - f.shade_half + (j + 0.5f) * delta;
-            V3 x = madd(ol, tj, dl);
-            x6[0] = x.x; x6[1] = x.y; x6[2] = x.z; x6[3] = dl.x; x6[4] = dl.y; x6[5] = dl.z;
-            sig = density(T, x, f.sigma_max, f.sdf_width);
-            if (j == 0) { pix_s[q] = p; wdelta_s[q] = I.s * delta; }
+        int n_pix = 0;                       // MODE 0: pixels in the tile
+        uint32_t pair = 0xFFFFFFFFu;         // MODE 1: the row's pair
+        if (MODE == 0) {
+            const unsigned long long first = (tile - C.h_tile[t]) * ppt;
+            n_pix = first < C.h_count[t] ? (int)min((unsigned long long)ppt, C.h_count[t] - first) : 0;
+            const int q = r / ns, j = r - q * ns;
+            if (q < n_pix) {
+                uint32_t p = ws.hlist[(size_t)t * npix + first + q];
+                DevInst I = ws.inst[ws.id[p]];
+                V3 o, d, ol, dl;
+                camera_ray(f, p % f.W, p / f.W, o, d);
+                to_local(I, o, d, ol, dl);
+                float Dl = ws.depth[p] / I.s;
+                float delta = 2.0f * f.shade_half / ns;
+                float tj = Dl - f.shade_half + (j + 0.5f) * delta;
+                V3 x = madd(ol, tj, dl);
+                x6[0] = x.x; x6[1] = x.y; x6[2] = x.z; x6[3] = dl.x; x6[4] = dl.y; x6[5] = dl.z;
+                sig = density(T, x, f.sigma_max, f.sdf_width);
+                if (j == 0) { pix_s[q] = p; wdelta_s[q] = I.s * delta; }
+            }
+        } else {
+            const unsigned long long end = min(mb.row_cursor[t], mb.row_off[t + 1]);
+            const unsigned long long row_i = mb.row_off[t] + (tile - mb.row_tile[t]) * kTcRows + r;
+            if (row_i < end) {
+                uint2 row = mb.rows[row_i];
+                uint2 pr = ws.ppairs[row.x];
+                DevInst I = ws.inst[pr.y];
+                V3 o, d, ol, dl;
+                camera_ray(f, pr.x % f.W, pr.x / f.W, o, d);
+                to_local(I, o, d, ol, dl);
+                Chord ch;
+                bound_chord(ol, dl, T.rb, ch);
+                float dt = (ch.tx - ch.te) / n_samples;
+                float Tr = mb.T_first[row.x];      // transmittance at sample k from the pair's first row
+                for (int jj = mb.k_first[row.x]; jj < (int)row.y; ++jj) {
+                    float sj = density(T, madd(ol, ch.te + (jj + 0.5f) * dt, dl), f.sigma_max, f.sdf_width);
+                    Tr *= expf(-sj * I.s * dt);
+                }
+                V3 x = madd(ol, ch.te + (row.y + 0.5f) * dt, dl);
+                x6[0] = x.x; x6[1] = x.y; x6[2] = x.z; x6[3] = dl.x; x6[4] = dl.y; x6[5] = dl.z;
+                sig = Tr * (1.0f - expf(-density(T, x, f.sigma_max, f.sdf_width) * I.s * dt));   // weight
+                pair = row.x;
+            }
+            pix_s[r] = pair;
         }
         sig_s[r] = sig;
         {
@@ -491,7 +527,7 @@ k_shade_tc(Workspace ws, const uint8_t *blobs, size_t blob_stride, int npix)
             } else {
                 unsigned long long nt = tile + gridDim.x;
                 if (nt < n_tiles) {
-                    next_t = shade_tile_type<N>(C, f.n_types, nt);
+                    next_t = tile_type(nt);
                     next_src = blobs + (size_t)next_t * blob_stride;
                 }
             }
@@ -513,20 +549,32 @@ k_shade_tc(Workspace ws, const uint8_t *blobs, size_t blob_stride, int npix)
             tc_fence_before();
             __syncthreads();
         }
+        const float wr = MODE == 0 ? 1.0f : sig;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) rgb_s[r][c] = 1.0f / (1.0f + expf(-out[c]));
+        for (int c = 0; c < 3; ++c) rgb_s[r][c] = wr / (1.0f + expf(-out[c]));
         __syncthreads();
-        // ---- front-to-back composite over each pixel's samples (Eq. 8 over the window) ---------
-        if (r < n_pix) {
-            float Tr = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, Aa = 0.f;
-            for (int k = 0; k < ns; ++k) {
-                int rr = r * ns + k;
-                float alpha = 1.0f - expf(-sig_s[rr] * wdelta_s[r]);
-                float w = Tr * alpha;
-                cr += w * rgb_s[rr][0]; cg += w * rgb_s[rr][1]; cb += w * rgb_s[rr][2]; Aa += w;
-                Tr *= 1.0f - alpha;
+        if (MODE == 0) {
+            // front-to-back composite over each pixel's samples (Eq. 8 over the window)
+            if (r < n_pix) {
+                float Tr = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, Aa = 0.f;
+                for (int k = 0; k < ns; ++k) {
+                    int rr = r * ns + k;
+                    float alpha = 1.0f - expf(-sig_s[rr] * wdelta_s[r]);
+                    float w = Tr * alpha;
+                    cr += w * rgb_s[rr][0]; cg += w * rgb_s[rr][1]; cb += w * rgb_s[rr][2]; Aa += w;
+                    Tr *= 1.0f - alpha;
+                }
+                ws.rgba[pix_s[r]] = make_float4(cr, cg, cb, Aa);
             }
-            ws.rgba[pix_s[r]] = make_float4(cr, cg, cb, Aa);
+        } else {
+            // one sum per run of rows of the same pair (runs are contiguous)
+            if (pair != 0xFFFFFFFFu && (r == 0 || pix_s[r - 1] != pair)) {
+                float a = 0.f, b = 0.f, c = 0.f;
+                for (int k = r; k < kTcRows && pix_s[k] == pair; ++k) { a += rgb_s[k][0]; b += rgb_s[k][1]; c += rgb_s[k][2]; }
+                atomicAdd(&mb.C[pair].x, a);
+                atomicAdd(&mb.C[pair].y, b);
+                atomicAdd(&mb.C[pair].z, c);
+            }
         }
         if (!__syncthreads_and(y.ok)) break;
     }
@@ -606,28 +654,42 @@ cudaError_t launch_nedf_tc(const Workspace &ws, const void *blobs, size_t stride
     }
 }
 
-template <int N>
-static cudaError_t launch_shade_tc_n(const Workspace &ws, const uint8_t *blobs, size_t stride, int npix, int grid,
-                                     cudaStream_t st)
+template <int N, int MODE>
+static cudaError_t launch_shade_tc_n(const Workspace &ws, const MarchBuffers &mb, const uint8_t *blobs, size_t stride,
+                                     int npix, int n_samples, int grid, cudaStream_t st)
 {
     size_t sm = shade_tc_smem<N>(ws.nerf_hidden);
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(k_shade_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_shade_tc<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_shade_tc<N><<<grid, kTcThreads, sm, st>>>(ws, blobs, stride, npix);
+    k_shade_tc<N, MODE><<<grid, kTcThreads, sm, st>>>(ws, mb, blobs, stride, npix, n_samples);
     return cudaGetLastError();
 }
 
-cudaError_t launch_shade_tc(const Workspace &ws, const void *blobs, size_t stride, int npix, int num_sms,
-                            cudaStream_t st)
+template <int MODE>
+static cudaError_t launch_colour_tc(const Workspace &ws, const MarchBuffers &mb, int npix, int n_samples, int num_sms,
+                                    cudaStream_t st)
 {
-    const uint8_t *b = (const uint8_t *)blobs;
+    const uint8_t *b = ws.nerf_tc;
+    const size_t stride = ws.nerf_tc_stride;
     switch (ws.nerf_width) {
-    case 64: return launch_shade_tc_n<64>(ws, b, stride, npix, num_sms, st);
-    case 128: return launch_shade_tc_n<128>(ws, b, stride, npix, num_sms, st);
-    case 256: return launch_shade_tc_n<256>(ws, b, stride, npix, num_sms, st);
+    case 64: return launch_shade_tc_n<64, MODE>(ws, mb, b, stride, npix, n_samples, num_sms, st);
+    case 128: return launch_shade_tc_n<128, MODE>(ws, mb, b, stride, npix, n_samples, num_sms, st);
+    case 256: return launch_shade_tc_n<256, MODE>(ws, mb, b, stride, npix, n_samples, num_sms, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_shade_tc(const Workspace &ws, const void *, size_t, int npix, int num_sms, cudaStream_t st)
+{
+    MarchBuffers none{};
+    return launch_colour_tc<0>(ws, none, npix, 0, num_sms, st);
+}
+
+cudaError_t launch_march_colour_tc(const Workspace &ws, const MarchBuffers &mb, int n_samples, int num_sms,
+                                   cudaStream_t st)
+{
+    return launch_colour_tc<1>(ws, mb, 0, n_samples, num_sms, st);
 }
 
 }  // namespace nedf

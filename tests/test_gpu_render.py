@@ -201,10 +201,10 @@ def test_pair_capacity_overflow_is_reported(orc):
     r.close()
 
 
-def _march_gpu(sc, n_samples, early_stop):
+def _march_gpu(sc, n_samples, early_stop, precision=0):
     import torch
     from paper_2308_04669_gb300 import native
-    r = native.renderer_for(sc)
+    r = native.renderer_for(sc, precision=precision)
     rgba = torch.empty(sc.W * sc.H, 4, device="cuda")
     r.render_march(r.camera(sc.eye, sc.target, sc.fov_deg), n_samples, early_stop, rgba)
     torch.cuda.synchronize()

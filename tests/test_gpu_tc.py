@@ -119,3 +119,18 @@ def test_bf16_thousand_instances_stats(orc):
     assert b["stats"].status == 0
     both = (a["id"] != NOID) & (b["id"] != NOID)
     assert (a["id"][both] == b["id"][both]).mean() > 0.97
+
+
+def test_bf16_plain_method_frame(orc):
+    """The plain method's colour frame with its NeRF on the tensor cores (sample rows of every
+    (ray, instance) pair, weights T * alpha, per-pair sums) against the BF16-operand oracle."""
+    from paper_2308_04669_gb300 import native
+    from .test_gpu_render import _march_gpu
+    sc = sg.three_types_scene(96, 96)
+    g = _march_gpu(sc, 64, 0, precision=native.PREC_BF16)
+    px = sg.pixel_subset(96, 96, 160, 3)
+    o = orc.volume_render(orc.OracleScene(sc), 64, px=px, n_threads=8, quant=orc.QUANT_BF16)
+    ok = close(g[px], o)
+    assert ok.mean() > 0.995 and (o[:, 3] > 0.5).sum() > 10
+    es = _march_gpu(sc, 64, 1, precision=native.PREC_BF16)
+    assert np.abs(es - g).max() < 2e-3
