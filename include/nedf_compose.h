@@ -246,6 +246,35 @@ int nedf_compose_get_stage_times(nedf_handle *h, float *ms, int n);
 int nedf_compose_nedf_query(nedf_handle *h, int type, int n, const float *o, const float *d,
                             float *out);
 
+/* ---- Step 1 without allocations ------------------------------------------------------------ */
+
+/* Depth and id buffers of Step 1 (same arithmetic as nedf_compose_render with default options)
+ * for callers that cannot allocate device memory: code embedded in a host whose device memory
+ * belongs to that host's own pool, real-time loops that must not block on or fail in an
+ * allocation, or phases in which the allocator may not be touched.  No handle is needed and
+ * nothing is allocated (no cudaMalloc, cudaFree or allocating library call); the caller passes
+ * every input and output, and the call's only scratch is a fixed array inside the library of
+ * 512 x 512 packed (depth, id) keys (2 MiB, held on every GPU that loads the library until
+ * the process exits).  The paper has no counterpart for this entry point.
+ *   width, height    framebuffer size; width * height must not exceed 512 * 512 (NEDF_ERR_ARG)
+ *   cam              host camera record
+ *   inst_dev         device array of n_inst nedf_instance records (id = index)
+ *   rb_host          host array of n_types bound radii
+ *   nedf_hidden, nedf_width, nedf_weights_dev
+ *                    NeDF shape and device array of n_types packed NeDF weight sets, back to back
+ *   depth_dev, id_dev  device outputs of width * height floats / uint32 (as in render)
+ *   cuda_stream      stream the work is queued on (asynchronous; NULL = legacy default stream)
+ * Every call shares the scratch array and clears the part it uses first; calls whose work
+ * overlaps on the GPU (other streams or threads) race on it and must be serialised by the caller.
+ * The first call on each device looks up the scratch array's device address (once, with that
+ * device current); make that first call before any stream capture.  Errors (null pointers,
+ * sizes, shapes, a CUDA failure) return a NEDF_ERR_* code; the text is available from
+ * nedf_compose_last_error(NULL) on the calling thread. */
+int nedf_compose_depth_noalloc(int width, int height, const nedf_camera *cam, int n_inst,
+                               const nedf_instance *inst_dev, int n_types, const float *rb_host,
+                               int nedf_hidden, int nedf_width, const float *nedf_weights_dev,
+                               float *depth_dev, uint32_t *id_dev, void *cuda_stream);
+
 /* ---- learned part -------------------------------------------------------------------------- */
 
 /* Builds the training set of one type on the device: n_rays rays with entry points uniform on

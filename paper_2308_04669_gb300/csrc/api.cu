@@ -84,6 +84,11 @@ struct nedf_handle {
 
 static thread_local std::string g_create_error;
 
+namespace nedf {
+// Error text of calls that have no handle (returned by nedf_compose_last_error(NULL)).
+void set_thread_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace nedf
+
 static int fail(nedf_handle *h, int code, const std::string &msg)
 {
     if (h) h->err = msg;

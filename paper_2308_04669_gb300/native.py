@@ -87,6 +87,8 @@ EXPORTS = {
     "nedf_compose_set_profiling": ([_H, C.c_int], C.c_int),
     "nedf_compose_get_stage_times": ([_H, _fp, C.c_int], C.c_int),
     "nedf_compose_nedf_query": ([_H, C.c_int, C.c_int, _vp, _vp, _vp], C.c_int),
+    "nedf_compose_depth_noalloc": ([C.c_int, C.c_int, C.POINTER(Camera), C.c_int, _vp, C.c_int, _fp, C.c_int, C.c_int,
+                                    _vp, _vp, _vp, _vp], C.c_int),
     "nedf_compose_make_labels": ([_H, C.c_int, C.c_int64, C.c_uint64, C.c_int, C.c_int, _vp, _vp, _vp, _vp],
                                  C.c_int),
     "nedf_compose_train_step": ([_H, C.c_int, C.c_int, C.c_float, _fp], C.c_int),
