@@ -37,6 +37,9 @@ WORKLOAD = ("1024 instances (sphere/torus/box, seed 3, T in [-20,20]^3) at 1024x
             "fallback below confidence 0.9, 4 refinement steps with outlier re-answering")
 FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1)
 NEDF_FLOP = 2 * (78 * 128 + 5 * 128 * 128 + 128 * 2)          # per query, unpadded
+# DRAM bytes (read + write) per launch of a stage's kernel from an ncu capture of the current
+# kernel source (profiles/); a stage is absent here once its kernel changed after the capture.
+PROFILED_TRAFFIC = {"step2_shade": 9.40e6}    # k_shade_tc<256,0>, profiles/k_shade_tc_1024inst_1024px_bf16.md
 NERF_FLOP = 2 * (90 * 256 + 7 * 256 * 256 + 256 * 3)          # per sample, unpadded
 
 
@@ -375,7 +378,7 @@ def run_ours(args):
     else:
         peak = pk["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "peak_basis": f"bf16 dense, {pk_kind} (burst)"}
+                "traffic": PROFILED_TRAFFIC.get(dom), "kernel": dom, "peak_basis": f"bf16 dense, {pk_kind} (burst)"}
 
     # ---- CPU baseline: the oracle on the host cores ------------------------------------------
     cpu = None
