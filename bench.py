@@ -39,7 +39,7 @@ FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1)
 NEDF_FLOP = 2 * (78 * 128 + 5 * 128 * 128 + 128 * 2)          # per query, unpadded
 # DRAM bytes (read + write) per launch of a stage's kernel from an ncu capture of the current
 # kernel source (profiles/); a stage is absent here once its kernel changed after the capture.
-PROFILED_TRAFFIC = {"step2_shade": 9.40e6}    # k_shade_tc<256,0>, profiles/k_shade_tc_1024inst_1024px_bf16.md
+PROFILED_TRAFFIC = {"step2_shade": 9.41e6}    # k_pipe<256,0>, profiles/k_pipe_1024inst_1024px_bf16.md
 NERF_FLOP = 2 * (90 * 256 + 7 * 256 * 256 + 256 * 3)          # per sample, unpadded
 
 

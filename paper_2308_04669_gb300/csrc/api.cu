@@ -214,9 +214,8 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
         return fail(nullptr, NEDF_ERR_UNSUPPORTED, "NeRF shape: hidden 0..16, width 64/128/256");
     if (c.precision != NEDF_PREC_FP32 && c.precision != NEDF_PREC_BF16)
         return fail(nullptr, NEDF_ERR_UNSUPPORTED, "precision");
-    if (c.precision == NEDF_PREC_BF16 && (c.nedf_width > 128 || (c.nedf_width == 128 && c.nedf_hidden > 7)))
-        return fail(nullptr, NEDF_ERR_UNSUPPORTED, "BF16 NeDF weights must fit in shared memory (width <= 128, "
-                                                   "at most 7 hidden layers of 128)");
+    if (c.precision == NEDF_PREC_BF16 && c.nedf_width > 128)
+        return fail(nullptr, NEDF_ERR_UNSUPPORTED, "BF16 NeDF width must be 64 or 128");
     if (c.primary_pair_capacity < 0 || c.shadow_pair_capacity < 0)
         return fail(nullptr, NEDF_ERR_ARG, "negative capacity");
 
@@ -280,10 +279,10 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
         CA(h->d_scan_tmp, sizeof(uint32_t) * 1024);
     }
     if (c.precision == NEDF_PREC_BF16) {
-        h->nedf_tc_stride = tc_blob_size(kNedfInPad, c.nedf_width, c.nedf_hidden, 2);
+        h->nedf_tc_stride = pipe_blob_size(kNedfInPad, c.nedf_width, c.nedf_hidden, 2);
         CA(h->d_nedf_tc, h->nedf_tc_stride * c.max_types);
         if (c.nerf_hidden > 0) {
-            h->nerf_tc_stride = tc_blob_size(kNerfInPad, c.nerf_width, c.nerf_hidden, 3);
+            h->nerf_tc_stride = pipe_blob_size(kNerfInPad, c.nerf_width, c.nerf_hidden, 3);
             CA(h->d_nerf_tc, h->nerf_tc_stride * c.max_types);
         }
     }
@@ -409,7 +408,7 @@ int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *ty
         ts.step = 0;
         ts.cursor = 0;
         if (h->d_nedf_tc)
-            CK(h, launch_pack_tc(ts.master, h->d_nedf_tc + (size_t)k * h->nedf_tc_stride, kNedfIn, kNedfInPad,
+            CK(h, launch_pack_pipe(ts.master, h->d_nedf_tc + (size_t)k * h->nedf_tc_stride, kNedfIn, kNedfInPad,
                                  h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->stream));
     }
     if (h->d_nerf_tc) {
@@ -419,7 +418,7 @@ int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *ty
             cudaError_t e = cudaMemcpy(tmp, types[k].nerf_weights, sizeof(float) * h->nerf_params,
                                        cudaMemcpyHostToDevice);
             if (e == cudaSuccess)
-                e = launch_pack_tc(tmp, h->d_nerf_tc + (size_t)k * h->nerf_tc_stride, kNerfIn, kNerfInPad,
+                e = launch_pack_pipe(tmp, h->d_nerf_tc + (size_t)k * h->nerf_tc_stride, kNerfIn, kNerfInPad,
                                    h->cfg.nerf_width, h->cfg.nerf_hidden, 3, h->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
             if (e != cudaSuccess) {
@@ -691,8 +690,7 @@ int nedf_compose_nedf_query(nedf_handle *h, int type, int n, const float *o, con
     if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
     if (n < 0) return fail(h, NEDF_ERR_ARG, "n < 0");
     if (h->cfg.precision == NEDF_PREC_BF16)
-        CK(h, launch_nedf_tc(make_ws(h), h->d_nedf_tc, h->nedf_tc_stride, 2, type, o, d, out, n, h->num_sms,
-                             h->stream));
+        CK(h, launch_nedf_pipe(make_ws(h), 2, type, o, d, out, n, h->num_sms, h->stream));
     else
         CK(h, launch_nedf_query_f32(make_ws(h), type, o, d, out, n, h->num_sms, h->stream));
     return NEDF_OK;
@@ -796,7 +794,7 @@ int nedf_compose_train_step(nedf_handle *h, int type, int batch, float lr, float
                             ts.adam_v, ts.step, lr));
     ts.cursor = (ts.cursor + batch) % ts.n_rays;
     if (h->d_nedf_tc)
-        CK(h, launch_pack_tc(ts.master, h->d_nedf_tc + (size_t)type * h->nedf_tc_stride, kNedfIn, kNedfInPad,
+        CK(h, launch_pack_pipe(ts.master, h->d_nedf_tc + (size_t)type * h->nedf_tc_stride, kNedfIn, kNedfInPad,
                              h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->stream));
     if (loss_host) {
         CK(h, cudaStreamSynchronize(h->stream));
@@ -868,7 +866,7 @@ int nedf_compose_load_state(nedf_handle *h, const void *buf, size_t size)
         TrainLaunch L = make_train_launch(h, k);
         CK(h, launch_refresh_weights(L));
         if (h->d_nedf_tc)
-            CK(h, launch_pack_tc(h->train[k].master, h->d_nedf_tc + (size_t)k * h->nedf_tc_stride, kNedfIn,
+            CK(h, launch_pack_pipe(h->train[k].master, h->d_nedf_tc + (size_t)k * h->nedf_tc_stride, kNedfIn,
                                  kNedfInPad, h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->stream));
     }
     CK(h, cudaStreamSynchronize(h->stream));

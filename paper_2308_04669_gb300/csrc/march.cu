@@ -262,10 +262,10 @@ cudaError_t launch_march_colour_frame(const FrameLaunch &L, void *scratch, long 
     if (early_stop) k_march_pairs<true><<<g * 2, 128, 0, st>>>(ws, mb, n_samples);
     else k_march_pairs<false><<<g * 2, 128, 0, st>>>(ws, mb, n_samples);
     const bool tc = ws.precision == 1 && ws.nerf_hidden > 0;
-    k_march_scan<<<1, 1, 0, st>>>(ws, mb, tc ? kTcTileRows : kTileRows);
+    k_march_scan<<<1, 1, 0, st>>>(ws, mb, tc ? kPipeTileRows : kTileRows);
     cudaError_t e = cudaSuccess;
     if (tc) {
-        e = launch_march_colour_tc(ws, mb, n_samples, L.num_sms, st);
+        e = launch_march_colour_pipe(ws, mb, n_samples, L.num_sms, st);
         if (e != cudaSuccess) return e;
     } else if (ws.nerf_hidden > 0) {
         switch (ws.nerf_width) {

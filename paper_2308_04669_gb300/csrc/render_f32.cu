@@ -493,8 +493,9 @@ cudaError_t launch_frame(FrameLaunch &L)
     // list scans must use the tile size of the kernel that consumes the list
     const bool tc_nedf = ws.precision == 1 && ws.depth_source == 0;
     const bool tc_shade = ws.precision == 1 && ws.nerf_hidden > 0;
-    const int nedf_rows = tc_nedf ? kTcTileRows : kTileRows;
-    const int shade_rows = tc_shade ? kTcTileRows : kTileRows;
+    const int nedf_rows = tc_nedf ? kPipeTileRows : kTileRows;
+    // the engine shades (128 / n_shade) pixels per 128-row half, two halves per tile
+    const int shade_ppt = tc_shade ? 2 * (kTcTileRows / L.n_shade) : kTileRows / L.n_shade;
     // external records: inside a captured graph they still mark the stage boundaries for timing
     auto mark = [&]() {
         if (L.events) cudaEventRecordWithFlags(L.events[stage], st, cudaEventRecordExternal);
@@ -508,7 +509,7 @@ cudaError_t launch_frame(FrameLaunch &L)
     k_scan_primary<<<1, 1, 0, st>>>(ws, nedf_rows);
     k_bin_primary<1><<<L.n_inst, kThreads, 0, st>>>(ws);
     mark();
-    cudaError_t e = tc_nedf ? launch_nedf_tc(ws, ws.nedf_tc, ws.nedf_tc_stride, 0, 0, nullptr, nullptr, nullptr, 0, gsm, st)
+    cudaError_t e = tc_nedf ? launch_nedf_pipe(ws, 0, 0, nullptr, nullptr, nullptr, 0, gsm, st)
                             : nedf_dispatch(ws, gsm * 4, 0, st);
     if (e != cudaSuccess) return e;
     int launches = 6;
@@ -518,18 +519,16 @@ cudaError_t launch_frame(FrameLaunch &L)
     }
     mark();
     k_resolve<<<gsm * 4, 256, 0, st>>>(ws, npix);
-    k_scan_shade<<<1, 1, 0, st>>>(ws, shade_rows / L.n_shade);
+    k_scan_shade<<<1, 1, 0, st>>>(ws, shade_ppt);
     mark();
-    e = tc_shade ? launch_shade_tc(ws, ws.nerf_tc, ws.nerf_tc_stride, npix, gsm, st)
-                 : shade_dispatch(ws, gsm * 4, npix, st);
+    e = tc_shade ? launch_shade_pipe(ws, npix, gsm, st) : shade_dispatch(ws, gsm * 4, npix, st);
     if (e != cudaSuccess) return e;
     mark();
     int nbin = 0;
     e = launch_shadow_binning(ws, npix, L.n_lights, L.n_inst, nedf_rows, gsm, st, &nbin);
     if (e != cudaSuccess) return e;
     mark();
-    e = tc_nedf ? launch_nedf_tc(ws, ws.nedf_tc, ws.nedf_tc_stride, 1, 0, nullptr, nullptr, nullptr, 0, gsm, st)
-                : nedf_dispatch(ws, gsm * 4, 1, st);
+    e = tc_nedf ? launch_nedf_pipe(ws, 1, 0, nullptr, nullptr, nullptr, 0, gsm, st) : nedf_dispatch(ws, gsm * 4, 1, st);
     if (e != cudaSuccess) return e;
     if (tc_nedf) {
         if ((e = launch_fallback(ws, 1, gsm, st)) != cudaSuccess) return e;

@@ -23,19 +23,18 @@ constexpr int kLightGridSize = 128;   // shadow-map camera grid (cells per side)
 
 cudaError_t launch_frame(FrameLaunch &L);
 
-// BF16 tensor-core path (render_tc.cu)
-size_t tc_blob_size(int K0, int N, int L, int n_out);
-cudaError_t launch_pack_tc(const float *master, void *blob, int K_in, int K0, int N, int L, int n_out,
-                           cudaStream_t st);
+// BF16 tensor-core engine (render_pipe.cu): tiles of 256 rows, weight chunks streamed per layer
+constexpr int kPipeTileRows = 256;
+size_t pipe_blob_size(int K0, int N, int L, int n_out);
+cudaError_t launch_pack_pipe(const float *master, void *blob, int K_in, int K0, int N, int L, int n_out,
+                             cudaStream_t st);
 // mode 0: Step-1 pairs, 1: Step-3 pairs, 2: n caller rays (o, d) of `type` -> out float4[n]
-cudaError_t launch_nedf_tc(const Workspace &ws, const void *blobs, size_t stride, int mode, int type,
-                           const float *o, const float *d, float *out, int n, int num_sms, cudaStream_t st);
-cudaError_t launch_shade_tc(const Workspace &ws, const void *blobs, size_t stride, int npix, int num_sms,
-                            cudaStream_t st);
+cudaError_t launch_nedf_pipe(const Workspace &ws, int mode, int type, const float *o, const float *d, float *out,
+                             int n, int num_sms, cudaStream_t st);
+cudaError_t launch_shade_pipe(const Workspace &ws, int npix, int num_sms, cudaStream_t st);
+cudaError_t launch_march_colour_pipe(const Workspace &ws, const MarchBuffers &mb, int n_samples, int num_sms,
+                                     cudaStream_t st);
 cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStream_t st);
-// plain-method colour rows on the tensor cores (march.cu builds the rows)
-cudaError_t launch_march_colour_tc(const Workspace &ws, const MarchBuffers &mb, int n_samples, int num_sms,
-                                   cudaStream_t st);
 
 // Step-3 binning through per-light shadow-map cameras (shadow_bin.cu)
 cudaError_t launch_shadow_binning(const Workspace &ws, int npix, int n_lights, int n_inst, int rows_per_tile,

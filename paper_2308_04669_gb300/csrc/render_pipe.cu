@@ -1,0 +1,659 @@
+// Warp-specialised tensor-core MLP engine for every render-time network (BF16, tcgen05/TMEM).
+//
+// Method: arXiv 2308.04669, Eq. 1-2 and 7 (NeDF queries of Steps 1 and 3), Eq. 8 with the sample
+// window (the radiance field of Step 2), and the plain method's colour frame (its NeRF at every
+// sample).
+//
+// A CTA works on tiles of 256 rows held as two 128-row halves X and Y.  Each hidden layer is two
+// tcgen05 MMAs per 16-column weight chunk (M = 128, N = width, K = 16), one per half, into two
+// TMEM accumulators (columns [0, N) and [N, 2N)), so every weight chunk fetched from L2 serves 256
+// rows.  Roles:
+//   warps 0-3   epilogue group X: row set-up of rows 0..127, layer epilogues (tcgen05.ld, bias,
+//               ReLU, BF16 A operand in shared memory), output layer and tail;
+//   warps 4-7   epilogue group Y: the same for rows 128..255 (TMEM lane quarter = warp % 4);
+//   warp 8      producer: streams the weight chunks of every layer of every tile, in MMA order,
+//               through a ring of shared-memory slots with bulk asynchronous copies;
+//   warp 9      MMA issuer (and TMEM owner).
+// The producer only waits for free slots, so while the epilogue warps work on layer l it is
+// already loading layer l+1.  Every wait is bounded: a timeout sets the status word and an abort
+// flag that ends every role's loop, and the teardown drains the kernel's own copies and MMAs
+// (again bounded) before TMEM is freed.
+#include "render_kernels.cuh"
+#include "render_launch.h"
+#include "tc_ptx.cuh"
+
+#include <algorithm>
+
+namespace nedf {
+
+using namespace tc;
+
+constexpr int kPipeRows = 256;              // rows per tile (two MMA halves of 128)
+constexpr int kHalf = 128;
+constexpr int kPipeThreads = 320;           // 8 epilogue warps, producer, MMA issuer
+constexpr int kKC = 16;                     // K columns per weight chunk (one MMA K step)
+
+enum PipeMode { kModeShade = 0, kModeMarch = 1, kModePrimary = 2, kModeShadow = 3, kModeQuery = 4 };
+
+// NERF: the colour network (90 inputs padded to 96, 3 outputs); otherwise the NeDF (78 -> 80, 2).
+template <int N, bool NERF>
+struct PipeShape {
+    static constexpr int K0 = NERF ? kNerfInPad : kNedfInPad;        // input width of layer 0
+    static constexpr int KA = K0 > N ? K0 : N;                       // A operand columns
+    static constexpr int CHUNK = N * kKC * 2;                        // bytes of one weight chunk
+    static constexpr int SLOTS = N == 256 ? 9 : (N == 128 ? 24 : 32);
+    static constexpr int NOUT = NERF ? 3 : 2;
+    static constexpr size_t A_BYTES = (size_t)kHalf * KA * 2;
+    static constexpr size_t FIXED = 2 * A_BYTES + (size_t)SLOTS * CHUNK;   // + the fp32 block (depends on L)
+};
+
+// ---- weight blobs: per layer, chunks of 16 input columns, each chunk N x 16 in the core-matrix
+// layout (SBO 256 bytes); then the fp32 block [bias L x N][w_out n_out x N (BF16 values)][b_out].
+__host__ __device__ inline size_t pipe_layer_off(int K0, int N, int l)
+{
+    return l == 0 ? 0 : (size_t)K0 * N * 2 + (size_t)(l - 1) * N * N * 2;
+}
+__host__ __device__ inline size_t pipe_w_bytes(int K0, int N, int L) { return pipe_layer_off(K0, N, L); }
+__host__ __device__ inline size_t pipe_f32_floats(int N, int L, int n_out)
+{
+    return ((size_t)L * N + (size_t)n_out * N + n_out + 3) & ~(size_t)3;
+}
+size_t pipe_blob_size(int K0, int N, int L, int n_out)
+{
+    size_t b = pipe_w_bytes(K0, N, L) + pipe_f32_floats(N, L, n_out) * 4;
+    return (b + 1023) & ~(size_t)1023;
+}
+
+// packed FP32 master (W[out][in] then b per layer) -> chunked BF16 blob; one thread per element
+__global__ void k_pack_pipe(const float *master, uint8_t *blob, int K_in, int K0, int N, int L, int n_out)
+{
+    const size_t wb = pipe_w_bytes(K0, N, L);
+    float *f32 = reinterpret_cast<float *>(blob + wb);
+    const long long total_w = (long long)N * K0 + (long long)(L - 1) * N * N;
+    const long long total = total_w + (long long)L * N + (long long)n_out * N + n_out;
+    const long long off_out = (long long)K_in * N + N + (long long)(L - 1) * (N * N + N);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        if (e < total_w) {
+            int l, K, Kin;
+            long long j, off_src;
+            if (e < (long long)N * K0) {
+                l = 0; j = e; K = K0; Kin = K_in; off_src = 0;
+            } else {
+                long long e2 = e - (long long)N * K0;
+                l = 1 + (int)(e2 / ((long long)N * N));
+                j = e2 - (long long)(l - 1) * N * N;
+                K = N; Kin = N;
+                off_src = (long long)K_in * N + N + (long long)(l - 1) * (N * N + N);
+            }
+            const int n = (int)(j / K), k = (int)(j - (long long)n * K);
+            const float v = k < Kin ? master[off_src + (long long)n * Kin + k] : 0.0f;
+            const size_t dst = pipe_layer_off(K0, N, l) + (size_t)(k / kKC) * N * kKC * 2 + cm_offset(n, k % kKC, kKC);
+            *reinterpret_cast<__nv_bfloat16 *>(blob + dst) = __float2bfloat16_rn(v);
+        } else {
+            const long long j = e - total_w;
+            if (j < (long long)L * N) {
+                const int l = (int)(j / N), n = (int)(j - (long long)l * N);
+                const long long off = l == 0 ? (long long)K_in * N
+                                             : (long long)K_in * N + N + (long long)(l - 1) * (N * N + N) + (long long)N * N;
+                f32[j] = master[off + n];
+            } else {
+                const long long q = j - (long long)L * N;
+                if (q < (long long)n_out * N) f32[j] = round_bf16(master[off_out + q]);
+                else f32[j] = master[off_out + (long long)n_out * N + (q - (long long)n_out * N)];
+            }
+        }
+    }
+}
+
+cudaError_t launch_pack_pipe(const float *master, void *blob, int K_in, int K0, int N, int L, int n_out, cudaStream_t st)
+{
+    const long long total = (long long)N * K0 + (long long)(L - 1) * N * N + (long long)L * N + (long long)n_out * N + n_out;
+    k_pack_pipe<<<(int)std::min<long long>((total + 255) / 256, 4096), 256, 0, st>>>(master, (uint8_t *)blob, K_in, K0, N,
+                                                                                     L, n_out);
+    return cudaGetLastError();
+}
+
+// ---- encodings into a BF16 A row (identity, sine blocks, cosine blocks; 2^k frequencies from the
+// double-angle identities applied to sincos(x)) ---------------------------------------------------
+template <int NIN, int F>
+__device__ __forceinline__ void pipe_encode(const float *x, float *out)
+{
+#pragma unroll
+    for (int c = 0; c < NIN; ++c) out[c] = x[c];
+#pragma unroll
+    for (int c = 0; c < NIN; ++c) {
+        float s, co;
+        sincosf(x[c], &s, &co);
+#pragma unroll
+        for (int k = 0; k < F; ++k) {
+            out[NIN + k * NIN + c] = s;
+            out[NIN + F * NIN + k * NIN + c] = co;
+            float s2 = 2.0f * s * co;
+            float c2 = (co - s) * (co + s);
+            s = s2;
+            co = c2;
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void pipe_store_row(uint8_t *A, int r, const float *f, int n_valid)
+{
+#pragma unroll
+    for (int c = 0; c < K / 8; ++c) {
+        uint32_t p[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = c * 8 + 2 * e;
+            p[e] = pack_bf16(k < n_valid ? f[k] : 0.0f, k + 1 < n_valid ? f[k + 1] : 0.0f);
+        }
+        *reinterpret_cast<uint4 *>(A + cm_offset(r, c * 8, K)) = make_uint4(p[0], p[1], p[2], p[3]);
+    }
+}
+
+struct PipeArgs {
+    const uint8_t *blobs;
+    size_t blob_stride;
+    int npix;
+    int n_samples;
+    int query_type;
+    const float *qo, *qd;
+    float4 *qout;
+    int qn;
+};
+
+struct PipeShared {
+    uint64_t a_ready, acc_full, fin;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ bool pipe_wait(uint64_t *bar, uint32_t parity, volatile int *abort, uint32_t *status)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!*abort) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > 1000000000ull) {
+            atomicOr(status, kStatusTimeout);
+            *abort = 1;
+            return false;
+        }
+    }
+    return false;
+}
+
+// Same wait without the abort shortcut: used by the teardown to drain in-flight work.
+__device__ __forceinline__ void pipe_drain(uint64_t *bar, uint32_t parity, uint32_t *status)
+{
+    mbar_wait(bar, parity, status, kStatusTimeout);
+}
+
+// OR of v over the 256 epilogue threads (named barrier 3); every one of them gets the result, so
+// both groups leave their loops at the same point.
+__device__ __forceinline__ bool epilogue_any(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 3, 256, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+template <int N, int MODE>
+__device__ __forceinline__ unsigned long long pipe_n_tiles(const Workspace &ws, const MarchBuffers &mb, const PipeArgs &a)
+{
+    const DevFrame &f = *ws.frame;
+    const Counters &C = *ws.cnt;
+    if (MODE == kModeQuery) return ((unsigned long long)a.qn + kPipeRows - 1) / kPipeRows;
+    if (MODE == kModeShade) return C.h_tile[f.n_types];
+    if (MODE == kModeMarch) return mb.row_tile[f.n_types];
+    if (MODE == kModePrimary) return C.p_tile[f.n_types];
+    return C.s_tile[f.n_types];
+}
+
+template <int MODE>
+__device__ __forceinline__ int pipe_tile_type(const Workspace &ws, const MarchBuffers &mb, const PipeArgs &a,
+                                              unsigned long long tile)
+{
+    if (MODE == kModeQuery) return a.query_type;
+    const DevFrame &f = *ws.frame;
+    const Counters &C = *ws.cnt;
+    const unsigned long long *off = MODE == kModeShade ? C.h_tile
+                                  : MODE == kModeMarch ? mb.row_tile
+                                  : MODE == kModePrimary ? C.p_tile : C.s_tile;
+    int t = 0;
+    while (t + 1 < f.n_types && off[t + 1] <= tile) ++t;
+    return t;
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuffers mb, PipeArgs a)
+{
+    constexpr bool NERF = MODE == kModeShade || MODE == kModeMarch;
+    using SH = PipeShape<N, NERF>;
+    constexpr int K0 = SH::K0, KA = SH::KA, S = SH::SLOTS, NOUT = SH::NOUT;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ PipeShared P;
+    __shared__ uint64_t w_full[S], w_empty[S];
+    // tail scratch of the two groups (shading composite; plain-method per-pair sums)
+    __shared__ float t_sig[kPipeRows], t_rgb[kPipeRows][3];
+    __shared__ uint32_t t_key[kPipeRows];
+    __shared__ float t_wd[kPipeRows];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = NERF ? ws.nerf_hidden : ws.nedf_hidden;
+    uint8_t *A[2] = {smem, smem + SH::A_BYTES};
+    uint8_t *ring = smem + 2 * SH::A_BYTES;
+    float *f32s = reinterpret_cast<float *>(smem + SH::FIXED);       // biases and output layer of one type
+    const int n_f32 = (int)pipe_f32_floats(N, NERF ? ws.nerf_hidden : ws.nedf_hidden, NOUT);
+    volatile int *abort = &P.abort;
+
+    if (warp == 9) tmem_alloc(&P.tmem_base, 2 * N);
+    if (threadIdx.x == 0) {
+        mbar_init(&P.a_ready, 2 * kHalf);
+        mbar_init(&P.acc_full, 1);
+        mbar_init(&P.fin, 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&w_full[s], 1);
+            mbar_init(&w_empty[s], 1);
+        }
+        P.abort = 0;
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = P.tmem_base;
+    const unsigned long long n_tiles = pipe_n_tiles<N, MODE>(ws, mb, a);
+    const DevFrame &f = *ws.frame;
+
+    if (warp == 8) {
+        // ------------------------------ producer ------------------------------------------------
+        if (lane == 0) {
+            unsigned long long q = 0;
+            for (unsigned long long tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x) {
+                const uint8_t *blob = a.blobs + (size_t)pipe_tile_type<MODE>(ws, mb, a, tile) * a.blob_stride;
+                for (int l = 0; l < L && !*abort; ++l) {
+                    const int K = l == 0 ? K0 : N;
+                    const uint8_t *src = blob + pipe_layer_off(K0, N, l);
+                    for (int c = 0; c < K / kKC; ++c, ++q) {
+                        const int s = (int)(q % S);
+                        const uint32_t round = (uint32_t)(q / S);
+                        if (!pipe_wait(&w_empty[s], (round & 1u) ^ 1u, abort, ws.status)) break;
+                        mbar_arrive_expect_tx(&w_full[s], SH::CHUNK);
+                        bulk_g2s(ring + (size_t)s * SH::CHUNK, src + (size_t)c * SH::CHUNK, SH::CHUNK, &w_full[s]);
+                    }
+                }
+            }
+            // drain: the last (up to S) copies may still be landing
+            const unsigned long long q0 = q > (unsigned long long)S ? q - S : 0;
+            for (unsigned long long k = q0; k < q; ++k) pipe_drain(&w_full[k % S], (uint32_t)((k / S) & 1u), ws.status);
+        }
+    } else if (warp == 9) {
+        // ------------------------------ MMA issuer ----------------------------------------------
+        if (lane == 0) {
+            unsigned long long q = 0, ja = 0;
+            const uint32_t idesc = idesc_bf16(128, N);
+            bool issued_any = false;
+            for (unsigned long long tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x) {
+                for (int l = 0; l < L && !*abort; ++l, ++ja) {
+                    const int K = l == 0 ? K0 : N;
+                    if (!pipe_wait(&P.a_ready, (uint32_t)(ja & 1u), abort, ws.status)) break;
+                    tc_fence_after();
+                    const uint32_t sbo_a = (uint32_t)(K / 8) * 128;
+                    const uint32_t ax = smem_addr(A[0]), ay = smem_addr(A[1]);
+                    for (int c = 0; c < K / kKC; ++c, ++q) {
+                        const int s = (int)(q % S);
+                        if (!pipe_wait(&w_full[s], (uint32_t)((q / S) & 1u), abort, ws.status)) break;
+                        tc_fence_after();
+                        const uint64_t bdesc = smem_desc(smem_addr(ring + (size_t)s * SH::CHUNK), 128, 256);
+                        mma_bf16(tmem, smem_desc(ax + c * 256, 128, sbo_a), bdesc, idesc, c > 0 ? 1u : 0u);
+                        mma_bf16(tmem + N, smem_desc(ay + c * 256, 128, sbo_a), bdesc, idesc, c > 0 ? 1u : 0u);
+                        mma_commit(&w_empty[s]);      // the slot is free once both MMAs have read it
+                        issued_any = true;
+                    }
+                    mma_commit(&P.acc_full);
+                }
+            }
+            if (issued_any) {                         // everything issued has completed before TMEM goes
+                mma_commit(&P.fin);
+                pipe_drain(&P.fin, 0u, ws.status);
+            }
+        }
+    } else {
+        // ------------------------------ epilogue groups -----------------------------------------
+        const int g = warp >> 2;                      // 0: rows 0..127 (X), 1: rows 128..255 (Y)
+        const int r = threadIdx.x & 127;              // row within the half
+        const int R = g * kHalf + r;                  // row within the tile
+        const uint32_t tmem_row = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(g * N);
+        uint8_t *Ag = A[g];
+        unsigned long long jb = 0;
+        const int ns = f.n_shade;
+        int f32_type = -1;
+        const float *f32 = f32s;
+        for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            if (epilogue_any(*abort != 0)) break;
+            const int t = pipe_tile_type<MODE>(ws, mb, a, tile);
+            const DevType T = ws.types[t];
+            if (t != f32_type) {
+                // both groups are past every read of the previous type's block before it is replaced
+                asm volatile("bar.sync 3, 256;" ::: "memory");
+                const float4 *src = reinterpret_cast<const float4 *>(a.blobs + (size_t)t * a.blob_stride +
+                                                                     pipe_w_bytes(K0, N, L));
+                for (int i = threadIdx.x; i < n_f32 / 4; i += 2 * kHalf)
+                    reinterpret_cast<float4 *>(f32s)[i] = src[i];
+                asm volatile("bar.sync 3, 256;" ::: "memory");
+                f32_type = t;
+            }
+            // ---- row set-up ---------------------------------------------------------------------
+            float x6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            PairRay pr;
+            pr.kept = false;
+            bool valid = false;
+            unsigned long long idx = 0;
+            float sig = 0.f;                          // shade: density; march: sample weight
+            if (MODE == kModeShade) {
+                const int ppg = kHalf / ns;           // pixels per half
+                const unsigned long long first = (tile - ws.cnt->h_tile[t]) * (unsigned long long)(2 * ppg) + g * ppg;
+                const unsigned long long cnt = ws.cnt->h_count[t];
+                const int q = r / ns, j = r - q * ns;
+                valid = q < ppg && first + q < cnt;
+                if (valid) {
+                    const uint32_t p = ws.hlist[(size_t)t * a.npix + first + q];
+                    const DevInst I = ws.inst[ws.id[p]];
+                    V3 o, d, ol, dl;
+                    camera_ray(f, p % f.W, p / f.W, o, d);
+                    to_local(I, o, d, ol, dl);
+                    const float Dl = ws.depth[p] / I.s;
+                    const float delta = 2.0f * f.shade_half / ns;
+                    const V3 x = madd(ol, Dl - f.shade_half + (j + 0.5f) * delta, dl);
+                    x6[0] = x.x; x6[1] = x.y; x6[2] = x.z; x6[3] = dl.x; x6[4] = dl.y; x6[5] = dl.z;
+                    sig = density(T, x, f.sigma_max, f.sdf_width);
+                    if (j == 0) { t_key[g * kHalf + q] = p; t_wd[g * kHalf + q] = I.s * delta; }
+                }
+            } else if (MODE == kModeMarch) {
+                const unsigned long long end = min(mb.row_cursor[t], mb.row_off[t + 1]);
+                idx = mb.row_off[t] + (tile - mb.row_tile[t]) * kPipeRows + R;
+                valid = idx < end;
+                uint32_t pair = 0xFFFFFFFFu;
+                if (valid) {
+                    const uint2 row = mb.rows[idx];
+                    const uint2 pp = ws.ppairs[row.x];
+                    const DevInst I = ws.inst[pp.y];
+                    V3 o, d, ol, dl;
+                    camera_ray(f, pp.x % f.W, pp.x / f.W, o, d);
+                    to_local(I, o, d, ol, dl);
+                    Chord ch;
+                    bound_chord(ol, dl, T.rb, ch);
+                    const float dt = (ch.tx - ch.te) / a.n_samples;
+                    float Tr = mb.T_first[row.x];
+                    for (int jj = mb.k_first[row.x]; jj < (int)row.y; ++jj)
+                        Tr *= expf(-density(T, madd(ol, ch.te + (jj + 0.5f) * dt, dl), f.sigma_max, f.sdf_width) * I.s * dt);
+                    const V3 x = madd(ol, ch.te + (row.y + 0.5f) * dt, dl);
+                    x6[0] = x.x; x6[1] = x.y; x6[2] = x.z; x6[3] = dl.x; x6[4] = dl.y; x6[5] = dl.z;
+                    sig = Tr * (1.0f - expf(-density(T, x, f.sigma_max, f.sdf_width) * I.s * dt));
+                    pair = row.x;
+                }
+                t_key[R] = pair;
+            } else {
+                if (MODE == kModeQuery) {
+                    idx = tile * kPipeRows + R;
+                    valid = idx < (unsigned long long)a.qn;
+                    if (valid) {
+                        pr.ol = v3(a.qo[3 * idx], a.qo[3 * idx + 1], a.qo[3 * idx + 2]);
+                        pr.dl = normalized(v3(a.qd[3 * idx], a.qd[3 * idx + 1], a.qd[3 * idx + 2]));
+                        Chord ch;
+                        pr.kept = bound_chord(pr.ol, pr.dl, T.rb, ch);
+                        pr.te = ch.te; pr.tx = ch.tx; pr.tp = ch.tp;
+                    }
+                } else {
+                    const Counters &C = *ws.cnt;
+                    const unsigned long long *toff = MODE == kModePrimary ? C.p_tile : C.s_tile;
+                    const unsigned long long *poff = MODE == kModePrimary ? C.p_off : C.s_off;
+                    idx = poff[t] + (tile - toff[t]) * kPipeRows + R;
+                    valid = idx < poff[t + 1];
+                    if (valid)
+                        setup_pair_ray(ws, f, MODE == kModeShadow, (MODE == kModePrimary ? ws.ppairs : ws.spairs)[idx], T.rb, pr);
+                }
+                if (valid && pr.kept) {
+                    const V3 pe = madd(pr.ol, pr.te, pr.dl);
+                    x6[0] = pe.x; x6[1] = pe.y; x6[2] = pe.z; x6[3] = pr.dl.x; x6[4] = pr.dl.y; x6[5] = pr.dl.z;
+                }
+            }
+            {
+                float feat[K0];
+                if (NERF) {
+                    pipe_encode<3, 10>(x6, feat);
+                    pipe_encode<3, 4>(x6 + 3, feat + 63);
+                    pipe_store_row<K0>(Ag, r, feat, kNerfIn);
+                } else {
+                    pipe_encode<6, 6>(x6, feat);
+                    pipe_store_row<K0>(Ag, r, feat, kNedfIn);
+                }
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            mbar_arrive(&P.a_ready);
+            // ---- layers -------------------------------------------------------------------------
+            float out[NOUT];
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) out[o] = f32[L * N + NOUT * N + o];
+            bool ok = true;
+            for (int l = 0; l < L; ++l, ++jb) {
+                // a warp-uniform outcome: the tcgen05.ld below is warp-collective
+                ok = __all_sync(0xffffffffu, pipe_wait(&P.acc_full, (uint32_t)(jb & 1u), abort, ws.status));
+                if (!ok) {
+                    *abort = 1;
+                    break;
+                }
+                tc_fence_after();
+                const float *bias = f32 + l * N;
+                if (l + 1 < L) {
+#pragma unroll 1
+                    for (int c0 = 0; c0 < N; c0 += 32) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem_row + c0, v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int qq = 0; qq < 4; ++qq) {
+                            uint32_t p[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int jj = qq * 8 + 2 * e;
+                                p[e] = pack_bf16(fmaxf(__uint_as_float(v[jj]) + bias[c0 + jj], 0.0f),
+                                                 fmaxf(__uint_as_float(v[jj + 1]) + bias[c0 + jj + 1], 0.0f));
+                            }
+                            *reinterpret_cast<uint4 *>(Ag + cm_offset(r, c0 + qq * 8, N)) = make_uint4(p[0], p[1], p[2], p[3]);
+                        }
+                    }
+                    fence_proxy_async_smem();
+                    tc_fence_before();
+                    mbar_arrive(&P.a_ready);
+                } else {
+                    const float *wout = f32 + L * N;
+#pragma unroll 1
+                    for (int c0 = 0; c0 < N; c0 += 32) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem_row + c0, v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            const float h = round_bf16(fmaxf(__uint_as_float(v[jj]) + bias[c0 + jj], 0.0f));
+#pragma unroll
+                            for (int o = 0; o < NOUT; ++o) out[o] = fmaf(h, wout[o * N + c0 + jj], out[o]);
+                        }
+                    }
+                    tc_fence_before();
+                }
+            }
+            // one outcome for both groups: the tails use named barriers and ballots
+            if (epilogue_any(!ok || *abort)) break;
+            // ---- tail ---------------------------------------------------------------------------
+            if (MODE == kModeShade || MODE == kModeMarch) {
+                const float wr = MODE == kModeShade ? 1.0f : sig;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) t_rgb[R][c] = wr / (1.0f + expf(-out[c]));
+                t_sig[R] = sig;
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kHalf) : "memory");
+                if (MODE == kModeShade) {
+                    const int ppg = kHalf / ns;
+                    const unsigned long long first = (tile - ws.cnt->h_tile[t]) * (unsigned long long)(2 * ppg) + g * ppg;
+                    if (r < ppg && first + r < ws.cnt->h_count[t]) {
+                        float Tr = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, Aa = 0.f;
+                        const float wd = t_wd[g * kHalf + r];
+                        for (int k = 0; k < ns; ++k) {
+                            const int rr = g * kHalf + r * ns + k;
+                            const float alpha = 1.0f - expf(-t_sig[rr] * wd);
+                            const float w = Tr * alpha;
+                            cr += w * t_rgb[rr][0]; cg += w * t_rgb[rr][1]; cb += w * t_rgb[rr][2]; Aa += w;
+                            Tr *= 1.0f - alpha;
+                        }
+                        ws.rgba[t_key[g * kHalf + r]] = make_float4(cr, cg, cb, Aa);
+                    }
+                } else {
+                    // one sum per run of rows of the same pair (runs are contiguous within a half)
+                    const uint32_t pair = t_key[R];
+                    if (pair != 0xFFFFFFFFu && (r == 0 || t_key[R - 1] != pair)) {
+                        float sa = 0.f, sb = 0.f, sc = 0.f;
+                        for (int k = R; k < (g + 1) * kHalf && t_key[k] == pair; ++k) {
+                            sa += t_rgb[k][0]; sb += t_rgb[k][1]; sc += t_rgb[k][2];
+                        }
+                        atomicAdd(&mb.C[pair].x, sa);
+                        atomicAdd(&mb.C[pair].y, sb);
+                        atomicAdd(&mb.C[pair].z, sc);
+                    }
+                }
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kHalf) : "memory");
+            } else if (MODE == kModeQuery) {
+                if (valid) {
+                    float4 res = make_float4(0.f, 0.f, __int_as_float(0x7f800000), 0.f);
+                    if (pr.kept) {
+                        const float Dl = pr.tp - T.rb * out[0];
+                        res = make_float4(out[0], out[1], Dl, (out[1] > 0.f && Dl > 0.f) ? 1.f : 0.f);
+                    }
+                    a.qout[idx] = res;
+                }
+            } else {
+                bool defer = false;
+                if (valid) {
+                    float Dl;
+                    bool hit;
+                    defer = nedf_decode(f, T, pr.ol, pr.dl, pr.tp, out[0], out[1], Dl, hit);
+                    if (!defer && hit) apply_hit(ws, f, MODE == kModeShadow, pr, Dl);
+                }
+                const int mode = MODE == kModeShadow ? 1 : 0;
+                const unsigned m = __ballot_sync(0xffffffffu, defer);
+                if (m) {
+                    const int leader = __ffs(m) - 1;
+                    unsigned long long start = 0;
+                    if (lane == leader) start = atomicAdd(&ws.cnt->fb_count[mode], (unsigned long long)__popc(m));
+                    start = __shfl_sync(0xffffffffu, start, leader);
+                    if (defer) ws.fb_list[mode][start + __popc(m & ((1u << lane) - 1u))] = (uint32_t)idx;
+                }
+            }
+        }
+    }
+    // ---- teardown ------------------------------------------------------------------------------
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 9) tmem_dealloc(tmem, 2 * N);
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Deferred plain-method pairs (low confidence or outliers), one thread per pair
+// ---------------------------------------------------------------------------------------------------
+__global__ void k_fallback(Workspace ws, int mode)
+{
+    const DevFrame &f = *ws.frame;
+    const unsigned long long n = ws.cnt->fb_count[mode];
+    const uint2 *pairs = mode == 1 ? ws.spairs : ws.ppairs;
+    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < n;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint2 pr = pairs[ws.fb_list[mode][e]];
+        const DevType T = ws.types[ws.inst[pr.y].type];
+        PairRay R;
+        setup_pair_ray(ws, f, mode == 1, pr, T.rb, R);
+        bool hit = false;
+        const float Dl = march_crossing(T, R.ol, R.dl, R.te, R.tx, f.march_steps, f.march_bisect, hit);
+        if (hit) apply_hit(ws, f, mode == 1, R, Dl);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ws.cnt->fallback, n);
+}
+
+cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStream_t st)
+{
+    k_fallback<<<num_sms * 8, 128, 0, st>>>(ws, mode);
+    return cudaGetLastError();
+}
+
+template <int N, int MODE>
+static cudaError_t launch_pipe_n(const Workspace &ws, const MarchBuffers &mb, const PipeArgs &a, int grid, cudaStream_t st)
+{
+    constexpr bool NERF = MODE == kModeShade || MODE == kModeMarch;
+    const int L = NERF ? ws.nerf_hidden : ws.nedf_hidden;
+    const size_t sm = PipeShape<N, NERF>::FIXED + ((pipe_f32_floats(N, L, NERF ? 3 : 2) * 4 + 1023) & ~(size_t)1023);
+    if (sm > 227 * 1024 - 8192) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(k_pipe<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_pipe<N, MODE><<<grid, kPipeThreads, sm, st>>>(ws, mb, a);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_pipe(const Workspace &ws, const MarchBuffers &mb, const PipeArgs &a, int width, int grid,
+                               cudaStream_t st)
+{
+    if (grid < 1) return cudaSuccess;
+    switch (width) {
+    case 64: return launch_pipe_n<64, MODE>(ws, mb, a, grid, st);
+    case 128: return launch_pipe_n<128, MODE>(ws, mb, a, grid, st);
+    case 256: return launch_pipe_n<256, MODE>(ws, mb, a, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_nedf_pipe(const Workspace &ws, int mode, int type, const float *o, const float *d, float *out, int n,
+                             int num_sms, cudaStream_t st)
+{
+    PipeArgs a{};
+    a.blobs = ws.nedf_tc;
+    a.blob_stride = ws.nedf_tc_stride;
+    a.query_type = type;
+    a.qo = o;
+    a.qd = d;
+    a.qout = reinterpret_cast<float4 *>(out);
+    a.qn = n;
+    MarchBuffers none{};
+    if (mode == 0) return launch_pipe<kModePrimary>(ws, none, a, ws.nedf_width, num_sms, st);
+    if (mode == 1) return launch_pipe<kModeShadow>(ws, none, a, ws.nedf_width, num_sms, st);
+    const int grid = (int)std::min<long long>(num_sms, ((long long)n + kPipeRows - 1) / kPipeRows);
+    return launch_pipe<kModeQuery>(ws, none, a, ws.nedf_width, grid, st);
+}
+
+cudaError_t launch_shade_pipe(const Workspace &ws, int npix, int num_sms, cudaStream_t st)
+{
+    PipeArgs a{};
+    a.blobs = ws.nerf_tc;
+    a.blob_stride = ws.nerf_tc_stride;
+    a.npix = npix;
+    MarchBuffers none{};
+    return launch_pipe<kModeShade>(ws, none, a, ws.nerf_width, num_sms, st);
+}
+
+cudaError_t launch_march_colour_pipe(const Workspace &ws, const MarchBuffers &mb, int n_samples, int num_sms, cudaStream_t st)
+{
+    PipeArgs a{};
+    a.blobs = ws.nerf_tc;
+    a.blob_stride = ws.nerf_tc_stride;
+    a.n_samples = n_samples;
+    return launch_pipe<kModeMarch>(ws, mb, a, ws.nerf_width, num_sms, st);
+}
+
+}  // namespace nedf
