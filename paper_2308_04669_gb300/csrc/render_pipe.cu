@@ -455,21 +455,27 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                 tc_fence_after();
                 const float *bias = f32 + l * N;
                 if (l + 1 < L) {
+                    // 64 accumulator columns per TMEM wait: two loads in flight, then bias, ReLU, BF16
 #pragma unroll 1
-                    for (int c0 = 0; c0 < N; c0 += 32) {
-                        uint32_t v[32];
-                        tmem_ld32(tmem_row + c0, v);
+                    for (int c0 = 0; c0 < N; c0 += 64) {
+                        uint32_t v[2][32];
+                        tmem_ld32(tmem_row + c0, v[0]);
+                        tmem_ld32(tmem_row + c0 + 32, v[1]);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int qq = 0; qq < 4; ++qq) {
-                            uint32_t p[4];
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const float4 *b4 = reinterpret_cast<const float4 *>(bias + c0 + 32 * hh);
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int jj = qq * 8 + 2 * e;
-                                p[e] = pack_bf16(fmaxf(__uint_as_float(v[jj]) + bias[c0 + jj], 0.0f),
-                                                 fmaxf(__uint_as_float(v[jj + 1]) + bias[c0 + jj + 1], 0.0f));
+                            for (int qq = 0; qq < 4; ++qq) {
+                                const float4 ba = b4[2 * qq], bb = b4[2 * qq + 1];
+                                const uint32_t *u = v[hh] + 8 * qq;
+                                uint4 pk;
+                                pk.x = pack_bf16(fmaxf(__uint_as_float(u[0]) + ba.x, 0.0f), fmaxf(__uint_as_float(u[1]) + ba.y, 0.0f));
+                                pk.y = pack_bf16(fmaxf(__uint_as_float(u[2]) + ba.z, 0.0f), fmaxf(__uint_as_float(u[3]) + ba.w, 0.0f));
+                                pk.z = pack_bf16(fmaxf(__uint_as_float(u[4]) + bb.x, 0.0f), fmaxf(__uint_as_float(u[5]) + bb.y, 0.0f));
+                                pk.w = pack_bf16(fmaxf(__uint_as_float(u[6]) + bb.z, 0.0f), fmaxf(__uint_as_float(u[7]) + bb.w, 0.0f));
+                                *reinterpret_cast<uint4 *>(Ag + cm_offset(r, c0 + 32 * hh + 8 * qq, N)) = pk;
                             }
-                            *reinterpret_cast<uint4 *>(Ag + cm_offset(r, c0 + qq * 8, N)) = make_uint4(p[0], p[1], p[2], p[3]);
                         }
                     }
                     fence_proxy_async_smem();
@@ -478,16 +484,20 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                 } else {
                     const float *wout = f32 + L * N;
 #pragma unroll 1
-                    for (int c0 = 0; c0 < N; c0 += 32) {
-                        uint32_t v[32];
-                        tmem_ld32(tmem_row + c0, v);
+                    for (int c0 = 0; c0 < N; c0 += 64) {
+                        uint32_t v[2][32];
+                        tmem_ld32(tmem_row + c0, v[0]);
+                        tmem_ld32(tmem_row + c0 + 32, v[1]);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) {
-                            const float h = round_bf16(fmaxf(__uint_as_float(v[jj]) + bias[c0 + jj], 0.0f));
+                        for (int hh = 0; hh < 2; ++hh)
 #pragma unroll
-                            for (int o = 0; o < NOUT; ++o) out[o] = fmaf(h, wout[o * N + c0 + jj], out[o]);
-                        }
+                            for (int jj = 0; jj < 32; ++jj) {
+                                const int c = c0 + 32 * hh + jj;
+                                const float h = round_bf16(fmaxf(__uint_as_float(v[hh][jj]) + bias[c], 0.0f));
+#pragma unroll
+                                for (int o = 0; o < NOUT; ++o) out[o] = fmaf(h, wout[o * N + c], out[o]);
+                            }
                     }
                     tc_fence_before();
                 }
