@@ -82,3 +82,60 @@ def test_training_reduces_loss_and_state_round_trip(lib):
     r.load_state(blob)
     assert np.array_equal(w0, r.get_nedf_weights(0, w0.shape[0]))
     r.close()
+
+
+def _depth_frame(r, sc, **opts):
+    import torch
+    o = r.get_options()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    r.set_options(o)
+    n = sc.W * sc.H
+    depth = torch.empty(n, device="cuda")
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = r.render(r.camera(sc.eye, sc.target, sc.fov_deg), r.lights(sc.lights), depth, ids, None, None, None,
+                  stats=True)
+    torch.cuda.synchronize()
+    return depth.cpu().numpy().astype(np.float64), ids.cpu().numpy(), st
+
+
+def _against_judge(frame, judge):
+    """Hit agreement, id agreement and depth error (in bound radii; every instance has s r_b = 1)."""
+    d, i, _ = frame
+    jd, ji, _ = judge
+    hit, jhit = i != -1, ji != -1
+    same = hit & jhit & (i == ji)
+    err = np.abs(d - jd)[same]
+    return dict(hit_agree=float((hit == jhit).mean()), id_agree=float((i == ji).mean()),
+                mean_err=float(err.mean()), median_err=float(np.median(err)), p99_err=float(np.quantile(err, 0.99)))
+
+
+def test_training_gain_over_untrained_network(lib):
+    """What the learned part buys: the bare NeDF against a fine ray-march judge, before and after
+    training each type on ray-march labels, and how many queries the confidence test hands to the
+    plain method (sections "Neural Depth Fields (NeDF)" and "Fast NeRF Composition with NeDF")."""
+    sc = sg.three_types_scene(256, 256, nerf=False)
+    r = lib.renderer_for(sc)
+    judge = _depth_frame(r, sc, depth_source=1, march_steps=1024, march_bisect=24, fallback_conf=0.0,
+                         refine_steps=0, outlier_resample=0)
+    bare = dict(depth_source=0, fallback_conf=0.0, refine_steps=0, outlier_resample=0)
+    full = dict(depth_source=0, fallback_conf=0.9, refine_steps=4, outlier_resample=1)
+    before = _against_judge(_depth_frame(r, sc, **bare), judge)
+    fb_before = _depth_frame(r, sc, **full)[2].fallback_pairs
+    for t in range(len(sc.types)):
+        r.make_labels(t, 1 << 18, 2 + t, 256, 8)
+        for _ in range(600):
+            r.train_step(t, 8192, 1e-3)
+    after = _against_judge(_depth_frame(r, sc, **bare), judge)
+    fr = _depth_frame(r, sc, **full)
+    with_checks = _against_judge(fr, judge)
+    fb_after = fr[2].fallback_pairs
+    primary = fr[2].primary_pairs
+    print(f"\nbefore {before}\nafter {after}\nwith fallback+refine {with_checks}\n"
+          f"fallback pairs {fb_before} -> {fb_after} of {primary}")
+    assert after["hit_agree"] > 0.97 and after["hit_agree"] > before["hit_agree"] + 0.1
+    assert after["median_err"] < 0.2 * before["median_err"]
+    assert after["median_err"] < 0.02
+    assert fb_after < 0.5 * fb_before
+    assert with_checks["id_agree"] > 0.99 and with_checks["median_err"] < 0.01
+    r.close()
