@@ -12,7 +12,8 @@
 //               ReLU, BF16 A operand in shared memory), output layer and tail;
 //   warps 4-7   epilogue group Y: the same for rows 128..255 (TMEM lane quarter = warp % 4);
 //   warp 8      producer: streams the weight chunks of every layer of every tile, in MMA order,
-//               through a ring of shared-memory slots with bulk asynchronous copies;
+//               through a ring of shared-memory stages (up to 16 KB, one bulk asynchronous copy
+//               each: a copy costs its issuing thread a few hundred cycles whatever its size);
 //   warp 9      MMA issuer (and TMEM owner).
 // The producer only waits for free slots, so while the epilogue warps work on layer l it is
 // already loading layer l+1.  Every wait is bounded: a timeout sets the status word and an abort
@@ -32,6 +33,7 @@ constexpr int kPipeRows = 256;              // rows per tile (two MMA halves of 
 constexpr int kHalf = 128;
 constexpr int kPipeThreads = 320;           // 8 epilogue warps, producer, MMA issuer
 constexpr int kKC = 16;                     // K columns per weight chunk (one MMA K step)
+constexpr int kStageBytes = 16384;          // weight bytes per bulk copy
 
 enum PipeMode { kModeShade = 0, kModeMarch = 1, kModePrimary = 2, kModeShadow = 3, kModeQuery = 4 };
 
@@ -39,24 +41,33 @@ enum PipeMode { kModeShade = 0, kModeMarch = 1, kModePrimary = 2, kModeShadow = 
 template <int N, bool NERF>
 struct PipeShape {
     static constexpr int K0 = NERF ? kNerfInPad : kNedfInPad;        // input width of layer 0
-    static constexpr int KA = K0 > N ? K0 : N;                       // A operand columns
+    // The bias of every layer is folded into its MMAs: two constant-one input columns times the
+    // bias split into BF16 high and low parts.  Layer 0 has them inside its input padding; hidden
+    // layers read them from a 16-column block at ONES, after every column a layer writes.
+    static constexpr int ONES = K0 > N ? K0 : N;
+    static constexpr int KA = ONES + kKC;                            // A operand columns
     static constexpr int CHUNK = N * kKC * 2;                        // bytes of one weight chunk
-    static constexpr int SLOTS = N == 256 ? 9 : (N == 128 ? 24 : 32);
+    static constexpr int GC = kStageBytes / CHUNK;                   // chunks per stage
+    static constexpr int STAGE = GC * CHUNK;
+    static constexpr int SLOTS = N == 128 ? 6 : 4;                   // ring stages
     static constexpr int NOUT = NERF ? 3 : 2;
     static constexpr size_t A_BYTES = (size_t)kHalf * KA * 2;
-    static constexpr size_t FIXED = 2 * A_BYTES + (size_t)SLOTS * CHUNK;   // + the fp32 block (depends on L)
+    static constexpr size_t FIXED = 2 * A_BYTES + (size_t)SLOTS * STAGE;   // + the fp32 block (depends on L)
 };
 
 // ---- weight blobs: per layer, chunks of 16 input columns, each chunk N x 16 in the core-matrix
-// layout (SBO 256 bytes); then the fp32 block [bias L x N][w_out n_out x N (BF16 values)][b_out].
+// layout (SBO 256 bytes).  Layer 0 has K0 / 16 chunks with the bias in input columns K_in, K_in + 1
+// (high and low BF16 parts); a hidden layer has N / 16 chunks plus one bias chunk (columns 0, 1).
+// Then the fp32 block [w_out n_out x N (BF16 values)][b_out].
 __host__ __device__ inline size_t pipe_layer_off(int K0, int N, int l)
 {
-    return l == 0 ? 0 : (size_t)K0 * N * 2 + (size_t)(l - 1) * N * N * 2;
+    return l == 0 ? 0 : (size_t)K0 * N * 2 + (size_t)(l - 1) * (N + kKC) * N * 2;
 }
 __host__ __device__ inline size_t pipe_w_bytes(int K0, int N, int L) { return pipe_layer_off(K0, N, L); }
 __host__ __device__ inline size_t pipe_f32_floats(int N, int L, int n_out)
 {
-    return ((size_t)L * N + (size_t)n_out * N + n_out + 3) & ~(size_t)3;
+    (void)L;
+    return ((size_t)n_out * N + n_out + 3) & ~(size_t)3;
 }
 size_t pipe_blob_size(int K0, int N, int L, int n_out)
 {
@@ -69,45 +80,45 @@ __global__ void k_pack_pipe(const float *master, uint8_t *blob, int K_in, int K0
 {
     const size_t wb = pipe_w_bytes(K0, N, L);
     float *f32 = reinterpret_cast<float *>(blob + wb);
-    const long long total_w = (long long)N * K0 + (long long)(L - 1) * N * N;
-    const long long total = total_w + (long long)L * N + (long long)n_out * N + n_out;
+    const long long KH = N + kKC;
+    const long long total_w = (long long)N * K0 + (long long)(L - 1) * N * KH;
+    const long long total = total_w + (long long)n_out * N + n_out;
     const long long off_out = (long long)K_in * N + N + (long long)(L - 1) * (N * N + N);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         if (e < total_w) {
             int l, K, Kin;
-            long long j, off_src;
+            long long j, off_w;
             if (e < (long long)N * K0) {
-                l = 0; j = e; K = K0; Kin = K_in; off_src = 0;
+                l = 0; j = e; K = K0; Kin = K_in; off_w = 0;
             } else {
-                long long e2 = e - (long long)N * K0;
-                l = 1 + (int)(e2 / ((long long)N * N));
-                j = e2 - (long long)(l - 1) * N * N;
-                K = N; Kin = N;
-                off_src = (long long)K_in * N + N + (long long)(l - 1) * (N * N + N);
+                const long long e2 = e - (long long)N * K0;
+                l = 1 + (int)(e2 / ((long long)N * KH));
+                j = e2 - (long long)(l - 1) * N * KH;
+                K = (int)KH; Kin = N;
+                off_w = (long long)K_in * N + N + (long long)(l - 1) * (N * N + N);
             }
             const int n = (int)(j / K), k = (int)(j - (long long)n * K);
-            const float v = k < Kin ? master[off_src + (long long)n * Kin + k] : 0.0f;
+            float v = 0.0f;
+            if (k < Kin) {
+                v = master[off_w + (long long)n * Kin + k];
+            } else if (k < Kin + 2) {
+                const float b = master[off_w + (long long)N * Kin + n];
+                const float hi = round_bf16(b);
+                v = k == Kin ? hi : b - hi;
+            }
             const size_t dst = pipe_layer_off(K0, N, l) + (size_t)(k / kKC) * N * kKC * 2 + cm_offset(n, k % kKC, kKC);
             *reinterpret_cast<__nv_bfloat16 *>(blob + dst) = __float2bfloat16_rn(v);
         } else {
-            const long long j = e - total_w;
-            if (j < (long long)L * N) {
-                const int l = (int)(j / N), n = (int)(j - (long long)l * N);
-                const long long off = l == 0 ? (long long)K_in * N
-                                             : (long long)K_in * N + N + (long long)(l - 1) * (N * N + N) + (long long)N * N;
-                f32[j] = master[off + n];
-            } else {
-                const long long q = j - (long long)L * N;
-                if (q < (long long)n_out * N) f32[j] = round_bf16(master[off_out + q]);
-                else f32[j] = master[off_out + (long long)n_out * N + (q - (long long)n_out * N)];
-            }
+            const long long q = e - total_w;
+            if (q < (long long)n_out * N) f32[q] = round_bf16(master[off_out + q]);
+            else f32[q] = master[off_out + (long long)n_out * N + (q - (long long)n_out * N)];
         }
     }
 }
 
 cudaError_t launch_pack_pipe(const float *master, void *blob, int K_in, int K0, int N, int L, int n_out, cudaStream_t st)
 {
-    const long long total = (long long)N * K0 + (long long)(L - 1) * N * N + (long long)L * N + (long long)n_out * N + n_out;
+    const long long total = (long long)N * K0 + (long long)(L - 1) * N * (N + kKC) + (long long)n_out * N + n_out;
     k_pack_pipe<<<(int)std::min<long long>((total + 255) / 256, 4096), 256, 0, st>>>(master, (uint8_t *)blob, K_in, K0, N,
                                                                                      L, n_out);
     return cudaGetLastError();
@@ -136,6 +147,15 @@ __device__ __forceinline__ void pipe_encode(const float *x, float *out)
     }
 }
 
+// A operand of one 128-row half, K-major without swizzle, with the 8-row groups of one 8-column
+// slice adjacent: element (r, k) at (k / 8) * 2048 + (r / 8) * 128 + (r % 8) * 16 + (k % 8) * 2
+// (leading byte offset 2048 to the next 8 columns, stride byte offset 128 to the next 8 rows), so
+// the 4 KB one MMA K step reads are contiguous.
+__device__ __forceinline__ uint32_t a_offset(int r, int k)
+{
+    return (uint32_t)((k >> 3) * 2048 + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
 template <int K>
 __device__ __forceinline__ void pipe_store_row(uint8_t *A, int r, const float *f, int n_valid)
 {
@@ -145,9 +165,42 @@ __device__ __forceinline__ void pipe_store_row(uint8_t *A, int r, const float *f
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int k = c * 8 + 2 * e;
-            p[e] = pack_bf16(k < n_valid ? f[k] : 0.0f, k + 1 < n_valid ? f[k + 1] : 0.0f);
+            // inputs, then the two constant-one columns the layer-0 bias is folded into, then zeros
+            const float v0 = k < n_valid ? f[k] : (k < n_valid + 2 ? 1.0f : 0.0f);
+            const float v1 = k + 1 < n_valid ? f[k + 1] : (k + 1 < n_valid + 2 ? 1.0f : 0.0f);
+            p[e] = pack_bf16(v0, v1);
         }
-        *reinterpret_cast<uint4 *>(A + cm_offset(r, c * 8, K)) = make_uint4(p[0], p[1], p[2], p[3]);
+        *reinterpret_cast<uint4 *>(A + a_offset(r, c * 8)) = make_uint4(p[0], p[1], p[2], p[3]);
+    }
+}
+
+// ReLU and BF16 of 32 accumulator columns of this thread's row (the bias is already in them),
+// stored as A columns [c0, c0 + 32) of row r.
+__device__ __forceinline__ void epi_convert(const uint32_t (&v)[32], uint8_t *A, int r, int c0)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t *u = v + 8 * q;
+        uint4 pk;
+        pk.x = pack_bf16_relu(__uint_as_float(u[0]), __uint_as_float(u[1]));
+        pk.y = pack_bf16_relu(__uint_as_float(u[2]), __uint_as_float(u[3]));
+        pk.z = pack_bf16_relu(__uint_as_float(u[4]), __uint_as_float(u[5]));
+        pk.w = pack_bf16_relu(__uint_as_float(u[6]), __uint_as_float(u[7]));
+        *reinterpret_cast<uint4 *>(A + a_offset(r, c0 + 8 * q)) = pk;
+    }
+}
+
+// Last hidden layer: ReLU and BF16 rounding of 32 columns, folded into the NOUT outputs (w_out
+// rows of length N).
+template <int NOUT, int N>
+__device__ __forceinline__ void epi_output(const uint32_t (&v)[32], const float *wout, float *out)
+{
+#pragma unroll
+    for (int jj = 0; jj < 32; jj += 2) {
+        const uint32_t p = pack_bf16_relu(__uint_as_float(v[jj]), __uint_as_float(v[jj + 1]));
+        const float h0 = __uint_as_float(p << 16), h1 = __uint_as_float(p & 0xFFFF0000u);
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) out[o] = fmaf(h1, wout[o * N + jj + 1], fmaf(h0, wout[o * N + jj], out[o]));
     }
 }
 
@@ -237,7 +290,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
 {
     constexpr bool NERF = MODE == kModeShade || MODE == kModeMarch;
     using SH = PipeShape<N, NERF>;
-    constexpr int K0 = SH::K0, KA = SH::KA, S = SH::SLOTS, NOUT = SH::NOUT;
+    constexpr int K0 = SH::K0, S = SH::SLOTS, NOUT = SH::NOUT;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ PipeShared P;
     __shared__ uint64_t w_full[S], w_empty[S];
@@ -250,7 +303,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
     const int L = NERF ? ws.nerf_hidden : ws.nedf_hidden;
     uint8_t *A[2] = {smem, smem + SH::A_BYTES};
     uint8_t *ring = smem + 2 * SH::A_BYTES;
-    float *f32s = reinterpret_cast<float *>(smem + SH::FIXED);       // biases and output layer of one type
+    float *f32s = reinterpret_cast<float *>(smem + SH::FIXED);       // output layer of one type
     const int n_f32 = (int)pipe_f32_floats(N, NERF ? ws.nerf_hidden : ws.nedf_hidden, NOUT);
     volatile int *abort = &P.abort;
 
@@ -280,14 +333,15 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
             for (unsigned long long tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x) {
                 const uint8_t *blob = a.blobs + (size_t)pipe_tile_type<MODE>(ws, mb, a, tile) * a.blob_stride;
                 for (int l = 0; l < L && !*abort; ++l) {
-                    const int K = l == 0 ? K0 : N;
                     const uint8_t *src = blob + pipe_layer_off(K0, N, l);
-                    for (int c = 0; c < K / kKC; ++c, ++q) {
+                    const int nk = l == 0 ? K0 / kKC : N / kKC + 1;
+                    for (int c0 = 0; c0 < nk; c0 += SH::GC, ++q) {
                         const int s = (int)(q % S);
                         const uint32_t round = (uint32_t)(q / S);
+                        const uint32_t bytes = (uint32_t)(min(SH::GC, nk - c0) * SH::CHUNK);
                         if (!pipe_wait(&w_empty[s], (round & 1u) ^ 1u, abort, ws.status)) break;
-                        mbar_arrive_expect_tx(&w_full[s], SH::CHUNK);
-                        bulk_g2s(ring + (size_t)s * SH::CHUNK, src + (size_t)c * SH::CHUNK, SH::CHUNK, &w_full[s]);
+                        mbar_arrive_expect_tx(&w_full[s], bytes);
+                        bulk_g2s(ring + (size_t)s * SH::STAGE, src + (size_t)c0 * SH::CHUNK, bytes, &w_full[s]);
                     }
                 }
             }
@@ -303,19 +357,23 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
             bool issued_any = false;
             for (unsigned long long tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x) {
                 for (int l = 0; l < L && !*abort; ++l, ++ja) {
-                    const int K = l == 0 ? K0 : N;
                     if (!pipe_wait(&P.a_ready, (uint32_t)(ja & 1u), abort, ws.status)) break;
                     tc_fence_after();
-                    const uint32_t sbo_a = (uint32_t)(K / 8) * 128;
                     const uint32_t ax = smem_addr(A[0]), ay = smem_addr(A[1]);
-                    for (int c = 0; c < K / kKC; ++c, ++q) {
+                    const int nk = l == 0 ? K0 / kKC : N / kKC + 1;
+                    for (int c0 = 0; c0 < nk; c0 += SH::GC, ++q) {
                         const int s = (int)(q % S);
                         if (!pipe_wait(&w_full[s], (uint32_t)((q / S) & 1u), abort, ws.status)) break;
                         tc_fence_after();
-                        const uint64_t bdesc = smem_desc(smem_addr(ring + (size_t)s * SH::CHUNK), 128, 256);
-                        mma_bf16(tmem, smem_desc(ax + c * 256, 128, sbo_a), bdesc, idesc, c > 0 ? 1u : 0u);
-                        mma_bf16(tmem + N, smem_desc(ay + c * 256, 128, sbo_a), bdesc, idesc, c > 0 ? 1u : 0u);
-                        mma_commit(&w_empty[s]);      // the slot is free once both MMAs have read it
+                        const uint32_t stage = smem_addr(ring + (size_t)s * SH::STAGE);
+                        for (int c = c0; c < min(nk, c0 + SH::GC); ++c) {
+                            const uint64_t bdesc = smem_desc(stage + (uint32_t)(c - c0) * SH::CHUNK, 128, 256);
+                            // a hidden layer's last chunk is its bias, against the constant-one block
+                            const uint32_t ac = (uint32_t)(l > 0 && c == N / kKC ? SH::ONES / kKC : c) * 4096u;
+                            mma_bf16(tmem, smem_desc(ax + ac, 2048, 128), bdesc, idesc, c > 0 ? 1u : 0u);
+                            mma_bf16(tmem + N, smem_desc(ay + ac, 2048, 128), bdesc, idesc, c > 0 ? 1u : 0u);
+                        }
+                        mma_commit(&w_empty[s]);      // the stage is free once its MMAs have read it
                         issued_any = true;
                     }
                     mma_commit(&P.acc_full);
@@ -333,6 +391,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
         const int R = g * kHalf + r;                  // row within the tile
         const uint32_t tmem_row = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(g * N);
         uint8_t *Ag = A[g];
+        // the constant-one block hidden-layer biases are folded into: columns ONES, ONES + 1 are 1
+        *reinterpret_cast<uint4 *>(Ag + a_offset(r, SH::ONES)) = make_uint4(pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(Ag + a_offset(r, SH::ONES + 8)) = make_uint4(0u, 0u, 0u, 0u);
         unsigned long long jb = 0;
         const int ns = f.n_shade;
         int f32_type = -1;
@@ -443,7 +504,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
             // ---- layers -------------------------------------------------------------------------
             float out[NOUT];
 #pragma unroll
-            for (int o = 0; o < NOUT; ++o) out[o] = f32[L * N + NOUT * N + o];
+            for (int o = 0; o < NOUT; ++o) out[o] = f32[NOUT * N + o];
             bool ok = true;
             for (int l = 0; l < L; ++l, ++jb) {
                 // a warp-uniform outcome: the tcgen05.ld below is warp-collective
@@ -453,51 +514,37 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                     break;
                 }
                 tc_fence_after();
-                const float *bias = f32 + l * N;
                 if (l + 1 < L) {
-                    // 64 accumulator columns per TMEM wait: two loads in flight, then bias, ReLU, BF16
+                    // 32-column blocks, double-buffered: block b + 1 is loading from TMEM while
+                    // block b gets bias, ReLU, BF16 and goes to the next layer's A operand
+                    uint32_t va[32], vb[32];
+                    tmem_ld32(tmem_row, va);
+                    tmem_wait_ld(va);
 #pragma unroll 1
                     for (int c0 = 0; c0 < N; c0 += 64) {
-                        uint32_t v[2][32];
-                        tmem_ld32(tmem_row + c0, v[0]);
-                        tmem_ld32(tmem_row + c0 + 32, v[1]);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const float4 *b4 = reinterpret_cast<const float4 *>(bias + c0 + 32 * hh);
-#pragma unroll
-                            for (int qq = 0; qq < 4; ++qq) {
-                                const float4 ba = b4[2 * qq], bb = b4[2 * qq + 1];
-                                const uint32_t *u = v[hh] + 8 * qq;
-                                uint4 pk;
-                                pk.x = pack_bf16(fmaxf(__uint_as_float(u[0]) + ba.x, 0.0f), fmaxf(__uint_as_float(u[1]) + ba.y, 0.0f));
-                                pk.y = pack_bf16(fmaxf(__uint_as_float(u[2]) + ba.z, 0.0f), fmaxf(__uint_as_float(u[3]) + ba.w, 0.0f));
-                                pk.z = pack_bf16(fmaxf(__uint_as_float(u[4]) + bb.x, 0.0f), fmaxf(__uint_as_float(u[5]) + bb.y, 0.0f));
-                                pk.w = pack_bf16(fmaxf(__uint_as_float(u[6]) + bb.z, 0.0f), fmaxf(__uint_as_float(u[7]) + bb.w, 0.0f));
-                                *reinterpret_cast<uint4 *>(Ag + cm_offset(r, c0 + 32 * hh + 8 * qq, N)) = pk;
-                            }
-                        }
+                        tmem_ld32(tmem_row + c0 + 32, vb);
+                        epi_convert(va, Ag, r, c0);
+                        tmem_wait_ld(vb);
+                        if (c0 + 64 < N) tmem_ld32(tmem_row + c0 + 64, va);
+                        epi_convert(vb, Ag, r, c0 + 32);
+                        if (c0 + 64 < N) tmem_wait_ld(va);
                     }
                     fence_proxy_async_smem();
                     tc_fence_before();
                     mbar_arrive(&P.a_ready);
                 } else {
-                    const float *wout = f32 + L * N;
+                    const float *wout = f32;
+                    uint32_t va[32], vb[32];
+                    tmem_ld32(tmem_row, va);
+                    tmem_wait_ld(va);
 #pragma unroll 1
                     for (int c0 = 0; c0 < N; c0 += 64) {
-                        uint32_t v[2][32];
-                        tmem_ld32(tmem_row + c0, v[0]);
-                        tmem_ld32(tmem_row + c0 + 32, v[1]);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-                            for (int jj = 0; jj < 32; ++jj) {
-                                const int c = c0 + 32 * hh + jj;
-                                const float h = round_bf16(fmaxf(__uint_as_float(v[hh][jj]) + bias[c], 0.0f));
-#pragma unroll
-                                for (int o = 0; o < NOUT; ++o) out[o] = fmaf(h, wout[o * N + c], out[o]);
-                            }
+                        tmem_ld32(tmem_row + c0 + 32, vb);
+                        epi_output<NOUT, N>(va, wout + c0, out);
+                        tmem_wait_ld(vb);
+                        if (c0 + 64 < N) tmem_ld32(tmem_row + c0 + 64, va);
+                        epi_output<NOUT, N>(vb, wout + c0 + 32, out);
+                        if (c0 + 64 < N) tmem_wait_ld(va);
                     }
                     tc_fence_before();
                 }
