@@ -39,7 +39,9 @@ FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1)
 NEDF_FLOP = 2 * (78 * 128 + 5 * 128 * 128 + 128 * 2)          # per query, unpadded
 # DRAM bytes (read + write) per launch of a stage's kernel from an ncu capture of the current
 # kernel source (profiles/); a stage is absent here once its kernel changed after the capture.
-PROFILED_TRAFFIC = {"step2_shade": 9.41e6}    # k_pipe<256,0>, profiles/k_pipe_1024inst_1024px_bf16.md
+# DRAM bytes per launch of the dominant kernel from an ncu capture of the current kernel (None until
+# the kernel's counters have been taken again after a change)
+PROFILED_TRAFFIC = {"step2_shade": 9.53e6}    # k_pipe<256,0>, profiles/k_pipe_1024inst_1024px_bf16.md
 NERF_FLOP = 2 * (90 * 256 + 7 * 256 * 256 + 256 * 3)          # per sample, unpadded
 
 
@@ -294,11 +296,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     both = (ids != -1) & (jids != -1)
     err = (depth.double() - jdepth.double()).abs()[both] / 1.0       # r_b = 1, s = 1: world = local
+    same = both & (ids == jids)
+    err_same = (depth.double() - jdepth.double()).abs()[same]
+    edges = [0.0, 1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 1e-1, 3e-1, 1.0, float("inf")]
+    hist = torch.histogram(err_same.cpu(), bins=torch.tensor(edges, dtype=torch.float64))[0] if err_same.numel() else None
     derr = {"mean_over_rb": float(err.mean()) if err.numel() else None,
             "median_over_rb": float(err.median()) if err.numel() else None,
             "p99_over_rb": float(torch.quantile(err.float(), 0.99)) if err.numel() else None,
             "pixels_both_hit": int(both.sum()),
             "id_agreement": float((ids == jids)[both].double().mean()) if err.numel() else None,
+            "mean_over_rb_same_id": float(err_same.mean()) if err_same.numel() else None,
+            "p99_over_rb_same_id": float(torch.quantile(err_same.float(), 0.99)) if err_same.numel() else None,
+            "histogram_same_id": {"edges_over_rb": edges[:-1] + ["inf"],
+                                  "counts": [int(c) for c in hist]} if hist is not None else None,
             "hit_mask_agreement": float(((ids != -1) == (jids != -1)).double().mean())}
 
     # ---- plain ray-march frame on the same GPU ------------------------------------------------
@@ -370,6 +380,9 @@ def run_ours(args):
     flops = {"step1_nedf": P1 * NEDF_FLOP, "step2_shade": Hv * sc.n_shade * NERF_FLOP, "step3_nedf": P3 * NEDF_FLOP}
     dom = max(flops, key=lambda k: stage_ms.get(k, 0.0))
     achieved = flops[dom] / (stage_ms[dom] * 1e-3) / 1e12
+    # every MLP stage against the same peak (the NeDF stages also hold their deferred plain-method pairs)
+    mlp_stages = {k: {"tflops": round(f / (stage_ms[k] * 1e-3) / 1e12, 1), "ms": round(stage_ms[k], 4)}
+                  for k, f in flops.items() if stage_ms.get(k)}
     if prec == native.PREC_FP32:
         peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -379,6 +392,8 @@ def run_ours(args):
         peak = pk["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": PROFILED_TRAFFIC.get(dom), "kernel": dom, "peak_basis": f"bf16 dense, {pk_kind} (burst)"}
+    for k in mlp_stages:
+        mlp_stages[k]["frac"] = round(mlp_stages[k]["tflops"] / roof["peak"], 3)
 
     # ---- CPU baseline: the oracle on the host cores ------------------------------------------
     cpu = None
@@ -405,6 +420,7 @@ def run_ours(args):
             "clocks": clocks,
             "frame": {"ms": frame_ms, "total_rays_per_s": n * (1 + 4) / (frame_ms * 1e-3),
                       "primary_pairs": P1, "shadow_pairs": P3, "hit_pixels": Hv, "fallback_pairs": st.fallback_pairs,
+                      "fallback_rate": st.fallback_pairs / max(1, P1 + P3), "mlp_stages": mlp_stages,
                       "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "wall_s": t_wall},
             "fp32_frame": fp32,
             "march_frame": march,
