@@ -35,6 +35,9 @@ METRIC = "composited rays/s & ms/frame at 1024², NeDF vs ray-march, same GPU, d
 WORKLOAD = ("1024 instances (sphere/torus/box, seed 3, T in [-20,20]^3) at 1024x1024, 4 point lights, "
             "NeDF 6x128 per type trained on ray-march labels, NeRF 8x256 per type, 8 shading samples, "
             "fallback below confidence 0.9, 4 refinement steps with outlier re-answering")
+WORKLOAD_STRESS = ("4096 instances (8 shape types x 512, seed 4, T in [-40,40]^3) at 2048x2048, 8 point lights, "
+                   "NeDF 6x128 per type trained on ray-march labels, NeRF 8x256 per type, 8 shading samples, "
+                   "fallback below confidence 0.9, 4 refinement steps with outlier re-answering")
 FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1)
 NEDF_FLOP = 2 * (78 * 128 + 5 * 128 * 128 + 128 * 2)          # per query, unpadded
 # DRAM bytes (read + write) per launch of a stage's kernel from an ncu capture of the current
@@ -230,7 +233,9 @@ def run_ours(args):
     from paper_2308_04669_gb300 import native
     from paper_2308_04669_gb300 import scenegen as sg
 
-    sc = sg.thousand_scene()
+    sc = sg.thousand_scene() if args.scene == "thousand" else sg.stress_scene()
+    workload = WORKLOAD if args.scene == "thousand" else WORKLOAD_STRESS
+    n_li = len(sc.lights)
     stream = torch.cuda.Stream()            # a non-default stream: frames are CUDA-graph captured
     torch.cuda.set_stream(stream)
     prec = native.PREC_BF16 if args.precision == "bf16" else native.PREC_FP32
@@ -403,22 +408,22 @@ def run_ours(args):
         threads = os.cpu_count() or 1
         rate, npx, secs = oracle_rate(sc, w_tr, args.cpu_seconds, threads)
         cpu = {"value": rate, "unit": "rays/s", "cores": threads, "kind": "oracle",
-               "sample": f"{npx} seeded pixels of the same 1024x1024 frame (same trained weights, all 1024 "
-                         f"instances, 4 lights), {secs:.1f} s on {threads} threads"}
+               "sample": f"{npx} seeded pixels of the same {sc.W}x{sc.H} frame (same trained weights, all {sc.n_inst} "
+                         f"instances, {n_li} lights), {secs:.1f} s on {threads} threads"}
     r.close()
 
     value = world * n / (frame_ms_max * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": frame_ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == native.PREC_FP32 else "bf16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "W": sc.W, "H": sc.H, "instances": sc.n_inst, "lights": 4,
+            "config": {"workload": workload, "W": sc.W, "H": sc.H, "instances": sc.n_inst, "lights": n_li,
                        "l2": "flushed between timed frames (256 MiB write, outside the timed events)",
                        "parallelism": f"replicas x{world} (one frame per GPU)"},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": world * n / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(st.kernel_launches) * args.steps,
             "clocks": clocks,
-            "frame": {"ms": frame_ms, "total_rays_per_s": n * (1 + 4) / (frame_ms * 1e-3),
+            "frame": {"ms": frame_ms, "total_rays_per_s": n * (1 + n_li) / (frame_ms * 1e-3),
                       "primary_pairs": P1, "shadow_pairs": P3, "hit_pixels": Hv, "fallback_pairs": st.fallback_pairs,
                       "fallback_rate": st.fallback_pairs / max(1, P1 + P3), "mlp_stages": mlp_stages,
                       "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "wall_s": t_wall},
@@ -440,6 +445,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--scene", default="thousand", choices=["thousand", "stress"],
+                    help="thousand: the metric's 1024-instance 1024^2 frame; stress: 4096 instances at 2048^2, 8 lights")
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--train-batch", type=int, default=16384)
     ap.add_argument("--label-rays", type=int, default=1 << 20)

@@ -24,7 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 DEPTH_MLP, DEPTH_EXACT, DEPTH_MARCH = 0, 1, 2
-QUANT_NONE, QUANT_BF16 = 0, 1
+QUANT_NONE, QUANT_BF16, QUANT_FP8 = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -83,6 +83,8 @@ def lib():
             l.orc_nedf_features.argtypes = [d, d, C.c_double, d, d]; l.orc_nedf_features.restype = C.c_int
             l.orc_mlp.argtypes = [d, C.c_int, i, d, d, C.c_int]
             l.orc_round_bf16.argtypes = [C.c_double]; l.orc_round_bf16.restype = C.c_double
+            l.orc_round_e4m3.argtypes = [C.c_double]; l.orc_round_e4m3.restype = C.c_double
+            l.orc_fp8_scale.argtypes = [C.c_double]; l.orc_fp8_scale.restype = C.c_double
             l.orc_query.argtypes = [sp, op, C.c_int, d, d, d, d]; l.orc_query.restype = C.c_int
             l.orc_exact_depth.argtypes = [C.c_int, d, d, d, C.c_double, C.c_double, i]
             l.orc_exact_depth.restype = C.c_double
@@ -240,6 +242,14 @@ def mlp(w, dims, x, quant=QUANT_NONE):
 
 def round_bf16(x):
     return lib().orc_round_bf16(float(x))
+
+
+def round_e4m3(x):
+    return lib().orc_round_e4m3(float(x))
+
+
+def fp8_scale(max_abs):
+    return lib().orc_fp8_scale(float(max_abs))
 
 
 def query(osc: OracleScene, inst, o, d, **kw):

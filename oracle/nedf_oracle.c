@@ -197,6 +197,32 @@ double orc_round_bf16(double x)
     return nearbyint(x / q) * q;
 }
 
+double orc_round_e4m3(double x)
+{
+    /* OCP FP8 E4M3 (no infinities): 3 fraction bits, exponent bias 7, normals from 2^-6, subnormal
+     * spacing 2^-9, largest finite 448.  Nearest value, ties to even; beyond 448 saturates to 448. */
+    if (x == 0.0 || isnan(x)) return x;
+    int e;
+    frexp(x, &e);                                   /* |x| in [2^(e-1), 2^e) */
+    int ulp_exp = e - 1 - 3;                        /* spacing of 4-bit significands in that binade */
+    if (ulp_exp < -9) ulp_exp = -9;                 /* subnormal range keeps the 2^-9 spacing */
+    double q = ldexp(nearbyint(ldexp(x, -ulp_exp)), ulp_exp);
+    if (q > 448.0) q = 448.0;
+    if (q < -448.0) q = -448.0;
+    return q;
+}
+
+double orc_fp8_scale(double max_abs)
+{
+    /* The power of two s with max_abs / s in (224, 448]; 1 for an all-zero layer. */
+    if (!(max_abs > 0.0)) return 1.0;
+    int e;
+    frexp(max_abs / 448.0, &e);                     /* max_abs / 448 in [2^(e-1), 2^e) */
+    double s = ldexp(1.0, e);
+    if (max_abs / ldexp(1.0, e - 1) <= 448.0) s = ldexp(1.0, e - 1);   /* exact power of two */
+    return s;
+}
+
 void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant)
 {
     int maxd = 0;
@@ -207,15 +233,29 @@ void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, do
     for (int l = 0; l < n_layers; ++l) {
         int fi = dims[l], fo = dims[l + 1];
         const double *W = p, *bias = p + (size_t)fi * fo;
+        /* FP8 mode: hidden-to-hidden layers (not the first, not the output layer) in E4M3 */
+        const int fp8_layer = quant == ORC_QUANT_FP8 && l > 0 && l + 1 < n_layers;
+        double s = 1.0;
+        if (fp8_layer) {
+            double m = 0.0;
+            for (size_t i = 0; i < (size_t)fi * fo; ++i) m = dmax(m, fabs(W[i]));
+            s = orc_fp8_scale(m);
+        }
         for (int o = 0; o < fo; ++o) {
             double acc = 0.0;
             for (int i = 0; i < fi; ++i) {
                 double wv = W[(size_t)o * fi + i], av = a[i];
                 if (quant == ORC_QUANT_BF16) { wv = orc_round_bf16(wv); av = orc_round_bf16(av); }
+                else if (quant == ORC_QUANT_FP8) {
+                    if (fp8_layer) wv = s * orc_round_e4m3(wv / s);
+                    else wv = orc_round_bf16(wv);
+                    if (l == 0) av = orc_round_bf16(av);   /* later inputs are E4M3 already */
+                }
                 acc += wv * av;
             }
             acc += bias[o];
             b[o] = (l + 1 < n_layers) ? dmax(acc, 0.0) : acc;
+            if (quant == ORC_QUANT_FP8 && l + 1 < n_layers) b[o] = orc_round_e4m3(b[o]);
         }
         memcpy(a, b, sizeof(double) * fo);
         p += (size_t)fi * fo + fo;

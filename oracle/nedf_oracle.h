@@ -25,7 +25,11 @@ extern "C" {
 enum { ORC_SPHERE = 0, ORC_TORUS, ORC_BOX, ORC_CAPSULE, ORC_ROUNDCONE, ORC_TWOSPHERE,
        ORC_TWISTTORUS, ORC_OCTA };
 enum { ORC_DEPTH_MLP = 0, ORC_DEPTH_EXACT = 1, ORC_DEPTH_MARCH = 2 };
-enum { ORC_QUANT_NONE = 0, ORC_QUANT_BF16 = 1 };
+/* NONE: double throughout.  BF16: every layer's weights and inputs rounded to BF16.  FP8: the
+ * first layer as BF16; every later hidden layer's weights as s_l * E4M3(W / s_l) with s_l the
+ * power of two that puts max|W| in (224, 448]; every hidden activation rounded to E4M3; the output
+ * layer's weights rounded to BF16.  Sums and biases stay in double in every mode. */
+enum { ORC_QUANT_NONE = 0, ORC_QUANT_BF16 = 1, ORC_QUANT_FP8 = 2 };
 
 typedef struct {
     int kind;
@@ -79,6 +83,8 @@ int orc_nedf_features(const double ol[3], const double dl[3], double rb, double 
 /* Networks */
 void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant);
 double orc_round_bf16(double x);
+double orc_round_e4m3(double x);
+double orc_fp8_scale(double max_abs);
 
 /* One (ray, instance) query: returns 1 on hit; out6 = {Dl, m, a, te, tx, tperp} */
 int orc_query(const orc_scene *sc, const orc_opts *op, int inst, const double o[3],

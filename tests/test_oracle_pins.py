@@ -153,6 +153,62 @@ def test_bf16_rounding_matches_torch(orc):
     assert np.array_equal(got, ref)
 
 
+def test_e4m3_rounding_matches_torch_and_closed_forms(orc):
+    """OCP E4M3: 3 fraction bits, normals from 2^-6, subnormal spacing 2^-9, largest finite 448."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    xs = rng.normal(size=4000) * 10.0 ** rng.uniform(-3.5, 2.3, 4000)
+    xs = xs[np.abs(xs) < 440.0]
+    ref = torch.tensor(xs).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    got = np.array([orc.round_e4m3(float(v)) for v in xs])
+    assert np.array_equal(got, ref)
+    # representable values are fixed points; the grid around 1 is 1/8
+    for v in (1.0, 1.125, 1.875, 448.0, 2.0 ** -6, 2.0 ** -9, 7 * 2.0 ** -9, -240.0):
+        assert orc.round_e4m3(v) == v
+    assert orc.round_e4m3(1.0625) == 1.0 and orc.round_e4m3(1.1875) == 1.25        # ties to even
+    assert orc.round_e4m3(2.0 ** -10) == 0.0 and orc.round_e4m3(3 * 2.0 ** -11) == 2.0 ** -9
+    assert orc.round_e4m3(500.0) == 448.0 and orc.round_e4m3(-1e6) == -448.0      # saturation
+    assert orc.round_e4m3(0.0) == 0.0
+
+
+def test_fp8_scale_is_the_power_of_two_filling_the_e4m3_range(orc):
+    for m in (448.0, 449.0, 0.1, 224.0, 224.0001, 3.0e-5, 1.0):
+        s = orc.fp8_scale(m)
+        assert s == 2.0 ** np.round(np.log2(s))
+        assert 224.0 < m / s <= 448.0
+    assert orc.fp8_scale(0.0) == 1.0
+
+
+def test_mlp_fp8_mode_matches_torch_float8(orc):
+    """FP8 mode: layer 0 in BF16, hidden layers' weights s * E4M3(W / s), activations E4M3, output
+    layer weights BF16; checked against torch's own float8 / bfloat16 casts and float64 matmuls."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(9)
+    dims = [78, 64, 64, 64, 2]
+    w = (rng.normal(size=sg.mlp_param_count(dims)) * 0.2).astype(np.float32).astype(np.float64)
+    x = rng.normal(size=78).astype(np.float32).astype(np.float64)
+    y = orc.mlp(w, dims, x, quant=orc.QUANT_FP8)
+    t = lambda a: torch.tensor(np.asarray(a, np.float64))
+    bf = lambda a: t(a).to(torch.float32).to(torch.bfloat16).to(torch.float64)
+    f8 = lambda a: t(a).to(torch.float8_e4m3fn).to(torch.float64)
+    h = bf(x)
+    off = 0
+    n = len(dims) - 1
+    for l in range(n):
+        fi, fo = dims[l], dims[l + 1]
+        W = w[off: off + fi * fo].reshape(fo, fi); off += fi * fo
+        b = t(w[off: off + fo]); off += fo
+        if 0 < l < n - 1:
+            s = 2.0 ** np.ceil(np.log2(np.abs(W).max() / 448.0))
+            Wq = s * f8(W / s)
+        else:
+            Wq = bf(W)
+        h = h @ Wq.T + b
+        if l + 1 < n:
+            h = f8(torch.relu(h).numpy())
+    assert np.allclose(y, h.numpy(), rtol=1e-12, atol=1e-12)
+
+
 def test_mlp_bf16_mode_matches_torch_rounded_operands(orc):
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(8)
