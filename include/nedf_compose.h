@@ -60,8 +60,11 @@ extern "C" {
 
 /* ---- enums --------------------------------------------------------------------------------- */
 enum nedf_precision {       /* arithmetic of the NeDF and NeRF layers (accumulation is FP32)   */
-    NEDF_PREC_FP32 = 0,
-    NEDF_PREC_BF16 = 1
+    NEDF_PREC_FP32 = 0,     /* CUDA cores                                                      */
+    NEDF_PREC_BF16 = 1,     /* tensor cores, BF16 weights and activations                      */
+    NEDF_PREC_FP8 = 2       /* tensor cores: first layer BF16, later hidden layers E4M3 weights
+                               (W / s_l, s_l a per-layer power of two) and E4M3 activations;
+                               the output layer in FP32 with BF16 weights                       */
 };
 enum nedf_depth_source {    /* what answers the (ray, instance) depth queries of Steps 1 and 3 */
     NEDF_DEPTH_NEDF = 0,    /* the Neural Depth Field (the method)                             */

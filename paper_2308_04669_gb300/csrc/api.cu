@@ -212,10 +212,10 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
     if (c.nerf_hidden < 0 || c.nerf_hidden > 16 ||
         (c.nerf_hidden > 0 && c.nerf_width != 64 && c.nerf_width != 128 && c.nerf_width != 256))
         return fail(nullptr, NEDF_ERR_UNSUPPORTED, "NeRF shape: hidden 0..16, width 64/128/256");
-    if (c.precision != NEDF_PREC_FP32 && c.precision != NEDF_PREC_BF16)
+    if (c.precision != NEDF_PREC_FP32 && c.precision != NEDF_PREC_BF16 && c.precision != NEDF_PREC_FP8)
         return fail(nullptr, NEDF_ERR_UNSUPPORTED, "precision");
-    if (c.precision == NEDF_PREC_BF16 && c.nedf_width > 128)
-        return fail(nullptr, NEDF_ERR_UNSUPPORTED, "BF16 NeDF width must be 64 or 128");
+    if (c.precision != NEDF_PREC_FP32 && c.nedf_width > 128)
+        return fail(nullptr, NEDF_ERR_UNSUPPORTED, "tensor-core NeDF width must be 64 or 128");
     if (c.primary_pair_capacity < 0 || c.shadow_pair_capacity < 0)
         return fail(nullptr, NEDF_ERR_ARG, "negative capacity");
 
@@ -278,11 +278,12 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
         CA(h->d_lg_big_count, sizeof(uint32_t) * NEDF_MAX_LIGHTS);
         CA(h->d_scan_tmp, sizeof(uint32_t) * 1024);
     }
-    if (c.precision == NEDF_PREC_BF16) {
-        h->nedf_tc_stride = pipe_blob_size(kNedfInPad, c.nedf_width, c.nedf_hidden, 2);
+    if (c.precision != NEDF_PREC_FP32) {
+        const bool f8 = c.precision == NEDF_PREC_FP8;
+        h->nedf_tc_stride = pipe_blob_size(kNedfInPad, c.nedf_width, c.nedf_hidden, 2, f8);
         CA(h->d_nedf_tc, h->nedf_tc_stride * c.max_types);
         if (c.nerf_hidden > 0) {
-            h->nerf_tc_stride = pipe_blob_size(kNerfInPad, c.nerf_width, c.nerf_hidden, 3);
+            h->nerf_tc_stride = pipe_blob_size(kNerfInPad, c.nerf_width, c.nerf_hidden, 3, f8);
             CA(h->d_nerf_tc, h->nerf_tc_stride * c.max_types);
         }
     }
@@ -409,7 +410,7 @@ int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *ty
         ts.cursor = 0;
         if (h->d_nedf_tc)
             CK(h, launch_pack_pipe(ts.master, h->d_nedf_tc + (size_t)k * h->nedf_tc_stride, kNedfIn, kNedfInPad,
-                                 h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->stream));
+                                 h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->cfg.precision == NEDF_PREC_FP8, h->stream));
     }
     if (h->d_nerf_tc) {
         float *tmp = nullptr;
@@ -419,7 +420,7 @@ int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *ty
                                        cudaMemcpyHostToDevice);
             if (e == cudaSuccess)
                 e = launch_pack_pipe(tmp, h->d_nerf_tc + (size_t)k * h->nerf_tc_stride, kNerfIn, kNerfInPad,
-                                   h->cfg.nerf_width, h->cfg.nerf_hidden, 3, h->stream);
+                                   h->cfg.nerf_width, h->cfg.nerf_hidden, 3, h->cfg.precision == NEDF_PREC_FP8, h->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
             if (e != cudaSuccess) {
                 cudaFree(tmp);
@@ -689,7 +690,7 @@ int nedf_compose_nedf_query(nedf_handle *h, int type, int n, const float *o, con
     if (!h || !o || !d || !out) return fail(h, NEDF_ERR_ARG, "null argument");
     if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
     if (n < 0) return fail(h, NEDF_ERR_ARG, "n < 0");
-    if (h->cfg.precision == NEDF_PREC_BF16)
+    if (h->cfg.precision != NEDF_PREC_FP32)
         CK(h, launch_nedf_pipe(make_ws(h), 2, type, o, d, out, n, h->num_sms, h->stream));
     else
         CK(h, launch_nedf_query_f32(make_ws(h), type, o, d, out, n, h->num_sms, h->stream));
@@ -795,7 +796,7 @@ int nedf_compose_train_step(nedf_handle *h, int type, int batch, float lr, float
     ts.cursor = (ts.cursor + batch) % ts.n_rays;
     if (h->d_nedf_tc)
         CK(h, launch_pack_pipe(ts.master, h->d_nedf_tc + (size_t)type * h->nedf_tc_stride, kNedfIn, kNedfInPad,
-                             h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->stream));
+                             h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->cfg.precision == NEDF_PREC_FP8, h->stream));
     if (loss_host) {
         CK(h, cudaStreamSynchronize(h->stream));
         CK(h, cudaMemcpy(loss_host, h->d_loss, sizeof(float), cudaMemcpyDeviceToHost));
@@ -867,7 +868,7 @@ int nedf_compose_load_state(nedf_handle *h, const void *buf, size_t size)
         CK(h, launch_refresh_weights(L));
         if (h->d_nedf_tc)
             CK(h, launch_pack_pipe(h->train[k].master, h->d_nedf_tc + (size_t)k * h->nedf_tc_stride, kNedfIn,
-                                 kNedfInPad, h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->stream));
+                                 kNedfInPad, h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->cfg.precision == NEDF_PREC_FP8, h->stream));
     }
     CK(h, cudaStreamSynchronize(h->stream));
     return NEDF_OK;

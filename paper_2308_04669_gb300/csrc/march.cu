@@ -261,7 +261,7 @@ cudaError_t launch_march_colour_frame(const FrameLaunch &L, void *scratch, long 
     k_march_clear<<<g, 256, 0, st>>>(ws, mb, npix, n_samples);
     if (early_stop) k_march_pairs<true><<<g * 2, 128, 0, st>>>(ws, mb, n_samples);
     else k_march_pairs<false><<<g * 2, 128, 0, st>>>(ws, mb, n_samples);
-    const bool tc = ws.precision == 1 && ws.nerf_hidden > 0;
+    const bool tc = ws.precision >= 1 && ws.nerf_hidden > 0;
     k_march_scan<<<1, 1, 0, st>>>(ws, mb, tc ? kPipeTileRows : kTileRows);
     cudaError_t e = cudaSuccess;
     if (tc) {

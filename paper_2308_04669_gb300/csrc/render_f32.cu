@@ -491,8 +491,8 @@ cudaError_t launch_frame(FrameLaunch &L)
     int stage = 0;
     // the tensor-core kernels take 128-row tiles, the CUDA-core kernels 64-row tiles; the work
     // list scans must use the tile size of the kernel that consumes the list
-    const bool tc_nedf = ws.precision == 1 && ws.depth_source == 0;
-    const bool tc_shade = ws.precision == 1 && ws.nerf_hidden > 0;
+    const bool tc_nedf = ws.precision >= 1 && ws.depth_source == 0;      // BF16 or E4M3 tensor-core layers
+    const bool tc_shade = ws.precision >= 1 && ws.nerf_hidden > 0;
     const int nedf_rows = tc_nedf ? kPipeTileRows : kTileRows;
     // the engine shades (128 / n_shade) pixels per 128-row half, two halves per tile
     const int shade_ppt = tc_shade ? 2 * (kTcTileRows / L.n_shade) : kTileRows / L.n_shade;

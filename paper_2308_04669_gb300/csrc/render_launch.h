@@ -23,10 +23,11 @@ constexpr int kLightGridSize = 128;   // shadow-map camera grid (cells per side)
 
 cudaError_t launch_frame(FrameLaunch &L);
 
-// BF16 tensor-core engine (render_pipe.cu): tiles of 256 rows, weight chunks streamed per layer
+// Tensor-core engine (render_pipe.cu): tiles of 256 rows, weight chunks streamed per layer; f8:
+// hidden layers after the first in E4M3 with per-layer scales
 constexpr int kPipeTileRows = 256;
-size_t pipe_blob_size(int K0, int N, int L, int n_out);
-cudaError_t launch_pack_pipe(const float *master, void *blob, int K_in, int K0, int N, int L, int n_out,
+size_t pipe_blob_size(int K0, int N, int L, int n_out, bool f8);
+cudaError_t launch_pack_pipe(const float *master, void *blob, int K_in, int K0, int N, int L, int n_out, bool f8,
                              cudaStream_t st);
 // mode 0: Step-1 pairs, 1: Step-3 pairs, 2: n caller rays (o, d) of `type` -> out float4[n]
 cudaError_t launch_nedf_pipe(const Workspace &ws, int mode, int type, const float *o, const float *d, float *out,

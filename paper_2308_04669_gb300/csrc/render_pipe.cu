@@ -23,6 +23,8 @@
 #include "render_launch.h"
 #include "tc_ptx.cuh"
 
+#include <cuda_fp8.h>
+
 #include <algorithm>
 
 namespace nedf {
@@ -38,51 +40,85 @@ constexpr int kStageBytes = 16384;          // weight bytes per bulk copy
 enum PipeMode { kModeShade = 0, kModeMarch = 1, kModePrimary = 2, kModeShadow = 3, kModeQuery = 4 };
 
 // NERF: the colour network (90 inputs padded to 96, 3 outputs); otherwise the NeDF (78 -> 80, 2).
-template <int N, bool NERF>
+// F8: hidden layers after the first in E4M3 (first layer BF16; output layer on CUDA cores).
+template <int N, bool NERF, bool F8>
 struct PipeShape {
     static constexpr int K0 = NERF ? kNerfInPad : kNedfInPad;        // input width of layer 0
-    // The bias of every layer is folded into its MMAs: two constant-one input columns times the
-    // bias split into BF16 high and low parts.  Layer 0 has them inside its input padding; hidden
-    // layers read them from a 16-column block at ONES, after every column a layer writes.
+    // BF16: the bias of every layer is folded into its MMAs: two constant-one input columns times
+    // the bias split into BF16 high and low parts.  Layer 0 has them inside its input padding;
+    // hidden layers read them from a 16-column block at ONES, after every column a layer writes.
+    // F8: layer 0 as in BF16; later biases are added (with the layer's scale) in the epilogue.
     static constexpr int ONES = K0 > N ? K0 : N;
-    static constexpr int KA = ONES + kKC;                            // A operand columns
-    static constexpr int CHUNK = N * kKC * 2;                        // bytes of one weight chunk
+    static constexpr int A_ROW = F8 ? (2 * K0 > N ? 2 * K0 : N) : 2 * (ONES + kKC);   // A bytes per row
+    static constexpr int CHUNK = N * 32;                             // N x 16 BF16 or N x 32 E4M3
     static constexpr int GC = kStageBytes / CHUNK;                   // chunks per stage
     static constexpr int STAGE = GC * CHUNK;
-    static constexpr int SLOTS = N == 128 ? 6 : 4;                   // ring stages
+    static constexpr int SLOTS = F8 ? (N == 64 ? 4 : 8) : (N == 128 ? 6 : 4);   // ring stages
     static constexpr int NOUT = NERF ? 3 : 2;
-    static constexpr size_t A_BYTES = (size_t)kHalf * KA * 2;
+    static constexpr size_t A_BYTES = (size_t)kHalf * A_ROW;
     static constexpr size_t FIXED = 2 * A_BYTES + (size_t)SLOTS * STAGE;   // + the fp32 block (depends on L)
 };
 
-// ---- weight blobs: per layer, chunks of 16 input columns, each chunk N x 16 in the core-matrix
-// layout (SBO 256 bytes).  Layer 0 has K0 / 16 chunks with the bias in input columns K_in, K_in + 1
-// (high and low BF16 parts); a hidden layer has N / 16 chunks plus one bias chunk (columns 0, 1).
-// Then the fp32 block [w_out n_out x N (BF16 values)][b_out].
-__host__ __device__ inline size_t pipe_layer_off(int K0, int N, int l)
+// ---- weight blobs: per layer, chunks of 32 bytes of input per output row, each chunk N rows in the
+// core-matrix layout (SBO 256 bytes).  Layer 0 (BF16) has K0 / 16 chunks with the bias in input
+// columns K_in, K_in + 1 (high and low BF16 parts).  A BF16 hidden layer has N / 16 chunks plus
+// one bias chunk (columns 0, 1); an E4M3 hidden layer has N / 32 chunks of W / s_l.  Then the fp32
+// block: [w_out n_out x N (BF16 values)][b_out], and for E4M3 at pipe_f8_bias_off
+// [bias L x N (row 0 unused)][s_l, L values (s_0 unused)].
+__host__ __device__ inline size_t pipe_layer_off(int K0, int N, int l, bool f8)
 {
-    return l == 0 ? 0 : (size_t)K0 * N * 2 + (size_t)(l - 1) * (N + kKC) * N * 2;
+    return l == 0 ? 0 : (size_t)K0 * N * 2 + (size_t)(l - 1) * (f8 ? (size_t)N * N : (size_t)(N + kKC) * N * 2);
 }
-__host__ __device__ inline size_t pipe_w_bytes(int K0, int N, int L) { return pipe_layer_off(K0, N, L); }
-__host__ __device__ inline size_t pipe_f32_floats(int N, int L, int n_out)
+__host__ __device__ inline size_t pipe_w_bytes(int K0, int N, int L, bool f8) { return pipe_layer_off(K0, N, L, f8); }
+__host__ __device__ inline size_t pipe_f8_bias_off(int N, int n_out) { return ((size_t)n_out * N + n_out + 3) & ~(size_t)3; }
+__host__ __device__ inline size_t pipe_f32_floats(int N, int L, int n_out, bool f8)
 {
-    (void)L;
-    return ((size_t)n_out * N + n_out + 3) & ~(size_t)3;
+    const size_t b = pipe_f8_bias_off(N, n_out);
+    return f8 ? (b + (size_t)L * N + L + 3) & ~(size_t)3 : b;
 }
-size_t pipe_blob_size(int K0, int N, int L, int n_out)
+size_t pipe_blob_size(int K0, int N, int L, int n_out, bool f8)
 {
-    size_t b = pipe_w_bytes(K0, N, L) + pipe_f32_floats(N, L, n_out) * 4;
+    size_t b = pipe_w_bytes(K0, N, L, f8) + pipe_f32_floats(N, L, n_out, f8) * 4;
     return (b + 1023) & ~(size_t)1023;
 }
 
-// packed FP32 master (W[out][in] then b per layer) -> chunked BF16 blob; one thread per element
-__global__ void k_pack_pipe(const float *master, uint8_t *blob, int K_in, int K0, int N, int L, int n_out)
+// E4M3 layer scales: s_l = the power of two with max|W_l| / s_l in (224, 448] (1 for a zero layer),
+// from the exponent of max|W_l| alone, so it is exact.  One block per hidden layer l >= 1.
+__global__ void k_fp8_scales(const float *master, uint8_t *blob, int K_in, int K0, int N, int L, int n_out)
 {
-    const size_t wb = pipe_w_bytes(K0, N, L);
+    const int l = 1 + blockIdx.x;
+    const float *W = master + (size_t)K_in * N + N + (size_t)(l - 1) * ((size_t)N * N + N);
+    float m = 0.0f;
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) m = fmaxf(m, fabsf(W[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wm[32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wm[w]);
+        float s = 1.0f;
+        if (m > 0.0f) {
+            int e;
+            const float fm = frexpf(m, &e);         // m = fm 2^e, fm in [0.5, 1)
+            // m / 2^k in (224, 448]: k = e - 9 when fm <= 7/8 (fm 512 <= 448), else e - 8
+            s = ldexpf(1.0f, fm <= 0.875f ? e - 9 : e - 8);
+        }
+        float *f32 = reinterpret_cast<float *>(blob + pipe_w_bytes(K0, N, L, true));
+        f32[pipe_f8_bias_off(N, n_out) + (size_t)L * N + l] = s;
+        if (l == 1) f32[pipe_f8_bias_off(N, n_out) + (size_t)L * N] = 1.0f;
+    }
+}
+
+// packed FP32 master (W[out][in] then b per layer) -> chunked blob; one thread per element
+__global__ void k_pack_pipe(const float *master, uint8_t *blob, int K_in, int K0, int N, int L, int n_out, bool f8)
+{
+    const size_t wb = pipe_w_bytes(K0, N, L, f8);
     float *f32 = reinterpret_cast<float *>(blob + wb);
-    const long long KH = N + kKC;
+    const size_t boff = pipe_f8_bias_off(N, n_out);
+    const long long KH = f8 ? N : N + kKC;
     const long long total_w = (long long)N * K0 + (long long)(L - 1) * N * KH;
-    const long long total = total_w + (long long)n_out * N + n_out;
+    const long long n_f32 = (long long)n_out * N + n_out + (f8 ? (long long)L * N : 0);
+    const long long total = total_w + n_f32;
     const long long off_out = (long long)K_in * N + N + (long long)(L - 1) * (N * N + N);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         if (e < total_w) {
@@ -98,6 +134,15 @@ __global__ void k_pack_pipe(const float *master, uint8_t *blob, int K_in, int K0
                 off_w = (long long)K_in * N + N + (long long)(l - 1) * (N * N + N);
             }
             const int n = (int)(j / K), k = (int)(j - (long long)n * K);
+            if (f8 && l > 0) {
+                const float sc = f32[boff + (size_t)L * N + l];
+                const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(master[off_w + (long long)n * Kin + k] / sc,
+                                                                    __NV_SATFINITE, __NV_E4M3);
+                const size_t dst = pipe_layer_off(K0, N, l, true) + (size_t)(k / 32) * N * 32 +
+                                   (size_t)(n >> 3) * 256 + ((k & 31) >> 4) * 128 + (n & 7) * 16 + (k & 15);
+                blob[dst] = (uint8_t)q;
+                continue;
+            }
             float v = 0.0f;
             if (k < Kin) {
                 v = master[off_w + (long long)n * Kin + k];
@@ -106,21 +151,35 @@ __global__ void k_pack_pipe(const float *master, uint8_t *blob, int K_in, int K0
                 const float hi = round_bf16(b);
                 v = k == Kin ? hi : b - hi;
             }
-            const size_t dst = pipe_layer_off(K0, N, l) + (size_t)(k / kKC) * N * kKC * 2 + cm_offset(n, k % kKC, kKC);
+            const size_t dst = pipe_layer_off(K0, N, l, false) + (size_t)(k / kKC) * N * kKC * 2 + cm_offset(n, k % kKC, kKC);
             *reinterpret_cast<__nv_bfloat16 *>(blob + dst) = __float2bfloat16_rn(v);
         } else {
             const long long q = e - total_w;
             if (q < (long long)n_out * N) f32[q] = round_bf16(master[off_out + q]);
-            else f32[q] = master[off_out + (long long)n_out * N + (q - (long long)n_out * N)];
+            else if (q < (long long)n_out * N + n_out) f32[q] = master[off_out + (long long)n_out * N + (q - (long long)n_out * N)];
+            else {
+                // E4M3 mode: the hidden biases, row l of [L x N] (row 0 is folded into layer 0)
+                const long long qq = q - ((long long)n_out * N + n_out);
+                const int l = (int)(qq / N), n = (int)(qq - (long long)l * N);
+                f32[boff + qq] = l == 0 ? 0.0f : master[(long long)K_in * N + N + (long long)(l - 1) * (N * N + N) + (long long)N * N + n];
+            }
         }
     }
 }
 
-cudaError_t launch_pack_pipe(const float *master, void *blob, int K_in, int K0, int N, int L, int n_out, cudaStream_t st)
+cudaError_t launch_pack_pipe(const float *master, void *blob, int K_in, int K0, int N, int L, int n_out, bool f8,
+                             cudaStream_t st)
 {
-    const long long total = (long long)N * K0 + (long long)(L - 1) * N * (N + kKC) + (long long)n_out * N + n_out;
+    if (f8 && L > 1) {
+        k_fp8_scales<<<L - 1, 256, 0, st>>>(master, (uint8_t *)blob, K_in, K0, N, L, n_out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const long long KH = f8 ? N : N + kKC;
+    const long long total = (long long)N * K0 + (long long)(L - 1) * N * KH + (long long)n_out * N + n_out +
+                            (f8 ? (long long)L * N : 0);
     k_pack_pipe<<<(int)std::min<long long>((total + 255) / 256, 4096), 256, 0, st>>>(master, (uint8_t *)blob, K_in, K0, N,
-                                                                                     L, n_out);
+                                                                                     L, n_out, f8);
     return cudaGetLastError();
 }
 
@@ -154,6 +213,13 @@ __device__ __forceinline__ void pipe_encode(const float *x, float *out)
 __device__ __forceinline__ uint32_t a_offset(int r, int k)
 {
     return (uint32_t)((k >> 3) * 2048 + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// The same layout for E4M3 activations: 16 columns per 16-byte slice, slice stride 2048; one
+// K = 32 MMA step again reads two slices (4 KB).
+__device__ __forceinline__ uint32_t a_offset8(int r, int k)
+{
+    return (uint32_t)((k >> 4) * 2048 + (r >> 3) * 128 + (r & 7) * 16 + (k & 15));
 }
 
 template <int K>
@@ -190,6 +256,28 @@ __device__ __forceinline__ void epi_convert(const uint32_t (&v)[32], uint8_t *A,
     }
 }
 
+// E4M3 activations: x = acc (AFF false: bias already in it) or acc * s + bias (AFF), then ReLU and
+// E4M3 of 32 columns, stored as A columns [c0, c0 + 32) of row r.
+template <bool AFF>
+__device__ __forceinline__ float epi_affine(uint32_t u, const float *bias, int j, float s)
+{
+    return AFF ? fmaf(__uint_as_float(u), s, bias[j]) : __uint_as_float(u);
+}
+
+template <bool AFF>
+__device__ __forceinline__ void epi_convert8(const uint32_t (&v)[32], const float *bias, float s, uint8_t *A, int r, int c0)
+{
+    uint32_t w[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int j = 4 * q;
+        w[q] = pack_e4m3_relu(epi_affine<AFF>(v[j], bias, j, s), epi_affine<AFF>(v[j + 1], bias, j + 1, s)) |
+               (pack_e4m3_relu(epi_affine<AFF>(v[j + 2], bias, j + 2, s), epi_affine<AFF>(v[j + 3], bias, j + 3, s)) << 16);
+    }
+    *reinterpret_cast<uint4 *>(A + a_offset8(r, c0)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4 *>(A + a_offset8(r, c0 + 16)) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
 // Last hidden layer: ReLU and BF16 rounding of 32 columns, folded into the NOUT outputs (w_out
 // rows of length N).
 template <int NOUT, int N>
@@ -201,6 +289,52 @@ __device__ __forceinline__ void epi_output(const uint32_t (&v)[32], const float 
         const float h0 = __uint_as_float(p << 16), h1 = __uint_as_float(p & 0xFFFF0000u);
 #pragma unroll
         for (int o = 0; o < NOUT; ++o) out[o] = fmaf(h1, wout[o * N + jj + 1], fmaf(h0, wout[o * N + jj], out[o]));
+    }
+}
+
+// The same with E4M3 rounding of the last hidden activation.
+template <int NOUT, int N, bool AFF>
+__device__ __forceinline__ void epi_output8(const uint32_t (&v)[32], const float *bias, float s, const float *wout, float *out)
+{
+#pragma unroll
+    for (int jj = 0; jj < 32; jj += 2) {
+        float h0, h1;
+        unpack_e4m3(pack_e4m3_relu(epi_affine<AFF>(v[jj], bias, jj, s), epi_affine<AFF>(v[jj + 1], bias, jj + 1, s)), h0, h1);
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) out[o] = fmaf(h1, wout[o * N + jj + 1], fmaf(h0, wout[o * N + jj], out[o]));
+    }
+}
+
+// One layer's epilogue over the N accumulator columns of this thread's row, TMEM loads
+// double-buffered (block b + 1 loads while block b is converted).  LAST: fold into the outputs;
+// otherwise write the next layer's A operand (BF16, or E4M3 when F8).
+template <int N, int NOUT, bool F8, bool AFF, bool LAST>
+__device__ __forceinline__ void epi_layer(uint32_t tmem_row, uint8_t *Ag, int r, const float *bias, float s,
+                                          const float *wout, float *out)
+{
+    uint32_t va[32], vb[32];
+    tmem_ld32(tmem_row, va);
+    tmem_wait_ld(va);
+#pragma unroll 1
+    for (int c0 = 0; c0 < N; c0 += 64) {
+        tmem_ld32(tmem_row + c0 + 32, vb);
+        if (LAST) {
+            if (F8) epi_output8<NOUT, N, AFF>(va, bias + c0, s, wout + c0, out);
+            else epi_output<NOUT, N>(va, wout + c0, out);
+        } else {
+            if (F8) epi_convert8<AFF>(va, bias + c0, s, Ag, r, c0);
+            else epi_convert(va, Ag, r, c0);
+        }
+        tmem_wait_ld(vb);
+        if (c0 + 64 < N) tmem_ld32(tmem_row + c0 + 64, va);
+        if (LAST) {
+            if (F8) epi_output8<NOUT, N, AFF>(vb, bias + c0 + 32, s, wout + c0 + 32, out);
+            else epi_output<NOUT, N>(vb, wout + c0 + 32, out);
+        } else {
+            if (F8) epi_convert8<AFF>(vb, bias + c0 + 32, s, Ag, r, c0 + 32);
+            else epi_convert(vb, Ag, r, c0 + 32);
+        }
+        if (c0 + 64 < N) tmem_wait_ld(va);
     }
 }
 
@@ -285,11 +419,11 @@ __device__ __forceinline__ int pipe_tile_type(const Workspace &ws, const MarchBu
     return t;
 }
 
-template <int N, int MODE>
+template <int N, int MODE, bool F8>
 __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuffers mb, PipeArgs a)
 {
     constexpr bool NERF = MODE == kModeShade || MODE == kModeMarch;
-    using SH = PipeShape<N, NERF>;
+    using SH = PipeShape<N, NERF, F8>;
     constexpr int K0 = SH::K0, S = SH::SLOTS, NOUT = SH::NOUT;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ PipeShared P;
@@ -304,7 +438,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
     uint8_t *A[2] = {smem, smem + SH::A_BYTES};
     uint8_t *ring = smem + 2 * SH::A_BYTES;
     float *f32s = reinterpret_cast<float *>(smem + SH::FIXED);       // output layer of one type
-    const int n_f32 = (int)pipe_f32_floats(N, NERF ? ws.nerf_hidden : ws.nedf_hidden, NOUT);
+    const int n_f32 = (int)pipe_f32_floats(N, L, NOUT, F8);
     volatile int *abort = &P.abort;
 
     if (warp == 9) tmem_alloc(&P.tmem_base, 2 * N);
@@ -333,8 +467,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
             for (unsigned long long tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x) {
                 const uint8_t *blob = a.blobs + (size_t)pipe_tile_type<MODE>(ws, mb, a, tile) * a.blob_stride;
                 for (int l = 0; l < L && !*abort; ++l) {
-                    const uint8_t *src = blob + pipe_layer_off(K0, N, l);
-                    const int nk = l == 0 ? K0 / kKC : N / kKC + 1;
+                    const uint8_t *src = blob + pipe_layer_off(K0, N, l, F8);
+                    const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
                     for (int c0 = 0; c0 < nk; c0 += SH::GC, ++q) {
                         const int s = (int)(q % S);
                         const uint32_t round = (uint32_t)(q / S);
@@ -353,14 +487,15 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
         // ------------------------------ MMA issuer ----------------------------------------------
         if (lane == 0) {
             unsigned long long q = 0, ja = 0;
-            const uint32_t idesc = idesc_bf16(128, N);
+            const uint32_t idesc = idesc_bf16(128, N), idesc8 = idesc_e4m3(128, N);
             bool issued_any = false;
             for (unsigned long long tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x) {
                 for (int l = 0; l < L && !*abort; ++l, ++ja) {
                     if (!pipe_wait(&P.a_ready, (uint32_t)(ja & 1u), abort, ws.status)) break;
                     tc_fence_after();
                     const uint32_t ax = smem_addr(A[0]), ay = smem_addr(A[1]);
-                    const int nk = l == 0 ? K0 / kKC : N / kKC + 1;
+                    const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
+                    const bool e4m3 = F8 && l > 0;
                     for (int c0 = 0; c0 < nk; c0 += SH::GC, ++q) {
                         const int s = (int)(q % S);
                         if (!pipe_wait(&w_full[s], (uint32_t)((q / S) & 1u), abort, ws.status)) break;
@@ -368,7 +503,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                         const uint32_t stage = smem_addr(ring + (size_t)s * SH::STAGE);
                         for (int c = c0; c < min(nk, c0 + SH::GC); ++c) {
                             const uint64_t bdesc = smem_desc(stage + (uint32_t)(c - c0) * SH::CHUNK, 128, 256);
-                            // a hidden layer's last chunk is its bias, against the constant-one block
+                            if (e4m3) {
+                                mma_e4m3(tmem, smem_desc(ax + c * 4096u, 2048, 128), bdesc, idesc8, c > 0 ? 1u : 0u);
+                                mma_e4m3(tmem + N, smem_desc(ay + c * 4096u, 2048, 128), bdesc, idesc8, c > 0 ? 1u : 0u);
+                                continue;
+                            }
+                            // a BF16 hidden layer's last chunk is its bias, against the constant-one block
                             const uint32_t ac = (uint32_t)(l > 0 && c == N / kKC ? SH::ONES / kKC : c) * 4096u;
                             mma_bf16(tmem, smem_desc(ax + ac, 2048, 128), bdesc, idesc, c > 0 ? 1u : 0u);
                             mma_bf16(tmem + N, smem_desc(ay + ac, 2048, 128), bdesc, idesc, c > 0 ? 1u : 0u);
@@ -391,9 +531,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
         const int R = g * kHalf + r;                  // row within the tile
         const uint32_t tmem_row = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(g * N);
         uint8_t *Ag = A[g];
-        // the constant-one block hidden-layer biases are folded into: columns ONES, ONES + 1 are 1
-        *reinterpret_cast<uint4 *>(Ag + a_offset(r, SH::ONES)) = make_uint4(pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
-        *reinterpret_cast<uint4 *>(Ag + a_offset(r, SH::ONES + 8)) = make_uint4(0u, 0u, 0u, 0u);
+        if (!F8) {
+            // the constant-one block BF16 hidden-layer biases are folded into: columns ONES, ONES + 1
+            *reinterpret_cast<uint4 *>(Ag + a_offset(r, SH::ONES)) = make_uint4(pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(Ag + a_offset(r, SH::ONES + 8)) = make_uint4(0u, 0u, 0u, 0u);
+        }
         unsigned long long jb = 0;
         const int ns = f.n_shade;
         int f32_type = -1;
@@ -406,7 +548,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                 // both groups are past every read of the previous type's block before it is replaced
                 asm volatile("bar.sync 3, 256;" ::: "memory");
                 const float4 *src = reinterpret_cast<const float4 *>(a.blobs + (size_t)t * a.blob_stride +
-                                                                     pipe_w_bytes(K0, N, L));
+                                                                     pipe_w_bytes(K0, N, L, F8));
                 for (int i = threadIdx.x; i < n_f32 / 4; i += 2 * kHalf)
                     reinterpret_cast<float4 *>(f32s)[i] = src[i];
                 asm volatile("bar.sync 3, 256;" ::: "memory");
@@ -514,38 +656,18 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                     break;
                 }
                 tc_fence_after();
+                // E4M3 layers after the first take their scale and bias here (layer 0's bias rides in its MMA)
+                const float *bias = f32 + pipe_f8_bias_off(N, NOUT) + (size_t)l * N;
+                const float sc = F8 && l > 0 ? f32[pipe_f8_bias_off(N, NOUT) + (size_t)L * N + l] : 1.0f;
                 if (l + 1 < L) {
-                    // 32-column blocks, double-buffered: block b + 1 is loading from TMEM while
-                    // block b gets bias, ReLU, BF16 and goes to the next layer's A operand
-                    uint32_t va[32], vb[32];
-                    tmem_ld32(tmem_row, va);
-                    tmem_wait_ld(va);
-#pragma unroll 1
-                    for (int c0 = 0; c0 < N; c0 += 64) {
-                        tmem_ld32(tmem_row + c0 + 32, vb);
-                        epi_convert(va, Ag, r, c0);
-                        tmem_wait_ld(vb);
-                        if (c0 + 64 < N) tmem_ld32(tmem_row + c0 + 64, va);
-                        epi_convert(vb, Ag, r, c0 + 32);
-                        if (c0 + 64 < N) tmem_wait_ld(va);
-                    }
+                    if (F8 && l > 0) epi_layer<N, NOUT, F8, true, false>(tmem_row, Ag, r, bias, sc, f32, out);
+                    else epi_layer<N, NOUT, F8, false, false>(tmem_row, Ag, r, bias, sc, f32, out);
                     fence_proxy_async_smem();
                     tc_fence_before();
                     mbar_arrive(&P.a_ready);
                 } else {
-                    const float *wout = f32;
-                    uint32_t va[32], vb[32];
-                    tmem_ld32(tmem_row, va);
-                    tmem_wait_ld(va);
-#pragma unroll 1
-                    for (int c0 = 0; c0 < N; c0 += 64) {
-                        tmem_ld32(tmem_row + c0 + 32, vb);
-                        epi_output<NOUT, N>(va, wout + c0, out);
-                        tmem_wait_ld(vb);
-                        if (c0 + 64 < N) tmem_ld32(tmem_row + c0 + 64, va);
-                        epi_output<NOUT, N>(vb, wout + c0 + 32, out);
-                        if (c0 + 64 < N) tmem_wait_ld(va);
-                    }
+                    if (F8 && l > 0) epi_layer<N, NOUT, F8, true, true>(tmem_row, Ag, r, bias, sc, f32, out);
+                    else epi_layer<N, NOUT, F8, false, true>(tmem_row, Ag, r, bias, sc, f32, out);
                     tc_fence_before();
                 }
             }
@@ -650,28 +772,30 @@ cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStre
     return cudaGetLastError();
 }
 
-template <int N, int MODE>
+template <int N, int MODE, bool F8>
 static cudaError_t launch_pipe_n(const Workspace &ws, const MarchBuffers &mb, const PipeArgs &a, int grid, cudaStream_t st)
 {
     constexpr bool NERF = MODE == kModeShade || MODE == kModeMarch;
     const int L = NERF ? ws.nerf_hidden : ws.nedf_hidden;
-    const size_t sm = PipeShape<N, NERF>::FIXED + ((pipe_f32_floats(N, L, NERF ? 3 : 2) * 4 + 1023) & ~(size_t)1023);
+    const size_t sm = PipeShape<N, NERF, F8>::FIXED + ((pipe_f32_floats(N, L, NERF ? 3 : 2, F8) * 4 + 1023) & ~(size_t)1023);
     if (sm > 227 * 1024 - 8192) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(k_pipe<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_pipe<N, MODE, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_pipe<N, MODE><<<grid, kPipeThreads, sm, st>>>(ws, mb, a);
+    k_pipe<N, MODE, F8><<<grid, kPipeThreads, sm, st>>>(ws, mb, a);
     return cudaGetLastError();
 }
 
+// precision 1: BF16 layers; precision 2: first layer BF16, later hidden layers E4M3
 template <int MODE>
 static cudaError_t launch_pipe(const Workspace &ws, const MarchBuffers &mb, const PipeArgs &a, int width, int grid,
                                cudaStream_t st)
 {
     if (grid < 1) return cudaSuccess;
+    const bool f8 = ws.precision == 2;
     switch (width) {
-    case 64: return launch_pipe_n<64, MODE>(ws, mb, a, grid, st);
-    case 128: return launch_pipe_n<128, MODE>(ws, mb, a, grid, st);
-    case 256: return launch_pipe_n<256, MODE>(ws, mb, a, grid, st);
+    case 64: return f8 ? launch_pipe_n<64, MODE, true>(ws, mb, a, grid, st) : launch_pipe_n<64, MODE, false>(ws, mb, a, grid, st);
+    case 128: return f8 ? launch_pipe_n<128, MODE, true>(ws, mb, a, grid, st) : launch_pipe_n<128, MODE, false>(ws, mb, a, grid, st);
+    case 256: return f8 ? launch_pipe_n<256, MODE, true>(ws, mb, a, grid, st) : launch_pipe_n<256, MODE, false>(ws, mb, a, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -10,6 +10,7 @@
 
 #include <cstdint>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace nedf {
@@ -38,6 +39,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ __forceinline__ constexpr uint32_t idesc_bf16(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor of kind::f8f6f4: D = F32, A = B = E4M3, both K-major, shape M x N.
+__host__ __device__ __forceinline__ constexpr uint32_t idesc_e4m3(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // ---- mbarrier ---------------------------------------------------------------------------------
@@ -139,6 +146,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
         : "memory");
 }
 
+// The same step with E4M3 operands (K = 32 per instruction: the same 32 bytes per row).
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrives once on bar when every MMA this thread issued before has completed.
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
@@ -190,6 +209,25 @@ __device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi)
     uint32_t d;
     asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
     return d;
+}
+
+// relu(lo), relu(hi) rounded to E4M3 (nearest even, saturating at 448) and packed, lo in the low
+// byte.
+__device__ __forceinline__ uint32_t pack_e4m3_relu(float lo, float hi)
+{
+    uint16_t d;
+    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// Two packed E4M3 values (low byte first) back to float.
+__device__ __forceinline__ void unpack_e4m3(uint32_t p, float &lo, float &hi)
+{
+    uint32_t h2;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"((uint16_t)p));
+    const __half2 v = *reinterpret_cast<const __half2 *>(&h2);
+    lo = __low2float(v);
+    hi = __high2float(v);
 }
 
 __device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }

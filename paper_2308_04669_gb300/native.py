@@ -22,7 +22,7 @@ _lib = C.CDLL(LIB_PATH)
 
 NEDF_OK, NEDF_ERR_ARG, NEDF_ERR_CUDA, NEDF_ERR_OOM = 0, -1, -2, -3
 NEDF_ERR_UNSUPPORTED, NEDF_ERR_CAPACITY, NEDF_ERR_TIMEOUT, NEDF_ERR_STATE = -4, -5, -6, -7
-PREC_FP32, PREC_BF16 = 0, 1
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 DEPTH_NEDF, DEPTH_MARCH = 0, 1
 MAX_LIGHTS = 32
 N_STAGES = 8
