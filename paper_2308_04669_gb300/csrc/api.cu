@@ -5,6 +5,7 @@
 // kernels; this file only moves and validates data.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -80,6 +81,7 @@ struct nedf_handle {
     bool graphs = true;
     cudaEvent_t ev[kStages + 1] = {};
     int last_launches = 0;
+    int stage_bytes[NEDF_N_SCHEDULE] = {0, 0, 0, 0, 0};   // tensor-core schedule (0 = default)
 };
 
 static thread_local std::string g_create_error;
@@ -166,6 +168,7 @@ static Workspace make_ws(nedf_handle *h)
     ws.depth_source = h->opt.depth_source;
     ws.nedf_tc = h->d_nedf_tc;
     ws.nedf_tc_stride = h->nedf_tc_stride;
+    for (int k = 0; k < NEDF_N_SCHEDULE; ++k) ws.pipe_stage_bytes[k] = h->stage_bytes[k];
     ws.nerf_tc = h->d_nerf_tc;
     ws.nerf_tc_stride = h->nerf_tc_stride;
     ws.fb_list[0] = h->d_fb[0];
@@ -682,6 +685,91 @@ int nedf_compose_get_stage_times(nedf_handle *h, float *ms, int n)
     if (!h->profiled) return fail(h, NEDF_ERR_STATE, "no profiled render");
     CK(h, cudaStreamSynchronize(h->stream));
     for (int i = 0; i < kStages; ++i) CK(h, cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
+    return NEDF_OK;
+}
+
+static void drop_graph(nedf_handle *h)
+{
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+}
+
+int nedf_compose_set_schedule(nedf_handle *h, const nedf_schedule *s)
+{
+    if (!h || !s) return fail(h, NEDF_ERR_ARG, "null argument");
+    for (int k = 0; k < NEDF_N_SCHEDULE; ++k) {
+        const int b = s->stage_bytes[k];
+        if (b != 0 && (b < 1024 || b > 262144 || b % 1024 != 0))
+            return fail(h, NEDF_ERR_ARG, "stage_bytes: 0 or a multiple of 1024 in [1024, 262144]");
+    }
+    for (int k = 0; k < NEDF_N_SCHEDULE; ++k) h->stage_bytes[k] = s->stage_bytes[k];
+    drop_graph(h);
+    return NEDF_OK;
+}
+
+int nedf_compose_get_schedule(nedf_handle *h, nedf_schedule *s)
+{
+    if (!h || !s) return fail(h, NEDF_ERR_ARG, "null argument");
+    for (int k = 0; k < NEDF_N_SCHEDULE; ++k) {
+        s->stage_bytes[k] = h->stage_bytes[k];
+        s->tuned_ms[k] = 0.0f;
+    }
+    return NEDF_OK;
+}
+
+int nedf_compose_autotune(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights, int reps,
+                          nedf_schedule *chosen)
+{
+    int r = check_frame_args(h, cam, lights, n_lights);
+    if (r != NEDF_OK) return r;
+    if (reps < 1) return fail(h, NEDF_ERR_ARG, "reps < 1");
+    if (h->cfg.precision != NEDF_PREC_FP32) {
+        static const int cand[4] = {8192, 16384, 32768, 65536};
+        // stage index of each tuned kernel: Step-2 shading, Step-1 NeDF, Step-3 NeDF
+        static const int kern[3] = {0, 2, 3}, stage[3] = {4, 2, 6};
+        float best[3] = {1e30f, 1e30f, 1e30f};
+        int pick[3] = {cand[1], cand[1], cand[1]};
+        const bool was_profiling = h->profiling;
+        r = nedf_compose_set_profiling(h, 1);
+        if (r != NEDF_OK) return r;
+        for (int c = 0; c < 4; ++c) {
+            for (int k = 0; k < NEDF_N_SCHEDULE; ++k) h->stage_bytes[k] = cand[c];
+            drop_graph(h);
+            float t[3] = {1e30f, 1e30f, 1e30f};
+            for (int i = 0; i <= reps; ++i) {              // the first render captures the graph
+                r = render_impl(h, cam, lights, n_lights);
+                if (r != NEDF_OK) return r;
+                float ms[kStages];
+                r = nedf_compose_get_stage_times(h, ms, kStages);
+                if (r != NEDF_OK) return r;
+                if (i == 0) continue;
+                for (int j = 0; j < 3; ++j) t[j] = std::min(t[j], ms[stage[j]]);
+            }
+            for (int j = 0; j < 3; ++j)
+                if (t[j] < best[j]) {
+                    best[j] = t[j];
+                    pick[j] = cand[c];
+                }
+        }
+        h->stage_bytes[0] = pick[0];
+        h->stage_bytes[1] = pick[0];
+        h->stage_bytes[2] = pick[1];
+        h->stage_bytes[3] = pick[2];
+        h->stage_bytes[4] = pick[1];
+        drop_graph(h);
+        h->profiling = was_profiling;
+        if (chosen) {
+            for (int k = 0; k < NEDF_N_SCHEDULE; ++k) {
+                chosen->stage_bytes[k] = h->stage_bytes[k];
+                chosen->tuned_ms[k] = 0.0f;
+            }
+            for (int j = 0; j < 3; ++j) chosen->tuned_ms[kern[j]] = best[j];
+        }
+        return NEDF_OK;
+    }
+    if (chosen) return nedf_compose_get_schedule(h, chosen);
     return NEDF_OK;
 }
 

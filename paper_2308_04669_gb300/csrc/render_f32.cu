@@ -496,9 +496,15 @@ cudaError_t launch_frame(FrameLaunch &L)
     const int nedf_rows = tc_nedf ? kPipeTileRows : kTileRows;
     // the engine shades (128 / n_shade) pixels per 128-row half, two halves per tile
     const int shade_ppt = tc_shade ? 2 * (kTcTileRows / L.n_shade) : kTileRows / L.n_shade;
-    // external records: inside a captured graph they still mark the stage boundaries for timing
+    // inside a captured graph the records are external (they still mark the stage boundaries for
+    // timing when the graph runs); on an uncaptured stream they are plain records
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (L.events) cudaStreamIsCapturing(st, &cap);
     auto mark = [&]() {
-        if (L.events) cudaEventRecordWithFlags(L.events[stage], st, cudaEventRecordExternal);
+        if (L.events) {
+            if (cap == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(L.events[stage], st, cudaEventRecordExternal);
+            else cudaEventRecord(L.events[stage], st);
+        }
         ++stage;
     };
     mark();

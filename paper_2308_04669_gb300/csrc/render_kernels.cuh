@@ -82,6 +82,9 @@ struct Workspace {
     int lg_G;
     int max_inst;
     uint32_t *scan_tmp;          // block sums of the grid scan
+    // tensor-core schedule: weight bytes per bulk copy of each engine mode (shade, march colour,
+    // primary NeDF, shadow NeDF, NeDF query); picked by the autotuner or set by the caller
+    int pipe_stage_bytes[5];
 };
 
 struct LightCam {

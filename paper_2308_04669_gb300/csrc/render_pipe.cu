@@ -35,7 +35,10 @@ constexpr int kPipeRows = 256;              // rows per tile (two MMA halves of 
 constexpr int kHalf = 128;
 constexpr int kPipeThreads = 320;           // 8 epilogue warps, producer, MMA issuer
 constexpr int kKC = 16;                     // K columns per weight chunk (one MMA K step)
-constexpr int kStageBytes = 16384;          // weight bytes per bulk copy
+// A bulk copy costs its issuing thread a few hundred cycles whatever its size, so weights move in
+// stages of several chunks (one copy, one full and one empty barrier phase each).  The stage size
+// is a run-time schedule parameter, the autotuner's; a shape's ring bytes are fixed.
+constexpr int kDefaultStageBytes = 16384;
 
 enum PipeMode { kModeShade = 0, kModeMarch = 1, kModePrimary = 2, kModeShadow = 3, kModeQuery = 4 };
 
@@ -51,12 +54,11 @@ struct PipeShape {
     static constexpr int ONES = K0 > N ? K0 : N;
     static constexpr int A_ROW = F8 ? (2 * K0 > N ? 2 * K0 : N) : 2 * (ONES + kKC);   // A bytes per row
     static constexpr int CHUNK = N * 32;                             // N x 16 BF16 or N x 32 E4M3
-    static constexpr int GC = kStageBytes / CHUNK;                   // chunks per stage
-    static constexpr int STAGE = GC * CHUNK;
-    static constexpr int SLOTS = F8 ? (N == 64 ? 4 : 8) : (N == 128 ? 6 : 4);   // ring stages
+    static constexpr int RING = F8 ? (N == 64 ? 65536 : 131072) : (N == 128 ? 98304 : 65536);   // ring bytes
+    static constexpr int SMAX = RING / CHUNK;                        // stages at one chunk per stage
     static constexpr int NOUT = NERF ? 3 : 2;
     static constexpr size_t A_BYTES = (size_t)kHalf * A_ROW;
-    static constexpr size_t FIXED = 2 * A_BYTES + (size_t)SLOTS * STAGE;   // + the fp32 block (depends on L)
+    static constexpr size_t FIXED = 2 * A_BYTES + (size_t)RING;      // + the fp32 block (depends on L)
 };
 
 // ---- weight blobs: per layer, chunks of 32 bytes of input per output row, each chunk N rows in the
@@ -339,6 +341,7 @@ __device__ __forceinline__ void epi_layer(uint32_t tmem_row, uint8_t *Ag, int r,
 }
 
 struct PipeArgs {
+    int stage_bytes;              // schedule: weight bytes per bulk copy
     const uint8_t *blobs;
     size_t blob_stride;
     int npix;
@@ -424,10 +427,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
 {
     constexpr bool NERF = MODE == kModeShade || MODE == kModeMarch;
     using SH = PipeShape<N, NERF, F8>;
-    constexpr int K0 = SH::K0, S = SH::SLOTS, NOUT = SH::NOUT;
+    constexpr int K0 = SH::K0, NOUT = SH::NOUT;
+    // schedule: GC chunks per stage (at least 2 stages in the ring), S stages
+    const int GC = max(1, min(a.stage_bytes / SH::CHUNK, SH::SMAX / 2));
+    const int STAGE = GC * SH::CHUNK, S = SH::RING / STAGE;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ PipeShared P;
-    __shared__ uint64_t w_full[S], w_empty[S];
+    __shared__ uint64_t w_full[SH::SMAX], w_empty[SH::SMAX];
     // tail scratch of the two groups (shading composite; plain-method per-pair sums)
     __shared__ float t_sig[kPipeRows], t_rgb[kPipeRows][3];
     __shared__ uint32_t t_key[kPipeRows];
@@ -469,13 +475,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                 for (int l = 0; l < L && !*abort; ++l) {
                     const uint8_t *src = blob + pipe_layer_off(K0, N, l, F8);
                     const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
-                    for (int c0 = 0; c0 < nk; c0 += SH::GC, ++q) {
+                    for (int c0 = 0; c0 < nk; c0 += GC, ++q) {
                         const int s = (int)(q % S);
                         const uint32_t round = (uint32_t)(q / S);
-                        const uint32_t bytes = (uint32_t)(min(SH::GC, nk - c0) * SH::CHUNK);
+                        const uint32_t bytes = (uint32_t)(min(GC, nk - c0) * SH::CHUNK);
                         if (!pipe_wait(&w_empty[s], (round & 1u) ^ 1u, abort, ws.status)) break;
                         mbar_arrive_expect_tx(&w_full[s], bytes);
-                        bulk_g2s(ring + (size_t)s * SH::STAGE, src + (size_t)c0 * SH::CHUNK, bytes, &w_full[s]);
+                        bulk_g2s(ring + (size_t)s * STAGE, src + (size_t)c0 * SH::CHUNK, bytes, &w_full[s]);
                     }
                 }
             }
@@ -496,12 +502,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                     const uint32_t ax = smem_addr(A[0]), ay = smem_addr(A[1]);
                     const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
                     const bool e4m3 = F8 && l > 0;
-                    for (int c0 = 0; c0 < nk; c0 += SH::GC, ++q) {
+                    for (int c0 = 0; c0 < nk; c0 += GC, ++q) {
                         const int s = (int)(q % S);
                         if (!pipe_wait(&w_full[s], (uint32_t)((q / S) & 1u), abort, ws.status)) break;
                         tc_fence_after();
-                        const uint32_t stage = smem_addr(ring + (size_t)s * SH::STAGE);
-                        for (int c = c0; c < min(nk, c0 + SH::GC); ++c) {
+                        const uint32_t stage = smem_addr(ring + (size_t)s * STAGE);
+                        for (int c = c0; c < min(nk, c0 + GC); ++c) {
                             const uint64_t bdesc = smem_desc(stage + (uint32_t)(c - c0) * SH::CHUNK, 128, 256);
                             if (e4m3) {
                                 mma_e4m3(tmem, smem_desc(ax + c * 4096u, 2048, 128), bdesc, idesc8, c > 0 ? 1u : 0u);
@@ -792,10 +798,12 @@ static cudaError_t launch_pipe(const Workspace &ws, const MarchBuffers &mb, cons
 {
     if (grid < 1) return cudaSuccess;
     const bool f8 = ws.precision == 2;
+    PipeArgs args = a;
+    args.stage_bytes = ws.pipe_stage_bytes[MODE] > 0 ? ws.pipe_stage_bytes[MODE] : kDefaultStageBytes;
     switch (width) {
-    case 64: return f8 ? launch_pipe_n<64, MODE, true>(ws, mb, a, grid, st) : launch_pipe_n<64, MODE, false>(ws, mb, a, grid, st);
-    case 128: return f8 ? launch_pipe_n<128, MODE, true>(ws, mb, a, grid, st) : launch_pipe_n<128, MODE, false>(ws, mb, a, grid, st);
-    case 256: return f8 ? launch_pipe_n<256, MODE, true>(ws, mb, a, grid, st) : launch_pipe_n<256, MODE, false>(ws, mb, a, grid, st);
+    case 64: return f8 ? launch_pipe_n<64, MODE, true>(ws, mb, args, grid, st) : launch_pipe_n<64, MODE, false>(ws, mb, args, grid, st);
+    case 128: return f8 ? launch_pipe_n<128, MODE, true>(ws, mb, args, grid, st) : launch_pipe_n<128, MODE, false>(ws, mb, args, grid, st);
+    case 256: return f8 ? launch_pipe_n<256, MODE, true>(ws, mb, args, grid, st) : launch_pipe_n<256, MODE, false>(ws, mb, args, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }

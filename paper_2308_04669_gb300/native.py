@@ -60,6 +60,14 @@ class Light(C.Structure):
     _fields_ = [("pos", C.c_float * 3)]
 
 
+N_SCHEDULE = 5
+SCHEDULE_KERNELS = ("step2_shade", "march_colour", "step1_nedf", "step3_nedf", "nedf_query")
+
+
+class Schedule(C.Structure):
+    _fields_ = [("stage_bytes", C.c_int * N_SCHEDULE), ("tuned_ms", C.c_float * N_SCHEDULE)]
+
+
 class FrameStats(C.Structure):
     _fields_ = [("primary_pairs", C.c_int64), ("shadow_pairs", C.c_int64), ("hit_pixels", C.c_int64),
                 ("fallback_pairs", C.c_int64), ("kernel_launches", C.c_int64), ("status", C.c_uint32)]
@@ -86,6 +94,10 @@ EXPORTS = {
     "nedf_compose_stage_name": ([C.c_int], C.c_char_p),
     "nedf_compose_set_profiling": ([_H, C.c_int], C.c_int),
     "nedf_compose_get_stage_times": ([_H, _fp, C.c_int], C.c_int),
+    "nedf_compose_set_schedule": ([_H, C.POINTER(Schedule)], C.c_int),
+    "nedf_compose_get_schedule": ([_H, C.POINTER(Schedule)], C.c_int),
+    "nedf_compose_autotune": ([_H, C.POINTER(Camera), C.POINTER(Light), C.c_int, C.c_int, C.POINTER(Schedule)],
+                              C.c_int),
     "nedf_compose_nedf_query": ([_H, C.c_int, C.c_int, _vp, _vp, _vp], C.c_int),
     "nedf_compose_depth_noalloc": ([C.c_int, C.c_int, C.POINTER(Camera), C.c_int, _vp, C.c_int, _fp, C.c_int, C.c_int,
                                     _vp, _vp, _vp, _vp], C.c_int),
@@ -264,6 +276,26 @@ class Renderer:
 
     def render_march(self, cam, n_samples, early_stop, rgba):
         return self._check(_lib.nedf_compose_render_march(self.h, C.byref(cam), n_samples, early_stop, _ptr(rgba)))
+
+    def set_schedule(self, stage_bytes):
+        s = Schedule()
+        for k, b in enumerate(stage_bytes):
+            s.stage_bytes[k] = int(b)
+        return self._check(_lib.nedf_compose_set_schedule(self.h, C.byref(s)))
+
+    def get_schedule(self) -> dict:
+        s = Schedule()
+        self._check(_lib.nedf_compose_get_schedule(self.h, C.byref(s)))
+        return {k: s.stage_bytes[i] for i, k in enumerate(SCHEDULE_KERNELS)}
+
+    def autotune(self, cam, lights, reps=3) -> dict:
+        """Picks the stage size of every tensor-core kernel by timing this frame; returns
+        {kernel: {"stage_bytes": b, "ms": best time (0 if not timed)}}."""
+        s = Schedule()
+        la, nl = lights
+        self._check(_lib.nedf_compose_autotune(self.h, C.byref(cam), la, nl, reps, C.byref(s)))
+        return {k: {"stage_bytes": s.stage_bytes[i], "ms": round(float(s.tuned_ms[i]), 4)}
+                for i, k in enumerate(SCHEDULE_KERNELS)}
 
     def nedf_query(self, type_, o, d, out):
         return self._check(_lib.nedf_compose_nedf_query(self.h, type_, int(o.shape[0]), _ptr(o), _ptr(d), _ptr(out)))

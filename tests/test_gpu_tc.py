@@ -134,3 +134,40 @@ def test_bf16_plain_method_frame(orc):
     assert ok.mean() > 0.995 and (o[:, 3] > 0.5).sum() > 10
     es = _march_gpu(sc, 64, 1, precision=native.PREC_BF16)
     assert np.abs(es - g).max() < 2e-3
+
+
+def test_schedule_changes_timing_not_results():
+    """The stage size of the weight stream (set by hand or by the autotuner) never changes a
+    frame: every schedule gives bitwise the same depth, id and colour buffers."""
+    import torch
+    from paper_2308_04669_gb300 import native
+    sc = sg.three_types_scene(128, 128)
+    for prec in (native.PREC_BF16, native.PREC_FP8):
+        r = native.renderer_for(sc, precision=prec)
+        o = r.get_options()
+        o.fallback_conf, o.refine_steps, o.outlier_resample = 0.9, 4, 1
+        r.set_options(o)
+        cam, li = r.camera(sc.eye, sc.target, sc.fov_deg), r.lights(sc.lights)
+        n = sc.W * sc.H
+
+        def frame():
+            d = torch.empty(n, device="cuda"); i = torch.empty(n, dtype=torch.int32, device="cuda")
+            c = torch.empty(n, 4, device="cuda")
+            r.render(cam, li, d, i, c, None, None)
+            torch.cuda.synchronize()
+            return d.cpu().numpy(), i.cpu().numpy(), c.cpu().numpy()
+
+        ref = frame()
+        for b in (8192, 32768, 65536, 1024):
+            r.set_schedule([b] * native.N_SCHEDULE)
+            got = frame()
+            assert all(np.array_equal(x, y) for x, y in zip(ref, got)), b
+        tuned = r.autotune(cam, li, reps=1)
+        assert all(v["stage_bytes"] in (8192, 16384, 32768, 65536) for v in tuned.values())
+        assert tuned["step2_shade"]["ms"] > 0 and tuned["step1_nedf"]["ms"] > 0
+        assert r.get_schedule()["step3_nedf"] == tuned["step3_nedf"]["stage_bytes"]
+        got = frame()
+        assert all(np.array_equal(x, y) for x, y in zip(ref, got))
+        with pytest.raises(native.NedfError):
+            r.set_schedule([1000] * native.N_SCHEDULE)
+        r.close()
