@@ -302,17 +302,30 @@ __global__ void k_resolve(Workspace ws, int npix)
         unsigned long long k = ws.keys[p];
         float D = __int_as_float(0x7f800000);
         uint32_t id = kNoId;
-        if (k != ~0ull) {
+        const bool hit = k != ~0ull;
+        uint32_t t = 0xFFFFFFFFu;
+        if (hit) {
             D = __uint_as_float((uint32_t)(k >> 32));
             id = (uint32_t)(k & 0xffffffffu);
-            uint32_t t = ws.inst[id].type;
-            unsigned long long pos = atomicAdd(&ws.cnt->h_count[t], 1ull);
-            ws.hlist[(size_t)t * npix + pos] = (uint32_t)p;
-            atomicAdd(&ws.cnt->hit_pixels, 1ull);
+            t = ws.inst[id].type;
         }
+        // one atomic per (warp, type) and one per warp for the hit count: a few types share
+        // their counters across the whole frame
+        const unsigned act = __activemask();
+        const int lane = threadIdx.x & 31;
+        const unsigned peers = __match_any_sync(act, t);
+        const unsigned hits = __ballot_sync(act, hit);
+        if (hit) {
+            const int leader = __ffs(peers) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(&ws.cnt->h_count[t], (unsigned long long)__popc(peers));
+            base = __shfl_sync(peers, base, leader);
+            ws.hlist[(size_t)t * npix + base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)p;
+        }
+        if (lane == __ffs(act) - 1 && hits) atomicAdd(&ws.cnt->hit_pixels, (unsigned long long)__popc(hits));
         ws.depth[p] = D;
         ws.id[p] = id;
-        ws.rgba[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!hit) ws.rgba[p] = make_float4(0.f, 0.f, 0.f, 0.f);   // hit pixels are written by Step 2
     }
     (void)f;
 }

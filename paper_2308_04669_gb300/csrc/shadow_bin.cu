@@ -227,14 +227,24 @@ template <int PASS>
 __global__ void __launch_bounds__(256) k_bin_shadow_grid(Workspace ws, int npix)
 {
     __shared__ unsigned long long cnt_t[kMaxTypes];
+    __shared__ unsigned long long hit_pre[kMaxTypes + 1];   // first flat hit index of each type's list
     const DevFrame &f = *ws.frame;
-    const int nl = f.n_lights, n_inst = f.n_inst, G = ws.lg_G;
-    const long long n_rays = (long long)npix * nl;
+    const int nl = f.n_lights, n_inst = f.n_inst, G = ws.lg_G, n_types = f.n_types;
     const int lane = threadIdx.x & 31;
-    if (PASS == 0) {
+    if (PASS == 0)
         for (int k = threadIdx.x; k < kMaxTypes; k += blockDim.x) cnt_t[k] = 0;
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long acc = 0;
+        for (int t = 0; t < n_types; ++t) {
+            hit_pre[t] = acc;
+            acc += ws.cnt->h_count[t];
+        }
+        hit_pre[n_types] = acc;
     }
+    __syncthreads();
+    // shadow rays only for pixels with a hit: the per-type hit lists of the resolve, one after
+    // another, each pixel's lights adjacent
+    const long long n_rays = (long long)hit_pre[n_types] * nl;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < n_rays; base += (long long)gridDim.x * blockDim.x) {
         const long long rr = base + threadIdx.x;
         bool valid = rr < n_rays;
@@ -245,9 +255,11 @@ __global__ void __launch_bounds__(256) k_bin_shadow_grid(Workspace ws, int npix)
         uint32_t c0 = 0;
         bool grid = false;
         if (valid) {
-            pix = (uint32_t)(rr / nl);
-            l = (uint32_t)(rr - (long long)pix * nl);
-            valid = ws.id[pix] != kNoId;
+            const unsigned long long h = (unsigned long long)(rr / nl);
+            l = (uint32_t)(rr - (long long)h * nl);
+            int t = 0;
+            while (t + 1 < n_types && hit_pre[t + 1] <= h) ++t;
+            pix = ws.hlist[(size_t)t * npix + (h - hit_pre[t])];
         }
         if (valid) {
             V3 oc, dc;
@@ -286,7 +298,11 @@ __global__ void __launch_bounds__(256) k_bin_shadow_grid(Workspace ws, int npix)
                 keep = bound_chord(ol, dl, ws.types[ty].rb, ch) && (ch.te * I.s < ell);
             }
             if (PASS == 0) {
-                if (keep) atomicAdd(&cnt_t[ty], 1ull);
+                const unsigned active = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const unsigned peers = __match_any_sync(active, ty);
+                    if (lane == __ffs(peers) - 1) atomicAdd(&cnt_t[ty], (unsigned long long)__popc(peers));
+                }
             } else {
                 unsigned active = __ballot_sync(0xffffffffu, keep);
                 if (keep) {
