@@ -752,6 +752,289 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
 }
 
 // ---------------------------------------------------------------------------------------------------
+// NeDF engine with two tiles in flight (widths 64 and 128): TMEM holds the accumulators of two
+// 256-row tiles (slots), so the tensor pipe works on one slot's layer while the epilogue warps
+// convert the other slot's previous layer, and a slot's tail and next set-up overlap the other
+// slot's MMAs.  The CTA's tiles alternate between the slots; the producer, the MMA issuer and the
+// epilogue walk the same sequence (round r: for each layer l, slot 0 then slot 1).
+// ---------------------------------------------------------------------------------------------------
+template <int N, bool F8>
+struct NedfShape2 {
+    using B = PipeShape<N, false, F8>;
+    static constexpr int RING = F8 ? 131072 : 65536;
+    static constexpr int SMAX = RING / B::CHUNK;
+    static constexpr size_t FIXED = 4 * B::A_BYTES + (size_t)RING;          // + two fp32 blocks
+};
+
+// Pair index, validity and local ray of row R of a NeDF tile (Step-1 pairs, Step-3 pairs or caller
+// queries); the set-up uses it to encode the row and the tail recomputes it instead of keeping it.
+template <int MODE>
+__device__ __forceinline__ void nedf_row(const Workspace &ws, const DevFrame &f, const PipeArgs &a, const DevType &T,
+                                         int t, unsigned long long tile, int R, unsigned long long &idx, bool &valid,
+                                         PairRay &pr)
+{
+    pr.kept = false;
+    valid = false;
+    if (MODE == kModeQuery) {
+        idx = tile * kPipeRows + R;
+        valid = idx < (unsigned long long)a.qn;
+        if (valid) {
+            pr.ol = v3(a.qo[3 * idx], a.qo[3 * idx + 1], a.qo[3 * idx + 2]);
+            pr.dl = normalized(v3(a.qd[3 * idx], a.qd[3 * idx + 1], a.qd[3 * idx + 2]));
+            Chord ch;
+            pr.kept = bound_chord(pr.ol, pr.dl, T.rb, ch);
+            pr.te = ch.te; pr.tx = ch.tx; pr.tp = ch.tp;
+        }
+    } else {
+        const Counters &C = *ws.cnt;
+        const unsigned long long *toff = MODE == kModePrimary ? C.p_tile : C.s_tile;
+        const unsigned long long *poff = MODE == kModePrimary ? C.p_off : C.s_off;
+        idx = poff[t] + (tile - toff[t]) * kPipeRows + R;
+        valid = idx < poff[t + 1];
+        if (valid) setup_pair_ray(ws, f, MODE == kModeShadow, (MODE == kModePrimary ? ws.ppairs : ws.spairs)[idx], T.rb, pr);
+    }
+}
+
+template <int N, int MODE, bool F8>
+__global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBuffers mb, PipeArgs a)
+{
+    using SH = PipeShape<N, false, F8>;
+    using S2 = NedfShape2<N, F8>;
+    constexpr int K0 = SH::K0, NOUT = 2;
+    const int GC = max(1, min(a.stage_bytes / SH::CHUNK, S2::SMAX / 2));
+    const int STAGE = GC * SH::CHUNK, S = S2::RING / STAGE;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t a_ready[2], acc_full[2], fin;
+    __shared__ uint64_t w_full[S2::SMAX], w_empty[S2::SMAX];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = ws.nedf_hidden;
+    uint8_t *ring = smem + 4 * SH::A_BYTES;
+    const int n_f32 = (int)pipe_f32_floats(N, L, NOUT, F8);
+    const size_t f32_bytes = ((size_t)n_f32 * 4 + 1023) & ~(size_t)1023;
+    volatile int *abort = &abort_flag;
+
+    if (warp == 9) tmem_alloc(&tmem_base, 4 * N);
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < 2; ++j) {
+            mbar_init(&a_ready[j], 2 * kHalf);
+            mbar_init(&acc_full[j], 1);
+        }
+        mbar_init(&fin, 1);
+        for (int q = 0; q < S; ++q) {
+            mbar_init(&w_full[q], 1);
+            mbar_init(&w_empty[q], 1);
+        }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const unsigned long long n_tiles = pipe_n_tiles<N, MODE>(ws, mb, a);
+    const unsigned long long gx = gridDim.x;
+    const DevFrame &f = *ws.frame;
+    auto A_of = [&](int s, int h) { return smem + (size_t)(2 * s + h) * SH::A_BYTES; };
+
+    if (warp == 8) {
+        // ------------------------------ producer ------------------------------------------------
+        if (lane == 0) {
+            unsigned long long q = 0;
+            for (unsigned long long t0 = blockIdx.x; t0 < n_tiles && !*abort; t0 += 2 * gx) {
+                for (int l = 0; l < L && !*abort; ++l)
+                    for (int s = 0; s < 2 && !*abort; ++s) {
+                        const unsigned long long tile = t0 + s * gx;
+                        if (tile >= n_tiles) continue;
+                        const uint8_t *src = a.blobs + (size_t)pipe_tile_type<MODE>(ws, mb, a, tile) * a.blob_stride +
+                                             pipe_layer_off(K0, N, l, F8);
+                        const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
+                        for (int c0 = 0; c0 < nk; c0 += GC, ++q) {
+                            const int st = (int)(q % S);
+                            const uint32_t round = (uint32_t)(q / S);
+                            const uint32_t bytes = (uint32_t)(min(GC, nk - c0) * SH::CHUNK);
+                            if (!pipe_wait(&w_empty[st], (round & 1u) ^ 1u, abort, ws.status)) break;
+                            mbar_arrive_expect_tx(&w_full[st], bytes);
+                            bulk_g2s(ring + (size_t)st * STAGE, src + (size_t)c0 * SH::CHUNK, bytes, &w_full[st]);
+                        }
+                    }
+            }
+            const unsigned long long q0 = q > (unsigned long long)S ? q - S : 0;
+            for (unsigned long long k = q0; k < q; ++k) pipe_drain(&w_full[k % S], (uint32_t)((k / S) & 1u), ws.status);
+        }
+    } else if (warp == 9) {
+        // ------------------------------ MMA issuer ----------------------------------------------
+        if (lane == 0) {
+            unsigned long long q = 0, ja[2] = {0, 0};
+            const uint32_t idesc = idesc_bf16(128, N), idesc8 = idesc_e4m3(128, N);
+            bool issued_any = false;
+            for (unsigned long long t0 = blockIdx.x; t0 < n_tiles && !*abort; t0 += 2 * gx) {
+                for (int l = 0; l < L && !*abort; ++l)
+                    for (int s = 0; s < 2 && !*abort; ++s) {
+                        if (t0 + s * gx >= n_tiles) continue;
+                        if (!pipe_wait(&a_ready[s], (uint32_t)(ja[s]++ & 1u), abort, ws.status)) break;
+                        tc_fence_after();
+                        const uint32_t ax = smem_addr(A_of(s, 0)), ay = smem_addr(A_of(s, 1));
+                        const uint32_t dx = tmem + (uint32_t)(2 * s) * N, dy = dx + N;
+                        const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
+                        const bool e4m3 = F8 && l > 0;
+                        for (int c0 = 0; c0 < nk; c0 += GC, ++q) {
+                            const int st = (int)(q % S);
+                            if (!pipe_wait(&w_full[st], (uint32_t)((q / S) & 1u), abort, ws.status)) break;
+                            tc_fence_after();
+                            const uint32_t stage = smem_addr(ring + (size_t)st * STAGE);
+                            for (int c = c0; c < min(nk, c0 + GC); ++c) {
+                                const uint64_t bdesc = smem_desc(stage + (uint32_t)(c - c0) * SH::CHUNK, 128, 256);
+                                if (e4m3) {
+                                    mma_e4m3(dx, smem_desc(ax + c * 4096u, 2048, 128), bdesc, idesc8, c > 0 ? 1u : 0u);
+                                    mma_e4m3(dy, smem_desc(ay + c * 4096u, 2048, 128), bdesc, idesc8, c > 0 ? 1u : 0u);
+                                } else {
+                                    const uint32_t ac = (uint32_t)(l > 0 && c == N / kKC ? SH::ONES / kKC : c) * 4096u;
+                                    mma_bf16(dx, smem_desc(ax + ac, 2048, 128), bdesc, idesc, c > 0 ? 1u : 0u);
+                                    mma_bf16(dy, smem_desc(ay + ac, 2048, 128), bdesc, idesc, c > 0 ? 1u : 0u);
+                                }
+                            }
+                            mma_commit(&w_empty[st]);
+                            issued_any = true;
+                        }
+                        mma_commit(&acc_full[s]);
+                    }
+            }
+            if (issued_any) {
+                mma_commit(&fin);
+                pipe_drain(&fin, 0u, ws.status);
+            }
+        }
+    } else {
+        // ------------------------------ epilogue groups -----------------------------------------
+        const int g = warp >> 2;                      // half: rows 0..127 (X) or 128..255 (Y)
+        const int r = threadIdx.x & 127;
+        const int R = g * kHalf + r;
+        const uint32_t lane_q = (uint32_t)((warp & 3) * 32) << 16;
+        float *f32s[2] = {reinterpret_cast<float *>(smem + S2::FIXED),
+                          reinterpret_cast<float *>(smem + S2::FIXED + f32_bytes)};
+        int f32_type[2] = {-1, -1};
+        unsigned long long jb[2] = {0, 0};
+        if (!F8)
+            for (int s = 0; s < 2; ++s) {
+                *reinterpret_cast<uint4 *>(A_of(s, g) + a_offset(r, SH::ONES)) = make_uint4(pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
+                *reinterpret_cast<uint4 *>(A_of(s, g) + a_offset(r, SH::ONES + 8)) = make_uint4(0u, 0u, 0u, 0u);
+            }
+        // set-up of slot s for `tile`: its type's fp32 block, the encoded rows, then a_ready
+        auto setup = [&](int s, unsigned long long tile) {
+            const int t = pipe_tile_type<MODE>(ws, mb, a, tile);
+            if (t != f32_type[s]) {
+                asm volatile("bar.sync 3, 256;" ::: "memory");   // every reader of the old block is done
+                const float4 *src = reinterpret_cast<const float4 *>(a.blobs + (size_t)t * a.blob_stride +
+                                                                     pipe_w_bytes(K0, N, L, F8));
+                for (int i = threadIdx.x; i < n_f32 / 4; i += 2 * kHalf) reinterpret_cast<float4 *>(f32s[s])[i] = src[i];
+                asm volatile("bar.sync 3, 256;" ::: "memory");
+                f32_type[s] = t;
+            }
+            const DevType T = ws.types[t];
+            unsigned long long idx;
+            bool valid;
+            PairRay pr;
+            nedf_row<MODE>(ws, f, a, T, t, tile, R, idx, valid, pr);
+            float x6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (valid && pr.kept) {
+                const V3 pe = madd(pr.ol, pr.te, pr.dl);
+                x6[0] = pe.x; x6[1] = pe.y; x6[2] = pe.z; x6[3] = pr.dl.x; x6[4] = pr.dl.y; x6[5] = pr.dl.z;
+            }
+            float feat[K0];
+            pipe_encode<6, 6>(x6, feat);
+            pipe_store_row<K0>(A_of(s, g), r, feat, kNedfIn);
+            fence_proxy_async_smem();
+            tc_fence_before();
+            mbar_arrive(&a_ready[s]);
+        };
+        // tail of slot s's tile: decode, z-min or occlusion, deferral to the plain method
+        auto tail = [&](int s, unsigned long long tile, const float *out) {
+            const int t = pipe_tile_type<MODE>(ws, mb, a, tile);
+            const DevType T = ws.types[t];
+            unsigned long long idx;
+            bool valid;
+            PairRay pr;
+            nedf_row<MODE>(ws, f, a, T, t, tile, R, idx, valid, pr);
+            if (MODE == kModeQuery) {
+                if (valid) {
+                    float4 res = make_float4(0.f, 0.f, __int_as_float(0x7f800000), 0.f);
+                    if (pr.kept) {
+                        const float Dl = pr.tp - T.rb * out[0];
+                        res = make_float4(out[0], out[1], Dl, (out[1] > 0.f && Dl > 0.f) ? 1.f : 0.f);
+                    }
+                    a.qout[idx] = res;
+                }
+            } else {
+                bool defer = false;
+                if (valid) {
+                    float Dl;
+                    bool hit;
+                    defer = nedf_decode(f, T, pr.ol, pr.dl, pr.tp, out[0], out[1], Dl, hit);
+                    if (!defer && hit) apply_hit(ws, f, MODE == kModeShadow, pr, Dl);
+                }
+                const int mode = MODE == kModeShadow ? 1 : 0;
+                const unsigned m = __ballot_sync(0xffffffffu, defer);
+                if (m) {
+                    const int leader = __ffs(m) - 1;
+                    unsigned long long start = 0;
+                    if (lane == leader) start = atomicAdd(&ws.cnt->fb_count[mode], (unsigned long long)__popc(m));
+                    start = __shfl_sync(0xffffffffu, start, leader);
+                    if (defer) ws.fb_list[mode][start + __popc(m & ((1u << lane) - 1u))] = (uint32_t)idx;
+                }
+            }
+        };
+        if (blockIdx.x < n_tiles) setup(0, blockIdx.x);
+        if (blockIdx.x + gx < n_tiles) setup(1, blockIdx.x + gx);
+        bool stop = false;
+        for (unsigned long long t0 = blockIdx.x; t0 < n_tiles && !stop; t0 += 2 * gx) {
+            for (int l = 0; l < L && !stop; ++l)
+                for (int s = 0; s < 2 && !stop; ++s) {
+                    const unsigned long long tile = t0 + s * gx;
+                    if (tile >= n_tiles) continue;
+                    // one outcome for all 256 epilogue threads before anything that synchronises them
+                    const bool okw = __all_sync(0xffffffffu, pipe_wait(&acc_full[s], (uint32_t)(jb[s]++ & 1u), abort, ws.status));
+                    const bool ok = !epilogue_any(!okw);
+                    if (ok) {
+                        tc_fence_after();
+                        const float *f32 = f32s[s];
+                        const uint32_t trow = tmem + lane_q + (uint32_t)(2 * s + g) * N;
+                        const float *bias = f32 + pipe_f8_bias_off(N, NOUT) + (size_t)l * N;
+                        const float sc = F8 && l > 0 ? f32[pipe_f8_bias_off(N, NOUT) + (size_t)L * N + l] : 1.0f;
+                        float out[NOUT] = {f32[NOUT * N], f32[NOUT * N + 1]};
+                        if (l + 1 < L) {
+                            if (F8 && l > 0) epi_layer<N, NOUT, F8, true, false>(trow, A_of(s, g), r, bias, sc, f32, out);
+                            else epi_layer<N, NOUT, F8, false, false>(trow, A_of(s, g), r, bias, sc, f32, out);
+                            fence_proxy_async_smem();
+                            tc_fence_before();
+                            mbar_arrive(&a_ready[s]);
+                        } else {
+                            if (F8 && l > 0) epi_layer<N, NOUT, F8, true, true>(trow, A_of(s, g), r, bias, sc, f32, out);
+                            else epi_layer<N, NOUT, F8, false, true>(trow, A_of(s, g), r, bias, sc, f32, out);
+                            tc_fence_before();
+                        }
+                        if (l + 1 == L) {
+                            tail(s, tile, out);
+                            const unsigned long long nxt = tile + 2 * gx;
+                            if (!epilogue_any(*abort != 0) && nxt < n_tiles) setup(s, nxt);
+                        }
+                    } else {
+                        *abort = 1;
+                    }
+                    stop = epilogue_any(!ok || *abort);
+                }
+        }
+    }
+    // ---- teardown ------------------------------------------------------------------------------
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 9) tmem_dealloc(tmem, 4 * N);
+}
+
+// ---------------------------------------------------------------------------------------------------
 // Deferred plain-method pairs (low confidence or outliers), one thread per pair
 // ---------------------------------------------------------------------------------------------------
 __global__ void k_fallback(Workspace ws, int mode)
@@ -808,6 +1091,33 @@ static cudaError_t launch_pipe(const Workspace &ws, const MarchBuffers &mb, cons
     }
 }
 
+template <int N, int MODE, bool F8>
+static cudaError_t launch_nedf2_n(const Workspace &ws, const PipeArgs &a, int grid, cudaStream_t st)
+{
+    const size_t f32b = (pipe_f32_floats(N, ws.nedf_hidden, 2, F8) * 4 + 1023) & ~(size_t)1023;
+    const size_t sm = NedfShape2<N, F8>::FIXED + 2 * f32b;
+    if (sm > 227 * 1024 - 8192) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(k_nedf2<N, MODE, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    MarchBuffers none{};
+    k_nedf2<N, MODE, F8><<<grid, kPipeThreads, sm, st>>>(ws, none, a);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_nedf2(const Workspace &ws, const PipeArgs &a, int grid, cudaStream_t st)
+{
+    if (grid < 1) return cudaSuccess;
+    const bool f8 = ws.precision == 2;
+    PipeArgs args = a;
+    args.stage_bytes = ws.pipe_stage_bytes[MODE] > 0 ? ws.pipe_stage_bytes[MODE] : kDefaultStageBytes;
+    switch (ws.nedf_width) {
+    case 64: return f8 ? launch_nedf2_n<64, MODE, true>(ws, args, grid, st) : launch_nedf2_n<64, MODE, false>(ws, args, grid, st);
+    case 128: return f8 ? launch_nedf2_n<128, MODE, true>(ws, args, grid, st) : launch_nedf2_n<128, MODE, false>(ws, args, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_nedf_pipe(const Workspace &ws, int mode, int type, const float *o, const float *d, float *out, int n,
                              int num_sms, cudaStream_t st)
 {
@@ -819,11 +1129,10 @@ cudaError_t launch_nedf_pipe(const Workspace &ws, int mode, int type, const floa
     a.qd = d;
     a.qout = reinterpret_cast<float4 *>(out);
     a.qn = n;
-    MarchBuffers none{};
-    if (mode == 0) return launch_pipe<kModePrimary>(ws, none, a, ws.nedf_width, num_sms, st);
-    if (mode == 1) return launch_pipe<kModeShadow>(ws, none, a, ws.nedf_width, num_sms, st);
+    if (mode == 0) return launch_nedf2<kModePrimary>(ws, a, num_sms, st);
+    if (mode == 1) return launch_nedf2<kModeShadow>(ws, a, num_sms, st);
     const int grid = (int)std::min<long long>(num_sms, ((long long)n + kPipeRows - 1) / kPipeRows);
-    return launch_pipe<kModeQuery>(ws, none, a, ws.nedf_width, grid, st);
+    return launch_nedf2<kModeQuery>(ws, a, grid, st);
 }
 
 cudaError_t launch_shade_pipe(const Workspace &ws, int npix, int num_sms, cudaStream_t st)
