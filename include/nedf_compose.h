@@ -241,6 +241,24 @@ int nedf_compose_set_profiling(nedf_handle *h, int on);
  * array of n >= NEDF_N_STAGES floats.  Errors: NEDF_ERR_STATE when nothing was profiled. */
 int nedf_compose_get_stage_times(nedf_handle *h, float *ms, int n);
 
+/* ---- checks (debug and tests; none of them faults, traps or hangs the GPU) -----------------------
+ * nedf_compose_validate: synchronises, then checks the 256 guard bytes the library places after
+ * every buffer it allocated at create (a kernel that wrote past a buffer's end shows here) and the
+ * last frame's work lists: per-type pair segments ordered and filled exactly (each type's write
+ * cursor ends at its segment's end), tile tables covering each segment at the consuming kernel's
+ * tile size, shading lists summing to the hit-pixel count, every deferred pair answered.  Returns
+ * NEDF_OK, or NEDF_ERR_STATE naming the first violation.  Skips the list checks when the frame
+ * reported an overflow or timeout (those come back through nedf_compose_sync).
+ * nedf_compose_inject_status: ORs bits into the device status word (host-side fault injection: the
+ * next nedf_compose_sync reports the error and clears the word).  Bits: 1 primary list overflow,
+ * 2 shadow list overflow, 4 timeout.
+ * nedf_compose_check_wait_limit: launches one kernel whose mbarrier wait can never complete; the
+ * wait gives up after its ~1 s limit and sets the timeout status.  Returns NEDF_OK when that timeout
+ * was reported (and clears it), so the handle and context remain usable; NEDF_ERR_STATE otherwise. */
+int nedf_compose_validate(nedf_handle *h);
+int nedf_compose_inject_status(nedf_handle *h, uint32_t bits);
+int nedf_compose_check_wait_limit(nedf_handle *h);
+
 /* ---- schedule of the tensor-core MLP kernels and its autotuner ----------------------------------
  * The tensor-core engine streams each type's weights through a fixed shared-memory ring in stages,
  * one bulk copy per stage; the stage size trades copy-issue cost against how far ahead the ring
@@ -336,7 +354,11 @@ int nedf_compose_loss_grad(nedf_handle *h, int type, int n, const float *o, cons
 /* Copies the type's current FP32 NeDF weights (packed layout) to host memory. */
 int nedf_compose_get_nedf_weights(nedf_handle *h, int type, float *host_out, int64_t n_floats);
 
-/* Training state of every type (weights, Adam moments, step counts) as one little-endian blob.
+/* Training state of every type (weights, Adam moments, step count, position in the training set)
+ * as one little-endian blob: header {magic, version 2, n_types, n_params} (int64 each), then per
+ * type int32 step, int64 batch cursor, FP32 master weights, Adam m, Adam v.  Training steps are
+ * deterministic (gradient splits summed in a fixed order), so a run resumed from a saved state
+ * repeats the uninterrupted run bit for bit on the same GPU.
  * save: with buf == NULL only *size is set; otherwise *size is the capacity in bytes.
  * load: the blob must come from a handle with the same config and types. */
 int nedf_compose_save_state(nedf_handle *h, void *buf, size_t *size);

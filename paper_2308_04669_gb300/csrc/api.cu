@@ -8,7 +8,10 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/nedf_compose.h"
 #include "render_launch.h"
@@ -82,6 +85,18 @@ struct nedf_handle {
     cudaEvent_t ev[kStages + 1] = {};
     int last_launches = 0;
     int stage_bytes[NEDF_N_SCHEDULE] = {0, 0, 0, 0, 0};   // tensor-core schedule (0 = default)
+    // guard bytes after every buffer allocated at create: (buffer, its size)
+    std::vector<std::pair<const uint8_t *, size_t>> guards;
+};
+
+// Bytes of a known pattern after each buffer allocated at create; nedf_compose_validate checks them.
+static constexpr size_t kGuardBytes = 256;
+static constexpr unsigned char kGuardByte = 0xA5;
+
+// NVTX range over one API call (shows the call in profilers' timelines; free without one)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
 };
 
 static thread_local std::string g_create_error;
@@ -238,10 +253,14 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
         return code;
     };
     cudaError_t e;
-#define CA(ptr, bytes)                                                   \
-    do {                                                                 \
-        e = cudaMalloc((void **)&(ptr), (bytes));                        \
-        if (e != cudaSuccess) return bail(e, "cudaMalloc " #ptr);        \
+#define CA(ptr, bytes)                                                                      \
+    do {                                                                                    \
+        const size_t nb_ = (bytes);                                                         \
+        e = cudaMalloc((void **)&(ptr), nb_ + kGuardBytes);                                 \
+        if (e != cudaSuccess) return bail(e, "cudaMalloc " #ptr);                           \
+        e = cudaMemset(reinterpret_cast<uint8_t *>(ptr) + nb_, kGuardByte, kGuardBytes);    \
+        if (e != cudaSuccess) return bail(e, "cudaMemset guard " #ptr);                     \
+        h->guards.emplace_back(reinterpret_cast<const uint8_t *>(ptr), nb_);               \
     } while (0)
     if ((e = cudaGetDevice(&h->device)) != cudaSuccess) return bail(e, "cudaGetDevice");
     if ((e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess)
@@ -365,6 +384,7 @@ int nedf_compose_sync(nedf_handle *h)
 
 int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *types)
 {
+    NvtxRange nvtx_("nedf_compose_set_types");
     if (!h || !types) return fail(h, NEDF_ERR_ARG, "null argument");
     if (n_types < 1 || n_types > h->cfg.max_types) return fail(h, NEDF_ERR_ARG, "n_types out of range");
     std::vector<DevType> dt(n_types);
@@ -438,6 +458,7 @@ int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *ty
 
 int nedf_compose_set_instances(nedf_handle *h, int n, const nedf_instance *inst)
 {
+    NvtxRange nvtx_("nedf_compose_set_instances");
     if (!h || (!inst && n > 0)) return fail(h, NEDF_ERR_ARG, "null argument");
     if (h->n_types == 0) return fail(h, NEDF_ERR_STATE, "set_types first");
     if (n < 0 || n > h->cfg.max_instances) return fail(h, NEDF_ERR_ARG, "instance count out of range");
@@ -602,6 +623,7 @@ int nedf_compose_render(nedf_handle *h, const nedf_camera *cam, const nedf_light
                         float *depth, uint32_t *id, float *rgba, float *shadow, float *out,
                         nedf_frame_stats *stats)
 {
+    NvtxRange nvtx_("nedf_compose_render");
     int r = check_frame_args(h, cam, lights, n_lights);
     if (r != NEDF_OK) return r;
     r = render_impl(h, cam, lights, n_lights, depth, id, rgba, shadow, out);
@@ -614,6 +636,7 @@ int nedf_compose_render_host(nedf_handle *h, const nedf_camera *cam, const nedf_
                              float *depth, uint32_t *id, float *rgba, float *shadow, float *out,
                              nedf_frame_stats *stats)
 {
+    NvtxRange nvtx_("nedf_compose_render_host");
     int r = check_frame_args(h, cam, lights, n_lights);
     if (r != NEDF_OK) return r;
     r = render_impl(h, cam, lights, n_lights);
@@ -631,6 +654,7 @@ int nedf_compose_render_host(nedf_handle *h, const nedf_camera *cam, const nedf_
 
 int nedf_compose_render_march(nedf_handle *h, const nedf_camera *cam, int n_samples, int early_stop, float *rgba)
 {
+    NvtxRange nvtx_("nedf_compose_render_march");
     nedf_light dummy{{0.f, 10.f, 0.f}};
     int r = check_frame_args(h, cam, &dummy, 1);
     if (r != NEDF_OK) return r;
@@ -688,6 +712,78 @@ int nedf_compose_get_stage_times(nedf_handle *h, float *ms, int n)
     return NEDF_OK;
 }
 
+int nedf_compose_validate(nedf_handle *h)
+{
+    if (!h) return NEDF_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    std::vector<uint8_t> g(kGuardBytes);
+    for (const auto &b : h->guards) {
+        CK(h, cudaMemcpy(g.data(), b.first + b.second, kGuardBytes, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < kGuardBytes; ++i)
+            if (g[i] != kGuardByte) {
+                char msg[160];
+                snprintf(msg, sizeof msg, "guard bytes after a %zu-byte device buffer were overwritten", b.second);
+                return fail(h, NEDF_ERR_STATE, msg);
+            }
+    }
+    if (!h->n_types) return NEDF_OK;
+    Counters c;
+    CK(h, cudaMemcpy(&c, h->d_cnt, sizeof(c), cudaMemcpyDeviceToHost));
+    uint32_t st = 0;
+    CK(h, cudaMemcpy(&st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st) return NEDF_OK;      // an overflow or timeout is reported by sync; the lists are then partial
+    const int T = h->n_types;
+    const bool tc_nedf = h->cfg.precision != NEDF_PREC_FP32 && h->opt.depth_source == NEDF_DEPTH_NEDF;
+    const bool tc_shade = h->cfg.precision != NEDF_PREC_FP32 && h->cfg.nerf_hidden > 0;
+    const unsigned long long rows = tc_nedf ? kPipeTileRows : 64;
+    const unsigned long long ppt = tc_shade ? 2 * (128 / h->opt.n_shade) : 64 / h->opt.n_shade;
+    unsigned long long hits = 0;
+    auto bad = [&](const char *what, int t) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "work-list invariant violated: %s (type %d)", what, t);
+        return fail(h, NEDF_ERR_STATE, msg);
+    };
+    if (c.p_off[0] != 0 || c.p_tile[0] != 0 || c.s_off[0] != 0 || c.s_tile[0] != 0 || c.h_tile[0] != 0)
+        return bad("segments do not start at 0", 0);
+    for (int t = 0; t < T; ++t) {
+        const unsigned long long pn = c.p_off[t + 1] - c.p_off[t], sn = c.s_off[t + 1] - c.s_off[t];
+        if (c.p_off[t + 1] < c.p_off[t] || c.s_off[t + 1] < c.s_off[t]) return bad("pair offsets decrease", t);
+        if (c.p_cursor[t] != c.p_off[t + 1]) return bad("primary segment not filled exactly", t);
+        if (c.s_cursor[t] != c.s_off[t + 1]) return bad("shadow segment not filled exactly", t);
+        if (c.p_tile[t + 1] - c.p_tile[t] != (pn + rows - 1) / rows) return bad("primary tiles do not cover the pairs", t);
+        if (c.s_tile[t + 1] - c.s_tile[t] != (sn + rows - 1) / rows) return bad("shadow tiles do not cover the pairs", t);
+        if (c.h_tile[t + 1] - c.h_tile[t] != (c.h_count[t] + ppt - 1) / ppt) return bad("shading tiles", t);
+        hits += c.h_count[t];
+    }
+    if (hits != c.hit_pixels) return bad("shading lists do not sum to the hit pixels", -1);
+    if (c.fb_count[0] > c.p_off[T] || c.fb_count[1] > c.s_off[T]) return bad("more deferred pairs than pairs", -1);
+    if (c.fallback != c.fb_count[0] + c.fb_count[1] && tc_nedf) return bad("deferred pairs not all answered", -1);
+    return NEDF_OK;
+}
+
+int nedf_compose_inject_status(nedf_handle *h, uint32_t bits)
+{
+    if (!h) return NEDF_ERR_ARG;
+    uint32_t st = 0;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(&st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+    st |= bits;
+    CK(h, cudaMemcpy(h->d_status, &st, sizeof(st), cudaMemcpyHostToDevice));
+    return NEDF_OK;
+}
+
+int nedf_compose_check_wait_limit(nedf_handle *h)
+{
+    if (!h) return NEDF_ERR_ARG;
+    CK(h, launch_wait_check(h->d_status, h->stream));
+    const int r = nedf_compose_sync(h);
+    if (r == NEDF_ERR_TIMEOUT) {
+        h->err.clear();
+        return NEDF_OK;                              // the wait gave up and reported it
+    }
+    return r != NEDF_OK ? r : fail(h, NEDF_ERR_STATE, "the bounded wait did not report its timeout");
+}
+
 static void drop_graph(nedf_handle *h)
 {
     if (h->gexec) {
@@ -722,6 +818,7 @@ int nedf_compose_get_schedule(nedf_handle *h, nedf_schedule *s)
 int nedf_compose_autotune(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights, int reps,
                           nedf_schedule *chosen)
 {
+    NvtxRange nvtx_("nedf_compose_autotune");
     int r = check_frame_args(h, cam, lights, n_lights);
     if (r != NEDF_OK) return r;
     if (reps < 1) return fail(h, NEDF_ERR_ARG, "reps < 1");
@@ -793,6 +890,7 @@ extern "C" {
 int nedf_compose_make_labels(nedf_handle *h, int type, int64_t n_rays, uint64_t seed, int march_steps,
                              int march_bisect, float *o, float *d, float *m_star, float *hit_star)
 {
+    NvtxRange nvtx_("nedf_compose_make_labels");
     if (!h) return NEDF_ERR_ARG;
     if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
     if (n_rays < 1 || n_rays > (1ll << 30)) return fail(h, NEDF_ERR_ARG, "n_rays 1..2^30");
@@ -869,6 +967,7 @@ int nedf_compose_loss_grad(nedf_handle *h, int type, int n, const float *o, cons
 
 int nedf_compose_train_step(nedf_handle *h, int type, int batch, float lr, float *loss_host)
 {
+    NvtxRange nvtx_("nedf_compose_train_step");
     if (!h) return NEDF_ERR_ARG;
     if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
     TrainState &ts = h->train[type];
@@ -906,7 +1005,7 @@ int nedf_compose_get_nedf_weights(nedf_handle *h, int type, float *host_out, int
 int nedf_compose_save_state(nedf_handle *h, void *buf, size_t *size)
 {
     if (!h || !size) return fail(h, NEDF_ERR_ARG, "null argument");
-    size_t per = sizeof(int32_t) + 3 * sizeof(float) * h->nedf_params;
+    size_t per = sizeof(int32_t) + sizeof(int64_t) + 3 * sizeof(float) * h->nedf_params;
     size_t need = 4 * sizeof(int64_t) + per * h->n_types;
     if (!buf) {
         *size = need;
@@ -915,14 +1014,17 @@ int nedf_compose_save_state(nedf_handle *h, void *buf, size_t *size)
     if (*size < need) return fail(h, NEDF_ERR_ARG, "buffer too small");
     CK(h, cudaStreamSynchronize(h->stream));
     char *p = (char *)buf;
-    int64_t hdr[4] = {0x4e45444653544154ll, 1, h->n_types, h->nedf_params};
+    int64_t hdr[4] = {0x4e45444653544154ll, 2, h->n_types, h->nedf_params};
     std::memcpy(p, hdr, sizeof(hdr));
     p += sizeof(hdr);
     size_t wb = sizeof(float) * h->nedf_params;
     for (int k = 0; k < h->n_types; ++k) {
         int32_t st = h->train[k].step;
+        int64_t cur = h->train[k].cursor;
         std::memcpy(p, &st, sizeof(st));
         p += sizeof(st);
+        std::memcpy(p, &cur, sizeof(cur));
+        p += sizeof(cur);
         CK(h, cudaMemcpy(p, h->train[k].master, wb, cudaMemcpyDeviceToHost)); p += wb;
         CK(h, cudaMemcpy(p, h->train[k].adam_m, wb, cudaMemcpyDeviceToHost)); p += wb;
         CK(h, cudaMemcpy(p, h->train[k].adam_v, wb, cudaMemcpyDeviceToHost)); p += wb;
@@ -937,8 +1039,8 @@ int nedf_compose_load_state(nedf_handle *h, const void *buf, size_t size)
     int64_t hdr[4];
     if (size < sizeof(hdr)) return fail(h, NEDF_ERR_ARG, "blob too small");
     std::memcpy(hdr, buf, sizeof(hdr));
-    size_t per = sizeof(int32_t) + 3 * sizeof(float) * h->nedf_params;
-    if (hdr[0] != 0x4e45444653544154ll || hdr[1] != 1 || hdr[2] != h->n_types || hdr[3] != h->nedf_params ||
+    size_t per = sizeof(int32_t) + sizeof(int64_t) + 3 * sizeof(float) * h->nedf_params;
+    if (hdr[0] != 0x4e45444653544154ll || hdr[1] != 2 || hdr[2] != h->n_types || hdr[3] != h->nedf_params ||
         size < sizeof(hdr) + per * h->n_types)
         return fail(h, NEDF_ERR_ARG, "blob does not match this handle");
     CK(h, cudaStreamSynchronize(h->stream));
@@ -946,9 +1048,13 @@ int nedf_compose_load_state(nedf_handle *h, const void *buf, size_t size)
     size_t wb = sizeof(float) * h->nedf_params;
     for (int k = 0; k < h->n_types; ++k) {
         int32_t st;
+        int64_t cur;
         std::memcpy(&st, p, sizeof(st));
         p += sizeof(st);
+        std::memcpy(&cur, p, sizeof(cur));
+        p += sizeof(cur);
         h->train[k].step = st;
+        h->train[k].cursor = cur;
         CK(h, cudaMemcpy(h->train[k].master, p, wb, cudaMemcpyHostToDevice)); p += wb;
         CK(h, cudaMemcpy(h->train[k].adam_m, p, wb, cudaMemcpyHostToDevice)); p += wb;
         CK(h, cudaMemcpy(h->train[k].adam_v, p, wb, cudaMemcpyHostToDevice)); p += wb;

@@ -502,8 +502,9 @@ cudaError_t launch_frame(FrameLaunch &L)
     int npix = L.W * L.H;
     int gsm = L.num_sms;
     int stage = 0;
-    // the tensor-core kernels take 128-row tiles, the CUDA-core kernels 64-row tiles; the work
-    // list scans must use the tile size of the kernel that consumes the list
+    // the tensor-core kernels take 256-row tiles (shading: two 128-row halves of n_shade-sample
+    // pixels), the CUDA-core kernels 64-row tiles; the work-list scans must use the tile size of
+    // the kernel that consumes the list
     const bool tc_nedf = ws.precision >= 1 && ws.depth_source == 0;      // BF16 or E4M3 tensor-core layers
     const bool tc_shade = ws.precision >= 1 && ws.nerf_hidden > 0;
     const int nedf_rows = tc_nedf ? kPipeTileRows : kTileRows;

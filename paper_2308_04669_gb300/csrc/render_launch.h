@@ -36,6 +36,8 @@ cudaError_t launch_shade_pipe(const Workspace &ws, int npix, int num_sms, cudaSt
 cudaError_t launch_march_colour_pipe(const Workspace &ws, const MarchBuffers &mb, int n_samples, int num_sms,
                                      cudaStream_t st);
 cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStream_t st);
+// one bounded mbarrier wait that nothing completes (sets the timeout status after its limit)
+cudaError_t launch_wait_check(uint32_t *status, cudaStream_t st);
 
 // Step-3 binning through per-light shadow-map cameras (shadow_bin.cu)
 cudaError_t launch_shadow_binning(const Workspace &ws, int npix, int n_lights, int n_inst, int rows_per_tile,

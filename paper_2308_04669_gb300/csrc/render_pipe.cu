@@ -1035,6 +1035,26 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
 }
 
 // ---------------------------------------------------------------------------------------------------
+// Wait-limit check: one thread waits on an mbarrier phase that nothing completes, with the same
+// bounded wait as the engine; the wait gives up after its limit and sets the timeout status.
+// ---------------------------------------------------------------------------------------------------
+__global__ void k_wait_check(uint32_t *status)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_wait(&bar, 0u, status, kStatusTimeout);      // phase 0 never completes
+    }
+}
+
+cudaError_t launch_wait_check(uint32_t *status, cudaStream_t st)
+{
+    k_wait_check<<<1, 32, 0, st>>>(status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------------
 // Deferred plain-method pairs (low confidence or outliers), one thread per pair
 // ---------------------------------------------------------------------------------------------------
 __global__ void k_fallback(Workspace ws, int mode)

@@ -74,12 +74,19 @@ cudaError_t launch_make_labels(const DevType *type, float rb, long long n_rays, 
 //   h[0]: B x 80 (encoded input), h[1..L]: B x w (hidden activations),
 //   dz[0..L-1]: B x w (gradient w.r.t. hidden pre-activations), dy: B x 2, valid: B, then grad.
 // ---------------------------------------------------------------------------------------------
+// Weight and bias gradients are summed over the batch in splits of kSplitRows rows; each split
+// writes its own partial gradient and k_sum_splits adds the splits in a fixed order, so a training
+// step is deterministic (and a resumed run repeats an uninterrupted one bit for bit).
+constexpr int kSplitRows = 2048;
+
 struct TrainScratch {
     float *h[17];
     float *dz[16];
     float *dy;
     float *valid;
     float *grad;
+    float *zero;                 // 512 zeros (bias operand of the backward products)
+    float *partial;              // [splits][n_params]
 };
 
 static TrainScratch carve(float *base, int B, int L, int w, long long n_params)
@@ -92,12 +99,15 @@ static TrainScratch carve(float *base, int B, int L, int w, long long n_params)
     s.dy = p; p += (size_t)B * 2;
     s.valid = p; p += (size_t)B;
     s.grad = p; p += n_params;
+    s.zero = p; p += 512;
+    s.partial = p;
     return s;
 }
 
 size_t train_scratch_bytes(int batch, int hidden, int width, long long n_params)
 {
-    size_t floats = (size_t)batch * (kNedfInPad + 2 * (size_t)hidden * width + 3) + n_params + 512;
+    const size_t splits = ((size_t)batch + kSplitRows - 1) / kSplitRows;
+    size_t floats = (size_t)batch * (kNedfInPad + 2 * (size_t)hidden * width + 3) + n_params + 512 + splits * n_params;
     return floats * sizeof(float);
 }
 
@@ -252,10 +262,12 @@ __global__ void __launch_bounds__(kThreads) k_train_bwd(int L, const float *mast
     }
 }
 
-// dW[out][in] += sum_b A[b][out] * Bm[b][in] over a K-range of rows; 64x64 output tile per block.
+// dW[out][in] = sum_b A[b][out] * Bm[b][in] over split z's rows, stored at dW + z * split_stride;
+// 64x64 output tile per block.
 __global__ void __launch_bounds__(256) k_grad_atb(const float *A, int lda, const float *Bm, int ldb, int n_out, int n_in,
-                                                  int rows, int rows_per_split, float *dW)
+                                                  int rows, int rows_per_split, float *dW, long long split_stride)
 {
+    dW += blockIdx.z * split_stride;
     __shared__ float As[32][64 + 4];
     __shared__ float Bs[32][64 + 4];
     const int o0 = blockIdx.x * 64, i0 = blockIdx.y * 64;
@@ -282,19 +294,30 @@ __global__ void __launch_bounds__(256) k_grad_atb(const float *A, int lda, const
     for (int p = 0; p < 4; ++p)
         for (int q = 0; q < 4; ++q) {
             int oo = o0 + ty * 4 + p, ii = i0 + tx * 4 + q;
-            if (oo < n_out && ii < n_in && acc[p][q] != 0.0f) atomicAdd(&dW[(size_t)oo * n_in + ii], acc[p][q]);
+            if (oo < n_out && ii < n_in) dW[(size_t)oo * n_in + ii] = acc[p][q];
         }
 }
 
-// db[out] += sum_b A[b][out]
-__global__ void k_grad_bias(const float *A, int lda, int n_out, int rows, int rows_per_split, float *db)
+// db[out] = sum_b A[b][out] over split y's rows, stored at db + y * split_stride
+__global__ void k_grad_bias(const float *A, int lda, int n_out, int rows, int rows_per_split, float *db,
+                            long long split_stride)
 {
     int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= n_out) return;
     int r0 = blockIdx.y * rows_per_split, r1 = min(rows, r0 + rows_per_split);
     float acc = 0.0f;
     for (int r = r0; r < r1; ++r) acc += A[(size_t)r * lda + o];
-    if (acc != 0.0f) atomicAdd(&db[o], acc);
+    db[blockIdx.y * split_stride + o] = acc;
+}
+
+// grad[i] = partial[0][i] + partial[1][i] + ... in split order
+__global__ void k_sum_splits(const float *partial, int splits, long long n, float *grad)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float acc = 0.0f;
+        for (int z = 0; z < splits; ++z) acc += partial[(size_t)z * n + i];
+        grad[i] = acc;
+    }
 }
 
 // Adam (Kingma & Ba 2015) on the packed master weights; the renderer's transposed copy is
@@ -338,8 +361,6 @@ static cudaError_t run_fwd_bwd(const TrainLaunch &L, const float *o, const float
     cudaStream_t st = L.stream;
     cudaError_t e = cudaMemsetAsync(L.loss, 0, sizeof(float) * 4, st);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(s.grad, 0, sizeof(float) * L.n_params, st);
-    if (e != cudaSuccess) return e;
     k_count_hits<<<std::min(1024, (B + 255) / 256), 256, 0, st>>>(hit_star, start, n, B, L.loss);
     size_t sm = (size_t)(W > kNedfInPad ? W : kNedfInPad) * kXStride * sizeof(float);
     if ((e = cudaFuncSetAttribute(k_train_fwd<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
@@ -350,13 +371,13 @@ static cudaError_t run_fwd_bwd(const TrainLaunch &L, const float *o, const float
     int grid = std::min(tiles, L.num_sms * 4);
     k_train_fwd<W><<<grid, kThreads, sm, st>>>(L.type, L.rb, L.hidden, L.kernel_w, o, d, m_star, hit_star, start, n,
                                                 B, s, L.loss);
-    // zero bias vector for the backward products (the scratch tail is zeroed here)
-    float *zero = s.grad + L.n_params;
+    // zero bias vector for the backward products
+    float *zero = s.zero;
     if ((e = cudaMemsetAsync(zero, 0, sizeof(float) * 512, st)) != cudaSuccess)
         return e;
     k_train_bwd<W><<<grid, kThreads, sm, st>>>(L.hidden, L.master, B, s, zero);
     // weight gradients: layer l uses dz_l (or dy for the output layer) against h_l
-    const int split_rows = 2048;
+    const int split_rows = kSplitRows;
     int splits = (B + split_rows - 1) / split_rows;
     long long off = 0;
     int fi = kNedfIn;
@@ -367,12 +388,14 @@ static cudaError_t run_fwd_bwd(const TrainLaunch &L, const float *o, const float
         const float *Bm = s.h[l];
         int ldb = l == 0 ? kNedfInPad : W;
         dim3 g((fo + 63) / 64, (fi + 63) / 64, splits);
-        k_grad_atb<<<g, 256, 0, st>>>(A, lda, Bm, ldb, fo, fi, B, split_rows, s.grad + off);
+        k_grad_atb<<<g, 256, 0, st>>>(A, lda, Bm, ldb, fo, fi, B, split_rows, s.partial + off, L.n_params);
         dim3 gb((fo + 127) / 128, splits);
-        k_grad_bias<<<gb, 128, 0, st>>>(A, lda, fo, B, split_rows, s.grad + off + (long long)fi * fo);
+        k_grad_bias<<<gb, 128, 0, st>>>(A, lda, fo, B, split_rows, s.partial + off + (long long)fi * fo, L.n_params);
         off += (long long)fi * fo + fo;
         fi = W;
     }
+    k_sum_splits<<<(int)std::min<long long>((L.n_params + 255) / 256, (long long)L.num_sms * 8), 256, 0, st>>>(
+        s.partial, splits, L.n_params, s.grad);
     return cudaGetLastError();
 }
 

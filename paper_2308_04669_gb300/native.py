@@ -94,6 +94,9 @@ EXPORTS = {
     "nedf_compose_stage_name": ([C.c_int], C.c_char_p),
     "nedf_compose_set_profiling": ([_H, C.c_int], C.c_int),
     "nedf_compose_get_stage_times": ([_H, _fp, C.c_int], C.c_int),
+    "nedf_compose_validate": ([_H], C.c_int),
+    "nedf_compose_inject_status": ([_H, C.c_uint32], C.c_int),
+    "nedf_compose_check_wait_limit": ([_H], C.c_int),
     "nedf_compose_set_schedule": ([_H, C.POINTER(Schedule)], C.c_int),
     "nedf_compose_get_schedule": ([_H, C.POINTER(Schedule)], C.c_int),
     "nedf_compose_autotune": ([_H, C.POINTER(Camera), C.POINTER(Light), C.c_int, C.c_int, C.POINTER(Schedule)],
@@ -276,6 +279,15 @@ class Renderer:
 
     def render_march(self, cam, n_samples, early_stop, rgba):
         return self._check(_lib.nedf_compose_render_march(self.h, C.byref(cam), n_samples, early_stop, _ptr(rgba)))
+
+    def validate(self):
+        return self._check(_lib.nedf_compose_validate(self.h))
+
+    def inject_status(self, bits):
+        return self._check(_lib.nedf_compose_inject_status(self.h, bits))
+
+    def check_wait_limit(self):
+        return self._check(_lib.nedf_compose_check_wait_limit(self.h))
 
     def set_schedule(self, stage_bytes):
         s = Schedule()
