@@ -340,6 +340,36 @@ __device__ __forceinline__ void epi_layer(uint32_t tmem_row, uint8_t *Ag, int r,
     }
 }
 
+// MMAs of chunks [c0, c1) of one layer for the two 128-row halves (accumulators dx, dy; A operands
+// at ax, ay; the stage's first chunk at `stage`).  Descriptors advance by constant steps of their
+// start-address field (16-byte units), so the issuing thread spends a few instructions per MMA;
+// chunk 0 overwrites the accumulators.  bias_chunk (-1: none) reads A at ones_off instead.
+template <bool E4M3>
+__device__ __forceinline__ void issue_chunks(uint32_t dx, uint32_t dy, uint32_t ax, uint32_t ay, uint32_t stage, int c0,
+                                             int c1, int chunk_bytes, uint32_t idesc, int bias_chunk, uint32_t ones_off)
+{
+    uint64_t bd = smem_desc(stage, 128, 256);
+    uint64_t adx = smem_desc(ax + (uint32_t)c0 * 4096u, 2048, 128), ady = smem_desc(ay + (uint32_t)c0 * 4096u, 2048, 128);
+    const uint64_t bstep = (uint64_t)(chunk_bytes >> 4), astep = 4096u >> 4;
+    for (int c = c0; c < c1; ++c) {
+        if (c == bias_chunk) {
+            adx = smem_desc(ax + ones_off, 2048, 128);
+            ady = smem_desc(ay + ones_off, 2048, 128);
+        }
+        const uint32_t acc = c > 0 ? 1u : 0u;
+        if (E4M3) {
+            mma_e4m3(dx, adx, bd, idesc, acc);
+            mma_e4m3(dy, ady, bd, idesc, acc);
+        } else {
+            mma_bf16(dx, adx, bd, idesc, acc);
+            mma_bf16(dy, ady, bd, idesc, acc);
+        }
+        adx += astep;
+        ady += astep;
+        bd += bstep;
+    }
+}
+
 struct PipeArgs {
     int stage_bytes;              // schedule: weight bytes per bulk copy
     const uint8_t *blobs;
@@ -507,18 +537,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                         if (!pipe_wait(&w_full[s], (uint32_t)((q / S) & 1u), abort, ws.status)) break;
                         tc_fence_after();
                         const uint32_t stage = smem_addr(ring + (size_t)s * STAGE);
-                        for (int c = c0; c < min(nk, c0 + GC); ++c) {
-                            const uint64_t bdesc = smem_desc(stage + (uint32_t)(c - c0) * SH::CHUNK, 128, 256);
-                            if (e4m3) {
-                                mma_e4m3(tmem, smem_desc(ax + c * 4096u, 2048, 128), bdesc, idesc8, c > 0 ? 1u : 0u);
-                                mma_e4m3(tmem + N, smem_desc(ay + c * 4096u, 2048, 128), bdesc, idesc8, c > 0 ? 1u : 0u);
-                                continue;
-                            }
-                            // a BF16 hidden layer's last chunk is its bias, against the constant-one block
-                            const uint32_t ac = (uint32_t)(l > 0 && c == N / kKC ? SH::ONES / kKC : c) * 4096u;
-                            mma_bf16(tmem, smem_desc(ax + ac, 2048, 128), bdesc, idesc, c > 0 ? 1u : 0u);
-                            mma_bf16(tmem + N, smem_desc(ay + ac, 2048, 128), bdesc, idesc, c > 0 ? 1u : 0u);
-                        }
+                        const int c1 = min(nk, c0 + GC);
+                        if (e4m3) issue_chunks<true>(tmem, tmem + N, ax, ay, stage, c0, c1, SH::CHUNK, idesc8, -1, 0u);
+                        else      // a BF16 hidden layer's last chunk is its bias, against the constant-one block
+                            issue_chunks<false>(tmem, tmem + N, ax, ay, stage, c0, c1, SH::CHUNK, idesc,
+                                                l > 0 ? N / kKC : -1, (uint32_t)(SH::ONES / kKC) * 4096u);
                         mma_commit(&w_empty[s]);      // the stage is free once its MMAs have read it
                         issued_any = true;
                     }
@@ -885,17 +908,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                             if (!pipe_wait(&w_full[st], (uint32_t)((q / S) & 1u), abort, ws.status)) break;
                             tc_fence_after();
                             const uint32_t stage = smem_addr(ring + (size_t)st * STAGE);
-                            for (int c = c0; c < min(nk, c0 + GC); ++c) {
-                                const uint64_t bdesc = smem_desc(stage + (uint32_t)(c - c0) * SH::CHUNK, 128, 256);
-                                if (e4m3) {
-                                    mma_e4m3(dx, smem_desc(ax + c * 4096u, 2048, 128), bdesc, idesc8, c > 0 ? 1u : 0u);
-                                    mma_e4m3(dy, smem_desc(ay + c * 4096u, 2048, 128), bdesc, idesc8, c > 0 ? 1u : 0u);
-                                } else {
-                                    const uint32_t ac = (uint32_t)(l > 0 && c == N / kKC ? SH::ONES / kKC : c) * 4096u;
-                                    mma_bf16(dx, smem_desc(ax + ac, 2048, 128), bdesc, idesc, c > 0 ? 1u : 0u);
-                                    mma_bf16(dy, smem_desc(ay + ac, 2048, 128), bdesc, idesc, c > 0 ? 1u : 0u);
-                                }
-                            }
+                            const int c1 = min(nk, c0 + GC);
+                            if (e4m3) issue_chunks<true>(dx, dy, ax, ay, stage, c0, c1, SH::CHUNK, idesc8, -1, 0u);
+                            else issue_chunks<false>(dx, dy, ax, ay, stage, c0, c1, SH::CHUNK, idesc,
+                                                     l > 0 ? N / kKC : -1, (uint32_t)(SH::ONES / kKC) * 4096u);
                             mma_commit(&w_empty[st]);
                             issued_any = true;
                         }
@@ -1016,9 +1032,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                             tc_fence_before();
                         }
                         if (l + 1 == L) {
-                            tail(s, tile, out);
+                            // the next tile's set-up first, so its MMAs start while this tile's
+                            // tail (decode, z-min, deferral) runs
                             const unsigned long long nxt = tile + 2 * gx;
                             if (!epilogue_any(*abort != 0) && nxt < n_tiles) setup(s, nxt);
+                            tail(s, tile, out);
                         }
                     } else {
                         *abort = 1;
