@@ -77,7 +77,7 @@ cudaError_t launch_make_labels(const DevType *type, float rb, long long n_rays, 
 // Weight and bias gradients are summed over the batch in splits of kSplitRows rows; each split
 // writes its own partial gradient and k_sum_splits adds the splits in a fixed order, so a training
 // step is deterministic (and a resumed run repeats an uninterrupted one bit for bit).
-constexpr int kSplitRows = 2048;
+constexpr int kSplitRows = 512;          // 128 splits at a batch of 65536
 
 struct TrainScratch {
     float *h[17];
@@ -298,16 +298,38 @@ __global__ void __launch_bounds__(256) k_grad_atb(const float *A, int lda, const
         }
 }
 
-// db[out] = sum_b A[b][out] over split y's rows, stored at db + y * split_stride
-__global__ void k_grad_bias(const float *A, int lda, int n_out, int rows, int rows_per_split, float *db,
-                            long long split_stride)
+// db[out] = sum_b A[b][out] over split y's rows, stored at db + y * split_stride.  A block takes
+// 128 columns: lane j sums columns 4j..4j+3 over every eighth row, then the eight warps are added in
+// order (fixed order: deterministic).
+__global__ void __launch_bounds__(256) k_grad_bias(const float *A, int lda, int n_out, int rows, int rows_per_split,
+                                                   float *db, long long split_stride)
 {
-    int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= n_out) return;
-    int r0 = blockIdx.y * rows_per_split, r1 = min(rows, r0 + rows_per_split);
-    float acc = 0.0f;
-    for (int r = r0; r < r1; ++r) acc += A[(size_t)r * lda + o];
-    db[blockIdx.y * split_stride + o] = acc;
+    __shared__ float red[8][128];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 128 + lane * 4;
+    const int r0 = blockIdx.y * rows_per_split, r1 = min(rows, r0 + rows_per_split);
+    const bool vec = (lda & 3) == 0 && c + 3 < n_out;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int r = r0 + warp; r < r1; r += 8) {
+        const float *row = A + (size_t)r * lda + c;
+        if (vec) {
+            const float4 v = *reinterpret_cast<const float4 *>(row);
+            a0 += v.x; a1 += v.y; a2 += v.z; a3 += v.w;
+        } else {
+            if (c < n_out) a0 += row[0];
+            if (c + 1 < n_out) a1 += row[1];
+            if (c + 2 < n_out) a2 += row[2];
+            if (c + 3 < n_out) a3 += row[3];
+        }
+    }
+    red[warp][lane * 4] = a0; red[warp][lane * 4 + 1] = a1; red[warp][lane * 4 + 2] = a2; red[warp][lane * 4 + 3] = a3;
+    __syncthreads();
+    if (threadIdx.x < 128) {
+        const int o = blockIdx.x * 128 + threadIdx.x;
+        float acc = 0.f;
+        for (int w = 0; w < 8; ++w) acc += red[w][threadIdx.x];
+        if (o < n_out) db[blockIdx.y * split_stride + o] = acc;
+    }
 }
 
 // grad[i] = partial[0][i] + partial[1][i] + ... in split order
@@ -390,7 +412,7 @@ static cudaError_t run_fwd_bwd(const TrainLaunch &L, const float *o, const float
         dim3 g((fo + 63) / 64, (fi + 63) / 64, splits);
         k_grad_atb<<<g, 256, 0, st>>>(A, lda, Bm, ldb, fo, fi, B, split_rows, s.partial + off, L.n_params);
         dim3 gb((fo + 127) / 128, splits);
-        k_grad_bias<<<gb, 128, 0, st>>>(A, lda, fo, B, split_rows, s.partial + off + (long long)fi * fo, L.n_params);
+        k_grad_bias<<<gb, 256, 0, st>>>(A, lda, fo, B, split_rows, s.partial + off + (long long)fi * fo, L.n_params);
         off += (long long)fi * fo + fo;
         fi = W;
     }
