@@ -1,21 +1,23 @@
-// Warp-specialised tensor-core MLP engine for every render-time network (BF16, tcgen05/TMEM).
+// Warp-specialised tensor-core MLP engines (tcgen05/TMEM; BF16, or E4M3 hidden layers) for every
+// render-time network.
 //
 // Method: arXiv 2308.04669, Eq. 1-2 and 7 (NeDF queries of Steps 1 and 3), Eq. 8 with the sample
 // window (the radiance field of Step 2), and the plain method's colour frame (its NeRF at every
 // sample).
 //
-// A CTA works on tiles of 256 rows held as two 128-row halves X and Y.  Each hidden layer is two
-// tcgen05 MMAs per 16-column weight chunk (M = 128, N = width, K = 16), one per half, into two
-// TMEM accumulators (columns [0, N) and [N, 2N)), so every weight chunk fetched from L2 serves 256
-// rows.  Roles:
-//   warps 0-3   epilogue group X: row set-up of rows 0..127, layer epilogues (tcgen05.ld, bias,
-//               ReLU, BF16 A operand in shared memory), output layer and tail;
+// k_pipe (the NeRF: shading and plain-method colour rows) works on tiles of 256 rows held as two
+// 128-row halves X and Y, with one TMEM accumulator per half.  Each hidden layer is two tcgen05
+// MMAs per weight chunk (M = 128, N = width), one per half, so every chunk fetched from L2 serves
+// 256 rows.  Roles:
+//   warps 0-3   epilogue group X: row set-up of rows 0..127, layer epilogues (tcgen05.ld, ReLU,
+//               rounding, A operand in shared memory), output layer and tail;
 //   warps 4-7   epilogue group Y: the same for rows 128..255 (TMEM lane quarter = warp % 4);
 //   warp 8      producer: streams the weight chunks of every layer of every tile, in MMA order,
-//               through a ring of shared-memory stages (up to 16 KB, one bulk asynchronous copy
-//               each: a copy costs its issuing thread a few hundred cycles whatever its size);
+//               through a ring of shared-memory stages (one bulk asynchronous copy each: a copy
+//               costs its issuing thread a few hundred cycles whatever its size);
 //   warp 9      MMA issuer (and TMEM owner).
-// The producer only waits for free slots, so while the epilogue warps work on layer l it is
+// k_nedf2 (the NeDF, widths up to 128) keeps two such tiles in flight (see its own comment).
+// The producer only waits for free stages, so while the epilogue warps work on layer l it is
 // already loading layer l+1.  Every wait is bounded: a timeout sets the status word and an abort
 // flag that ends every role's loop, and the teardown drains the kernel's own copies and MMAs
 // (again bounded) before TMEM is freed.
@@ -455,7 +457,8 @@ __device__ __forceinline__ int pipe_tile_type(const Workspace &ws, const MarchBu
 template <int N, int MODE, bool F8>
 __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuffers mb, PipeArgs a)
 {
-    constexpr bool NERF = MODE == kModeShade || MODE == kModeMarch;
+    static_assert(MODE == kModeShade || MODE == kModeMarch, "the NeDF modes run in k_nedf2");
+    constexpr bool NERF = true;
     using SH = PipeShape<N, NERF, F8>;
     constexpr int K0 = SH::K0, NOUT = SH::NOUT;
     // schedule: GC chunks per stage (at least 2 stages in the ring), S stages
@@ -585,8 +588,6 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
             }
             // ---- row set-up ---------------------------------------------------------------------
             float x6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            PairRay pr;
-            pr.kept = false;
             bool valid = false;
             unsigned long long idx = 0;
             float sig = 0.f;                          // shade: density; march: sample weight
@@ -633,41 +634,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                     pair = row.x;
                 }
                 t_key[R] = pair;
-            } else {
-                if (MODE == kModeQuery) {
-                    idx = tile * kPipeRows + R;
-                    valid = idx < (unsigned long long)a.qn;
-                    if (valid) {
-                        pr.ol = v3(a.qo[3 * idx], a.qo[3 * idx + 1], a.qo[3 * idx + 2]);
-                        pr.dl = normalized(v3(a.qd[3 * idx], a.qd[3 * idx + 1], a.qd[3 * idx + 2]));
-                        Chord ch;
-                        pr.kept = bound_chord(pr.ol, pr.dl, T.rb, ch);
-                        pr.te = ch.te; pr.tx = ch.tx; pr.tp = ch.tp;
-                    }
-                } else {
-                    const Counters &C = *ws.cnt;
-                    const unsigned long long *toff = MODE == kModePrimary ? C.p_tile : C.s_tile;
-                    const unsigned long long *poff = MODE == kModePrimary ? C.p_off : C.s_off;
-                    idx = poff[t] + (tile - toff[t]) * kPipeRows + R;
-                    valid = idx < poff[t + 1];
-                    if (valid)
-                        setup_pair_ray(ws, f, MODE == kModeShadow, (MODE == kModePrimary ? ws.ppairs : ws.spairs)[idx], T.rb, pr);
-                }
-                if (valid && pr.kept) {
-                    const V3 pe = madd(pr.ol, pr.te, pr.dl);
-                    x6[0] = pe.x; x6[1] = pe.y; x6[2] = pe.z; x6[3] = pr.dl.x; x6[4] = pr.dl.y; x6[5] = pr.dl.z;
-                }
             }
             {
                 float feat[K0];
-                if (NERF) {
-                    pipe_encode<3, 10>(x6, feat);
-                    pipe_encode<3, 4>(x6 + 3, feat + 63);
-                    pipe_store_row<K0>(Ag, r, feat, kNerfIn);
-                } else {
-                    pipe_encode<6, 6>(x6, feat);
-                    pipe_store_row<K0>(Ag, r, feat, kNedfIn);
-                }
+                pipe_encode<3, 10>(x6, feat);
+                pipe_encode<3, 4>(x6 + 3, feat + 63);
+                pipe_store_row<K0>(Ag, r, feat, kNerfIn);
             }
             fence_proxy_async_smem();
             tc_fence_before();
@@ -703,7 +675,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
             // one outcome for both groups: the tails use named barriers and ballots
             if (epilogue_any(!ok || *abort)) break;
             // ---- tail ---------------------------------------------------------------------------
-            if (MODE == kModeShade || MODE == kModeMarch) {
+            {
                 const float wr = MODE == kModeShade ? 1.0f : sig;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) t_rgb[R][c] = wr / (1.0f + expf(-out[c]));
@@ -738,32 +710,6 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                     }
                 }
                 asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kHalf) : "memory");
-            } else if (MODE == kModeQuery) {
-                if (valid) {
-                    float4 res = make_float4(0.f, 0.f, __int_as_float(0x7f800000), 0.f);
-                    if (pr.kept) {
-                        const float Dl = pr.tp - T.rb * out[0];
-                        res = make_float4(out[0], out[1], Dl, (out[1] > 0.f && Dl > 0.f) ? 1.f : 0.f);
-                    }
-                    a.qout[idx] = res;
-                }
-            } else {
-                bool defer = false;
-                if (valid) {
-                    float Dl;
-                    bool hit;
-                    defer = nedf_decode(f, T, pr.ol, pr.dl, pr.tp, out[0], out[1], Dl, hit);
-                    if (!defer && hit) apply_hit(ws, f, MODE == kModeShadow, pr, Dl);
-                }
-                const int mode = MODE == kModeShadow ? 1 : 0;
-                const unsigned m = __ballot_sync(0xffffffffu, defer);
-                if (m) {
-                    const int leader = __ffs(m) - 1;
-                    unsigned long long start = 0;
-                    if (lane == leader) start = atomicAdd(&ws.cnt->fb_count[mode], (unsigned long long)__popc(m));
-                    start = __shfl_sync(0xffffffffu, start, leader);
-                    if (defer) ws.fb_list[mode][start + __popc(m & ((1u << lane) - 1u))] = (uint32_t)idx;
-                }
             }
         }
     }
