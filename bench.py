@@ -428,9 +428,12 @@ def run_ours(args):
                 for t in range(len(sc.types))}
         threads = os.cpu_count() or 1
         rate, npx, secs = oracle_rate(sc, w_tr, args.cpu_seconds, threads)
+        rate1, npx1, secs1 = oracle_rate(sc, w_tr, max(2.0, args.cpu_seconds / 3), 1, seed=71)
         cpu = {"value": rate, "unit": "rays/s", "cores": threads, "kind": "oracle",
                "sample": f"{npx} seeded pixels of the same {sc.W}x{sc.H} frame (same trained weights, all {sc.n_inst} "
-                         f"instances, {n_li} lights), {secs:.1f} s on {threads} threads"}
+                         f"instances, {n_li} lights), {secs:.1f} s on {threads} threads",
+               "single_core": {"value": rate1, "unit": "rays/s", "cores": 1,
+                               "sample": f"{npx1} seeded pixels, {secs1:.1f} s on 1 thread"}}
     r.close()
 
     value = job_value(n, frame_ms_max, world)
