@@ -823,7 +823,10 @@ int nedf_compose_autotune(nedf_handle *h, const nedf_camera *cam, const nedf_lig
     if (r != NEDF_OK) return r;
     if (reps < 1) return fail(h, NEDF_ERR_ARG, "reps < 1");
     if (h->cfg.precision != NEDF_PREC_FP32) {
-        static const int cand[4] = {8192, 16384, 32768, 65536};
+        // stage sizes: the kernels round to whole weight chunks (2-8 KB), so 12 and 24 KB give stages
+        // of three and six chunks, which divide the 9-chunk NeDF layers evenly
+        static const int cand[7] = {8192, 12288, 16384, 24576, 32768, 49152, 65536};
+        constexpr int n_cand = 7;
         // stage index of each tuned kernel: Step-2 shading, Step-1 NeDF, Step-3 NeDF
         static const int kern[3] = {0, 2, 3}, stage[3] = {4, 2, 6};
         float best[3] = {1e30f, 1e30f, 1e30f};
@@ -831,7 +834,7 @@ int nedf_compose_autotune(nedf_handle *h, const nedf_camera *cam, const nedf_lig
         const bool was_profiling = h->profiling;
         r = nedf_compose_set_profiling(h, 1);
         if (r != NEDF_OK) return r;
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < n_cand; ++c) {
             for (int k = 0; k < NEDF_N_SCHEDULE; ++k) h->stage_bytes[k] = cand[c];
             drop_graph(h);
             float t[3] = {1e30f, 1e30f, 1e30f};

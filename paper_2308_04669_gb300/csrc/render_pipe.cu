@@ -951,9 +951,17 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
         if (blockIdx.x < n_tiles) setup(0, blockIdx.x);
         if (blockIdx.x + gx < n_tiles) setup(1, blockIdx.x + gx);
         bool stop = false;
+        // a finished tile's tail waits until its slot's next layer-0 epilogue is done: the epilogue
+        // warps then have slack (the slot's layer-1 MMAs run), and the other slot's last epilogue
+        // and set-up are not held up behind it
+        bool pend[2] = {false, false};
+        unsigned long long pend_tile[2] = {0, 0};
+        float pend_out[2][NOUT] = {};
         for (unsigned long long t0 = blockIdx.x; t0 < n_tiles && !stop; t0 += 2 * gx) {
             for (int l = 0; l < L && !stop; ++l)
-                for (int s = 0; s < 2 && !stop; ++s) {
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    if (stop) continue;
                     const unsigned long long tile = t0 + s * gx;
                     if (tile >= n_tiles) continue;
                     // one outcome for all 256 epilogue threads before anything that synchronises them
@@ -978,17 +986,29 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                             tc_fence_before();
                         }
                         if (l + 1 == L) {
-                            // the next tile's set-up first, so its MMAs start while this tile's
-                            // tail (decode, z-min, deferral) runs
                             const unsigned long long nxt = tile + 2 * gx;
                             if (!epilogue_any(*abort != 0) && nxt < n_tiles) setup(s, nxt);
-                            tail(s, tile, out);
+                        }
+                        if (l == 0 && pend[s]) {
+                            tail(s, pend_tile[s], pend_out[s]);
+                            pend[s] = false;
+                        }
+                        if (l + 1 == L) {
+                            pend[s] = true;
+                            pend_tile[s] = tile;
+#pragma unroll
+                            for (int o = 0; o < NOUT; ++o) pend_out[s][o] = out[o];
                         }
                     } else {
                         *abort = 1;
                     }
                     stop = epilogue_any(!ok || *abort);
                 }
+        }
+        if (!stop) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+                if (pend[s]) tail(s, pend_tile[s], pend_out[s]);
         }
     }
     // ---- teardown ------------------------------------------------------------------------------
