@@ -279,7 +279,7 @@ int nedf_compose_set_schedule(nedf_handle *h, const nedf_schedule *s);
 int nedf_compose_get_schedule(nedf_handle *h, nedf_schedule *s);
 
 /* Autotuner: renders the given frame (into the handle's own buffers) with each candidate stage
- * size (8, 12, 16, 24, 32, 48, 64 KB) for every tensor-core kernel, reps timed frames per candidate with stage
+ * size (8, 12, 16, 24, 32, 36, 48, 64 KB) for every tensor-core kernel, reps timed frames per candidate with stage
  * events, and keeps per kernel the size with the smallest time (the plain-method colour rows take
  * the shading kernel's choice, NeDF queries Step 1's).  Synchronises; leaves profiling as it was.
  * chosen (may be NULL) receives the result.  With FP32 precision there is nothing to tune and the

@@ -825,8 +825,8 @@ int nedf_compose_autotune(nedf_handle *h, const nedf_camera *cam, const nedf_lig
     if (h->cfg.precision != NEDF_PREC_FP32) {
         // stage sizes: the kernels round to whole weight chunks (2-8 KB), so 12 and 24 KB give stages
         // of three and six chunks, which divide the 9-chunk NeDF layers evenly
-        static const int cand[7] = {8192, 12288, 16384, 24576, 32768, 49152, 65536};
-        constexpr int n_cand = 7;
+        static const int cand[8] = {8192, 12288, 16384, 24576, 32768, 36864, 49152, 65536};
+        constexpr int n_cand = 8;
         // stage index of each tuned kernel: Step-2 shading, Step-1 NeDF, Step-3 NeDF
         static const int kern[3] = {0, 2, 3}, stage[3] = {4, 2, 6};
         float best[3] = {1e30f, 1e30f, 1e30f};

@@ -730,7 +730,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
 template <int N, bool F8>
 struct NedfShape2 {
     using B = PipeShape<N, false, F8>;
-    static constexpr int RING = F8 ? 131072 : 65536;
+    // BF16 width 128: room for two whole 9-chunk layers (36 KB each), so a layer can be one stage
+    static constexpr int RING = F8 ? 131072 : (N == 128 ? 73728 : 65536);
     static constexpr int SMAX = RING / B::CHUNK;
     static constexpr size_t FIXED = 4 * B::A_BYTES + (size_t)RING;          // + two fp32 blocks
 };
@@ -782,7 +783,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
     const int L = ws.nedf_hidden;
     uint8_t *ring = smem + 4 * SH::A_BYTES;
     const int n_f32 = (int)pipe_f32_floats(N, L, NOUT, F8);
-    const size_t f32_bytes = ((size_t)n_f32 * 4 + 1023) & ~(size_t)1023;
+    const size_t f32_bytes = ((size_t)n_f32 * 4 + 15) & ~(size_t)15;
     volatile int *abort = &abort_flag;
 
     if (warp == 9) tmem_alloc(&tmem_base, 4 * N);
@@ -1098,7 +1099,7 @@ static cudaError_t launch_pipe(const Workspace &ws, const MarchBuffers &mb, cons
 template <int N, int MODE, bool F8>
 static cudaError_t launch_nedf2_n(const Workspace &ws, const PipeArgs &a, int grid, cudaStream_t st)
 {
-    const size_t f32b = (pipe_f32_floats(N, ws.nedf_hidden, 2, F8) * 4 + 1023) & ~(size_t)1023;
+    const size_t f32b = (pipe_f32_floats(N, ws.nedf_hidden, 2, F8) * 4 + 15) & ~(size_t)15;
     const size_t sm = NedfShape2<N, F8>::FIXED + 2 * f32b;
     if (sm > 227 * 1024 - 8192) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(k_nedf2<N, MODE, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

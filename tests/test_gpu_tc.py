@@ -163,7 +163,7 @@ def test_schedule_changes_timing_not_results():
             got = frame()
             assert all(np.array_equal(x, y) for x, y in zip(ref, got)), b
         tuned = r.autotune(cam, li, reps=1)
-        assert all(v["stage_bytes"] in (8192, 12288, 16384, 24576, 32768, 49152, 65536) for v in tuned.values())
+        assert all(v["stage_bytes"] in (8192, 12288, 16384, 24576, 32768, 36864, 49152, 65536) for v in tuned.values())
         assert tuned["step2_shade"]["ms"] > 0 and tuned["step1_nedf"]["ms"] > 0
         assert r.get_schedule()["step3_nedf"] == tuned["step3_nedf"]["stage_bytes"]
         got = frame()
