@@ -263,7 +263,12 @@ def run_ours(args):
     n = sc.W * sc.H
     dev = "cuda"
     # the library's autotuner picks the tensor-core kernels' schedule on this frame (untimed)
-    schedule = r.autotune(cam, lights, reps=2) if prec != native.PREC_FP32 and not args.no_autotune else None
+    schedule = None
+    if args.schedule and prec != native.PREC_FP32:        # a fixed schedule (reproducible profiles)
+        r.set_schedule([int(x) for x in args.schedule.split(",")])
+        schedule = {"fixed": r.get_schedule()}
+    elif prec != native.PREC_FP32 and not args.no_autotune:
+        schedule = r.autotune(cam, lights, reps=2)
     depth = torch.empty(n, device=dev)
     ids = torch.empty(n, dtype=torch.int32, device=dev)
     out = torch.empty(n, 4, device=dev)
@@ -479,6 +484,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tensor-core schedule")
+    ap.add_argument("--schedule", default="", help="fixed stage bytes per tensor-core kernel (shade, march colour, "
+                    "Step-1 NeDF, Step-3 NeDF, query), comma-separated; skips the autotuner")
     ap.add_argument("--no-march-dense", dest="march_dense", action="store_false",
                     help="skip the dense 128-sample ray-march frame (timed by default beside the early-stop one)")
     ap.add_argument("--frames-only", action="store_true",
