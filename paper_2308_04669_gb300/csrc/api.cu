@@ -49,6 +49,8 @@ struct nedf_handle {
     uint32_t *d_id = nullptr, *d_occl = nullptr, *d_hlist = nullptr, *d_status = nullptr;
     float4 *d_rgba = nullptr, *d_out = nullptr;
     uint2 *d_ppairs = nullptr, *d_spairs = nullptr;
+    float4 *d_pgeo = nullptr, *d_sgeo = nullptr;
+    float *d_sell = nullptr;
     Counters *d_cnt = nullptr;
     float *d_train_scratch = nullptr;
     size_t train_scratch_bytes = 0;
@@ -167,6 +169,9 @@ static Workspace make_ws(nedf_handle *h)
     ws.ppairs = h->d_ppairs;
     ws.pcap = h->cfg.primary_pair_capacity;
     ws.spairs = h->d_spairs;
+    ws.pgeo = h->d_pgeo;
+    ws.sgeo = h->d_sgeo;
+    ws.sell = h->d_sell;
     ws.scap = h->cfg.shadow_pair_capacity;
     ws.hlist = h->d_hlist;
     ws.cnt = h->d_cnt;
@@ -283,6 +288,9 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
     CA(h->d_out, sizeof(float4) * npix);
     CA(h->d_ppairs, sizeof(uint2) * h->cfg.primary_pair_capacity);
     CA(h->d_spairs, sizeof(uint2) * h->cfg.shadow_pair_capacity);
+    CA(h->d_pgeo, 2 * sizeof(float4) * h->cfg.primary_pair_capacity);
+    CA(h->d_sgeo, 2 * sizeof(float4) * h->cfg.shadow_pair_capacity);
+    CA(h->d_sell, sizeof(float) * h->cfg.shadow_pair_capacity);
     CA(h->d_cnt, sizeof(Counters));
     CA(h->d_status, sizeof(uint32_t));
     CA(h->d_loss, sizeof(float) * 4);
@@ -324,7 +332,7 @@ void nedf_compose_destroy(nedf_handle *h)
     cudaStreamSynchronize(h->stream);
     void *dev[] = {h->d_frame, h->d_cam, h->d_types, h->d_inst, h->d_nedf_w, h->d_nerf_w, h->d_keys,
                    h->d_depth, h->d_shadow, h->d_id, h->d_occl, h->d_hlist, h->d_rgba, h->d_out,
-                   h->d_ppairs, h->d_spairs, h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch,
+                   h->d_ppairs, h->d_spairs, h->d_pgeo, h->d_sgeo, h->d_sell, h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch,
                    h->d_march_scratch, h->d_nedf_tc, h->d_nerf_tc, h->d_fb[0], h->d_fb[1], h->d_lcam,
                    h->d_lg_count, h->d_lg_off, h->d_lg_cursor, h->d_lg_items, h->d_lg_big,
                    h->d_lg_big_count, h->d_scan_tmp};

@@ -76,11 +76,13 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
-// Appends (a, b) for every lane with keep set to segment `type` of a list; returns false when
-// the segment was full (the pair is dropped and the status word flagged).
+// Appends (a, b) for every lane with keep set to segment `type` of a list (and, when geo is not
+// null, the pair's two geometry vectors at the same index); a pair beyond the segment is dropped
+// and the status word flagged.
 __device__ __forceinline__ void warp_append(bool keep, uint2 val, unsigned long long *cursor,
                                             const unsigned long long *seg_end, uint2 *list,
-                                            uint32_t *status, uint32_t flag)
+                                            uint32_t *status, uint32_t flag, float4 *geo = nullptr,
+                                            float4 g0 = float4{}, float4 g1 = float4{})
 {
     unsigned mask = __ballot_sync(0xffffffffu, keep);
     if (!mask) return;
@@ -90,8 +92,15 @@ __device__ __forceinline__ void warp_append(bool keep, uint2 val, unsigned long 
     start = __shfl_sync(0xffffffffu, start, leader);
     if (keep) {
         unsigned long long idx = start + __popc(mask & lanemask_lt());
-        if (idx < *seg_end) list[idx] = val;
-        else atomicOr(status, flag);
+        if (idx < *seg_end) {
+            list[idx] = val;
+            if (geo) {
+                geo[2 * idx] = g0;
+                geo[2 * idx + 1] = g1;
+            }
+        } else {
+            atomicOr(status, flag);
+        }
     }
 }
 
@@ -114,19 +123,22 @@ __global__ void __launch_bounds__(kThreads) k_bin_primary(Workspace ws)
         int p = base + threadIdx.x;
         bool keep = false;
         int i = 0, j = 0;
+        V3 ol = v3(0, 0, 0), dl = v3(0, 0, 0);
+        Chord c{};
         if (p < npx) {
             i = i0 + p % bw; j = j0 + p / bw;
-            V3 o, d, ol, dl;
+            V3 o, d;
             camera_ray(f, i, j, o, d);
             to_local(I, o, d, ol, dl);
-            Chord c;
             keep = bound_chord(ol, dl, T.rb, c);
         }
         if (PASS == 0) {
             local += keep;
         } else {
             warp_append(keep, make_uint2((uint32_t)(j * f.W + i), (uint32_t)inst), &ws.cnt->p_cursor[I.type],
-                        &ws.cnt->p_off[I.type + 1], ws.ppairs, ws.status, kStatusPrimaryOverflow);
+                        &ws.cnt->p_off[I.type + 1], ws.ppairs, ws.status, kStatusPrimaryOverflow,
+                        ws.precision >= 1 ? ws.pgeo : nullptr, make_float4(ol.x, ol.y, ol.z, c.te),
+                        make_float4(dl.x, dl.y, dl.z, c.tp));
         }
     }
     if (PASS == 0) {

@@ -52,6 +52,12 @@ struct Workspace {
     long long pcap;
     uint2 *spairs;               // shadow (pixel * n_lights + light, instance)
     long long scap;
+    // pair geometry from the binning passes, for the tensor-core NeDF engine (precision >= 1): per
+    // pair (local origin, t_entry) and (local direction, t_perp); per shadow pair the world length
+    // from the light to the lit point
+    float4 *pgeo;                // [2 * pcap]
+    float4 *sgeo;                // [2 * scap]
+    float *sell;                 // [scap]
     uint32_t *hlist;             // [n_types][W*H] valid pixels per type
     Counters *cnt;
     uint32_t *status;

@@ -226,7 +226,9 @@ __device__ __forceinline__ uint32_t a_offset8(int r, int k)
     return (uint32_t)((k >> 4) * 2048 + (r >> 3) * 128 + (r & 7) * 16 + (k & 15));
 }
 
-template <int K>
+// KG: bytes between 8-column groups (2048 for a 128-row half; 4096 for the 256 rows of a swapped
+// NeDF tile, whose B operand spans both halves)
+template <int K, int KG = 2048>
 __device__ __forceinline__ void pipe_store_row(uint8_t *A, int r, const float *f, int n_valid)
 {
 #pragma unroll
@@ -240,7 +242,7 @@ __device__ __forceinline__ void pipe_store_row(uint8_t *A, int r, const float *f
             const float v1 = k + 1 < n_valid ? f[k + 1] : (k + 1 < n_valid + 2 ? 1.0f : 0.0f);
             p[e] = pack_bf16(v0, v1);
         }
-        *reinterpret_cast<uint4 *>(A + a_offset(r, c * 8)) = make_uint4(p[0], p[1], p[2], p[3]);
+        *reinterpret_cast<uint4 *>(A + (uint32_t)(c * KG + (r >> 3) * 128 + (r & 7) * 16)) = make_uint4(p[0], p[1], p[2], p[3]);
     }
 }
 
@@ -339,6 +341,43 @@ __device__ __forceinline__ void epi_layer(uint32_t tmem_row, uint8_t *Ag, int r,
             else epi_convert(vb, Ag, r, c0 + 32);
         }
         if (c0 + 64 < N) tmem_wait_ld(va);
+    }
+}
+
+// 32 rows of one feature (ReLU, BF16): four 16-byte vectors of eight rows, 128 bytes apart.
+__device__ __forceinline__ void epi_rows8(const uint32_t (&v)[32], uint8_t *dst)
+{
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const uint32_t *u = v + 8 * b;
+        uint4 pk;
+        pk.x = pack_bf16_relu(__uint_as_float(u[0]), __uint_as_float(u[1]));
+        pk.y = pack_bf16_relu(__uint_as_float(u[2]), __uint_as_float(u[3]));
+        pk.z = pack_bf16_relu(__uint_as_float(u[4]), __uint_as_float(u[5]));
+        pk.w = pack_bf16_relu(__uint_as_float(u[6]), __uint_as_float(u[7]));
+        *reinterpret_cast<uint4 *>(dst + b * 128) = pk;
+    }
+}
+
+// Epilogue of a swapped NeDF layer (D = W H^T: TMEM lane = output feature f, column = tile row):
+// the 128 columns from tcol are rows row0 .. row0 + 127.  Each value is ReLU'd, rounded to BF16 and
+// stored as the next layer's B operand, MN-major: 16-feature chunk f / 16 at 8 KB steps, 8-feature
+// group at 4 KB, feature f % 8 at 16 bytes, rows contiguous in 16-byte vectors of eight (128 bytes
+// per 8-row group).  TMEM loads double-buffered as in epi_layer.
+__device__ __forceinline__ void epi_swapped(uint32_t tcol, uint8_t *H, int f, int row0)
+{
+    uint8_t *dst = H + (f >> 4) * 8192 + ((f >> 3) & 1) * 4096 + (f & 7) * 16 + (row0 >> 3) * 128;
+    uint32_t va[32], vb[32];
+    tmem_ld32(tcol, va);
+    tmem_wait_ld(va);
+#pragma unroll 1
+    for (int c0 = 0; c0 < 128; c0 += 64) {
+        tmem_ld32(tcol + c0 + 32, vb);
+        epi_rows8(va, dst + (c0 >> 3) * 128);
+        tmem_wait_ld(vb);
+        if (c0 + 64 < 128) tmem_ld32(tcol + c0 + 64, va);
+        epi_rows8(vb, dst + ((c0 + 32) >> 3) * 128);
+        if (c0 + 64 < 128) tmem_wait_ld(va);
     }
 }
 
@@ -726,19 +765,38 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
 // convert the other slot's previous layer, and a slot's tail and next set-up overlap the other
 // slot's MMAs.  The CTA's tiles alternate between the slots; the producer, the MMA issuer and the
 // epilogue walk the same sequence (round r: for each layer l, slot 0 then slot 1).
+//
+// BF16 width 128 swaps the operands of every layer but the last: D^T = W H^T with the weight chunk
+// as A (M = 128 output features) and the tile's 256 rows as B (N = 256), one MMA per chunk.  A
+// thread issues a tcgen05.mma about every 50 cycles, so M = N = 128 MMAs (64 cycles of the pipe)
+// leave the issuer no room for its waits and commits; N = 256 MMAs (128 cycles) do.  The swapped
+// accumulator has a feature per TMEM lane and a tile row per column, so the epilogue thread of
+// feature f writes the next layer's activations MN-major (eight rows per 16-byte vector).  Layer 0
+// reads the encoded rows K-major (as the set-up writes them, one thread per row), and the last
+// hidden layer runs unswapped (A = the MN-major activations of each half, B = the weight chunk) so
+// that its accumulator is row-per-lane for the output fold and the tail.  The hidden biases fold
+// into one more chunk whose B (or, unswapped, A) operand is a constant block of ones shared by both
+// slots.
 // ---------------------------------------------------------------------------------------------------
 template <int N, bool F8>
 struct NedfShape2 {
     using B = PipeShape<N, false, F8>;
+    static constexpr bool SW = N == 128 && !F8;                             // swapped operands
+    static constexpr size_t H_BYTES = 65536;        // swapped: 8 chunks x 256 rows x 16 BF16 columns
+    static constexpr size_t ONES_BYTES = 8192;      // swapped: the bias chunk's constant operand
     // BF16 width 128: room for two whole 9-chunk layers (36 KB each), so a layer can be one stage
-    static constexpr int RING = F8 ? 131072 : (N == 128 ? 73728 : 65536);
+    static constexpr int RING = SW ? 81920 : F8 ? 131072 : (N == 128 ? 73728 : 65536);
     static constexpr int SMAX = RING / B::CHUNK;
-    static constexpr size_t FIXED = 4 * B::A_BYTES + (size_t)RING;          // + two fp32 blocks
+    static constexpr size_t ACT = SW ? 2 * H_BYTES + ONES_BYTES : 4 * B::A_BYTES;
+    static constexpr size_t FIXED = ACT + (size_t)RING;                     // + two fp32 blocks
 };
 
 // Pair index, validity and local ray of row R of a NeDF tile (Step-1 pairs, Step-3 pairs or caller
-// queries); the set-up uses it to encode the row and the tail recomputes it instead of keeping it.
-template <int MODE>
+// queries).  The set-up uses it to encode the row and the tail reloads it instead of keeping it.
+// A listed pair's local ray and chord come from the binning pass (one coalesced load, no chain of
+// dependent loads through the pair and instance records); the tail (TAIL) also needs the pair's
+// key, instance, scale and, for a shadow pair, the light-to-point length.
+template <int MODE, bool TAIL>
 __device__ __forceinline__ void nedf_row(const Workspace &ws, const DevFrame &f, const PipeArgs &a, const DevType &T,
                                          int t, unsigned long long tile, int R, unsigned long long &idx, bool &valid,
                                          PairRay &pr)
@@ -761,7 +819,22 @@ __device__ __forceinline__ void nedf_row(const Workspace &ws, const DevFrame &f,
         const unsigned long long *poff = MODE == kModePrimary ? C.p_off : C.s_off;
         idx = poff[t] + (tile - toff[t]) * kPipeRows + R;
         valid = idx < poff[t + 1];
-        if (valid) setup_pair_ray(ws, f, MODE == kModeShadow, (MODE == kModePrimary ? ws.ppairs : ws.spairs)[idx], T.rb, pr);
+        if (valid) {
+            const float4 *geo = MODE == kModePrimary ? ws.pgeo : ws.sgeo;
+            const float4 g0 = __ldg(&geo[2 * idx]), g1 = __ldg(&geo[2 * idx + 1]);
+            pr.ol = v3(g0.x, g0.y, g0.z);
+            pr.te = g0.w;
+            pr.dl = v3(g1.x, g1.y, g1.z);
+            pr.tp = g1.w;
+            pr.kept = true;                      // the binning lists only pairs that meet the bound
+            if (TAIL) {
+                const uint2 pp = __ldg(&(MODE == kModePrimary ? ws.ppairs : ws.spairs)[idx]);
+                pr.key = pp.x;
+                pr.inst = pp.y;
+                pr.s = __ldg(&ws.inst[pp.y].s);
+                pr.ell = MODE == kModeShadow ? __ldg(&ws.sell[idx]) : 0.0f;
+            }
+        }
     }
 }
 
@@ -779,9 +852,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
+    constexpr bool SW = S2::SW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = ws.nedf_hidden;
-    uint8_t *ring = smem + 4 * SH::A_BYTES;
+    uint8_t *ring = smem + S2::ACT;
+    uint8_t *ones_blk = smem + 2 * S2::H_BYTES;                 // swapped only
     const int n_f32 = (int)pipe_f32_floats(N, L, NOUT, F8);
     const size_t f32_bytes = ((size_t)n_f32 * 4 + 15) & ~(size_t)15;
     volatile int *abort = &abort_flag;
@@ -807,7 +882,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
     const unsigned long long n_tiles = pipe_n_tiles<N, MODE>(ws, mb, a);
     const unsigned long long gx = gridDim.x;
     const DevFrame &f = *ws.frame;
-    auto A_of = [&](int s, int h) { return smem + (size_t)(2 * s + h) * SH::A_BYTES; };
+    auto A_of = [&](int s, int h) { return smem + (size_t)(2 * s + h) * SH::A_BYTES; };   // unswapped
+    auto H_of = [&](int s) { return smem + (size_t)s * S2::H_BYTES; };                     // swapped
 
     if (warp == 8) {
         // ------------------------------ producer ------------------------------------------------
@@ -848,6 +924,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                         tc_fence_after();
                         const uint32_t ax = smem_addr(A_of(s, 0)), ay = smem_addr(A_of(s, 1));
                         const uint32_t dx = tmem + (uint32_t)(2 * s) * N, dy = dx + N;
+                        const uint32_t hs = smem_addr(H_of(s)), ones = smem_addr(ones_blk);
+                        // swapped layers: N = 256 rows, B MN-major (bit 16) after layer 0; the last
+                        // layer unswapped: A MN-major (bit 15) after layer 0
+                        const bool swapped = SW && l + 1 < L;
+                        const uint32_t id_sw = swapped ? idesc_bf16(128, 256) | (l > 0 ? 1u << 16 : 0u)
+                                                       : idesc_bf16(128, N) | (l > 0 ? 1u << 15 : 0u);
                         const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
                         const bool e4m3 = F8 && l > 0;
                         for (int c0 = 0; c0 < nk; c0 += GC, ++q) {
@@ -856,9 +938,28 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                             tc_fence_after();
                             const uint32_t stage = smem_addr(ring + (size_t)st * STAGE);
                             const int c1 = min(nk, c0 + GC);
-                            if (e4m3) issue_chunks<true>(dx, dy, ax, ay, stage, c0, c1, SH::CHUNK, idesc8, -1, 0u);
-                            else issue_chunks<false>(dx, dy, ax, ay, stage, c0, c1, SH::CHUNK, idesc,
-                                                     l > 0 ? N / kKC : -1, (uint32_t)(SH::ONES / kKC) * 4096u);
+                            if (SW) {
+                                // chunk c: input columns 16c..16c+15, 8 KB of the slot's
+                                // activations (8-column groups 4 KB apart, 8-row groups 128 bytes
+                                // apart); a hidden layer's bias chunk reads the ones block
+                                uint64_t wd = smem_desc(stage, 128, 256);
+                                for (int c = c0; c < c1; ++c) {
+                                    const uint32_t src = (l > 0 && c == N / kKC) ? ones : hs + (uint32_t)c * 8192u;
+                                    const uint32_t acc = c > 0 ? 1u : 0u;
+                                    if (swapped) {
+                                        mma_bf16(dx, wd, smem_desc(src, 4096, 128), id_sw, acc);
+                                    } else {
+                                        mma_bf16(dx, smem_desc(src, 4096, 128), wd, id_sw, acc);
+                                        mma_bf16(dy, smem_desc(src + 2048u, 4096, 128), wd, id_sw, acc);
+                                    }
+                                    wd += (uint64_t)(SH::CHUNK >> 4);
+                                }
+                            } else if (e4m3) {
+                                issue_chunks<true>(dx, dy, ax, ay, stage, c0, c1, SH::CHUNK, idesc8, -1, 0u);
+                            } else {
+                                issue_chunks<false>(dx, dy, ax, ay, stage, c0, c1, SH::CHUNK, idesc,
+                                                    l > 0 ? N / kKC : -1, (uint32_t)(SH::ONES / kKC) * 4096u);
+                            }
                             mma_commit(&w_empty[st]);
                             issued_any = true;
                         }
@@ -880,11 +981,20 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                           reinterpret_cast<float *>(smem + S2::FIXED + f32_bytes)};
         int f32_type[2] = {-1, -1};
         unsigned long long jb[2] = {0, 0};
-        if (!F8)
+        if (SW) {
+            // the ones block, MN-major like the activations: input columns 0 and 1 are 1 for all 256
+            // rows (the 16-byte vectors 0 and 1 of each 8-row group), the rest 0
+            for (int u = threadIdx.x; u < (int)(S2::ONES_BYTES / 16); u += 2 * kHalf) {
+                const bool one = u * 16 < 4096 && ((u * 16) & 127) < 32;
+                const uint32_t w = one ? pack_bf16(1.0f, 1.0f) : 0u;
+                reinterpret_cast<uint4 *>(ones_blk)[u] = make_uint4(w, w, w, w);
+            }
+        } else if (!F8) {
             for (int s = 0; s < 2; ++s) {
                 *reinterpret_cast<uint4 *>(A_of(s, g) + a_offset(r, SH::ONES)) = make_uint4(pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
                 *reinterpret_cast<uint4 *>(A_of(s, g) + a_offset(r, SH::ONES + 8)) = make_uint4(0u, 0u, 0u, 0u);
             }
+        }
         // set-up of slot s for `tile`: its type's fp32 block, the encoded rows, then a_ready
         auto setup = [&](int s, unsigned long long tile) {
             const int t = pipe_tile_type<MODE>(ws, mb, a, tile);
@@ -900,7 +1010,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
             unsigned long long idx;
             bool valid;
             PairRay pr;
-            nedf_row<MODE>(ws, f, a, T, t, tile, R, idx, valid, pr);
+            nedf_row<MODE, false>(ws, f, a, T, t, tile, R, idx, valid, pr);
             float x6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (valid && pr.kept) {
                 const V3 pe = madd(pr.ol, pr.te, pr.dl);
@@ -908,7 +1018,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
             }
             float feat[K0];
             pipe_encode<6, 6>(x6, feat);
-            pipe_store_row<K0>(A_of(s, g), r, feat, kNedfIn);
+            if (SW) pipe_store_row<K0, 4096>(H_of(s), R, feat, kNedfIn);
+            else pipe_store_row<K0>(A_of(s, g), r, feat, kNedfIn);
             fence_proxy_async_smem();
             tc_fence_before();
             mbar_arrive(&a_ready[s]);
@@ -920,7 +1031,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
             unsigned long long idx;
             bool valid;
             PairRay pr;
-            nedf_row<MODE>(ws, f, a, T, t, tile, R, idx, valid, pr);
+            nedf_row<MODE, true>(ws, f, a, T, t, tile, R, idx, valid, pr);
             if (MODE == kModeQuery) {
                 if (valid) {
                     float4 res = make_float4(0.f, 0.f, __int_as_float(0x7f800000), 0.f);
@@ -976,7 +1087,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                         const float sc = F8 && l > 0 ? f32[pipe_f8_bias_off(N, NOUT) + (size_t)L * N + l] : 1.0f;
                         float out[NOUT] = {f32[NOUT * N], f32[NOUT * N + 1]};
                         if (l + 1 < L) {
-                            if (F8 && l > 0) epi_layer<N, NOUT, F8, true, false>(trow, A_of(s, g), r, bias, sc, f32, out);
+                            if (SW) epi_swapped(tmem + lane_q + (uint32_t)(2 * s * N + g * kHalf), H_of(s), (warp & 3) * 32 + lane, g * kHalf);
+                            else if (F8 && l > 0) epi_layer<N, NOUT, F8, true, false>(trow, A_of(s, g), r, bias, sc, f32, out);
                             else epi_layer<N, NOUT, F8, false, false>(trow, A_of(s, g), r, bias, sc, f32, out);
                             fence_proxy_async_smem();
                             tc_fence_before();

@@ -288,13 +288,13 @@ __global__ void __launch_bounds__(256) k_bin_shadow_grid(Workspace ws, int npix)
         for (int k = 0; k < maxc; ++k) {
             bool keep = false;
             uint32_t inst = 0, ty = 0;
+            V3 ol = v3(0, 0, 0), dl = v3(0, 0, 0);
+            Chord ch{};
             if (k < count) {
                 inst = grid ? (k < nc ? ws.lg_items[c0 + k] : ws.lg_big[(size_t)l * ws.max_inst + (k - nc)]) : (uint32_t)k;
                 DevInst I = ws.inst[inst];
                 ty = I.type;
-                V3 ol, dl;
                 to_local(I, o, d, ol, dl);
-                Chord ch;
                 keep = bound_chord(ol, dl, ws.types[ty].rb, ch) && (ch.te * I.s < ell);
             }
             if (PASS == 0) {
@@ -312,8 +312,16 @@ __global__ void __launch_bounds__(256) k_bin_shadow_grid(Workspace ws, int npix)
                     if (lane == leader) start = atomicAdd(&ws.cnt->s_cursor[ty], (unsigned long long)__popc(peers));
                     start = __shfl_sync(peers, start, leader);
                     unsigned long long idx = start + __popc(peers & lane_lt());
-                    if (idx < ws.cnt->s_off[ty + 1]) ws.spairs[idx] = make_uint2(pix * nl + l, inst);
-                    else atomicOr(ws.status, kStatusShadowOverflow);
+                    if (idx < ws.cnt->s_off[ty + 1]) {
+                        ws.spairs[idx] = make_uint2(pix * nl + l, inst);
+                        if (ws.precision >= 1) {
+                            ws.sgeo[2 * idx] = make_float4(ol.x, ol.y, ol.z, ch.te);
+                            ws.sgeo[2 * idx + 1] = make_float4(dl.x, dl.y, dl.z, ch.tp);
+                            ws.sell[idx] = ell;
+                        }
+                    } else {
+                        atomicOr(ws.status, kStatusShadowOverflow);
+                    }
                 }
             }
         }
