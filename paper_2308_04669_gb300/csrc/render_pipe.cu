@@ -423,6 +423,21 @@ struct PipeArgs {
     int qn;
 };
 
+// Position in a ring of S weight stages: the stage and the parity of its current fill, kept by
+// increments (a 64-bit division by the run-time S would cost the issuing thread hundreds of cycles
+// per stage).
+struct RingPos {
+    int st = 0;
+    uint32_t ph = 0;
+    __device__ __forceinline__ void next(int S)
+    {
+        if (++st == S) {
+            st = 0;
+            ph ^= 1u;
+        }
+    }
+};
+
 struct PipeShared {
     uint64_t a_ready, acc_full, fin;
     uint32_t tmem_base;
@@ -542,16 +557,16 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
         // ------------------------------ producer ------------------------------------------------
         if (lane == 0) {
             unsigned long long q = 0;
+            RingPos rp;
             for (unsigned long long tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x) {
                 const uint8_t *blob = a.blobs + (size_t)pipe_tile_type<MODE>(ws, mb, a, tile) * a.blob_stride;
                 for (int l = 0; l < L && !*abort; ++l) {
                     const uint8_t *src = blob + pipe_layer_off(K0, N, l, F8);
                     const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
-                    for (int c0 = 0; c0 < nk; c0 += GC, ++q) {
-                        const int s = (int)(q % S);
-                        const uint32_t round = (uint32_t)(q / S);
+                    for (int c0 = 0; c0 < nk; c0 += GC, ++q, rp.next(S)) {
+                        const int s = rp.st;
                         const uint32_t bytes = (uint32_t)(min(GC, nk - c0) * SH::CHUNK);
-                        if (!pipe_wait(&w_empty[s], (round & 1u) ^ 1u, abort, ws.status)) break;
+                        if (!pipe_wait(&w_empty[s], rp.ph ^ 1u, abort, ws.status)) break;
                         mbar_arrive_expect_tx(&w_full[s], bytes);
                         bulk_g2s(ring + (size_t)s * STAGE, src + (size_t)c0 * SH::CHUNK, bytes, &w_full[s]);
                     }
@@ -564,7 +579,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
     } else if (warp == 9) {
         // ------------------------------ MMA issuer ----------------------------------------------
         if (lane == 0) {
-            unsigned long long q = 0, ja = 0;
+            unsigned long long ja = 0;
+            RingPos rp;
             const uint32_t idesc = idesc_bf16(128, N), idesc8 = idesc_e4m3(128, N);
             bool issued_any = false;
             for (unsigned long long tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x) {
@@ -574,9 +590,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                     const uint32_t ax = smem_addr(A[0]), ay = smem_addr(A[1]);
                     const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
                     const bool e4m3 = F8 && l > 0;
-                    for (int c0 = 0; c0 < nk; c0 += GC, ++q) {
-                        const int s = (int)(q % S);
-                        if (!pipe_wait(&w_full[s], (uint32_t)((q / S) & 1u), abort, ws.status)) break;
+                    for (int c0 = 0; c0 < nk; c0 += GC, rp.next(S)) {
+                        const int s = rp.st;
+                        if (!pipe_wait(&w_full[s], rp.ph, abort, ws.status)) break;
                         tc_fence_after();
                         const uint32_t stage = smem_addr(ring + (size_t)s * STAGE);
                         const int c1 = min(nk, c0 + GC);
@@ -846,6 +862,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
     constexpr int K0 = SH::K0, NOUT = 2;
     const int GC = max(1, min(a.stage_bytes / SH::CHUNK, S2::SMAX / 2));
     const int STAGE = GC * SH::CHUNK, S = S2::RING / STAGE;
+    // When a round's two tiles have the same type, one copy of each layer's weights serves both
+    // slots: the stages stay until the second slot's MMAs have read them, so the ring must hold
+    // every stage of a layer at once.
+    const int NK_MAX = max(K0 / kKC, F8 ? N / 32 : N / kKC + 1);
+    const bool can_share = S >= (NK_MAX + GC - 1) / GC;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t a_ready[2], acc_full[2], fin;
     __shared__ uint64_t w_full[S2::SMAX], w_empty[S2::SMAX];
@@ -889,19 +910,21 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
         // ------------------------------ producer ------------------------------------------------
         if (lane == 0) {
             unsigned long long q = 0;
+            RingPos rp;
             for (unsigned long long t0 = blockIdx.x; t0 < n_tiles && !*abort; t0 += 2 * gx) {
+                const bool two = t0 + gx < n_tiles;
+                const int ty0 = pipe_tile_type<MODE>(ws, mb, a, t0), ty1 = two ? pipe_tile_type<MODE>(ws, mb, a, t0 + gx) : ty0;
+                const bool share = can_share && ty0 == ty1;
                 for (int l = 0; l < L && !*abort; ++l)
                     for (int s = 0; s < 2 && !*abort; ++s) {
                         const unsigned long long tile = t0 + s * gx;
-                        if (tile >= n_tiles) continue;
-                        const uint8_t *src = a.blobs + (size_t)pipe_tile_type<MODE>(ws, mb, a, tile) * a.blob_stride +
-                                             pipe_layer_off(K0, N, l, F8);
+                        if (tile >= n_tiles || (s == 1 && share)) continue;
+                        const uint8_t *src = a.blobs + (size_t)(s ? ty1 : ty0) * a.blob_stride + pipe_layer_off(K0, N, l, F8);
                         const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
-                        for (int c0 = 0; c0 < nk; c0 += GC, ++q) {
-                            const int st = (int)(q % S);
-                            const uint32_t round = (uint32_t)(q / S);
+                        for (int c0 = 0; c0 < nk; c0 += GC, ++q, rp.next(S)) {
+                            const int st = rp.st;
                             const uint32_t bytes = (uint32_t)(min(GC, nk - c0) * SH::CHUNK);
-                            if (!pipe_wait(&w_empty[st], (round & 1u) ^ 1u, abort, ws.status)) break;
+                            if (!pipe_wait(&w_empty[st], rp.ph ^ 1u, abort, ws.status)) break;
                             mbar_arrive_expect_tx(&w_full[st], bytes);
                             bulk_g2s(ring + (size_t)st * STAGE, src + (size_t)c0 * SH::CHUNK, bytes, &w_full[st]);
                         }
@@ -913,15 +936,23 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
     } else if (warp == 9) {
         // ------------------------------ MMA issuer ----------------------------------------------
         if (lane == 0) {
-            unsigned long long q = 0, ja[2] = {0, 0};
+            unsigned long long ja[2] = {0, 0};
+            RingPos rp;
             const uint32_t idesc = idesc_bf16(128, N), idesc8 = idesc_e4m3(128, N);
             bool issued_any = false;
             for (unsigned long long t0 = blockIdx.x; t0 < n_tiles && !*abort; t0 += 2 * gx) {
-                for (int l = 0; l < L && !*abort; ++l)
+                // the same decision as the producer's: shared stages are walked twice and released
+                // by the second slot
+                const bool two = t0 + gx < n_tiles;
+                const bool share = can_share && (!two || pipe_tile_type<MODE>(ws, mb, a, t0) == pipe_tile_type<MODE>(ws, mb, a, t0 + gx));
+                for (int l = 0; l < L && !*abort; ++l) {
+                    const RingPos rp_layer = rp;
                     for (int s = 0; s < 2 && !*abort; ++s) {
                         if (t0 + s * gx >= n_tiles) continue;
                         if (!pipe_wait(&a_ready[s], (uint32_t)(ja[s]++ & 1u), abort, ws.status)) break;
                         tc_fence_after();
+                        if (share) rp = rp_layer;
+                        const bool release = !share || s == 1 || !two;
                         const uint32_t ax = smem_addr(A_of(s, 0)), ay = smem_addr(A_of(s, 1));
                         const uint32_t dx = tmem + (uint32_t)(2 * s) * N, dy = dx + N;
                         const uint32_t hs = smem_addr(H_of(s)), ones = smem_addr(ones_blk);
@@ -932,9 +963,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                                                        : idesc_bf16(128, N) | (l > 0 ? 1u << 15 : 0u);
                         const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
                         const bool e4m3 = F8 && l > 0;
-                        for (int c0 = 0; c0 < nk; c0 += GC, ++q) {
-                            const int st = (int)(q % S);
-                            if (!pipe_wait(&w_full[st], (uint32_t)((q / S) & 1u), abort, ws.status)) break;
+                        for (int c0 = 0; c0 < nk; c0 += GC, rp.next(S)) {
+                            const int st = rp.st;
+                            if (!pipe_wait(&w_full[st], rp.ph, abort, ws.status)) break;
                             tc_fence_after();
                             const uint32_t stage = smem_addr(ring + (size_t)st * STAGE);
                             const int c1 = min(nk, c0 + GC);
@@ -960,11 +991,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                                 issue_chunks<false>(dx, dy, ax, ay, stage, c0, c1, SH::CHUNK, idesc,
                                                     l > 0 ? N / kKC : -1, (uint32_t)(SH::ONES / kKC) * 4096u);
                             }
-                            mma_commit(&w_empty[st]);
+                            if (release) mma_commit(&w_empty[st]);
                             issued_any = true;
                         }
                         mma_commit(&acc_full[s]);
                     }
+                }
             }
             if (issued_any) {
                 mma_commit(&fin);
