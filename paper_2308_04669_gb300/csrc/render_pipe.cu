@@ -593,7 +593,6 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                     for (int c0 = 0; c0 < nk; c0 += GC, rp.next(S)) {
                         const int s = rp.st;
                         if (!pipe_wait(&w_full[s], rp.ph, abort, ws.status)) break;
-                        tc_fence_after();
                         const uint32_t stage = smem_addr(ring + (size_t)s * STAGE);
                         const int c1 = min(nk, c0 + GC);
                         if (e4m3) issue_chunks<true>(tmem, tmem + N, ax, ay, stage, c0, c1, SH::CHUNK, idesc8, -1, 0u);
@@ -966,7 +965,6 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                         for (int c0 = 0; c0 < nk; c0 += GC, rp.next(S)) {
                             const int st = rp.st;
                             if (!pipe_wait(&w_full[st], rp.ph, abort, ws.status)) break;
-                            tc_fence_after();
                             const uint32_t stage = smem_addr(ring + (size_t)st * STAGE);
                             const int c1 = min(nk, c0 + GC);
                             if (SW) {
@@ -1108,9 +1106,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                     if (stop) continue;
                     const unsigned long long tile = t0 + s * gx;
                     if (tile >= n_tiles) continue;
-                    // one outcome for all 256 epilogue threads before anything that synchronises them
+                    // a warp-uniform outcome (tcgen05.ld and the tail's ballots are warp-collective);
+                    // the last layer's step also synchronises the 256 epilogue threads (set-up), so
+                    // its outcome, and the decision to stop, are made for all of them there
+                    const bool last = l + 1 == L;
                     const bool okw = __all_sync(0xffffffffu, pipe_wait(&acc_full[s], (uint32_t)(jb[s]++ & 1u), abort, ws.status));
-                    const bool ok = !epilogue_any(!okw);
+                    const bool ok = last ? !epilogue_any(!okw) : okw;
                     if (ok) {
                         tc_fence_after();
                         const float *f32 = f32s[s];
@@ -1147,7 +1148,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                     } else {
                         *abort = 1;
                     }
-                    stop = epilogue_any(!ok || *abort);
+                    if (last) stop = epilogue_any(!ok || *abort);
                 }
         }
         if (!stop) {
