@@ -51,6 +51,7 @@ struct nedf_handle {
     uint2 *d_ppairs = nullptr, *d_spairs = nullptr;
     float4 *d_pgeo = nullptr, *d_sgeo = nullptr;
     float *d_sell = nullptr;
+    float2 *d_nout[2] = {nullptr, nullptr};
     Counters *d_cnt = nullptr;
     float *d_train_scratch = nullptr;
     size_t train_scratch_bytes = 0;
@@ -172,6 +173,8 @@ static Workspace make_ws(nedf_handle *h)
     ws.pgeo = h->d_pgeo;
     ws.sgeo = h->d_sgeo;
     ws.sell = h->d_sell;
+    ws.nout[0] = h->d_nout[0];
+    ws.nout[1] = h->d_nout[1];
     ws.scap = h->cfg.shadow_pair_capacity;
     ws.hlist = h->d_hlist;
     ws.cnt = h->d_cnt;
@@ -291,6 +294,8 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
     CA(h->d_pgeo, 2 * sizeof(float4) * h->cfg.primary_pair_capacity);
     CA(h->d_sgeo, 2 * sizeof(float4) * h->cfg.shadow_pair_capacity);
     CA(h->d_sell, sizeof(float) * h->cfg.shadow_pair_capacity);
+    CA(h->d_nout[0], sizeof(float2) * h->cfg.primary_pair_capacity);
+    CA(h->d_nout[1], sizeof(float2) * h->cfg.shadow_pair_capacity);
     CA(h->d_cnt, sizeof(Counters));
     CA(h->d_status, sizeof(uint32_t));
     CA(h->d_loss, sizeof(float) * 4);
@@ -332,7 +337,7 @@ void nedf_compose_destroy(nedf_handle *h)
     cudaStreamSynchronize(h->stream);
     void *dev[] = {h->d_frame, h->d_cam, h->d_types, h->d_inst, h->d_nedf_w, h->d_nerf_w, h->d_keys,
                    h->d_depth, h->d_shadow, h->d_id, h->d_occl, h->d_hlist, h->d_rgba, h->d_out,
-                   h->d_ppairs, h->d_spairs, h->d_pgeo, h->d_sgeo, h->d_sell, h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch,
+                   h->d_ppairs, h->d_spairs, h->d_pgeo, h->d_sgeo, h->d_sell, h->d_nout[0], h->d_nout[1], h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch,
                    h->d_march_scratch, h->d_nedf_tc, h->d_nerf_tc, h->d_fb[0], h->d_fb[1], h->d_lcam,
                    h->d_lg_count, h->d_lg_off, h->d_lg_cursor, h->d_lg_items, h->d_lg_big,
                    h->d_lg_big_count, h->d_scan_tmp};

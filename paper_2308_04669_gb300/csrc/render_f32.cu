@@ -545,9 +545,10 @@ cudaError_t launch_frame(FrameLaunch &L)
                             : nedf_dispatch(ws, gsm * 4, 0, st);
     if (e != cudaSuccess) return e;
     int launches = 6;
-    if (tc_nedf) {                        // pairs the tensor-core kernel deferred to the plain method
+    if (tc_nedf) {                        // decode, then the pairs deferred to the plain method
+        if ((e = launch_nedf_decode(ws, 0, gsm, st)) != cudaSuccess) return e;
         if ((e = launch_fallback(ws, 0, gsm, st)) != cudaSuccess) return e;
-        ++launches;
+        launches += 2;
     }
     mark();
     k_resolve<<<gsm * 4, 256, 0, st>>>(ws, npix);
@@ -563,8 +564,9 @@ cudaError_t launch_frame(FrameLaunch &L)
     e = tc_nedf ? launch_nedf_pipe(ws, 1, 0, nullptr, nullptr, nullptr, 0, gsm, st) : nedf_dispatch(ws, gsm * 4, 1, st);
     if (e != cudaSuccess) return e;
     if (tc_nedf) {
+        if ((e = launch_nedf_decode(ws, 1, gsm, st)) != cudaSuccess) return e;
         if ((e = launch_fallback(ws, 1, gsm, st)) != cudaSuccess) return e;
-        ++launches;
+        launches += 2;
     }
     mark();
     k_composite<<<gsm * 4, 256, 0, st>>>(ws, npix);

@@ -58,6 +58,7 @@ struct Workspace {
     float4 *pgeo;                // [2 * pcap]
     float4 *sgeo;                // [2 * scap]
     float *sell;                 // [scap]
+    float2 *nout[2];             // the engine's NeDF outputs (m, a) per listed pair: primary, shadow
     uint32_t *hlist;             // [n_types][W*H] valid pixels per type
     Counters *cnt;
     uint32_t *status;

@@ -36,6 +36,8 @@ cudaError_t launch_shade_pipe(const Workspace &ws, int npix, int num_sms, cudaSt
 cudaError_t launch_march_colour_pipe(const Workspace &ws, const MarchBuffers &mb, int n_samples, int num_sms,
                                      cudaStream_t st);
 cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStream_t st);
+// decode of the tensor-core engine's outputs of every listed pair (mode 0: Step 1, 1: Step 3)
+cudaError_t launch_nedf_decode(const Workspace &ws, int mode, int num_sms, cudaStream_t st);
 // one bounded mbarrier wait that nothing completes (sets the timeout status after its limit)
 cudaError_t launch_wait_check(uint32_t *status, cudaStream_t st);
 

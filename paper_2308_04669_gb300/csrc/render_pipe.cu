@@ -806,51 +806,113 @@ struct NedfShape2 {
     static constexpr size_t FIXED = ACT + (size_t)RING;                     // + two fp32 blocks
 };
 
-// Pair index, validity and local ray of row R of a NeDF tile (Step-1 pairs, Step-3 pairs or caller
-// queries).  The set-up uses it to encode the row and the tail reloads it instead of keeping it.
-// A listed pair's local ray and chord come from the binning pass (one coalesced load, no chain of
-// dependent loads through the pair and instance records); the tail (TAIL) also needs the pair's
-// key, instance, scale and, for a shadow pair, the light-to-point length.
-template <int MODE, bool TAIL>
-__device__ __forceinline__ void nedf_row(const Workspace &ws, const DevFrame &f, const PipeArgs &a, const DevType &T,
-                                         int t, unsigned long long tile, int R, unsigned long long &idx, bool &valid,
-                                         PairRay &pr)
+// Pair index of row R of a NeDF tile of type t (Step-1 pairs, Step-3 pairs or caller queries);
+// false past the end of the type's list (or of the queries).
+template <int MODE>
+__device__ __forceinline__ bool nedf_row_index(const Workspace &ws, const PipeArgs &a, int t, unsigned long long tile, int R,
+                                               unsigned long long &idx)
 {
-    pr.kept = false;
-    valid = false;
     if (MODE == kModeQuery) {
         idx = tile * kPipeRows + R;
-        valid = idx < (unsigned long long)a.qn;
-        if (valid) {
-            pr.ol = v3(a.qo[3 * idx], a.qo[3 * idx + 1], a.qo[3 * idx + 2]);
-            pr.dl = normalized(v3(a.qd[3 * idx], a.qd[3 * idx + 1], a.qd[3 * idx + 2]));
-            Chord ch;
-            pr.kept = bound_chord(pr.ol, pr.dl, T.rb, ch);
-            pr.te = ch.te; pr.tx = ch.tx; pr.tp = ch.tp;
-        }
+        return idx < (unsigned long long)a.qn;
+    }
+    const Counters &C = *ws.cnt;
+    const unsigned long long *toff = MODE == kModePrimary ? C.p_tile : C.s_tile;
+    const unsigned long long *poff = MODE == kModePrimary ? C.p_off : C.s_off;
+    idx = poff[t] + (tile - toff[t]) * kPipeRows + R;
+    return idx < poff[t + 1];
+}
+
+// Validity and local ray of row R of a NeDF tile, for its set-up (and a query's output).  A listed
+// pair's local ray and chord come from the binning pass: one coalesced load, no chain of dependent
+// loads through the pair and instance records.
+template <int MODE>
+__device__ __forceinline__ void nedf_row(const Workspace &ws, const PipeArgs &a, const DevType &T, int t,
+                                         unsigned long long tile, int R, unsigned long long &idx, bool &valid, PairRay &pr)
+{
+    pr.kept = false;
+    valid = nedf_row_index<MODE>(ws, a, t, tile, R, idx);
+    if (!valid) return;
+    if (MODE == kModeQuery) {
+        pr.ol = v3(a.qo[3 * idx], a.qo[3 * idx + 1], a.qo[3 * idx + 2]);
+        pr.dl = normalized(v3(a.qd[3 * idx], a.qd[3 * idx + 1], a.qd[3 * idx + 2]));
+        Chord ch;
+        pr.kept = bound_chord(pr.ol, pr.dl, T.rb, ch);
+        pr.te = ch.te; pr.tx = ch.tx; pr.tp = ch.tp;
     } else {
-        const Counters &C = *ws.cnt;
-        const unsigned long long *toff = MODE == kModePrimary ? C.p_tile : C.s_tile;
-        const unsigned long long *poff = MODE == kModePrimary ? C.p_off : C.s_off;
-        idx = poff[t] + (tile - toff[t]) * kPipeRows + R;
-        valid = idx < poff[t + 1];
-        if (valid) {
-            const float4 *geo = MODE == kModePrimary ? ws.pgeo : ws.sgeo;
-            const float4 g0 = __ldg(&geo[2 * idx]), g1 = __ldg(&geo[2 * idx + 1]);
+        const float4 *geo = MODE == kModePrimary ? ws.pgeo : ws.sgeo;
+        const float4 g0 = __ldg(&geo[2 * idx]), g1 = __ldg(&geo[2 * idx + 1]);
+        pr.ol = v3(g0.x, g0.y, g0.z);
+        pr.te = g0.w;
+        pr.dl = v3(g1.x, g1.y, g1.z);
+        pr.tp = g1.w;
+        pr.kept = true;                          // the binning lists only pairs that meet the bound
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Decode of the NeDF outputs of every listed pair (Eq. 2 and 7): depth and hit, the confidence
+// fallback, refinement and outlier re-answering, then the z-min (Step 1) or the occlusion bit
+// (Step 3); pairs deferred to the plain method go to its list.  One thread per pair, after the
+// engine (which only stores each pair's two outputs, keeping this work off its epilogue warps).
+// ---------------------------------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(256) k_nedf_decode(Workspace ws)
+{
+    static_assert(MODE == kModePrimary || MODE == kModeShadow, "listed pairs only");
+    constexpr bool SHADOW = MODE == kModeShadow;
+    const DevFrame &f = *ws.frame;
+    const Counters &C = *ws.cnt;
+    const unsigned long long *off = SHADOW ? C.s_off : C.p_off;
+    const int nt = f.n_types;
+    const unsigned long long n = off[nt];
+    const float4 *geo = SHADOW ? ws.sgeo : ws.pgeo;
+    const uint2 *pairs = SHADOW ? ws.spairs : ws.ppairs;
+    const float2 *nout = ws.nout[SHADOW ? 1 : 0];
+    const int lane = threadIdx.x & 31;
+    // the trip count is uniform within a block, so the ballot below sees whole warps
+    for (unsigned long long base = blockIdx.x * (unsigned long long)blockDim.x; base < n;
+         base += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long idx = base + threadIdx.x;
+        bool defer = false;
+        if (idx < n) {
+            int t = 0;
+            while (t + 1 < nt && off[t + 1] <= idx) ++t;
+            const DevType T = ws.types[t];
+            const float4 g0 = geo[2 * idx], g1 = geo[2 * idx + 1];
+            const uint2 pp = pairs[idx];
+            const float2 o = nout[idx];
+            PairRay pr;
             pr.ol = v3(g0.x, g0.y, g0.z);
             pr.te = g0.w;
             pr.dl = v3(g1.x, g1.y, g1.z);
             pr.tp = g1.w;
-            pr.kept = true;                      // the binning lists only pairs that meet the bound
-            if (TAIL) {
-                const uint2 pp = __ldg(&(MODE == kModePrimary ? ws.ppairs : ws.spairs)[idx]);
-                pr.key = pp.x;
-                pr.inst = pp.y;
-                pr.s = __ldg(&ws.inst[pp.y].s);
-                pr.ell = MODE == kModeShadow ? __ldg(&ws.sell[idx]) : 0.0f;
-            }
+            pr.key = pp.x;
+            pr.inst = pp.y;
+            pr.s = ws.inst[pp.y].s;
+            pr.ell = SHADOW ? ws.sell[idx] : 0.0f;
+            pr.kept = true;
+            float Dl;
+            bool hit;
+            defer = nedf_decode(f, T, pr.ol, pr.dl, pr.tp, o.x, o.y, Dl, hit);
+            if (!defer && hit) apply_hit(ws, f, SHADOW, pr, Dl);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, defer);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long start = 0;
+            if (lane == leader) start = atomicAdd(&ws.cnt->fb_count[SHADOW ? 1 : 0], (unsigned long long)__popc(m));
+            start = __shfl_sync(0xffffffffu, start, leader);
+            if (defer) ws.fb_list[SHADOW ? 1 : 0][start + __popc(m & ((1u << lane) - 1u))] = (uint32_t)idx;
         }
     }
+}
+
+cudaError_t launch_nedf_decode(const Workspace &ws, int mode, int num_sms, cudaStream_t st)
+{
+    if (mode == 1) k_nedf_decode<kModeShadow><<<num_sms * 8, 256, 0, st>>>(ws);
+    else k_nedf_decode<kModePrimary><<<num_sms * 8, 256, 0, st>>>(ws);
+    return cudaGetLastError();
 }
 
 template <int N, int MODE, bool F8>
@@ -1040,7 +1102,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
             unsigned long long idx;
             bool valid;
             PairRay pr;
-            nedf_row<MODE, false>(ws, f, a, T, t, tile, R, idx, valid, pr);
+            nedf_row<MODE>(ws, a, T, t, tile, R, idx, valid, pr);
             float x6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (valid && pr.kept) {
                 const V3 pe = madd(pr.ol, pr.te, pr.dl);
@@ -1054,15 +1116,16 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
             tc_fence_before();
             mbar_arrive(&a_ready[s]);
         };
-        // tail of slot s's tile: decode, z-min or occlusion, deferral to the plain method
-        auto tail = [&](int s, unsigned long long tile, const float *out) {
+        // output of a finished tile's row: a query's (m, a, D_l, hit), or a listed pair's (m, a) for
+        // the decode pass
+        auto emit = [&](unsigned long long tile, const float *out) {
             const int t = pipe_tile_type<MODE>(ws, mb, a, tile);
-            const DevType T = ws.types[t];
             unsigned long long idx;
-            bool valid;
-            PairRay pr;
-            nedf_row<MODE, true>(ws, f, a, T, t, tile, R, idx, valid, pr);
             if (MODE == kModeQuery) {
+                const DevType T = ws.types[t];
+                bool valid;
+                PairRay pr;
+                nedf_row<MODE>(ws, a, T, t, tile, R, idx, valid, pr);
                 if (valid) {
                     float4 res = make_float4(0.f, 0.f, __int_as_float(0x7f800000), 0.f);
                     if (pr.kept) {
@@ -1071,34 +1134,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                     }
                     a.qout[idx] = res;
                 }
-            } else {
-                bool defer = false;
-                if (valid) {
-                    float Dl;
-                    bool hit;
-                    defer = nedf_decode(f, T, pr.ol, pr.dl, pr.tp, out[0], out[1], Dl, hit);
-                    if (!defer && hit) apply_hit(ws, f, MODE == kModeShadow, pr, Dl);
-                }
-                const int mode = MODE == kModeShadow ? 1 : 0;
-                const unsigned m = __ballot_sync(0xffffffffu, defer);
-                if (m) {
-                    const int leader = __ffs(m) - 1;
-                    unsigned long long start = 0;
-                    if (lane == leader) start = atomicAdd(&ws.cnt->fb_count[mode], (unsigned long long)__popc(m));
-                    start = __shfl_sync(0xffffffffu, start, leader);
-                    if (defer) ws.fb_list[mode][start + __popc(m & ((1u << lane) - 1u))] = (uint32_t)idx;
-                }
+            } else if (nedf_row_index<MODE>(ws, a, t, tile, R, idx)) {
+                ws.nout[MODE == kModeShadow ? 1 : 0][idx] = make_float2(out[0], out[1]);
             }
         };
         if (blockIdx.x < n_tiles) setup(0, blockIdx.x);
         if (blockIdx.x + gx < n_tiles) setup(1, blockIdx.x + gx);
         bool stop = false;
-        // a finished tile's tail waits until its slot's next layer-0 epilogue is done: the epilogue
-        // warps then have slack (the slot's layer-1 MMAs run), and the other slot's last epilogue
-        // and set-up are not held up behind it
-        bool pend[2] = {false, false};
-        unsigned long long pend_tile[2] = {0, 0};
-        float pend_out[2][NOUT] = {};
         for (unsigned long long t0 = blockIdx.x; t0 < n_tiles && !stop; t0 += 2 * gx) {
             for (int l = 0; l < L && !stop; ++l)
 #pragma unroll
@@ -1106,7 +1148,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                     if (stop) continue;
                     const unsigned long long tile = t0 + s * gx;
                     if (tile >= n_tiles) continue;
-                    // a warp-uniform outcome (tcgen05.ld and the tail's ballots are warp-collective);
+                    // a warp-uniform outcome (tcgen05.ld is warp-collective);
                     // the last layer's step also synchronises the 256 epilogue threads (set-up), so
                     // its outcome, and the decision to stop, are made for all of them there
                     const bool last = l + 1 == L;
@@ -1132,29 +1174,15 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                             tc_fence_before();
                         }
                         if (l + 1 == L) {
+                            emit(tile, out);
                             const unsigned long long nxt = tile + 2 * gx;
                             if (!epilogue_any(*abort != 0) && nxt < n_tiles) setup(s, nxt);
-                        }
-                        if (l == 0 && pend[s]) {
-                            tail(s, pend_tile[s], pend_out[s]);
-                            pend[s] = false;
-                        }
-                        if (l + 1 == L) {
-                            pend[s] = true;
-                            pend_tile[s] = tile;
-#pragma unroll
-                            for (int o = 0; o < NOUT; ++o) pend_out[s][o] = out[o];
                         }
                     } else {
                         *abort = 1;
                     }
                     if (last) stop = epilogue_any(!ok || *abort);
                 }
-        }
-        if (!stop) {
-#pragma unroll
-            for (int s = 0; s < 2; ++s)
-                if (pend[s]) tail(s, pend_tile[s], pend_out[s]);
         }
     }
     // ---- teardown ------------------------------------------------------------------------------
