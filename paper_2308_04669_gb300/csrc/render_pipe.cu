@@ -36,7 +36,6 @@ using namespace tc;
 constexpr int kPipeRows = 256;              // rows per tile (two MMA halves of 128)
 constexpr int kHalf = 128;
 constexpr int kPipeThreads = 320;           // 8 epilogue warps, producer, MMA issuer
-constexpr int kNedfThreads = 352;           // k_nedf2: 8 epilogue warps, producer, an MMA issuer per slot
 constexpr int kKC = 16;                     // K columns per weight chunk (one MMA K step)
 // A bulk copy costs its issuing thread a few hundred cycles whatever its size, so weights move in
 // stages of several chunks (one copy, one full and one empty barrier phase each).  The stage size
@@ -917,15 +916,20 @@ cudaError_t launch_nedf_decode(const Workspace &ws, int mode, int num_sms, cudaS
 }
 
 template <int N, int MODE, bool F8>
-__global__ void __launch_bounds__(kNedfThreads, 1) k_nedf2(Workspace ws, MarchBuffers mb, PipeArgs a)
+__global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBuffers mb, PipeArgs a)
 {
     using SH = PipeShape<N, false, F8>;
     using S2 = NedfShape2<N, F8>;
     constexpr int K0 = SH::K0, NOUT = 2;
     const int GC = max(1, min(a.stage_bytes / SH::CHUNK, S2::SMAX / 2));
     const int STAGE = GC * SH::CHUNK, S = S2::RING / STAGE;
+    // When a round's two tiles have the same type, one copy of each layer's weights serves both
+    // slots: the stages stay until the second slot's MMAs have read them, so the ring must hold
+    // every stage of a layer at once.
+    const int NK_MAX = max(K0 / kKC, F8 ? N / 32 : N / kKC + 1);
+    const bool can_share = S >= (NK_MAX + GC - 1) / GC;
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t a_ready[2], acc_full[2], fin[2];
+    __shared__ uint64_t a_ready[2], acc_full[2], fin;
     __shared__ uint64_t w_full[S2::SMAX], w_empty[S2::SMAX];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -945,8 +949,7 @@ __global__ void __launch_bounds__(kNedfThreads, 1) k_nedf2(Workspace ws, MarchBu
             mbar_init(&a_ready[j], 2 * kHalf);
             mbar_init(&acc_full[j], 1);
         }
-        mbar_init(&fin[0], 1);
-        mbar_init(&fin[1], 1);
+        mbar_init(&fin, 1);
         for (int q = 0; q < S; ++q) {
             mbar_init(&w_full[q], 1);
             mbar_init(&w_empty[q], 1);
@@ -972,10 +975,11 @@ __global__ void __launch_bounds__(kNedfThreads, 1) k_nedf2(Workspace ws, MarchBu
             for (unsigned long long t0 = blockIdx.x; t0 < n_tiles && !*abort; t0 += 2 * gx) {
                 const bool two = t0 + gx < n_tiles;
                 const int ty0 = pipe_tile_type<MODE>(ws, mb, a, t0), ty1 = two ? pipe_tile_type<MODE>(ws, mb, a, t0 + gx) : ty0;
+                const bool share = can_share && ty0 == ty1;
                 for (int l = 0; l < L && !*abort; ++l)
                     for (int s = 0; s < 2 && !*abort; ++s) {
                         const unsigned long long tile = t0 + s * gx;
-                        if (tile >= n_tiles) continue;
+                        if (tile >= n_tiles || (s == 1 && share)) continue;
                         const uint8_t *src = a.blobs + (size_t)(s ? ty1 : ty0) * a.blob_stride + pipe_layer_off(K0, N, l, F8);
                         const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
                         for (int c0 = 0; c0 < nk; c0 += GC, ++q, rp.next(S)) {
@@ -990,29 +994,26 @@ __global__ void __launch_bounds__(kNedfThreads, 1) k_nedf2(Workspace ws, MarchBu
             const unsigned long long q0 = q > (unsigned long long)S ? q - S : 0;
             for (unsigned long long k = q0; k < q; ++k) pipe_drain(&w_full[k % S], (uint32_t)((k / S) & 1u), ws.status);
         }
-    } else if (warp >= 9) {
-        // ------------------------------ MMA issuers ---------------------------------------------
-        // one per slot (warp 9: slot 0, warp 10: slot 1): a thread issues a tcgen05.mma about every
-        // 50 cycles and its waits and commits come on top, so each slot's issuer works while the
-        // other waits.  Both walk the producer's stage sequence, each using (and releasing) only
-        // its own slot's stages.
+    } else if (warp == 9) {
+        // ------------------------------ MMA issuer ----------------------------------------------
         if (lane == 0) {
-            const int ms = warp - 9;
-            unsigned long long ja = 0;
+            unsigned long long ja[2] = {0, 0};
             RingPos rp;
             const uint32_t idesc = idesc_bf16(128, N), idesc8 = idesc_e4m3(128, N);
             bool issued_any = false;
             for (unsigned long long t0 = blockIdx.x; t0 < n_tiles && !*abort; t0 += 2 * gx) {
+                // the same decision as the producer's: shared stages are walked twice and released
+                // by the second slot
+                const bool two = t0 + gx < n_tiles;
+                const bool share = can_share && (!two || pipe_tile_type<MODE>(ws, mb, a, t0) == pipe_tile_type<MODE>(ws, mb, a, t0 + gx));
                 for (int l = 0; l < L && !*abort; ++l) {
+                    const RingPos rp_layer = rp;
                     for (int s = 0; s < 2 && !*abort; ++s) {
                         if (t0 + s * gx >= n_tiles) continue;
-                        const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
-                        if (s != ms) {                       // the other slot's stages
-                            for (int c0 = 0; c0 < nk; c0 += GC) rp.next(S);
-                            continue;
-                        }
-                        if (!pipe_wait(&a_ready[s], (uint32_t)(ja++ & 1u), abort, ws.status)) break;
+                        if (!pipe_wait(&a_ready[s], (uint32_t)(ja[s]++ & 1u), abort, ws.status)) break;
                         tc_fence_after();
+                        if (share) rp = rp_layer;
+                        const bool release = !share || s == 1 || !two;
                         const uint32_t ax = smem_addr(A_of(s, 0)), ay = smem_addr(A_of(s, 1));
                         const uint32_t dx = tmem + (uint32_t)(2 * s) * N, dy = dx + N;
                         const uint32_t hs = smem_addr(H_of(s)), ones = smem_addr(ones_blk);
@@ -1021,6 +1022,7 @@ __global__ void __launch_bounds__(kNedfThreads, 1) k_nedf2(Workspace ws, MarchBu
                         const bool swapped = SW && l + 1 < L;
                         const uint32_t id_sw = swapped ? idesc_bf16(128, 256) | (l > 0 ? 1u << 16 : 0u)
                                                        : idesc_bf16(128, N) | (l > 0 ? 1u << 15 : 0u);
+                        const int nk = l == 0 ? K0 / kKC : (F8 ? N / 32 : N / kKC + 1);
                         const bool e4m3 = F8 && l > 0;
                         for (int c0 = 0; c0 < nk; c0 += GC, rp.next(S)) {
                             const int st = rp.st;
@@ -1049,7 +1051,7 @@ __global__ void __launch_bounds__(kNedfThreads, 1) k_nedf2(Workspace ws, MarchBu
                                 issue_chunks<false>(dx, dy, ax, ay, stage, c0, c1, SH::CHUNK, idesc,
                                                     l > 0 ? N / kKC : -1, (uint32_t)(SH::ONES / kKC) * 4096u);
                             }
-                            mma_commit(&w_empty[st]);
+                            if (release) mma_commit(&w_empty[st]);
                             issued_any = true;
                         }
                         mma_commit(&acc_full[s]);
@@ -1057,8 +1059,8 @@ __global__ void __launch_bounds__(kNedfThreads, 1) k_nedf2(Workspace ws, MarchBu
                 }
             }
             if (issued_any) {
-                mma_commit(&fin[ms]);
-                pipe_drain(&fin[ms], 0u, ws.status);
+                mma_commit(&fin);
+                pipe_drain(&fin, 0u, ws.status);
             }
         }
     } else {
@@ -1276,7 +1278,7 @@ static cudaError_t launch_nedf2_n(const Workspace &ws, const PipeArgs &a, int gr
     cudaError_t e = cudaFuncSetAttribute(k_nedf2<N, MODE, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     MarchBuffers none{};
-    k_nedf2<N, MODE, F8><<<grid, kNedfThreads, sm, st>>>(ws, none, a);
+    k_nedf2<N, MODE, F8><<<grid, kPipeThreads, sm, st>>>(ws, none, a);
     return cudaGetLastError();
 }
 
