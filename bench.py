@@ -279,7 +279,7 @@ def run_ours(args):
     st = r.render(cam, lights, depth, ids, None, None, out, stats=True)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stage_sum = {}
+    stage_sum, engine_sum = {}, {}
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -291,19 +291,22 @@ def run_ours(args):
             ev[k][1].record(stream)
             for name, ms in r.stage_times().items():
                 stage_sum[name] = stage_sum.get(name, 0.0) + ms
+            for name, ms in r.engine_times().items():
+                engine_sum[name] = engine_sum.get(name, 0.0) + ms
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     barrier(world)
     frame_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     frame_ms_max = allmax(frame_ms, world)
     stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
+    engine_ms = {k: v / args.steps for k, v in engine_sum.items() if v > 0}   # the NeDF engine launches alone
     clocks = clk.summary()
 
     if args.frames_only:
         r.close()
         if rank == 0:
             print(json.dumps({"frames_only": True, "schedule": schedule, "ms_per_frame": frame_ms, "rays_per_s": n / (frame_ms * 1e-3),
-                              "stage_ms": stage_ms, "primary_pairs": st.primary_pairs, "shadow_pairs": st.shadow_pairs,
+                              "stage_ms": stage_ms, "engine_ms": engine_ms, "primary_pairs": st.primary_pairs, "shadow_pairs": st.shadow_pairs,
                               "hit_pixels": st.hit_pixels, "fallback_pairs": st.fallback_pairs}), flush=True)
         return
 
@@ -425,6 +428,10 @@ def run_ours(args):
                 "peak_basis": f"fp8 dense = bf16 dense {pk_kind} (burst) x 2 (nominal 4.5 / 2.25 PFLOP/s)"}
     for k in mlp_stages:
         mlp_stages[k]["frac"] = round(mlp_stages[k]["tflops"] / roof["peak"], 3)
+        if k in engine_ms:                 # the engine kernel alone (CUDA events around its launch)
+            t = flops[k] / (engine_ms[k] * 1e-3) / 1e12
+            mlp_stages[k].update(engine_ms=round(engine_ms[k], 4), engine_tflops=round(t, 1),
+                                 engine_frac=round(t / roof["peak"], 3))
 
     # ---- CPU baseline: the oracle on the host cores ------------------------------------------
     cpu = None

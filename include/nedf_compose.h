@@ -241,6 +241,14 @@ int nedf_compose_set_profiling(nedf_handle *h, int on);
  * array of n >= NEDF_N_STAGES floats.  Errors: NEDF_ERR_STATE when nothing was profiled. */
 int nedf_compose_get_stage_times(nedf_handle *h, float *ms, int n);
 
+#define NEDF_N_ENGINE_TIMES 2
+/* Device milliseconds of the tensor-core NeDF engine launch alone within the Step-1 and the
+ * Step-3 stage of the last profiled render (the stages also hold the output decode and the
+ * plain-method pairs): ms[0] Step 1, ms[1] Step 3; 0 where the frame ran no such launch (FP32
+ * precision or plain-method depth).  ms is a host array of n >= NEDF_N_ENGINE_TIMES floats;
+ * synchronises.  Errors: NEDF_ERR_STATE when nothing was profiled. */
+int nedf_compose_get_engine_times(nedf_handle *h, float *ms, int n);
+
 /* ---- checks (debug and tests; none of them faults, traps or hangs the GPU) -----------------------
  * nedf_compose_validate: synchronises, then checks the 256 guard bytes the library places after
  * every buffer it allocated at create (a kernel that wrote past a buffer's end shows here) and the

@@ -86,6 +86,8 @@ struct nedf_handle {
     int glaunches = 0;
     bool graphs = true;
     cudaEvent_t ev[kStages + 1] = {};
+    cudaEvent_t eng_ev[4] = {};       // around the Step-1 and Step-3 tensor-core NeDF engine launches
+    bool engines_timed = false, gengines = false;
     int last_launches = 0;
     int stage_bytes[NEDF_N_SCHEDULE] = {0, 0, 0, 0, 0};   // tensor-core schedule (0 = default)
     // guard bytes after every buffer allocated at create: (buffer, its size)
@@ -597,11 +599,14 @@ static int render_impl(nedf_handle *h, const nedf_camera *cam, const nedf_light 
     L.n_lights = n_lights;
     L.cam = h->d_cam;
     L.events = h->profiling ? h->ev : nullptr;
+    L.engine_events = h->profiling ? h->eng_ev : nullptr;
     L.launches = 0;
+    L.engines_timed = false;
     if (!h->graphs || h->stream == nullptr) {
         CK(h, enqueue_upload(h));
         CK(h, launch_frame(L));
         h->last_launches = L.launches;
+        h->engines_timed = L.engines_timed;
     } else {
         nedf_handle::FrameKey key{h->n_inst, n_lights, h->opt.depth_source, h->opt.n_shade, h->profiling ? 1 : 0,
                                   {depth, id, rgba, shadow, out}};
@@ -624,9 +629,11 @@ static int render_impl(nedf_handle *h, const nedf_camera *cam, const nedf_light 
             }
             h->gkey = key;
             h->glaunches = L.launches;
+            h->gengines = L.engines_timed;
         }
         CK(h, cudaGraphLaunch(h->gexec, h->stream));
         h->last_launches = h->glaunches;
+        h->engines_timed = h->gengines;
     }
     if (h->profiling) h->profiled = true;
     return NEDF_OK;
@@ -710,8 +717,10 @@ const char *nedf_compose_stage_name(int stage)
 int nedf_compose_set_profiling(nedf_handle *h, int on)
 {
     if (!h) return NEDF_ERR_ARG;
-    if (on && !h->ev[0])
+    if (on && !h->ev[0]) {
         for (cudaEvent_t &e : h->ev) CK(h, cudaEventCreate(&e));
+        for (cudaEvent_t &e : h->eng_ev) CK(h, cudaEventCreate(&e));
+    }
     h->profiling = on != 0;
     return NEDF_OK;
 }
@@ -722,6 +731,18 @@ int nedf_compose_get_stage_times(nedf_handle *h, float *ms, int n)
     if (!h->profiled) return fail(h, NEDF_ERR_STATE, "no profiled render");
     CK(h, cudaStreamSynchronize(h->stream));
     for (int i = 0; i < kStages; ++i) CK(h, cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
+    return NEDF_OK;
+}
+
+int nedf_compose_get_engine_times(nedf_handle *h, float *ms, int n)
+{
+    if (!h || !ms || n < NEDF_N_ENGINE_TIMES) return fail(h, NEDF_ERR_ARG, "ms must hold NEDF_N_ENGINE_TIMES floats");
+    if (!h->profiled) return fail(h, NEDF_ERR_STATE, "no profiled render");
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < NEDF_N_ENGINE_TIMES; ++i) {
+        ms[i] = 0.0f;
+        if (h->engines_timed) CK(h, cudaEventElapsedTime(&ms[i], h->eng_ev[2 * i], h->eng_ev[2 * i + 1]));
+    }
     return NEDF_OK;
 }
 

@@ -540,9 +540,18 @@ cudaError_t launch_frame(FrameLaunch &L)
     k_bin_primary<0><<<L.n_inst, kThreads, 0, st>>>(ws);
     k_scan_primary<<<1, 1, 0, st>>>(ws, nedf_rows);
     k_bin_primary<1><<<L.n_inst, kThreads, 0, st>>>(ws);
+    // the engine launch alone, inside its stage (the stage also holds the decode and fallback)
+    auto mark_engine = [&](int k) {
+        if (!L.events || !L.engine_events || !tc_nedf) return;
+        if (cap == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(L.engine_events[k], st, cudaEventRecordExternal);
+        else cudaEventRecord(L.engine_events[k], st);
+        L.engines_timed = true;
+    };
     mark();
+    mark_engine(0);
     cudaError_t e = tc_nedf ? launch_nedf_pipe(ws, 0, 0, nullptr, nullptr, nullptr, 0, gsm, st)
                             : nedf_dispatch(ws, gsm * 4, 0, st);
+    mark_engine(1);
     if (e != cudaSuccess) return e;
     int launches = 6;
     if (tc_nedf) {                        // decode, then the pairs deferred to the plain method
@@ -561,7 +570,9 @@ cudaError_t launch_frame(FrameLaunch &L)
     e = launch_shadow_binning(ws, npix, L.n_lights, L.n_inst, nedf_rows, gsm, st, &nbin);
     if (e != cudaSuccess) return e;
     mark();
+    mark_engine(2);
     e = tc_nedf ? launch_nedf_pipe(ws, 1, 0, nullptr, nullptr, nullptr, 0, gsm, st) : nedf_dispatch(ws, gsm * 4, 1, st);
+    mark_engine(3);
     if (e != cudaSuccess) return e;
     if (tc_nedf) {
         if ((e = launch_nedf_decode(ws, 1, gsm, st)) != cudaSuccess) return e;

@@ -15,6 +15,8 @@ struct FrameLaunch {
     int n_lights;
     const HostCamera *cam;   // device copy of this frame's camera
     cudaEvent_t *events;     // NULL, or kStages + 1 events recorded between the stages
+    cudaEvent_t *engine_events;   // with events: 4 more, around the Step-1 and Step-3 NeDF engine launches
+    bool engines_timed;      // out: the engine events were recorded
     int launches;            // out: kernels launched
 };
 

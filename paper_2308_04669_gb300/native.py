@@ -94,6 +94,7 @@ EXPORTS = {
     "nedf_compose_stage_name": ([C.c_int], C.c_char_p),
     "nedf_compose_set_profiling": ([_H, C.c_int], C.c_int),
     "nedf_compose_get_stage_times": ([_H, _fp, C.c_int], C.c_int),
+    "nedf_compose_get_engine_times": ([_H, _fp, C.c_int], C.c_int),
     "nedf_compose_validate": ([_H], C.c_int),
     "nedf_compose_inject_status": ([_H, C.c_uint32], C.c_int),
     "nedf_compose_check_wait_limit": ([_H], C.c_int),
@@ -276,6 +277,13 @@ class Renderer:
         ms = np.zeros(N_STAGES, np.float32)
         self._check(_lib.nedf_compose_get_stage_times(self.h, _fptr(ms), N_STAGES))
         return {_lib.nedf_compose_stage_name(i).decode(): float(ms[i]) for i in range(N_STAGES)}
+
+    def engine_times(self) -> dict:
+        """Milliseconds of the Step-1 and Step-3 tensor-core NeDF engine launches alone (last
+        profiled render; 0 where the frame ran none)."""
+        ms = np.zeros(2, np.float32)
+        self._check(_lib.nedf_compose_get_engine_times(self.h, _fptr(ms), 2))
+        return {"step1_nedf": float(ms[0]), "step3_nedf": float(ms[1])}
 
     def render_march(self, cam, n_samples, early_stop, rgba):
         return self._check(_lib.nedf_compose_render_march(self.h, C.byref(cam), n_samples, early_stop, _ptr(rgba)))

@@ -136,6 +136,39 @@ def test_bf16_plain_method_frame(orc):
     assert np.abs(es - g).max() < 2e-3
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_every_stage_size_on_a_large_frame(prec):
+    """The weight ring's handshake at every stage size the autotuner tries (and the smallest and
+    largest the API accepts) on the 1024-instance scene, where each CTA walks many tiles of both
+    slots and every type: a clean status word (no bounded wait ran out) and bitwise the same
+    depth, id and colour buffers as the default schedule."""
+    import torch
+    from paper_2308_04669_gb300 import native
+    sc = sg.thousand_scene(512, 512)
+    r = native.renderer_for(sc, precision=native.PREC_BF16 if prec == "bf16" else native.PREC_FP8)
+    o = r.get_options()
+    o.fallback_conf, o.refine_steps, o.outlier_resample = 0.9, 4, 1
+    r.set_options(o)
+    cam, li = r.camera(sc.eye, sc.target, sc.fov_deg), r.lights(sc.lights)
+    n = sc.W * sc.H
+
+    def frame():
+        d = torch.empty(n, device="cuda"); i = torch.empty(n, dtype=torch.int32, device="cuda")
+        c = torch.empty(n, 4, device="cuda")
+        st = r.render(cam, li, d, i, c, None, None, stats=True)
+        torch.cuda.synchronize()
+        assert st.status == 0 and st.primary_pairs > 100000 and st.shadow_pairs > 100000
+        return d.cpu().numpy(), i.cpu().numpy(), c.cpu().numpy()
+
+    ref = frame()
+    for b in (1024, 4096, 8192, 12288, 16384, 20480, 24576, 28672, 32768, 36864, 40960, 49152, 65536, 131072):
+        r.set_schedule([b] * native.N_SCHEDULE)
+        for _ in range(2):
+            got = frame()
+            assert all(np.array_equal(x, y) for x, y in zip(ref, got)), b
+    r.close()
+
+
 def test_schedule_changes_timing_not_results():
     """The stage size of the weight stream (set by hand or by the autotuner) never changes a
     frame: every schedule gives bitwise the same depth, id and colour buffers."""
