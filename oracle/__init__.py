@@ -60,7 +60,8 @@ class OrcScene(C.Structure):
 class OrcOpts(C.Structure):
     _fields_ = [("depth_mode", C.c_int), ("march_n", C.c_int), ("march_b", C.c_int),
                 ("quant", C.c_int), ("fallback_conf", C.c_double), ("refine_steps", C.c_int),
-                ("n_threads", C.c_int), ("outlier_resample", C.c_int)]
+                ("n_threads", C.c_int), ("outlier_resample", C.c_int), ("shade_resample", C.c_int),
+                ("shade_sigma_min", C.c_double)]
 
 
 def _dp(a):
@@ -91,7 +92,7 @@ def lib():
             l.orc_march_depth.argtypes = [sp, C.c_int, d, d, C.c_double, C.c_double, C.c_int, C.c_int, i]
             l.orc_march_depth.restype = C.c_double
             l.orc_composite_samples.argtypes = [C.c_int, d, d, C.c_double, d]
-            l.orc_render.argtypes = [sp, op, C.c_int64, i64, d, u32, d, d, d, d, d, d]
+            l.orc_render.argtypes = [sp, op, C.c_int64, i64, d, u32, d, d, d, d, d, d, d]
             l.orc_volume_render.argtypes = [sp, op, C.c_int, C.c_int64, i64, d]
             l.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]; l.orc_splitmix64.restype = C.c_uint64
             l.orc_train_rays.argtypes = [C.c_double, C.c_uint64, C.c_int64, C.c_int, d, d]
@@ -157,8 +158,9 @@ class OracleScene:
 
 
 def opts(depth_mode=DEPTH_MLP, march_n=128, march_b=4, quant=QUANT_NONE, fallback_conf=0.0,
-         refine_steps=0, n_threads=1, outlier_resample=0) -> OrcOpts:
-    return OrcOpts(depth_mode, march_n, march_b, quant, fallback_conf, refine_steps, n_threads, outlier_resample)
+         refine_steps=0, n_threads=1, outlier_resample=0, shade_resample=0, shade_sigma_min=1.0) -> OrcOpts:
+    return OrcOpts(depth_mode, march_n, march_b, quant, fallback_conf, refine_steps, n_threads, outlier_resample,
+                   shade_resample, shade_sigma_min)
 
 
 def render(osc: OracleScene, px=None, **kw):
@@ -169,12 +171,13 @@ def render(osc: OracleScene, px=None, **kw):
     px = np.ascontiguousarray(px, np.int64)
     n = px.shape[0]
     out = dict(depth=np.empty(n), id=np.empty(n, np.uint32), gap=np.empty(n), pmargin=np.empty(n),
-               rgba=np.empty((n, 4)), shadow=np.empty(n), smargin=np.empty(n), out=np.empty((n, 4)))
+               rgba=np.empty((n, 4)), shadow=np.empty(n), smargin=np.empty(n), out=np.empty((n, 4)),
+               shade_smax=np.empty(n))
     o = opts(**kw)
     lib().orc_render(osc.ptr, C.byref(o), n, px.ctypes.data_as(C.POINTER(C.c_int64)),
                      _dp(out["depth"]), out["id"].ctypes.data_as(C.POINTER(C.c_uint32)),
                      _dp(out["gap"]), _dp(out["pmargin"]), _dp(out["rgba"]), _dp(out["shadow"]),
-                     _dp(out["smargin"]), _dp(out["out"]))
+                     _dp(out["smargin"]), _dp(out["out"]), _dp(out["shade_smax"]))
     out["px"] = px
     return out
 

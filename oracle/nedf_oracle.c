@@ -472,8 +472,9 @@ static void sample_colour(const orc_type *t, const double x[3], const double dl[
     for (int c = 0; c < 3; ++c) rgb[c] = 1.0 / (1.0 + exp(-y[c]));
 }
 
-static void shade_pixel(const orc_scene *sc, const orc_opts *op, const double o[3], const double d[3],
-                        int inst, double depth, double rgba[4])
+/* Step 2 for one pixel; returns the largest sample density (the outlier test of "rs") */
+static double shade_pixel(const orc_scene *sc, const orc_opts *op, const double o[3], const double d[3],
+                          int inst, double depth, double rgba[4])
 {
     const orc_type *t = &sc->types[sc->inst_type[inst]];
     double ol[3], dl[3], s = sc->inst_s[inst];
@@ -489,9 +490,16 @@ static void shade_pixel(const orc_scene *sc, const orc_opts *op, const double o[
         sample_colour(t, x, dl, op->quant, rgb + 3 * j);
     }
     orc_composite_samples(n, sig, rgb, s * delta, rgba);
+    double smax = 0.0;
+    for (int j = 0; j < n; ++j) smax = dmax(smax, sig[j]);
     free(sig);
     free(rgb);
+    return smax;
 }
+
+/* The plain method's colour of one pixel (defined with the volume renderer below). */
+typedef struct { double te_world; int inst; } vr_pair;
+static void vr_pixel(const orc_scene *sc, const orc_opts *op, int ns, int64_t p, vr_pair *pairs, double rgba[4]);
 
 /* ------------------------------------------------------------------------------------------ */
 /* Algorithm 1 (Steps 1-2) and Algorithm 2 (Step 3) for one pixel                               */
@@ -501,7 +509,7 @@ typedef struct {
     const orc_opts *op;
     const int64_t *px;
     int64_t begin, end;
-    double *depth, *gap, *pmargin, *rgba, *shadow, *smargin, *out;
+    double *depth, *gap, *pmargin, *rgba, *shadow, *smargin, *out, *shade_smax;
     uint32_t *id;
 } render_job;
 
@@ -523,10 +531,17 @@ static void render_one(const render_job *jb, int64_t k)
         if (D < best) { second = best; best = D; bid = (uint32_t)m; }
         else if (D < second) second = D;
     }
-    double rgba[4] = {0, 0, 0, 0}, S = 1.0, sm = INFINITY;
+    double rgba[4] = {0, 0, 0, 0}, S = 1.0, sm = INFINITY, smax = NAN;
     if (bid != 0xFFFFFFFFu) {
         /* STEP 2: shade with the winning model's radiance field only. */
-        shade_pixel(sc, op, o, d, (int)bid, best, rgba);
+        smax = shade_pixel(sc, op, o, d, (int)bid, best, rgba);
+        /* Outlier resampling: an extremely small density says the depth missed the surface; the
+         * pixel's colour then comes from the primary volume rendering of every model. */
+        if (op->shade_resample > 0 && smax < op->shade_sigma_min) {
+            vr_pair *buf = (vr_pair *)malloc(sizeof(vr_pair) * (sc->n_inst > 0 ? sc->n_inst : 1));
+            vr_pixel(sc, op, op->shade_resample, p, buf, rgba);
+            free(buf);
+        }
         /* STEP 3: x on the surface, shadow ray from each light towards x; an occluder hit
          * closer to the light than x by more than eps darkens by beta; lights averaged. */
         double x[3];
@@ -561,6 +576,7 @@ static void render_one(const render_job *jb, int64_t k)
     if (jb->rgba) for (int c = 0; c < 4; ++c) jb->rgba[4 * k + c] = rgba[c];
     if (jb->shadow) jb->shadow[k] = S;
     if (jb->smargin) jb->smargin[k] = sm;
+    if (jb->shade_smax) jb->shade_smax[k] = smax;
     if (jb->out) {
         for (int c = 0; c < 3; ++c) jb->out[4 * k + c] = rgba[c] * S;
         jb->out[4 * k + 3] = rgba[3];
@@ -576,7 +592,7 @@ static void *render_worker(void *arg)
 
 int orc_render(const orc_scene *sc, const orc_opts *op, int64_t n_px, const int64_t *px, double *depth,
                uint32_t *id, double *gap, double *pmargin, double *rgba, double *shadow, double *smargin,
-               double *out)
+               double *out, double *shade_smax)
 {
     int nt = op->n_threads > 1 ? op->n_threads : 1;
     if (nt > 256) nt = 256;
@@ -584,7 +600,7 @@ int orc_render(const orc_scene *sc, const orc_opts *op, int64_t n_px, const int6
     pthread_t th[256];
     for (int t = 0; t < nt; ++t) {
         render_job jb = {sc, op, px, n_px * t / nt, n_px * (t + 1) / nt, depth, gap, pmargin, rgba,
-                         shadow, smargin, out, id};
+                         shadow, smargin, out, shade_smax, id};
         jobs[t] = jb;
     }
     if (nt == 1) { render_worker(&jobs[0]); return 0; }
@@ -596,8 +612,6 @@ int orc_render(const orc_scene *sc, const orc_opts *op, int64_t n_px, const int6
 /* ------------------------------------------------------------------------------------------ */
 /* Plain method colour: every NeRF volume-rendered front to back (ordered by entry distance)    */
 /* ------------------------------------------------------------------------------------------ */
-typedef struct { double te_world; int inst; } vr_pair;
-
 static int cmp_pair(const void *a, const void *b)
 {
     const vr_pair *x = (const vr_pair *)a, *y = (const vr_pair *)b;
@@ -610,44 +624,48 @@ typedef struct {
     const orc_scene *sc; const orc_opts *op; int ns; const int64_t *px; int64_t begin, end; double *rgba;
 } vr_job;
 
+/* Pixel p: its (ray, model) pairs that meet the bounds, front to back by (entry distance, id),
+ * each volume rendered with ns midpoint samples over its chord. */
+static void vr_pixel(const orc_scene *sc, const orc_opts *op, int ns, int64_t p, vr_pair *pairs, double rgba[4])
+{
+    double o[3], d[3], ol[3], dl[3], bd[4];
+    orc_camera_ray(sc, (int)(p % sc->W), (int)(p / sc->W), o, d);
+    int np = 0;
+    for (int m = 0; m < sc->n_inst; ++m) {
+        orc_to_local(sc, m, o, d, ol, dl);
+        if (!orc_bound(ol, dl, sc->types[sc->inst_type[m]].rb, bd)) continue;
+        pairs[np].te_world = bd[0] * sc->inst_s[m];
+        pairs[np].inst = m;
+        ++np;
+    }
+    qsort(pairs, np, sizeof(vr_pair), cmp_pair);
+    double T = 1.0, C[3] = {0, 0, 0};
+    for (int q = 0; q < np; ++q) {
+        int m = pairs[q].inst;
+        const orc_type *t = &sc->types[sc->inst_type[m]];
+        double s = sc->inst_s[m];
+        orc_to_local(sc, m, o, d, ol, dl);
+        orc_bound(ol, dl, t->rb, bd);
+        double dt = (bd[1] - bd[0]) / ns;
+        for (int j = 0; j < ns; ++j) {
+            double tj = bd[0] + (j + 0.5) * dt, x[3], rgb[3];
+            for (int c = 0; c < 3; ++c) x[c] = ol[c] + tj * dl[c];
+            double alpha = 1.0 - exp(-orc_density(sc, sc->inst_type[m], x) * s * dt);
+            sample_colour(t, x, dl, op->quant, rgb);
+            for (int c = 0; c < 3; ++c) C[c] += T * alpha * rgb[c];
+            T *= 1.0 - alpha;
+        }
+    }
+    for (int c = 0; c < 3; ++c) rgba[c] = C[c];
+    rgba[3] = 1.0 - T;
+}
+
 static void *vr_worker(void *arg)
 {
     const vr_job *jb = (const vr_job *)arg;
     const orc_scene *sc = jb->sc;
     vr_pair *pairs = (vr_pair *)malloc(sizeof(vr_pair) * (sc->n_inst > 0 ? sc->n_inst : 1));
-    for (int64_t k = jb->begin; k < jb->end; ++k) {
-        int64_t p = jb->px[k];
-        double o[3], d[3], ol[3], dl[3], bd[4];
-        orc_camera_ray(sc, (int)(p % sc->W), (int)(p / sc->W), o, d);
-        int np = 0;
-        for (int m = 0; m < sc->n_inst; ++m) {
-            orc_to_local(sc, m, o, d, ol, dl);
-            if (!orc_bound(ol, dl, sc->types[sc->inst_type[m]].rb, bd)) continue;
-            pairs[np].te_world = bd[0] * sc->inst_s[m];
-            pairs[np].inst = m;
-            ++np;
-        }
-        qsort(pairs, np, sizeof(vr_pair), cmp_pair);
-        double T = 1.0, C[3] = {0, 0, 0};
-        for (int q = 0; q < np; ++q) {
-            int m = pairs[q].inst;
-            const orc_type *t = &sc->types[sc->inst_type[m]];
-            double s = sc->inst_s[m];
-            orc_to_local(sc, m, o, d, ol, dl);
-            orc_bound(ol, dl, t->rb, bd);
-            double dt = (bd[1] - bd[0]) / jb->ns;
-            for (int j = 0; j < jb->ns; ++j) {
-                double tj = bd[0] + (j + 0.5) * dt, x[3], rgb[3];
-                for (int c = 0; c < 3; ++c) x[c] = ol[c] + tj * dl[c];
-                double alpha = 1.0 - exp(-orc_density(sc, sc->inst_type[m], x) * s * dt);
-                sample_colour(t, x, dl, jb->op->quant, rgb);
-                for (int c = 0; c < 3; ++c) C[c] += T * alpha * rgb[c];
-                T *= 1.0 - alpha;
-            }
-        }
-        for (int c = 0; c < 3; ++c) jb->rgba[4 * k + c] = C[c];
-        jb->rgba[4 * k + 3] = 1.0 - T;
-    }
+    for (int64_t k = jb->begin; k < jb->end; ++k) vr_pixel(sc, jb->op, jb->ns, jb->px[k], pairs, jb->rgba + 4 * k);
     free(pairs);
     return NULL;
 }

@@ -67,6 +67,11 @@ typedef struct {
     int n_threads;
     int outlier_resample;  /* MLP mode, with refine_steps > 0: a NeDF hit whose window [D-h, D+h]
                               holds no density crossing is re-answered by the plain method */
+    int shade_resample;    /* Step-2 outlier resampling (Section "Deferred Shading", "rs"): a shaded
+                              pixel whose largest density over its n_shade samples is below
+                              shade_sigma_min is re-rendered by the plain method's volume rendering
+                              (this many samples per pair); 0 = off */
+    double shade_sigma_min;
 } orc_opts;
 
 /* Geometry and encoding */
@@ -101,7 +106,7 @@ void orc_composite_samples(int n, const double *sigma, const double *rgb, double
 /* Steps 1-3 of Algorithm 1 / Algorithm 2 for a list of pixels. */
 int orc_render(const orc_scene *sc, const orc_opts *op, int64_t n_px, const int64_t *px,
                double *depth, uint32_t *id, double *gap, double *pmargin, double *rgba,
-               double *shadow, double *smargin, double *out);
+               double *shadow, double *smargin, double *out, double *shade_smax);
 
 /* Plain method: dense front-to-back volume rendering with n samples per (ray, instance). */
 int orc_volume_render(const orc_scene *sc, const orc_opts *op, int n_samples, int64_t n_px,

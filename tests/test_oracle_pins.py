@@ -540,3 +540,52 @@ def test_adam_first_step_is_signed_lr(orc):
     m, v = np.zeros(4), np.zeros(4)
     orc.adam(theta, g, m, v, 1, 1e-3)
     assert np.allclose(theta, np.array([1.0, -2.0, 0.5, 3.0]) - 1e-3 * np.sign(g), rtol=0, atol=1e-3 * 1e-5)
+
+
+def _sphere_sample_smax(o, d, depth, n=8):
+    """Largest density over the n midpoint samples of [D - h, D + h] on the world ray (identity
+    instance): the analytic sphere density 50 sigmoid(-(|x| - 0.5) / w), in closed form, with the
+    scene's FP32 constants h = 0.05 and w = 0.01 as the oracle and the GPU receive them."""
+    h, w = float(np.float32(0.05)), float(np.float32(0.01))
+    ts = depth - h + (np.arange(n) + 0.5) * (2 * h / n)
+    x = o[None, :] + ts[:, None] * d[None, :]
+    sdf = np.linalg.norm(x, axis=1) - 0.5
+    return float(np.max(50.0 / (1.0 + np.exp(sdf / w))))
+
+
+def test_shade_outlier_resampling(orc):
+    """Step-2 outlier resampling ("rs", Section "Deferred Shading"; threshold 1 = 2 % of the peak
+    density, the reading of "extremely small"): on the tiny sphere with the untrained 4x64 NeDF,
+    whose depths mostly miss the surface, a pixel is re-rendered exactly when the largest of its 8
+    sample densities (closed form) is below the threshold; a re-rendered pixel whose ray passes deep
+    through the sphere gets the volume-rendered colour of an opaque albedo-0.7 object, (0.7, 0.7,
+    0.7, 1) (the quadrature telescopes to c (1 - T) and T vanishes); every other pixel keeps its
+    deferred-shading colour; with exact depths nothing is re-rendered."""
+    sc = sg.tiny_sphere_scene()
+    osc = orc.OracleScene(sc)
+    base = orc.render(osc, depth_mode=orc.DEPTH_MLP, n_threads=4)
+    rs = orc.render(osc, depth_mode=orc.DEPTH_MLP, n_threads=4, shade_resample=128, shade_sigma_min=1.0)
+    hit = base["id"] != 0xFFFFFFFF
+    assert hit.sum() > 500
+    n_rs = deep = 0
+    for k in np.nonzero(hit)[0]:
+        p = int(base["px"][k])
+        o, d = orc.camera_ray(osc, p % sc.W, p // sc.W)
+        smax = _sphere_sample_smax(np.asarray(o), np.asarray(d), base["depth"][k])
+        assert abs(rs["shade_smax"][k] - smax) <= 1e-9 * max(1.0, smax)
+        if abs(smax - 1.0) < 1e-6:
+            continue                                   # knife edge of the threshold
+        if smax < 1.0:
+            n_rs += 1
+            b = np.linalg.norm(np.cross(o, d))           # the ray's distance from the centre
+            if b < 0.45:
+                deep += 1
+                assert np.allclose(rs["rgba"][k], [0.7, 0.7, 0.7, 1.0], atol=1e-8), (k, rs["rgba"][k])
+        else:
+            assert np.array_equal(rs["rgba"][k], base["rgba"][k])
+    assert n_rs > 100 and deep >= 10, (n_rs, deep)
+    assert np.array_equal(rs["rgba"][~hit], base["rgba"][~hit])
+    ex = orc.render(osc, depth_mode=orc.DEPTH_EXACT, n_threads=4)
+    ex_rs = orc.render(osc, depth_mode=orc.DEPTH_EXACT, n_threads=4, shade_resample=128, shade_sigma_min=1.0)
+    assert np.nanmin(ex_rs["shade_smax"]) > 20.0
+    assert np.array_equal(ex["rgba"], ex_rs["rgba"])
