@@ -359,6 +359,55 @@ def run_ours(args):
         except native.NedfError as e:
             march[key] = {"unavailable": str(e)}
 
+    # ---- the same frame with Step-2 outlier resampling ("rs": pixels whose sample densities are
+    # all below 1 re-rendered by the plain method, 128 samples per pair), as the paper times it ----
+    rs = None
+    if not args.no_resample:
+        o_keep = r.get_options()
+        o_rs = r.get_options()
+        o_rs.shade_resample, o_rs.shade_sigma_min = 128, 1.0
+        r.set_options(o_rs)
+        for _ in range(2):
+            r.render(cam, lights, depth, ids, None, None, out)
+        st_rs = r.render(cam, lights, depth, ids, None, None, out, stats=True)
+        torch.cuda.synchronize()
+        ev_rs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for a, b in ev_rs:
+            flush.zero_()
+            a.record(stream)
+            r.render(cam, lights, depth, ids, None, None, out)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms_rs = sum(a.elapsed_time(b) for a, b in ev_rs) / len(ev_rs)
+        rs = {"ms_per_frame": ms_rs, "rays_per_s": n / (ms_rs * 1e-3), "resampled_pixels": int(st_rs.resampled_pixels),
+              "samples_per_pair": 128, "sigma_min": 1.0}
+        # the paper's order: no Step-1 refinement or re-answering, Step 2's density test instead
+        o_rs.refine_steps, o_rs.outlier_resample = 0, 0
+        r.set_options(o_rs)
+        for _ in range(2):
+            r.render(cam, lights, depth, ids, None, None, out)
+        st_nr = r.render(cam, lights, depth, ids, None, None, out, stats=True)
+        torch.cuda.synchronize()
+        for a, b in ev_rs:
+            flush.zero_()
+            a.record(stream)
+            r.render(cam, lights, depth, ids, None, None, out)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms_nr = sum(a.elapsed_time(b) for a, b in ev_rs) / len(ev_rs)
+        o_rs.shade_resample = 0
+        r.set_options(o_rs)
+        for a, b in ev_rs:
+            flush.zero_()
+            a.record(stream)
+            r.render(cam, lights, depth, ids, None, None, out)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms_wo = sum(a.elapsed_time(b) for a, b in ev_rs) / len(ev_rs)
+        rs["without_refinement"] = {"rs_ms_per_frame": ms_nr, "wo_rs_ms_per_frame": ms_wo,
+                                    "resampled_pixels": int(st_nr.resampled_pixels)}
+        r.set_options(o_keep)
+
     # ---- the same frame with the FP32 CUDA-core networks (reference precision) -----------------
     fp32 = None
     if prec != native.PREC_FP32 and not args.no_fp32:
@@ -465,6 +514,7 @@ def run_ours(args):
                       "fallback_rate": st.fallback_pairs / max(1, P1 + P3), "mlp_stages": mlp_stages,
                       "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "wall_s": t_wall},
             "fp32_frame": fp32,
+            "rs_frame": rs,
             "march_frame": march,
             "speedup_vs_march": {k: v["ms_per_frame"] / frame_ms for k, v in march.items() if "ms_per_frame" in v},
             "depth_err": derr, "schedule": schedule, **log}
@@ -491,6 +541,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tensor-core schedule")
+    ap.add_argument("--no-resample", action="store_true", help="skip the frame with Step-2 outlier resampling")
     ap.add_argument("--schedule", default="", help="fixed stage bytes per tensor-core kernel (shade, march colour, "
                     "Step-1 NeDF, Step-3 NeDF, query), comma-separated; skips the autotuner")
     ap.add_argument("--no-march-dense", dest="march_dense", action="store_false",

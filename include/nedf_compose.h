@@ -111,6 +111,13 @@ typedef struct nedf_options {
                              /* no crossing of the half-density level is an outlier (the density */
                              /* check of Section "Deferred Shading") and is re-answered by the   */
                              /* plain method; default 0                                          */
+    int shade_resample;      /* Step-2 outlier resampling ("rs", Section "Deferred Shading"): a     */
+                             /* shaded pixel whose largest density over its n_shade samples is    */
+                             /* below shade_sigma_min (its depth missed the surface) is re-rendered */
+                             /* by the plain method's volume rendering of every object on its ray  */
+                             /* with this many samples per pair (1 .. 1024); 0 = off (default)     */
+    float shade_sigma_min;   /* the outlier threshold ("extremely small" density); default 1.0,   */
+                             /* 2 % of the default peak density                                   */
 } nedf_options;
 
 typedef struct nedf_type_desc {
@@ -146,6 +153,7 @@ typedef struct nedf_frame_stats {
     int64_t fallback_pairs;        /* pairs re-answered by the plain method                     */
     int64_t kernel_launches;       /* kernels this library launched for the frame               */
     uint32_t status;               /* device status bits (0 = clean)                            */
+    int64_t resampled_pixels;      /* pixels re-rendered by Step-2 outlier resampling           */
 } nedf_frame_stats;
 
 typedef struct nedf_handle nedf_handle;

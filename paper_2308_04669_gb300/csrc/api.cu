@@ -67,15 +67,21 @@ struct nedf_handle {
     size_t nedf_tc_stride = 0, nerf_tc_stride = 0;
     void *d_march_scratch = nullptr;
     size_t march_scratch_bytes = 0;
+    uint32_t *d_rs_mask = nullptr;
+    uint2 *d_rs_pairs = nullptr;
+    Counters *d_rs_cnt = nullptr;
+    void *d_rs_scratch = nullptr;
+    size_t rs_scratch_bytes = 0;
+    long long rs_cap = 0;
     bool profiling = false, profiled = false;
     // CUDA graph of one frame, relaunched while its shape key is unchanged
     struct FrameKey {
-        int n_inst, n_lights, depth_source, n_shade, profiling;
+        int n_inst, n_lights, depth_source, n_shade, profiling, shade_resample;
         const void *out[5];
         bool operator==(const FrameKey &o) const
         {
             if (n_inst != o.n_inst || n_lights != o.n_lights || depth_source != o.depth_source ||
-                n_shade != o.n_shade || profiling != o.profiling)
+                n_shade != o.n_shade || profiling != o.profiling || shade_resample != o.shade_resample)
                 return false;
             for (int i = 0; i < 5; ++i)
                 if (out[i] != o.out[i]) return false;
@@ -177,6 +183,11 @@ static Workspace make_ws(nedf_handle *h)
     ws.sell = h->d_sell;
     ws.nout[0] = h->d_nout[0];
     ws.nout[1] = h->d_nout[1];
+    ws.rs_mask = h->d_rs_mask;
+    ws.rs_pairs = h->d_rs_pairs;
+    ws.rs_cnt = h->d_rs_cnt;
+    ws.rs_scratch = h->d_rs_scratch;
+    ws.rs_cap = h->rs_cap;
     ws.scap = h->cfg.shadow_pair_capacity;
     ws.hlist = h->d_hlist;
     ws.cnt = h->d_cnt;
@@ -253,7 +264,7 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
     if (h->cfg.primary_pair_capacity == 0) h->cfg.primary_pair_capacity = 8 * npix;
     if (h->cfg.shadow_pair_capacity == 0) h->cfg.shadow_pair_capacity = 4 * npix * NEDF_MAX_LIGHTS / 8;
     h->stream = (cudaStream_t)cuda_stream;
-    h->opt = nedf_options{8, 0.05f, 0.5f, 0.02f, 50.0f, 0.01f, NEDF_DEPTH_NEDF, 128, 4, 0.0f, 0, 0};
+    h->opt = nedf_options{8, 0.05f, 0.5f, 0.02f, 50.0f, 0.01f, NEDF_DEPTH_NEDF, 128, 4, 0.0f, 0, 0, 0, 1.0f};
     h->nedf_params = mlp_params(kNedfIn, c.nedf_hidden, c.nedf_width, 2);
     h->nerf_params = mlp_params(kNerfIn, c.nerf_hidden, c.nerf_width, 3);
     auto bail = [&](cudaError_t e, const char *what) {
@@ -339,7 +350,7 @@ void nedf_compose_destroy(nedf_handle *h)
     cudaStreamSynchronize(h->stream);
     void *dev[] = {h->d_frame, h->d_cam, h->d_types, h->d_inst, h->d_nedf_w, h->d_nerf_w, h->d_keys,
                    h->d_depth, h->d_shadow, h->d_id, h->d_occl, h->d_hlist, h->d_rgba, h->d_out,
-                   h->d_ppairs, h->d_spairs, h->d_pgeo, h->d_sgeo, h->d_sell, h->d_nout[0], h->d_nout[1], h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch,
+                   h->d_ppairs, h->d_spairs, h->d_pgeo, h->d_sgeo, h->d_sell, h->d_nout[0], h->d_nout[1], h->d_rs_mask, h->d_rs_pairs, h->d_rs_cnt, h->d_rs_scratch, h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch,
                    h->d_march_scratch, h->d_nedf_tc, h->d_nerf_tc, h->d_fb[0], h->d_fb[1], h->d_lcam,
                    h->d_lg_count, h->d_lg_off, h->d_lg_cursor, h->d_lg_items, h->d_lg_big,
                    h->d_lg_big_count, h->d_scan_tmp};
@@ -371,6 +382,32 @@ int nedf_compose_set_options(nedf_handle *h, const nedf_options *o)
         return fail(h, NEDF_ERR_ARG, "march_steps 1..65536, march_bisect 0..64");
     if (!(o->fallback_conf >= 0.f && o->fallback_conf <= 1.f) || o->refine_steps < 0 || o->refine_steps > 64)
         return fail(h, NEDF_ERR_ARG, "fallback_conf / refine_steps");
+    if (o->shade_resample < 0 || o->shade_resample > 1024 || !(o->shade_sigma_min >= 0.f) || !std::isfinite(o->shade_sigma_min))
+        return fail(h, NEDF_ERR_ARG, "shade_resample 0..1024, shade_sigma_min >= 0");
+    if (o->shade_resample > 0) {
+        // buffers of Step-2 resampling: outlier flags, a pair list of up to a quarter of the
+        // pixels' worth of pairs and the plain method's scratch for it (grown with the samples)
+        const long long npix = (long long)h->cfg.width * h->cfg.height;
+        const long long cap = std::max<long long>(1 << 16, std::min<long long>(h->cfg.primary_pair_capacity, npix / 4));
+        const size_t need = march_bytes((int)npix, cap, o->shade_resample);
+        if (!h->d_rs_mask) {
+            cudaError_t e = cudaMalloc((void **)&h->d_rs_mask, sizeof(uint32_t) * npix);
+            if (e == cudaSuccess) e = cudaMemset(h->d_rs_mask, 0, sizeof(uint32_t) * npix);
+            if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_rs_pairs, sizeof(uint2) * cap);
+            if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_rs_cnt, sizeof(Counters));
+            if (e != cudaSuccess) return cuda_fail(h, e, "resampling buffers");
+            h->rs_cap = cap;
+        }
+        if (need > h->rs_scratch_bytes) {
+            cudaStreamSynchronize(h->stream);
+            if (h->d_rs_scratch) cudaFree(h->d_rs_scratch);
+            h->d_rs_scratch = nullptr;
+            h->rs_scratch_bytes = 0;
+            cudaError_t e = cudaMalloc(&h->d_rs_scratch, need);
+            if (e != cudaSuccess) return cuda_fail(h, e, "resampling scratch");
+            h->rs_scratch_bytes = need;
+        }
+    }
     h->opt = *o;
     return NEDF_OK;
 }
@@ -392,7 +429,8 @@ int nedf_compose_sync(nedf_handle *h)
         CK(h, cudaMemset(h->d_status, 0, sizeof(uint32_t)));
         if (st & kStatusTimeout) return fail(h, NEDF_ERR_TIMEOUT, "a bounded device wait gave up");
         return fail(h, NEDF_ERR_CAPACITY, st & kStatusPrimaryOverflow ? "primary pair list overflowed"
-                                                                      : "shadow pair list overflowed");
+                                          : st & kStatusShadowOverflow ? "shadow pair list overflowed"
+                                                                       : "resampling pair list overflowed");
     }
     return NEDF_OK;
 }
@@ -537,6 +575,8 @@ static cudaError_t stage_frame(nedf_handle *h, const nedf_camera *cam, const ned
     f.fallback_conf = h->opt.fallback_conf;
     f.refine_steps = h->opt.refine_steps;
     f.outlier_resample = h->opt.outlier_resample;
+    f.shade_resample = h->opt.shade_resample;
+    f.shade_sigma_min = h->opt.shade_sigma_min;
     f.n_inst = h->n_inst;
     f.n_types = h->n_types;
     std::memcpy(h->h_cam->eye, cam->eye, sizeof(cam->eye));
@@ -571,6 +611,7 @@ static int fill_stats(nedf_handle *h, nedf_frame_stats *stats)
     stats->fallback_pairs = (int64_t)c.fallback;
     stats->kernel_launches = h->last_launches;
     stats->status = st;
+    stats->resampled_pixels = (int64_t)c.rs_pixels;
     return nedf_compose_sync(h);
 }
 
@@ -597,6 +638,7 @@ static int render_impl(nedf_handle *h, const nedf_camera *cam, const nedf_light 
     L.n_inst = h->n_inst;
     L.n_shade = h->opt.n_shade;
     L.n_lights = n_lights;
+    L.shade_resample = h->opt.shade_resample;
     L.cam = h->d_cam;
     L.events = h->profiling ? h->ev : nullptr;
     L.engine_events = h->profiling ? h->eng_ev : nullptr;
@@ -609,7 +651,7 @@ static int render_impl(nedf_handle *h, const nedf_camera *cam, const nedf_light 
         h->engines_timed = L.engines_timed;
     } else {
         nedf_handle::FrameKey key{h->n_inst, n_lights, h->opt.depth_source, h->opt.n_shade, h->profiling ? 1 : 0,
-                                  {depth, id, rgba, shadow, out}};
+                                  h->opt.shade_resample, {depth, id, rgba, shadow, out}};
         if (!h->gexec || !(key == h->gkey)) {
             if (h->gexec) {
                 cudaGraphExecDestroy(h->gexec);

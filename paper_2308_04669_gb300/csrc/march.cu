@@ -183,10 +183,13 @@ __global__ void __launch_bounds__(kThreads) k_march_colour(Workspace ws, MarchBu
     }
 }
 
-// Front-to-back over the pixel's pairs in (entry distance, instance id) order.
+// Front-to-back over the pixel's pairs in (entry distance, instance id) order.  LISTED: only the
+// pixels that have pairs in the list are written (Step-2 resampling runs on a subset).
+template <bool LISTED>
 __global__ void k_march_composite(Workspace ws, MarchBuffers mb, float4 *rgba, int npix)
 {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+        if (LISTED && mb.head[p] < 0) continue;
         float Tr = 1.0f, r = 0.f, g = 0.f, b = 0.f;
         float last_te = -1.0f;
         uint32_t last_id = 0;
@@ -276,7 +279,94 @@ cudaError_t launch_march_colour_frame(const FrameLaunch &L, void *scratch, long 
         }
         if (e != cudaSuccess) return e;
     }
-    k_march_composite<<<g, 256, 0, st>>>(ws, mb, rgba, npix);
+    k_march_composite<false><<<g, 256, 0, st>>>(ws, mb, rgba, npix);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Step-2 outlier resampling ("rs", Section "Deferred Shading"): the primary pairs of every pixel
+// the shading flagged (an extremely small density around its depth) become a pair list of their
+// own, with its own counters, and the kernels above render exactly those pixels by the plain
+// method (dense, n samples per pair, front to back) into the colour buffer.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_rs_collect(Workspace ws)
+{
+    const DevFrame &f = *ws.frame;
+    const unsigned long long n = ws.cnt->p_off[f.n_types];
+    const int lane = threadIdx.x & 31;
+    // the trip count is uniform within a block, so the ballots below see whole warps
+    for (unsigned long long base = blockIdx.x * (unsigned long long)blockDim.x; base < n;
+         base += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long q = base + threadIdx.x;
+        bool keep = false;
+        uint2 pp = make_uint2(0u, 0u);
+        uint32_t ty = 0;
+        if (q < n) {
+            pp = ws.ppairs[q];
+            keep = ws.rs_mask[pp.x] != 0u;
+            if (keep) ty = ws.inst[pp.y].type;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (!m) continue;
+        unsigned long long start = 0;
+        if (lane == __ffs(m) - 1) start = atomicAdd(&ws.rs_cnt->p_cursor[0], (unsigned long long)__popc(m));
+        start = __shfl_sync(0xffffffffu, start, __ffs(m) - 1);
+        if (keep) {
+            const unsigned long long idx = start + __popc(m & ((1u << lane) - 1u));
+            const bool fits = idx < (unsigned long long)ws.rs_cap;
+            if (fits) ws.rs_pairs[idx] = pp;
+            else atomicOr(ws.status, kStatusResampleOverflow);
+            // per-type counts of the kept pairs (they size the plain method's sample rows)
+            const unsigned kept = __ballot_sync(m, fits);
+            if (fits) {
+                const unsigned peers = __match_any_sync(kept, ty);
+                if (lane == __ffs(peers) - 1) atomicAdd(&ws.rs_cnt->p_count[ty], (unsigned long long)__popc(peers));
+            }
+        }
+    }
+}
+
+__global__ void k_rs_close(Workspace ws)
+{
+    const DevFrame &f = *ws.frame;
+    Counters &C = *ws.rs_cnt;
+    unsigned long long o = 0;
+    for (int t = 0; t < f.n_types; ++t) {
+        C.p_off[t] = o;
+        o += C.p_count[t];
+    }
+    C.p_off[f.n_types] = o;                  // = min(collected, capacity)
+}
+
+cudaError_t launch_shade_resample(const FrameLaunch &L)
+{
+    const Workspace &ws = L.ws;
+    cudaStream_t st = L.stream;
+    const int npix = L.W * L.H, g = L.num_sms * 4, n = L.shade_resample;
+    k_rs_collect<<<g * 2, 256, 0, st>>>(ws);
+    k_rs_close<<<1, 1, 0, st>>>(ws);
+    Workspace wr = ws;                       // the same frame, the resampling list as its pairs
+    wr.ppairs = ws.rs_pairs;
+    wr.pcap = ws.rs_cap;
+    wr.cnt = ws.rs_cnt;
+    MarchBuffers mb = carve_march(ws.rs_scratch, npix, ws.rs_cap, n);
+    k_march_clear<<<g, 256, 0, st>>>(wr, mb, npix, n);
+    k_march_pairs<false><<<g * 2, 128, 0, st>>>(wr, mb, n);
+    const bool tc = ws.precision >= 1 && ws.nerf_hidden > 0;
+    k_march_scan<<<1, 1, 0, st>>>(wr, mb, tc ? kPipeTileRows : kTileRows);
+    cudaError_t e = cudaSuccess;
+    if (tc) {
+        e = launch_march_colour_pipe(wr, mb, n, L.num_sms, st);
+    } else if (ws.nerf_hidden > 0) {
+        switch (ws.nerf_width) {
+        case 64: e = launch_colour<64>(wr, mb, n, g, st); break;
+        case 128: e = launch_colour<128>(wr, mb, n, g, st); break;
+        case 256: e = launch_colour<256>(wr, mb, n, g, st); break;
+        default: e = cudaErrorInvalidValue;
+        }
+    }
+    if (e != cudaSuccess) return e;
+    k_march_composite<true><<<g, 256, 0, st>>>(wr, mb, ws.rgba, npix);
     return cudaGetLastError();
 }
 

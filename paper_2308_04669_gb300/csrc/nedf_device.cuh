@@ -22,6 +22,7 @@ constexpr uint32_t kNoId = 0xFFFFFFFFu;
 constexpr uint32_t kStatusPrimaryOverflow = 1u << 0;
 constexpr uint32_t kStatusShadowOverflow = 1u << 1;
 constexpr uint32_t kStatusTimeout = 1u << 2;
+constexpr uint32_t kStatusResampleOverflow = 1u << 3;   // Step-2 resampling: more pairs than its buffers
 
 struct DevType {
     int kind;
@@ -53,6 +54,8 @@ struct DevFrame {
     float fallback_conf;
     int refine_steps;
     int outlier_resample;
+    int shade_resample;          // Step-2 outlier resampling: plain-method samples per pair (0 = off)
+    float shade_sigma_min;
     int n_inst, n_types;
 };
 

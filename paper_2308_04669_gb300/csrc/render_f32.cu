@@ -30,6 +30,10 @@ __global__ void k_setup(Workspace ws, const HostCamera *cam)
     }
     unsigned long long *c = reinterpret_cast<unsigned long long *>(ws.cnt);
     for (int i = threadIdx.x; i < (int)(sizeof(Counters) / 8); i += blockDim.x) c[i] = 0ull;
+    if (ws.rs_cnt) {
+        unsigned long long *cr = reinterpret_cast<unsigned long long *>(ws.rs_cnt);
+        for (int i = threadIdx.x; i < (int)(sizeof(Counters) / 8); i += blockDim.x) cr[i] = 0ull;
+    }
 }
 
 __global__ void k_clear(Workspace ws, int npix)
@@ -37,6 +41,7 @@ __global__ void k_clear(Workspace ws, int npix)
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
         ws.keys[p] = ~0ull;
         ws.occl[p] = 0u;
+        if (ws.rs_mask) ws.rs_mask[p] = 0u;
     }
 }
 
@@ -404,9 +409,10 @@ __global__ void __launch_bounds__(kThreads) k_shade_tiles(Workspace ws, int npix
         // front-to-back composite of each pixel's samples (Eq. 8 over the window)
         if (threadIdx.x < n_pix) {
             int q = threadIdx.x;
-            float Tr = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
+            float Tr = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f, smax = 0.f;
             for (int j = 0; j < ns; ++j) {
                 int r = q * ns + j;
+                smax = fmaxf(smax, sig[r]);
                 float alpha = 1.0f - expf(-sig[r] * tile_ws[q]);
                 float R, G, B;
                 if (T.nerf) {
@@ -421,6 +427,7 @@ __global__ void __launch_bounds__(kThreads) k_shade_tiles(Workspace ws, int npix
                 Tr *= 1.0f - alpha;
             }
             ws.rgba[tile_pix[q]] = make_float4(cr, cg, cb, A);
+            flag_shade_outlier(ws, f, tile_pix[q], smax);
         }
         __syncthreads();
     }
@@ -565,6 +572,10 @@ cudaError_t launch_frame(FrameLaunch &L)
     mark();
     e = tc_shade ? launch_shade_pipe(ws, npix, gsm, st) : shade_dispatch(ws, gsm * 4, npix, st);
     if (e != cudaSuccess) return e;
+    if (L.shade_resample > 0 && ws.rs_mask) {       // Step-2 outliers: the plain method's colour
+        if ((e = launch_shade_resample(L)) != cudaSuccess) return e;
+        launches += ws.nerf_hidden > 0 ? 7 : 6;
+    }
     mark();
     int nbin = 0;
     e = launch_shadow_binning(ws, npix, L.n_lights, L.n_inst, nedf_rows, gsm, st, &nbin);

@@ -31,6 +31,7 @@ struct Counters {
     unsigned long long h_tile[kMaxTypes + 1];
     unsigned long long fallback;
     unsigned long long hit_pixels;
+    unsigned long long rs_pixels;                // Step-2 outliers re-rendered by the plain method
     unsigned long long p_total_requested;
     unsigned long long s_total_requested;
     unsigned long long fb_count[2];              // deferred plain-method pairs (primary, shadow)
@@ -59,6 +60,14 @@ struct Workspace {
     float4 *sgeo;                // [2 * scap]
     float *sell;                 // [scap]
     float2 *nout[2];             // the engine's NeDF outputs (m, a) per listed pair: primary, shadow
+    // Step-2 outlier resampling: per-pixel outlier flags, and the outliers' primary pairs as a list
+    // of their own with its own counters (the plain method's colour kernels then run on it as on
+    // the whole frame's pairs), plus their scratch
+    uint32_t *rs_mask;           // [W*H], or null while resampling was never enabled
+    uint2 *rs_pairs;             // [rs_cap]
+    Counters *rs_cnt;
+    void *rs_scratch;
+    long long rs_cap;
     uint32_t *hlist;             // [n_types][W*H] valid pixels per type
     Counters *cnt;
     uint32_t *status;
@@ -126,6 +135,20 @@ struct PairRay {
     uint32_t key, inst;
     bool kept;
 };
+
+// Step-2 outlier test ("rs", Section "Deferred Shading"): an extremely small density at every
+// sample around the predicted depth says the depth missed the surface; the pixel is flagged for
+// the plain method's volume rendering.  Called by the lanes that composite a pixel (any subset of
+// the warp); the count is warp-aggregated.
+__device__ __forceinline__ void flag_shade_outlier(const Workspace &ws, const DevFrame &f, uint32_t pix, float smax)
+{
+    const bool rs = f.shade_resample > 0 && smax < f.shade_sigma_min;
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, rs);
+    if (!m) return;
+    if (rs) ws.rs_mask[pix] = 1u;
+    if ((threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&ws.cnt->rs_pixels, (unsigned long long)__popc(m));
+}
 
 __device__ __forceinline__ void setup_pair_ray(const Workspace &ws, const DevFrame &f, bool shadow, uint2 pr,
                                                float rb, PairRay &R)

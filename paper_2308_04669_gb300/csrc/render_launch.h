@@ -13,6 +13,7 @@ struct FrameLaunch {
     int n_inst;
     int n_shade;
     int n_lights;
+    int shade_resample;      // Step-2 outlier resampling: plain-method samples per pair (0 = off)
     const HostCamera *cam;   // device copy of this frame's camera
     cudaEvent_t *events;     // NULL, or kStages + 1 events recorded between the stages
     cudaEvent_t *engine_events;   // with events: 4 more, around the Step-1 and Step-3 NeDF engine launches
@@ -38,6 +39,8 @@ cudaError_t launch_shade_pipe(const Workspace &ws, int npix, int num_sms, cudaSt
 cudaError_t launch_march_colour_pipe(const Workspace &ws, const MarchBuffers &mb, int n_samples, int num_sms,
                                      cudaStream_t st);
 cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStream_t st);
+// Step-2 outlier resampling (march.cu): the flagged pixels re-rendered by the plain method
+cudaError_t launch_shade_resample(const FrameLaunch &L);
 // decode of the tensor-core engine's outputs of every listed pair (mode 0: Step 1, 1: Step 3)
 cudaError_t launch_nedf_decode(const Workspace &ws, int mode, int num_sms, cudaStream_t st);
 // one bounded mbarrier wait that nothing completes (sets the timeout status after its limit)

@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                     const int ppg = kHalf / ns;
                     const unsigned long long first = (tile - ws.cnt->h_tile[t]) * (unsigned long long)(2 * ppg) + g * ppg;
                     if (r < ppg && first + r < ws.cnt->h_count[t]) {
-                        float Tr = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, Aa = 0.f;
+                        float Tr = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, Aa = 0.f, smax = 0.f;
                         const float wd = t_wd[g * kHalf + r];
                         for (int k = 0; k < ns; ++k) {
                             const int rr = g * kHalf + r * ns + k;
@@ -747,8 +747,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                             const float w = Tr * alpha;
                             cr += w * t_rgb[rr][0]; cg += w * t_rgb[rr][1]; cb += w * t_rgb[rr][2]; Aa += w;
                             Tr *= 1.0f - alpha;
+                            smax = fmaxf(smax, t_sig[rr]);
                         }
-                        ws.rgba[t_key[g * kHalf + r]] = make_float4(cr, cg, cb, Aa);
+                        const uint32_t pix = t_key[g * kHalf + r];
+                        ws.rgba[pix] = make_float4(cr, cg, cb, Aa);
+                        flag_shade_outlier(ws, f, pix, smax);
                     }
                 } else {
                     // one sum per run of rows of the same pair (runs are contiguous within a half)

@@ -39,7 +39,8 @@ class Options(C.Structure):
     _fields_ = [("n_shade", C.c_int), ("shade_half", C.c_float), ("shadow_beta", C.c_float),
                 ("shadow_eps", C.c_float), ("sigma_max", C.c_float), ("sdf_width", C.c_float),
                 ("depth_source", C.c_int), ("march_steps", C.c_int), ("march_bisect", C.c_int),
-                ("fallback_conf", C.c_float), ("refine_steps", C.c_int), ("outlier_resample", C.c_int)]
+                ("fallback_conf", C.c_float), ("refine_steps", C.c_int), ("outlier_resample", C.c_int),
+                ("shade_resample", C.c_int), ("shade_sigma_min", C.c_float)]
 
 
 class TypeDesc(C.Structure):
@@ -70,7 +71,8 @@ class Schedule(C.Structure):
 
 class FrameStats(C.Structure):
     _fields_ = [("primary_pairs", C.c_int64), ("shadow_pairs", C.c_int64), ("hit_pixels", C.c_int64),
-                ("fallback_pairs", C.c_int64), ("kernel_launches", C.c_int64), ("status", C.c_uint32)]
+                ("fallback_pairs", C.c_int64), ("kernel_launches", C.c_int64), ("status", C.c_uint32),
+                ("resampled_pixels", C.c_int64)]
 
 
 _H = C.c_void_p
