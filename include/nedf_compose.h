@@ -225,6 +225,28 @@ int nedf_compose_render_host(nedf_handle *h, const nedf_camera *cam, const nedf_
                              int n_lights, float *depth, uint32_t *id, float *rgba, float *shadow,
                              float *out, nedf_frame_stats *stats);
 
+/* ---- buffer reuse while one object is manipulated (Section "CUDA implementation") ----------
+ * While the user moves one instance the other objects' work is frozen and their buffers reused.
+ * nedf_compose_begin_edit renders the frozen part of the frame — every instance but `inst` — for
+ * this camera and these lights into the handle's reuse buffers (packed depth/id keys, colours,
+ * per-light occlusion bits; 28 bytes per pixel, allocated on first use).  After the caller moves
+ * `inst` (nedf_compose_set_instances with every other record unchanged),
+ * nedf_compose_render_edit renders the whole frame from those buffers plus `inst` alone: Step 1
+ * for inst's pairs only (z-min against the frozen keys), Step 2 only for the pixels inst wins
+ * (every other pixel keeps its frozen colour), Step 3 with full shadow queries for those pixels
+ * and, for every other pixel, its frozen occlusion bits plus a test against inst alone.  Its
+ * buffers equal nedf_compose_render's for the same scene bit for bit.  Outputs as in
+ * nedf_compose_render (caller device buffers, any may be NULL).  nedf_compose_end_edit ends the
+ * session (any number of ordinary renders may happen during it).
+ * Errors: NEDF_ERR_ARG (inst out of range), NEDF_ERR_STATE (render_edit without a session, or
+ * another instance, the instance count or the type set changed), NEDF_ERR_UNSUPPORTED (Step-2
+ * outlier resampling on: its re-rendered pixels depend on every object). */
+int nedf_compose_begin_edit(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights,
+                            int inst);
+int nedf_compose_render_edit(nedf_handle *h, float *depth, uint32_t *id, float *rgba, float *shadow,
+                             float *out, nedf_frame_stats *stats);
+int nedf_compose_end_edit(nedf_handle *h);
+
 /* Plain method colour (the baseline of the paper's speed comparison, Section "Storage and
  * Speed"): every (pixel ray, instance) pair that survives the bound cull is volume rendered
  * with n_samples midpoint samples of its NeRF over the bound chord, pairs composited front to

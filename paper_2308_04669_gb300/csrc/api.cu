@@ -31,6 +31,17 @@ struct TrainState {
 struct nedf_handle {
     nedf_config cfg{};
     nedf_options opt{};
+    // buffer reuse (an edit session): frozen buffers, the session's camera, lights and instances
+    std::vector<DevInst> h_inst;                 // host copy of the current instances
+    bool edit_active = false;
+    int edit_inst = -1, edit_mode = 0, last_mode = 0;
+    std::vector<DevInst> edit_inst_snapshot;
+    nedf_camera edit_cam{};
+    std::vector<nedf_light> edit_lights;
+    unsigned long long version = 0, edit_version = 0;   // bumped by anything that changes a frame's result
+    unsigned long long *d_edit_keys = nullptr;
+    float4 *d_edit_rgba = nullptr;
+    uint32_t *d_edit_occl = nullptr;
     cudaStream_t stream = nullptr;
     int device = 0, num_sms = 0;
     std::string err;
@@ -76,12 +87,13 @@ struct nedf_handle {
     bool profiling = false, profiled = false;
     // CUDA graph of one frame, relaunched while its shape key is unchanged
     struct FrameKey {
-        int n_inst, n_lights, depth_source, n_shade, profiling, shade_resample;
+        int n_inst, n_lights, depth_source, n_shade, profiling, shade_resample, edit_mode;
         const void *out[5];
         bool operator==(const FrameKey &o) const
         {
             if (n_inst != o.n_inst || n_lights != o.n_lights || depth_source != o.depth_source ||
-                n_shade != o.n_shade || profiling != o.profiling || shade_resample != o.shade_resample)
+                n_shade != o.n_shade || profiling != o.profiling || shade_resample != o.shade_resample ||
+                edit_mode != o.edit_mode)
                 return false;
             for (int i = 0; i < 5; ++i)
                 if (out[i] != o.out[i]) return false;
@@ -188,6 +200,9 @@ static Workspace make_ws(nedf_handle *h)
     ws.rs_cnt = h->d_rs_cnt;
     ws.rs_scratch = h->d_rs_scratch;
     ws.rs_cap = h->rs_cap;
+    ws.edit_keys = h->d_edit_keys;
+    ws.edit_rgba = h->d_edit_rgba;
+    ws.edit_occl = h->d_edit_occl;
     ws.scap = h->cfg.shadow_pair_capacity;
     ws.hlist = h->d_hlist;
     ws.cnt = h->d_cnt;
@@ -350,7 +365,7 @@ void nedf_compose_destroy(nedf_handle *h)
     cudaStreamSynchronize(h->stream);
     void *dev[] = {h->d_frame, h->d_cam, h->d_types, h->d_inst, h->d_nedf_w, h->d_nerf_w, h->d_keys,
                    h->d_depth, h->d_shadow, h->d_id, h->d_occl, h->d_hlist, h->d_rgba, h->d_out,
-                   h->d_ppairs, h->d_spairs, h->d_pgeo, h->d_sgeo, h->d_sell, h->d_nout[0], h->d_nout[1], h->d_rs_mask, h->d_rs_pairs, h->d_rs_cnt, h->d_rs_scratch, h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch,
+                   h->d_ppairs, h->d_spairs, h->d_pgeo, h->d_sgeo, h->d_sell, h->d_nout[0], h->d_nout[1], h->d_rs_mask, h->d_rs_pairs, h->d_rs_cnt, h->d_rs_scratch, h->d_edit_keys, h->d_edit_rgba, h->d_edit_occl, h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch,
                    h->d_march_scratch, h->d_nedf_tc, h->d_nerf_tc, h->d_fb[0], h->d_fb[1], h->d_lcam,
                    h->d_lg_count, h->d_lg_off, h->d_lg_cursor, h->d_lg_items, h->d_lg_big,
                    h->d_lg_big_count, h->d_scan_tmp};
@@ -409,6 +424,7 @@ int nedf_compose_set_options(nedf_handle *h, const nedf_options *o)
         }
     }
     h->opt = *o;
+    ++h->version;
     return NEDF_OK;
 }
 
@@ -437,6 +453,7 @@ int nedf_compose_sync(nedf_handle *h)
 
 int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *types)
 {
+    if (h) ++h->version;
     NvtxRange nvtx_("nedf_compose_set_types");
     if (!h || !types) return fail(h, NEDF_ERR_ARG, "null argument");
     if (n_types < 1 || n_types > h->cfg.max_types) return fail(h, NEDF_ERR_ARG, "n_types out of range");
@@ -531,6 +548,8 @@ int nedf_compose_set_instances(nedf_handle *h, int n, const nedf_instance *inst)
         CK(h, cudaMemcpyAsync(h->d_inst, di.data(), sizeof(DevInst) * n, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));   // di is a host temporary
     h->n_inst = n;
+    di.resize(n);
+    h->h_inst = std::move(di);
     return NEDF_OK;
 }
 
@@ -577,6 +596,8 @@ static cudaError_t stage_frame(nedf_handle *h, const nedf_camera *cam, const ned
     f.outlier_resample = h->opt.outlier_resample;
     f.shade_resample = h->opt.shade_resample;
     f.shade_sigma_min = h->opt.shade_sigma_min;
+    f.edit_mode = h->edit_mode;
+    f.edit_inst = h->edit_inst;
     f.n_inst = h->n_inst;
     f.n_types = h->n_types;
     std::memcpy(h->h_cam->eye, cam->eye, sizeof(cam->eye));
@@ -639,6 +660,8 @@ static int render_impl(nedf_handle *h, const nedf_camera *cam, const nedf_light 
     L.n_shade = h->opt.n_shade;
     L.n_lights = n_lights;
     L.shade_resample = h->opt.shade_resample;
+    L.edit_mode = h->edit_mode;
+    h->last_mode = h->edit_mode;
     L.cam = h->d_cam;
     L.events = h->profiling ? h->ev : nullptr;
     L.engine_events = h->profiling ? h->eng_ev : nullptr;
@@ -651,7 +674,7 @@ static int render_impl(nedf_handle *h, const nedf_camera *cam, const nedf_light 
         h->engines_timed = L.engines_timed;
     } else {
         nedf_handle::FrameKey key{h->n_inst, n_lights, h->opt.depth_source, h->opt.n_shade, h->profiling ? 1 : 0,
-                                  h->opt.shade_resample, {depth, id, rgba, shadow, out}};
+                                  h->opt.shade_resample, h->edit_mode, {depth, id, rgba, shadow, out}};
         if (!h->gexec || !(key == h->gkey)) {
             if (h->gexec) {
                 cudaGraphExecDestroy(h->gexec);
@@ -691,6 +714,69 @@ int nedf_compose_render(nedf_handle *h, const nedf_camera *cam, const nedf_light
     r = render_impl(h, cam, lights, n_lights, depth, id, rgba, shadow, out);
     if (r != NEDF_OK) return r;
     if (stats) return fill_stats(h, stats);
+    return NEDF_OK;
+}
+
+int nedf_compose_begin_edit(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights, int inst)
+{
+    NvtxRange nvtx_("nedf_compose_begin_edit");
+    int r = check_frame_args(h, cam, lights, n_lights);
+    if (r != NEDF_OK) return r;
+    if (inst < 0 || inst >= h->n_inst) return fail(h, NEDF_ERR_ARG, "inst out of range");
+    if (h->opt.shade_resample > 0)
+        return fail(h, NEDF_ERR_UNSUPPORTED, "buffer reuse with Step-2 outlier resampling (its pixels depend on every object)");
+    const size_t npix = (size_t)h->cfg.width * h->cfg.height;
+    if (!h->d_edit_keys) {
+        cudaError_t e = cudaMalloc((void **)&h->d_edit_keys, sizeof(unsigned long long) * npix);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_edit_rgba, sizeof(float4) * npix);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_edit_occl, sizeof(uint32_t) * npix);
+        if (e != cudaSuccess) return cuda_fail(h, e, "buffer reuse buffers");
+    }
+    h->edit_active = false;
+    h->edit_inst = inst;
+    h->edit_mode = 1;                                      // the frozen part, into the handle's buffers
+    r = render_impl(h, cam, lights, n_lights);
+    h->edit_mode = 0;
+    if (r != NEDF_OK) return r;
+    CK(h, cudaMemcpyAsync(h->d_edit_keys, h->d_keys, sizeof(unsigned long long) * npix, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->d_edit_rgba, h->d_rgba, sizeof(float4) * npix, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->d_edit_occl, h->d_occl, sizeof(uint32_t) * npix, cudaMemcpyDeviceToDevice, h->stream));
+    r = nedf_compose_sync(h);                              // the frozen frame's device status
+    if (r != NEDF_OK) return r;
+    h->edit_active = true;
+    h->edit_inst_snapshot = h->h_inst;
+    h->edit_cam = *cam;
+    h->edit_lights.assign(lights, lights + n_lights);
+    h->edit_version = h->version;
+    return NEDF_OK;
+}
+
+int nedf_compose_render_edit(nedf_handle *h, float *depth, uint32_t *id, float *rgba, float *shadow, float *out,
+                             nedf_frame_stats *stats)
+{
+    NvtxRange nvtx_("nedf_compose_render_edit");
+    if (!h) return NEDF_ERR_ARG;
+    if (!h->edit_active) return fail(h, NEDF_ERR_STATE, "no edit session (nedf_compose_begin_edit)");
+    if (h->opt.shade_resample > 0)
+        return fail(h, NEDF_ERR_UNSUPPORTED, "buffer reuse with Step-2 outlier resampling (its pixels depend on every object)");
+    if (h->version != h->edit_version || h->h_inst.size() != h->edit_inst_snapshot.size())
+        return fail(h, NEDF_ERR_STATE, "types, options, weights or the instance count changed since begin_edit");
+    for (size_t i = 0; i < h->h_inst.size(); ++i)
+        if ((int)i != h->edit_inst && std::memcmp(&h->h_inst[i], &h->edit_inst_snapshot[i], sizeof(DevInst)) != 0)
+            return fail(h, NEDF_ERR_STATE, "an instance other than the manipulated one changed");
+    h->edit_mode = 2;
+    int r = render_impl(h, &h->edit_cam, h->edit_lights.data(), (int)h->edit_lights.size(), depth, id, rgba, shadow, out);
+    h->edit_mode = 0;
+    if (r != NEDF_OK) return r;
+    if (stats) return fill_stats(h, stats);
+    return NEDF_OK;
+}
+
+int nedf_compose_end_edit(nedf_handle *h)
+{
+    if (!h) return NEDF_ERR_ARG;
+    h->edit_active = false;
+    h->edit_inst = -1;
     return NEDF_OK;
 }
 
@@ -831,7 +917,8 @@ int nedf_compose_validate(nedf_handle *h)
         if (c.h_tile[t + 1] - c.h_tile[t] != (c.h_count[t] + ppt - 1) / ppt) return bad("shading tiles", t);
         hits += c.h_count[t];
     }
-    if (hits != c.hit_pixels) return bad("shading lists do not sum to the hit pixels", -1);
+    // an edit frame lists only the pixels the manipulated instance wins
+    if (h->last_mode != 2 && hits != c.hit_pixels) return bad("shading lists do not sum to the hit pixels", -1);
     if (c.fb_count[0] > c.p_off[T] || c.fb_count[1] > c.s_off[T]) return bad("more deferred pairs than pairs", -1);
     if (c.fallback != c.fb_count[0] + c.fb_count[1] && tc_nedf) return bad("deferred pairs not all answered", -1);
     return NEDF_OK;
@@ -1046,6 +1133,7 @@ int nedf_compose_loss_grad(nedf_handle *h, int type, int n, const float *o, cons
 
 int nedf_compose_train_step(nedf_handle *h, int type, int batch, float lr, float *loss_host)
 {
+    if (h) ++h->version;                           // the weights change
     NvtxRange nvtx_("nedf_compose_train_step");
     if (!h) return NEDF_ERR_ARG;
     if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
@@ -1114,6 +1202,7 @@ int nedf_compose_save_state(nedf_handle *h, void *buf, size_t *size)
 
 int nedf_compose_load_state(nedf_handle *h, const void *buf, size_t size)
 {
+    if (h) ++h->version;
     if (!h || !buf) return fail(h, NEDF_ERR_ARG, "null argument");
     int64_t hdr[4];
     if (size < sizeof(hdr)) return fail(h, NEDF_ERR_ARG, "blob too small");

@@ -56,6 +56,9 @@ struct DevFrame {
     int outlier_resample;
     int shade_resample;          // Step-2 outlier resampling: plain-method samples per pair (0 = off)
     float shade_sigma_min;
+    // buffer reuse while one instance is manipulated: 0 a whole frame; 1 the frozen part (every
+    // instance but edit_inst); 2 an edit frame (the frozen buffers plus edit_inst alone)
+    int edit_mode, edit_inst;
     int n_inst, n_types;
 };
 

@@ -38,9 +38,10 @@ __global__ void k_setup(Workspace ws, const HostCamera *cam)
 
 __global__ void k_clear(Workspace ws, int npix)
 {
+    const bool edit = ws.frame->edit_mode == 2;            // an edit frame starts from the frozen part
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
-        ws.keys[p] = ~0ull;
-        ws.occl[p] = 0u;
+        ws.keys[p] = edit ? ws.edit_keys[p] : ~0ull;
+        ws.occl[p] = edit ? ws.edit_occl[p] : 0u;
         if (ws.rs_mask) ws.rs_mask[p] = 0u;
     }
 }
@@ -115,6 +116,8 @@ __global__ void __launch_bounds__(kThreads) k_bin_primary(Workspace ws)
     const DevFrame &f = *ws.frame;
     int inst = blockIdx.x;
     if (inst >= f.n_inst) return;
+    // buffer reuse: the frozen part leaves the manipulated instance out, an edit frame has only it
+    if ((f.edit_mode == 1 && inst == f.edit_inst) || (f.edit_mode == 2 && inst != f.edit_inst)) return;
     DevInst I = ws.inst[inst];
     DevType T = ws.types[I.type];
     int i0, i1, j0, j1;
@@ -326,13 +329,22 @@ __global__ void k_resolve(Workspace ws, int npix)
             id = (uint32_t)(k & 0xffffffffu);
             t = ws.inst[id].type;
         }
+        // an edit frame shades and fully re-shadows only the pixels the manipulated instance
+        // wins; every other pixel keeps the frozen part's colour and occlusion bits
+        bool listed = hit;
+        if (f.edit_mode == 2 && hit) {
+            listed = id == (uint32_t)f.edit_inst;
+            if (listed) ws.occl[p] = 0u;
+            else ws.rgba[p] = ws.edit_rgba[p];
+            if (!listed) t = 0xFFFFFFFFu;
+        }
         // one atomic per (warp, type) and one per warp for the hit count: a few types share
         // their counters across the whole frame
         const unsigned act = __activemask();
         const int lane = threadIdx.x & 31;
         const unsigned peers = __match_any_sync(act, t);
         const unsigned hits = __ballot_sync(act, hit);
-        if (hit) {
+        if (listed) {
             const int leader = __ffs(peers) - 1;
             unsigned long long base = 0;
             if (lane == leader) base = atomicAdd(&ws.cnt->h_count[t], (unsigned long long)__popc(peers));
@@ -344,7 +356,6 @@ __global__ void k_resolve(Workspace ws, int npix)
         ws.id[p] = id;
         if (!hit) ws.rgba[p] = make_float4(0.f, 0.f, 0.f, 0.f);   // hit pixels are written by Step 2
     }
-    (void)f;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -578,7 +589,7 @@ cudaError_t launch_frame(FrameLaunch &L)
     }
     mark();
     int nbin = 0;
-    e = launch_shadow_binning(ws, npix, L.n_lights, L.n_inst, nedf_rows, gsm, st, &nbin);
+    e = launch_shadow_binning(ws, npix, L.n_lights, L.n_inst, nedf_rows, gsm, st, &nbin, L.edit_mode == 2);
     if (e != cudaSuccess) return e;
     mark();
     mark_engine(2);

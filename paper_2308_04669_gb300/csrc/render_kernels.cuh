@@ -68,6 +68,10 @@ struct Workspace {
     Counters *rs_cnt;
     void *rs_scratch;
     long long rs_cap;
+    // buffer reuse: the frozen part's packed depth/id keys, colours and occlusion bits [W*H]
+    const unsigned long long *edit_keys;
+    const float4 *edit_rgba;
+    const uint32_t *edit_occl;
     uint32_t *hlist;             // [n_types][W*H] valid pixels per type
     Counters *cnt;
     uint32_t *status;

@@ -14,6 +14,7 @@ struct FrameLaunch {
     int n_shade;
     int n_lights;
     int shade_resample;      // Step-2 outlier resampling: plain-method samples per pair (0 = off)
+    int edit_mode;           // buffer reuse: 0 a whole frame, 1 the frozen part, 2 an edit frame
     const HostCamera *cam;   // device copy of this frame's camera
     cudaEvent_t *events;     // NULL, or kStages + 1 events recorded between the stages
     cudaEvent_t *engine_events;   // with events: 4 more, around the Step-1 and Step-3 NeDF engine launches
@@ -47,8 +48,9 @@ cudaError_t launch_nedf_decode(const Workspace &ws, int mode, int num_sms, cudaS
 cudaError_t launch_wait_check(uint32_t *status, cudaStream_t st);
 
 // Step-3 binning through per-light shadow-map cameras (shadow_bin.cu)
+// edit_frame: buffer reuse's edit frame (the frozen pixels' shadow rays against the manipulated instance too)
 cudaError_t launch_shadow_binning(const Workspace &ws, int npix, int n_lights, int n_inst, int rows_per_tile,
-                                  int num_sms, cudaStream_t st, int *launches);
+                                  int num_sms, cudaStream_t st, int *launches, bool edit_frame = false);
 cudaError_t launch_nedf_query_f32(const Workspace &ws, int type, const float *o, const float *d,
                                   float *out, int n, int num_sms, cudaStream_t st);
 cudaError_t launch_primary_binning(FrameLaunch &L);

@@ -121,6 +121,7 @@ __global__ void k_light_bin(Workspace ws, int n_lights)
         int l = (int)(e / n_inst), i = (int)(e - (long long)l * n_inst);
         const LightCam cam = ws.lcam[l];
         if (!cam.valid) continue;
+        if (f.edit_mode == 1 && i == f.edit_inst) continue;     // the frozen part has no manipulated instance
         DevInst I = ws.inst[i];
         float r = I.s * ws.types[I.type].rb;
         int i0, i1, j0, j1;
@@ -295,7 +296,8 @@ __global__ void __launch_bounds__(256) k_bin_shadow_grid(Workspace ws, int npix)
                 DevInst I = ws.inst[inst];
                 ty = I.type;
                 to_local(I, o, d, ol, dl);
-                keep = bound_chord(ol, dl, ws.types[ty].rb, ch) && (ch.te * I.s < ell);
+                keep = bound_chord(ol, dl, ws.types[ty].rb, ch) && (ch.te * I.s < ell) &&
+                       !(f.edit_mode == 1 && inst == (uint32_t)f.edit_inst);
             }
             if (PASS == 0) {
                 const unsigned active = __ballot_sync(0xffffffffu, keep);
@@ -333,6 +335,67 @@ __global__ void __launch_bounds__(256) k_bin_shadow_grid(Workspace ws, int npix)
     }
 }
 
+// Buffer reuse, edit frame: the shadow rays of the pixels the frozen part wins (their surface
+// points and their occlusion by the frozen instances are unchanged) tested against the
+// manipulated instance alone; the pairs join the same per-type lists (count pass, then fill).
+template <int PASS>
+__global__ void __launch_bounds__(256) k_edit_shadow(Workspace ws, int npix)
+{
+    const DevFrame &f = *ws.frame;
+    const int nl = f.n_lights, lane = threadIdx.x & 31;
+    const uint32_t e = (uint32_t)f.edit_inst;
+    const DevInst I = ws.inst[e];
+    const uint32_t ty = I.type;
+    const float rb = ws.types[ty].rb;
+    const long long n_rays = (long long)npix * nl;
+    // the trip count is uniform within a block, so the ballots below see whole warps
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < n_rays; base += (long long)gridDim.x * blockDim.x) {
+        const long long rr = base + threadIdx.x;
+        bool keep = false;
+        uint32_t pix = 0, l = 0;
+        V3 ol = v3(0, 0, 0), dl = v3(0, 0, 0);
+        Chord ch{};
+        float ell = 0.0f;
+        if (rr < n_rays) {
+            pix = (uint32_t)(rr / nl);
+            l = (uint32_t)(rr - (long long)pix * nl);
+            const uint32_t id = ws.id[pix];
+            if (id != kNoId && id != e) {
+                V3 oc, dc;
+                camera_ray(f, pix % f.W, pix / f.W, oc, dc);
+                const V3 x = madd(oc, ws.depth[pix], dc);
+                const V3 o = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
+                const V3 v = sub(x, o);
+                ell = sqrtf(dot(v, v));
+                to_local(I, o, normalized(v), ol, dl);
+                keep = bound_chord(ol, dl, rb, ch) && (ch.te * I.s < ell);
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (!m) continue;
+        unsigned long long start = 0;
+        if (PASS == 0) {
+            if (lane == __ffs(m) - 1) atomicAdd(&ws.cnt->s_count[ty], (unsigned long long)__popc(m));
+            continue;
+        }
+        if (lane == __ffs(m) - 1) start = atomicAdd(&ws.cnt->s_cursor[ty], (unsigned long long)__popc(m));
+        start = __shfl_sync(0xffffffffu, start, __ffs(m) - 1);
+        if (keep) {
+            const unsigned long long idx = start + __popc(m & lane_lt());
+            if (idx < ws.cnt->s_off[ty + 1]) {
+                ws.spairs[idx] = make_uint2(pix * nl + l, e);
+                if (ws.precision >= 1) {
+                    ws.sgeo[2 * idx] = make_float4(ol.x, ol.y, ol.z, ch.te);
+                    ws.sgeo[2 * idx + 1] = make_float4(dl.x, dl.y, dl.z, ch.tp);
+                    ws.sell[idx] = ell;
+                }
+            } else {
+                atomicOr(ws.status, kStatusShadowOverflow);
+            }
+        }
+    }
+}
+
 __global__ void k_scan_shadow_pairs(Workspace ws, int rows_per_tile)
 {
     const DevFrame &f = *ws.frame;
@@ -358,7 +421,7 @@ __global__ void k_scan_shadow_pairs(Workspace ws, int rows_per_tile)
 }
 
 cudaError_t launch_shadow_binning(const Workspace &ws, int npix, int n_lights, int n_inst, int rows_per_tile,
-                                  int num_sms, cudaStream_t st, int *launches)
+                                  int num_sms, cudaStream_t st, int *launches, bool edit_frame)
 {
     const int G = ws.lg_G;
     const long long cells = (long long)n_lights * G * G;
@@ -374,9 +437,11 @@ cudaError_t launch_shadow_binning(const Workspace &ws, int npix, int n_lights, i
     k_scan_add<<<num_sms * 2, 256, 0, st>>>(ws.lg_off, ws.lg_cursor, ws.scan_tmp, cells);
     k_light_bin<1><<<gb, 256, 0, st>>>(ws, n_lights);
     k_bin_shadow_grid<0><<<num_sms * 8, 256, 0, st>>>(ws, npix);
+    if (edit_frame) k_edit_shadow<0><<<num_sms * 8, 256, 0, st>>>(ws, npix);
     k_scan_shadow_pairs<<<1, 1, 0, st>>>(ws, rows_per_tile);
     k_bin_shadow_grid<1><<<num_sms * 8, 256, 0, st>>>(ws, npix);
-    *launches = 10;
+    if (edit_frame) k_edit_shadow<1><<<num_sms * 8, 256, 0, st>>>(ws, npix);
+    *launches = edit_frame ? 12 : 10;
     return cudaGetLastError();
 }
 

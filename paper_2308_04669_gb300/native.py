@@ -93,6 +93,9 @@ EXPORTS = {
     "nedf_compose_render_host": ([_H, C.POINTER(Camera), C.POINTER(Light), C.c_int, _vp, _vp, _vp, _vp, _vp,
                                   C.POINTER(FrameStats)], C.c_int),
     "nedf_compose_render_march": ([_H, C.POINTER(Camera), C.c_int, C.c_int, _vp], C.c_int),
+    "nedf_compose_begin_edit": ([_H, C.POINTER(Camera), C.POINTER(Light), C.c_int, C.c_int], C.c_int),
+    "nedf_compose_render_edit": ([_H, _vp, _vp, _vp, _vp, _vp, C.POINTER(FrameStats)], C.c_int),
+    "nedf_compose_end_edit": ([_H], C.c_int),
     "nedf_compose_stage_name": ([C.c_int], C.c_char_p),
     "nedf_compose_set_profiling": ([_H, C.c_int], C.c_int),
     "nedf_compose_get_stage_times": ([_H, _fp, C.c_int], C.c_int),
@@ -262,6 +265,21 @@ class Renderer:
         self._check(_lib.nedf_compose_render(self.h, C.byref(cam), la, nl, _ptr(depth), _ptr(id), _ptr(rgba),
                                              _ptr(shadow), _ptr(out), C.byref(st) if st is not None else None))
         return st
+
+    def begin_edit(self, cam, lights, inst):
+        """Buffer reuse: renders the frozen part (every instance but `inst`) for this camera and
+        these lights; later render_edit calls redo only what `inst` changes."""
+        la, nl = lights
+        self._check(_lib.nedf_compose_begin_edit(self.h, C.byref(cam), la, nl, int(inst)))
+
+    def render_edit(self, depth=None, id=None, rgba=None, shadow=None, out=None, stats=False):
+        st = FrameStats() if stats else None
+        self._check(_lib.nedf_compose_render_edit(self.h, _ptr(depth), _ptr(id), _ptr(rgba), _ptr(shadow), _ptr(out),
+                                                  C.byref(st) if st is not None else None))
+        return st
+
+    def end_edit(self):
+        self._check(_lib.nedf_compose_end_edit(self.h))
 
     def render_host(self, cam, lights, depth=None, id=None, rgba=None, shadow=None, out=None, stats=False):
         """Host numpy outputs (pinned torch tensors also work through their data_ptr)."""
