@@ -54,7 +54,8 @@ class OrcScene(C.Structure):
                 ("inst_type", C.POINTER(C.c_int)), ("inst_R", C.POINTER(C.c_double)),
                 ("inst_T", C.POINTER(C.c_double)), ("inst_s", C.POINTER(C.c_double)),
                 ("n_shade", C.c_int), ("shade_half", C.c_double), ("beta", C.c_double),
-                ("eps", C.c_double), ("sigma_max", C.c_double), ("sdf_width", C.c_double)]
+                ("eps", C.c_double), ("sigma_max", C.c_double), ("sdf_width", C.c_double),
+                ("light_parallel", C.POINTER(C.c_int))]
 
 
 class OrcOpts(C.Structure):
@@ -150,6 +151,12 @@ class OracleScene:
         sc.n_shade, sc.shade_half = scene.n_shade, float(np.float32(scene.shade_half))
         sc.beta, sc.eps = float(np.float32(scene.shadow_beta)), float(np.float32(scene.shadow_eps))
         sc.sigma_max, sc.sdf_width = float(np.float32(scene.sigma_max)), float(np.float32(scene.sdf_width))
+        lp = getattr(scene, "light_parallel", None)
+        if lp is not None:
+            self.lpar = np.ascontiguousarray(np.asarray(lp).reshape(-1) != 0, np.int32)
+            sc.light_parallel = self.lpar.ctypes.data_as(C.POINTER(C.c_int))
+        else:
+            sc.light_parallel = C.POINTER(C.c_int)()
         self.c = sc
 
     @property

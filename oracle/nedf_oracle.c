@@ -549,6 +549,19 @@ static void render_one(const render_job *jb, int64_t k)
         double acc = 0.0;
         for (int l = 0; l < sc->n_lights; ++l) {
             const double *L = sc->lights + 3 * l;
+            double Lp[3];
+            if (sc->light_parallel && sc->light_parallel[l]) {
+                /* A parallel light reaches x from infinity along its direction w: the shadow ray
+                 * starts on that line beyond every object's bound (any such start gives the same
+                 * answers: the same entry points and directions, the same order along the ray). */
+                double w[3] = {L[0], L[1], L[2]}, wl = len3(w), far = 1.0 + len3(x);
+                for (int m = 0; m < sc->n_inst; ++m) {
+                    const double *Tm = sc->inst_T + 3 * m;
+                    far = dmax(far, 2.0 * (len3(Tm) + sc->inst_s[m] * sc->types[sc->inst_type[m]].rb + len3(x)));
+                }
+                for (int c = 0; c < 3; ++c) Lp[c] = x[c] - far * w[c] / wl;
+                L = Lp;
+            }
             double v[3] = {x[0] - L[0], x[1] - L[1], x[2] - L[2]};
             double ell = len3(v), dir[3] = {v[0] / ell, v[1] / ell, v[2] / ell};
             int occluded = 0;

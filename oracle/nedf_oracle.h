@@ -56,6 +56,8 @@ typedef struct {
     const double *inst_s; /* [n] */
     int n_shade;
     double shade_half, beta, eps, sigma_max, sdf_width;
+    const int *light_parallel; /* [n_lights] or NULL: nonzero = a parallel light, lights[l] its
+                                  travel direction (the "parallel light sources" of Section 1) */
 } orc_scene;
 
 typedef struct {

@@ -152,6 +152,9 @@ class Scene:
     sdf_width: float = 0.01
     half_extent: float = 1.0
     extra: dict = field(default_factory=dict)
+    # per light: nonzero = a parallel light whose `lights` row is the direction it travels
+    # (None: every light is a point light at its `lights` row)
+    light_parallel: np.ndarray = None
 
     @property
     def n_inst(self):

@@ -589,3 +589,41 @@ def test_shade_outlier_resampling(orc):
     ex_rs = orc.render(osc, depth_mode=orc.DEPTH_EXACT, n_threads=4, shade_resample=128, shade_sigma_min=1.0)
     assert np.nanmin(ex_rs["shade_smax"]) > 20.0
     assert np.array_equal(ex["rgba"], ex_rs["rgba"])
+
+
+def test_parallel_light_shadow_is_an_orthographic_projection(orc):
+    """A parallel light (direction w) shadows a floor point x exactly when the half-line from x
+    towards the light, x - t w (t > 0), passes within the ball's radius of its centre: the ball's
+    orthographic projection along w.  The ball itself is lit on the side facing the light."""
+    floor = sg.make_type(sg.SDF_BOX, 0, 0, 2, 8, params=[4.0, 0.05, 4.0], rb=5.7, nedf_seed=2)
+    ball = sg.make_type(sg.SDF_SPHERE, 0, 1, 2, 8, nedf_seed=3)
+    w = np.array([0.35, -1.0, 0.2])
+    sc = sg.Scene("plane-parallel", 48, 48, sg.f32([0, 4, 5]), sg.f32([0, 0, 0]), 40.0, sg.f32([w]), [floor, ball],
+                  np.array([0, 1], np.uint32), sg.f32(np.tile(np.eye(3).reshape(1, 9), (2, 1))),
+                  sg.f32([[0, -0.05, 0], [0, 0.6, 0]]), sg.f32([1, 1]), light_parallel=np.array([1]))
+    osc = orc.OracleScene(sc)
+    r = orc.render(osc, depth_mode=orc.DEPTH_EXACT)
+    c = np.array([0, 0.6, 0])
+    wn = np.asarray(sg.f32(w), np.float64)
+    wn = wn / np.linalg.norm(wn)
+    n_shadow = n_checked = n_ball = 0
+    for k in np.nonzero(r["id"] != 0xFFFFFFFF)[0]:
+        o, d = orc.camera_ray(osc, k % 48, k // 48)
+        x = o + r["depth"][k] * d
+        if r["id"][k] == 0:
+            t = max(0.0, float((c - x) @ (-wn)))                 # closest point of the half-line
+            dist = np.linalg.norm(c - (x - t * wn))
+            if abs(dist - 0.5) < 1e-3:
+                continue
+            n_checked += 1
+            expect = 0.5 if dist < 0.5 else 1.0
+            n_shadow += expect == 0.5
+            assert r["shadow"][k] == expect
+        else:
+            nrm = (x - c) / np.linalg.norm(x - c)
+            cosl = float(nrm @ (-wn))
+            if abs(cosl) < 0.1:
+                continue
+            n_ball += 1
+            assert r["shadow"][k] == (1.0 if cosl > 0 else 0.5)
+    assert n_checked > 500 and n_shadow > 20 and n_ball > 50, (n_checked, n_shadow, n_ball)
