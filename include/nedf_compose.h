@@ -9,8 +9,9 @@
  *   Step 2, deferred shading (Algorithm 1, second half; Eq. 8): only the winning instance's
  *     radiance field is evaluated, at samples bracketing the stored depth, into the colour
  *     buffer.
- *   Step 3, shadows (Algorithm 2): shadow rays from each point light towards the surface point
- *     are answered by NeDF queries into a shadow buffer that multiplies the colour.
+ *   Step 3, shadows (Algorithm 2): shadow rays from each light towards the surface point (from
+ *     a point light's position, or from infinity along a parallel light's direction) are
+ *     answered by NeDF queries into a shadow buffer that multiplies the colour.
  * The learned part (Section "Intersection network", Eq. 5-6, "Training details") trains each
  * type's NeDF on depth / hit labels that the plain ray-marching method computes on the device.
  *
@@ -84,7 +85,8 @@ enum nedf_sdf_kind {        /* analytic object densities sigma = sigma_max * sig
 /* ---- records ------------------------------------------------------------------------------- */
 typedef struct nedf_config {
     int width, height;             /* framebuffer size, 1 .. 16384 each                         */
-    int max_instances;             /* capacity of set_instances()                               */
+    int max_instances;             /* capacity of set_instances(); the shadow-map binning keeps */
+                                   /* 64 KiB per instance (grid cells over all lights)          */
     int max_types;                 /* capacity of set_types(), <= NEDF_MAX_TYPES                */
     int nedf_hidden, nedf_width;   /* NeDF shape shared by all types: hidden layers, width      */
     int nerf_hidden, nerf_width;   /* NeRF shape shared by all types; nerf_hidden = 0 means a   */
@@ -143,7 +145,10 @@ typedef struct nedf_camera {
 } nedf_camera;
 
 typedef struct nedf_light {
-    float pos[3];                  /* point-light position, world                               */
+    float pos[3];                  /* point light: its position, world; parallel light: the     */
+                                   /* direction its light travels (any non-zero length)         */
+    int parallel;                  /* 0: point light; non-zero: parallel light (Section 1's      */
+                                   /* "parallel light sources"; rays from infinity along pos)   */
 } nedf_light;
 
 typedef struct nedf_frame_stats {

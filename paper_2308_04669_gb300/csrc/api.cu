@@ -331,7 +331,9 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
     CA(h->d_fb[1], sizeof(uint32_t) * h->cfg.shadow_pair_capacity);
     {
         const size_t cells = (size_t)NEDF_MAX_LIGHTS * kLightGridSize * kLightGridSize;
-        h->lg_cap = (long long)c.max_instances * 64 * 8;
+        // grid items over all lights: 512 cells per instance per light on average (one instance
+        // covers at most 1024 of a light's cells; larger ones are listed apart)
+        h->lg_cap = (long long)c.max_instances * 512 * NEDF_MAX_LIGHTS;
         CA(h->d_lcam, sizeof(LightCam) * NEDF_MAX_LIGHTS);
         CA(h->d_lg_count, sizeof(uint32_t) * cells);
         CA(h->d_lg_off, sizeof(uint32_t) * (cells + 1));
@@ -564,8 +566,11 @@ static int check_frame_args(nedf_handle *h, const nedf_camera *cam, const nedf_l
     float dy = cam->target[1] - cam->eye[1];
     if (dx * dx + dz * dz <= 1e-12f * (dx * dx + dy * dy + dz * dz) || (dx == 0.f && dy == 0.f && dz == 0.f))
         return fail(h, NEDF_ERR_ARG, "camera must not look along the up axis");
-    for (int l = 0; l < n_lights; ++l)
+    for (int l = 0; l < n_lights; ++l) {
         if (!finite3(lights[l].pos, 3)) return fail(h, NEDF_ERR_ARG, "light");
+        if (lights[l].parallel && !(std::fabs(lights[l].pos[0]) + std::fabs(lights[l].pos[1]) + std::fabs(lights[l].pos[2]) > 0.f))
+            return fail(h, NEDF_ERR_ARG, "a parallel light needs a non-zero direction");
+    }
     return NEDF_OK;
 }
 
@@ -580,8 +585,16 @@ static cudaError_t stage_frame(nedf_handle *h, const nedf_camera *cam, const ned
     f.W = h->cfg.width;
     f.H = h->cfg.height;
     f.n_lights = n_lights;
-    for (int l = 0; l < n_lights; ++l)
-        for (int c = 0; c < 3; ++c) f.lights[l][c] = lights[l].pos[c];
+    f.parallel_mask = 0u;
+    for (int l = 0; l < n_lights; ++l) {
+        float p[3] = {lights[l].pos[0], lights[l].pos[1], lights[l].pos[2]};
+        if (lights[l].parallel) {                  // a parallel light's direction, normalised
+            const float n = std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+            for (float &v : p) v /= n;
+            f.parallel_mask |= 1u << l;
+        }
+        for (int c = 0; c < 3; ++c) f.lights[l][c] = p[c];
+    }
     f.n_shade = h->opt.n_shade;
     f.shade_half = h->opt.shade_half;
     f.beta = h->opt.shadow_beta;

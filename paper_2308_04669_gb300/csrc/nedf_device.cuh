@@ -45,7 +45,8 @@ struct DevFrame {
     float tan_h, aspect;
     int W, H;
     int n_lights;
-    float lights[kMaxLights][3];
+    float lights[kMaxLights][3];       // point: position; parallel: unit travel direction
+    uint32_t parallel_mask;            // bit l: light l is a parallel light
     // options
     int n_shade;
     float shade_half, beta, eps, sigma_max, sdf_width;

@@ -252,10 +252,7 @@ __global__ void __launch_bounds__(kThreads) k_nedf_tiles(Workspace ws, int shado
                     V3 oc, dc;
                     camera_ray(f, pix % f.W, pix / f.W, oc, dc);
                     V3 x = madd(oc, ws.depth[pix], dc);
-                    o = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
-                    V3 v = sub(x, o);
-                    ri.ell = sqrtf(dot(v, v));
-                    d = normalized(v);
+                    light_ray(ws.lcam, f, (int)l, x, o, d, ri.ell);
                 }
                 V3 ol, dl;
                 to_local(I, o, d, ol, dl);

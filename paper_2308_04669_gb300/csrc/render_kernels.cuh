@@ -111,7 +111,32 @@ struct LightCam {
     float eye[3], right[3], up[3], fwd[3];
     float tan_h;
     int valid;                   // 0: light inside the scene bound or too wide a view -> all instances
+    int ortho;                   // a parallel light: an orthographic grid across its direction
+    float ctr[3], rad;           // the scene's bound sphere (parallel lights' rays start on it)
 };
+
+// The shadow ray of light l towards the surface point x (Algorithm 2): o = the light, d = the unit
+// direction from o to x, ell = |x - o|.  A parallel light (unit travel direction w) reaches x from
+// infinity; its ray starts where the line x - t w leaves the scene's bound sphere (just outside,
+// so outside every object's bound): the same entry points, directions and order along the ray as
+// from infinity.
+__device__ __forceinline__ void light_ray(const LightCam *lcam, const DevFrame &f, int l, V3 x, V3 &o, V3 &d, float &ell)
+{
+    if ((f.parallel_mask >> l) & 1u) {
+        const LightCam &cam = lcam[l];
+        d = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
+        const V3 p = sub(x, v3(cam.ctr[0], cam.ctr[1], cam.ctr[2]));
+        const float b = dot(p, d);                       // |p - t d| = rad at t = b + sqrt(...)
+        const float disc = fmaxf(b * b - dot(p, p) + cam.rad * cam.rad, 0.0f);
+        ell = fmaxf(b + sqrtf(disc), 0.0f) + 1e-3f * cam.rad + 1e-3f;
+        o = madd(x, -ell, d);
+    } else {
+        o = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
+        const V3 v = sub(x, o);
+        ell = sqrtf(dot(v, v));
+        d = normalized(v);
+    }
+}
 
 // Plain-method colour frame buffers (march.cu): per pair, its samples' transmittance and the
 // weighted colour accumulated by the colour-network tiles over its run of sample rows.
@@ -170,10 +195,7 @@ __device__ __forceinline__ void setup_pair_ray(const Workspace &ws, const DevFra
         V3 oc, dc;
         camera_ray(f, pix % f.W, pix / f.W, oc, dc);
         V3 x = madd(oc, ws.depth[pix], dc);
-        o = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
-        V3 v = sub(x, o);
-        R.ell = sqrtf(dot(v, v));
-        d = normalized(v);
+        light_ray(ws.lcam, f, (int)l, x, o, d, R.ell);
     }
     to_local(I, o, d, R.ol, R.dl);
     Chord ch;

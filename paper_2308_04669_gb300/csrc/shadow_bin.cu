@@ -54,9 +54,27 @@ __global__ void __launch_bounds__(256) k_light_setup(Workspace ws)
     float blo[3] = {red[0][0], red[1][0], red[2][0]}, bhi[3] = {red[3][0], red[4][0], red[5][0]};
     V3 L = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
     LightCam cam{};
+    V3 ctr = v3(0.5f * (blo[0] + bhi[0]), 0.5f * (blo[1] + bhi[1]), 0.5f * (blo[2] + bhi[2]));
+    const V3 half = v3(0.5f * (bhi[0] - blo[0]), 0.5f * (bhi[1] - blo[1]), 0.5f * (bhi[2] - blo[2]));
+    cam.ctr[0] = ctr.x; cam.ctr[1] = ctr.y; cam.ctr[2] = ctr.z;
+    cam.rad = sqrtf(dot(half, half)) * 1.001f + 1e-3f;   // contains every instance's bound sphere
+    if ((f.parallel_mask >> l) & 1u) {
+        // a parallel light: an orthographic grid across its direction, over the bound sphere
+        const V3 w = L;
+        const V3 a0 = fabsf(w.y) < 0.9f ? v3(0.f, 1.f, 0.f) : v3(1.f, 0.f, 0.f);
+        const V3 rt = normalized(v3(w.y * a0.z - w.z * a0.y, w.z * a0.x - w.x * a0.z, w.x * a0.y - w.y * a0.x));
+        const V3 u2 = v3(rt.y * w.z - rt.z * w.y, rt.z * w.x - rt.x * w.z, rt.x * w.y - rt.y * w.x);
+        cam.valid = f.n_inst > 0;
+        cam.ortho = 1;
+        cam.tan_h = 1.0f;
+        cam.fwd[0] = w.x; cam.fwd[1] = w.y; cam.fwd[2] = w.z;
+        cam.right[0] = rt.x; cam.right[1] = rt.y; cam.right[2] = rt.z;
+        cam.up[0] = u2.x; cam.up[1] = u2.y; cam.up[2] = u2.z;
+        ws.lcam[l] = cam;
+        return;
+    }
     bool inside = L.x >= blo[0] && L.x <= bhi[0] && L.y >= blo[1] && L.y <= bhi[1] && L.z >= blo[2] && L.z <= bhi[2];
     cam.valid = !inside && f.n_inst > 0;
-    V3 ctr = v3(0.5f * (blo[0] + bhi[0]), 0.5f * (blo[1] + bhi[1]), 0.5f * (blo[2] + bhi[2]));
     V3 fwd = normalized(sub(ctr, L));
     V3 up0 = fabsf(fwd.y) < 0.9f ? v3(0.f, 1.f, 0.f) : v3(1.f, 0.f, 0.f);
     V3 right = normalized(v3(fwd.y * up0.z - fwd.z * up0.y, fwd.z * up0.x - fwd.x * up0.z, fwd.x * up0.y - fwd.y * up0.x));
@@ -89,6 +107,16 @@ __device__ __forceinline__ int cell_of(float u, float tan_h, int G)
 __device__ __forceinline__ bool light_rect(const LightCam &cam, int G, V3 c, float r, int &i0, int &i1, int &j0,
                                            int &j1)
 {
+    if (cam.ortho) {                 // a parallel light: the sphere's orthographic shadow is a disc
+        const V3 p = sub(c, v3(cam.ctr[0], cam.ctr[1], cam.ctr[2]));
+        const float cu = dot(p, v3(cam.right[0], cam.right[1], cam.right[2])) / cam.rad;
+        const float cv = dot(p, v3(cam.up[0], cam.up[1], cam.up[2])) / cam.rad, rr = r / cam.rad;
+        i0 = max(cell_of(cu - rr, 1.0f, G) - 1, 0);
+        i1 = min(cell_of(cu + rr, 1.0f, G) + 1, G - 1);
+        j0 = max(cell_of(cv - rr, 1.0f, G) - 1, 0);
+        j1 = min(cell_of(cv + rr, 1.0f, G) + 1, G - 1);
+        return true;
+    }
     V3 e = sub(c, v3(cam.eye[0], cam.eye[1], cam.eye[2]));
     float cx = dot(e, v3(cam.right[0], cam.right[1], cam.right[2]));
     float cy = dot(e, v3(cam.up[0], cam.up[1], cam.up[2]));
@@ -266,16 +294,20 @@ __global__ void __launch_bounds__(256) k_bin_shadow_grid(Workspace ws, int npix)
             V3 oc, dc;
             camera_ray(f, pix % f.W, pix / f.W, oc, dc);
             V3 x = madd(oc, ws.depth[pix], dc);
-            o = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
-            V3 v = sub(x, o);
-            ell = sqrtf(dot(v, v));
-            d = normalized(v);
+            light_ray(ws.lcam, f, (int)l, x, o, d, ell);
             const LightCam &cam = ws.lcam[l];
             grid = cam.valid;
             if (grid) {
-                float z = dot(d, v3(cam.fwd[0], cam.fwd[1], cam.fwd[2]));
-                float u = dot(d, v3(cam.right[0], cam.right[1], cam.right[2])) / z;
-                float w = dot(d, v3(cam.up[0], cam.up[1], cam.up[2])) / z;
+                float u, w;
+                if (cam.ortho) {                 // a parallel light: where the ray crosses the grid
+                    const V3 p = sub(o, v3(cam.ctr[0], cam.ctr[1], cam.ctr[2]));
+                    u = dot(p, v3(cam.right[0], cam.right[1], cam.right[2])) / cam.rad;
+                    w = dot(p, v3(cam.up[0], cam.up[1], cam.up[2])) / cam.rad;
+                } else {
+                    const float z = dot(d, v3(cam.fwd[0], cam.fwd[1], cam.fwd[2]));
+                    u = dot(d, v3(cam.right[0], cam.right[1], cam.right[2])) / z;
+                    w = dot(d, v3(cam.up[0], cam.up[1], cam.up[2])) / z;
+                }
                 size_t cell = ((size_t)l * G + cell_of(w, cam.tan_h, G)) * G + cell_of(u, cam.tan_h, G);
                 c0 = ws.lg_off[cell];
                 long long end = min((long long)ws.lg_off[cell + 1], ws.lg_cap);   // overflow: flagged in the fill
@@ -364,10 +396,9 @@ __global__ void __launch_bounds__(256) k_edit_shadow(Workspace ws, int npix)
                 V3 oc, dc;
                 camera_ray(f, pix % f.W, pix / f.W, oc, dc);
                 const V3 x = madd(oc, ws.depth[pix], dc);
-                const V3 o = v3(f.lights[l][0], f.lights[l][1], f.lights[l][2]);
-                const V3 v = sub(x, o);
-                ell = sqrtf(dot(v, v));
-                to_local(I, o, normalized(v), ol, dl);
+                V3 o, d;
+                light_ray(ws.lcam, f, (int)l, x, o, d, ell);
+                to_local(I, o, d, ol, dl);
                 keep = bound_chord(ol, dl, rb, ch) && (ch.te * I.s < ell);
             }
         }

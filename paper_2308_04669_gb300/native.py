@@ -58,7 +58,7 @@ class Camera(C.Structure):
 
 
 class Light(C.Structure):
-    _fields_ = [("pos", C.c_float * 3)]
+    _fields_ = [("pos", C.c_float * 3), ("parallel", C.c_int)]
 
 
 N_SCHEDULE = 5
@@ -251,12 +251,15 @@ class Renderer:
         return c
 
     @staticmethod
-    def lights(pos):
+    def lights(pos, parallel=None):
+        """Point lights at the rows of pos; with parallel[i] non-zero, row i is instead the travel
+        direction of a parallel light."""
         pos = np.asarray(pos, np.float32).reshape(-1, 3)
         arr = (Light * len(pos))()
         for i in range(len(pos)):
             for k in range(3):
                 arr[i].pos[k] = float(pos[i, k])
+            arr[i].parallel = int(parallel[i] != 0) if parallel is not None else 0
         return arr, len(pos)
 
     def render(self, cam, lights, depth=None, id=None, rgba=None, shadow=None, out=None, stats=False):

@@ -27,7 +27,7 @@ def gpu_frame(scene, precision=0, **opts):
     rgba = torch.empty(n, 4, dtype=torch.float32, device=dev)
     shadow = torch.empty(n, dtype=torch.float32, device=dev)
     out = torch.empty(n, 4, dtype=torch.float32, device=dev)
-    st = r.render(r.camera(scene.eye, scene.target, scene.fov_deg), r.lights(scene.lights), depth, ids, rgba,
+    st = r.render(r.camera(scene.eye, scene.target, scene.fov_deg), r.lights(scene.lights, scene.light_parallel), depth, ids, rgba,
                   shadow, out, stats=True)
     torch.cuda.synchronize()
     res = dict(depth=depth.cpu().numpy().astype(np.float64), id=ids.cpu().numpy().view(np.uint32),

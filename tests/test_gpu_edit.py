@@ -36,7 +36,7 @@ def _run(sc, precision, moves):
     o = r.get_options()
     o.fallback_conf, o.refine_steps, o.outlier_resample = 0.9, 4, 1
     r.set_options(o)
-    cam, li = r.camera(sc.eye, sc.target, sc.fov_deg), r.lights(sc.lights)
+    cam, li = r.camera(sc.eye, sc.target, sc.fov_deg), r.lights(sc.lights, sc.light_parallel)
     n = sc.W * sc.H
     full, st0 = _buffers(r, n, lambda d, i, c, s, o_: r.render(cam, li, d, i, c, s, o_, stats=True))
     ids = full[1].view(np.uint32)
@@ -74,6 +74,14 @@ def test_edit_frames_equal_whole_frames(prec):
     from paper_2308_04669_gb300 import native
     p = {"fp32": native.PREC_FP32, "bf16": native.PREC_BF16, "fp8": native.PREC_FP8}[prec]
     _run(sg.three_types_scene(128, 128), p, [(0.3, -0.2, 0.1), (-0.6, 0.4, 0.5), (1.5, 0.0, -1.0)])
+
+
+def test_edit_frames_with_a_parallel_light():
+    from paper_2308_04669_gb300 import native
+    sc = sg.three_types_scene(128, 128, nerf=False)
+    sc.lights = sg.f32([[-0.4, -1.0, -0.3], [1.0, 9.0, 2.0]])
+    sc.light_parallel = np.array([1, 0])
+    _run(sc, native.PREC_BF16, [(0.3, -0.2, 0.1), (-0.6, 0.4, 0.5)])
 
 
 def test_edit_frames_equal_whole_frames_thousand_instances():

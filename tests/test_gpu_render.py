@@ -96,6 +96,26 @@ def test_light_inside_scene_bound(orc):
     assert rep["shadowed"] > 50
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_parallel_lights(orc, precision):
+    """A parallel light (rays from infinity along its direction; the shadow-map grid is then
+    orthographic) beside a point light: Steps 1-3 against the oracle, whose parallel-light rays start
+    far beyond every object's bound."""
+    from paper_2308_04669_gb300 import native
+    sc = sg.three_types_scene(96, 96, nerf=False)
+    sc.lights = sg.f32([[-0.4, -1.0, -0.3], [1.0, 9.0, 2.0]])
+    sc.light_parallel = np.array([1, 0])
+    if precision == "fp32":
+        g = gpu_frame(sc, depth_source=1)
+        o = orc.render(orc.OracleScene(sc), depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4, n_threads=8)
+        rep = compare_frame(g, o, o["px"])
+    else:
+        g = gpu_frame(sc, precision=native.PREC_BF16)
+        o = orc.render(orc.OracleScene(sc), quant=orc.QUANT_BF16, n_threads=8)
+        rep = compare_frame(g, o, o["px"], check_colour=False, max_excluded=0.1)
+    assert rep["shadowed"] > 50 and g["stats"].status == 0
+
+
 def test_empty_and_out_of_view(orc):
     sc = sg.tiny_sphere_scene()
     sc.inst_T = sg.f32([[0, 50, 0]])          # far outside the frustum
