@@ -25,6 +25,8 @@ _lib = None
 
 DEPTH_MLP, DEPTH_EXACT, DEPTH_MARCH = 0, 1, 2
 QUANT_NONE, QUANT_BF16, QUANT_FP8 = 0, 1, 2
+ARCH_REGRESSION, ARCH_CLASSIFIER = 0, 1
+CLS_IN, CLS_OUT, CLS_NC, CLS_NF = 1008, 1 + 64 + 128, 64, 128
 
 
 def build(force: bool = False) -> str:
@@ -44,7 +46,8 @@ class OrcType(C.Structure):
     _fields_ = [("kind", C.c_int), ("params", C.c_double * 8), ("rb", C.c_double),
                 ("albedo", C.c_double * 3), ("nedf_hidden", C.c_int), ("nedf_width", C.c_int),
                 ("nedf_w", C.POINTER(C.c_double)), ("nerf_hidden", C.c_int), ("nerf_width", C.c_int),
-                ("nerf_w", C.POINTER(C.c_double))]
+                ("nerf_w", C.POINTER(C.c_double)), ("nedf_arch", C.c_int),
+                ("nedf_wq", C.POINTER(C.c_double))]
 
 
 class OrcScene(C.Structure):
@@ -101,6 +104,13 @@ def lib():
             l.orc_nedf_loss_grad.argtypes = [sp, C.c_int, C.c_int, d, d, d, i, d, C.c_int]
             l.orc_nedf_loss_grad.restype = C.c_double
             l.orc_adam.argtypes = [C.c_int64, d, d, d, d, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
+            l.orc_cls_param_count.argtypes = []; l.orc_cls_param_count.restype = C.c_int64
+            l.orc_cls_features.argtypes = [d, d, C.c_double, d, d]; l.orc_cls_features.restype = C.c_int
+            l.orc_cls_round_bf16.argtypes = [d, d]
+            l.orc_cls_forward.argtypes = [d, d, d, C.c_int]
+            l.orc_cls_segment.argtypes = [C.c_double, i, i]
+            l.orc_cls_decode.argtypes = [d, d, d, i, i]; l.orc_cls_decode.restype = C.c_double
+            l.orc_cls_loss_grad.argtypes = [d, C.c_int, d, d, i, d]; l.orc_cls_loss_grad.restype = C.c_double
             _lib = l
     return _lib
 
@@ -125,6 +135,13 @@ class OracleScene:
                 (nedf_override[k] if nedf_override and k in nedf_override else t.nedf_w), np.float64)
             self._keep.append(w)
             ct.nedf_hidden, ct.nedf_width, ct.nedf_w = t.nedf_hidden, t.nedf_width, _dp(w)
+            ct.nedf_arch = int(getattr(t, "nedf_arch", 0))
+            if ct.nedf_arch == ARCH_CLASSIFIER:
+                wq = cls_round_bf16(w)
+                self._keep.append(wq)
+                ct.nedf_wq = _dp(wq)
+            else:
+                ct.nedf_wq = C.POINTER(C.c_double)()
             if t.nerf_hidden:
                 wn = np.ascontiguousarray(t.nerf_w, np.float64)
                 self._keep.append(wn)
@@ -327,3 +344,60 @@ def adam(theta, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     """In-place Adam step on float64 arrays."""
     lib().orc_adam(theta.shape[0], _dp(theta), _dp(np.ascontiguousarray(g, np.float64)), _dp(m), _dp(v),
                    t, lr, b1, b2, eps)
+
+
+# ---- the paper's intersection network (two-level classifier) ---------------------------------
+def cls_param_count() -> int:
+    return int(lib().orc_cls_param_count())
+
+
+def cls_features(ol, dl, rb):
+    """16 encoded points on the chord through the bound: (feat[1008], (te, tx, tperp, disc)) or
+    (None, bound) when the ray misses the bound."""
+    ol = np.ascontiguousarray(ol, np.float64); dl = np.ascontiguousarray(dl, np.float64)
+    feat, bd = np.zeros(CLS_IN), np.zeros(4)
+    ok = lib().orc_cls_features(_dp(ol), _dp(dl), float(rb), _dp(feat), _dp(bd))
+    return (feat if ok else None), bd
+
+
+def cls_round_bf16(w):
+    w = np.ascontiguousarray(w, np.float64)
+    wq = np.empty_like(w)
+    lib().orc_cls_round_bf16(_dp(w), _dp(wq))
+    return wq
+
+
+def cls_forward(w, x, quant=QUANT_NONE):
+    """Logits [hit, 64 coarse, 128 fine] for one input x[1008]; BF16 mode rounds w itself."""
+    w = np.ascontiguousarray(w, np.float64)
+    if quant != QUANT_NONE:
+        w = cls_round_bf16(w)
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.empty(CLS_OUT)
+    lib().orc_cls_forward(_dp(w), _dp(x), _dp(y), int(quant))
+    return y
+
+
+def cls_segment(m):
+    c, f = C.c_int(), C.c_int()
+    lib().orc_cls_segment(float(m), C.byref(c), C.byref(f))
+    return c.value, f.value
+
+
+def cls_decode(logits):
+    """(m = mu / l, hit logit, coarse bin, fine bin, smaller top-2 gap)"""
+    logits = np.ascontiguousarray(logits, np.float64)
+    m, a, c, f = C.c_double(), C.c_double(), C.c_int(), C.c_int()
+    gap = lib().orc_cls_decode(_dp(logits), C.byref(m), C.byref(a), C.byref(c), C.byref(f))
+    return m.value, a.value, c.value, f.value, gap
+
+
+def cls_loss_grad(w, x, m_star, hit_star):
+    w = np.ascontiguousarray(w, np.float64)
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, CLS_IN)
+    m_star = np.ascontiguousarray(m_star, np.float64)
+    hit_star = np.ascontiguousarray(hit_star, np.int32)
+    g = np.empty_like(w)
+    L = lib().orc_cls_loss_grad(_dp(w), x.shape[0], _dp(x), _dp(m_star),
+                                hit_star.ctypes.data_as(C.POINTER(C.c_int)), _dp(g))
+    return L, g

@@ -282,6 +282,228 @@ static int nerf_dims(const orc_type *t, int *dims)
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* The paper's intersection network (Section "Intersection network", Eq. 3-4 and 6, Appendix A) */
+/* ------------------------------------------------------------------------------------------ */
+/* Offsets into the packed weights (W[out][in] then b[out], layer after layer). */
+static size_t cls_block_off(int k) { return (size_t)ORC_CLS_IN * ORC_CLS_W + ORC_CLS_W + (size_t)k * 2 * (ORC_CLS_W * ORC_CLS_W + ORC_CLS_W); }
+static size_t cls_tail_off(void) { return cls_block_off(ORC_CLS_BLOCKS); }
+
+int64_t orc_cls_param_count(void)
+{
+    return (int64_t)cls_tail_off() + (int64_t)(1 + ORC_CLS_NC) * (ORC_CLS_W + 1) + (int64_t)ORC_CLS_NF * (ORC_CLS_W + 1);
+}
+
+/* Input (Section "NeDF": a ray is represented by 16 points sampled within a local range along it;
+ * reading: uniform over the chord [t_e, t_x] through the bound sphere, both ends included), each
+ * point encoded as in NeRF with 10 frequencies: [p, sin(2^k p), cos(2^k p)], 63 values. */
+int orc_cls_features(const double ol[3], const double dl[3], double rb, double *feat, double out4[4])
+{
+    if (!orc_bound(ol, dl, rb, out4)) return 0;
+    for (int j = 0; j < ORC_CLS_PTS; ++j) {
+        const double t = out4[0] + (out4[1] - out4[0]) * j / (ORC_CLS_PTS - 1);
+        double p[3];
+        for (int c = 0; c < 3; ++c) p[c] = ol[c] + t * dl[c];
+        orc_posenc(p, 3, ORC_CLS_FREQ, feat + 63 * j);
+    }
+    return 1;
+}
+
+/* The BF16 copy of the weights: every matrix entry rounded, biases kept. */
+void orc_cls_round_bf16(const double *w, double *wq)
+{
+    const int64_t n = orc_cls_param_count();
+    for (int64_t i = 0; i < n; ++i) wq[i] = w[i];
+    const int fi[4] = {ORC_CLS_IN, ORC_CLS_W, ORC_CLS_W, ORC_CLS_W};
+    size_t off = 0;
+    /* head, then 32 body layers, then the two tails: round W, skip b */
+    for (int l = 0; l < 1 + 2 * ORC_CLS_BLOCKS + 2; ++l) {
+        const int in = l == 0 ? fi[0] : ORC_CLS_W;
+        const int out = l < 1 + 2 * ORC_CLS_BLOCKS ? ORC_CLS_W : (l == 1 + 2 * ORC_CLS_BLOCKS ? 1 + ORC_CLS_NC : ORC_CLS_NF);
+        for (size_t i = 0; i < (size_t)in * out; ++i) wq[off + i] = orc_round_bf16(w[off + i]);
+        off += (size_t)in * out + out;
+    }
+}
+
+/* y = W x + b for one packed layer */
+static void cls_affine(const double *W, int fi, int fo, const double *x, double *y)
+{
+    const double *b = W + (size_t)fi * fo;
+    for (int o = 0; o < fo; ++o) {
+        const double *row = W + (size_t)o * fi;
+        double acc = 0.0;
+        for (int i = 0; i < fi; ++i) acc += row[i] * x[i];
+        y[o] = acc + b[o];
+    }
+}
+
+static double cls_q(double v, int quant) { return quant == ORC_QUANT_NONE ? v : orc_round_bf16(v); }
+
+/* Forward pass, saving what the backward pass needs (any pointer may be NULL):
+ *   h[k] (k = 0..16): the input of block k (h[16] feeds the tails), u[k] = W1 h + b1,
+ *   z[k] = h + W2 ReLU(u) + b2.
+ * Head: a single linear layer.  Residual block (reading of "two fully connected layers followed
+ * by ReLU" with a skip connection, as in He et al.'s basic block): h' = ReLU(h + W2 ReLU(W1 h + b1)
+ * + b2).  Tails: linear.  quant BF16 (or FP8, which the classifier runs as BF16): the network input
+ * and every layer's input rounded to BF16 (weights come pre-rounded in w); sums and biases in
+ * double. */
+static void cls_forward_saved(const double *w, const double *x, double *logits, int quant, double *hs, double *us,
+                              double *zs)
+{
+    double xin[ORC_CLS_IN], h[ORC_CLS_W], u[ORC_CLS_W], t[ORC_CLS_W], z[ORC_CLS_W];
+    for (int i = 0; i < ORC_CLS_IN; ++i) xin[i] = cls_q(x[i], quant);
+    cls_affine(w, ORC_CLS_IN, ORC_CLS_W, xin, h);
+    for (int i = 0; i < ORC_CLS_W; ++i) h[i] = cls_q(h[i], quant);
+    for (int k = 0; k < ORC_CLS_BLOCKS; ++k) {
+        const double *W1 = w + cls_block_off(k), *W2 = W1 + ORC_CLS_W * ORC_CLS_W + ORC_CLS_W;
+        if (hs) memcpy(hs + (size_t)k * ORC_CLS_W, h, sizeof(h));
+        cls_affine(W1, ORC_CLS_W, ORC_CLS_W, h, u);
+        for (int i = 0; i < ORC_CLS_W; ++i) t[i] = cls_q(dmax(u[i], 0.0), quant);
+        cls_affine(W2, ORC_CLS_W, ORC_CLS_W, t, z);
+        for (int i = 0; i < ORC_CLS_W; ++i) z[i] += h[i];
+        if (us) memcpy(us + (size_t)k * ORC_CLS_W, u, sizeof(u));
+        if (zs) memcpy(zs + (size_t)k * ORC_CLS_W, z, sizeof(z));
+        for (int i = 0; i < ORC_CLS_W; ++i) h[i] = cls_q(dmax(z[i], 0.0), quant);
+    }
+    if (hs) memcpy(hs + (size_t)ORC_CLS_BLOCKS * ORC_CLS_W, h, sizeof(h));
+    const double *TA = w + cls_tail_off(), *TB = TA + (size_t)(1 + ORC_CLS_NC) * (ORC_CLS_W + 1);
+    cls_affine(TA, ORC_CLS_W, 1 + ORC_CLS_NC, h, logits);
+    cls_affine(TB, ORC_CLS_W, ORC_CLS_NF, h, logits + 1 + ORC_CLS_NC);
+}
+
+void orc_cls_forward(const double *w, const double *x, double *logits, int quant)
+{
+    cls_forward_saved(w, x, logits, quant, NULL, NULL, NULL);
+}
+
+/* Segment operator S (Section "Intersection network"): m = mu / l in [-1, 1] to the coarse bin c
+ * of N_c over [-1, 1] and the fine bin f of N_f inside it. */
+void orc_cls_segment(double m, int *c, int *f)
+{
+    const double u = (m + 1.0) * 0.5 * ORC_CLS_NC;      /* coarse position in bins */
+    int cc = (int)floor(u);
+    cc = cc < 0 ? 0 : (cc >= ORC_CLS_NC ? ORC_CLS_NC - 1 : cc);
+    int ff = (int)floor((u - cc) * ORC_CLS_NF);
+    ff = ff < 0 ? 0 : (ff >= ORC_CLS_NF ? ORC_CLS_NF - 1 : ff);
+    *c = cc;
+    *f = ff;
+}
+
+/* Eq. 4: mu = 2l argmax(v_c) / N_c + (2l / N_c) argmax(v_f) / N_f - l, returned as m = mu / l;
+ * a = the hit logit.  Returns the smaller of the two top-2 logit gaps (how far the argmax
+ * decisions are from a tie); the first maximum wins a tie. */
+double orc_cls_decode(const double *logits, double *m, double *a, int *c, int *f)
+{
+    double gap = INFINITY;
+    int best[2];
+    const int base[2] = {1, 1 + ORC_CLS_NC}, nb[2] = {ORC_CLS_NC, ORC_CLS_NF};
+    for (int s = 0; s < 2; ++s) {
+        int bi = 0;
+        double b1 = -INFINITY, b2 = -INFINITY;
+        for (int i = 0; i < nb[s]; ++i) {
+            const double v = logits[base[s] + i];
+            if (v > b1) { b2 = b1; b1 = v; bi = i; }
+            else if (v > b2) b2 = v;
+        }
+        best[s] = bi;
+        gap = dmin(gap, b1 - b2);
+    }
+    *c = best[0];
+    *f = best[1];
+    *m = 2.0 * best[0] / ORC_CLS_NC + (2.0 / ORC_CLS_NC) * best[1] / ORC_CLS_NF - 1.0;
+    *a = logits[0];
+    return gap;
+}
+
+static double bce_logit(double x, double y) { return dmax(x, 0.0) - x * y + log1p(exp(-fabs(x))); }
+
+/* Eq. 6 for a batch of n rays given as network inputs x[n][1008] with labels (m*, hit*):
+ *   L = mean over labelled hits of [BCE(v_c, onehot S_c(m*)) + BCE(v_f, onehot S_f(m*))]
+ *       + 0.1 * mean over all rays of BCE(a, hit*),
+ * each BCE the mean over its bins of the logistic cross-entropy (reading: the bin terms are
+ * defined only where the ray hits).  grad receives dL/dtheta in the packed layout (double
+ * arithmetic, no rounding).  Returns L. */
+double orc_cls_loss_grad(const double *w, int n, const double *x, const double *m_star, const int *hit_star,
+                         double *grad)
+{
+    const int64_t np = orc_cls_param_count();
+    memset(grad, 0, sizeof(double) * np);
+    const size_t HW = (size_t)(ORC_CLS_BLOCKS + 1) * ORC_CLS_W;
+    double *hs = (double *)malloc(sizeof(double) * HW), *us = (double *)malloc(sizeof(double) * HW);
+    double *zs = (double *)malloc(sizeof(double) * HW);
+    double logits[ORC_CLS_OUT], g[ORC_CLS_OUT], dh[ORC_CLS_W], dz[ORC_CLS_W], dt[ORC_CLS_W], du[ORC_CLS_W];
+    int n_hit = 0;
+    for (int k = 0; k < n; ++k) n_hit += hit_star[k] != 0;
+    double loss = 0.0;
+    for (int r = 0; r < n; ++r) {
+        const double *xr = x + (size_t)r * ORC_CLS_IN;
+        cls_forward_saved(w, xr, logits, ORC_QUANT_NONE, hs, us, zs);
+        const double al = hit_star[r] ? 1.0 : 0.0;
+        loss += 0.1 * bce_logit(logits[0], al) / n;
+        g[0] = 0.1 * (1.0 / (1.0 + exp(-logits[0])) - al) / n;
+        for (int i = 1; i < ORC_CLS_OUT; ++i) g[i] = 0.0;
+        if (hit_star[r]) {
+            int c, f;
+            orc_cls_segment(m_star[r], &c, &f);
+            for (int i = 0; i < ORC_CLS_NC; ++i) {
+                const double v = logits[1 + i], y = i == c ? 1.0 : 0.0;
+                loss += bce_logit(v, y) / ORC_CLS_NC / n_hit;
+                g[1 + i] = (1.0 / (1.0 + exp(-v)) - y) / ORC_CLS_NC / n_hit;
+            }
+            for (int i = 0; i < ORC_CLS_NF; ++i) {
+                const double v = logits[1 + ORC_CLS_NC + i], y = i == f ? 1.0 : 0.0;
+                loss += bce_logit(v, y) / ORC_CLS_NF / n_hit;
+                g[1 + ORC_CLS_NC + i] = (1.0 / (1.0 + exp(-v)) - y) / ORC_CLS_NF / n_hit;
+            }
+        }
+        /* tails: dW = g h^T, db = g, dh = W^T g */
+        const double *h16 = hs + (size_t)ORC_CLS_BLOCKS * ORC_CLS_W;
+        for (int i = 0; i < ORC_CLS_W; ++i) dh[i] = 0.0;
+        for (int s = 0; s < 2; ++s) {
+            const int no = s == 0 ? 1 + ORC_CLS_NC : ORC_CLS_NF, g0 = s == 0 ? 0 : 1 + ORC_CLS_NC;
+            const size_t off = cls_tail_off() + (s == 0 ? 0 : (size_t)(1 + ORC_CLS_NC) * (ORC_CLS_W + 1));
+            for (int o = 0; o < no; ++o) {
+                for (int i = 0; i < ORC_CLS_W; ++i) {
+                    grad[off + (size_t)o * ORC_CLS_W + i] += g[g0 + o] * h16[i];
+                    dh[i] += w[off + (size_t)o * ORC_CLS_W + i] * g[g0 + o];
+                }
+                grad[off + (size_t)no * ORC_CLS_W + o] += g[g0 + o];
+            }
+        }
+        /* blocks, last to first */
+        for (int k = ORC_CLS_BLOCKS - 1; k >= 0; --k) {
+            const size_t o1 = cls_block_off(k), o2 = o1 + ORC_CLS_W * ORC_CLS_W + ORC_CLS_W;
+            const double *h = hs + (size_t)k * ORC_CLS_W, *u = us + (size_t)k * ORC_CLS_W, *z = zs + (size_t)k * ORC_CLS_W;
+            for (int i = 0; i < ORC_CLS_W; ++i) dz[i] = z[i] > 0.0 ? dh[i] : 0.0;
+            for (int i = 0; i < ORC_CLS_W; ++i) dt[i] = 0.0;
+            for (int o = 0; o < ORC_CLS_W; ++o) {
+                for (int i = 0; i < ORC_CLS_W; ++i) {
+                    const double ti = dmax(u[i], 0.0);
+                    grad[o2 + (size_t)o * ORC_CLS_W + i] += dz[o] * ti;
+                    dt[i] += w[o2 + (size_t)o * ORC_CLS_W + i] * dz[o];
+                }
+                grad[o2 + (size_t)ORC_CLS_W * ORC_CLS_W + o] += dz[o];
+            }
+            for (int i = 0; i < ORC_CLS_W; ++i) du[i] = u[i] > 0.0 ? dt[i] : 0.0;
+            for (int i = 0; i < ORC_CLS_W; ++i) dh[i] = dz[i];       /* the skip connection */
+            for (int o = 0; o < ORC_CLS_W; ++o) {
+                for (int i = 0; i < ORC_CLS_W; ++i) {
+                    grad[o1 + (size_t)o * ORC_CLS_W + i] += du[o] * h[i];
+                    dh[i] += w[o1 + (size_t)o * ORC_CLS_W + i] * du[o];
+                }
+                grad[o1 + (size_t)ORC_CLS_W * ORC_CLS_W + o] += du[o];
+            }
+        }
+        /* head (linear) */
+        for (int o = 0; o < ORC_CLS_W; ++o) {
+            for (int i = 0; i < ORC_CLS_IN; ++i) grad[(size_t)o * ORC_CLS_IN + i] += dh[o] * xr[i];
+            grad[(size_t)ORC_CLS_IN * ORC_CLS_W + o] += dh[o];
+        }
+    }
+    free(hs); free(us); free(zs);
+    return loss;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Depth queries: EXACT (analytic root), MARCH (plain method), MLP (NeDF, Eq. 1-2)              */
 /* ------------------------------------------------------------------------------------------ */
 static double march_root_sdf(int kind, const double *params, const double ol[3], const double dl[3],
@@ -377,9 +599,10 @@ int orc_query(const orc_scene *sc, const orc_opts *op, int inst, const double o[
               double out6[6], double *margin)
 {
     const orc_type *t = &sc->types[sc->inst_type[inst]];
-    double ol[3], dl[3], bd[4], feat[78];
+    double ol[3], dl[3], bd[4], feat[ORC_CLS_IN];
     orc_to_local(sc, inst, o, d, ol, dl);
-    int kept = orc_nedf_features(ol, dl, t->rb, feat, bd);
+    int kept = t->nedf_arch == ORC_ARCH_CLASSIFIER ? orc_cls_features(ol, dl, t->rb, feat, bd)
+                                                   : orc_nedf_features(ol, dl, t->rb, feat, bd);
     double mg = fabs(bd[3]) / (t->rb * t->rb);
     if (kept) mg = dmin(mg, fabs(bd[1]) / t->rb);
     out6[0] = INFINITY; out6[1] = out6[2] = 0.0;
@@ -394,9 +617,17 @@ int orc_query(const orc_scene *sc, const orc_opts *op, int inst, const double o[
     } else {
         /* Eq. 1: F_Phi(r) -> (mu, alpha); mu = l * m with l = rb (reading: the mu range [-l, l]
          * is the bound sphere's).  Eq. 2: D = |o - p_perp| - mu with the signed t_perp. */
-        int dims[64], nl = nedf_dims(t, dims);
         double y[2];
-        orc_mlp(t->nedf_w, nl, dims, feat, y, op->quant);
+        if (t->nedf_arch == ORC_ARCH_CLASSIFIER) {
+            /* Eq. 3-4: the two-level classifier's argmax bins give m = mu / l */
+            double logits[ORC_CLS_OUT];
+            int c, f;
+            orc_cls_forward(op->quant == ORC_QUANT_NONE ? t->nedf_w : t->nedf_wq, feat, logits, op->quant);
+            mg = dmin(mg, orc_cls_decode(logits, &y[0], &y[1], &c, &f));
+        } else {
+            int dims[64], nl = nedf_dims(t, dims);
+            orc_mlp(t->nedf_w, nl, dims, feat, y, op->quant);
+        }
         out6[1] = y[0];
         out6[2] = y[1];
         Dl = bd[2] - t->rb * y[0];

@@ -31,6 +31,15 @@ enum { ORC_DEPTH_MLP = 0, ORC_DEPTH_EXACT = 1, ORC_DEPTH_MARCH = 2 };
  * layer's weights rounded to BF16.  Sums and biases stay in double in every mode. */
 enum { ORC_QUANT_NONE = 0, ORC_QUANT_BF16 = 1, ORC_QUANT_FP8 = 2 };
 
+/* The paper's intersection network (Section "Intersection network", Appendix A): 16 points per
+ * ray, 10 encoding frequencies (16 x 63 = 1008 inputs), a 256-wide head, 16 residual blocks, a
+ * two-level classifier of 64 coarse and 128 fine bins.  Packed weights, W[out][in] then b[out]:
+ * head 1008 -> 256; per block W1, b1, W2, b2 (256 -> 256 each); tail A 256 -> 65 (row 0 the hit
+ * logit, rows 1..64 the coarse bins); tail B 256 -> 128 (the fine bins). */
+enum { ORC_CLS_PTS = 16, ORC_CLS_FREQ = 10, ORC_CLS_IN = 1008, ORC_CLS_W = 256, ORC_CLS_BLOCKS = 16,
+       ORC_CLS_NC = 64, ORC_CLS_NF = 128, ORC_CLS_OUT = 1 + 64 + 128 };
+enum { ORC_ARCH_REGRESSION = 0, ORC_ARCH_CLASSIFIER = 1 };
+
 typedef struct {
     int kind;
     double params[8];
@@ -40,6 +49,9 @@ typedef struct {
     const double *nedf_w;
     int nerf_hidden, nerf_width; /* nerf_hidden == 0: constant albedo colour */
     const double *nerf_w;
+    int nedf_arch;               /* ORC_ARCH_*: the regression MLP above or the classifier */
+    const double *nedf_wq;       /* classifier: nedf_w with every weight (not bias) rounded to BF16
+                                    (orc_cls_round_bf16), used by the BF16 mode */
 } orc_type;
 
 typedef struct {
@@ -92,6 +104,16 @@ void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, do
 double orc_round_bf16(double x);
 double orc_round_e4m3(double x);
 double orc_fp8_scale(double max_abs);
+
+/* The classifier intersection network */
+int64_t orc_cls_param_count(void);
+int orc_cls_features(const double ol[3], const double dl[3], double rb, double *feat1008, double out4[4]);
+void orc_cls_round_bf16(const double *w, double *wq);
+void orc_cls_forward(const double *w, const double *x, double *logits, int quant);
+void orc_cls_segment(double m, int *c, int *f);
+double orc_cls_decode(const double *logits, double *m, double *a, int *c, int *f);
+double orc_cls_loss_grad(const double *w, int n, const double *x, const double *m_star,
+                         const int *hit_star, double *grad);
 
 /* One (ray, instance) query: returns 1 on hit; out6 = {Dl, m, a, te, tx, tperp} */
 int orc_query(const orc_scene *sc, const orc_opts *op, int inst, const double o[3],

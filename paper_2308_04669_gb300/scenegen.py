@@ -50,6 +50,12 @@ PE_NERF_POS_FREQS = 10     # NeRF position encoding -> 63
 PE_NERF_DIR_FREQS = 4      # NeRF direction encoding -> 27
 NEDF_IN = 6 * (1 + 2 * PE_NEDF_FREQS)
 NERF_IN = 3 * (1 + 2 * PE_NERF_POS_FREQS) + 3 * (1 + 2 * PE_NERF_DIR_FREQS)
+# the paper's intersection network (Appendix A): 16 points x 10-frequency encoding = 1008 inputs,
+# 256 features, 16 residual blocks, 64 coarse and 128 fine bins plus the hit logit
+CLS_PTS, CLS_FREQ, CLS_W, CLS_BLOCKS, CLS_NC, CLS_NF = 16, 10, 256, 16, 64, 128
+CLS_IN = CLS_PTS * 3 * (1 + 2 * CLS_FREQ)
+CLS_OUT = 1 + CLS_NC + CLS_NF
+ARCH_REGRESSION, ARCH_CLASSIFIER = 0, 1
 
 
 # ----------------------------------------------------------------------------------------------
@@ -105,6 +111,31 @@ def xavier_mlp(seed: int, dims: list[int]) -> np.ndarray:
     return np.concatenate(parts)
 
 
+def cls_layers() -> list[tuple[int, int]]:
+    """(in, out) of the classifier's packed layers: head, W1 and W2 of each block, tails A and B."""
+    return ([(CLS_IN, CLS_W)] + [(CLS_W, CLS_W)] * (2 * CLS_BLOCKS) +
+            [(CLS_W, 1 + CLS_NC), (CLS_W, CLS_NF)])
+
+
+def cls_param_count() -> int:
+    return sum(fi * fo + fo for fi, fo in cls_layers())
+
+
+def cls_weights(seed: int, residual_gain: float = 0.5, bias: float = 0.05) -> np.ndarray:
+    """Packed float32 classifier weights (W[out][in] then b[out] per layer): Xavier-uniform
+    matrices, the second layer of every residual block scaled by residual_gain, biases uniform in
+    [-bias, bias]."""
+    parts = []
+    off = 0
+    for i, (fi, fo) in enumerate(cls_layers()):
+        a = math.sqrt(6.0 / (fi + fo)) * (residual_gain if 1 <= i <= 2 * CLS_BLOCKS and i % 2 == 0 else 1.0)
+        u = uniform(seed, fi * fo + fo, off)
+        off += fi * fo + fo
+        parts.append(((2.0 * u[: fi * fo] - 1.0) * a).astype(np.float32))
+        parts.append(((2.0 * u[fi * fo:] - 1.0) * bias).astype(np.float32))
+    return np.concatenate(parts)
+
+
 # ----------------------------------------------------------------------------------------------
 # Scene records
 # ----------------------------------------------------------------------------------------------
@@ -120,6 +151,7 @@ class ObjType:
     nerf_hidden: int = 0
     nerf_width: int = 0
     nerf_w: np.ndarray | None = None   # packed float32, dims [90, w * hidden, 3] or None
+    nedf_arch: int = ARCH_REGRESSION   # ARCH_CLASSIFIER: nedf_w holds the classifier (cls_layers)
 
     @property
     def nedf_dims(self):
@@ -177,18 +209,21 @@ def f32(x):
 
 def make_type(kind: int, seed: int, type_index: int, nedf_hidden: int, nedf_width: int,
               nerf_hidden: int = 0, nerf_width: int = 0, albedo=(0.7, 0.7, 0.7), rb: float = 1.0,
-              params=None, nedf_seed: int | None = None) -> ObjType:
+              params=None, nedf_seed: int | None = None, nedf_arch: int = ARCH_REGRESSION) -> ObjType:
     p = np.zeros(8, np.float32)
     vals = DEFAULT_PARAMS[kind] if params is None else params
     p[: len(vals)] = f32(vals)
     ns = substream(seed, TAG_NEDF, type_index) if nedf_seed is None else nedf_seed
-    nedf = xavier_mlp(ns, mlp_dims(NEDF_IN, nedf_hidden, nedf_width, 2))
+    if nedf_arch == ARCH_CLASSIFIER:
+        nedf, nedf_hidden, nedf_width = cls_weights(ns), 2 * CLS_BLOCKS, CLS_W
+    else:
+        nedf = xavier_mlp(ns, mlp_dims(NEDF_IN, nedf_hidden, nedf_width, 2))
     nerf = None
     if nerf_hidden:
         nerf = xavier_mlp(substream(seed, TAG_NERF, type_index),
                           mlp_dims(NERF_IN, nerf_hidden, nerf_width, 3))
     return ObjType(kind, p, float(np.float32(rb)), f32(albedo), nedf_hidden, nedf_width, nedf,
-                   nerf_hidden, nerf_width, nerf)
+                   nerf_hidden, nerf_width, nerf, nedf_arch)
 
 
 def uniform_rotations(seed: int, n: int) -> np.ndarray:
