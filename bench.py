@@ -46,6 +46,9 @@ NEDF_FLOP = 2 * (78 * 128 + 5 * 128 * 128 + 128 * 2)          # per query, unpad
 # the kernel's counters have been taken again after a change)
 PROFILED_TRAFFIC = {"step2_shade": 9.53e6}    # k_pipe<256,0>, profiles/k_pipe_1024inst_1024px_bf16.md
 NERF_FLOP = 2 * (90 * 256 + 7 * 256 * 256 + 256 * 3)          # per sample, unpadded
+# the paper's intersection network: head 1008 -> 256, 16 residual blocks of two 256 x 256 layers,
+# tails 256 -> 65 and 256 -> 128; per query, unpadded
+CLS_FLOP = 2 * (1008 * 256 + 32 * 256 * 256 + 256 * (65 + 128))
 
 
 def peaks():
@@ -435,6 +438,57 @@ def run_ours(args):
                 "instance": e_inst, "pixels_won": int(won[e_inst]),
                 "note": "device time of render_edit; set_instances (host upload) between frames is not timed"}
 
+    # ---- the same scene with the paper's classifier intersection network on every type --------
+    cls = None
+    if prec == native.PREC_BF16 and not args.no_cls:
+        import copy
+        scc = copy.copy(sc)
+        scc.types = []
+        for i, t in enumerate(sc.types):
+            tc = sg.make_type(t.kind, 1, i, 0, 0, rb=t.rb, params=t.params, nedf_arch=sg.ARCH_CLASSIFIER)
+            tc.nerf_hidden, tc.nerf_width, tc.nerf_w, tc.albedo = t.nerf_hidden, t.nerf_width, t.nerf_w, t.albedo
+            scc.types.append(tc)
+        rc = native.renderer_for(scc, precision=prec, stream=stream)
+        oc = rc.get_options()
+        for k, v in FRAME_OPTS.items():
+            setattr(oc, k, v)
+        oc.fallback_conf, oc.outlier_resample = 0.0, 0      # untrained weights: their confidence means nothing
+        rc.set_options(oc)
+        cls_sched = rc.autotune(cam, lights, reps=2) if not args.no_autotune else None
+        rc.set_profiling(True)
+        for _ in range(2):
+            rc.render(cam, lights, depth, ids, None, None, out)
+        stc = rc.render(cam, lights, depth, ids, None, None, out, stats=True)
+        torch.cuda.synchronize()
+        ev_c = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        eng_c, stg_c = {}, {}
+        for a, b in ev_c:
+            flush.zero_()
+            a.record(stream)
+            rc.render(cam, lights, depth, ids, None, None, out)
+            b.record(stream)
+            for name, ms in rc.engine_times().items():
+                eng_c[name] = eng_c.get(name, 0.0) + ms / len(ev_c)
+            for name, ms in rc.stage_times().items():
+                stg_c[name] = stg_c.get(name, 0.0) + ms / len(ev_c)
+        torch.cuda.synchronize()
+        ms_c = sum(a.elapsed_time(b) for a, b in ev_c) / len(ev_c)
+        pk_c, pk_kind_c = peaks()
+        pairs_c = {"step1_nedf": stc.primary_pairs, "step3_nedf": stc.shadow_pairs}
+        eng = {}
+        for k, np_ in pairs_c.items():
+            if eng_c.get(k):
+                tf = np_ * CLS_FLOP / (eng_c[k] * 1e-3) / 1e12
+                eng[k] = {"engine_ms": round(eng_c[k], 4), "pairs": int(np_), "engine_tflops": round(tf, 1),
+                          "engine_frac": round(tf / pk_c["bf16_tflops"], 3)}
+        cls = {"ms_per_frame": ms_c, "rays_per_s": n / (ms_c * 1e-3), "flop_per_query": CLS_FLOP,
+               "engines": eng, "stage_ms": {k: round(v, 4) for k, v in stg_c.items()},
+               "hit_pixels": int(stc.hit_pixels), "schedule": cls_sched,
+               "peak_basis": f"bf16 dense, {pk_kind_c} (burst)",
+               "note": "same instances, lights and NeRF colour networks; every type's NeDF is the paper's "
+                       "classifier network with seeded random weights; no confidence fallback"}
+        rc.close()
+
     # ---- the same frame with the FP32 CUDA-core networks (reference precision) -----------------
     fp32 = None
     if prec != native.PREC_FP32 and not args.no_fp32:
@@ -543,6 +597,7 @@ def run_ours(args):
             "fp32_frame": fp32,
             "rs_frame": rs,
             "edit_frame": edit,
+            "classifier_frame": cls,
             "march_frame": march,
             "speedup_vs_march": {k: v["ms_per_frame"] / frame_ms for k, v in march.items() if "ms_per_frame" in v},
             "depth_err": derr, "schedule": schedule, **log}
@@ -571,6 +626,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tensor-core schedule")
     ap.add_argument("--no-resample", action="store_true", help="skip the frame with Step-2 outlier resampling")
     ap.add_argument("--no-edit", action="store_true", help="skip the buffer-reuse (edit) frames")
+    ap.add_argument("--no-cls", action="store_true", help="skip the classifier-network frames")
     ap.add_argument("--schedule", default="", help="fixed stage bytes per tensor-core kernel (shade, march colour, "
                     "Step-1 NeDF, Step-3 NeDF, query), comma-separated; skips the autotuner")
     ap.add_argument("--no-march-dense", dest="march_dense", action="store_false",

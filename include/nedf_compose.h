@@ -67,6 +67,18 @@ enum nedf_precision {       /* arithmetic of the NeDF and NeRF layers (accumulat
                                (W / s_l, s_l a per-layer power of two) and E4M3 activations;
                                the output layer in FP32 with BF16 weights                       */
 };
+enum nedf_arch {            /* the NeDF network of every type                                   */
+    NEDF_ARCH_REGRESSION = 0, /* a ReLU MLP (nedf_hidden x nedf_width) on the entry point and
+                               direction (78 encoded inputs) regressing m = mu / l and a hit logit */
+    NEDF_ARCH_CLASSIFIER = 1  /* the paper's intersection network (Section "Intersection network",
+                               Appendix A): 16 chord points x 10-frequency encoding (1008 inputs),
+                               linear head to 256, 16 residual blocks
+                               h' = ReLU(h + W2 ReLU(W1 h + b1) + b2), tails 256 -> 1 + 64 (hit
+                               logit, coarse bins) and 256 -> 128 (fine bins), argmax decode of
+                               Eq. 4.  Packed weights W[out][in] then b[out]: head, per block W1,
+                               b1, W2, b2, tail A, tail B (2,413,249 floats).  BF16 precision only;
+                               no training call */
+};
 enum nedf_depth_source {    /* what answers the (ray, instance) depth queries of Steps 1 and 3 */
     NEDF_DEPTH_NEDF = 0,    /* the Neural Depth Field (the method)                             */
     NEDF_DEPTH_MARCH = 1    /* the plain method: density ray-marching plus bisection           */
@@ -94,6 +106,8 @@ typedef struct nedf_config {
     int precision;                 /* enum nedf_precision                                       */
     int64_t primary_pair_capacity; /* (ray, instance) pairs of Step 1; 0 = 8 * width * height   */
     int64_t shadow_pair_capacity;  /* pairs of Step 3; 0 = 4 * width * height * NEDF_MAX_LIGHTS/8 */
+    int nedf_arch;                 /* enum nedf_arch; with NEDF_ARCH_CLASSIFIER nedf_hidden and */
+                                   /* nedf_width are ignored                                    */
 } nedf_config;
 
 typedef struct nedf_options {

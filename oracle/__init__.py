@@ -378,6 +378,17 @@ def cls_forward(w, x, quant=QUANT_NONE):
     return y
 
 
+def cls_logits(w_used, X, quant=QUANT_NONE):
+    """Logits of every row of X[n][1008] with the weights as given (pass cls_round_bf16(w) for
+    the BF16 mode: no rounding per call)."""
+    w_used = np.ascontiguousarray(w_used, np.float64)
+    X = np.ascontiguousarray(X, np.float64).reshape(-1, CLS_IN)
+    Y = np.empty((X.shape[0], CLS_OUT))
+    for i in range(X.shape[0]):
+        lib().orc_cls_forward(_dp(w_used), _dp(X[i]), _dp(Y[i]), int(quant))
+    return Y
+
+
 def cls_segment(m):
     c, f = C.c_int(), C.c_int()
     lib().orc_cls_segment(float(m), C.byref(c), C.byref(f))

@@ -213,6 +213,7 @@ static Workspace make_ws(nedf_handle *h)
     ws.nerf_stride = h->nerf_params;
     ws.nedf_hidden = h->cfg.nedf_hidden;
     ws.nedf_width = h->cfg.nedf_width;
+    ws.nedf_arch = h->cfg.nedf_arch;
     ws.nerf_hidden = h->cfg.nerf_hidden;
     ws.nerf_width = h->cfg.nerf_width;
     ws.precision = h->cfg.precision;
@@ -261,14 +262,19 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
         return fail(nullptr, NEDF_ERR_ARG, "width/height out of range");
     if (c.max_instances < 1 || c.max_types < 1 || c.max_types > NEDF_MAX_TYPES)
         return fail(nullptr, NEDF_ERR_ARG, "max_instances/max_types out of range");
-    if (c.nedf_hidden < 1 || c.nedf_hidden > 16 || (c.nedf_width != 64 && c.nedf_width != 128 && c.nedf_width != 256))
+    if (c.nedf_arch != NEDF_ARCH_REGRESSION && c.nedf_arch != NEDF_ARCH_CLASSIFIER)
+        return fail(nullptr, NEDF_ERR_UNSUPPORTED, "nedf_arch");
+    if (c.nedf_arch == NEDF_ARCH_CLASSIFIER && c.precision != NEDF_PREC_BF16)
+        return fail(nullptr, NEDF_ERR_UNSUPPORTED, "the classifier network runs in BF16 precision only");
+    if (c.nedf_arch == NEDF_ARCH_REGRESSION &&
+        (c.nedf_hidden < 1 || c.nedf_hidden > 16 || (c.nedf_width != 64 && c.nedf_width != 128 && c.nedf_width != 256)))
         return fail(nullptr, NEDF_ERR_UNSUPPORTED, "NeDF shape: hidden 1..16, width 64/128/256");
     if (c.nerf_hidden < 0 || c.nerf_hidden > 16 ||
         (c.nerf_hidden > 0 && c.nerf_width != 64 && c.nerf_width != 128 && c.nerf_width != 256))
         return fail(nullptr, NEDF_ERR_UNSUPPORTED, "NeRF shape: hidden 0..16, width 64/128/256");
     if (c.precision != NEDF_PREC_FP32 && c.precision != NEDF_PREC_BF16 && c.precision != NEDF_PREC_FP8)
         return fail(nullptr, NEDF_ERR_UNSUPPORTED, "precision");
-    if (c.precision != NEDF_PREC_FP32 && c.nedf_width > 128)
+    if (c.nedf_arch == NEDF_ARCH_REGRESSION && c.precision != NEDF_PREC_FP32 && c.nedf_width > 128)
         return fail(nullptr, NEDF_ERR_UNSUPPORTED, "tensor-core NeDF width must be 64 or 128");
     if (c.primary_pair_capacity < 0 || c.shadow_pair_capacity < 0)
         return fail(nullptr, NEDF_ERR_ARG, "negative capacity");
@@ -280,7 +286,11 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
     if (h->cfg.shadow_pair_capacity == 0) h->cfg.shadow_pair_capacity = 4 * npix * NEDF_MAX_LIGHTS / 8;
     h->stream = (cudaStream_t)cuda_stream;
     h->opt = nedf_options{8, 0.05f, 0.5f, 0.02f, 50.0f, 0.01f, NEDF_DEPTH_NEDF, 128, 4, 0.0f, 0, 0, 0, 1.0f};
-    h->nedf_params = mlp_params(kNedfIn, c.nedf_hidden, c.nedf_width, 2);
+    if (c.nedf_arch == NEDF_ARCH_CLASSIFIER) {     // the fixed shape; the CUDA-core NeDF is unused
+        h->cfg.nedf_hidden = 1;
+        h->cfg.nedf_width = 64;
+    }
+    h->nedf_params = c.nedf_arch == NEDF_ARCH_CLASSIFIER ? kClsParams : mlp_params(kNedfIn, c.nedf_hidden, c.nedf_width, 2);
     h->nerf_params = mlp_params(kNerfIn, c.nerf_hidden, c.nerf_width, 3);
     auto bail = [&](cudaError_t e, const char *what) {
         int code = e == cudaErrorMemoryAllocation ? NEDF_ERR_OOM : NEDF_ERR_CUDA;
@@ -345,7 +355,8 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
     }
     if (c.precision != NEDF_PREC_FP32) {
         const bool f8 = c.precision == NEDF_PREC_FP8;
-        h->nedf_tc_stride = pipe_blob_size(kNedfInPad, c.nedf_width, c.nedf_hidden, 2, f8);
+        h->nedf_tc_stride = c.nedf_arch == NEDF_ARCH_CLASSIFIER ? cls_blob_size()
+                                                                : pipe_blob_size(kNedfInPad, c.nedf_width, c.nedf_hidden, 2, f8);
         CA(h->d_nedf_tc, h->nedf_tc_stride * c.max_types);
         if (c.nerf_hidden > 0) {
             h->nerf_tc_stride = pipe_blob_size(kNerfInPad, c.nerf_width, c.nerf_hidden, 3, f8);
@@ -453,6 +464,14 @@ int nedf_compose_sync(nedf_handle *h)
     return NEDF_OK;
 }
 
+// Packs one type's FP32 master weights (device) into its tensor-core blob.
+static cudaError_t pack_nedf(nedf_handle *h, const float *master, uint8_t *blob)
+{
+    if (h->cfg.nedf_arch == NEDF_ARCH_CLASSIFIER) return launch_pack_cls(master, blob, h->stream);
+    return launch_pack_pipe(master, blob, kNedfIn, kNedfInPad, h->cfg.nedf_width, h->cfg.nedf_hidden, 2,
+                            h->cfg.precision == NEDF_PREC_FP8, h->stream);
+}
+
 int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *types)
 {
     if (h) ++h->version;
@@ -476,8 +495,9 @@ int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *ty
         dt[k].rb = t.rb;
         for (int i = 0; i < 3; ++i) dt[k].albedo[i] = t.albedo[i];
         dt[k].nerf = h->cfg.nerf_hidden > 0;
-        to_kernel_layout(t.nedf_weights, nedf.data() + (size_t)k * h->nedf_params, kNedfIn, h->cfg.nedf_hidden,
-                         h->cfg.nedf_width, 2);
+        if (h->cfg.nedf_arch == NEDF_ARCH_REGRESSION)
+            to_kernel_layout(t.nedf_weights, nedf.data() + (size_t)k * h->nedf_params, kNedfIn, h->cfg.nedf_hidden,
+                             h->cfg.nedf_width, 2);
         if (h->nerf_params)
             to_kernel_layout(t.nerf_weights, nerf.data() + (size_t)k * h->nerf_params, kNerfIn,
                              h->cfg.nerf_hidden, h->cfg.nerf_width, 3);
@@ -504,8 +524,7 @@ int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *ty
         ts.step = 0;
         ts.cursor = 0;
         if (h->d_nedf_tc)
-            CK(h, launch_pack_pipe(ts.master, h->d_nedf_tc + (size_t)k * h->nedf_tc_stride, kNedfIn, kNedfInPad,
-                                 h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->cfg.precision == NEDF_PREC_FP8, h->stream));
+            CK(h, pack_nedf(h, ts.master, h->d_nedf_tc + (size_t)k * h->nedf_tc_stride));
     }
     if (h->d_nerf_tc) {
         float *tmp = nullptr;
@@ -1101,6 +1120,8 @@ int nedf_compose_make_labels(nedf_handle *h, int type, int64_t n_rays, uint64_t 
 
 static int ensure_train_scratch(nedf_handle *h, int batch)
 {
+    if (h->cfg.nedf_arch != NEDF_ARCH_REGRESSION)
+        return fail(h, NEDF_ERR_UNSUPPORTED, "training is implemented for the regression NeDF only");
     size_t need = train_scratch_bytes(batch, h->cfg.nedf_hidden, h->cfg.nedf_width, h->nedf_params);
     if (need > h->train_scratch_bytes) {
         if (h->d_train_scratch) cudaFree(h->d_train_scratch);
@@ -1162,8 +1183,7 @@ int nedf_compose_train_step(nedf_handle *h, int type, int batch, float lr, float
                             ts.adam_v, ts.step, lr));
     ts.cursor = (ts.cursor + batch) % ts.n_rays;
     if (h->d_nedf_tc)
-        CK(h, launch_pack_pipe(ts.master, h->d_nedf_tc + (size_t)type * h->nedf_tc_stride, kNedfIn, kNedfInPad,
-                             h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->cfg.precision == NEDF_PREC_FP8, h->stream));
+        CK(h, pack_nedf(h, ts.master, h->d_nedf_tc + (size_t)type * h->nedf_tc_stride));
     if (loss_host) {
         CK(h, cudaStreamSynchronize(h->stream));
         CK(h, cudaMemcpy(loss_host, h->d_loss, sizeof(float), cudaMemcpyDeviceToHost));
@@ -1242,8 +1262,7 @@ int nedf_compose_load_state(nedf_handle *h, const void *buf, size_t size)
         TrainLaunch L = make_train_launch(h, k);
         CK(h, launch_refresh_weights(L));
         if (h->d_nedf_tc)
-            CK(h, launch_pack_pipe(h->train[k].master, h->d_nedf_tc + (size_t)k * h->nedf_tc_stride, kNedfIn,
-                                 kNedfInPad, h->cfg.nedf_width, h->cfg.nedf_hidden, 2, h->cfg.precision == NEDF_PREC_FP8, h->stream));
+            CK(h, pack_nedf(h, h->train[k].master, h->d_nedf_tc + (size_t)k * h->nedf_tc_stride));
     }
     CK(h, cudaStreamSynchronize(h->stream));
     return NEDF_OK;

@@ -81,6 +81,7 @@ struct Workspace {
     const float *nerf_w;
     long long nerf_stride;
     int nedf_hidden, nedf_width, nerf_hidden, nerf_width;
+    int nedf_arch;               // 0: regression MLP, 1: the paper's classifier network (nedf_tc only)
     // BF16 tensor-core weight blobs (per type, fixed stride); precision 1 selects them
     int precision;
     int depth_source;            // host copy of the frame option (selects kernels)

@@ -37,6 +37,15 @@ cudaError_t launch_pack_pipe(const float *master, void *blob, int K_in, int K0, 
 cudaError_t launch_nedf_pipe(const Workspace &ws, int mode, int type, const float *o, const float *d, float *out,
                              int n, int num_sms, cudaStream_t st);
 cudaError_t launch_shade_pipe(const Workspace &ws, int npix, int num_sms, cudaStream_t st);
+// The paper's classifier intersection network (render_cls.cu): packed FP32 master weights (head
+// 1008 -> 256, 16 residual blocks, tails 256 -> 65 and 256 -> 128) -> per-type BF16 blob; the
+// engine in the same three modes as launch_nedf_pipe, writing the same (m, a) outputs
+constexpr int kClsIn = 1008;
+constexpr long long kClsParams = 2413249;
+size_t cls_blob_size();
+cudaError_t launch_pack_cls(const float *master, void *blob, cudaStream_t st);
+cudaError_t launch_cls_pipe(const Workspace &ws, int mode, int type, const float *o, const float *d, float *out,
+                            int n, int num_sms, cudaStream_t st);
 cudaError_t launch_march_colour_pipe(const Workspace &ws, const MarchBuffers &mb, int n_samples, int num_sms,
                                      cudaStream_t st);
 cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStream_t st);

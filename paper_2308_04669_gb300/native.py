@@ -24,6 +24,7 @@ NEDF_OK, NEDF_ERR_ARG, NEDF_ERR_CUDA, NEDF_ERR_OOM = 0, -1, -2, -3
 NEDF_ERR_UNSUPPORTED, NEDF_ERR_CAPACITY, NEDF_ERR_TIMEOUT, NEDF_ERR_STATE = -4, -5, -6, -7
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 DEPTH_NEDF, DEPTH_MARCH = 0, 1
+ARCH_REGRESSION, ARCH_CLASSIFIER = 0, 1
 MAX_LIGHTS = 32
 N_STAGES = 8
 
@@ -32,7 +33,7 @@ class Config(C.Structure):
     _fields_ = [("width", C.c_int), ("height", C.c_int), ("max_instances", C.c_int), ("max_types", C.c_int),
                 ("nedf_hidden", C.c_int), ("nedf_width", C.c_int), ("nerf_hidden", C.c_int),
                 ("nerf_width", C.c_int), ("precision", C.c_int), ("primary_pair_capacity", C.c_int64),
-                ("shadow_pair_capacity", C.c_int64)]
+                ("shadow_pair_capacity", C.c_int64), ("nedf_arch", C.c_int)]
 
 
 class Options(C.Structure):
@@ -155,9 +156,9 @@ class Renderer:
 
     def __init__(self, width, height, max_instances, max_types, nedf_hidden, nedf_width, nerf_hidden=0,
                  nerf_width=0, precision=PREC_FP32, primary_pair_capacity=0, shadow_pair_capacity=0,
-                 stream=None):
+                 stream=None, nedf_arch=0):
         cfg = Config(width, height, max_instances, max_types, nedf_hidden, nedf_width, nerf_hidden, nerf_width,
-                     precision, primary_pair_capacity, shadow_pair_capacity)
+                     precision, primary_pair_capacity, shadow_pair_capacity, nedf_arch)
         h = _H()
         st = stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None else None)
         rc = _lib.nedf_compose_create(C.byref(cfg), st, C.byref(h))
@@ -380,6 +381,7 @@ class Renderer:
 def renderer_for(scene, precision=PREC_FP32, stream=None, **kw) -> Renderer:
     """A Renderer sized for a scenegen.Scene with its types and instances loaded."""
     t0 = scene.types[0]
+    kw.setdefault("nedf_arch", getattr(t0, "nedf_arch", 0))
     r = Renderer(scene.W, scene.H, max(scene.n_inst, 1), len(scene.types), t0.nedf_hidden, t0.nedf_width,
                  t0.nerf_hidden, t0.nerf_width, precision, stream=stream, **kw)
     r.load_scene(scene)

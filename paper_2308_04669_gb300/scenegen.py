@@ -294,6 +294,17 @@ def three_types_scene(W: int = 512, H: int = 512, nerf: bool = True) -> Scene:
     return _many_scene("3x16-512", [SDF_SPHERE, SDF_TORUS, SDF_BOX], 48, 1, W, H, 4.0, 2, nerf)
 
 
+def classifier_scene(W: int = 64, H: int = 64, n_inst: int = 12, seed: int = 5, E: float = 2.5) -> Scene:
+    """Sphere / torus / box types carrying the paper's classifier intersection network (seeded
+    random weights), n_inst instances in [-E, E]^3, 2 lights, constant albedo."""
+    kinds = [SDF_SPHERE, SDF_TORUS, SDF_BOX]
+    types = [make_type(k, seed, i, 0, 0, nedf_arch=ARCH_CLASSIFIER) for i, k in enumerate(kinds)]
+    it, R, T, s = random_instances(seed, n_inst, len(kinds), E)
+    eye, target = orbit_camera(E)
+    return Scene(f"cls{len(kinds)}x{n_inst}-{W}", W, H, eye, target, 40.0, ring_lights(E, 2), types, it, R, T, s,
+                 half_extent=E)
+
+
 def thousand_scene(W: int = 1024, H: int = 1024, nerf: bool = True) -> Scene:
     """1024 sphere/torus/box instances in [-20,20]^3, seed 3, 1024^2, 4 lights."""
     return _many_scene("1024inst-1024", [SDF_SPHERE, SDF_TORUS, SDF_BOX], 1024, 3, W, H, 20.0, 4, nerf)

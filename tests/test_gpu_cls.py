@@ -1,0 +1,122 @@
+"""The paper's intersection network on the tensor cores (render_cls.cu) against the oracle.
+
+Tolerance, from the arithmetic: the network is 34 BF16 layers deep with a BF16 residual stream.
+A BF16 rounding that lands on the other side of a boundary (FP32 sums on the GPU, double sums in
+the oracle) perturbs one activation by an ulp, which moves every activation of the next layer by
+about ulp / 16 and so flips several of them: the rounding differences avalanche, and two BF16
+evaluations of the same network end up as far apart as either is from the unrounded network.
+So the GPU is judged against the oracle's FP64 network with the oracle's own BF16 mode as the
+yardstick: its logit error distribution must match that of the BF16 oracle, its argmax bins must
+agree with the FP64 network as often as the BF16 oracle's do, and bit for bit with the BF16 oracle
+wherever the top-2 logit gap exceeds GAP_EXACT (several times the largest logit difference the
+rounding produces).  Misses of the bound are exact.
+"""
+import numpy as np
+import pytest
+
+from paper_2308_04669_gb300 import scenegen as sg
+
+from .gpu_helpers import NOID, MARGIN, close, gpu_frame
+
+pytestmark = pytest.mark.gpu
+
+GAP_EXACT = 0.1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2308_04669_gb300 import build
+    build.build()
+
+
+def _query(sc, t, o32, d32):
+    import torch
+    from paper_2308_04669_gb300 import native
+    r = native.renderer_for(sc, precision=native.PREC_BF16)
+    out = torch.empty(o32.shape[0], 4, device="cuda")
+    r.nedf_query(t, torch.tensor(o32, device="cuda"), torch.tensor(d32, device="cuda"), out)
+    torch.cuda.synchronize()
+    r.close()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def test_classifier_query_matches_oracle(orc):
+    sc = sg.classifier_scene(8, 8)
+    rng = np.random.default_rng(7)
+    n = 600                       # two full 256-row tiles and a ragged one
+    o32 = rng.normal(size=(n, 3))
+    o32 = (2.5 * o32 / np.linalg.norm(o32, axis=1, keepdims=True)).astype(np.float32)
+    d32 = (-o32 + rng.normal(size=(n, 3)) * 0.8).astype(np.float32)
+    for t in (0, 2):
+        g = _query(sc, t, o32, d32)
+        w = sc.types[t].nedf_w.astype(np.float64)
+        rows, X, misses = [], [], 0
+        for i in range(n):
+            dd = d32[i].astype(np.float64); dd /= np.linalg.norm(dd)
+            feat, bd = orc.cls_features(o32[i].astype(np.float64), dd, float(sc.types[t].rb))
+            if feat is None:
+                if abs(bd[3]) > 1e-4:
+                    assert g[i, 3] == 0 and np.isinf(g[i, 2]) and g[i, 0] == 0
+                    misses += 1
+                continue
+            rows.append(i)
+            X.append(feat)
+        assert len(rows) > 300 and misses > 20
+        X = np.array(X)
+        dq = [orc.cls_decode(y) for y in orc.cls_logits(orc.cls_round_bf16(w), X, orc.QUANT_BF16)]
+        df = [orc.cls_decode(y) for y in orc.cls_logits(w, X)]
+        gm, ga = g[rows, 0], g[rows, 1]
+        mq, aq, gap = (np.array([d[k] for d in dq]) for k in (0, 1, 4))
+        mf, af = (np.array([d[k] for d in df]) for k in (0, 1))
+        # hit logits: the GPU's error against the FP64 network is the BF16 oracle's
+        eg, eq = np.abs(ga - af), np.abs(aq - af)
+        assert np.median(eg) <= 1.5 * np.median(eq) and np.percentile(eg, 99) <= 2.0 * np.percentile(eq, 99) + 1e-3
+        assert np.abs(ga - aq).max() <= 8 * np.median(eq) + 1e-3
+        # bins: as often equal to the FP64 network's as the BF16 oracle's are; exact away from ties
+        assert (gm == mf).mean() >= (mq == mf).mean() - 0.01
+        sel = gap > GAP_EXACT
+        assert sel.mean() > 0.6 and np.array_equal(gm[sel], mq[sel])
+        # depth and hit from (m, a) as Eq. 2 gives them
+        Dl = g[rows, 2]
+        assert np.array_equal(g[rows, 3] == 1, (ga > 0) & (Dl > 0))
+        print(f"type {t}: {len(rows)} rays; |logit - fp64| median gpu {np.median(eg):.2e} bf16 oracle "
+              f"{np.median(eq):.2e}; bins = fp64: gpu {(gm == mf).mean():.4f} bf16 oracle {(mq == mf).mean():.4f}")
+
+
+def test_classifier_frame_matches_oracle(orc):
+    """Steps 1 and 3 with the classifier on every pair, against the oracle's BF16 frame: ids,
+    depths and shadow factors on the decided pixels, with the argmax rounding ties of the test
+    above (a few per cent of pairs) allowed to change a pixel's winner."""
+    from paper_2308_04669_gb300 import native
+    sc = sg.classifier_scene(48, 48)
+    g = gpu_frame(sc, precision=native.PREC_BF16)
+    o = orc.render(orc.OracleScene(sc), quant=orc.QUANT_BF16, n_threads=16)
+    px = o["px"]
+    assert g["stats"].status == 0
+    decided = (o["pmargin"] > MARGIN) & ((o["gap"] > 1e-4) | (o["id"] == NOID))
+    assert decided.mean() > 0.9
+    same = decided & (g["id"][px] == o["id"])
+    assert same.sum() >= 0.95 * decided.sum(), (same.sum(), decided.sum())
+    hit = same & (o["id"] != NOID)
+    assert hit.sum() > 100
+    # a pixel's depth is its winning pair's bin: the bin ties of the query test (under 2 % of
+    # pairs) give the same instance a different depth
+    assert close(g["depth"][px][hit], o["depth"][hit]).mean() >= 0.97
+    sd = hit & (o["smargin"] > MARGIN)
+    assert (g["shadow"][px][sd] == o["shadow"][sd]).mean() >= 0.95
+    print(dict(pixels=len(px), hit=int(hit.sum()), same=float(same.sum() / decided.sum())))
+
+
+def test_classifier_limits():
+    """BF16 only; the training calls refuse the classifier."""
+    from paper_2308_04669_gb300 import native
+    sc = sg.classifier_scene(16, 16)
+    with pytest.raises(native.NedfError) as e:
+        native.renderer_for(sc, precision=native.PREC_FP32)
+    assert e.value.code == native.NEDF_ERR_UNSUPPORTED
+    r = native.renderer_for(sc, precision=native.PREC_BF16)
+    r.make_labels(0, 1024, 1)
+    with pytest.raises(native.NedfError) as e:
+        r.train_step(0, 64, 1e-3)
+    assert e.value.code == native.NEDF_ERR_UNSUPPORTED
+    r.close()
