@@ -104,6 +104,8 @@ def lib():
             l.orc_nedf_loss_grad.argtypes = [sp, C.c_int, C.c_int, d, d, d, i, d, C.c_int]
             l.orc_nedf_loss_grad.restype = C.c_double
             l.orc_adam.argtypes = [C.c_int64, d, d, d, d, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
+            l.orc_density_net.argtypes = [d, C.c_int, C.c_int, d]; l.orc_density_net.restype = C.c_double
+            l.orc_density_labels.argtypes = [d, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, d, d, d, i, d]
             l.orc_cls_param_count.argtypes = []; l.orc_cls_param_count.restype = C.c_int64
             l.orc_cls_features.argtypes = [d, d, C.c_double, d, d]; l.orc_cls_features.restype = C.c_int
             l.orc_cls_round_bf16.argtypes = [d, d]
@@ -412,3 +414,22 @@ def cls_loss_grad(w, x, m_star, hit_star):
     L = lib().orc_cls_loss_grad(_dp(w), x.shape[0], _dp(x), _dp(m_star),
                                 hit_star.ctypes.data_as(C.POINTER(C.c_int)), _dp(g))
     return L, g
+
+
+# ---- supervision by a density network (plugin mode) -------------------------------------------
+def density_net(w, hidden, width, x):
+    w = np.ascontiguousarray(w, np.float64)
+    x = np.ascontiguousarray(x, np.float64)
+    return float(lib().orc_density_net(_dp(w), int(hidden), int(width), _dp(x)))
+
+
+def density_labels(w, hidden, width, rb, n_samples, o, d):
+    """(m*, hit*, opacity) of rays (o, d) in the object frame, from Eq. 5 on the density net."""
+    w = np.ascontiguousarray(w, np.float64)
+    o = np.ascontiguousarray(o, np.float64).reshape(-1, 3)
+    d = np.ascontiguousarray(d, np.float64).reshape(-1, 3)
+    n = o.shape[0]
+    m, h, a = np.empty(n), np.empty(n, np.int32), np.empty(n)
+    lib().orc_density_labels(_dp(w), int(hidden), int(width), float(rb), int(n_samples), n, _dp(o), _dp(d), _dp(m),
+                             h.ctypes.data_as(C.POINTER(C.c_int)), _dp(a))
+    return m, h, a

@@ -1086,3 +1086,58 @@ void orc_adam(int64_t n, double *theta, const double *g, double *m, double *v, i
         theta[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
     }
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Supervision by a generic radiance field's density (Section "Intersection network": the NeDF  */
+/* is supervised with a pre-trained NeRF through Eq. 5; here any density network)               */
+/* ------------------------------------------------------------------------------------------ */
+/* sigma(x) = ReLU(o), o the output of the density MLP on the position encoded with 10
+ * frequencies (NeRF's density activation). */
+double orc_density_net(const double *w, int hidden, int width, const double x[3])
+{
+    int dims[66];
+    dims[0] = 63;
+    for (int l = 1; l <= hidden; ++l) dims[l] = width;
+    dims[hidden + 1] = 1;
+    double f[63], y;
+    orc_posenc(x, 3, 10, f);
+    orc_mlp(w, hidden + 1, dims, f, &y, ORC_QUANT_NONE);
+    return dmax(y, 0.0);
+}
+
+/* Labels of n rays (o, d in the object's local frame): n_samples midpoints t_i of the chord
+ * [t_e, t_x] through the bound, spacing delta; alpha_i = 1 - exp(-sigma(o + t_i d) delta),
+ * T_i = prod_{j<i} (1 - alpha_j), w_i = T_i alpha_i (Eq. 5's weights).  Readings: the label depth
+ * is Eq. 5 normalised by the ray's opacity A = sum w_i (the expected termination depth given a
+ * termination inside the bound; Eq. 5 itself is the unnormalised sum), and the hit label is
+ * A > 0.5.  m* = (t_perp - D) / rb (Eq. 2 inverted); rays missing the bound get A = 0. */
+void orc_density_labels(const double *w, int hidden, int width, double rb, int n_samples, int n,
+                        const double *o, const double *d, double *m_star, int *hit_star, double *opacity)
+{
+    for (int k = 0; k < n; ++k) {
+        double ol[3], dl[3], bd[4];
+        for (int c = 0; c < 3; ++c) { ol[c] = o[3 * k + c]; dl[c] = d[3 * k + c]; }
+        normalize3(dl);
+        m_star[k] = 0.0;
+        hit_star[k] = 0;
+        opacity[k] = 0.0;
+        if (!orc_bound(ol, dl, rb, bd)) continue;
+        const double delta = (bd[1] - bd[0]) / n_samples;
+        double T = 1.0, A = 0.0, Dw = 0.0;
+        for (int i = 0; i < n_samples; ++i) {
+            const double t = bd[0] + (i + 0.5) * delta;
+            double x[3];
+            for (int c = 0; c < 3; ++c) x[c] = ol[c] + t * dl[c];
+            const double alpha = 1.0 - exp(-orc_density_net(w, hidden, width, x) * delta);
+            const double wi = T * alpha;
+            A += wi;
+            Dw += wi * t;
+            T *= 1.0 - alpha;
+        }
+        opacity[k] = A;
+        if (A > 0.5) {
+            hit_star[k] = 1;
+            m_star[k] = (bd[2] - Dw / A) / rb;
+        }
+    }
+}

@@ -146,6 +146,13 @@ double orc_nedf_loss_grad(const orc_scene *sc, int type, int n, const double *o,
 void orc_adam(int64_t n, double *theta, const double *g, double *m, double *v, int t, double lr,
               double b1, double b2, double eps);
 
+/* Supervision by a generic radiance field's density network (plugin mode): sigma(x) =
+ * ReLU(MLP(gamma_10(x))), the MLP [63, width x hidden, 1] in the packed layout; labels from Eq. 5
+ * over n_samples midpoints of the chord through the bound (see orc_density_labels). */
+double orc_density_net(const double *w, int hidden, int width, const double x[3]);
+void orc_density_labels(const double *w, int hidden, int width, double rb, int n_samples, int n,
+                        const double *o, const double *d, double *m_star, int *hit_star, double *opacity);
+
 #ifdef __cplusplus
 }
 #endif

@@ -136,6 +136,22 @@ def cls_weights(seed: int, residual_gain: float = 0.5, bias: float = 0.05) -> np
     return np.concatenate(parts)
 
 
+DENS_IN = 3 * (1 + 2 * 10)        # a radiance field's density input: position, 10 frequencies
+
+
+def density_weights(seed: int, hidden: int = 2, width: int = 64, gain: float = 24.0,
+                    shift: float = -10.0) -> np.ndarray:
+    """A generic radiance field's density network, packed like xavier_mlp with dims
+    [63, width x hidden, 1]: Xavier-uniform matrices, zero hidden biases, the output layer scaled
+    by gain and biased by shift so that sigma = ReLU(output) is zero over part of the bound and
+    reaches tens elsewhere (seeded blobs with sharp edges)."""
+    w = xavier_mlp(seed, mlp_dims(DENS_IN, hidden, width, 1)).astype(np.float64)
+    n_out = width + 1
+    w[-n_out:-1] *= gain
+    w[-1] = shift
+    return w.astype(np.float32)
+
+
 # ----------------------------------------------------------------------------------------------
 # Scene records
 # ----------------------------------------------------------------------------------------------
