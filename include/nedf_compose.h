@@ -393,6 +393,22 @@ int nedf_compose_make_labels(nedf_handle *h, int type, int64_t n_rays, uint64_t 
                              int march_steps, int march_bisect, float *o, float *d,
                              float *m_star, float *hit_star);
 
+/* The same training set (same rays for the same seed) labelled by a generic radiance field's
+ * density network instead of the type's analytic density (Section "Intersection network": the
+ * NeDF is supervised with a pre-trained NeRF through Eq. 5; plugin mode).  dens_weights: host,
+ * packed W[out][in] then b[out] per layer with dims [63, dens_width x dens_hidden, 1]
+ * (dens_hidden 1..8, dens_width 64 or 128); the input is the object-local position encoded with
+ * 10 frequencies (identity, sin block, cos block) and sigma = ReLU(output).  Per ray, n_samples
+ * (1..1024) midpoints of the chord through the bound give Eq. 5's weights w_i = T_i (1 -
+ * exp(-sigma_i delta)); the label depth D is Eq. 5's sum normalised by the opacity A = sum w_i,
+ * hit* = A > 0.5 and m* = (t_perp - D) / rb.  FP32 on CUDA cores; synchronous.  Outputs as for
+ * nedf_compose_make_labels.  Errors: NEDF_ERR_ARG (range, null, non-finite weight),
+ * NEDF_ERR_UNSUPPORTED (network shape), NEDF_ERR_CUDA. */
+int nedf_compose_make_labels_density(nedf_handle *h, int type, int64_t n_rays, uint64_t seed,
+                                     int n_samples, int dens_hidden, int dens_width,
+                                     const float *dens_weights, float *o, float *d, float *m_star,
+                                     float *hit_star);
+
 /* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) of the type's NeDF on `batch`
  * consecutive rays of its training set (wrapping around), starting where the previous step
  * ended.  Loss (regression form of Eq. 6): mean over labelled hits of (m - m*)^2 plus

@@ -1085,15 +1085,9 @@ int nedf_compose_nedf_query(nedf_handle *h, int type, int n, const float *o, con
 // ---- learned part -------------------------------------------------------------------------------
 extern "C" {
 
-int nedf_compose_make_labels(nedf_handle *h, int type, int64_t n_rays, uint64_t seed, int march_steps,
-                             int march_bisect, float *o, float *d, float *m_star, float *hit_star)
+// The type's training set sized for n_rays rows (reallocated when the size changes).
+static int ensure_train_set(nedf_handle *h, int type, int64_t n_rays)
 {
-    NvtxRange nvtx_("nedf_compose_make_labels");
-    if (!h) return NEDF_ERR_ARG;
-    if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
-    if (n_rays < 1 || n_rays > (1ll << 30)) return fail(h, NEDF_ERR_ARG, "n_rays 1..2^30");
-    if (march_steps < 1 || march_steps > 65536 || march_bisect < 0 || march_bisect > 64)
-        return fail(h, NEDF_ERR_ARG, "march parameters");
     TrainState &ts = h->train[type];
     if (ts.n_rays != n_rays) {
         float *p[] = {ts.o, ts.d, ts.m_star, ts.hit_star};
@@ -1108,14 +1102,66 @@ int nedf_compose_make_labels(nedf_handle *h, int type, int64_t n_rays, uint64_t 
         ts.n_rays = n_rays;
     }
     ts.cursor = 0;
-    CK(h, launch_make_labels(h->d_types + type, h->types_host[type].rb, n_rays, seed, march_steps, march_bisect,
-                             ts.o, ts.d, ts.m_star, ts.hit_star, h->num_sms, h->stream));
+    return NEDF_OK;
+}
+
+// Copies of the training set to the caller's device buffers (any may be NULL).
+static int copy_train_set(nedf_handle *h, int type, int64_t n_rays, float *o, float *d, float *m_star, float *hit_star)
+{
+    TrainState &ts = h->train[type];
     size_t b3 = sizeof(float) * 3 * n_rays, b1 = sizeof(float) * n_rays;
     if (o) CK(h, cudaMemcpyAsync(o, ts.o, b3, cudaMemcpyDeviceToDevice, h->stream));
     if (d) CK(h, cudaMemcpyAsync(d, ts.d, b3, cudaMemcpyDeviceToDevice, h->stream));
     if (m_star) CK(h, cudaMemcpyAsync(m_star, ts.m_star, b1, cudaMemcpyDeviceToDevice, h->stream));
     if (hit_star) CK(h, cudaMemcpyAsync(hit_star, ts.hit_star, b1, cudaMemcpyDeviceToDevice, h->stream));
     return NEDF_OK;
+}
+
+int nedf_compose_make_labels(nedf_handle *h, int type, int64_t n_rays, uint64_t seed, int march_steps,
+                             int march_bisect, float *o, float *d, float *m_star, float *hit_star)
+{
+    NvtxRange nvtx_("nedf_compose_make_labels");
+    if (!h) return NEDF_ERR_ARG;
+    if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
+    if (n_rays < 1 || n_rays > (1ll << 30)) return fail(h, NEDF_ERR_ARG, "n_rays 1..2^30");
+    if (march_steps < 1 || march_steps > 65536 || march_bisect < 0 || march_bisect > 64)
+        return fail(h, NEDF_ERR_ARG, "march parameters");
+    int r = ensure_train_set(h, type, n_rays);
+    if (r != NEDF_OK) return r;
+    TrainState &ts = h->train[type];
+    CK(h, launch_make_labels(h->d_types + type, h->types_host[type].rb, n_rays, seed, march_steps, march_bisect,
+                             ts.o, ts.d, ts.m_star, ts.hit_star, h->num_sms, h->stream));
+    return copy_train_set(h, type, n_rays, o, d, m_star, hit_star);
+}
+
+int nedf_compose_make_labels_density(nedf_handle *h, int type, int64_t n_rays, uint64_t seed, int n_samples,
+                                     int dens_hidden, int dens_width, const float *dens_weights, float *o, float *d,
+                                     float *m_star, float *hit_star)
+{
+    NvtxRange nvtx_("nedf_compose_make_labels_density");
+    if (!h || !dens_weights) return fail(h, NEDF_ERR_ARG, "null argument");
+    if (type < 0 || type >= h->n_types) return fail(h, NEDF_ERR_ARG, "type out of range");
+    if (n_rays < 1 || n_rays > (1ll << 30)) return fail(h, NEDF_ERR_ARG, "n_rays 1..2^30");
+    if (n_samples < 1 || n_samples > kMaxDensSamples) return fail(h, NEDF_ERR_ARG, "n_samples 1..1024");
+    if (dens_hidden < 1 || dens_hidden > 8 || (dens_width != 64 && dens_width != 128))
+        return fail(h, NEDF_ERR_UNSUPPORTED, "density network: hidden 1..8, width 64 or 128");
+    const long long np = mlp_params(kDensIn, dens_hidden, dens_width, 1);
+    if (!finite3(dens_weights, (int)np)) return fail(h, NEDF_ERR_ARG, "non-finite density weight");
+    int r = ensure_train_set(h, type, n_rays);
+    if (r != NEDF_OK) return r;
+    std::vector<float> wk((size_t)np);
+    to_kernel_layout(dens_weights, wk.data(), kDensIn, dens_hidden, dens_width, 1);
+    float *dw = nullptr;
+    CK(h, cudaMalloc((void **)&dw, sizeof(float) * np));
+    cudaError_t e = cudaMemcpy(dw, wk.data(), sizeof(float) * np, cudaMemcpyHostToDevice);
+    TrainState &ts = h->train[type];
+    if (e == cudaSuccess)
+        e = launch_density_labels(dw, dens_hidden, dens_width, h->types_host[type].rb, n_rays, seed, n_samples, ts.o,
+                                  ts.d, ts.m_star, ts.hit_star, h->num_sms, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dw);
+    if (e != cudaSuccess) return cuda_fail(h, e, "density labels");
+    return copy_train_set(h, type, n_rays, o, d, m_star, hit_star);
 }
 
 static int ensure_train_scratch(nedf_handle *h, int batch)

@@ -16,31 +16,39 @@ namespace nedf {
 // ---------------------------------------------------------------------------------------------
 // training set: rays entering the bound sphere, labelled by the plain method
 // ---------------------------------------------------------------------------------------------
+// Ray r of a training set: entry point uniform on the bound sphere, cosine-weighted inward
+// direction, from four counter-based uniforms.
+__device__ __forceinline__ void label_ray(uint64_t seed, long long r, float rb, V3 &org, V3 &dir)
+{
+    float u0 = uniform24(seed, 4ull * r), u1 = uniform24(seed, 4ull * r + 1);
+    float u2 = uniform24(seed, 4ull * r + 2), u3 = uniform24(seed, 4ull * r + 3);
+    // entry point uniform on the sphere
+    float z = 1.0f - 2.0f * u0, phi = 6.283185307179586f * u1;
+    float rho = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+    float sp, cp;
+    sincosf(phi, &sp, &cp);
+    V3 nrm = v3(rho * cp, rho * sp, z);
+    V3 w = v3(-nrm.x, -nrm.y, -nrm.z);
+    // tangent frame about the inward normal (Duff et al., JCGT 2017)
+    float sg = w.z >= 0.0f ? 1.0f : -1.0f;
+    float a = -1.0f / (sg + w.z), b = w.x * w.y * a;
+    V3 b1 = v3(1.0f + sg * w.x * w.x * a, sg * b, -sg * w.x);
+    V3 b2 = v3(b, sg + w.y * w.y * a, -w.y);
+    // cosine-weighted direction
+    float rr = sqrtf(u2), st, ct;
+    sincosf(6.283185307179586f * u3, &st, &ct);
+    float lx = rr * ct, ly = rr * st, lz = sqrtf(fmaxf(0.0f, 1.0f - u2));
+    dir = v3(lx * b1.x + ly * b2.x + lz * w.x, lx * b1.y + ly * b2.y + lz * w.y, lx * b1.z + ly * b2.z + lz * w.z);
+    org = v3(rb * nrm.x, rb * nrm.y, rb * nrm.z);
+}
+
 __global__ void k_make_labels(const DevType *type_p, float rb, long long n, uint64_t seed, int steps, int bisect,
                               float *o, float *d, float *m_star, float *hit_star)
 {
     const DevType T = *type_p;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-        float u0 = uniform24(seed, 4ull * r), u1 = uniform24(seed, 4ull * r + 1);
-        float u2 = uniform24(seed, 4ull * r + 2), u3 = uniform24(seed, 4ull * r + 3);
-        // entry point uniform on the sphere
-        float z = 1.0f - 2.0f * u0, phi = 6.283185307179586f * u1;
-        float rho = sqrtf(fmaxf(0.0f, 1.0f - z * z));
-        float sp, cp;
-        sincosf(phi, &sp, &cp);
-        V3 nrm = v3(rho * cp, rho * sp, z);
-        V3 w = v3(-nrm.x, -nrm.y, -nrm.z);
-        // tangent frame about the inward normal (Duff et al., JCGT 2017)
-        float sg = w.z >= 0.0f ? 1.0f : -1.0f;
-        float a = -1.0f / (sg + w.z), b = w.x * w.y * a;
-        V3 b1 = v3(1.0f + sg * w.x * w.x * a, sg * b, -sg * w.x);
-        V3 b2 = v3(b, sg + w.y * w.y * a, -w.y);
-        // cosine-weighted direction
-        float rr = sqrtf(u2), st, ct;
-        sincosf(6.283185307179586f * u3, &st, &ct);
-        float lx = rr * ct, ly = rr * st, lz = sqrtf(fmaxf(0.0f, 1.0f - u2));
-        V3 dir = v3(lx * b1.x + ly * b2.x + lz * w.x, lx * b1.y + ly * b2.y + lz * w.y, lx * b1.z + ly * b2.z + lz * w.z);
-        V3 org = v3(rb * nrm.x, rb * nrm.y, rb * nrm.z);
+        V3 org, dir;
+        label_ray(seed, r, rb, org, dir);
         o[3 * r] = org.x; o[3 * r + 1] = org.y; o[3 * r + 2] = org.z;
         d[3 * r] = dir.x; d[3 * r + 1] = dir.y; d[3 * r + 2] = dir.z;
         V3 dl = normalized(dir);
@@ -66,6 +74,82 @@ cudaError_t launch_make_labels(const DevType *type, float rb, long long n_rays, 
     long long blocks = (n_rays + 255) / 256;
     if (blocks > (long long)num_sms * 32) blocks = (long long)num_sms * 32;
     k_make_labels<<<(int)blocks, 256, 0, st>>>(type, rb, n_rays, seed, steps, bisect, o, d, m_star, hit_star);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// training set labelled by a generic radiance field's density network (plugin mode): the same
+// rays; per ray, sigma = ReLU(MLP(gamma_10(x))) at n_samples chord midpoints (64-row FP32 tiles),
+// then Eq. 5's weights w_i = T_i (1 - exp(-sigma_i delta)).  Label depth: the opacity-normalised
+// Eq. 5 depth; hit: opacity > 0.5; m* = (t_perp - D) / rb.  One block per ray.
+// ---------------------------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_density_labels(const float *wk, int hidden, float rb, long long n,
+                                                             uint64_t seed, int n_samples, float *o, float *d,
+                                                             float *m_star, float *hit_star)
+{
+    __shared__ __align__(16) float X[(W > kDensIn ? W : kDensIn) * kXStride];
+    __shared__ float y[kTileRows][4];
+    __shared__ float sig[kMaxDensSamples];
+    const float *wo = wk + (size_t)kDensIn * W + W + (size_t)(hidden - 1) * (W * W + W);
+    for (long long r = blockIdx.x; r < n; r += gridDim.x) {
+        V3 org, dir;
+        label_ray(seed, r, rb, org, dir);
+        if (threadIdx.x == 0) {
+            o[3 * r] = org.x; o[3 * r + 1] = org.y; o[3 * r + 2] = org.z;
+            d[3 * r] = dir.x; d[3 * r + 1] = dir.y; d[3 * r + 2] = dir.z;
+        }
+        const V3 dl = normalized(dir);
+        Chord ch;
+        const bool kept = bound_chord(org, dl, rb, ch);      // the same outcome in every thread
+        if (!kept) {
+            if (threadIdx.x == 0) { m_star[r] = 0.0f; hit_star[r] = 0.0f; }
+            continue;
+        }
+        const float delta = (ch.tx - ch.te) / n_samples;
+        for (int t0 = 0; t0 < n_samples; t0 += kTileRows) {
+            for (int e = threadIdx.x; e < kTileRows * kDensIn; e += blockDim.x) {
+                const int rr = e % kTileRows, fi = e / kTileRows;
+                const V3 x = madd(org, ch.te + (t0 + rr + 0.5f) * delta, dl);
+                const float xs[3] = {x.x, x.y, x.z};
+                X[fi * kXStride + rr] = posenc_feature(xs, 3, 10, fi);
+            }
+            __syncthreads();
+            mlp_hidden_f32<W>(X, kDensIn, hidden, wk);
+            out_layer_f32(X, W, wo, wo + W, 1, y);
+            if (threadIdx.x < kTileRows && t0 + (int)threadIdx.x < n_samples)
+                sig[t0 + threadIdx.x] = fmaxf(y[threadIdx.x][0], 0.0f);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            float T = 1.0f, A = 0.0f, Dw = 0.0f;
+            for (int i = 0; i < n_samples; ++i) {
+                const float alpha = 1.0f - expf(-sig[i] * delta);
+                const float wi = T * alpha;
+                A += wi;
+                Dw += wi * (ch.te + (i + 0.5f) * delta);
+                T *= 1.0f - alpha;
+            }
+            const bool hit = A > 0.5f;
+            m_star[r] = hit ? (ch.tp - Dw / A) / rb : 0.0f;
+            hit_star[r] = hit ? 1.0f : 0.0f;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_density_labels(const float *wk, int hidden, int width, float rb, long long n_rays, uint64_t seed,
+                                  int n_samples, float *o, float *d, float *m_star, float *hit_star, int num_sms,
+                                  cudaStream_t st)
+{
+    if (n_samples < 1 || n_samples > kMaxDensSamples || hidden < 1) return cudaErrorInvalidValue;
+    const int blocks = (int)std::min<long long>(n_rays, (long long)num_sms * 8);
+    if (width == 64)
+        k_density_labels<64><<<blocks, kThreads, 0, st>>>(wk, hidden, rb, n_rays, seed, n_samples, o, d, m_star, hit_star);
+    else if (width == 128)
+        k_density_labels<128><<<blocks, kThreads, 0, st>>>(wk, hidden, rb, n_rays, seed, n_samples, o, d, m_star, hit_star);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

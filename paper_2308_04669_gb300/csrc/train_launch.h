@@ -24,6 +24,14 @@ cudaError_t launch_make_labels(const DevType *type, float rb, long long n_rays, 
                                int bisect, float *o, float *d, float *m_star, float *hit_star, int num_sms,
                                cudaStream_t st);
 
+// The same rays labelled by a density network [63, width x hidden, 1] (kernel layout: per layer
+// Wt[in][out] then b; width 64 or 128) through Eq. 5 over n_samples chord midpoints (<= 1024).
+constexpr int kDensIn = 63;
+constexpr int kMaxDensSamples = 1024;
+cudaError_t launch_density_labels(const float *wk, int hidden, int width, float rb, long long n_rays, uint64_t seed,
+                                  int n_samples, float *o, float *d, float *m_star, float *hit_star, int num_sms,
+                                  cudaStream_t st);
+
 // Loss and gradient on rows [0, n) of (o, d, m_star, hit_star); gradient written to grad (packed).
 cudaError_t launch_loss_grad(const TrainLaunch &L, const float *o, const float *d, const float *m_star,
                              const float *hit_star, int n, float *grad);

@@ -113,6 +113,8 @@ EXPORTS = {
                                     _vp, _vp, _vp, _vp], C.c_int),
     "nedf_compose_make_labels": ([_H, C.c_int, C.c_int64, C.c_uint64, C.c_int, C.c_int, _vp, _vp, _vp, _vp],
                                  C.c_int),
+    "nedf_compose_make_labels_density": ([_H, C.c_int, C.c_int64, C.c_uint64, C.c_int, C.c_int, C.c_int, _fp, _vp,
+                                          _vp, _vp, _vp], C.c_int),
     "nedf_compose_train_step": ([_H, C.c_int, C.c_int, C.c_float, _fp], C.c_int),
     "nedf_compose_loss_grad": ([_H, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _fp], C.c_int),
     "nedf_compose_get_nedf_weights": ([_H, C.c_int, _fp, C.c_int64], C.c_int),
@@ -349,6 +351,13 @@ class Renderer:
                     hit_star=None):
         return self._check(_lib.nedf_compose_make_labels(self.h, type_, n_rays, seed, march_steps, march_bisect,
                                                          _ptr(o), _ptr(d), _ptr(m_star), _ptr(hit_star)))
+
+    def make_labels_density(self, type_, n_rays, seed, n_samples, dens_hidden, dens_width, dens_w, o=None, d=None,
+                            m_star=None, hit_star=None):
+        w = np.ascontiguousarray(dens_w, np.float32)
+        return self._check(_lib.nedf_compose_make_labels_density(self.h, type_, n_rays, seed, n_samples, dens_hidden,
+                                                                 dens_width, _fptr(w), _ptr(o), _ptr(d), _ptr(m_star),
+                                                                 _ptr(hit_star)))
 
     def train_step(self, type_, batch, lr, want_loss=False):
         loss = C.c_float(0.0)
