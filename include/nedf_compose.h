@@ -76,8 +76,9 @@ enum nedf_arch {            /* the NeDF network of every type                   
                                h' = ReLU(h + W2 ReLU(W1 h + b1) + b2), tails 256 -> 1 + 64 (hit
                                logit, coarse bins) and 256 -> 128 (fine bins), argmax decode of
                                Eq. 4.  Packed weights W[out][in] then b[out]: head, per block W1,
-                               b1, W2, b2, tail A, tail B (2,413,249 floats).  BF16 precision only;
-                               no training call */
+                               b1, W2, b2, tail A, tail B (2,413,249 floats).  BF16 precision only
+                               for rendering; training (loss_grad, train_step) uses the BCE loss of
+                               Eq. 6 in FP32 with the dense products in cuBLAS */
 };
 enum nedf_depth_source {    /* what answers the (ray, instance) depth queries of Steps 1 and 3 */
     NEDF_DEPTH_NEDF = 0,    /* the Neural Depth Field (the method)                             */

@@ -3,6 +3,7 @@
 // Host side of the renderer: argument checks, ownership of device workspace, weight layout
 // conversion, and the launch sequence of each call.  All arithmetic of the method runs in the
 // kernels; this file only moves and validates data.
+#include <cublas_v2.h>
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
@@ -66,6 +67,7 @@ struct nedf_handle {
     Counters *d_cnt = nullptr;
     float *d_train_scratch = nullptr;
     size_t train_scratch_bytes = 0;
+    cublasHandle_t cublas = nullptr;             // classifier training's dense products (created on first use)
     float *d_loss = nullptr;
     std::vector<TrainState> train;
     std::vector<DevType> types_host;
@@ -389,6 +391,7 @@ void nedf_compose_destroy(nedf_handle *h)
         for (void *p : tp)
             if (p) cudaFree(p);
     }
+    if (h->cublas) cublasDestroy(h->cublas);
     if (h->h_frame) cudaFreeHost(h->h_frame);
     if (h->h_cam) cudaFreeHost(h->h_cam);
     for (cudaEvent_t e : h->ev)
@@ -1166,9 +1169,16 @@ int nedf_compose_make_labels_density(nedf_handle *h, int type, int64_t n_rays, u
 
 static int ensure_train_scratch(nedf_handle *h, int batch)
 {
-    if (h->cfg.nedf_arch != NEDF_ARCH_REGRESSION)
-        return fail(h, NEDF_ERR_UNSUPPORTED, "training is implemented for the regression NeDF only");
-    size_t need = train_scratch_bytes(batch, h->cfg.nedf_hidden, h->cfg.nedf_width, h->nedf_params);
+    const bool cls = h->cfg.nedf_arch == NEDF_ARCH_CLASSIFIER;
+    if (cls && !h->cublas) {
+        if (cublasCreate(&h->cublas) != CUBLAS_STATUS_SUCCESS) {
+            h->cublas = nullptr;
+            return fail(h, NEDF_ERR_CUDA, "cublasCreate");
+        }
+    }
+    if (cls && cublasSetStream(h->cublas, h->stream) != CUBLAS_STATUS_SUCCESS) return fail(h, NEDF_ERR_CUDA, "cublasSetStream");
+    size_t need = cls ? cls_train_scratch_bytes(batch)
+                      : train_scratch_bytes(batch, h->cfg.nedf_hidden, h->cfg.nedf_width, h->nedf_params);
     if (need > h->train_scratch_bytes) {
         if (h->d_train_scratch) cudaFree(h->d_train_scratch);
         h->d_train_scratch = nullptr;
@@ -1177,6 +1187,19 @@ static int ensure_train_scratch(nedf_handle *h, int batch)
         h->train_scratch_bytes = need;
     }
     return NEDF_OK;
+}
+
+static ClsTrainLaunch make_cls_train_launch(nedf_handle *h, int type)
+{
+    ClsTrainLaunch L{};
+    L.rb = h->types_host[type].rb;
+    L.master = h->train[type].master;
+    L.scratch = h->d_train_scratch;
+    L.loss = h->d_loss;
+    L.cublas = h->cublas;
+    L.num_sms = h->num_sms;
+    L.stream = h->stream;
+    return L;
 }
 
 static TrainLaunch make_train_launch(nedf_handle *h, int type)
@@ -1204,8 +1227,12 @@ int nedf_compose_loss_grad(nedf_handle *h, int type, int n, const float *o, cons
     if (n < 1 || n > (1 << 24)) return fail(h, NEDF_ERR_ARG, "n out of range");
     int r = ensure_train_scratch(h, n);
     if (r != NEDF_OK) return r;
-    TrainLaunch L = make_train_launch(h, type);
-    CK(h, launch_loss_grad(L, o, d, m_star, hit_star, n, grad));
+    if (h->cfg.nedf_arch == NEDF_ARCH_CLASSIFIER) {
+        CK(h, launch_cls_loss_grad(make_cls_train_launch(h, type), o, d, m_star, hit_star, n, grad));
+    } else {
+        TrainLaunch L = make_train_launch(h, type);
+        CK(h, launch_loss_grad(L, o, d, m_star, hit_star, n, grad));
+    }
     CK(h, cudaStreamSynchronize(h->stream));
     if (loss_host) CK(h, cudaMemcpy(loss_host, h->d_loss, sizeof(float), cudaMemcpyDeviceToHost));
     return nedf_compose_sync(h);
@@ -1223,10 +1250,15 @@ int nedf_compose_train_step(nedf_handle *h, int type, int batch, float lr, float
     if (!(lr > 0.f) || !std::isfinite(lr)) return fail(h, NEDF_ERR_ARG, "lr");
     int r = ensure_train_scratch(h, batch);
     if (r != NEDF_OK) return r;
-    TrainLaunch L = make_train_launch(h, type);
     ts.step += 1;
-    CK(h, launch_train_step(L, ts.o, ts.d, ts.m_star, ts.hit_star, ts.n_rays, ts.cursor, batch, ts.adam_m,
-                            ts.adam_v, ts.step, lr));
+    if (h->cfg.nedf_arch == NEDF_ARCH_CLASSIFIER) {
+        CK(h, launch_cls_train_step(make_cls_train_launch(h, type), ts.o, ts.d, ts.m_star, ts.hit_star, ts.n_rays,
+                                    ts.cursor, batch, ts.adam_m, ts.adam_v, ts.step, lr));
+    } else {
+        TrainLaunch L = make_train_launch(h, type);
+        CK(h, launch_train_step(L, ts.o, ts.d, ts.m_star, ts.hit_star, ts.n_rays, ts.cursor, batch, ts.adam_m,
+                                ts.adam_v, ts.step, lr));
+    }
     ts.cursor = (ts.cursor + batch) % ts.n_rays;
     if (h->d_nedf_tc)
         CK(h, pack_nedf(h, ts.master, h->d_nedf_tc + (size_t)type * h->nedf_tc_stride));

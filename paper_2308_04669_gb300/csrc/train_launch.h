@@ -41,6 +41,24 @@ cudaError_t launch_train_step(const TrainLaunch &L, const float *o, const float 
                               const float *hit_star, long long n_rays, long long start, int batch,
                               float *adam_m, float *adam_v, int step, float lr);
 
+// The paper's classifier network (train_cls.cu): Eq. 6 and its gradient by hand, dense products
+// in cuBLAS, Adam; the scratch holds a batch's activations (cls_train_scratch_bytes).
+struct ClsTrainLaunch {
+    float rb;
+    float *master;           // packed FP32 weights (head, 16 x (W1, b1, W2, b2), tail A, tail B)
+    float *scratch;
+    float *loss;             // device float[4]: loss, hit rows
+    void *cublas;            // cublasHandle_t bound to stream
+    int num_sms;
+    cudaStream_t stream;
+};
+size_t cls_train_scratch_bytes(long long batch);
+cudaError_t launch_cls_loss_grad(const ClsTrainLaunch &L, const float *o, const float *d, const float *m_star,
+                                 const float *hit_star, int n, float *grad);
+cudaError_t launch_cls_train_step(const ClsTrainLaunch &L, const float *o, const float *d, const float *m_star,
+                                  const float *hit_star, long long n_rays, long long start, int batch, float *adam_m,
+                                  float *adam_v, int step, float lr);
+
 // Re-derives the renderer's copy of the weights from the master weights.
 cudaError_t launch_refresh_weights(const TrainLaunch &L);
 

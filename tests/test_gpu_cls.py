@@ -107,16 +107,84 @@ def test_classifier_frame_matches_oracle(orc):
     print(dict(pixels=len(px), hit=int(hit.sum()), same=float(same.sum() / decided.sum())))
 
 
-def test_classifier_limits():
-    """BF16 only; the training calls refuse the classifier."""
+def test_classifier_renders_in_bf16_only():
     from paper_2308_04669_gb300 import native
     sc = sg.classifier_scene(16, 16)
     with pytest.raises(native.NedfError) as e:
         native.renderer_for(sc, precision=native.PREC_FP32)
     assert e.value.code == native.NEDF_ERR_UNSUPPORTED
+
+
+def _fine_centres(m):
+    """Labels moved to the centre of their fine bin, away from the segment operator's edges."""
+    u = (np.asarray(m, np.float64) + 1.0) * 0.5 * sg.CLS_NC
+    c = np.clip(np.floor(u), 0, sg.CLS_NC - 1)
+    f = np.clip(np.floor((u - c) * sg.CLS_NF), 0, sg.CLS_NF - 1)
+    return ((c + (f + 0.5) / sg.CLS_NF) * 2.0 / sg.CLS_NC - 1.0).astype(np.float32)
+
+
+def test_classifier_loss_and_gradient_match_oracle(orc):
+    """Eq. 6 and its gradient on the GPU (FP32, dense products in cuBLAS) against the oracle's
+    hand-written FP64 backward pass, on march labels of a sphere."""
+    import torch
+    from paper_2308_04669_gb300 import native
+    sc = sg.classifier_scene(16, 16)
     r = native.renderer_for(sc, precision=native.PREC_BF16)
-    r.make_labels(0, 1024, 1)
-    with pytest.raises(native.NedfError) as e:
-        r.train_step(0, 64, 1e-3)
-    assert e.value.code == native.NEDF_ERR_UNSUPPORTED
+    n = 96
+    o = torch.empty(n, 3, device="cuda"); d = torch.empty(n, 3, device="cuda")
+    m = torch.empty(n, device="cuda"); h = torch.empty(n, device="cuda")
+    r.make_labels(0, n, 4, 256, 8, o, d, m, h)
+    torch.cuda.synchronize()
+    ms = torch.tensor(_fine_centres(m.cpu().numpy()), device="cuda")
+    g = torch.zeros(sg.cls_param_count(), device="cuda")
+    loss = r.loss_grad(0, o, d, ms, h, g)
+    go, gd = o.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.float64)
+    X = []
+    for i in range(n):
+        dd = gd[i] / np.linalg.norm(gd[i])
+        feat, _ = orc.cls_features(go[i], dd, 1.0)
+        X.append(feat)
+    hit = (h.cpu().numpy() > 0.5).astype(np.int32)
+    assert 5 < hit.sum() < n - 5
+    ol, og = orc.cls_loss_grad(sc.types[0].nedf_w.astype(np.float64), np.array(X), ms.cpu().numpy().astype(np.float64), hit)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert abs(loss - ol) <= 1e-4 * abs(ol), (loss, ol)
+    assert np.linalg.norm(gg - og) <= 1e-3 * np.linalg.norm(og)
+    offs = np.cumsum([0] + [fi * fo + fo for fi, fo in sg.cls_layers()])
+    for li in range(len(offs) - 1):                      # every layer, not only the largest terms
+        a, b = gg[offs[li]:offs[li + 1]], og[offs[li]:offs[li + 1]]
+        assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b) + 1e-9, li
+    r.close()
+
+
+def test_classifier_training_learns_march_labels():
+    """The paper's training loop (Adam on Eq. 6) on march labels of a sphere: the loss falls and
+    the tensor-core engine, on held-out rays, finds the hits and their bins."""
+    import torch
+    from paper_2308_04669_gb300 import native
+    sc = sg.classifier_scene(16, 16)
+    r = native.renderer_for(sc, precision=native.PREC_BF16)
+    n = 1 << 13
+    ho = torch.empty(n, 3, device="cuda"); hd = torch.empty(n, 3, device="cuda")
+    hm = torch.empty(n, device="cuda"); hh = torch.empty(n, device="cuda")
+    r.make_labels(0, n, 91, 256, 8, ho, hd, hm, hh)
+
+    def judge():
+        out = torch.empty(n, 4, device="cuda")
+        r.nedf_query(0, ho, hd, out)
+        torch.cuda.synchronize()
+        q = out.cpu().numpy()
+        lab = hh.cpu().numpy() > 0.5
+        both = lab & (q[:, 3] > 0.5)
+        return dict(hit_agree=float(((q[:, 3] > 0.5) == lab).mean()),
+                    median_err=float(np.median(np.abs(q[both, 0] - hm.cpu().numpy()[both]))) if both.any() else 2.0)
+
+    before = judge()
+    r.make_labels(0, 1 << 16, 5, 256, 8)
+    losses = [r.train_step(0, 2048, 5e-4, want_loss=True) for _ in range(300)]
+    after = judge()
+    print(f"before {before} after {after}; loss {losses[0]:.4f} -> {np.mean(losses[-20:]):.4f}")
+    assert np.mean(losses[-20:]) < 0.5 * losses[0]
+    assert after["hit_agree"] > before["hit_agree"] + 0.1
+    assert after["median_err"] < 0.5 * before["median_err"]
     r.close()
