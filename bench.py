@@ -238,6 +238,67 @@ def train_types(r, scene, steps, batch, n_rays, log):
                     "loss_first_last": [[round(a, 5), round(b, 5)] for a, b in losses]}
 
 
+def classifier_frame(sc, stream, cam, lights, args, frames=5):
+    """The workload's instances, lights and NeRF colour networks with every type's NeDF replaced
+    by the paper's classifier network (seeded weights): frame time and the NeDF engines alone."""
+    import copy
+    import torch
+    from paper_2308_04669_gb300 import native
+    from paper_2308_04669_gb300 import scenegen as sg
+    n = sc.W * sc.H
+    scc = copy.copy(sc)
+    scc.types = []
+    for i, t in enumerate(sc.types):
+        tc = sg.make_type(t.kind, 1, i, 0, 0, rb=t.rb, params=t.params, nedf_arch=sg.ARCH_CLASSIFIER)
+        tc.nerf_hidden, tc.nerf_width, tc.nerf_w, tc.albedo = t.nerf_hidden, t.nerf_width, t.nerf_w, t.albedo
+        scc.types.append(tc)
+    rc = native.renderer_for(scc, precision=native.PREC_BF16, stream=stream)
+    oc = rc.get_options()
+    for k, v in FRAME_OPTS.items():
+        setattr(oc, k, v)
+    oc.fallback_conf, oc.outlier_resample = 0.0, 0          # untrained weights: their confidence means nothing
+    rc.set_options(oc)
+    cam, lights = rc.camera(sc.eye, sc.target, sc.fov_deg), rc.lights(sc.lights)
+    cls_sched = rc.autotune(cam, lights, reps=2) if not args.no_autotune else None
+    depth = torch.empty(n, device="cuda")
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    out = torch.empty(n, 4, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rc.set_profiling(True)
+    for _ in range(2):
+        rc.render(cam, lights, depth, ids, None, None, out)
+    stc = rc.render(cam, lights, depth, ids, None, None, out, stats=True)
+    torch.cuda.synchronize()
+    ev_c = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(frames)]
+    eng_c, stg_c = {}, {}
+    for a, b in ev_c:
+        flush.zero_()
+        a.record(stream)
+        rc.render(cam, lights, depth, ids, None, None, out)
+        b.record(stream)
+        for name, ms in rc.engine_times().items():
+            eng_c[name] = eng_c.get(name, 0.0) + ms / len(ev_c)
+        for name, ms in rc.stage_times().items():
+            stg_c[name] = stg_c.get(name, 0.0) + ms / len(ev_c)
+    torch.cuda.synchronize()
+    ms_c = sum(a.elapsed_time(b) for a, b in ev_c) / len(ev_c)
+    pk_c, pk_kind_c = peaks()
+    pairs_c = {"step1_nedf": stc.primary_pairs, "step3_nedf": stc.shadow_pairs}
+    eng = {}
+    for k, np_ in pairs_c.items():
+        if eng_c.get(k):
+            tf = np_ * CLS_FLOP / (eng_c[k] * 1e-3) / 1e12
+            eng[k] = {"engine_ms": round(eng_c[k], 4), "pairs": int(np_), "engine_tflops": round(tf, 1),
+                      "engine_frac": round(tf / pk_c["bf16_tflops"], 3)}
+    rc.close()
+    return {"ms_per_frame": ms_c, "rays_per_s": n / (ms_c * 1e-3), "flop_per_query": CLS_FLOP,
+            "engines": eng, "stage_ms": {k: round(v, 4) for k, v in stg_c.items()},
+            "hit_pixels": int(stc.hit_pixels), "schedule": cls_sched,
+            "peak_basis": f"bf16 dense, {pk_kind_c} (burst)",
+            "note": "same instances, lights and NeRF colour networks; every type's NeDF is the paper's "
+                    "classifier network with seeded random weights; no confidence fallback"}
+
+
 def run_ours(args):
     import torch
     from paper_2308_04669_gb300 import build as nbuild
@@ -253,6 +314,11 @@ def run_ours(args):
     n_li = len(sc.lights)
     stream = torch.cuda.Stream()            # a non-default stream: frames are CUDA-graph captured
     torch.cuda.set_stream(stream)
+    if args.cls_only:                       # the classifier frame alone (profiling)
+        if rank == 0:
+            print(json.dumps({"classifier_frame": classifier_frame(sc, stream, None, None, args, frames=args.steps)}),
+                  flush=True)
+        return
     prec = {"fp32": native.PREC_FP32, "bf16": native.PREC_BF16, "fp8": native.PREC_FP8}[args.precision]
     r = native.renderer_for(sc, precision=prec, stream=stream)
     log = {}
@@ -441,53 +507,7 @@ def run_ours(args):
     # ---- the same scene with the paper's classifier intersection network on every type --------
     cls = None
     if prec == native.PREC_BF16 and not args.no_cls:
-        import copy
-        scc = copy.copy(sc)
-        scc.types = []
-        for i, t in enumerate(sc.types):
-            tc = sg.make_type(t.kind, 1, i, 0, 0, rb=t.rb, params=t.params, nedf_arch=sg.ARCH_CLASSIFIER)
-            tc.nerf_hidden, tc.nerf_width, tc.nerf_w, tc.albedo = t.nerf_hidden, t.nerf_width, t.nerf_w, t.albedo
-            scc.types.append(tc)
-        rc = native.renderer_for(scc, precision=prec, stream=stream)
-        oc = rc.get_options()
-        for k, v in FRAME_OPTS.items():
-            setattr(oc, k, v)
-        oc.fallback_conf, oc.outlier_resample = 0.0, 0      # untrained weights: their confidence means nothing
-        rc.set_options(oc)
-        cls_sched = rc.autotune(cam, lights, reps=2) if not args.no_autotune else None
-        rc.set_profiling(True)
-        for _ in range(2):
-            rc.render(cam, lights, depth, ids, None, None, out)
-        stc = rc.render(cam, lights, depth, ids, None, None, out, stats=True)
-        torch.cuda.synchronize()
-        ev_c = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
-        eng_c, stg_c = {}, {}
-        for a, b in ev_c:
-            flush.zero_()
-            a.record(stream)
-            rc.render(cam, lights, depth, ids, None, None, out)
-            b.record(stream)
-            for name, ms in rc.engine_times().items():
-                eng_c[name] = eng_c.get(name, 0.0) + ms / len(ev_c)
-            for name, ms in rc.stage_times().items():
-                stg_c[name] = stg_c.get(name, 0.0) + ms / len(ev_c)
-        torch.cuda.synchronize()
-        ms_c = sum(a.elapsed_time(b) for a, b in ev_c) / len(ev_c)
-        pk_c, pk_kind_c = peaks()
-        pairs_c = {"step1_nedf": stc.primary_pairs, "step3_nedf": stc.shadow_pairs}
-        eng = {}
-        for k, np_ in pairs_c.items():
-            if eng_c.get(k):
-                tf = np_ * CLS_FLOP / (eng_c[k] * 1e-3) / 1e12
-                eng[k] = {"engine_ms": round(eng_c[k], 4), "pairs": int(np_), "engine_tflops": round(tf, 1),
-                          "engine_frac": round(tf / pk_c["bf16_tflops"], 3)}
-        cls = {"ms_per_frame": ms_c, "rays_per_s": n / (ms_c * 1e-3), "flop_per_query": CLS_FLOP,
-               "engines": eng, "stage_ms": {k: round(v, 4) for k, v in stg_c.items()},
-               "hit_pixels": int(stc.hit_pixels), "schedule": cls_sched,
-               "peak_basis": f"bf16 dense, {pk_kind_c} (burst)",
-               "note": "same instances, lights and NeRF colour networks; every type's NeDF is the paper's "
-                       "classifier network with seeded random weights; no confidence fallback"}
-        rc.close()
+        cls = classifier_frame(sc, stream, cam, lights, args)
 
     # ---- the same frame with the FP32 CUDA-core networks (reference precision) -----------------
     fp32 = None
@@ -627,6 +647,7 @@ def main():
     ap.add_argument("--no-resample", action="store_true", help="skip the frame with Step-2 outlier resampling")
     ap.add_argument("--no-edit", action="store_true", help="skip the buffer-reuse (edit) frames")
     ap.add_argument("--no-cls", action="store_true", help="skip the classifier-network frames")
+    ap.add_argument("--cls-only", action="store_true", help="only the classifier-network frame (for profiling)")
     ap.add_argument("--schedule", default="", help="fixed stage bytes per tensor-core kernel (shade, march colour, "
                     "Step-1 NeDF, Step-3 NeDF, query), comma-separated; skips the autotuner")
     ap.add_argument("--no-march-dense", dest="march_dense", action="store_false",
