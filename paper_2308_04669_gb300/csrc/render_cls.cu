@@ -13,7 +13,8 @@
 // points at a time), 32 body layers and the tail.  Every weight chunk (256 outputs x 16 inputs,
 // 8 KB) feeds one M = 128, N = 256 MMA per half.
 //   warps 0-3 / 4-7  epilogue of rows 0..127 / 128..255: encoding, then per step tcgen05.ld of
-//                    the accumulator, bias, ReLU, BF16, next A operand in shared memory;
+//                    the accumulator, bias (the tile type's FP32 biases, kept in shared memory),
+//                    ReLU, BF16, next A operand in shared memory;
 //   warp 8           producer: the type's weight chunks, step after step, through the stage ring;
 //   warp 9           MMA issuer and TMEM owner.
 // Residual stream: a block's input h is the A operand of W1 (BF16).  W1's epilogue reads it back
@@ -39,7 +40,8 @@ constexpr int kClsBiasRows = 34;            // head, 32 body layers, tail (193 o
 constexpr size_t kClsABytes = 65536;        // one half's A operand: 128 rows x 256 BF16
 constexpr int kClsRing = 65536;
 constexpr int kClsSMax = kClsRing / kClsChunkBytes;
-constexpr size_t kClsSmem = 2 * kClsABytes + kClsRing;
+constexpr size_t kClsBiasBytes = (size_t)kClsBiasRows * kClsW * 4;
+constexpr size_t kClsSmem = 2 * kClsABytes + kClsRing + kClsBiasBytes;   // + the type's FP32 biases
 
 // Packed FP32 master layout (W[out][in] then b[out]): head, 16 x (W1, b1, W2, b2), tail A, tail B.
 constexpr long long kClsHeadW = (long long)kClsIn * kClsW;
@@ -168,8 +170,14 @@ __device__ __forceinline__ void cls_store(uint8_t *A, int r, int c0, const uint3
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         float x[8];
+        float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
+        if (b) {
+            b0 = *reinterpret_cast<const float4 *>(b + c0 + 8 * q);
+            b1 = *reinterpret_cast<const float4 *>(b + c0 + 8 * q + 4);
+        }
+        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-        for (int e = 0; e < 8; ++e) x[e] = u2f(v[8 * q + e]) + (b ? __ldg(b + c0 + 8 * q + e) : 0.0f);
+        for (int e = 0; e < 8; ++e) x[e] = u2f(v[8 * q + e]) + bb[e];
         uint4 pk;
         if (RELU) {
             pk.x = pack_bf16_relu(x[0], x[1]); pk.y = pack_bf16_relu(x[2], x[3]);
@@ -192,11 +200,14 @@ __device__ __forceinline__ void cls_block_first(uint8_t *A, int r, int c0, const
     for (int q = 0; q < 4; ++q) {
         const uint4 h = *reinterpret_cast<const uint4 *>(A + a_offset(r, c0 + 8 * q));
         const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+        const float4 p0 = *reinterpret_cast<const float4 *>(b2 + c0 + 8 * q);
+        const float4 p1 = *reinterpret_cast<const float4 *>(b2 + c0 + 8 * q + 4);
+        const float bb[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int j = 8 * q + 2 * e;
-            res[j] = __float_as_uint(__uint_as_float(hw[e] << 16) + __ldg(b2 + c0 + j));
-            res[j + 1] = __float_as_uint(__uint_as_float(hw[e] & 0xFFFF0000u) + __ldg(b2 + c0 + j + 1));
+            res[j] = __float_as_uint(__uint_as_float(hw[e] << 16) + bb[2 * e]);
+            res[j + 1] = __float_as_uint(__uint_as_float(hw[e] & 0xFFFF0000u) + bb[2 * e + 1]);
         }
     }
     cls_store<true>(A, r, c0, v, b1);
@@ -308,12 +319,22 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedfc(Workspace ws, PipeArg
         const int R = g * kHalf + r;
         const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(g * kClsW);
         uint8_t *Ag = A[g];
+        float *bias = reinterpret_cast<float *>(smem + 2 * kClsABytes + kClsRing);   // the tile type's biases
+        int bias_type = -1;
         unsigned long long jb = 0;
         for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
             if (epilogue_any(*abort != 0)) break;
             const int t = pipe_tile_type<MODE>(ws, none, a, tile);
             const DevType T = ws.types[t];
-            const float *bias = reinterpret_cast<const float *>(a.blobs + (size_t)t * a.blob_stride + kClsWBytes);
+            if (t != bias_type) {
+                // both groups are past every read of the previous type's biases before they are replaced
+                asm volatile("bar.sync 3, 256;" ::: "memory");
+                const float4 *src = reinterpret_cast<const float4 *>(a.blobs + (size_t)t * a.blob_stride + kClsWBytes);
+                for (int i = threadIdx.x; i < kClsBiasRows * kClsW / 4; i += 2 * kHalf)
+                    reinterpret_cast<float4 *>(bias)[i] = __ldg(src + i);
+                asm volatile("bar.sync 3, 256;" ::: "memory");
+                bias_type = t;
+            }
             unsigned long long idx;
             bool valid;
             PairRay pr{};
@@ -353,14 +374,14 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedfc(Workspace ws, PipeArg
                     }
                 } else {
                     // tail: hit logit, first maximum of the coarse and of the fine logits (Eq. 4)
-                    const float *bt = bias + (size_t)33 * kClsW;
+                    const float *bt = bias + (size_t)33 * kClsW;       // shared memory
                     float bc = -INFINITY, bf = -INFINITY, al = 0.f;
                     int ic = 0, jf = 0;
                     cls_rows(trow, [&](int c0, const uint32_t (&v)[32]) {
 #pragma unroll
                         for (int e = 0; e < 32; ++e) {
                             const int col = c0 + e;
-                            const float x = u2f(v[e]) + __ldg(bt + col);
+                            const float x = u2f(v[e]) + bt[col];
                             if (col == 0) al = x;
                             else if (col <= kClsNC) { if (x > bc) { bc = x; ic = col - 1; } }
                             else if (col <= kClsNC + kClsNF) { if (x > bf) { bf = x; jf = col - 1 - kClsNC; } }
