@@ -103,8 +103,9 @@ cudaError_t launch_pack_cls(const float *master, void *blob, cudaStream_t st)
 
 // ---- epilogue pieces (one thread = one row of its half) -------------------------------------------
 // Encoded points 4p .. 4p + 3 of this row as A columns 0..255: per point [x, sin(2^k x), cos(2^k x)]
-// (k = 0..9, coordinate fastest) and a zero.  sin/cos of 2^k x come from sincosf at k = 0, 4, 8 and
-// the double-angle identities in between (at most three doublings: a few ulp).
+// (k = 0..9, coordinate fastest) and a zero.  sin/cos of 2^k x come from sincosf at k = 0 and 5 and
+// the double-angle identities in between (at most four doublings: about 16 ulp, far below a BF16
+// step).
 __device__ __forceinline__ void cls_encode_pass(uint8_t *A, int r, V3 pe, V3 step, int p, bool valid)
 {
 #pragma unroll 1
@@ -118,7 +119,7 @@ __device__ __forceinline__ void cls_encode_pass(uint8_t *A, int r, V3 pe, V3 ste
             float s = 0.f, co = 1.f;
 #pragma unroll
             for (int k = 0; k < 10; ++k) {
-                if ((k & 3) == 0) {
+                if (k == 0 || k == 5) {
                     sincosf(ldexpf(xs[c], k), &s, &co);
                 } else {
                     const float s2 = 2.0f * s * co, c2 = (co - s) * (co + s);
@@ -211,8 +212,7 @@ __device__ __forceinline__ void cls_block_first(uint8_t *A, int r, int c0, const
         }
     }
     cls_store<true>(A, r, c0, v, b1);
-    tmem_st32(tcol, res);
-    tmem_wait_st();          // res is a temporary: its registers are free once the store is done
+    tmem_st32(tcol, res);    // the caller waits for all of the layer's stores at once
 }
 
 // ---- the engine ------------------------------------------------------------------------------------
@@ -369,6 +369,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedfc(Workspace ws, PipeArg
                         cls_rows(trow, [&](int c0, const uint32_t (&v)[32]) {
                             cls_block_first(Ag, r, c0, v, bl, bl + kClsW, trow + c0);
                         });
+                        tmem_wait_st();
                     } else {
                         cls_rows(trow, [&](int c0, const uint32_t (&v)[32]) { cls_store<true>(Ag, r, c0, v, nullptr); });
                     }
