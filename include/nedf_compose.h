@@ -412,10 +412,14 @@ int nedf_compose_make_labels_density(nedf_handle *h, int type, int64_t n_rays, u
 
 /* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) of the type's NeDF on `batch`
  * consecutive rays of its training set (wrapping around), starting where the previous step
- * ended.  Loss (regression form of Eq. 6): mean over labelled hits of (m - m*)^2 plus
- * 0.1 * mean BCE(a, hit*).  FP32 master weights and moments; the rendering copy is refreshed.
- * loss_host (host float, may be NULL) receives the loss of this batch; giving it synchronises.
- * Errors: NEDF_ERR_STATE (no training set for the type), NEDF_ERR_ARG. */
+ * ended.  Loss, NEDF_ARCH_REGRESSION (regression form of Eq. 6): mean over labelled hits of
+ * (m - m*)^2 plus 0.1 * mean BCE(a, hit*).  NEDF_ARCH_CLASSIFIER (Eq. 6 itself): mean over
+ * labelled hits of BCE(coarse logits, one-hot S_c(m*)) + BCE(fine logits, one-hot S_f(m*)), each
+ * the mean over its bins, plus 0.1 * mean BCE(hit logit, hit*); the segment operator S takes
+ * u = (m* + 1) 32 to c = floor(u), f = floor((u - c) 128); dense products in cuBLAS.  FP32 master
+ * weights and moments; the rendering copy is refreshed.  loss_host (host float, may be NULL)
+ * receives the loss of this batch; giving it synchronises.  Errors: NEDF_ERR_STATE (no training
+ * set for the type), NEDF_ERR_ARG, NEDF_ERR_CUDA. */
 int nedf_compose_train_step(nedf_handle *h, int type, int batch, float lr, float *loss_host);
 
 /* Loss and gradient of the type's current NeDF weights on n caller rays / labels (all device:
