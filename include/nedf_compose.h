@@ -51,7 +51,7 @@ extern "C" {
 #define NEDF_ERR_ARG (-1)          /* invalid argument (null, out of range, non-finite)          */
 #define NEDF_ERR_CUDA (-2)         /* a CUDA runtime call failed                                 */
 #define NEDF_ERR_OOM (-3)          /* device allocation failed                                   */
-#define NEDF_ERR_UNSUPPORTED (-4)  /* configuration this build does not implement                */
+#define NEDF_ERR_UNSUPPORTED (-4)  /* configuration the library does not implement              */
 #define NEDF_ERR_CAPACITY (-5)     /* a device work list overflowed; the frame is incomplete     */
 #define NEDF_ERR_TIMEOUT (-6)      /* a bounded device wait gave up                              */
 #define NEDF_ERR_STATE (-7)        /* call out of order (e.g. render before set_types)           */
