@@ -355,8 +355,9 @@ int nedf_compose_nedf_query(nedf_handle *h, int type, int n, const float *o, con
 
 /* ---- Step 1 without allocations ------------------------------------------------------------ */
 
-/* Depth and id buffers of Step 1 (same arithmetic as nedf_compose_render with default options)
- * for callers that cannot allocate device memory: code embedded in a host whose device memory
+/* Depth and id buffers of Step 1 (the same method as nedf_compose_render with default options,
+ * in FP32 with its own summation order: depths agree within the render tolerance, ids wherever
+ * the two nearest hits are not tied to within that tolerance) for callers that cannot allocate device memory: code embedded in a host whose device memory
  * belongs to that host's own pool, real-time loops that must not block on or fail in an
  * allocation, or phases in which the allocator may not be touched.  No handle is needed and
  * nothing is allocated (no cudaMalloc, cudaFree or allocating library call); the caller passes
@@ -365,7 +366,10 @@ int nedf_compose_nedf_query(nedf_handle *h, int type, int n, const float *o, con
  * the process exits).  The paper has no counterpart for this entry point.
  *   width, height    framebuffer size; width * height must not exceed 512 * 512 (NEDF_ERR_ARG)
  *   cam              host camera record
- *   inst_dev         device array of n_inst nedf_instance records (id = index)
+ *   inst_dev         device array of n_inst nedf_instance records (id = index); each record's
+ *                    type must be < n_types and its s a positive finite number: the records are
+ *                    in device memory where the call cannot check them, so an instance that breaks
+ *                    this is skipped (it writes no pixel) rather than reported
  *   rb_host          host array of n_types bound radii
  *   nedf_hidden, nedf_width, nedf_weights_dev
  *                    NeDF shape and device array of n_types packed NeDF weight sets, back to back
@@ -373,8 +377,9 @@ int nedf_compose_nedf_query(nedf_handle *h, int type, int n, const float *o, con
  *   cuda_stream      stream the work is queued on (asynchronous; NULL = legacy default stream)
  * Every call shares the scratch array and clears the part it uses first; calls whose work
  * overlaps on the GPU (other streams or threads) race on it and must be serialised by the caller.
- * The first call on each device looks up the scratch array's device address (once, with that
- * device current); make that first call before any stream capture.  Errors (null pointers,
+ * The first successful call on each device looks up the scratch array's device address (with
+ * that device current; a failed lookup is retried by the next call); make that first call before
+ * any stream capture.  Errors (null pointers,
  * sizes, shapes, a CUDA failure) return a NEDF_ERR_* code; the text is available from
  * nedf_compose_last_error(NULL) on the calling thread. */
 int nedf_compose_depth_noalloc(int width, int height, const nedf_camera *cam, int n_inst,

@@ -3,8 +3,9 @@
 // Some callers cannot call cudaMalloc at all: a renderer embedded in a host application whose
 // device memory is owned by that application's own pool, a real-time loop that must not block
 // on or fail in an allocation mid-frame, or code that runs while the host is forbidden from
-// touching the allocator.  For them, nedf_compose_depth_noalloc runs the same Step-1 arithmetic
-// as the handle-based renderer (ray transform, bound cull, NeDF MLP, strict-'<' z-min) with only
+// touching the allocator.  For them, nedf_compose_depth_noalloc runs the same Step-1 method as
+// the handle-based renderer (ray transform, bound cull, NeDF MLP, strict-'<' z-min; FP32, with its
+// own loop order, so results agree within the render tolerance) with only
 // caller-owned inputs and outputs and one fixed scratch array that lives in this file:
 // the packed (depth, id) keys of at most kNoAllocMaxPixels pixels.
 //
@@ -12,8 +13,9 @@
 // and every call shares it: calls whose work overlaps on the GPU (two streams, or two threads)
 // race on it.  Each call clears the part it uses before writing.
 //
-// The first call on a device looks up the device address of the array (cudaGetSymbolAddress,
-// once per device with that device current); make that first call before any stream capture.
+// The first successful call on a device looks up the device address of the array
+// (cudaGetSymbolAddress, with that device current); make that first call before any stream
+// capture.
 // The paper has no counterpart for this entry point.
 #include <mutex>
 #include <string>
@@ -28,9 +30,11 @@ constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned long long g_noalloc_keys[kNoAllocMaxPixels];
 
+// Device address of g_noalloc_keys per device, looked up on the first call that succeeds; a
+// failed lookup is not remembered, so a later call (for example once a context is current)
+// tries again.
 static unsigned long long *g_keys_dev[kNoAllocMaxDevices];
-static std::once_flag g_keys_once[kNoAllocMaxDevices];
-static cudaError_t g_keys_err[kNoAllocMaxDevices];
+static std::mutex g_keys_mutex;
 void set_thread_error(const std::string &msg);   // api.cu
 
 struct NoAllocParams {
@@ -39,6 +43,7 @@ struct NoAllocParams {
     const nedf_instance *inst;
     const float *w;              // packed NeDF weights, n_types x n_params
     long long n_params;
+    int n_types;                 // instances with type >= n_types are skipped (never read)
     float rb[kMaxTypes];
     int hidden, width;
     unsigned long long *keys;
@@ -161,6 +166,9 @@ __global__ void __launch_bounds__(kThreads) k_na_step1(NoAllocParams P)
     }
     __syncthreads();
     const nedf_instance src = P.inst[inst];
+    // The records live in device memory, so the host cannot check them; an instance of an unknown
+    // type or with a scale that is not a positive finite number is skipped (the test is uniform over the block, which returns as a whole).
+    if (src.type >= (uint32_t)P.n_types || !(src.s > 0.0f) || !isfinite(src.s)) return;
     DevInst I;
     for (int c = 0; c < 9; ++c) I.R[c] = src.R[c];
     for (int c = 0; c < 3; ++c) I.T[c] = src.T[c];
@@ -279,13 +287,20 @@ extern "C" int nedf_compose_depth_noalloc(int width, int height, const nedf_came
     if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
         return fail(NEDF_ERR_CUDA, "nedf_compose_depth_noalloc: cudaGetDevice failed");
     // once per device, with that device current: the device address of the scratch array
-    std::call_once(g_keys_once[dev], [dev]() {
-        void *p = nullptr;
-        g_keys_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_keys);
-        g_keys_dev[dev] = static_cast<unsigned long long *>(p);
-    });
-    if (g_keys_err[dev] != cudaSuccess || !g_keys_dev[dev])
-        return fail(NEDF_ERR_CUDA, "nedf_compose_depth_noalloc: cudaGetSymbolAddress of the scratch array failed");
+    unsigned long long *keys = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_keys_mutex);
+        if (!g_keys_dev[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_keys);
+            if (e != cudaSuccess || !p) {
+                (void)cudaGetLastError();
+                return fail(NEDF_ERR_CUDA, "nedf_compose_depth_noalloc: cudaGetSymbolAddress of the scratch array failed");
+            }
+            g_keys_dev[dev] = static_cast<unsigned long long *>(p);
+        }
+        keys = g_keys_dev[dev];
+    }
     NoAllocParams P{};
     P.f.W = width;
     P.f.H = height;
@@ -299,10 +314,11 @@ extern "C" int nedf_compose_depth_noalloc(int width, int height, const nedf_came
     P.n_params = (long long)kNedfIn * nedf_width + nedf_width +
                  (long long)(nedf_hidden - 1) * ((long long)nedf_width * nedf_width + nedf_width) +
                  (long long)nedf_width * 2 + 2;
+    P.n_types = n_types;
     for (int t = 0; t < n_types; ++t) P.rb[t] = rb_host[t];
     P.hidden = nedf_hidden;
     P.width = nedf_width;
-    P.keys = g_keys_dev[dev];
+    P.keys = keys;
     P.depth = depth_dev;
     P.id = id_dev;
     cudaStream_t st = (cudaStream_t)cuda_stream;

@@ -1,0 +1,268 @@
+"""Pins of the oracle's remaining decision logic against closed forms.
+
+* The MLP-mode decisions of a depth query (Algorithm 1's NeDF generation with the confidence
+  fallback and the depth check of Section "Deferred Shading"): constant-output networks on the
+  analytic sphere, whose surface depth is a quadratic root, so each branch's result is known.
+* The signed distance functions of the five extra object kinds of the 4096-instance workload,
+  against their zero sets and distances in closed form, and the plain volume rendering of several
+  instances on one ray (front to back by entry distance, Algorithm 1's plain counterpart).
+
+Each test is chosen so that breaking its branch (a reversed comparison, a wrong bracket, a wrong
+order or axis) fails it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2308_04669_gb300 import scenegen as sg
+
+from .test_oracle_pins import constant_nedf, one_instance_scene
+
+LN9 = math.log(9.0)              # logit whose confidence max(p, 1 - p) is exactly 0.9
+EYE, DIR = np.array([0.0, 0.0, 3.0]), np.array([0.0, 0.0, -1.0])
+SURF = 2.5                       # ray from (0,0,3) along -z meets the r = 0.5 sphere at t = 2.5
+H = float(np.float32(0.05))       # the depth check's half window (shade_half, a float32 input)
+
+
+def _query(orc, m, a, **kw):
+    """Query of the one-sphere scene with a network whose output is the constant (m, a)."""
+    sc = one_instance_scene(sg.SDF_SPHERE, nedf_w=constant_nedf(m, a))
+    osc = orc.OracleScene(sc)
+    assert osc.c.shade_half == H
+    kw.setdefault("march_n", 4096)
+    kw.setdefault("march_b", 60)
+    hit, out, _ = orc.query(osc, 0, EYE, DIR, **kw)
+    return hit, out[0]
+
+
+def _m_for_depth(D):
+    """m such that the NeDF's depth on the test ray is D (Eq. 2: D = t_perp - rb m, t_perp = 3),
+    rounded to float32 as the weights are; _depth_of(m) is the depth the network then gives."""
+    return float(np.float32(3.0 - D))
+
+
+def _depth_of(m):
+    return 3.0 - m
+
+
+# ------------------------------------------------------------------------------------------------
+# confidence fallback
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_confidence_below_threshold_goes_to_the_plain_method(orc, sign):
+    """conf = max(p, 1-p) with p = sigmoid(a): just under 0.9 the pair is re-answered by the plain
+    method (exact surface 2.5), just over it keeps the network's answer."""
+    m = _m_for_depth(2.8)                                        # the network says 2.8, 0.3 off
+    D_net = _depth_of(m)
+    hit, D = _query(orc, m, sign * (LN9 - 1e-3), fallback_conf=0.9)
+    assert hit and abs(D - SURF) < 1e-9                          # marched: the true surface
+    hit, D = _query(orc, m, sign * (LN9 + 1e-3), fallback_conf=0.9)
+    if sign > 0:
+        assert hit and abs(D - D_net) < 1e-12                    # confident hit: the network's depth
+    else:
+        assert not hit                                           # confident miss stays a miss
+    # without the fallback the network's answer stands at any confidence
+    hit, D = _query(orc, m, sign * (LN9 - 1e-3), fallback_conf=0.0)
+    assert hit == (sign > 0) and (not hit or abs(D - D_net) < 1e-12)
+
+
+def test_confidence_threshold_is_a_probability_not_a_logit(orc):
+    """A logit of 0.95 (p = 0.72) is below the 0.9 confidence although above 0.9 as a number."""
+    hit, D = _query(orc, _m_for_depth(2.8), 0.95, fallback_conf=0.9)
+    assert hit and abs(D - SURF) < 1e-9
+
+
+# ------------------------------------------------------------------------------------------------
+# depth check and refinement in [D - h, D + h]
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("delta", [-0.049, -0.031, -0.004, 0.0007, 0.017, 0.0449])
+@pytest.mark.parametrize("steps", [1, 2, 4, 8])
+def test_refinement_halves_the_window_towards_the_surface(orc, delta, steps):
+    """A NeDF hit within h of the surface is bisected `steps` times on the half-density level:
+    the result is the midpoint of a bracket of width 2h / 2^steps that holds the surface, i.e. a
+    point D - h + (k + 1/2) 2h / 2^steps within h / 2^steps of the closed-form root."""
+    m = _m_for_depth(SURF + delta)
+    D0 = _depth_of(m)
+    hit, D = _query(orc, m, 5.0, refine_steps=steps)
+    assert hit
+    w = 2 * H / 2 ** steps
+    assert abs(D - SURF) <= 0.5 * w + 1e-12
+    k = (D - (D0 - H)) / w - 0.5
+    assert abs(k - round(k)) < 1e-6 and 0 <= round(k) < 2 ** steps
+
+
+def test_refinement_error_shrinks_with_each_step(orc):
+    errs = [abs(_query(orc, _m_for_depth(SURF + 0.0371), 5.0, refine_steps=s)[1] - SURF) for s in range(1, 13)]
+    assert errs[-1] <= 2 * H / 2 ** 13 + 1e-15 and errs[-1] < errs[0] / 100
+
+
+@pytest.mark.parametrize("delta", [0.2, -0.2, 0.07, -0.06])
+def test_hit_outside_the_window_is_an_outlier(orc, delta):
+    """No half-density crossing inside [D - h, D + h]: with outlier re-answering the plain method
+    gives the surface; without it the network's depth is kept unrefined."""
+    m = _m_for_depth(SURF + delta)
+    D0 = _depth_of(m)
+    hit, D = _query(orc, m, 5.0, refine_steps=4, outlier_resample=1)
+    assert hit and abs(D - SURF) < 1e-9
+    hit, D = _query(orc, m, 5.0, refine_steps=4, outlier_resample=0)
+    assert hit and abs(D - D0) < 1e-12
+
+
+def test_low_confidence_pairs_are_not_refined(orc):
+    """A pair sent to the plain method by the confidence test keeps the plain method's finer depth
+    (it is not bisected again in the window)."""
+    hit, D = _query(orc, _m_for_depth(SURF + 0.03), LN9 - 0.5, fallback_conf=0.9, refine_steps=1)
+    assert hit and abs(D - SURF) < 1e-9                          # 1 refinement step would leave ~0.025
+
+
+def test_refinement_does_not_touch_misses(orc):
+    hit, D = _query(orc, _m_for_depth(SURF + 0.01), -5.0, refine_steps=4, outlier_resample=1)
+    assert not hit
+
+
+# ------------------------------------------------------------------------------------------------
+# signed distance functions of the extra object kinds
+# ------------------------------------------------------------------------------------------------
+def _sdf(orc, kind, x):
+    return orc.sdf(kind, sg.DEFAULT_PARAMS[kind], np.asarray(x, np.float64))
+
+
+def test_capsule_cylinder_caps_and_distances(orc):
+    a, r = sg.DEFAULT_PARAMS[sg.SDF_CAPSULE]
+    a, r = float(np.float32(a)), float(np.float32(r))
+    for phi in np.linspace(0, 2 * np.pi, 7):
+        for y in (-a, -0.1, 0.0, 0.2, a):                        # side of the cylinder
+            assert abs(_sdf(orc, sg.SDF_CAPSULE, [r * math.cos(phi), y, r * math.sin(phi)])) < 1e-7
+        for th in (0.0, 0.4, 1.2):                               # the two hemispherical caps
+            p = [r * math.sin(th) * math.cos(phi), a + r * math.cos(th), r * math.sin(th) * math.sin(phi)]
+            assert abs(_sdf(orc, sg.SDF_CAPSULE, p)) < 1e-7
+            p[1] = -p[1]
+            assert abs(_sdf(orc, sg.SDF_CAPSULE, p)) < 1e-7
+    assert abs(_sdf(orc, sg.SDF_CAPSULE, [0.5, 0.1, 0.0]) - (0.5 - r)) < 1e-7
+    assert abs(_sdf(orc, sg.SDF_CAPSULE, [0.0, 0.8, 0.0]) - (0.8 - a - r)) < 1e-7
+    assert abs(_sdf(orc, sg.SDF_CAPSULE, [0.0, 0.0, 0.0]) + r) < 1e-7
+
+
+def test_rounded_cone_is_the_hull_of_its_two_spheres(orc):
+    """The convex hull of two balls is the union of the balls interpolated between them (centre
+    and radius linear in t); outside it the distance is min_t |x - c(t)| - r(t), found here by
+    brute force over t.  Its poles are the closed-form zero set."""
+    r1, y1, r2, y2 = [float(np.float32(v)) for v in sg.DEFAULT_PARAMS[sg.SDF_ROUNDCONE]]
+    assert abs(_sdf(orc, sg.SDF_ROUNDCONE, [0, y1 - r1, 0])) < 1e-7
+    assert abs(_sdf(orc, sg.SDF_ROUNDCONE, [0, y2 + r2, 0])) < 1e-7
+    t = np.linspace(0.0, 1.0, 200001)
+    c_y, rad = y1 + t * (y2 - y1), r1 + t * (r2 - r1)
+    rng = np.random.default_rng(5)
+    n_out = 0
+    for _ in range(300):
+        x = rng.uniform(-0.7, 0.7, size=3)
+        q = math.hypot(x[0], x[2])
+        brute = np.min(np.hypot(q, x[1] - c_y) - rad)
+        got = _sdf(orc, sg.SDF_ROUNDCONE, x)
+        if brute > 0:
+            assert abs(got - brute) < 1e-6, (x, got, brute)
+            n_out += 1
+        else:
+            assert got <= 1e-9                                   # inside the hull: non-positive
+    assert n_out > 100
+
+
+def test_two_sphere_union(orc):
+    c, r = [float(np.float32(v)) for v in sg.DEFAULT_PARAMS[sg.SDF_TWOSPHERE]]
+    for sx in (-1, 1):
+        for th in np.linspace(0, 2 * np.pi, 9):
+            p = [sx * c + r * math.cos(th), r * math.sin(th) * 0.6, r * math.sin(th) * 0.8]
+            if math.dist(p, [-sx * c, 0, 0]) >= r:                # not inside the other sphere
+                assert abs(_sdf(orc, sg.SDF_TWOSPHERE, p)) < 1e-7
+    assert abs(_sdf(orc, sg.SDF_TWOSPHERE, [0, 0, 0]) + (r - c)) < 1e-7       # between the centres
+    assert abs(_sdf(orc, sg.SDF_TWOSPHERE, [0, 0.9, 0]) - (math.hypot(c, 0.9) - r)) < 1e-7
+    assert abs(_sdf(orc, sg.SDF_TWOSPHERE, [1.0, 0, 0]) - (1.0 - c - r)) < 1e-7
+
+
+def test_octahedron_vertices_faces_and_face_normal_distance(orc):
+    a = float(np.float32(sg.DEFAULT_PARAMS[sg.SDF_OCTA][0]))
+    for ax in range(3):
+        for sgn in (-1, 1):
+            v = [0.0, 0.0, 0.0]
+            v[ax] = sgn * a
+            assert abs(_sdf(orc, sg.SDF_OCTA, v)) < 1e-7
+    rng = np.random.default_rng(3)
+    for _ in range(50):                                          # points on the faces
+        b = rng.dirichlet([1, 1, 1]) * a * rng.choice([-1, 1], size=3)
+        assert abs(_sdf(orc, sg.SDF_OCTA, b)) < 1e-7
+    # along a face normal through the face centre the closest point is that centre: exact distance
+    n = np.array([1.0, -1.0, 1.0]) / math.sqrt(3)
+    for t in (0.5, 0.8, 1.3):
+        assert abs(_sdf(orc, sg.SDF_OCTA, t * n) - (t - a / math.sqrt(3))) < 1e-7
+    assert _sdf(orc, sg.SDF_OCTA, [0, 0, 0]) < 0
+
+
+def _plain_torus_z(p, R, r):
+    """Ring of radius R in the xy plane (axis z), tube radius r: exact distance."""
+    return math.hypot(math.hypot(p[0], p[1]) - R, p[2]) - r
+
+
+def test_twisted_torus_untwists_to_the_plain_torus(orc):
+    """Rotating a point about y by the twist angle k y (the rotation that takes (x, z) to
+    (x cos - z sin, x sin + z cos)) turns the twisted torus back into the plain ring in the xy
+    plane: the twist is about y, proportional to y, and the ring's axis is z."""
+    R, r, k = [float(np.float32(v)) for v in sg.DEFAULT_PARAMS[sg.SDF_TWISTTORUS]]
+    rng = np.random.default_rng(9)
+    for _ in range(200):
+        x = rng.uniform(-0.8, 0.8, size=3)
+        th = k * x[1]
+        u = [x[0] * math.cos(th) - x[2] * math.sin(th), x[1], x[0] * math.sin(th) + x[2] * math.cos(th)]
+        assert abs(_sdf(orc, sg.SDF_TWISTTORUS, x) - _plain_torus_z(u, R, r)) < 1e-7
+    # in the plane y = 0 there is no twist: the tube centres (+-R, 0, 0) of the plain ring
+    for c in ([R, 0.0, 0.0], [-R, 0.0, 0.0]):
+        assert abs(_sdf(orc, sg.SDF_TWISTTORUS, c) + r) < 1e-7
+    # a tube centre off the plane y = 0 is found by twisting the plain ring's point back
+    for phi in (0.5, 1.1, 2.0, -0.8):
+        c = np.array([R * math.cos(phi), R * math.sin(phi), 0.0])
+        th = -k * c[1]
+        x = [c[0] * math.cos(th) - c[2] * math.sin(th), c[1], c[0] * math.sin(th) + c[2] * math.cos(th)]
+        assert abs(_sdf(orc, sg.SDF_TWISTTORUS, x) + r) < 1e-7
+        assert abs(_sdf(orc, sg.SDF_TWISTTORUS, c) + r) > 1e-3   # the untwisted point is not the centre
+
+
+# ------------------------------------------------------------------------------------------------
+# plain volume rendering of several instances on one ray
+# ------------------------------------------------------------------------------------------------
+def _two_sphere_colour_scene(order):
+    """Two opaque spheres (r 0.5) on the camera's axis at z = +1 (front, red) and z = -1.5 (back,
+    blue); `order` lists which of the two is instance 0."""
+    red = sg.make_type(sg.SDF_SPHERE, 0, 0, 2, 8, albedo=(1.0, 0.0, 0.0), nedf_seed=1)
+    blue = sg.make_type(sg.SDF_SPHERE, 0, 1, 2, 8, albedo=(0.0, 0.0, 1.0), nedf_seed=2)
+    T = {"front": [0.0, 0.0, 1.0], "back": [0.0, 0.0, -1.5]}
+    ty = {"front": 0, "back": 1}
+    return sg.Scene("two-colours", 33, 33, sg.f32([0, 0, 4]), sg.f32([0, 0, 0]), 40.0, sg.f32([[2, 3, 2]]),
+                    [red, blue], np.array([ty[k] for k in order], np.uint32),
+                    sg.f32(np.tile(np.eye(3).reshape(1, 9), (2, 1))), sg.f32([T[k] for k in order]),
+                    sg.f32([1, 1]))
+
+
+@pytest.mark.parametrize("order", [("front", "back"), ("back", "front")])
+def test_volume_render_composites_front_to_back_in_both_index_orders(orc, order):
+    osc = orc.OracleScene(_two_sphere_colour_scene(order))
+    centre = 16 * 33 + 16
+    rgba = orc.volume_render(osc, 128, px=np.array([centre]))[0]
+    assert np.allclose(rgba, [1.0, 0.0, 0.0, 1.0], atol=1e-12)   # the front sphere's colour only
+
+
+def test_volume_render_semi_transparent_front_lets_the_back_through(orc):
+    """A front sphere thinner than one optical depth: the back sphere's colour is attenuated by the
+    front's transmittance, whatever the index order (closed form for two constant media)."""
+    res = []
+    for order in (("front", "back"), ("back", "front")):
+        sc = _two_sphere_colour_scene(order)
+        sc.types[0].params[0] = np.float32(0.0)                 # front type: a point sphere ...
+        sc.sigma_max = 50.0
+        osc = orc.OracleScene(sc)
+        res.append(orc.volume_render(osc, 512, px=np.array([16 * 33 + 16]))[0])
+    assert np.allclose(res[0], res[1], atol=1e-12)
+    # ... whose density on the axis is 50 sigmoid(-|x|/0.01): integral over the line is
+    # 2 * 50 * 0.01 * ln 2, so the red opacity is 1 - exp(-0.693...) = 0.5 and blue gets the rest
+    a_red = 1 - math.exp(-2 * 50 * 0.01 * math.log(2.0))
+    assert abs(res[0][0] - a_red) < 2e-3
+    assert abs(res[0][2] - (1 - a_red)) < 2e-3 and abs(res[0][3] - 1) < 1e-9
