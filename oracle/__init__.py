@@ -87,7 +87,9 @@ def lib():
             l.orc_posenc.argtypes = [d, C.c_int, C.c_int, d]; l.orc_posenc.restype = C.c_int
             l.orc_nedf_features.argtypes = [d, d, C.c_double, d, d]; l.orc_nedf_features.restype = C.c_int
             l.orc_mlp.argtypes = [d, C.c_int, i, d, d, C.c_int]
+            l.orc_mlp_qmargin.argtypes = [d, C.c_int, i, d, d, C.c_int]; l.orc_mlp_qmargin.restype = C.c_double
             l.orc_round_bf16.argtypes = [C.c_double]; l.orc_round_bf16.restype = C.c_double
+            l.orc_round_margin.argtypes = [C.c_double, C.c_int]; l.orc_round_margin.restype = C.c_double
             l.orc_round_e4m3.argtypes = [C.c_double]; l.orc_round_e4m3.restype = C.c_double
             l.orc_fp8_scale.argtypes = [C.c_double]; l.orc_fp8_scale.restype = C.c_double
             l.orc_query.argtypes = [sp, op, C.c_int, d, d, d, d]; l.orc_query.restype = C.c_int
@@ -269,8 +271,23 @@ def mlp(w, dims, x, quant=QUANT_NONE):
     return y
 
 
+def mlp_qmargin(w, dims, x, quant):
+    """(y, margin): the MLP output and the row's rounding knife edge (see orc_mlp_qmargin)."""
+    w = np.ascontiguousarray(w, np.float64)
+    dims_c = (C.c_int * len(dims))(*dims)
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.empty(dims[-1])
+    m = lib().orc_mlp_qmargin(_dp(w), len(dims) - 1, dims_c, _dp(x), _dp(y), quant)
+    return y, m
+
+
 def round_bf16(x):
     return lib().orc_round_bf16(float(x))
+
+
+def round_margin(x, fmt):
+    """Distance of x to its nearest BF16 (fmt 0) / E4M3 (fmt 1) rounding boundary."""
+    return lib().orc_round_margin(float(x), int(fmt))
 
 
 def round_e4m3(x):

@@ -223,12 +223,42 @@ double orc_fp8_scale(double max_abs)
     return s;
 }
 
-void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant)
+/* Distance from v to the nearest rounding boundary of the BF16 (fmt 0) or E4M3 (fmt 1) grid: how
+ * far v may move before it rounds to another value.  Zero stays zero.  Boundaries are the
+ * midpoints between neighbouring representable values; below a binade's first value the grid is
+ * twice as fine (except below E4M3's smallest normal), hence the second candidate.  E4M3 saturates at 448, so the last boundary is 432. */
+double orc_round_margin(double v, int fmt)
+{
+    double a = fabs(v);
+    if (a == 0.0 || !isfinite(a)) return INFINITY;
+    if (fmt == 1 && a >= 448.0) return a - 432.0;
+    int e;
+    frexp(a, &e);                                   /* a in [2^(e-1), 2^e) */
+    int qe = fmt == 0 ? e - 8 : e - 1 - 3;
+    int sub = fmt == 1 && qe < -9;
+    if (sub) qe = -9;
+    double q = ldexp(1.0, qe), u = a / q;
+    double m = fabs(u - floor(u) - 0.5) * q;
+    if (!sub && !(fmt == 1 && qe == -9)) m = dmin(m, a - ldexp(1.0, e - 1) + 0.25 * q);   /* E4M3's subnormals
+                                                        keep the smallest normal binade's spacing */
+    return m;
+}
+
+/* The MLP of reading 20/21 with an optional rounding diagnostic: *qmargin (if not NULL) receives
+ * the smallest distance of any rounded value to its rounding boundary, relative to the scale that
+ * bounds a floating-point sum's error there (sum of |w a| plus |b| for a layer's output, |v| for
+ * an input feature).  A row whose margin exceeds the relative error of another implementation's
+ * sums rounds every value the same way in both. */
+static void mlp_core(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
+                     double *qmargin)
 {
     int maxd = 0;
     for (int l = 0; l <= n_layers; ++l) maxd = dims[l] > maxd ? dims[l] : maxd;
     double *a = (double *)malloc(sizeof(double) * maxd), *b = (double *)malloc(sizeof(double) * maxd);
     memcpy(a, x, sizeof(double) * dims[0]);
+    double qm = INFINITY;
+    if (quant != ORC_QUANT_NONE)
+        for (int i = 0; i < dims[0]; ++i) qm = dmin(qm, orc_round_margin(x[i], 0) / dmax(fabs(x[i]), 1e-300));
     const double *p = w;
     for (int l = 0; l < n_layers; ++l) {
         int fi = dims[l], fo = dims[l + 1];
@@ -242,7 +272,7 @@ void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, do
             s = orc_fp8_scale(m);
         }
         for (int o = 0; o < fo; ++o) {
-            double acc = 0.0;
+            double acc = 0.0, mag = 0.0;
             for (int i = 0; i < fi; ++i) {
                 double wv = W[(size_t)o * fi + i], av = a[i];
                 if (quant == ORC_QUANT_BF16) { wv = orc_round_bf16(wv); av = orc_round_bf16(av); }
@@ -252,17 +282,37 @@ void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, do
                     if (l == 0) av = orc_round_bf16(av);   /* later inputs are E4M3 already */
                 }
                 acc += wv * av;
+                mag += fabs(wv * av);
             }
             acc += bias[o];
+            mag += fabs(bias[o]);
             b[o] = (l + 1 < n_layers) ? dmax(acc, 0.0) : acc;
-            if (quant == ORC_QUANT_FP8 && l + 1 < n_layers) b[o] = orc_round_e4m3(b[o]);
+            if (quant == ORC_QUANT_FP8 && l + 1 < n_layers) {
+                qm = dmin(qm, orc_round_margin(b[o], 1) / dmax(mag, 1e-300));
+                b[o] = orc_round_e4m3(b[o]);
+            } else if (quant == ORC_QUANT_BF16 && l + 1 < n_layers) {
+                qm = dmin(qm, orc_round_margin(b[o], 0) / dmax(mag, 1e-300));
+            }
         }
         memcpy(a, b, sizeof(double) * fo);
         p += (size_t)fi * fo + fo;
     }
     memcpy(y, a, sizeof(double) * dims[n_layers]);
+    if (qmargin) *qmargin = qm;
     free(a);
     free(b);
+}
+
+void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant)
+{
+    mlp_core(w, n_layers, dims, x, y, quant, NULL);
+}
+
+double orc_mlp_qmargin(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant)
+{
+    double qm;
+    mlp_core(w, n_layers, dims, x, y, quant, &qm);
+    return qm;
 }
 
 static int nedf_dims(const orc_type *t, int *dims)

@@ -101,6 +101,12 @@ int orc_nedf_features(const double ol[3], const double dl[3], double rb, double 
 
 /* Networks */
 void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant);
+/* Distance from v to the nearest rounding boundary of BF16 (fmt 0) or E4M3 (fmt 1). */
+double orc_round_margin(double v, int fmt);
+/* orc_mlp plus the row's rounding knife edge: the smallest distance of a BF16 / E4M3-rounded value
+ * to its rounding boundary relative to the magnitude of the sum that produced it (INFINITY in the
+ * unrounded mode). */
+double orc_mlp_qmargin(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant);
 double orc_round_bf16(double x);
 double orc_round_e4m3(double x);
 double orc_fp8_scale(double max_abs);

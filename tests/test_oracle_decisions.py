@@ -266,3 +266,48 @@ def test_volume_render_semi_transparent_front_lets_the_back_through(orc):
     a_red = 1 - math.exp(-2 * 50 * 0.01 * math.log(2.0))
     assert abs(res[0][0] - a_red) < 2e-3
     assert abs(res[0][2] - (1 - a_red)) < 2e-3 and abs(res[0][3] - 1) < 1e-9
+
+
+# ------------------------------------------------------------------------------------------------
+# rounding knife edges (how far a value may move before a BF16 / E4M3 cast changes)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_round_margin_is_the_distance_to_the_next_rounding_change(orc, fmt):
+    """Against torch's own casts: moving x by 0.98 of its margin keeps the rounded value, moving it
+    by 1.02 of the margin in one of the two directions changes it."""
+    torch = pytest.importorskip("torch")
+    cast = torch.bfloat16 if fmt == 0 else torch.float8_e4m3fn
+    rng = np.random.default_rng(21 + fmt)
+    lo, hi = (-6, 6) if fmt == 0 else (-3.2, 2.6)
+    xs = rng.normal(size=3000) * 10.0 ** rng.uniform(lo, hi, 3000)
+    xs = np.concatenate([xs, [1.0, 1.5, 2.0 ** -7 * 3, 100.3]])
+    if fmt == 1:                            # torch's cast does not saturate: compare below 432
+        xs = np.concatenate([xs[np.abs(xs) < 420], [2.0 ** -9, 0.001, 300.0]])
+        # saturating convention: everything above the 416 / 448 midpoint rounds to 448
+        assert orc.round_margin(470.0, 1) == 38.0 and orc.round_margin(-448.0, 1) == 16.0
+    rnd = lambda v: torch.tensor(np.asarray(v, np.float64)).to(cast).to(torch.float64).numpy()
+    m = np.array([orc.round_margin(v, fmt) for v in xs])
+    assert np.all(m > 0)
+    assert orc.round_margin(100.0, 1) == 0.0 and orc.round_margin(1.0 + 2.0 ** -8, 0) == 0.0   # ties
+    keep = m > 1e-5 * np.abs(xs)            # torch casts doubles through float32: 2% of m must exceed its ulp
+    xs, m = xs[keep], m[keep]
+    base = rnd(xs)
+    assert np.array_equal(rnd(xs + 0.98 * m), base) and np.array_equal(rnd(xs - 0.98 * m), base)
+    moved = (rnd(xs + 1.02 * m) != base) | (rnd(xs - 1.02 * m) != base)
+    assert moved.all(), xs[~moved][:5]
+
+
+def test_mlp_qmargin_reports_the_tightest_rounded_value(orc):
+    """A one-hidden-unit network whose activation is placed at a chosen distance from a BF16
+    boundary: the row's margin is that distance over the sum's magnitude."""
+    dims = [78, 1, 2]
+    w = np.zeros(sg.mlp_param_count(dims))
+    x = np.zeros(78)
+    x[0] = 1.0                                                   # an exactly representable input
+    w[0] = 1.0                                                   # W0[0][0]
+    boundary = 1.0 + 2.0 ** -8                                   # midpoint of 1 and 1 + 2^-7
+    w[78] = boundary - 1.0 - 3e-5                                # bias: pre-activation 3e-5 below it
+    y, m = orc.mlp_qmargin(w, dims, x, orc.QUANT_BF16)
+    assert abs(m - 3e-5 / (1.0 + abs(w[78]))) < 1e-12
+    _, m_none = orc.mlp_qmargin(w, dims, x, orc.QUANT_NONE)
+    assert m_none == math.inf
