@@ -166,7 +166,7 @@ def oracle_rate(scene, nedf_weights, target_s, threads, seed=11):
     while secs < target_s and done < scene.W * scene.H:
         px = sg.pixel_subset(scene.W, scene.H, batch, seed + n)
         t0 = time.perf_counter()
-        oracle.render(osc, px=px, march_n=128, march_b=4, n_threads=threads, **FRAME_OPTS)
+        oracle.render(osc, px=px, alt=False, march_n=128, march_b=4, n_threads=threads, **FRAME_OPTS)
         secs += time.perf_counter() - t0
         done += len(px)
         n += 1
@@ -187,13 +187,13 @@ def run_reference(args):
     osc = oracle.OracleScene(sc)
     # calibrate a per-step pixel sample that takes about per_step_s on the host cores
     t0 = time.perf_counter()
-    oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, 256, 99), n_threads=threads, **FRAME_OPTS)
+    oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, 256, 99), alt=False, n_threads=threads, **FRAME_OPTS)
     n = int(max(64, 256 * per_step_s / max(time.perf_counter() - t0, 1e-3)))
     for w in range(args.warmup):
-        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 200 + w), n_threads=threads, **FRAME_OPTS)
+        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 200 + w), alt=False, n_threads=threads, **FRAME_OPTS)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 300 + k), n_threads=threads, **FRAME_OPTS)
+        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 300 + k), alt=False, n_threads=threads, **FRAME_OPTS)
     dt = time.perf_counter() - t0
     value = n * args.steps / dt
     ms_frame = 1000.0 * sc.W * sc.H / value

@@ -98,8 +98,10 @@ def lib():
             l.orc_march_depth.argtypes = [sp, C.c_int, d, d, C.c_double, C.c_double, C.c_int, C.c_int, i]
             l.orc_march_depth.restype = C.c_double
             l.orc_composite_samples.argtypes = [C.c_int, d, d, C.c_double, d]
-            l.orc_render.argtypes = [sp, op, C.c_int64, i64, d, u32, d, d, d, d, d, d, d]
-            l.orc_volume_render.argtypes = [sp, op, C.c_int, C.c_int64, i64, d]
+            l.orc_render.argtypes = [sp, op, C.c_int64, i64, d, u32, d, d, d, d, d, d, d, d, d]
+            l.orc_query_diag.argtypes = [sp, op, C.c_int, d, d, d, d, C.c_double]; l.orc_query_diag.restype = C.c_int
+            l.orc_mlp_flip.argtypes = [d, C.c_int, i, d, d, C.c_int, C.c_int, C.c_int, i, d]
+            l.orc_volume_render.argtypes = [sp, op, C.c_int, C.c_int64, i64, d, d]
             l.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]; l.orc_splitmix64.restype = C.c_uint64
             l.orc_train_rays.argtypes = [C.c_double, C.c_uint64, C.c_int64, C.c_int, d, d]
             l.orc_train_labels.argtypes = [sp, C.c_int, C.c_int, d, d, C.c_int, C.c_int, d, i]
@@ -191,8 +193,10 @@ def opts(depth_mode=DEPTH_MLP, march_n=128, march_b=4, quant=QUANT_NONE, fallbac
                    shade_resample, shade_sigma_min)
 
 
-def render(osc: OracleScene, px=None, **kw):
-    """Steps 1-3 for the pixels `px` (default: all).  Returns a dict of arrays."""
+def render(osc: OracleScene, px=None, alt=True, **kw):
+    """Steps 1-3 for the pixels `px` (default: all).  Returns a dict of arrays; with alt=True the
+    pixels near a depth decision also carry the alternative outcome (see orc_render): alt_depth,
+    alt_id, alt_rgba, alt_shadow, alt_out, has_alt."""
     s = osc.scene
     if px is None:
         px = np.arange(s.W * s.H, dtype=np.int64)
@@ -200,26 +204,37 @@ def render(osc: OracleScene, px=None, **kw):
     n = px.shape[0]
     out = dict(depth=np.empty(n), id=np.empty(n, np.uint32), gap=np.empty(n), pmargin=np.empty(n),
                rgba=np.empty((n, 4)), shadow=np.empty(n), smargin=np.empty(n), out=np.empty((n, 4)),
-               shade_smax=np.empty(n))
+               shade_smax=np.empty(n), dmargin=np.empty(n))
+    a = np.empty((n, 12)) if alt else None
     o = opts(**kw)
     lib().orc_render(osc.ptr, C.byref(o), n, px.ctypes.data_as(C.POINTER(C.c_int64)),
                      _dp(out["depth"]), out["id"].ctypes.data_as(C.POINTER(C.c_uint32)),
                      _dp(out["gap"]), _dp(out["pmargin"]), _dp(out["rgba"]), _dp(out["shadow"]),
-                     _dp(out["smargin"]), _dp(out["out"]), _dp(out["shade_smax"]))
+                     _dp(out["smargin"]), _dp(out["out"]), _dp(out["shade_smax"]), _dp(out["dmargin"]),
+                     _dp(a) if alt else C.POINTER(C.c_double)())
     out["px"] = px
+    if alt:
+        out["has_alt"] = a[:, 11] == 1.0
+        out["alt_depth"] = a[:, 0]
+        out["alt_id"] = np.where(a[:, 1] < 0, 0xFFFFFFFF, np.nan_to_num(a[:, 1])).astype(np.uint32)
+        out["alt_rgba"] = a[:, 2:6]
+        out["alt_shadow"] = a[:, 6]
+        out["alt_out"] = a[:, 7:11]
     return out
 
 
-def volume_render(osc: OracleScene, n_samples=128, px=None, n_threads=1, quant=QUANT_NONE):
+def volume_render(osc: OracleScene, n_samples=128, px=None, n_threads=1, quant=QUANT_NONE, margins=False):
+    """Plain-method colour of pixels px; with margins=True returns (rgba, vmargin)."""
     s = osc.scene
     if px is None:
         px = np.arange(s.W * s.H, dtype=np.int64)
     px = np.ascontiguousarray(px, np.int64)
     rgba = np.empty((px.shape[0], 4))
+    vm = np.empty(px.shape[0])
     o = opts(n_threads=n_threads, quant=quant)
     lib().orc_volume_render(osc.ptr, C.byref(o), n_samples, px.shape[0],
-                            px.ctypes.data_as(C.POINTER(C.c_int64)), _dp(rgba))
-    return rgba
+                            px.ctypes.data_as(C.POINTER(C.c_int64)), _dp(rgba), _dp(vm))
+    return (rgba, vm) if margins else rgba
 
 
 def sdf(kind, params, x):
@@ -281,6 +296,20 @@ def mlp_qmargin(w, dims, x, quant):
     return y, m
 
 
+def mlp_flip(w, dims, x, quant, flip_idx=-1, n_cand=0):
+    """(y, cand_idx, cand_margin): the MLP with value flip_idx rounded the other way, and the
+    n_cand values nearest to a rounding boundary (see orc_mlp_flip)."""
+    w = np.ascontiguousarray(w, np.float64)
+    dims_c = (C.c_int * len(dims))(*dims)
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.empty(dims[-1])
+    ci = np.full(max(n_cand, 1), -1, np.int32)
+    cm = np.empty(max(n_cand, 1))
+    lib().orc_mlp_flip(_dp(w), len(dims) - 1, dims_c, _dp(x), _dp(y), int(quant), int(flip_idx), int(n_cand),
+                       ci.ctypes.data_as(C.POINTER(C.c_int)), _dp(cm))
+    return y, ci[:n_cand], cm[:n_cand]
+
+
 def round_bf16(x):
     return lib().orc_round_bf16(float(x))
 
@@ -304,6 +333,15 @@ def query(osc: OracleScene, inst, o, d, **kw):
     op = opts(**kw)
     hit = lib().orc_query(osc.ptr, C.byref(op), inst, _dp(o), _dp(d), _dp(out), C.byref(mg))
     return bool(hit), out, mg.value
+
+
+def query_diag(osc: OracleScene, inst, o, d, need=0.0, **kw):
+    """(hit, out6, (margin, dmargin, dspread)) of one query (see orc_query_diag)."""
+    o = np.ascontiguousarray(o, np.float64); d = np.ascontiguousarray(d, np.float64)
+    out, dg = np.empty(6), np.empty(3)
+    op = opts(**kw)
+    hit = lib().orc_query_diag(osc.ptr, C.byref(op), inst, _dp(o), _dp(d), _dp(out), _dp(dg), float(need))
+    return bool(hit), out, tuple(dg)
 
 
 def exact_depth(kind, params, ol, dl, te, tx):

@@ -244,21 +244,57 @@ double orc_round_margin(double v, int fmt)
     return m;
 }
 
-/* The MLP of reading 20/21 with an optional rounding diagnostic: *qmargin (if not NULL) receives
- * the smallest distance of any rounded value to its rounding boundary, relative to the scale that
- * bounds a floating-point sum's error there (sum of |w a| plus |b| for a layer's output, |v| for
- * an input feature).  A row whose margin exceeds the relative error of another implementation's
- * sums rounds every value the same way in both. */
+/* Rounds v to BF16 (fmt 0) or E4M3 (fmt 1); with `flip` set, to the representable value on the
+ * other side of v's nearest rounding boundary instead (the value a slightly different sum of the
+ * same terms would have rounded to). */
+static double round_fmt(double v, int fmt, int flip)
+{
+    double q = fmt == 0 ? orc_round_bf16(v) : orc_round_e4m3(v);
+    if (!flip) return q;
+    double m = orc_round_margin(v, fmt);
+    if (!isfinite(m)) return q;
+    double step = m * (1.0 + 1e-9) + 1e-300;
+    double up = fmt == 0 ? orc_round_bf16(v + step) : orc_round_e4m3(v + step);
+    double dn = fmt == 0 ? orc_round_bf16(v - step) : orc_round_e4m3(v - step);
+    return up != q ? up : dn;
+}
+
+/* The MLP of readings 20/21 with rounding diagnostics.  Every BF16 / E4M3-rounded value has an
+ * index: the input features 0 .. dims[0]-1, then each hidden layer's outputs in order.
+ *   qmargin   (may be NULL) the row's smallest distance of a rounded value to its rounding
+ *             boundary, relative to the scale that bounds another implementation's error there
+ *             (sum of |w a| plus |b| for a layer's output, |v| for an input feature);
+ *   flip_idx  index of one value rounded to its other neighbour (-1: none);
+ *   n_cand    the n_cand values of smallest relative margin are listed in cand_idx / cand_margin
+ *             (ascending; unused entries get index -1). */
 static void mlp_core(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
-                     double *qmargin)
+                     double *qmargin, int flip_idx, int n_cand, int *cand_idx, double *cand_margin)
 {
     int maxd = 0;
     for (int l = 0; l <= n_layers; ++l) maxd = dims[l] > maxd ? dims[l] : maxd;
     double *a = (double *)malloc(sizeof(double) * maxd), *b = (double *)malloc(sizeof(double) * maxd);
-    memcpy(a, x, sizeof(double) * dims[0]);
+    for (int c = 0; c < n_cand; ++c) { cand_idx[c] = -1; cand_margin[c] = INFINITY; }
     double qm = INFINITY;
-    if (quant != ORC_QUANT_NONE)
-        for (int i = 0; i < dims[0]; ++i) qm = dmin(qm, orc_round_margin(x[i], 0) / dmax(fabs(x[i]), 1e-300));
+    int vidx = 0;
+    /* records value index vidx with relative margin r among the smallest n_cand */
+#define NOTE_MARGIN(r)                                                                     \
+    do {                                                                                   \
+        double r_ = (r);                                                                   \
+        qm = dmin(qm, r_);                                                                 \
+        if (n_cand > 0 && r_ < cand_margin[n_cand - 1]) {                                  \
+            int c_ = n_cand - 1;                                                           \
+            while (c_ > 0 && cand_margin[c_ - 1] > r_) {                                   \
+                cand_margin[c_] = cand_margin[c_ - 1]; cand_idx[c_] = cand_idx[c_ - 1]; --c_; \
+            }                                                                              \
+            cand_margin[c_] = r_; cand_idx[c_] = vidx;                                     \
+        }                                                                                  \
+    } while (0)
+    for (int i = 0; i < dims[0]; ++i, ++vidx) {
+        a[i] = x[i];
+        if (quant == ORC_QUANT_NONE) continue;
+        NOTE_MARGIN(orc_round_margin(x[i], 0) / dmax(fabs(x[i]), 1e-300));
+        a[i] = round_fmt(x[i], 0, vidx == flip_idx);
+    }
     const double *p = w;
     for (int l = 0; l < n_layers; ++l) {
         int fi = dims[l], fo = dims[l + 1];
@@ -275,28 +311,26 @@ static void mlp_core(const double *w, int n_layers, const int *dims, const doubl
             double acc = 0.0, mag = 0.0;
             for (int i = 0; i < fi; ++i) {
                 double wv = W[(size_t)o * fi + i], av = a[i];
-                if (quant == ORC_QUANT_BF16) { wv = orc_round_bf16(wv); av = orc_round_bf16(av); }
-                else if (quant == ORC_QUANT_FP8) {
-                    if (fp8_layer) wv = s * orc_round_e4m3(wv / s);
-                    else wv = orc_round_bf16(wv);
-                    if (l == 0) av = orc_round_bf16(av);   /* later inputs are E4M3 already */
-                }
+                if (quant == ORC_QUANT_BF16) wv = orc_round_bf16(wv);
+                else if (quant == ORC_QUANT_FP8) wv = fp8_layer ? s * orc_round_e4m3(wv / s) : orc_round_bf16(wv);
                 acc += wv * av;
                 mag += fabs(wv * av);
             }
             acc += bias[o];
             mag += fabs(bias[o]);
             b[o] = (l + 1 < n_layers) ? dmax(acc, 0.0) : acc;
-            if (quant == ORC_QUANT_FP8 && l + 1 < n_layers) {
-                qm = dmin(qm, orc_round_margin(b[o], 1) / dmax(mag, 1e-300));
-                b[o] = orc_round_e4m3(b[o]);
-            } else if (quant == ORC_QUANT_BF16 && l + 1 < n_layers) {
-                qm = dmin(qm, orc_round_margin(b[o], 0) / dmax(mag, 1e-300));
+            if (quant != ORC_QUANT_NONE && l + 1 < n_layers) {
+                /* hidden activations: BF16, or E4M3 in the FP8 mode (they feed E4M3 layers) */
+                int fmt = quant == ORC_QUANT_FP8 ? 1 : 0;
+                NOTE_MARGIN(orc_round_margin(b[o], fmt) / dmax(mag, 1e-300));
+                b[o] = round_fmt(b[o], fmt, vidx == flip_idx);
+                ++vidx;
             }
         }
         memcpy(a, b, sizeof(double) * fo);
         p += (size_t)fi * fo + fo;
     }
+#undef NOTE_MARGIN
     memcpy(y, a, sizeof(double) * dims[n_layers]);
     if (qmargin) *qmargin = qm;
     free(a);
@@ -305,14 +339,20 @@ static void mlp_core(const double *w, int n_layers, const int *dims, const doubl
 
 void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant)
 {
-    mlp_core(w, n_layers, dims, x, y, quant, NULL);
+    mlp_core(w, n_layers, dims, x, y, quant, NULL, -1, 0, NULL, NULL);
 }
 
 double orc_mlp_qmargin(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant)
 {
     double qm;
-    mlp_core(w, n_layers, dims, x, y, quant, &qm);
+    mlp_core(w, n_layers, dims, x, y, quant, &qm, -1, 0, NULL, NULL);
     return qm;
+}
+
+void orc_mlp_flip(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
+                  int flip_idx, int n_cand, int *cand_idx, double *cand_margin)
+{
+    mlp_core(w, n_layers, dims, x, y, quant, NULL, flip_idx, n_cand, cand_idx, cand_margin);
 }
 
 static int nedf_dims(const orc_type *t, int *dims)
@@ -615,22 +655,89 @@ double orc_exact_depth(int kind, const double *p, const double ol[3], const doub
 
 /* Plain method (our reading of the label depth): N uniform steps over [te, tx], the first step
  * whose density reaches sigma_max/2 after one below it, then B bisection steps; midpoint. */
-double orc_march_depth(const orc_scene *sc, int type, const double ol[3], const double dl[3],
-                       double te, double tx, int n, int b, int *hit)
+/* Depth-decision diagnostics of one query (diagnostic only; the depth itself does not use them).
+ * Every inside/outside test at a point x = ol + t dl has a margin, |sdf(x)| (the distance the
+ * point may move before the test changes, the SDFs being distance bounds) less the shift `u`
+ * another implementation's inputs may carry, relative to the coordinate magnitude |ol| + |t| + rb
+ * that bounds its rounding error; and a consequence, how far the depth can move if the test goes
+ * the other way: half the bracket for a bisection step, unbounded for the plain method's samples
+ * and the refinement window's ends (a crossing found elsewhere or not at all, an outlier). */
+#define ORC_DEC_CAP 1e-4      /* tests with a larger margin are never knife edges: not recorded */
+#define ORC_DEC_MAX 32
+typedef struct {
+    int count;                  /* tests taken so far (a test's index) */
+    int flip;                   /* index of a test to take the other way (-1: none) */
+    int n;                      /* recorded tests with a margin below ORC_DEC_CAP */
+    double m[ORC_DEC_MAX], c[ORC_DEC_MAX];
+    int idx[ORC_DEC_MAX];
+} dec_diag;
+
+static void dec_init(dec_diag *g, int flip) { g->count = 0; g->flip = flip; g->n = 0; }
+
+/* One inside/outside test at x = ol + t dl (the half-density level, reading 9) with margin
+ * bookkeeping; taken the other way when it is the test to flip. */
+static int decide(dec_diag *g, const orc_scene *sc, int type, const double ol[3], double t, const double x[3],
+                  double u, double consequence)
+{
+    int in = inside_solid(sc, type, x);
+    if (!g) return in;
+    const orc_type *ty = &sc->types[type];
+    double mg = dmax(fabs(orc_sdf(ty->kind, ty->params, x)) - u, 0.0) / (len3(ol) + fabs(t) + ty->rb);
+    if (mg < ORC_DEC_CAP) {
+        int slot = g->n;
+        if (g->n == ORC_DEC_MAX) {              /* full: replace the largest margin if larger */
+            slot = 0;
+            for (int i = 1; i < ORC_DEC_MAX; ++i) if (g->m[i] > g->m[slot]) slot = i;
+            if (g->m[slot] <= mg) slot = -1;
+        } else {
+            ++g->n;
+        }
+        if (slot >= 0) { g->m[slot] = mg; g->c[slot] = consequence; g->idx[slot] = g->count; }
+    }
+    if (g->count == g->flip) in = !in;
+    ++g->count;
+    return in;
+}
+
+/* The smallest margin among the recorded tests whose consequence reaches `need` (local length). */
+static double dec_margin(const dec_diag *g, double need)
+{
+    double r = INFINITY;
+    for (int i = 0; i < g->n; ++i)
+        if (g->c[i] >= need) r = dmin(r, g->m[i]);
+    return r;
+}
+
+/* The two most critical tests of a pixel, each named by where it ran: stage 1 = the Step-1 query
+ * of instance `inst`, stage 2 = the shadow query of `inst` for light `light`; idx = its index. */
+typedef struct { double m; int stage, light, inst, idx; } crit_test;
+
+static void crit_feed(crit_test cr[2], const dec_diag *g, double need, int stage, int light, int inst)
+{
+    for (int i = 0; i < g->n; ++i) {
+        if (!(g->c[i] >= need)) continue;
+        crit_test t = {g->m[i], stage, light, inst, g->idx[i]};
+        if (t.m < cr[0].m) { cr[1] = cr[0]; cr[0] = t; }
+        else if (t.m < cr[1].m) cr[1] = t;
+    }
+}
+
+static double march_core(const orc_scene *sc, int type, const double ol[3], const double dl[3], double te,
+                         double tx, int n, int b, int *hit, dec_diag *dg)
 {
     double x[3], prev_t = te;
     for (int c = 0; c < 3; ++c) x[c] = ol[c] + te * dl[c];
-    int prev_in = inside_solid(sc, type, x);
+    int prev_in = decide(dg, sc, type, ol, te, x, 0.0, INFINITY);
     for (int k = 1; k <= n; ++k) {
         double t = te + (tx - te) * k / n;
         for (int c = 0; c < 3; ++c) x[c] = ol[c] + t * dl[c];
-        int in = inside_solid(sc, type, x);
+        int in = decide(dg, sc, type, ol, t, x, 0.0, INFINITY);
         if (in && !prev_in) {
             double lo = prev_t, hi = t;
             for (int it = 0; it < b; ++it) {
                 double mid = 0.5 * (lo + hi);
                 for (int c = 0; c < 3; ++c) x[c] = ol[c] + mid * dl[c];
-                if (inside_solid(sc, type, x)) hi = mid; else lo = mid;
+                if (decide(dg, sc, type, ol, mid, x, 0.0, 0.5 * (hi - lo))) hi = mid; else lo = mid;
             }
             *hit = 1;
             return 0.5 * (lo + hi);
@@ -642,32 +749,66 @@ double orc_march_depth(const orc_scene *sc, int type, const double ol[3], const 
     return INFINITY;
 }
 
-/* One (ray, instance) query of Step 1 / Step 3.  World ray (o, d) with |d| = 1.
- * Returns 1 on hit; out6 = {D_local, m, a, te, tx, tperp}; *margin = distance of this query's
- * discrete decisions from their thresholds (cull discriminant, hit logit, D > 0, fallback). */
-int orc_query(const orc_scene *sc, const orc_opts *op, int inst, const double o[3], const double d[3],
-              double out6[6], double *margin)
+double orc_march_depth(const orc_scene *sc, int type, const double ol[3], const double dl[3],
+                       double te, double tx, int n, int b, int *hit)
+{
+    return march_core(sc, type, ol, dl, te, tx, n, b, hit, NULL);
+}
+
+/* Network-rounding spread of a regression NeDF row in the BF16 / E4M3 modes: the largest change of
+ * (m, a) when one of its ORC_FLIP_CAND values nearest to a rounding boundary (relative margin below
+ * ORC_FLIP_MARGIN, i.e. within reach of FP32 summation error) rounds the other way. */
+#define ORC_FLIP_CAND 6
+#define ORC_FLIP_MARGIN 1e-5
+static void nedf_spread(const orc_type *t, const int *dims, int nl, const double *feat, const double y[2],
+                        int quant, double spread[2])
+{
+    spread[0] = spread[1] = 0.0;
+    if (quant == ORC_QUANT_NONE || t->nedf_arch == ORC_ARCH_CLASSIFIER) return;
+    int ci[ORC_FLIP_CAND];
+    double cm[ORC_FLIP_CAND], yf[2];
+    mlp_core(t->nedf_w, nl, dims, feat, yf, quant, NULL, -1, ORC_FLIP_CAND, ci, cm);
+    for (int c = 0; c < ORC_FLIP_CAND; ++c) {
+        if (ci[c] < 0 || !(cm[c] < ORC_FLIP_MARGIN)) break;
+        mlp_core(t->nedf_w, nl, dims, feat, yf, quant, NULL, ci[c], 0, NULL, NULL);
+        spread[0] = dmax(spread[0], fabs(yf[0] - y[0]));
+        spread[1] = dmax(spread[1], fabs(yf[1] - y[1]));
+    }
+}
+
+/* One (ray, instance) query of Step 1 / Step 3 with its knife-edge diagnostics:
+ *   *margin   distance of the query's discrete decisions from their thresholds (cull
+ *             discriminant, bound exit, hit logit, D > 0, fallback confidence, the depth check's
+ *             window ends), each reduced by the network-rounding spread it can move by;
+ *   *dg       the depth-decision diagnostics (dec_diag) of the plain method's tests and of the
+ *             refinement (none when the depth comes from the network alone);
+ *   *dspread  the local depth shift a single network-rounding flip can cause (rb times the
+ *             spread of m; 0 for depths from the plain method). */
+static int query_ex(const orc_scene *sc, const orc_opts *op, int inst, const double o[3], const double d[3],
+                    double out6[6], double *margin, dec_diag *dg, int flip, double *dspread)
 {
     const orc_type *t = &sc->types[sc->inst_type[inst]];
+    const int type = sc->inst_type[inst];
     double ol[3], dl[3], bd[4], feat[ORC_CLS_IN];
     orc_to_local(sc, inst, o, d, ol, dl);
     int kept = t->nedf_arch == ORC_ARCH_CLASSIFIER ? orc_cls_features(ol, dl, t->rb, feat, bd)
                                                    : orc_nedf_features(ol, dl, t->rb, feat, bd);
-    double mg = fabs(bd[3]) / (t->rb * t->rb);
+    double mg = fabs(bd[3]) / (t->rb * t->rb), dsp = 0.0;
+    dec_init(dg, flip);
     if (kept) mg = dmin(mg, fabs(bd[1]) / t->rb);
     out6[0] = INFINITY; out6[1] = out6[2] = 0.0;
     out6[3] = bd[0]; out6[4] = bd[1]; out6[5] = bd[2];
-    if (!kept) { *margin = mg; return 0; }
+    if (!kept) { *margin = mg; *dspread = dsp; return 0; }
     int hit = 0;
     double Dl = INFINITY;
     if (op->depth_mode == ORC_DEPTH_EXACT) {
         Dl = orc_exact_depth(t->kind, t->params, ol, dl, bd[0], bd[1], &hit);
     } else if (op->depth_mode == ORC_DEPTH_MARCH) {
-        Dl = orc_march_depth(sc, sc->inst_type[inst], ol, dl, bd[0], bd[1], op->march_n, op->march_b, &hit);
+        Dl = march_core(sc, type, ol, dl, bd[0], bd[1], op->march_n, op->march_b, &hit, dg);
     } else {
         /* Eq. 1: F_Phi(r) -> (mu, alpha); mu = l * m with l = rb (reading: the mu range [-l, l]
          * is the bound sphere's).  Eq. 2: D = |o - p_perp| - mu with the signed t_perp. */
-        double y[2];
+        double y[2], spread[2] = {0.0, 0.0};
         if (t->nedf_arch == ORC_ARCH_CLASSIFIER) {
             /* Eq. 3-4: the two-level classifier's argmax bins give m = mu / l */
             double logits[ORC_CLS_OUT];
@@ -677,18 +818,21 @@ int orc_query(const orc_scene *sc, const orc_opts *op, int inst, const double o[
         } else {
             int dims[64], nl = nedf_dims(t, dims);
             orc_mlp(t->nedf_w, nl, dims, feat, y, op->quant);
+            nedf_spread(t, dims, nl, feat, y, op->quant, spread);
         }
         out6[1] = y[0];
         out6[2] = y[1];
         Dl = bd[2] - t->rb * y[0];
+        dsp = t->rb * spread[0];
         hit = (y[1] > 0.0) && (Dl > 0.0);
-        mg = dmin(mg, dmin(fabs(y[1]), fabs(Dl) / t->rb));
+        mg = dmin(mg, dmin(fabs(y[1]) - spread[1], (fabs(Dl) - dsp) / t->rb));
         /* Low-confidence pairs are re-answered by the plain method. */
         int march = 0;
         if (op->fallback_conf > 0.0) {
             double pr = 1.0 / (1.0 + exp(-y[1]));
             double conf = dmax(pr, 1.0 - pr);
-            mg = dmin(mg, fabs(conf - op->fallback_conf));
+            /* d conf / d a is at most 1/4 */
+            mg = dmin(mg, fabs(conf - op->fallback_conf) - 0.25 * spread[1]);
             march = conf < op->fallback_conf;
         }
         /* Depth check of a NeDF hit (Section "Deferred Shading": the density at the predicted
@@ -698,29 +842,49 @@ int orc_query(const orc_scene *sc, const orc_opts *op, int inst, const double o[
         if (!march && hit && op->refine_steps > 0) {
             double lo = Dl - sc->shade_half, hi = Dl + sc->shade_half, x[3];
             for (int c = 0; c < 3; ++c) x[c] = ol[c] + lo * dl[c];
-            int in_lo = inside_solid(sc, sc->inst_type[inst], x);
-            mg = dmin(mg, fabs(orc_sdf(t->kind, t->params, x)));
+            int in_lo = decide(dg, sc, type, ol, lo, x, dsp, INFINITY);
+            mg = dmin(mg, fabs(orc_sdf(t->kind, t->params, x)) - dsp);
             for (int c = 0; c < 3; ++c) x[c] = ol[c] + hi * dl[c];
-            int in_hi = inside_solid(sc, sc->inst_type[inst], x);
-            mg = dmin(mg, fabs(orc_sdf(t->kind, t->params, x)));
+            int in_hi = decide(dg, sc, type, ol, hi, x, dsp, INFINITY);
+            mg = dmin(mg, fabs(orc_sdf(t->kind, t->params, x)) - dsp);
             if (!in_lo && in_hi) {
                 for (int it = 0; it < op->refine_steps; ++it) {
                     double mid = 0.5 * (lo + hi);
                     for (int c = 0; c < 3; ++c) x[c] = ol[c] + mid * dl[c];
-                    if (inside_solid(sc, sc->inst_type[inst], x)) hi = mid; else lo = mid;
+                    if (decide(dg, sc, type, ol, mid, x, dsp, 0.5 * (hi - lo))) hi = mid; else lo = mid;
                 }
                 Dl = 0.5 * (lo + hi);
                 hit = Dl > 0.0;
-                mg = dmin(mg, fabs(Dl) / t->rb);
+                mg = dmin(mg, (fabs(Dl) - dsp) / t->rb);
             } else if (op->outlier_resample) {
                 march = 1;
             }
         }
-        if (march)
-            Dl = orc_march_depth(sc, sc->inst_type[inst], ol, dl, bd[0], bd[1], op->march_n, op->march_b, &hit);
+        if (march) {
+            Dl = march_core(sc, type, ol, dl, bd[0], bd[1], op->march_n, op->march_b, &hit, dg);
+            dsp = 0.0;
+        }
     }
     out6[0] = Dl;
     *margin = mg;
+    *dspread = dsp;
+    return hit;
+}
+
+int orc_query(const orc_scene *sc, const orc_opts *op, int inst, const double o[3], const double d[3],
+              double out6[6], double *margin)
+{
+    double dsp;
+    dec_diag dg;
+    return query_ex(sc, op, inst, o, d, out6, margin, &dg, -1, &dsp);
+}
+
+int orc_query_diag(const orc_scene *sc, const orc_opts *op, int inst, const double o[3], const double d[3],
+                   double out6[6], double diag[3], double need)
+{
+    dec_diag dg;
+    int hit = query_ex(sc, op, inst, o, d, out6, &diag[0], &dg, -1, &diag[2]);
+    diag[1] = dec_margin(&dg, need);
     return hit;
 }
 
@@ -780,7 +944,8 @@ static double shade_pixel(const orc_scene *sc, const orc_opts *op, const double 
 
 /* The plain method's colour of one pixel (defined with the volume renderer below). */
 typedef struct { double te_world; int inst; } vr_pair;
-static void vr_pixel(const orc_scene *sc, const orc_opts *op, int ns, int64_t p, vr_pair *pairs, double rgba[4]);
+static void vr_pixel(const orc_scene *sc, const orc_opts *op, int ns, int64_t p, vr_pair *pairs, double rgba[4],
+                     double *vmargin);
 
 /* ------------------------------------------------------------------------------------------ */
 /* Algorithm 1 (Steps 1-2) and Algorithm 2 (Step 3) for one pixel                               */
@@ -790,28 +955,53 @@ typedef struct {
     const orc_opts *op;
     const int64_t *px;
     int64_t begin, end;
-    double *depth, *gap, *pmargin, *rgba, *shadow, *smargin, *out, *shade_smax;
+    double *depth, *gap, *pmargin, *rgba, *shadow, *smargin, *out, *shade_smax, *dmargin;
     uint32_t *id;
+    double *alt;                 /* per pixel: depth, id (as double), rgba[4], shadow, out[4] */
 } render_job;
 
-static void render_one(const render_job *jb, int64_t k)
+#define ORC_ALT_MARGIN 1e-6      /* pixels whose most critical depth test is closer get an alternative */
+
+typedef struct {
+    double depth, gap, pm, sm, smax, rgba[4], S;
+    uint32_t id;
+} pixel_result;
+
+/* Steps 1-3 for pixel p.  `fl` names one depth test to take the other way (stage 0: none);
+ * cr[2] receives the pixel's two most critical depth tests (see render_one). */
+static void render_pixel(const orc_scene *sc, const orc_opts *op, int64_t p, const crit_test *fl,
+                         pixel_result *r, crit_test cr[2])
 {
-    const orc_scene *sc = jb->sc;
-    const orc_opts *op = jb->op;
-    int64_t p = jb->px[k];
     int i = (int)(p % sc->W), j = (int)(p / sc->W);
-    double o[3], d[3], q[6], mg, best = INFINITY, second = INFINITY, pm = INFINITY;
+    double o[3], d[3], q[6], mg, dsp, best = INFINITY, second = INFINITY, pm = INFINITY;
+    double u_best = 0.0, u_second = 0.0;
     uint32_t bid = 0xFFFFFFFFu;
+    dec_diag dg;
+    cr[0].m = cr[1].m = INFINITY;
+    cr[0].stage = cr[1].stage = 0;
     orc_camera_ray(sc, i, j, o, d);
     /* STEP 1: clear to infinity; visit models in id order; strict '<' keeps the lowest id on ties. */
+    const int ni = sc->n_inst > 0 ? sc->n_inst : 1;
+    double *Dq = (double *)malloc(sizeof(double) * ni);
+    dec_diag *dq = (dec_diag *)malloc(sizeof(dec_diag) * ni);
     for (int m = 0; m < sc->n_inst; ++m) {
-        int hit = orc_query(sc, op, m, o, d, q, &mg);
+        int flip = (fl->stage == 1 && fl->inst == m) ? fl->idx : -1;
+        int hit = query_ex(sc, op, m, o, d, q, &mg, &dq[m], flip, &dsp);
         pm = dmin(pm, mg);
-        if (!hit) continue;
-        double D = sc->inst_s[m] * q[0];
-        if (D < best) { second = best; best = D; bid = (uint32_t)m; }
-        else if (D < second) second = D;
+        Dq[m] = hit ? sc->inst_s[m] * q[0] : INFINITY;
+        if (!hit) { crit_feed(cr, &dq[m], INFINITY, 1, 0, m); continue; }   /* could it become a hit? */
+        double D = Dq[m], u = sc->inst_s[m] * dsp;
+        if (D < best) { second = best; u_second = u_best; best = D; u_best = u; bid = (uint32_t)m; }
+        else if (D < second) { second = D; u_second = u; }
     }
+    /* Depth tests that can change this pixel: every one of the winner's (its depth feeds Steps 2
+     * and 3), and those of each other hit whose consequence reaches the winner. */
+    for (int m = 0; m < sc->n_inst; ++m) {
+        if (!isfinite(Dq[m])) continue;
+        crit_feed(cr, &dq[m], (uint32_t)m == bid ? 0.0 : (Dq[m] - best) / sc->inst_s[m], 1, 0, m);
+    }
+    free(Dq);
+    free(dq);
     double rgba[4] = {0, 0, 0, 0}, S = 1.0, sm = INFINITY, smax = NAN;
     if (bid != 0xFFFFFFFFu) {
         /* STEP 2: shade with the winning model's radiance field only. */
@@ -820,7 +1010,7 @@ static void render_one(const render_job *jb, int64_t k)
          * pixel's colour then comes from the primary volume rendering of every model. */
         if (op->shade_resample > 0 && smax < op->shade_sigma_min) {
             vr_pair *buf = (vr_pair *)malloc(sizeof(vr_pair) * (sc->n_inst > 0 ? sc->n_inst : 1));
-            vr_pixel(sc, op, op->shade_resample, p, buf, rgba);
+            vr_pixel(sc, op, op->shade_resample, p, buf, rgba, NULL);
             free(buf);
         }
         /* STEP 3: x on the surface, shadow ray from each light towards x; an occluder hit
@@ -847,33 +1037,81 @@ static void render_one(const render_job *jb, int64_t k)
             double ell = len3(v), dir[3] = {v[0] / ell, v[1] / ell, v[2] / ell};
             int occluded = 0;
             for (int m = 0; m < sc->n_inst; ++m) {
-                int hit = orc_query(sc, op, m, L, dir, q, &mg);
+                int flip = (fl->stage == 2 && fl->light == l && fl->inst == m) ? fl->idx : -1;
+                int hit = query_ex(sc, op, m, L, dir, q, &mg, &dg, flip, &dsp);
                 double s = sc->inst_s[m];
                 if (!(q[3] <= q[4]) || q[4] < 0.0) { sm = dmin(sm, mg); continue; } /* culled */
                 /* Reading: only bounds the shadow segment enters before x can occlude x. */
                 sm = dmin(sm, fabs(q[3] * s - ell));
                 if (!(q[3] * s < ell)) continue;
                 sm = dmin(sm, mg);
-                if (!hit) continue;
+                if (!hit) { crit_feed(cr, &dg, INFINITY, 2, l, m); continue; }
                 double Dk = s * q[0];
-                sm = dmin(sm, fabs(Dk + sc->eps - ell));
+                sm = dmin(sm, fabs(Dk + sc->eps - ell) - s * dsp);
+                /* a depth test matters here only if its consequence can cross the shadow test */
+                crit_feed(cr, &dg, fabs(Dk + sc->eps - ell) / s, 2, l, m);
                 if (Dk + sc->eps < ell) occluded = 1;
             }
             acc += occluded ? sc->beta : 1.0;
         }
         S = acc / sc->n_lights;
     }
-    jb->depth[k] = best;
-    jb->id[k] = bid;
-    if (jb->gap) jb->gap[k] = (bid != 0xFFFFFFFFu) ? second - best : INFINITY;
-    if (jb->pmargin) jb->pmargin[k] = pm;
-    if (jb->rgba) for (int c = 0; c < 4; ++c) jb->rgba[4 * k + c] = rgba[c];
-    if (jb->shadow) jb->shadow[k] = S;
-    if (jb->smargin) jb->smargin[k] = sm;
-    if (jb->shade_smax) jb->shade_smax[k] = smax;
+    r->depth = best;
+    r->id = bid;
+    /* the gap less the depth shift single network-rounding flips can cause on either side */
+    r->gap = (bid != 0xFFFFFFFFu) ? second - best - u_best - u_second : INFINITY;
+    r->pm = pm;
+    r->sm = sm;
+    r->smax = smax;
+    for (int c = 0; c < 4; ++c) r->rgba[c] = rgba[c];
+    r->S = S;
+}
+
+/* Pixel k of the job.  dmargin is the margin of its most critical depth test.  When that is below
+ * ORC_ALT_MARGIN the pixel is rendered a second time with that one test taken the other way (what
+ * an implementation whose coordinates differ by rounding may do) into `alt`, and dmargin becomes
+ * the margin of the second most critical test: the alternative covers the first. */
+static void render_one(const render_job *jb, int64_t k)
+{
+    const orc_scene *sc = jb->sc;
+    const orc_opts *op = jb->op;
+    const crit_test none = {INFINITY, 0, 0, 0, -1};
+    crit_test cr[2], cr2[2];
+    pixel_result r, ra;
+    render_pixel(sc, op, jb->px[k], &none, &r, cr);
+    double dm = cr[0].m;
+    int has_alt = jb->alt && cr[0].m < ORC_ALT_MARGIN;
+    if (has_alt) {
+        render_pixel(sc, op, jb->px[k], &cr[0], &ra, cr2);
+        dm = cr[1].m;
+    }
+    jb->depth[k] = r.depth;
+    jb->id[k] = r.id;
+    if (jb->gap) jb->gap[k] = r.gap;
+    if (jb->pmargin) jb->pmargin[k] = r.pm;
+    if (jb->dmargin) jb->dmargin[k] = dm;
+    if (jb->rgba) for (int c = 0; c < 4; ++c) jb->rgba[4 * k + c] = r.rgba[c];
+    if (jb->shadow) jb->shadow[k] = r.S;
+    if (jb->smargin) jb->smargin[k] = r.sm;
+    if (jb->shade_smax) jb->shade_smax[k] = r.smax;
     if (jb->out) {
-        for (int c = 0; c < 3; ++c) jb->out[4 * k + c] = rgba[c] * S;
-        jb->out[4 * k + 3] = rgba[3];
+        for (int c = 0; c < 3; ++c) jb->out[4 * k + c] = r.rgba[c] * r.S;
+        jb->out[4 * k + 3] = r.rgba[3];
+    }
+    if (jb->alt) {
+        double *a = jb->alt + 12 * k;
+        if (has_alt) {
+            a[0] = ra.depth;
+            a[1] = ra.id == 0xFFFFFFFFu ? -1.0 : (double)ra.id;
+            for (int c = 0; c < 4; ++c) a[2 + c] = ra.rgba[c];
+            a[6] = ra.S;
+            for (int c = 0; c < 3; ++c) a[7 + c] = ra.rgba[c] * ra.S;
+            a[10] = ra.rgba[3];
+            a[11] = 1.0;
+        } else {
+            for (int c = 0; c < 12; ++c) a[c] = NAN;
+            a[11] = 0.0;
+        }
     }
 }
 
@@ -886,7 +1124,7 @@ static void *render_worker(void *arg)
 
 int orc_render(const orc_scene *sc, const orc_opts *op, int64_t n_px, const int64_t *px, double *depth,
                uint32_t *id, double *gap, double *pmargin, double *rgba, double *shadow, double *smargin,
-               double *out, double *shade_smax)
+               double *out, double *shade_smax, double *dmargin, double *alt)
 {
     int nt = op->n_threads > 1 ? op->n_threads : 1;
     if (nt > 256) nt = 256;
@@ -894,7 +1132,7 @@ int orc_render(const orc_scene *sc, const orc_opts *op, int64_t n_px, const int6
     pthread_t th[256];
     for (int t = 0; t < nt; ++t) {
         render_job jb = {sc, op, px, n_px * t / nt, n_px * (t + 1) / nt, depth, gap, pmargin, rgba,
-                         shadow, smargin, out, shade_smax, id};
+                         shadow, smargin, out, shade_smax, dmargin, id, alt};
         jobs[t] = jb;
     }
     if (nt == 1) { render_worker(&jobs[0]); return 0; }
@@ -915,24 +1153,31 @@ static int cmp_pair(const void *a, const void *b)
 }
 
 typedef struct {
-    const orc_scene *sc; const orc_opts *op; int ns; const int64_t *px; int64_t begin, end; double *rgba;
+    const orc_scene *sc; const orc_opts *op; int ns; const int64_t *px; int64_t begin, end; double *rgba, *vmargin;
 } vr_job;
 
 /* Pixel p: its (ray, model) pairs that meet the bounds, front to back by (entry distance, id),
- * each volume rendered with ns midpoint samples over its chord. */
-static void vr_pixel(const orc_scene *sc, const orc_opts *op, int ns, int64_t p, vr_pair *pairs, double rgba[4])
+ * each volume rendered with ns midpoint samples over its chord.  *vmargin (may be NULL) receives the
+ * distance of its discrete decisions from their thresholds: each bound's cull discriminant over
+ * rb^2 and the entry-distance differences that order the pairs (diagnostic only). */
+static void vr_pixel(const orc_scene *sc, const orc_opts *op, int ns, int64_t p, vr_pair *pairs, double rgba[4],
+                     double *vmargin)
 {
-    double o[3], d[3], ol[3], dl[3], bd[4];
+    double o[3], d[3], ol[3], dl[3], bd[4], vm = INFINITY;
     orc_camera_ray(sc, (int)(p % sc->W), (int)(p / sc->W), o, d);
     int np = 0;
     for (int m = 0; m < sc->n_inst; ++m) {
         orc_to_local(sc, m, o, d, ol, dl);
-        if (!orc_bound(ol, dl, sc->types[sc->inst_type[m]].rb, bd)) continue;
+        double rb = sc->types[sc->inst_type[m]].rb;
+        int kept = orc_bound(ol, dl, rb, bd);
+        vm = dmin(vm, fabs(bd[3]) / (rb * rb));
+        if (!kept) continue;
         pairs[np].te_world = bd[0] * sc->inst_s[m];
         pairs[np].inst = m;
         ++np;
     }
     qsort(pairs, np, sizeof(vr_pair), cmp_pair);
+    for (int q = 1; q < np; ++q) vm = dmin(vm, pairs[q].te_world - pairs[q - 1].te_world);
     double T = 1.0, C[3] = {0, 0, 0};
     for (int q = 0; q < np; ++q) {
         int m = pairs[q].inst;
@@ -952,6 +1197,7 @@ static void vr_pixel(const orc_scene *sc, const orc_opts *op, int ns, int64_t p,
     }
     for (int c = 0; c < 3; ++c) rgba[c] = C[c];
     rgba[3] = 1.0 - T;
+    if (vmargin) *vmargin = vm;
 }
 
 static void *vr_worker(void *arg)
@@ -959,20 +1205,21 @@ static void *vr_worker(void *arg)
     const vr_job *jb = (const vr_job *)arg;
     const orc_scene *sc = jb->sc;
     vr_pair *pairs = (vr_pair *)malloc(sizeof(vr_pair) * (sc->n_inst > 0 ? sc->n_inst : 1));
-    for (int64_t k = jb->begin; k < jb->end; ++k) vr_pixel(sc, jb->op, jb->ns, jb->px[k], pairs, jb->rgba + 4 * k);
+    for (int64_t k = jb->begin; k < jb->end; ++k)
+        vr_pixel(sc, jb->op, jb->ns, jb->px[k], pairs, jb->rgba + 4 * k, jb->vmargin ? jb->vmargin + k : NULL);
     free(pairs);
     return NULL;
 }
 
 int orc_volume_render(const orc_scene *sc, const orc_opts *op, int n_samples, int64_t n_px,
-                      const int64_t *px, double *rgba)
+                      const int64_t *px, double *rgba, double *vmargin)
 {
     int nt = op->n_threads > 1 ? op->n_threads : 1;
     if (nt > 256) nt = 256;
     vr_job jobs[256];
     pthread_t th[256];
     for (int t = 0; t < nt; ++t) {
-        vr_job jb = {sc, op, n_samples, px, n_px * t / nt, n_px * (t + 1) / nt, rgba};
+        vr_job jb = {sc, op, n_samples, px, n_px * t / nt, n_px * (t + 1) / nt, rgba, vmargin};
         jobs[t] = jb;
     }
     if (nt == 1) { vr_worker(&jobs[0]); return 0; }

@@ -107,6 +107,11 @@ double orc_round_margin(double v, int fmt);
  * to its rounding boundary relative to the magnitude of the sum that produced it (INFINITY in the
  * unrounded mode). */
 double orc_mlp_qmargin(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant);
+/* orc_mlp with value flip_idx (inputs first, then each hidden layer's outputs; -1 none) rounded to
+ * its other neighbour; the n_cand values nearest to a rounding boundary (relative margin,
+ * ascending) are listed in cand_idx / cand_margin. */
+void orc_mlp_flip(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
+                  int flip_idx, int n_cand, int *cand_idx, double *cand_margin);
 double orc_round_bf16(double x);
 double orc_round_e4m3(double x);
 double orc_fp8_scale(double max_abs);
@@ -124,6 +129,15 @@ double orc_cls_loss_grad(const double *w, int n, const double *x, const double *
 /* One (ray, instance) query: returns 1 on hit; out6 = {Dl, m, a, te, tx, tperp} */
 int orc_query(const orc_scene *sc, const orc_opts *op, int inst, const double o[3],
               const double d[3], double out6[6], double *margin);
+/* orc_query with its knife-edge diagnostics: diag = {margin, dmargin, dspread}.  dmargin is the
+ * smallest margin of the plain method's and the refinement's inside tests whose consequence (how
+ * far the depth moves if the test goes the other way: half the bracket for a bisection step,
+ * unbounded otherwise) is at least `need` (local length); a test's margin is |sdf| at its point,
+ * less the network-rounding depth shift, over |o_local| + |t| + rb (INFINITY when no such test
+ * ran).  dspread is the local depth shift a single BF16 / E4M3 rounding flip of the network can
+ * cause. */
+int orc_query_diag(const orc_scene *sc, const orc_opts *op, int inst, const double o[3], const double d[3],
+                   double out6[6], double diag[3], double need);
 double orc_exact_depth(int kind, const double *params, const double ol[3], const double dl[3],
                        double te, double tx, int *hit);
 double orc_march_depth(const orc_scene *sc, int type, const double ol[3], const double dl[3],
@@ -133,14 +147,29 @@ double orc_march_depth(const orc_scene *sc, int type, const double ol[3], const 
 void orc_composite_samples(int n, const double *sigma, const double *rgb, double world_delta,
                            double rgba[4]);
 
-/* Steps 1-3 of Algorithm 1 / Algorithm 2 for a list of pixels. */
+/* Steps 1-3 of Algorithm 1 / Algorithm 2 for a list of pixels.  Besides the buffers, per pixel:
+ * gap      distance from the nearest hit to the next one, less the depth shift that single
+ *          network-rounding flips can cause on either (BF16 / E4M3 modes);
+ * pmargin  smallest distance of a Step-1 decision (cull, hit logit, D > 0, confidence, depth-check
+ *          window) from its threshold;
+ * smargin  the same for the shadow tests of Step 3;
+ * dmargin  relative margin (see orc_query_diag) of the most critical depth test (the plain
+ *          method's and the refinement's inside tests) among those that can change the pixel:
+ *          all of the winner's, those of another hit or a shadow query whose consequence reaches
+ *          the winner or the shadow test, and the unbounded ones of misses.  When `alt` is given
+ *          and that margin is below 1e-6, the pixel is rendered again with that test taken the
+ *          other way into alt[12 k ..] = {depth, id (-1: none), rgba[4], shadow, out[4], 1}
+ *          (NaN and 0 otherwise), and dmargin is the second most critical test's margin. */
 int orc_render(const orc_scene *sc, const orc_opts *op, int64_t n_px, const int64_t *px,
                double *depth, uint32_t *id, double *gap, double *pmargin, double *rgba,
-               double *shadow, double *smargin, double *out, double *shade_smax);
+               double *shadow, double *smargin, double *out, double *shade_smax, double *dmargin,
+               double *alt);
 
-/* Plain method: dense front-to-back volume rendering with n samples per (ray, instance). */
+/* Plain method: dense front-to-back volume rendering with n samples per (ray, instance).
+ * vmargin (may be NULL): per pixel, the smallest cull-discriminant / rb^2 and entry-distance
+ * difference between consecutive pairs (the decisions a rounding change could flip). */
 int orc_volume_render(const orc_scene *sc, const orc_opts *op, int n_samples, int64_t n_px,
-                      const int64_t *px, double *rgba);
+                      const int64_t *px, double *rgba, double *vmargin);
 
 /* Learned part */
 uint64_t orc_splitmix64(uint64_t seed, uint64_t index);

@@ -326,11 +326,13 @@ def thousand_scene(W: int = 1024, H: int = 1024, nerf: bool = True) -> Scene:
     return _many_scene("1024inst-1024", [SDF_SPHERE, SDF_TORUS, SDF_BOX], 1024, 3, W, H, 20.0, 4, nerf)
 
 
-def stress_scene(W: int = 2048, H: int = 2048, nerf: bool = True) -> Scene:
-    """8 types x 512 instances in [-40,40]^3, seed 4, 2048^2, 8 lights."""
+def stress_scene(W: int = 2048, H: int = 2048, nerf: bool = True, n_inst: int = 4096) -> Scene:
+    """8 types x 512 instances in [-40,40]^3, seed 4, 2048^2, 8 lights.  A smaller n_inst keeps the
+    instance density: the cube's half extent shrinks as the cube root of the count."""
     kinds = [SDF_SPHERE, SDF_TORUS, SDF_BOX, SDF_CAPSULE, SDF_ROUNDCONE, SDF_TWOSPHERE,
              SDF_TWISTTORUS, SDF_OCTA]
-    return _many_scene("4096inst-2048", kinds, 4096, 4, W, H, 40.0, 8, nerf)
+    E = 40.0 * (n_inst / 4096.0) ** (1.0 / 3.0)
+    return _many_scene(f"{n_inst}inst-{W}", kinds, n_inst, 4, W, H, E, 8, nerf)
 
 
 def pixel_subset(W: int, H: int, n: int, seed: int) -> np.ndarray:

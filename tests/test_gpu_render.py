@@ -4,7 +4,7 @@ import pytest
 
 from paper_2308_04669_gb300 import scenegen as sg
 
-from .gpu_helpers import NOID, close, compare_frame, gpu_frame
+from .gpu_helpers import NOID, close, compare_frame, compare_volume, gpu_frame
 
 pytestmark = pytest.mark.gpu
 
@@ -112,7 +112,7 @@ def test_parallel_lights(orc, precision):
     else:
         g = gpu_frame(sc, precision=native.PREC_BF16)
         o = orc.render(orc.OracleScene(sc), quant=orc.QUANT_BF16, n_threads=8)
-        rep = compare_frame(g, o, o["px"], check_colour=False, max_excluded=0.1)
+        rep = compare_frame(g, o, o["px"], max_excluded=0.1)
     assert rep["shadowed"] > 50 and g["stats"].status == 0
 
 
@@ -162,7 +162,7 @@ def test_nedf_query_isolated(orc):
                 assert g[i, 3] == 0 and np.isinf(g[i, 2])
                 continue
             y = orc.mlp(sc.types[t].nedf_w.astype(np.float64), sc.types[t].nedf_dims, f)
-            assert close([g[i, 0], g[i, 1]], y, 2e-4, 1e-4).all(), (i, g[i], y)
+            assert close([g[i, 0], g[i, 1]], y, 1e-5, 1e-5).all(), (i, g[i], y)   # FP32 sums, FP32 sin/cos
             assert g[i, 3] == float(y[1] > 0 and b[2] - y[0] > 0) or abs(y[1]) < 1e-4
     r.close()
 
@@ -238,19 +238,19 @@ def test_plain_method_frame_dense_matches_oracle(orc):
     """Plain method (every NeRF volume rendered front to back), albedo sphere, full frame."""
     sc = sg.tiny_sphere_scene()
     g = _march_gpu(sc, 128, 0)
-    o = orc.volume_render(orc.OracleScene(sc), 128)
-    ok = close(g, o)
-    assert ok.mean() > 0.999 and (o[:, 3] > 0.5).sum() > 500
+    o, vm = orc.volume_render(orc.OracleScene(sc), 128, margins=True)
+    compare_volume(g, o, vm)
+    assert (o[:, 3] > 0.5).sum() > 500
 
 
 def test_plain_method_frame_nerf_subset(orc):
     """Three types with 8x256 colour networks, overlapping bounds; subset of pixels."""
     sc = sg.three_types_scene(96, 96)
     g = _march_gpu(sc, 64, 0)
-    px = sg.pixel_subset(96, 96, 160, 3)
-    o = orc.volume_render(orc.OracleScene(sc), 64, px=px, n_threads=8)
-    ok = close(g[px], o)
-    assert ok.mean() > 0.995 and (o[:, 3] > 0.5).sum() > 10
+    px = sg.pixel_subset(96, 96, 400, 3)
+    o, vm = orc.volume_render(orc.OracleScene(sc), 64, px=px, n_threads=8, margins=True)
+    compare_volume(g[px], o, vm)
+    assert (o[:, 3] > 0.5).sum() > 30
 
 
 def test_plain_method_early_stop_bound(orc):

@@ -11,7 +11,7 @@ import pytest
 
 from paper_2308_04669_gb300 import scenegen as sg
 
-from .gpu_helpers import MARGIN, GAP, NOID, close, gpu_frame
+from .gpu_helpers import NOID, close, decided_pixels, gpu_frame
 
 pytestmark = pytest.mark.gpu
 
@@ -22,20 +22,27 @@ def _built():
     build.build()
 
 
-def _compare(sc, g, o, px, abs_tol, rel_tol, frac):
+def _compare(sc, g, o, px, abs_tol, rel_tol):
+    """Element-wise colour of decided pixels (decided_pixels: the Step-1 margins include every
+    bound's cull discriminant on the ray, the plain method's only other decisions), with the
+    knife edges of the re-render test itself (sample maximum within 1 % of the threshold) counted
+    and left out."""
     gid = g["id"][px]
-    decided = (o["pmargin"] > MARGIN) & ((o["gap"] > GAP) | (o["id"] == NOID))
+    decided = decided_pixels(o)
     same = decided & (gid == o["id"]) & (o["id"] != NOID)
+    assert not (decided & (gid != o["id"])).any()
     edge = np.abs(o["shade_smax"] - 1.0) < 0.01
     rs = same & ~edge & (o["shade_smax"] < 1.0)
     kept = same & ~edge & (o["shade_smax"] >= 1.0)
     assert rs.sum() > 50 and kept.sum() > 10, (rs.sum(), kept.sum())
     for m in (rs, kept):
         ok = close(g["rgba"][px][m], o["rgba"][m], abs_tol, rel_tol).all(axis=1)
-        assert ok.mean() >= frac, (ok.mean(), np.abs(g["rgba"][px][m] - o["rgba"][m]).max())
+        assert ok.all(), ((~ok).sum(), np.abs(g["rgba"][px][m] - o["rgba"][m]).max())
     # the count of re-rendered pixels: the oracle's decisions, give or take the knife edges
     n_or = int((o["shade_smax"] < 1.0).sum())
     n_edge = int((np.abs(o["shade_smax"] - 1.0) < 0.01).sum())
+    print(f"re-rendered {rs.sum()}, kept {kept.sum()}, knife edges {int((same & edge).sum())}, "
+          f"undecided {int((~decided).sum())} of {len(px)}")
     return n_or, n_edge, rs.sum()
 
 
@@ -47,7 +54,7 @@ def test_resampling_fp32_matches_oracle(orc):
     g = gpu_frame(sc, precision=native.PREC_FP32, shade_resample=128, shade_sigma_min=1.0)
     o = orc.render(orc.OracleScene(sc), n_threads=8, shade_resample=128, shade_sigma_min=1.0)
     px = o["px"]
-    n_or, n_edge, n_cmp = _compare(sc, g, o, px, 2e-3, 1e-3, 1.0)
+    n_or, n_edge, n_cmp = _compare(sc, g, o, px, 2e-3, 1e-3)
     assert abs(int(g["stats"].resampled_pixels) - n_or) <= n_edge + 2, (g["stats"].resampled_pixels, n_or, n_edge)
     assert g["stats"].status == 0
     # off: nothing re-rendered
@@ -65,5 +72,5 @@ def test_resampling_bf16_nerf_matches_oracle(orc):
     px = sg.pixel_subset(96, 96, 700, 21)
     o = orc.render(orc.OracleScene(sc), px=px, n_threads=8, quant=orc.QUANT_BF16, shade_resample=64,
                    shade_sigma_min=1.0)
-    _compare(sc, g, o, px, 5e-3, 5e-3, 0.97)
+    _compare(sc, g, o, px, 2e-3, 1e-3)
     assert g["stats"].resampled_pixels > 0 and g["stats"].status == 0

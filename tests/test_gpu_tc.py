@@ -1,22 +1,24 @@
 """BF16 tensor-core path (tcgen05 MMAs, TMEM accumulators) vs the oracle in BF16-operand mode.
 
 The oracle's QUANT_BF16 mode rounds every layer's inputs and weights to BF16 and accumulates in
-FP64; the kernels accumulate in FP32 in TMEM.  Differences come from accumulation order and from
-the rare activation that lands on the other side of a BF16 rounding boundary (one BF16 ulp,
-2^-8 relative, on one of 128-256 inputs of the next layer), so the network outputs are compared
-with a 1e-2 absolute + 1e-2 relative bound and a median error bound of 1e-3.  The error of the
-BF16 path against the unrounded FP64 network is reported alongside.
+FP64; the kernels accumulate in FP32 in TMEM.  Network rows agree to the FP32 summation order
+(within 1e-7, bounded at 1e-6) unless an FP32 sum lands on the other side of a BF16 rounding
+boundary than the FP64 sum; such a row is accepted only when rounding one of the oracle's six
+values nearest to a boundary the other way reproduces it within the same bound, and those rows are
+counted.  Frames then compare element by element at the FP32 tolerance, the oracle's knife edges
+(flip spreads included) counted and left out.
 """
 import numpy as np
 import pytest
 
 from paper_2308_04669_gb300 import scenegen as sg
 
-from .gpu_helpers import NOID, close, compare_frame, gpu_frame
+from .gpu_helpers import NOID, check_network_rows, compare_frame, compare_volume, gpu_frame
 
 pytestmark = pytest.mark.gpu
 
-BF16_ABS, BF16_REL = 1e-2, 1e-2
+# rows explained by one rounding flip: measured 2.2-2.7 % of rows (6 x 128 network)
+BF16_FLIP_ROWS = 0.05
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -36,51 +38,59 @@ def run_query(sc, t, o32, d32, precision):
     return out.cpu().numpy().astype(np.float64)
 
 
+def query_rays(seed, n):
+    rng = np.random.default_rng(seed)
+    o32 = rng.normal(size=(n, 3))
+    o32 = (2.5 * o32 / np.linalg.norm(o32, axis=1, keepdims=True)).astype(np.float32)
+    d32 = (-o32 + rng.normal(size=(n, 3)) * 0.8).astype(np.float32)   # mostly towards the bound
+    return o32, d32
+
+
+def query_features(orc, o32, d32, rb):
+    """The oracle's encoded inputs of each ray (None where the bound culls it), and the culled rows
+    that are no knife edge of the cull."""
+    feats, culled = [], []
+    for i in range(o32.shape[0]):
+        dd = d32[i].astype(np.float64); dd /= np.linalg.norm(dd)
+        kept, f, b = orc.nedf_features(o32[i].astype(np.float64), dd, float(rb))
+        feats.append(f if kept else None)
+        if not kept and abs(b[3]) > 1e-4:
+            culled.append(i)
+    return feats, np.array(culled, np.int64)
+
+
 @pytest.mark.parametrize("scene_fn", [sg.tiny_sphere_scene, lambda: sg.three_types_scene(8, 8, nerf=False)])
 def test_bf16_nedf_query_matches_bf16_oracle(orc, scene_fn):
     from paper_2308_04669_gb300 import native
     sc = scene_fn()
-    rng = np.random.default_rng(4)
-    n = 1500                      # 11 full tiles of 128 rows and a ragged tail
-    o32 = rng.normal(size=(n, 3))
-    o32 = (2.5 * o32 / np.linalg.norm(o32, axis=1, keepdims=True)).astype(np.float32)
-    d32 = (-o32 + rng.normal(size=(n, 3)) * 0.8).astype(np.float32)   # mostly towards the bound
+    n = 1500                      # 5 full tiles of 256 rows and a ragged tail
+    o32, d32 = query_rays(4, n)
     for t in range(len(sc.types)):
         g = run_query(sc, t, o32, d32, native.PREC_BF16)
+        feats, culled = query_features(orc, o32, d32, sc.types[t].rb)
+        assert np.all(g[culled, 3] == 0) and np.all(np.isinf(g[culled, 2]))
         w = sc.types[t].nedf_w.astype(np.float64)
-        errs, errs_fp = [], []
-        for i in range(n):
-            dd = d32[i].astype(np.float64); dd /= np.linalg.norm(dd)
-            kept, f, b = orc.nedf_features(o32[i].astype(np.float64), dd, float(sc.types[t].rb))
-            if not kept:
-                if abs(b[3]) > 1e-4:
-                    assert g[i, 3] == 0 and np.isinf(g[i, 2])
-                continue
-            yq = orc.mlp(w, sc.types[t].nedf_dims, f, quant=orc.QUANT_BF16)
-            yf = orc.mlp(w, sc.types[t].nedf_dims, f)
-            assert close(g[i, :2], yq, BF16_ABS, BF16_REL).all(), (i, g[i, :2], yq)
-            errs.append(np.abs(g[i, :2] - yq).max())
-            errs_fp.append(np.abs(g[i, :2] - yf).max())
-        assert len(errs) > 600
-        assert np.median(errs) < 1e-3
-        print(f"type {t}: median |bf16 gpu - bf16 oracle| {np.median(errs):.2e}, "
-              f"median |bf16 gpu - fp64 network| {np.median(errs_fp):.2e}")
+        rep = check_network_rows(orc, g[:, :2], w, sc.types[t].nedf_dims, feats, orc.QUANT_BF16, BF16_FLIP_ROWS)
+        assert rep["rows"] > 600
+        errs_fp = [np.abs(g[i, :2] - orc.mlp(w, sc.types[t].nedf_dims, f)).max() for i, f in enumerate(feats)
+                   if f is not None]
+        print(f"type {t}: {rep}; median |bf16 gpu - fp64 network| {np.median(errs_fp):.2e}")
 
 
 def test_bf16_shading_matches_bf16_oracle(orc):
     """Step 2 on the tensor cores (NeRF 8x256 streamed layer by layer), surface depths from the
-    plain method so that every shaded pixel has non-trivial opacity and colour."""
+    plain method so that every shaded pixel has non-trivial opacity and colour: element-wise at the
+    FP32 tolerance (a BF16 rounding flip in the colour network moves a colour by ~1e-4)."""
     from paper_2308_04669_gb300 import native
     sc = sg.three_types_scene(128, 128)
-    px = sg.pixel_subset(128, 128, 500, 8)
+    px = sg.pixel_subset(128, 128, 800, 8)
     g = gpu_frame(sc, precision=native.PREC_BF16, depth_source=1)
     o = orc.render(orc.OracleScene(sc), px=px, depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4,
                    quant=orc.QUANT_BF16, n_threads=8)
-    same = (g["id"][px] == o["id"]) & (o["id"] != NOID) & (o["pmargin"] > 1e-3) & (o["gap"] > 1e-4)
-    assert same.sum() > 40
-    ok = close(g["rgba"][px][same], o["rgba"][same], 2e-3, 2e-3)
-    assert ok.mean() > 0.995, np.abs(g["rgba"][px][same] - o["rgba"][same]).max()
-    assert (o["rgba"][same][:, 3] > 0.3).mean() > 0.5
+    rep = compare_frame(g, o, px)
+    assert rep["hit"] > 200 and rep["colour_max_err"] < 5e-4
+    hit = o["id"] != NOID
+    assert (o["rgba"][hit][:, 3] > 0.3).mean() > 0.5
 
 
 def test_bf16_full_frame_nedf(orc):
@@ -108,19 +118,6 @@ def test_bf16_refine_and_outlier_resample(orc):
     assert g["stats"].fallback_pairs > 0 and rep["hit"] > 100
 
 
-def test_bf16_thousand_instances_stats(orc):
-    """The 1024-instance workload runs clean on the tensor-core path and agrees with FP32 on the
-    pair counts (binning does not depend on precision)."""
-    from paper_2308_04669_gb300 import native
-    sc = sg.thousand_scene()
-    a = gpu_frame(sc, precision=native.PREC_FP32)
-    b = gpu_frame(sc, precision=native.PREC_BF16)
-    assert a["stats"].primary_pairs == b["stats"].primary_pairs
-    assert b["stats"].status == 0
-    both = (a["id"] != NOID) & (b["id"] != NOID)
-    assert (a["id"][both] == b["id"][both]).mean() > 0.97
-
-
 def test_bf16_plain_method_frame(orc):
     """The plain method's colour frame with its NeRF on the tensor cores (sample rows of every
     (ray, instance) pair, weights T * alpha, per-pair sums) against the BF16-operand oracle."""
@@ -128,10 +125,10 @@ def test_bf16_plain_method_frame(orc):
     from .test_gpu_render import _march_gpu
     sc = sg.three_types_scene(96, 96)
     g = _march_gpu(sc, 64, 0, precision=native.PREC_BF16)
-    px = sg.pixel_subset(96, 96, 160, 3)
-    o = orc.volume_render(orc.OracleScene(sc), 64, px=px, n_threads=8, quant=orc.QUANT_BF16)
-    ok = close(g[px], o)
-    assert ok.mean() > 0.995 and (o[:, 3] > 0.5).sum() > 10
+    px = sg.pixel_subset(96, 96, 400, 3)
+    o, vm = orc.volume_render(orc.OracleScene(sc), 64, px=px, n_threads=8, quant=orc.QUANT_BF16, margins=True)
+    compare_volume(g[px], o, vm)
+    assert (o[:, 3] > 0.5).sum() > 30
     es = _march_gpu(sc, 64, 1, precision=native.PREC_BF16)
     assert np.abs(es - g).max() < 2e-3
 

@@ -311,3 +311,164 @@ def test_mlp_qmargin_reports_the_tightest_rounded_value(orc):
     assert abs(m - 3e-5 / (1.0 + abs(w[78]))) < 1e-12
     _, m_none = orc.mlp_qmargin(w, dims, x, orc.QUANT_NONE)
     assert m_none == math.inf
+
+
+# ------------------------------------------------------------------------------------------------
+# knife-edge diagnostics of queries and frames
+# ------------------------------------------------------------------------------------------------
+def _flip_net(pre, w_out, b_m=0.0, a=5.0, width=8):
+    """One-hidden-layer NeDF weights whose first hidden unit has pre-activation `pre` for every
+    input (its bias), every other unit 0; m = b_m + w_out * (that unit, as rounded), a = `a`."""
+    dims = sg.mlp_dims(sg.NEDF_IN, 1, width, 2)
+    w = np.zeros(sg.mlp_param_count(dims))
+    off = sg.NEDF_IN * width
+    w[off] = pre                                                 # bias of unit 0, layer 0
+    off += width
+    w[off] = w_out                                               # W_out[0][0]
+    w[off + 2 * width] = b_m
+    w[off + 2 * width + 1] = a
+    return w.astype(np.float32).astype(np.float64), dims
+
+
+def test_mlp_flip_rounds_one_value_the_other_way(orc):
+    pre = 1.0 + 2.0 ** -8 - 3e-7                                 # just below the 1 | 1+2^-7 midpoint
+    w, dims = _flip_net(pre, 0.5)
+    x = np.zeros(sg.NEDF_IN)
+    y, ci, cm = orc.mlp_flip(w, dims, x, orc.QUANT_BF16, -1, 3)
+    assert abs(y[0] - 0.5 * 1.0) < 1e-15                         # rounds down to 1
+    assert ci[0] == sg.NEDF_IN and cm[0] < 1e-6                  # unit 0 of layer 0 is the knife edge
+    yf, _, _ = orc.mlp_flip(w, dims, x, orc.QUANT_BF16, int(ci[0]), 0)
+    assert abs(yf[0] - 0.5 * (1.0 + 2.0 ** -7)) < 1e-15          # ... and up when flipped
+    assert np.all(np.diff(cm[np.isfinite(cm)]) >= 0)
+    # E4M3 (FP8 mode: every hidden activation is E4M3): the grid at 1 is 1/8
+    w2, dims2 = _flip_net(1.0 + 2.0 ** -4 + 1e-7, 0.5)
+    y2, ci2, _ = orc.mlp_flip(w2, dims2, x, orc.QUANT_FP8, -1, 1)
+    yf2, _, _ = orc.mlp_flip(w2, dims2, x, orc.QUANT_FP8, int(ci2[0]), 0)
+    assert {round(y2[0] / 0.5, 12), round(yf2[0] / 0.5, 12)} == {1.0, 1.125}
+
+
+def test_query_spread_is_the_depth_change_of_one_flip(orc):
+    """A row with one activation 3e-7 below a BF16 boundary: its depth may move by rb * w_out *
+    2^-7; the FP32 mode has no spread."""
+    for rb in (1.0, 2.0):
+        w, dims = _flip_net(1.0 + 2.0 ** -8 - 3e-7, 0.25, b_m=0.1)
+        sc = one_instance_scene(sg.SDF_SPHERE, nedf_w=w, hidden=1, width=8, rb=rb)
+        osc = orc.OracleScene(sc)
+        _, _, (mg, dm, dsp) = orc.query_diag(osc, 0, EYE, DIR, quant=orc.QUANT_BF16)
+        assert abs(dsp - rb * 0.25 * 2.0 ** -7) < 1e-12 and dm == math.inf
+        _, _, (mg, dm, dsp) = orc.query_diag(osc, 0, EYE, DIR)
+        assert dsp == 0.0
+        # far from any boundary there is nothing to flip
+        w, dims = _flip_net(1.0 + 2.0 ** -9, 0.25, b_m=0.1)
+        sc = one_instance_scene(sg.SDF_SPHERE, nedf_w=w, hidden=1, width=8, rb=rb)
+        assert orc.query_diag(orc.OracleScene(sc), 0, EYE, DIR, quant=orc.QUANT_BF16)[2][2] == 0.0
+
+
+def _inside_sphere(t, r=0.5):
+    """The one-sphere test ray's point at t is inside the r-sphere (closed form: |3 - t| <= r)."""
+    return abs(3.0 - t) <= r
+
+
+CAP = 1e-4      # tests with a larger relative margin are never knife edges and are not recorded
+
+
+def _capped_min(items, need=0.0):
+    return min((r for r, c in items if r < CAP and c >= need), default=math.inf)
+
+
+@pytest.mark.parametrize("delta", [-3e-4, 2e-4, 0.0251, -0.0124, 0.04])
+def test_query_dmargin_of_the_refinement_is_the_closest_tested_point(orc, delta):
+    """The refinement tests the window ends and its midpoints; a test's margin is
+    | |3 - t| - r | over |o_local| + |t| + rb, and its consequence half its bracket (H, H/2, ...;
+    unbounded for the window's ends)."""
+    m = _m_for_depth(SURF + delta)
+    D0 = _depth_of(m)
+    sc = one_instance_scene(sg.SDF_SPHERE, nedf_w=constant_nedf(m, 5.0))
+    osc = orc.OracleScene(sc)
+    _, out, (mg, dm, dsp) = orc.query_diag(osc, 0, EYE, DIR, refine_steps=4)
+    lo, hi = D0 - H, D0 + H
+    rel = lambda t: abs(abs(3.0 - t) - 0.5) / (3.0 + abs(t) + 1.0)
+    items = [(rel(lo), math.inf), (rel(hi), math.inf)]
+    for _ in range(4):
+        mid = 0.5 * (lo + hi)
+        items.append((rel(mid), 0.5 * (hi - lo)))
+        if _inside_sphere(mid):
+            hi = mid
+        else:
+            lo = mid
+    assert abs(out[0] - 0.5 * (lo + hi)) < 1e-12 and dsp == 0.0
+    assert dm == _capped_min(items) or abs(dm - _capped_min(items)) < 1e-12
+    if abs(delta) < 1e-3:
+        assert dm < CAP                                          # the first midpoint is D0 itself
+    for k in range(5):
+        need = H / 2 ** k + 1e-12
+        got = orc.query_diag(osc, 0, EYE, DIR, need=need, refine_steps=4)[2][1]
+        want = _capped_min(items, need)
+        assert got == want or abs(got - want) < 1e-12, k
+
+
+@pytest.mark.parametrize("n", [16, 13, 29])
+def test_query_dmargin_of_the_plain_method(orc, n):
+    """MARCH mode: the samples t_k = te + k (tx - te) / N up to the crossing (unbounded
+    consequence), then the bisection steps (half their bracket)."""
+    sc = one_instance_scene(sg.SDF_SPHERE)
+    osc = orc.OracleScene(sc)
+    _, out, (mg, dm, _) = orc.query_diag(osc, 0, EYE, DIR, depth_mode=orc.DEPTH_MARCH, march_n=n, march_b=3)
+    te, tx = 2.0, 4.0                                            # the unit bound along the axis
+    rel = lambda t: abs(abs(3.0 - t) - 0.5) / (3.0 + abs(t) + 1.0)
+    items, ts, lo, hi = [], [], None, None
+    for k in range(n + 1):
+        t = te + (tx - te) * k / n
+        ts.append(t)
+        items.append((rel(t), math.inf))
+        if k > 0 and _inside_sphere(t) and not _inside_sphere(ts[-2]):
+            lo, hi = ts[-2], t
+            break
+    for _ in range(3):
+        mid = 0.5 * (lo + hi)
+        items.append((rel(mid), 0.5 * (hi - lo)))
+        if _inside_sphere(mid):
+            hi = mid
+        else:
+            lo = mid
+    assert abs(out[0] - 0.5 * (lo + hi)) < 1e-12
+    assert dm == _capped_min(items) or abs(dm - _capped_min(items)) < 1e-12
+    big = orc.query_diag(osc, 0, EYE, DIR, need=1.0, depth_mode=orc.DEPTH_MARCH, march_n=n, march_b=3)[2][1]
+    assert big == _capped_min(items, 1.0)
+
+
+def test_frame_gap_is_reduced_by_both_depth_spreads(orc):
+    """Two instances with the same knife-edge network one behind the other: the reported gap is
+    the depth difference less both instances' flip shifts (BF16), the plain difference in FP32."""
+    w, dims = _flip_net(1.0 + 2.0 ** -8 - 3e-7, 0.25, b_m=0.1)
+    t = sg.make_type(sg.SDF_SPHERE, 0, 0, 1, 8, nedf_seed=1)
+    t.nedf_w = w.astype(np.float32)
+    sc = sg.Scene("two", 33, 33, sg.f32([0, 0, 4]), sg.f32([0, 0, 0]), 40.0, sg.f32([[2, 3, 2]]), [t],
+                  np.zeros(2, np.uint32), sg.f32(np.tile(np.eye(3).reshape(1, 9), (2, 1))),
+                  sg.f32([[0, 0, 0.5], [0, 0, -0.25]]), sg.f32([1, 1]))
+    px = np.array([16 * 33 + 16])
+    o32 = orc.render(orc.OracleScene(sc), px=px)
+    ob = orc.render(orc.OracleScene(sc), px=px, quant=orc.QUANT_BF16)
+    assert abs(o32["gap"][0] - 0.75) < 1e-6 and o32["dmargin"][0] == math.inf
+    assert abs(ob["gap"][0] - (o32["gap"][0] - 2 * 0.25 * 2.0 ** -7)) < 1e-6
+
+
+def test_frame_alternative_outcome_takes_the_critical_test_the_other_way(orc):
+    """Centre pixel of the one-sphere frame, plain-method depths with 16 samples over the bound
+    chord [2, 4]: sample 4 lies exactly on the surface (t = 2.5, margin 0).  Taken as inside it ends
+    the march there and 3 bisections of [2.375, 2.5] give 2.4921875; taken the other way the
+    crossing moves to 2.625 and the bisections of [2.5, 2.625] give 2.5078125."""
+    sc = one_instance_scene(sg.SDF_SPHERE)
+    px = np.array([32 * 65 + 32])
+    o = orc.render(orc.OracleScene(sc), px=px, depth_mode=orc.DEPTH_MARCH, march_n=16, march_b=3)
+    assert o["depth"][0] == 2.4921875 and o["has_alt"][0] and o["alt_depth"][0] == 2.5078125
+    assert o["alt_id"][0] == 0 and o["dmargin"][0] > 1e-6               # no second knife edge
+    # the alternative shading is the primary's window moved by the depth difference
+    assert not np.allclose(o["alt_rgba"][0], o["rgba"][0], atol=1e-6)
+    # a sphere of radius 0.45 puts the surface at 0.275 of the chord, which no sample or
+    # bisection midpoint of 17 samples comes within 1e-6 (relative) of: no alternative
+    sc45 = one_instance_scene(sg.SDF_SPHERE, params=[0.45])
+    o = orc.render(orc.OracleScene(sc45), px=px, depth_mode=orc.DEPTH_MARCH, march_n=17, march_b=3)
+    assert not o["has_alt"][0] and np.isnan(o["alt_depth"][0]) and abs(o["depth"][0] - 2.55) < 0.01
+    o = orc.render(orc.OracleScene(sc), px=px, alt=False, depth_mode=orc.DEPTH_MARCH, march_n=16, march_b=3)
+    assert "has_alt" not in o
