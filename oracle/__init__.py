@@ -99,6 +99,7 @@ def lib():
             l.orc_march_depth.restype = C.c_double
             l.orc_composite_samples.argtypes = [C.c_int, d, d, C.c_double, d]
             l.orc_render.argtypes = [sp, op, C.c_int64, i64, d, u32, d, d, d, d, d, d, d, d, d]
+            l.orc_steps23.argtypes = [sp, op, C.c_int64, i64, u32, d, d, d, d, d]
             l.orc_query_diag.argtypes = [sp, op, C.c_int, d, d, d, d, C.c_double]; l.orc_query_diag.restype = C.c_int
             l.orc_mlp_flip.argtypes = [d, C.c_int, i, d, d, C.c_int, C.c_int, C.c_int, i, d]
             l.orc_volume_render.argtypes = [sp, op, C.c_int, C.c_int64, i64, d, d]
@@ -220,6 +221,21 @@ def render(osc: OracleScene, px=None, alt=True, **kw):
         out["alt_rgba"] = a[:, 2:6]
         out["alt_shadow"] = a[:, 6]
         out["alt_out"] = a[:, 7:11]
+    return out
+
+
+def steps23(osc: OracleScene, px, ids, depth, **kw):
+    """Steps 2-3 of pixels px given each pixel's winner id (uint32, 0xFFFFFFFF none) and world depth:
+    dict(rgba, shadow, smargin, out)."""
+    px = np.ascontiguousarray(px, np.int64)
+    ids = np.ascontiguousarray(ids, np.uint32)
+    depth = np.ascontiguousarray(depth, np.float64)
+    n = px.shape[0]
+    out = dict(rgba=np.empty((n, 4)), shadow=np.empty(n), smargin=np.empty(n), out=np.empty((n, 4)))
+    o = opts(**kw)
+    lib().orc_steps23(osc.ptr, C.byref(o), n, px.ctypes.data_as(C.POINTER(C.c_int64)),
+                      ids.ctypes.data_as(C.POINTER(C.c_uint32)), _dp(depth), _dp(out["rgba"]), _dp(out["shadow"]),
+                      _dp(out["smargin"]), _dp(out["out"]))
     return out
 
 

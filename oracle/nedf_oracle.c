@@ -757,19 +757,23 @@ double orc_march_depth(const orc_scene *sc, int type, const double ol[3], const 
 
 /* Network-rounding spread of a regression NeDF row in the BF16 / E4M3 modes: the largest change of
  * (m, a) when one of its ORC_FLIP_CAND values nearest to a rounding boundary (relative margin below
- * ORC_FLIP_MARGIN, i.e. within reach of FP32 summation error) rounds the other way. */
-#define ORC_FLIP_CAND 6
-#define ORC_FLIP_MARGIN 1e-5
+ * the format's limit, i.e. within reach of another implementation's sums) rounds the other way. */
+#define ORC_FLIP_CAND 16
+/* BF16: FP32 sums plus a bias carried to ~16 significant bits (relative 2^-17 of |b|); E4M3: FP32
+ * sums with the bias added in FP32 */
+#define ORC_FLIP_MARGIN_BF16 1e-5
+#define ORC_FLIP_MARGIN_FP8 1e-6
 static void nedf_spread(const orc_type *t, const int *dims, int nl, const double *feat, const double y[2],
                         int quant, double spread[2])
 {
     spread[0] = spread[1] = 0.0;
     if (quant == ORC_QUANT_NONE || t->nedf_arch == ORC_ARCH_CLASSIFIER) return;
+    const double lim = quant == ORC_QUANT_FP8 ? ORC_FLIP_MARGIN_FP8 : ORC_FLIP_MARGIN_BF16;
     int ci[ORC_FLIP_CAND];
     double cm[ORC_FLIP_CAND], yf[2];
     mlp_core(t->nedf_w, nl, dims, feat, yf, quant, NULL, -1, ORC_FLIP_CAND, ci, cm);
     for (int c = 0; c < ORC_FLIP_CAND; ++c) {
-        if (ci[c] < 0 || !(cm[c] < ORC_FLIP_MARGIN)) break;
+        if (ci[c] < 0 || !(cm[c] < lim)) break;
         mlp_core(t->nedf_w, nl, dims, feat, yf, quant, NULL, ci[c], 0, NULL, NULL);
         spread[0] = dmax(spread[0], fabs(yf[0] - y[0]));
         spread[1] = dmax(spread[1], fabs(yf[1] - y[1]));
@@ -967,45 +971,22 @@ typedef struct {
     uint32_t id;
 } pixel_result;
 
-/* Steps 1-3 for pixel p.  `fl` names one depth test to take the other way (stage 0: none);
- * cr[2] receives the pixel's two most critical depth tests (see render_one). */
-static void render_pixel(const orc_scene *sc, const orc_opts *op, int64_t p, const crit_test *fl,
-                         pixel_result *r, crit_test cr[2])
+/* Steps 2 and 3 of pixel p (camera ray o, d) given its winning instance `inst` and world depth:
+ * the shading of Eq. 8 over the sample window (or the plain method's colour for an outlier with
+ * resampling), then the shadow rays of Algorithm 2.  rgba, *S (the shadow factor), *sm (the shadow
+ * tests' margin) and *smax (the largest sample density) are written; fl / cr as in render_pixel
+ * (cr may be NULL). */
+static void steps23(const orc_scene *sc, const orc_opts *op, int64_t p, const double o[3], const double d[3], int inst,
+                    double depth, const crit_test *fl, double rgba[4], double *S_out, double *sm_out, double *smax_out,
+                    crit_test *cr)
 {
-    int i = (int)(p % sc->W), j = (int)(p / sc->W);
-    double o[3], d[3], q[6], mg, dsp, best = INFINITY, second = INFINITY, pm = INFINITY;
-    double u_best = 0.0, u_second = 0.0;
-    uint32_t bid = 0xFFFFFFFFu;
+    double q[6], mg, dsp, S = 1.0, sm = INFINITY, smax = NAN;
     dec_diag dg;
-    cr[0].m = cr[1].m = INFINITY;
-    cr[0].stage = cr[1].stage = 0;
-    orc_camera_ray(sc, i, j, o, d);
-    /* STEP 1: clear to infinity; visit models in id order; strict '<' keeps the lowest id on ties. */
-    const int ni = sc->n_inst > 0 ? sc->n_inst : 1;
-    double *Dq = (double *)malloc(sizeof(double) * ni);
-    dec_diag *dq = (dec_diag *)malloc(sizeof(dec_diag) * ni);
-    for (int m = 0; m < sc->n_inst; ++m) {
-        int flip = (fl->stage == 1 && fl->inst == m) ? fl->idx : -1;
-        int hit = query_ex(sc, op, m, o, d, q, &mg, &dq[m], flip, &dsp);
-        pm = dmin(pm, mg);
-        Dq[m] = hit ? sc->inst_s[m] * q[0] : INFINITY;
-        if (!hit) { crit_feed(cr, &dq[m], INFINITY, 1, 0, m); continue; }   /* could it become a hit? */
-        double D = Dq[m], u = sc->inst_s[m] * dsp;
-        if (D < best) { second = best; u_second = u_best; best = D; u_best = u; bid = (uint32_t)m; }
-        else if (D < second) { second = D; u_second = u; }
-    }
-    /* Depth tests that can change this pixel: every one of the winner's (its depth feeds Steps 2
-     * and 3), and those of each other hit whose consequence reaches the winner. */
-    for (int m = 0; m < sc->n_inst; ++m) {
-        if (!isfinite(Dq[m])) continue;
-        crit_feed(cr, &dq[m], (uint32_t)m == bid ? 0.0 : (Dq[m] - best) / sc->inst_s[m], 1, 0, m);
-    }
-    free(Dq);
-    free(dq);
-    double rgba[4] = {0, 0, 0, 0}, S = 1.0, sm = INFINITY, smax = NAN;
-    if (bid != 0xFFFFFFFFu) {
+    crit_test none2[2];
+    if (!cr) { cr = none2; cr[0].m = cr[1].m = INFINITY; }
+    {
         /* STEP 2: shade with the winning model's radiance field only. */
-        smax = shade_pixel(sc, op, o, d, (int)bid, best, rgba);
+        smax = shade_pixel(sc, op, o, d, inst, depth, rgba);
         /* Outlier resampling: an extremely small density says the depth missed the surface; the
          * pixel's colour then comes from the primary volume rendering of every model. */
         if (op->shade_resample > 0 && smax < op->shade_sigma_min) {
@@ -1016,7 +997,7 @@ static void render_pixel(const orc_scene *sc, const orc_opts *op, int64_t p, con
         /* STEP 3: x on the surface, shadow ray from each light towards x; an occluder hit
          * closer to the light than x by more than eps darkens by beta; lights averaged. */
         double x[3];
-        for (int c = 0; c < 3; ++c) x[c] = o[c] + best * d[c];
+        for (int c = 0; c < 3; ++c) x[c] = o[c] + depth * d[c];
         double acc = 0.0;
         for (int l = 0; l < sc->n_lights; ++l) {
             const double *L = sc->lights + 3 * l;
@@ -1056,6 +1037,47 @@ static void render_pixel(const orc_scene *sc, const orc_opts *op, int64_t p, con
         }
         S = acc / sc->n_lights;
     }
+    *S_out = S;
+    *sm_out = sm;
+    *smax_out = smax;
+}
+
+/* Steps 1-3 for pixel p.  `fl` names one depth test to take the other way (stage 0: none);
+ * cr[2] receives the pixel's two most critical depth tests (see render_one). */
+static void render_pixel(const orc_scene *sc, const orc_opts *op, int64_t p, const crit_test *fl,
+                         pixel_result *r, crit_test cr[2])
+{
+    int i = (int)(p % sc->W), j = (int)(p / sc->W);
+    double o[3], d[3], q[6], mg, dsp, best = INFINITY, second = INFINITY, pm = INFINITY;
+    double u_best = 0.0, u_second = 0.0;
+    uint32_t bid = 0xFFFFFFFFu;
+    cr[0].m = cr[1].m = INFINITY;
+    cr[0].stage = cr[1].stage = 0;
+    orc_camera_ray(sc, i, j, o, d);
+    /* STEP 1: clear to infinity; visit models in id order; strict '<' keeps the lowest id on ties. */
+    const int ni = sc->n_inst > 0 ? sc->n_inst : 1;
+    double *Dq = (double *)malloc(sizeof(double) * ni);
+    dec_diag *dq = (dec_diag *)malloc(sizeof(dec_diag) * ni);
+    for (int m = 0; m < sc->n_inst; ++m) {
+        int flip = (fl->stage == 1 && fl->inst == m) ? fl->idx : -1;
+        int hit = query_ex(sc, op, m, o, d, q, &mg, &dq[m], flip, &dsp);
+        pm = dmin(pm, mg);
+        Dq[m] = hit ? sc->inst_s[m] * q[0] : INFINITY;
+        if (!hit) { crit_feed(cr, &dq[m], INFINITY, 1, 0, m); continue; }   /* could it become a hit? */
+        double D = Dq[m], u = sc->inst_s[m] * dsp;
+        if (D < best) { second = best; u_second = u_best; best = D; u_best = u; bid = (uint32_t)m; }
+        else if (D < second) { second = D; u_second = u; }
+    }
+    /* Depth tests that can change this pixel: every one of the winner's (its depth feeds Steps 2
+     * and 3), and those of each other hit whose consequence reaches the winner. */
+    for (int m = 0; m < sc->n_inst; ++m) {
+        if (!isfinite(Dq[m])) continue;
+        crit_feed(cr, &dq[m], (uint32_t)m == bid ? 0.0 : (Dq[m] - best) / sc->inst_s[m], 1, 0, m);
+    }
+    free(Dq);
+    free(dq);
+    double rgba[4] = {0, 0, 0, 0}, S = 1.0, sm = INFINITY, smax = NAN;
+    if (bid != 0xFFFFFFFFu) steps23(sc, op, p, o, d, (int)bid, best, fl, rgba, &S, &sm, &smax, cr);
     r->depth = best;
     r->id = bid;
     /* the gap less the depth shift single network-rounding flips can cause on either side */
@@ -1137,6 +1159,55 @@ int orc_render(const orc_scene *sc, const orc_opts *op, int64_t n_px, const int6
     }
     if (nt == 1) { render_worker(&jobs[0]); return 0; }
     for (int t = 0; t < nt; ++t) pthread_create(&th[t], NULL, render_worker, &jobs[t]);
+    for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
+    return 0;
+}
+
+/* Steps 2-3 alone for pixels whose winner and world depth are given (id 0xFFFFFFFF: no hit). */
+typedef struct {
+    const orc_scene *sc;
+    const orc_opts *op;
+    const int64_t *px;
+    const uint32_t *id;
+    const double *depth;
+    int64_t begin, end;
+    double *rgba, *shadow, *smargin, *out;
+} s23_job;
+
+static void *s23_worker(void *arg)
+{
+    const s23_job *jb = (const s23_job *)arg;
+    const crit_test none = {INFINITY, 0, 0, 0, -1};
+    for (int64_t k = jb->begin; k < jb->end; ++k) {
+        double rgba[4] = {0, 0, 0, 0}, S = 1.0, sm = INFINITY, smax = NAN;
+        if (jb->id[k] != 0xFFFFFFFFu && (int64_t)jb->id[k] < jb->sc->n_inst) {
+            double o[3], d[3];
+            const int64_t p = jb->px[k];
+            orc_camera_ray(jb->sc, (int)(p % jb->sc->W), (int)(p / jb->sc->W), o, d);
+            steps23(jb->sc, jb->op, p, o, d, (int)jb->id[k], jb->depth[k], &none, rgba, &S, &sm, &smax, NULL);
+        }
+        for (int c = 0; c < 4; ++c) jb->rgba[4 * k + c] = rgba[c];
+        jb->shadow[k] = S;
+        jb->smargin[k] = sm;
+        for (int c = 0; c < 3; ++c) jb->out[4 * k + c] = rgba[c] * S;
+        jb->out[4 * k + 3] = rgba[3];
+    }
+    return NULL;
+}
+
+int orc_steps23(const orc_scene *sc, const orc_opts *op, int64_t n_px, const int64_t *px, const uint32_t *id,
+                const double *depth, double *rgba, double *shadow, double *smargin, double *out)
+{
+    int nt = op->n_threads > 1 ? op->n_threads : 1;
+    if (nt > 256) nt = 256;
+    s23_job jobs[256];
+    pthread_t th[256];
+    for (int t = 0; t < nt; ++t) {
+        s23_job jb = {sc, op, px, id, depth, n_px * t / nt, n_px * (t + 1) / nt, rgba, shadow, smargin, out};
+        jobs[t] = jb;
+    }
+    if (nt == 1) { s23_worker(&jobs[0]); return 0; }
+    for (int t = 0; t < nt; ++t) pthread_create(&th[t], NULL, s23_worker, &jobs[t]);
     for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
     return 0;
 }
@@ -1366,6 +1437,11 @@ double orc_nedf_loss_grad(const orc_scene *sc, int type, int n, const double *o,
                 dnx[i] = pre[l * maxd + i] > 0.0 ? acc : 0.0;
             }
             memcpy(dlt, dnx, sizeof(double) * fi);
+            /* BF16 training (reading 29): the error signal of a hidden layer enters its weight
+             * product, its bias sum and the next input-gradient product as a BF16 operand; the
+             * output layer's (the loss derivative) stays unrounded. */
+            if (quant == ORC_QUANT_BF16)
+                for (int i = 0; i < fi; ++i) dlt[i] = orc_round_bf16(dlt[i]);
         }
     }
     free(act); free(pre); free(dlt); free(dnx);

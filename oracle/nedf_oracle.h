@@ -165,6 +165,13 @@ int orc_render(const orc_scene *sc, const orc_opts *op, int64_t n_px, const int6
                double *shadow, double *smargin, double *out, double *shade_smax, double *dmargin,
                double *alt);
 
+/* Steps 2-3 (Eq. 8 shading, Algorithm 2 shadows, the composite) of pixels px given each pixel's
+ * winning instance id and world depth (id 0xFFFFFFFF: no hit): the oracle's answer to another
+ * implementation's Step-1 result, so that its Steps 2-3 can be checked exactly given that result.
+ * smargin as in orc_render. */
+int orc_steps23(const orc_scene *sc, const orc_opts *op, int64_t n_px, const int64_t *px, const uint32_t *id,
+                const double *depth, double *rgba, double *shadow, double *smargin, double *out);
+
 /* Plain method: dense front-to-back volume rendering with n samples per (ray, instance).
  * vmargin (may be NULL): per pixel, the smallest cull-discriminant / rb^2 and entry-distance
  * difference between consecutive pairs (the decisions a rounding change could flip). */
@@ -176,6 +183,11 @@ uint64_t orc_splitmix64(uint64_t seed, uint64_t index);
 void orc_train_rays(double rb, uint64_t seed, int64_t first, int n, double *o, double *d);
 void orc_train_labels(const orc_scene *sc, int type, int n, const double *o, const double *d,
                       int march_n, int march_b, double *m_star, int *hit_star);
+/* Loss (the regression form of Eq. 6, reading 18) and its gradient by hand.  quant = BF16 is the
+ * BF16 training of reading 29: forward operands (weights, layer inputs) rounded to BF16; in the
+ * backward pass the weights and the saved activations are the BF16 values and each hidden layer's
+ * error signal is rounded to BF16 before its weight product, bias sum and input-gradient product;
+ * the loss derivative at the output stays unrounded. */
 double orc_nedf_loss_grad(const orc_scene *sc, int type, int n, const double *o, const double *d,
                           const double *m_star, const int *hit_star, double *grad, int quant);
 void orc_adam(int64_t n, double *theta, const double *g, double *m, double *v, int t, double lr,

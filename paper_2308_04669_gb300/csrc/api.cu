@@ -1167,6 +1167,14 @@ int nedf_compose_make_labels_density(nedf_handle *h, int type, int64_t n_rays, u
     return copy_train_set(h, type, n_rays, o, d, m_star, hit_star);
 }
 
+// BF16 and E4M3 handles train the regression NeDF with BF16 operands on the tensor cores; FP32
+// handles (and shapes the tensor-core path does not take) keep the FP32 CUDA-core path.
+static bool train_on_tensor_cores(const nedf_handle *h)
+{
+    return h->cfg.nedf_arch != NEDF_ARCH_CLASSIFIER && h->cfg.precision != NEDF_PREC_FP32 &&
+           train_tc_supported(h->cfg.nedf_width, h->cfg.nedf_hidden);
+}
+
 static int ensure_train_scratch(nedf_handle *h, int batch)
 {
     const bool cls = h->cfg.nedf_arch == NEDF_ARCH_CLASSIFIER;
@@ -1178,7 +1186,8 @@ static int ensure_train_scratch(nedf_handle *h, int batch)
     }
     if (cls && cublasSetStream(h->cublas, h->stream) != CUBLAS_STATUS_SUCCESS) return fail(h, NEDF_ERR_CUDA, "cublasSetStream");
     size_t need = cls ? cls_train_scratch_bytes(batch)
-                      : train_scratch_bytes(batch, h->cfg.nedf_hidden, h->cfg.nedf_width, h->nedf_params);
+                  : train_on_tensor_cores(h) ? train_tc_scratch_bytes(batch, h->cfg.nedf_hidden, h->cfg.nedf_width, h->nedf_params)
+                                             : train_scratch_bytes(batch, h->cfg.nedf_hidden, h->cfg.nedf_width, h->nedf_params);
     if (need > h->train_scratch_bytes) {
         if (h->d_train_scratch) cudaFree(h->d_train_scratch);
         h->d_train_scratch = nullptr;
@@ -1214,6 +1223,7 @@ static TrainLaunch make_train_launch(nedf_handle *h, int type)
     L.kernel_w = h->d_nedf_w + (size_t)type * h->nedf_params;
     L.scratch = h->d_train_scratch;
     L.loss = h->d_loss;
+    L.status = h->d_status;
     L.num_sms = h->num_sms;
     L.stream = h->stream;
     return L;
@@ -1229,6 +1239,8 @@ int nedf_compose_loss_grad(nedf_handle *h, int type, int n, const float *o, cons
     if (r != NEDF_OK) return r;
     if (h->cfg.nedf_arch == NEDF_ARCH_CLASSIFIER) {
         CK(h, launch_cls_loss_grad(make_cls_train_launch(h, type), o, d, m_star, hit_star, n, grad));
+    } else if (train_on_tensor_cores(h)) {
+        CK(h, launch_loss_grad_tc(make_train_launch(h, type), o, d, m_star, hit_star, n, grad));
     } else {
         TrainLaunch L = make_train_launch(h, type);
         CK(h, launch_loss_grad(L, o, d, m_star, hit_star, n, grad));
@@ -1254,6 +1266,9 @@ int nedf_compose_train_step(nedf_handle *h, int type, int batch, float lr, float
     if (h->cfg.nedf_arch == NEDF_ARCH_CLASSIFIER) {
         CK(h, launch_cls_train_step(make_cls_train_launch(h, type), ts.o, ts.d, ts.m_star, ts.hit_star, ts.n_rays,
                                     ts.cursor, batch, ts.adam_m, ts.adam_v, ts.step, lr));
+    } else if (train_on_tensor_cores(h)) {
+        CK(h, launch_train_step_tc(make_train_launch(h, type), ts.o, ts.d, ts.m_star, ts.hit_star, ts.n_rays,
+                                   ts.cursor, batch, ts.adam_m, ts.adam_v, ts.step, lr));
     } else {
         TrainLaunch L = make_train_launch(h, type);
         CK(h, launch_train_step(L, ts.o, ts.d, ts.m_star, ts.hit_star, ts.n_rays, ts.cursor, batch, ts.adam_m,

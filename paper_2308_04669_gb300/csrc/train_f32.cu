@@ -532,9 +532,14 @@ cudaError_t launch_train_step(const TrainLaunch &L, const float *o, const float 
     TrainScratch s = carve(L.scratch, batch, L.hidden, L.width, L.n_params);
     cudaError_t e = fwd_bwd(L, o, d, m_star, hit_star, start, n_rays, batch, s);
     if (e != cudaSuccess) return e;
+    return launch_adam(L, s.grad, adam_m, adam_v, step, lr);
+}
+
+cudaError_t launch_adam(const TrainLaunch &L, const float *grad, float *adam_m, float *adam_v, int step, float lr)
+{
     float c1 = (float)(1.0 - std::pow(0.9, step)), c2 = (float)(1.0 - std::pow(0.999, step));
     int blocks = (int)std::min<long long>((L.n_params + 255) / 256, (long long)L.num_sms * 8);
-    k_adam<<<blocks, 256, 0, L.stream>>>(L.master, L.kernel_w, s.grad, adam_m, adam_v, L.n_params, L.hidden, L.width,
+    k_adam<<<blocks, 256, 0, L.stream>>>(L.master, L.kernel_w, grad, adam_m, adam_v, L.n_params, L.hidden, L.width,
                                          lr, c1, c2, 1);
     return cudaGetLastError();
 }

@@ -14,11 +14,26 @@ struct TrainLaunch {
     float *kernel_w;         // the renderer's copy (per layer Wt[in][out] then b)
     float *scratch;          // activations, deltas, gradient (train_scratch_bytes)
     float *loss;             // device float[4]: loss, hit count, row count
+    uint32_t *status;        // device status word (bounded waits of the tensor-core path)
     int num_sms;
     cudaStream_t stream;
 };
 
 size_t train_scratch_bytes(int batch, int hidden, int width, long long n_params);
+
+// Adam (beta 0.9 / 0.999, eps 1e-8, bias-corrected) on the master weights with the given gradient;
+// the renderer's FP32 copy is rewritten in the same pass.
+cudaError_t launch_adam(const TrainLaunch &L, const float *grad, float *adam_m, float *adam_v, int step, float lr);
+
+// The same step with BF16 operands on the tensor cores (train_tc.cu), widths 64 and 128: products
+// in tcgen05 GEMMs with FP32 accumulation, FP32 master weights and Adam.
+bool train_tc_supported(int width, int hidden);
+size_t train_tc_scratch_bytes(int batch, int hidden, int width, long long n_params);
+cudaError_t launch_loss_grad_tc(const TrainLaunch &L, const float *o, const float *d, const float *m_star,
+                                const float *hit_star, int n, float *grad);
+cudaError_t launch_train_step_tc(const TrainLaunch &L, const float *o, const float *d, const float *m_star,
+                                 const float *hit_star, long long n_rays, long long start, int batch, float *adam_m,
+                                 float *adam_v, int step, float lr);
 
 cudaError_t launch_make_labels(const DevType *type, float rb, long long n_rays, uint64_t seed, int steps,
                                int bisect, float *o, float *d, float *m_star, float *hit_star, int num_sms,

@@ -1,0 +1,423 @@
+// Learned part on the tensor cores: BF16 NeDF training with FP32 accumulation, FP32 master weights
+// and Adam (Section "Intersection network": supervision of F_Phi through Eq. 2 and Eq. 5; the
+// regression form of Eq. 6; "Training details": Adam).
+//
+// A step on a batch of B rows, width W, L hidden layers (all products tcgen05 GEMMs, tc_gemm.cuh):
+//   encode    X0[b] = BF16(gamma([p_e, d])) (78 features, 2 zero pads)              CUDA cores
+//   forward   H_{l+1} = BF16(ReLU(H_l Wb_l^T + b_l)),  l = 0 .. L-1                   M = B, N = W
+//   loss      y = W_out H_L + b_out (FP32), the loss of Eq. 6 (regression form), dy,
+//             dZ_{L-1} = BF16((W_out^T dy) * [H_L > 0]), and dW_out, db_out per split  CUDA cores
+//   backward  dZ_{l-1} = BF16((dZ_l Wb_l) * [H_l > 0]),  l = L-1 .. 1                 M = B, N = W
+//   weights   [dW_l | db_l] = dZ_l^T [H_l | 1]  (split-K over the batch, all layers in one launch)
+//   then the split partials are summed in a fixed order and Adam updates the FP32 master.
+// Activations and error signals are BF16 operands (reading 29 of the oracle: the error signal of a
+// hidden layer is rounded to BF16 where it enters a product); every sum is FP32.  The split sums
+// keep a step deterministic, so a resumed run repeats an uninterrupted one bit for bit.
+#include <algorithm>
+#include <cmath>
+
+#include "mlp_f32.cuh"
+#include "tc_gemm.cuh"
+#include "train_launch.h"
+
+namespace nedf {
+
+using tcg::Operand;
+
+constexpr int kTcSplitRows = 1024;       // batch rows per weight-gradient split (a multiple of 64)
+constexpr int kTcStages = 3;
+
+// ---- scratch ----------------------------------------------------------------------------------
+struct TcTrainScratch {
+    __nv_bfloat16 *x0;           // [B][80]
+    __nv_bfloat16 *h[17];        // h[l]: [B][W], l = 1 .. L
+    __nv_bfloat16 *dz[16];       // dz[l]: [B][W], l = 0 .. L-1
+    __nv_bfloat16 *wb;           // BF16 weights: layer 0 [W][80], layers 1 .. L-1 [W][W], output [2][W]
+    float *dy;                   // [B][2]
+    float *grad;                 // [n_params]
+    float *partial;              // [splits][n_params]
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+__host__ __device__ __forceinline__ long long wb_elems(int L, int W) { return (long long)W * kNedfInPad + (long long)(L - 1) * W * W + 2LL * W; }
+
+size_t train_tc_scratch_bytes(int batch, int hidden, int width, long long n_params)
+{
+    const size_t B = (size_t)batch, splits = (B + kTcSplitRows - 1) / kTcSplitRows;
+    size_t bytes = align256(B * kNedfInPad * 2) + 2 * (size_t)hidden * align256(B * width * 2) +
+                   align256((size_t)wb_elems(hidden, width) * 2) + align256(B * 2 * 4) + align256(n_params * 4) +
+                   splits * (size_t)n_params * 4;
+    return bytes + 256;
+}
+
+static TcTrainScratch carve_tc(void *base, int B, int L, int W, long long n_params)
+{
+    TcTrainScratch s{};
+    uint8_t *p = reinterpret_cast<uint8_t *>(align256(reinterpret_cast<size_t>(base)));
+    s.x0 = reinterpret_cast<__nv_bfloat16 *>(p); p += align256((size_t)B * kNedfInPad * 2);
+    for (int l = 1; l <= L; ++l) { s.h[l] = reinterpret_cast<__nv_bfloat16 *>(p); p += align256((size_t)B * W * 2); }
+    for (int l = 0; l < L; ++l) { s.dz[l] = reinterpret_cast<__nv_bfloat16 *>(p); p += align256((size_t)B * W * 2); }
+    s.wb = reinterpret_cast<__nv_bfloat16 *>(p); p += align256((size_t)wb_elems(L, W) * 2);
+    s.dy = reinterpret_cast<float *>(p); p += align256((size_t)B * 2 * 4);
+    s.grad = reinterpret_cast<float *>(p); p += align256((size_t)n_params * 4);
+    s.partial = reinterpret_cast<float *>(p);
+    return s;
+}
+
+// offset of layer l's weights in the packed layout (W[out][in] then b[out] per layer)
+__host__ __device__ __forceinline__ long long packed_off(int l, int W)
+{
+    return l == 0 ? 0 : (long long)kNedfIn * W + W + (long long)(l - 1) * (W * W + W);
+}
+// offset of layer l's BF16 weights in wb
+__host__ __device__ __forceinline__ long long wb_off(int l, int W)
+{
+    return l == 0 ? 0 : (long long)W * kNedfInPad + (long long)(l - 1) * W * W;
+}
+
+// ---- BF16 weights from the FP32 master ----------------------------------------------------------
+__global__ void k_tc_pack_weights(const float *master, __nv_bfloat16 *wb, int L, int W)
+{
+    const long long n = wb_elems(L, W);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        float v = 0.0f;
+        if (e < (long long)W * kNedfInPad) {                        // layer 0, padded to 80 inputs
+            const int o = (int)(e / kNedfInPad), i = (int)(e % kNedfInPad);
+            v = i < kNedfIn ? master[(long long)o * kNedfIn + i] : 0.0f;
+        } else {
+            long long r = e - (long long)W * kNedfInPad;
+            const long long hid = (long long)(L - 1) * W * W;
+            if (r < hid) {
+                const int l = 1 + (int)(r / ((long long)W * W));
+                v = master[packed_off(l, W) + r % ((long long)W * W)];
+            } else {
+                v = master[packed_off(L, W) + (r - hid)];            // output layer [2][W]
+            }
+        }
+        wb[e] = __float2bfloat16_rn(v);
+    }
+}
+
+// ---- encoding ------------------------------------------------------------------------------------
+__global__ void k_tc_encode(float rb, const float *o, const float *d, long long start, long long n, int B,
+                            __nv_bfloat16 *x0, float *loss_hits, const float *hit_star)
+{
+    float hits = 0.0f;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x) {
+        const long long i = (start + b) % n;
+        const V3 ol = v3(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
+        const V3 dl = normalized(v3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
+        Chord ch;
+        float x6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (bound_chord(ol, dl, rb, ch)) {
+            const V3 pe = madd(ol, ch.te, dl);
+            x6[0] = pe.x; x6[1] = pe.y; x6[2] = pe.z; x6[3] = dl.x; x6[4] = dl.y; x6[5] = dl.z;
+        }
+        uint32_t pk[kNedfInPad / 2];
+        for (int f = 0; f < kNedfInPad; f += 2) {
+            const float a = f < kNedfIn ? posenc_feature(x6, 6, 6, f) : 0.0f;
+            const float c = f + 1 < kNedfIn ? posenc_feature(x6, 6, 6, f + 1) : 0.0f;
+            pk[f / 2] = tc::pack_bf16(a, c);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(x0 + b * kNedfInPad);
+        for (int q = 0; q < kNedfInPad / 8; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        hits += hit_star[i];
+    }
+    for (int off = 16; off; off >>= 1) hits += __shfl_down_sync(0xffffffffu, hits, off);
+    if ((threadIdx.x & 31) == 0 && hits != 0.0f) atomicAdd(loss_hits, hits);
+}
+
+// ---- GEMM epilogues --------------------------------------------------------------------------------
+// forward: out[row][n] = BF16(ReLU(acc + bias[n]))
+struct EpiForward {
+    __nv_bfloat16 *out;
+    const float *bias;
+    int M, W;
+    __device__ __forceinline__ void operator()(int row, int c0, const uint32_t (&v)[32]) const
+    {
+        if (row >= M || c0 >= W) return;
+        uint32_t pk[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            pk[i] = tc::pack_bf16_relu(__uint_as_float(v[2 * i]) + __ldg(bias + c0 + 2 * i),
+                                       __uint_as_float(v[2 * i + 1]) + __ldg(bias + c0 + 2 * i + 1));
+        uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)row * W + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    }
+};
+
+// backward: out[row][n] = BF16(acc * [h[row][n] > 0])
+struct EpiBackward {
+    __nv_bfloat16 *out;
+    const __nv_bfloat16 *h;
+    int M, W;
+    __device__ __forceinline__ void operator()(int row, int c0, const uint32_t (&v)[32]) const
+    {
+        if (row >= M || c0 >= W) return;
+        const uint4 *hs = reinterpret_cast<const uint4 *>(h + (size_t)row * W + c0);
+        uint32_t pk[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 hv = hs[q];
+            const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = 4 * q + j;
+                // a BF16 activation is positive iff its low and high halves have sign 0 and are nonzero
+                const float m0 = ((hw[j] & 0xFFFFu) != 0u && !(hw[j] & 0x8000u)) ? 1.0f : 0.0f;
+                const float m1 = ((hw[j] >> 16) != 0u && !(hw[j] & 0x80000000u)) ? 1.0f : 0.0f;
+                pk[i] = tc::pack_bf16(__uint_as_float(v[2 * i]) * m0, __uint_as_float(v[2 * i + 1]) * m1);
+            }
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)row * W + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    }
+};
+
+// weight gradient of one layer, one split: row = output feature, column n < fi: dW[row][n],
+// column n == ones (the synthesized column of ones): db[row]; written into the split's partial
+// gradient in the packed layout
+struct EpiWeightGrad {
+    float *partial;              // this layer's block of split 0
+    long long split_stride;
+    int fo, fi, ones;
+    __device__ __forceinline__ void operator()(int row, int c0, const uint32_t (&v)[32]) const
+    {
+        if (row >= fo) return;
+        float *p = partial + blockIdx.z * split_stride;       // blockIdx.z: the split
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int n = c0 + i;
+            if (n < fi) p[(long long)row * fi + n] = __uint_as_float(v[i]);
+            else if (n == ones) p[(long long)fo * fi + row] = __uint_as_float(v[i]);
+        }
+    }
+};
+
+// One 128 x BN tile per CTA: blockIdx.x = 128-row block of M (N fits one block).
+template <int BN, class Epi>
+__global__ void __launch_bounds__(tcg::kThreads) k_tc_gemm(Operand A, Operand B, long long k_total, Epi epi,
+                                                           uint32_t *status)
+{
+    tcg::gemm_tile<BN, kTcStages>(A, B, blockIdx.x * tcg::kBM, 0, 0, k_total, epi, status, kStatusTimeout);
+}
+
+// The weight and bias gradients of every hidden layer in one launch: blockIdx.y = layer,
+// blockIdx.z = split of the batch (rows z * split_rows .. ), each layer's [dW | db] one tile.
+struct WgradLayers {
+    Operand a[16], b[16];
+    EpiWeightGrad epi[16];
+};
+
+template <int BN>
+__global__ void __launch_bounds__(tcg::kThreads) k_tc_wgrad(WgradLayers P, long long k_total, int split_rows,
+                                                            uint32_t *status)
+{
+    const int l = blockIdx.y;
+    const long long kb = (long long)blockIdx.z * split_rows;
+    const long long ke = kb + split_rows < k_total ? kb + split_rows : k_total;
+    tcg::gemm_tile<BN, kTcStages>(P.a[l], P.b[l], 0, 0, kb, ke, P.epi[l], status, kStatusTimeout);
+}
+
+// ---- loss, output layer, first error signal ----------------------------------------------------
+// One thread per row: y = W_out h_L + b_out with the BF16 output weights, the loss terms and
+// dL/dy, and dZ_{L-1} = BF16((W_out^T dy) * [h_L > 0]).
+template <int W>
+__global__ void k_tc_loss(const __nv_bfloat16 *hL, const __nv_bfloat16 *wout, const float *bout, const float *o,
+                          const float *d, const float *m_star, const float *hit_star, float rb, long long start,
+                          long long n, int B, float *dy, __nv_bfloat16 *dz, float *loss)
+{
+    __shared__ float wsm[2][W];
+    __shared__ float red[32];
+    for (int k = threadIdx.x; k < 2 * W; k += blockDim.x) wsm[k / W][k % W] = __bfloat162float(wout[k]);
+    __syncthreads();
+    const float n_hit = loss[1];
+    float part = 0.0f;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x) {
+        const long long i = (start + b) % n;
+        const V3 ol = v3(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
+        const V3 dl = normalized(v3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
+        Chord ch;
+        const bool kept = bound_chord(ol, dl, rb, ch);
+        const uint4 *hrow = reinterpret_cast<const uint4 *>(hL + (size_t)b * W);
+        float y0 = bout[0], y1 = bout[1];
+        for (int q = 0; q < W / 8; ++q) {
+            const uint4 hv = hrow[q];
+            const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+            for (int j = 0; j < 4; ++j) {
+                const float a = __uint_as_float(hw[j] << 16), c = __uint_as_float(hw[j] & 0xFFFF0000u);
+                const int k = 8 * q + 2 * j;
+                y0 = fmaf(wsm[0][k], a, fmaf(wsm[0][k + 1], c, y0));
+                y1 = fmaf(wsm[1][k], a, fmaf(wsm[1][k + 1], c, y1));
+            }
+        }
+        float dm = 0.0f, da = 0.0f;
+        if (kept) {
+            const float al = hit_star[i];
+            const float bce = fmaxf(y1, 0.0f) - al * y1 + log1pf(expf(-fabsf(y1)));
+            part += 0.1f * bce / (float)B;
+            if (al > 0.5f) {
+                const float e = y0 - m_star[i];
+                part += e * e / n_hit;
+                dm = 2.0f * e / n_hit;
+            }
+            da = 0.1f * (1.0f / (1.0f + expf(-y1)) - al) / (float)B;
+        }
+        dy[2 * b] = dm;
+        dy[2 * b + 1] = da;
+        uint4 *dst = reinterpret_cast<uint4 *>(dz + (size_t)b * W);
+        for (int q = 0; q < W / 8; ++q) {
+            const uint4 hv = hrow[q];
+            const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+            uint32_t pk[4];
+            for (int j = 0; j < 4; ++j) {
+                const int k = 8 * q + 2 * j;
+                const float g0 = (hw[j] & 0xFFFFu) != 0u && !(hw[j] & 0x8000u) ? wsm[0][k] * dm + wsm[1][k] * da : 0.0f;
+                const float g1 = (hw[j] >> 16) != 0u && !(hw[j] & 0x80000000u) ? wsm[0][k + 1] * dm + wsm[1][k + 1] * da
+                                                                                 : 0.0f;
+                pk[j] = tc::pack_bf16(g0, g1);
+            }
+            dst[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+    }
+    for (int off = 16; off; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+        atomicAdd(&loss[0], t);
+    }
+}
+
+// Output-layer gradient of one split (blockIdx.x): dW_out[o][k] = sum_b dy[b][o] h_L[b][k] and
+// db_out[o] = sum_b dy[b][o] over the split's rows, in row order, into the split's partial.
+template <int W>
+__global__ void k_tc_out_grad(const __nv_bfloat16 *hL, const float *dy, int B, int rows_per_split, float *partial,
+                              long long split_stride, long long off)
+{
+    const int r0 = blockIdx.x * rows_per_split, r1 = min(B, r0 + rows_per_split);
+    float *p = partial + blockIdx.x * split_stride + off;
+    for (int j = threadIdx.x; j < 2 * W + 2; j += blockDim.x) {
+        float acc = 0.0f;
+        if (j < 2 * W) {
+            const int o = j / W, k = j % W;
+            for (int b = r0; b < r1; ++b) acc = fmaf(dy[2 * b + o], __bfloat162float(hL[(size_t)b * W + k]), acc);
+            p[(long long)o * W + k] = acc;
+        } else {
+            const int o = j - 2 * W;
+            for (int b = r0; b < r1; ++b) acc += dy[2 * b + o];
+            p[2LL * W + o] = acc;
+        }
+    }
+}
+
+__global__ void k_tc_sum_splits(const float *partial, int splits, long long n, float *grad)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float acc = 0.0f;
+        for (int z = 0; z < splits; ++z) acc += partial[(size_t)z * n + i];
+        grad[i] = acc;
+    }
+}
+
+// ---- one forward / backward pass ----------------------------------------------------------------
+template <int BN, class Epi>
+static cudaError_t gemm(const Operand &A, const Operand &B, int m_blocks, long long k_total, const Epi &epi,
+                        uint32_t *status, cudaStream_t st)
+{
+    using SM = tcg::GemmSmem<BN, kTcStages>;
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::BYTES);
+    if (e != cudaSuccess) return e;
+    k_tc_gemm<BN, Epi><<<m_blocks, tcg::kThreads, SM::BYTES, st>>>(A, B, k_total, epi, status);
+    return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t run_tc(const TrainLaunch &L, const float *o, const float *d, const float *m_star,
+                          const float *hit_star, long long start, long long n, int B, TcTrainScratch s)
+{
+    cudaStream_t st = L.stream;
+    const int nl = L.hidden;
+    cudaError_t e = cudaMemsetAsync(L.loss, 0, sizeof(float) * 4, st);
+    if (e != cudaSuccess) return e;
+    k_tc_pack_weights<<<L.num_sms * 2, 256, 0, st>>>(L.master, s.wb, nl, W);
+    const int eb = (int)std::min<long long>((B + 255) / 256, (long long)L.num_sms * 8);
+    k_tc_encode<<<eb, 256, 0, st>>>(L.rb, o, d, start, n, B, s.x0, L.loss + 1, hit_star);
+    const int mb = (B + tcg::kBM - 1) / tcg::kBM;
+    // forward
+    for (int l = 0; l < nl; ++l) {
+        const int fi = l == 0 ? kNedfInPad : W;
+        const Operand A{l == 0 ? s.x0 : s.h[l], fi, B, fi, tcg::kKMajor, -1};
+        const Operand Bw{s.wb + wb_off(l, W), fi, W, fi, tcg::kKMajor, -1};
+        const EpiForward epi{s.h[l + 1], L.master + packed_off(l, W) + (long long)(l == 0 ? kNedfIn : W) * W, B, W};
+        if ((e = gemm<W>(A, Bw, mb, fi, epi, L.status, st)) != cudaSuccess) return e;
+    }
+    // loss, dy, first error signal
+    k_tc_loss<W><<<eb, 256, 0, st>>>(s.h[nl], s.wb + wb_off(nl, W), L.master + packed_off(nl, W) + 2LL * W, o, d, m_star,
+                                     hit_star, L.rb, start, n, B, s.dy, s.dz[nl - 1], L.loss);
+    // backward through the hidden layers
+    for (int l = nl - 1; l >= 1; --l) {
+        const Operand A{s.dz[l], W, B, W, tcg::kKMajor, -1};
+        const Operand Bw{s.wb + wb_off(l, W), W, W, W, tcg::kMNMajor, -1};       // element (i, o) = W_l[o][i]
+        const EpiBackward epi{s.dz[l - 1], s.h[l], B, W};
+        if ((e = gemm<W>(A, Bw, mb, W, epi, L.status, st)) != cudaSuccess) return e;
+    }
+    // weight and bias gradients of every hidden layer, split over the batch, one launch
+    const int splits = (B + kTcSplitRows - 1) / kTcSplitRows;
+    WgradLayers P{};
+    for (int l = 0; l < nl; ++l) {
+        const int fi = l == 0 ? kNedfIn : W, fip = l == 0 ? kNedfInPad : W;
+        P.a[l] = Operand{s.dz[l], W, W, B, tcg::kMNMajor, -1};                    // (o, b) = dZ_l[b][o]
+        P.b[l] = Operand{l == 0 ? s.x0 : s.h[l], fip, fip, B, tcg::kMNMajor, fip}; // (i, b) = H_l[b][i]; row fip = 1
+        P.epi[l] = EpiWeightGrad{s.partial + packed_off(l, W), L.n_params, W, fi, fip};
+    }
+    {
+        constexpr int BN = W + 16;
+        using SM = tcg::GemmSmem<BN, kTcStages>;
+        if ((e = cudaFuncSetAttribute(k_tc_wgrad<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::BYTES)) !=
+            cudaSuccess)
+            return e;
+        k_tc_wgrad<BN><<<dim3(1, nl, splits), tcg::kThreads, SM::BYTES, st>>>(P, B, kTcSplitRows, L.status);
+    }
+    k_tc_out_grad<W><<<splits, 256, 0, st>>>(s.h[nl], s.dy, B, kTcSplitRows, s.partial, L.n_params, packed_off(nl, W));
+    k_tc_sum_splits<<<(int)std::min<long long>((L.n_params + 255) / 256, (long long)L.num_sms * 8), 256, 0, st>>>(
+        s.partial, splits, L.n_params, s.grad);
+    return cudaGetLastError();
+}
+
+static cudaError_t tc_fwd_bwd(const TrainLaunch &L, const float *o, const float *d, const float *m_star,
+                              const float *hit_star, long long start, long long n, int B, TcTrainScratch s)
+{
+    switch (L.width) {
+    case 64: return run_tc<64>(L, o, d, m_star, hit_star, start, n, B, s);
+    case 128: return run_tc<128>(L, o, d, m_star, hit_star, start, n, B, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+bool train_tc_supported(int width, int hidden) { return (width == 64 || width == 128) && hidden >= 1 && hidden <= 16; }
+
+cudaError_t launch_loss_grad_tc(const TrainLaunch &L, const float *o, const float *d, const float *m_star,
+                                const float *hit_star, int n, float *grad)
+{
+    TcTrainScratch s = carve_tc(L.scratch, n, L.hidden, L.width, L.n_params);
+    cudaError_t e = tc_fwd_bwd(L, o, d, m_star, hit_star, 0, n, n, s);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(grad, s.grad, sizeof(float) * L.n_params, cudaMemcpyDeviceToDevice, L.stream);
+}
+
+cudaError_t launch_train_step_tc(const TrainLaunch &L, const float *o, const float *d, const float *m_star,
+                                 const float *hit_star, long long n_rays, long long start, int batch, float *adam_m,
+                                 float *adam_v, int step, float lr)
+{
+    TcTrainScratch s = carve_tc(L.scratch, batch, L.hidden, L.width, L.n_params);
+    cudaError_t e = tc_fwd_bwd(L, o, d, m_star, hit_star, start, n_rays, batch, s);
+    if (e != cudaSuccess) return e;
+    return launch_adam(L, s.grad, adam_m, adam_v, step, lr);
+}
+
+}  // namespace nedf

@@ -14,7 +14,7 @@ import pytest
 
 from paper_2308_04669_gb300 import scenegen as sg
 
-from .gpu_helpers import NOID, check_network_rows, compare_frame, compare_volume, gpu_frame
+from .gpu_helpers import NOID, check_network_rows, compare_volume, frame_vs_oracle, gpu_frame
 from .test_gpu_tc import query_features, query_rays, run_query
 
 pytestmark = pytest.mark.gpu
@@ -54,9 +54,8 @@ def test_fp8_shading_matches_fp8_oracle(orc):
     sc = sg.three_types_scene(128, 128)
     px = sg.pixel_subset(128, 128, 800, 8)
     g = gpu_frame(sc, precision=native.PREC_FP8, depth_source=1)
-    o = orc.render(orc.OracleScene(sc), px=px, depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4,
-                   quant=orc.QUANT_FP8, n_threads=8)
-    rep = compare_frame(g, o, px, colour_tol=FP8_COLOUR_TOL)
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc), px=px, depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4,
+                             quant=orc.QUANT_FP8, n_threads=8, colour_tol=FP8_COLOUR_TOL)
     assert rep["hit"] > 200
     hit = o["id"] != NOID
     assert (o["rgba"][hit][:, 3] > 0.3).mean() > 0.5
@@ -71,8 +70,7 @@ def test_fp8_frame_with_refinement_matches_fp8_oracle(orc):
     px = sg.pixel_subset(128, 128, 600, 10)
     kw = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1)
     g = gpu_frame(sc, precision=native.PREC_FP8, **kw)
-    o = orc.render(orc.OracleScene(sc), px=px, quant=orc.QUANT_FP8, march_n=128, march_b=4, n_threads=8, **kw)
-    rep = compare_frame(g, o, px, max_excluded=0.1, colour_tol=FP8_COLOUR_TOL)
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc), px=px, quant=orc.QUANT_FP8, march_n=128, march_b=4, n_threads=8, **kw, max_excluded=0.1, colour_tol=FP8_COLOUR_TOL)
     assert rep["hit"] > 100
     assert g["stats"].fallback_pairs > 0 and g["stats"].status == 0
 

@@ -4,7 +4,7 @@ import pytest
 
 from paper_2308_04669_gb300 import scenegen as sg
 
-from .gpu_helpers import NOID, close, compare_frame, compare_volume, gpu_frame
+from .gpu_helpers import NOID, close, compare_volume, frame_vs_oracle, gpu_frame
 
 pytestmark = pytest.mark.gpu
 
@@ -21,8 +21,7 @@ def test_tiny_sphere_full_frame_nedf(orc):
     """64x64, one sphere, NeDF 4x64 (random init): every pixel, every buffer."""
     sc = sg.tiny_sphere_scene()
     g = gpu_frame(sc)
-    o = orc.render(orc.OracleScene(sc))
-    rep = compare_frame(g, o, o["px"])
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc))
     assert rep["hit"] > 1000
     assert g["stats"].status == 0
 
@@ -31,8 +30,7 @@ def test_tiny_sphere_full_frame_march(orc):
     """Same scene answered by the plain method (surface depths, real shading and shadows)."""
     sc = sg.tiny_sphere_scene()
     g = gpu_frame(sc, depth_source=1, march_steps=128, march_bisect=4)
-    o = orc.render(orc.OracleScene(sc), depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4)
-    rep = compare_frame(g, o, o["px"])
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc), depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4)
     assert rep["hit"] > 500 and rep["shadowed"] > 50
     assert (o["rgba"][:, 3] > 0.5).sum() > 500
 
@@ -41,8 +39,7 @@ def test_tiny_sphere_full_frame_march(orc):
 def test_ragged_sizes(orc, W, H):
     sc = sg.three_types_scene(W, H, nerf=False)
     g = gpu_frame(sc)
-    o = orc.render(orc.OracleScene(sc))
-    compare_frame(g, o, o["px"], max_excluded=0.2 if W * H < 10 else 0.05)
+    o = frame_vs_oracle(g, orc.OracleScene(sc), max_excluded=0.2 if W * H < 10 else 0.05)[1]
 
 
 def test_three_types_nerf_subset(orc):
@@ -51,9 +48,8 @@ def test_three_types_nerf_subset(orc):
     px = sg.pixel_subset(128, 128, 600, 5)
     for mode, kw in [(0, {}), (1, dict(depth_source=1))]:
         g = gpu_frame(sc, **kw)
-        o = orc.render(orc.OracleScene(sc), px=px, depth_mode=orc.DEPTH_MLP if mode == 0 else orc.DEPTH_MARCH,
-                       march_n=128, march_b=4, n_threads=8)
-        rep = compare_frame(g, o, px)
+        rep, o = frame_vs_oracle(g, orc.OracleScene(sc), px=px, march_n=128, march_b=4, n_threads=8,
+                                 depth_mode=orc.DEPTH_MLP if mode == 0 else orc.DEPTH_MARCH)
         assert rep["hit"] > 30
 
 
@@ -62,8 +58,7 @@ def test_three_types_full_size_sampled(orc):
     sc = sg.three_types_scene()
     px = sg.pixel_subset(512, 512, 300, 6)
     g = gpu_frame(sc, depth_source=1)
-    o = orc.render(orc.OracleScene(sc), px=px, depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4, n_threads=8)
-    compare_frame(g, o, px)
+    o = frame_vs_oracle(g, orc.OracleScene(sc), px=px, depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4, n_threads=8)[1]
 
 
 def test_thousand_instances_sampled(orc):
@@ -71,8 +66,7 @@ def test_thousand_instances_sampled(orc):
     sc = sg.thousand_scene()
     px = sg.pixel_subset(1024, 1024, 200, 7)
     g = gpu_frame(sc)
-    o = orc.render(orc.OracleScene(sc), px=px, n_threads=8)
-    rep = compare_frame(g, o, px)
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc), px=px, n_threads=8)
     assert g["stats"].status == 0 and g["stats"].primary_pairs > 500000
 
 
@@ -81,8 +75,7 @@ def test_refine_and_outlier_resample_fp32(orc):
     sc = sg.three_types_scene(96, 96, nerf=False)
     kw = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1)
     g = gpu_frame(sc, **kw)
-    o = orc.render(orc.OracleScene(sc), march_n=128, march_b=4, n_threads=8, **kw)
-    rep = compare_frame(g, o, o["px"], max_excluded=0.08)
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc), march_n=128, march_b=4, n_threads=8, **kw, max_excluded=0.08)
     assert g["stats"].fallback_pairs > 0 and rep["hit"] > 500
 
 
@@ -91,8 +84,7 @@ def test_light_inside_scene_bound(orc):
     sc = sg.three_types_scene(96, 96, nerf=False)
     sc.lights = sg.f32([[0.3, 0.2, -0.1], [1.0, 9.0, 2.0]])
     g = gpu_frame(sc, depth_source=1)
-    o = orc.render(orc.OracleScene(sc), depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4, n_threads=8)
-    rep = compare_frame(g, o, o["px"])
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc), depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4, n_threads=8)
     assert rep["shadowed"] > 50
 
 
@@ -107,12 +99,10 @@ def test_parallel_lights(orc, precision):
     sc.light_parallel = np.array([1, 0])
     if precision == "fp32":
         g = gpu_frame(sc, depth_source=1)
-        o = orc.render(orc.OracleScene(sc), depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4, n_threads=8)
-        rep = compare_frame(g, o, o["px"])
+        rep, o = frame_vs_oracle(g, orc.OracleScene(sc), depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4, n_threads=8)
     else:
         g = gpu_frame(sc, precision=native.PREC_BF16)
-        o = orc.render(orc.OracleScene(sc), quant=orc.QUANT_BF16, n_threads=8)
-        rep = compare_frame(g, o, o["px"], max_excluded=0.1)
+        rep, o = frame_vs_oracle(g, orc.OracleScene(sc), quant=orc.QUANT_BF16, n_threads=8, max_excluded=0.1)
     assert rep["shadowed"] > 50 and g["stats"].status == 0
 
 

@@ -13,7 +13,7 @@ import pytest
 
 from paper_2308_04669_gb300 import scenegen as sg
 
-from .gpu_helpers import NOID, check_network_rows, compare_frame, compare_volume, gpu_frame
+from .gpu_helpers import NOID, check_network_rows, compare_volume, frame_vs_oracle, gpu_frame
 
 pytestmark = pytest.mark.gpu
 
@@ -85,9 +85,8 @@ def test_bf16_shading_matches_bf16_oracle(orc):
     sc = sg.three_types_scene(128, 128)
     px = sg.pixel_subset(128, 128, 800, 8)
     g = gpu_frame(sc, precision=native.PREC_BF16, depth_source=1)
-    o = orc.render(orc.OracleScene(sc), px=px, depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4,
-                   quant=orc.QUANT_BF16, n_threads=8)
-    rep = compare_frame(g, o, px)
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc), px=px, depth_mode=orc.DEPTH_MARCH, march_n=128, march_b=4,
+                             quant=orc.QUANT_BF16, n_threads=8)
     assert rep["hit"] > 200 and rep["colour_max_err"] < 5e-4
     hit = o["id"] != NOID
     assert (o["rgba"][hit][:, 3] > 0.3).mean() > 0.5
@@ -100,8 +99,7 @@ def test_bf16_full_frame_nedf(orc):
     sc = sg.three_types_scene(128, 128)
     px = sg.pixel_subset(128, 128, 500, 9)
     g = gpu_frame(sc, precision=native.PREC_BF16)
-    o = orc.render(orc.OracleScene(sc), px=px, quant=orc.QUANT_BF16, n_threads=8)
-    rep = compare_frame(g, o, px)
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc), px=px, quant=orc.QUANT_BF16, n_threads=8)
     assert rep["hit"] > 100
 
 
@@ -113,8 +111,7 @@ def test_bf16_refine_and_outlier_resample(orc):
     px = sg.pixel_subset(128, 128, 600, 10)
     kw = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1)
     g = gpu_frame(sc, precision=native.PREC_BF16, **kw)
-    o = orc.render(orc.OracleScene(sc), px=px, quant=orc.QUANT_BF16, march_n=128, march_b=4, n_threads=8, **kw)
-    rep = compare_frame(g, o, px, max_excluded=0.08)
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc), px=px, quant=orc.QUANT_BF16, march_n=128, march_b=4, n_threads=8, **kw, max_excluded=0.08)
     assert g["stats"].fallback_pairs > 0 and rep["hit"] > 100
 
 

@@ -82,9 +82,42 @@ def test_loss_and_gradient_match_oracle(lib, orc):
     r.close()
 
 
-def test_training_reduces_loss_and_state_round_trip(lib):
+@pytest.mark.parametrize("scene_fn,t,n", [(lambda: sg.three_types_scene(8, 8, nerf=False), 1, 300),
+                                           (lambda: sg.three_types_scene(8, 8, nerf=False), 2, 3000),
+                                           (sg.tiny_sphere_scene, 0, 777)])
+def test_bf16_loss_and_gradient_match_oracle(lib, orc, scene_fn, t, n):
+    """The tensor-core training path (BF16 operands, FP32 accumulation; BF16 handles) against the
+    oracle's BF16-training gradient (reading 29): the loss to 1e-5 relative, every gradient element
+    within 2e-4 of the largest plus 2e-3 of its own size.  Widths 128 and 64; ragged row counts
+    (300: two 128-row tiles and a tail; 3000: three batch splits of 1024, the last ragged)."""
+    import torch
+    sc = scene_fn()
+    osc = orc.OracleScene(sc)
+    r0, o, d, m, h = labels_on_gpu(lib, sc, t, n, 9)
+    r0.close()
+    r = lib.renderer_for(sc, precision=lib.PREC_BF16)
+    g = torch.zeros(sc.types[t].nedf_w.shape[0], device="cuda")
+    loss = r.loss_grad(t, o, d, m, h, g)
+    ol, og = orc.nedf_loss_grad(osc, t, o.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.float64),
+                                m.cpu().numpy().astype(np.float64), (h.cpu().numpy() > 0.5).astype(np.int32),
+                                quant=orc.QUANT_BF16)
+    gg = g.cpu().numpy().astype(np.float64)
+    scale = np.abs(og).max()
+    err = np.abs(gg - og)
+    print(f"loss gpu {loss:.6f} oracle {ol:.6f}; max |g - g_orc| / max |g_orc| = {err.max() / scale:.2e}")
+    assert abs(loss - ol) <= 1e-5 * abs(ol)
+    assert np.all(err <= 2e-4 * scale + 2e-3 * np.abs(og))
+    # the FP64 gradient (no rounding) is further away: the comparison sees the BF16 rounding points
+    _, og64 = orc.nedf_loss_grad(osc, t, o.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.float64),
+                                 m.cpu().numpy().astype(np.float64), (h.cpu().numpy() > 0.5).astype(np.int32))
+    print(f"max |g_bf16 orc - g_fp64| / max = {np.abs(og - og64).max() / scale:.2e}")
+    r.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_training_reduces_loss_and_state_round_trip(lib, prec):
     sc = sg.three_types_scene(8, 8, nerf=False)
-    r = lib.renderer_for(sc)
+    r = lib.renderer_for(sc, precision=lib.PREC_FP32 if prec == "fp32" else lib.PREC_BF16)
     r.make_labels(0, 1 << 16, 2)
     first = r.train_step(0, 4096, 1e-3, want_loss=True)
     for _ in range(150):
@@ -158,12 +191,13 @@ def test_training_gain_over_untrained_network(lib):
     r.close()
 
 
-def test_resumed_training_repeats_the_uninterrupted_run_bitwise(lib):
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_resumed_training_repeats_the_uninterrupted_run_bitwise(lib, prec):
     """Training steps are deterministic, and the saved state holds everything a step depends on
     (weights, Adam moments, step count, batch cursor): save after 20 steps, run 15 more, reload and
     run the same 15 again; both runs end with identical weights, bit for bit."""
     sc = sg.three_types_scene(8, 8, nerf=False)
-    r = lib.renderer_for(sc)
+    r = lib.renderer_for(sc, precision=lib.PREC_FP32 if prec == "fp32" else lib.PREC_BF16)
     r.make_labels(1, 1 << 15, 3)
     for _ in range(20):
         r.train_step(1, 3000, 1e-3)           # 3000 rows: two gradient splits, one ragged

@@ -472,3 +472,70 @@ def test_frame_alternative_outcome_takes_the_critical_test_the_other_way(orc):
     assert not o["has_alt"][0] and np.isnan(o["alt_depth"][0]) and abs(o["depth"][0] - 2.55) < 0.01
     o = orc.render(orc.OracleScene(sc), px=px, alt=False, depth_mode=orc.DEPTH_MARCH, march_n=16, march_b=3)
     assert "has_alt" not in o
+
+
+# ------------------------------------------------------------------------------------------------
+# BF16 training: the gradient with BF16 operands, against torch autograd
+# ------------------------------------------------------------------------------------------------
+def test_bf16_training_gradient_matches_torch_autograd(orc):
+    """The oracle's BF16-mode loss and gradient (reading 29) against torch's autograd in float64 on
+    the same rounded operands: weights and layer inputs rounded to BF16 in the forward pass (the
+    saved activations are those BF16 values), the error signal of each hidden layer rounded to BF16
+    on its way back (a rounding applied to the gradient alone), the loss derivative unrounded."""
+    torch = pytest.importorskip("torch")
+    hidden, width = 3, 16
+    sc = one_instance_scene(sg.SDF_TORUS, params=[0.4, 0.15], hidden=hidden, width=width)
+    rng = np.random.default_rng(31)
+    t = sc.types[0]
+    t.nedf_w = (rng.normal(size=t.nedf_w.shape[0]) * 0.4).astype(np.float32)
+    osc = orc.OracleScene(sc)
+    o, d = orc.train_rays(1.0, 3, 0, 48)
+    m_star, h_star = orc.train_labels(osc, 0, o, d)
+    loss_o, g_o = orc.nedf_loss_grad(osc, 0, o, d, m_star, h_star, quant=orc.QUANT_BF16)
+
+    # a rounded operand: the value rounded to BF16, the derivative passed through unchanged
+    rnd = lambda x: x.detach().to(torch.float32).to(torch.bfloat16).to(torch.float64)
+    bf = lambda x: x + (rnd(x) - x).detach()
+
+    class GradBF16(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x):
+            return x.clone()
+
+        @staticmethod
+        def backward(ctx, g):
+            return rnd(g)
+
+    dims = sg.mlp_dims(sg.NEDF_IN, hidden, width, 2)
+    w = torch.tensor(t.nedf_w.astype(np.float64), requires_grad=True)
+    feats, keep = [], []
+    for k in range(o.shape[0]):
+        dd = d[k] / np.linalg.norm(d[k])
+        kept, f, _ = orc.nedf_features(o[k], dd, 1.0)
+        keep.append(kept)
+        feats.append(f if kept else np.zeros(sg.NEDF_IN))
+    X = torch.tensor(np.array(feats))
+    keep = torch.tensor(keep)
+    off, h = 0, bf(X)
+    for l in range(len(dims) - 1):
+        fi, fo = dims[l], dims[l + 1]
+        W = w[off: off + fi * fo].reshape(fo, fi); off += fi * fo
+        b = w[off: off + fo]; off += fo
+        z = h @ bf(W).T + b
+        if l + 1 < len(dims) - 1:
+            z = GradBF16.apply(z)                   # the hidden layer's error signal in BF16
+            h = bf(torch.relu(z))
+        else:
+            h = z
+    mm, aa = h[:, 0], h[:, 1]
+    hs = torch.tensor(h_star.astype(np.float64))
+    ms = torch.tensor(m_star)
+    bce = torch.clamp(aa, min=0) - hs * aa + torch.log1p(torch.exp(-aa.abs()))
+    n_hit = hs.sum()
+    loss = (0.1 * bce * keep).sum() / o.shape[0] + ((mm - ms) ** 2 * hs * keep).sum() / n_hit
+    loss.backward()
+    assert abs(loss.item() - loss_o) < 1e-12
+    assert np.allclose(w.grad.numpy(), g_o, rtol=1e-10, atol=1e-13)
+    # the unrounded oracle differs from it: the rounding points are real
+    _, g_n = orc.nedf_loss_grad(osc, 0, o, d, m_star, h_star)
+    assert np.abs(g_n - g_o).max() > 1e-6
