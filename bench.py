@@ -40,6 +40,13 @@ WORKLOAD_STRESS = ("4096 instances (8 shape types x 512, seed 4, T in [-40,40]^3
                    "fallback below confidence 0.9, 4 refinement steps with outlier re-answering")
 FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1)
 NEDF_FLOP = 2 * (78 * 128 + 5 * 128 * 128 + 128 * 2)          # per query, unpadded
+# one training ray of the 6 x 128 NeDF: the forward pass, the input gradients of the hidden layers
+# (5 x 128 x 128) and of the output layer (2 x 128), and every weight gradient (as the forward)
+TRAIN_FLOP = NEDF_FLOP + 2 * (5 * 128 * 128 + 2 * 128) + NEDF_FLOP
+# the trained NeDF weights of the 1024-instance workload (the bench's own training schedule, written by
+# paper_2308_04669_gb300/data/make_trained_weights.py): the reference arm renders with them, so both arms
+# time the same frame
+TRAINED_WEIGHTS = os.path.join(ROOT, "paper_2308_04669_gb300", "data", "nedf_thousand_trained.npz")
 # DRAM bytes (read + write) per launch of a stage's kernel from an ncu capture of the current
 # kernel source (profiles/); a stage is absent here once its kernel changed after the capture.
 # DRAM bytes per launch of the dominant kernel from an ncu capture of the current kernel (None until
@@ -184,7 +191,8 @@ def run_reference(args):
     per_step_s = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     import oracle
     oracle.build()
-    osc = oracle.OracleScene(sc)
+    w_ref = reference_weights(sc)
+    osc = oracle.OracleScene(sc, nedf_override=w_ref)
     # calibrate a per-step pixel sample that takes about per_step_s on the host cores
     t0 = time.perf_counter()
     oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, 256, 99), alt=False, n_threads=threads, **FRAME_OPTS)
@@ -203,18 +211,34 @@ def run_reference(args):
             "config": {"workload": WORLOAD_REF, "sample_px_per_step": n},
             "cpu_baseline": {"value": value, "unit": "rays/s", "cores": threads, "kind": "oracle",
                              "sample": f"{n} seeded pixels of the 1024x1024 frame per step, all 1024 instances, "
-                                       f"untrained NeDF weights; ms_per_step extrapolates to the full frame"},
+                                       + ("the trained NeDF weights of the bench's schedule" if w_ref else
+                                          "untrained NeDF weights (no trained-weights file)")
+                                       + "; ms_per_step extrapolates to the full frame"},
             "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-WORLOAD_REF = WORKLOAD.replace("trained on ray-march labels", "(oracle: FP64, same scene)")
+WORLOAD_REF = WORKLOAD.replace("trained on ray-march labels", "trained on ray-march labels (oracle: FP64, same scene and weights)")
+
+
+def reference_weights(sc):
+    """The committed trained NeDF weights of the 1024-instance workload (per type, FP32), or None."""
+    if not os.path.exists(TRAINED_WEIGHTS):
+        return None
+    z = np.load(TRAINED_WEIGHTS)
+    w = {t: z[f"type{t}"].astype(np.float64) for t in range(len(sc.types))}
+    if any(w[t].shape != sc.types[t].nedf_w.shape for t in w):
+        return None
+    return w
 
 
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
-def train_types(r, scene, steps, batch, n_rays, log):
+def train_types(r, scene, steps, batch, n_rays, log, stream, peak_tflops):
+    """The learned part on the GPU: each type's training set (n_rays plain-method labels), then
+    `steps` Adam steps of `batch` rays per type.  Device time from CUDA events on the stream."""
+    import hashlib
     import torch
     t0 = time.perf_counter()
     for t in range(len(scene.types)):
@@ -222,20 +246,31 @@ def train_types(r, scene, steps, batch, n_rays, log):
     torch.cuda.synchronize()
     t_labels = time.perf_counter() - t0
     losses = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
+    e0.record(stream)
     for t in range(len(scene.types)):
         first = r.train_step(t, batch, 1e-3, want_loss=True)
         for s in range(steps - 2):
             r.train_step(t, batch, 1e-3)
         last = r.train_step(t, batch, 1e-3, want_loss=True)
         losses.append((first, last))
+    e1.record(stream)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    dev_s = e0.elapsed_time(e1) * 1e-3
+    rays_s = len(scene.types) * steps * batch / dev_s
+    tflops = rays_s * TRAIN_FLOP / 1e12
+    w = np.concatenate([r.get_nedf_weights(t, scene.types[t].nedf_w.shape[0]) for t in range(len(scene.types))])
     log["train"] = {"types": len(scene.types), "steps_per_type": steps, "batch": batch,
                     "label_rays_per_type": n_rays, "label_s": round(t_labels, 3),
-                    "train_steps_per_s": round(len(scene.types) * steps / t_train, 2),
-                    "train_rays_per_s": round(len(scene.types) * steps * batch / t_train, 1),
-                    "loss_first_last": [[round(a, 5), round(b, 5)] for a, b in losses]}
+                    "ms_per_step": round(1e3 * dev_s / (len(scene.types) * steps), 4),
+                    "train_rays_per_s": round(rays_s, 1), "wall_s": round(t_train, 2),
+                    "flop_per_ray": TRAIN_FLOP, "tflops": round(tflops, 2),
+                    "roofline": {"bound": "tensor", "achieved": round(tflops, 2), "peak": peak_tflops,
+                                 "unit": "TFLOP/s", "frac": round(tflops / peak_tflops, 4)},
+                    "loss_first_last": [[round(a, 5), round(b, 5)] for a, b in losses],
+                    "weights_sha256": hashlib.sha256(w.astype(np.float32).tobytes()).hexdigest()}
 
 
 def classifier_frame(sc, stream, cam, lights, args, frames=5):
@@ -323,7 +358,12 @@ def run_ours(args):
     r = native.renderer_for(sc, precision=prec, stream=stream)
     log = {}
     if args.train_steps > 0:
-        train_types(r, sc, args.train_steps, args.train_batch, args.label_rays, log)
+        train_types(r, sc, args.train_steps, args.train_batch, args.label_rays, log, stream, peaks()[0]["bf16_tflops"])
+        ref_w = reference_weights(sc) if args.scene == "thousand" else None
+        if ref_w is not None:
+            log["train"]["same_weights_as_reference_arm"] = all(
+                np.array_equal(ref_w[t].astype(np.float32), r.get_nedf_weights(t, sc.types[t].nedf_w.shape[0]))
+                for t in range(len(sc.types)))
     o = r.get_options()
     for k, v in FRAME_OPTS.items():
         setattr(o, k, v)
@@ -637,9 +677,9 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--scene", default="thousand", choices=["thousand", "stress"],
                     help="thousand: the metric's 1024-instance 1024^2 frame; stress: 4096 instances at 2048^2, 8 lights")
-    ap.add_argument("--train-steps", type=int, default=1500)
-    ap.add_argument("--train-batch", type=int, default=16384)
-    ap.add_argument("--label-rays", type=int, default=1 << 20)
+    ap.add_argument("--train-steps", type=int, default=20000, help="Adam steps per type (the workload's 20k)")
+    ap.add_argument("--train-batch", type=int, default=65536)
+    ap.add_argument("--label-rays", type=int, default=1 << 22, help="plain-method labelled rays per type (2^22)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")

@@ -102,6 +102,7 @@ def lib():
             l.orc_steps23.argtypes = [sp, op, C.c_int64, i64, u32, d, d, d, d, d]
             l.orc_query_diag.argtypes = [sp, op, C.c_int, d, d, d, d, C.c_double]; l.orc_query_diag.restype = C.c_int
             l.orc_mlp_flip.argtypes = [d, C.c_int, i, d, d, C.c_int, C.c_int, C.c_int, i, d]
+            l.orc_mlp_flip2.argtypes = [d, C.c_int, i, d, d, C.c_int, C.c_int, C.c_int]
             l.orc_volume_render.argtypes = [sp, op, C.c_int, C.c_int64, i64, d, d]
             l.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]; l.orc_splitmix64.restype = C.c_uint64
             l.orc_train_rays.argtypes = [C.c_double, C.c_uint64, C.c_int64, C.c_int, d, d]
@@ -324,6 +325,16 @@ def mlp_flip(w, dims, x, quant, flip_idx=-1, n_cand=0):
     lib().orc_mlp_flip(_dp(w), len(dims) - 1, dims_c, _dp(x), _dp(y), int(quant), int(flip_idx), int(n_cand),
                        ci.ctypes.data_as(C.POINTER(C.c_int)), _dp(cm))
     return y, ci[:n_cand], cm[:n_cand]
+
+
+def mlp_flip2(w, dims, x, quant, flip_a, flip_b):
+    """The MLP with two rounded values taken the other way (see orc_mlp_flip2)."""
+    w = np.ascontiguousarray(w, np.float64)
+    dims_c = (C.c_int * len(dims))(*dims)
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.empty(dims[-1])
+    lib().orc_mlp_flip2(_dp(w), len(dims) - 1, dims_c, _dp(x), _dp(y), int(quant), int(flip_a), int(flip_b))
+    return y
 
 
 def round_bf16(x):

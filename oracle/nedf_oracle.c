@@ -263,12 +263,12 @@ static double round_fmt(double v, int fmt, int flip)
  * index: the input features 0 .. dims[0]-1, then each hidden layer's outputs in order.
  *   qmargin   (may be NULL) the row's smallest distance of a rounded value to its rounding
  *             boundary, relative to the scale that bounds another implementation's error there
- *             (sum of |w a| plus |b| for a layer's output, |v| for an input feature);
- *   flip_idx  index of one value rounded to its other neighbour (-1: none);
+ *             (sum of |w a| plus |b| for a layer's output, max(|v|, 1/4) for an input feature);
+ *   flip_idx  index of one value rounded to its other neighbour (-1: none; flip_idx2 a second);
  *   n_cand    the n_cand values of smallest relative margin are listed in cand_idx / cand_margin
  *             (ascending; unused entries get index -1). */
-static void mlp_core(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
-                     double *qmargin, int flip_idx, int n_cand, int *cand_idx, double *cand_margin)
+static void mlp_core2(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
+                      double *qmargin, int flip_idx, int flip_idx2, int n_cand, int *cand_idx, double *cand_margin)
 {
     int maxd = 0;
     for (int l = 0; l <= n_layers; ++l) maxd = dims[l] > maxd ? dims[l] : maxd;
@@ -292,8 +292,11 @@ static void mlp_core(const double *w, int n_layers, const int *dims, const doubl
     for (int i = 0; i < dims[0]; ++i, ++vidx) {
         a[i] = x[i];
         if (quant == ORC_QUANT_NONE) continue;
-        NOTE_MARGIN(orc_round_margin(x[i], 0) / dmax(fabs(x[i]), 1e-300));
-        a[i] = round_fmt(x[i], 0, vidx == flip_idx);
+        /* an input feature (a coordinate, or the sine or cosine of one scaled by up to 2^9) carries
+         * an absolute error from the coordinates: its margin is measured against |v| but no less
+         * than 1/4 */
+        NOTE_MARGIN(orc_round_margin(x[i], 0) / dmax(fabs(x[i]), 0.25));
+        a[i] = round_fmt(x[i], 0, vidx == flip_idx || vidx == flip_idx2);
     }
     const double *p = w;
     for (int l = 0; l < n_layers; ++l) {
@@ -323,7 +326,7 @@ static void mlp_core(const double *w, int n_layers, const int *dims, const doubl
                 /* hidden activations: BF16, or E4M3 in the FP8 mode (they feed E4M3 layers) */
                 int fmt = quant == ORC_QUANT_FP8 ? 1 : 0;
                 NOTE_MARGIN(orc_round_margin(b[o], fmt) / dmax(mag, 1e-300));
-                b[o] = round_fmt(b[o], fmt, vidx == flip_idx);
+                b[o] = round_fmt(b[o], fmt, vidx == flip_idx || vidx == flip_idx2);
                 ++vidx;
             }
         }
@@ -335,6 +338,12 @@ static void mlp_core(const double *w, int n_layers, const int *dims, const doubl
     if (qmargin) *qmargin = qm;
     free(a);
     free(b);
+}
+
+static void mlp_core(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
+                     double *qmargin, int flip_idx, int n_cand, int *cand_idx, double *cand_margin)
+{
+    mlp_core2(w, n_layers, dims, x, y, quant, qmargin, flip_idx, -1, n_cand, cand_idx, cand_margin);
 }
 
 void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant)
@@ -353,6 +362,12 @@ void orc_mlp_flip(const double *w, int n_layers, const int *dims, const double *
                   int flip_idx, int n_cand, int *cand_idx, double *cand_margin)
 {
     mlp_core(w, n_layers, dims, x, y, quant, NULL, flip_idx, n_cand, cand_idx, cand_margin);
+}
+
+void orc_mlp_flip2(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant, int flip_a,
+                   int flip_b)
+{
+    mlp_core2(w, n_layers, dims, x, y, quant, NULL, flip_a, flip_b, 0, NULL, NULL);
 }
 
 static int nedf_dims(const orc_type *t, int *dims)
@@ -709,7 +724,7 @@ static double dec_margin(const dec_diag *g, double need)
 }
 
 /* The two most critical tests of a pixel, each named by where it ran: stage 1 = the Step-1 query
- * of instance `inst`, stage 2 = the shadow query of `inst` for light `light`; idx = its index. */
+ * of instance `inst` (stage 0: none); idx = its index in that query. */
 typedef struct { double m; int stage, light, inst, idx; } crit_test;
 
 static void crit_feed(crit_test cr[2], const dec_diag *g, double need, int stage, int light, int inst)
@@ -759,10 +774,10 @@ double orc_march_depth(const orc_scene *sc, int type, const double ol[3], const 
  * (m, a) when one of its ORC_FLIP_CAND values nearest to a rounding boundary (relative margin below
  * the format's limit, i.e. within reach of another implementation's sums) rounds the other way. */
 #define ORC_FLIP_CAND 16
-/* BF16: FP32 sums plus a bias carried to ~16 significant bits (relative 2^-17 of |b|); E4M3: FP32
- * sums with the bias added in FP32 */
+/* BF16: FP32 sums plus a bias carried to ~16 significant bits (relative 2^-17 of |b|); E4M3: the
+ * accumulation of E4M3 products, coarser than FP32 (flips measured at relative margins to ~1e-4) */
 #define ORC_FLIP_MARGIN_BF16 1e-5
-#define ORC_FLIP_MARGIN_FP8 1e-6
+#define ORC_FLIP_MARGIN_FP8 2e-5
 static void nedf_spread(const orc_type *t, const int *dims, int nl, const double *feat, const double y[2],
                         int quant, double spread[2])
 {
@@ -965,6 +980,10 @@ typedef struct {
 } render_job;
 
 #define ORC_ALT_MARGIN 1e-6      /* pixels whose most critical depth test is closer get an alternative */
+/* The depth tolerance of the comparisons (1e-3 relative, 2e-3 absolute: the FP32 contract of the
+ * render path): a depth test whose consequence stays below it cannot decide a depth comparison. */
+#define ORC_DEPTH_TOL_ABS 2e-3
+#define ORC_DEPTH_TOL_REL 1e-3
 
 typedef struct {
     double depth, gap, pm, sm, smax, rgba[4], S;
@@ -974,16 +993,13 @@ typedef struct {
 /* Steps 2 and 3 of pixel p (camera ray o, d) given its winning instance `inst` and world depth:
  * the shading of Eq. 8 over the sample window (or the plain method's colour for an outlier with
  * resampling), then the shadow rays of Algorithm 2.  rgba, *S (the shadow factor), *sm (the shadow
- * tests' margin) and *smax (the largest sample density) are written; fl / cr as in render_pixel
- * (cr may be NULL). */
+ * tests' margin, 0 where a depth test of a shadow query could move its depth across the test) and
+ * *smax (the largest sample density) are written. */
 static void steps23(const orc_scene *sc, const orc_opts *op, int64_t p, const double o[3], const double d[3], int inst,
-                    double depth, const crit_test *fl, double rgba[4], double *S_out, double *sm_out, double *smax_out,
-                    crit_test *cr)
+                    double depth, double rgba[4], double *S_out, double *sm_out, double *smax_out)
 {
     double q[6], mg, dsp, S = 1.0, sm = INFINITY, smax = NAN;
     dec_diag dg;
-    crit_test none2[2];
-    if (!cr) { cr = none2; cr[0].m = cr[1].m = INFINITY; }
     {
         /* STEP 2: shade with the winning model's radiance field only. */
         smax = shade_pixel(sc, op, o, d, inst, depth, rgba);
@@ -1018,19 +1034,23 @@ static void steps23(const orc_scene *sc, const orc_opts *op, int64_t p, const do
             double ell = len3(v), dir[3] = {v[0] / ell, v[1] / ell, v[2] / ell};
             int occluded = 0;
             for (int m = 0; m < sc->n_inst; ++m) {
-                int flip = (fl->stage == 2 && fl->light == l && fl->inst == m) ? fl->idx : -1;
-                int hit = query_ex(sc, op, m, L, dir, q, &mg, &dg, flip, &dsp);
+                int hit = query_ex(sc, op, m, L, dir, q, &mg, &dg, -1, &dsp);
                 double s = sc->inst_s[m];
                 if (!(q[3] <= q[4]) || q[4] < 0.0) { sm = dmin(sm, mg); continue; } /* culled */
                 /* Reading: only bounds the shadow segment enters before x can occlude x. */
                 sm = dmin(sm, fabs(q[3] * s - ell));
                 if (!(q[3] * s < ell)) continue;
                 sm = dmin(sm, mg);
-                if (!hit) { crit_feed(cr, &dg, INFINITY, 2, l, m); continue; }
+                /* a depth test of this query that could go the other way (margin below
+                 * ORC_ALT_MARGIN) and move its depth across the shadow test makes the test a knife
+                 * edge */
+                if (!hit) {
+                    if (dec_margin(&dg, INFINITY) < ORC_ALT_MARGIN) sm = 0.0;
+                    continue;
+                }
                 double Dk = s * q[0];
                 sm = dmin(sm, fabs(Dk + sc->eps - ell) - s * dsp);
-                /* a depth test matters here only if its consequence can cross the shadow test */
-                crit_feed(cr, &dg, fabs(Dk + sc->eps - ell) / s, 2, l, m);
+                if (dec_margin(&dg, fabs(Dk + sc->eps - ell) / s) < ORC_ALT_MARGIN) sm = 0.0;
                 if (Dk + sc->eps < ell) occluded = 1;
             }
             acc += occluded ? sc->beta : 1.0;
@@ -1068,16 +1088,18 @@ static void render_pixel(const orc_scene *sc, const orc_opts *op, int64_t p, con
         if (D < best) { second = best; u_second = u_best; best = D; u_best = u; bid = (uint32_t)m; }
         else if (D < second) { second = D; u_second = u; }
     }
-    /* Depth tests that can change this pixel: every one of the winner's (its depth feeds Steps 2
-     * and 3), and those of each other hit whose consequence reaches the winner. */
+    /* Depth tests that can change this pixel's Step-1 result: the winner's whose consequence
+     * reaches the depth tolerance (ORC_DEPTH_TOL_*: Steps 2-3 are answered for a given depth by
+     * orc_steps23), and those of each other hit whose consequence reaches the winner. */
     for (int m = 0; m < sc->n_inst; ++m) {
         if (!isfinite(Dq[m])) continue;
-        crit_feed(cr, &dq[m], (uint32_t)m == bid ? 0.0 : (Dq[m] - best) / sc->inst_s[m], 1, 0, m);
+        const double need = (uint32_t)m == bid ? dmax(ORC_DEPTH_TOL_ABS, ORC_DEPTH_TOL_REL * best) : Dq[m] - best;
+        crit_feed(cr, &dq[m], need / sc->inst_s[m], 1, 0, m);
     }
     free(Dq);
     free(dq);
     double rgba[4] = {0, 0, 0, 0}, S = 1.0, sm = INFINITY, smax = NAN;
-    if (bid != 0xFFFFFFFFu) steps23(sc, op, p, o, d, (int)bid, best, fl, rgba, &S, &sm, &smax, cr);
+    if (bid != 0xFFFFFFFFu) steps23(sc, op, p, o, d, (int)bid, best, rgba, &S, &sm, &smax);
     r->depth = best;
     r->id = bid;
     /* the gap less the depth shift single network-rounding flips can cause on either side */
@@ -1177,14 +1199,13 @@ typedef struct {
 static void *s23_worker(void *arg)
 {
     const s23_job *jb = (const s23_job *)arg;
-    const crit_test none = {INFINITY, 0, 0, 0, -1};
     for (int64_t k = jb->begin; k < jb->end; ++k) {
         double rgba[4] = {0, 0, 0, 0}, S = 1.0, sm = INFINITY, smax = NAN;
         if (jb->id[k] != 0xFFFFFFFFu && (int64_t)jb->id[k] < jb->sc->n_inst) {
             double o[3], d[3];
             const int64_t p = jb->px[k];
             orc_camera_ray(jb->sc, (int)(p % jb->sc->W), (int)(p / jb->sc->W), o, d);
-            steps23(jb->sc, jb->op, p, o, d, (int)jb->id[k], jb->depth[k], &none, rgba, &S, &sm, &smax, NULL);
+            steps23(jb->sc, jb->op, p, o, d, (int)jb->id[k], jb->depth[k], rgba, &S, &sm, &smax);
         }
         for (int c = 0; c < 4; ++c) jb->rgba[4 * k + c] = rgba[c];
         jb->shadow[k] = S;

@@ -104,14 +104,17 @@ void orc_mlp(const double *w, int n_layers, const int *dims, const double *x, do
 /* Distance from v to the nearest rounding boundary of BF16 (fmt 0) or E4M3 (fmt 1). */
 double orc_round_margin(double v, int fmt);
 /* orc_mlp plus the row's rounding knife edge: the smallest distance of a BF16 / E4M3-rounded value
- * to its rounding boundary relative to the magnitude of the sum that produced it (INFINITY in the
- * unrounded mode). */
+ * to its rounding boundary relative to the magnitude of the sum that produced it, max(|v|, 1/4) for
+ * an input feature (INFINITY in the unrounded mode). */
 double orc_mlp_qmargin(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant);
 /* orc_mlp with value flip_idx (inputs first, then each hidden layer's outputs; -1 none) rounded to
  * its other neighbour; the n_cand values nearest to a rounding boundary (relative margin,
  * ascending) are listed in cand_idx / cand_margin. */
 void orc_mlp_flip(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
                   int flip_idx, int n_cand, int *cand_idx, double *cand_margin);
+/* orc_mlp with two values (flip_a, flip_b) rounded to their other neighbours. */
+void orc_mlp_flip2(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant, int flip_a,
+                   int flip_b);
 double orc_round_bf16(double x);
 double orc_round_e4m3(double x);
 double orc_fp8_scale(double max_abs);

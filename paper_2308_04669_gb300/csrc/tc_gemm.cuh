@@ -16,7 +16,7 @@
 // so that a K step of 16 is two 8-column groups 16R bytes apart (leading byte offset 16R) of
 // 8-row core matrices 128 bytes apart (stride byte offset 128) in either order, the order being
 // told to the MMA by the instruction descriptor (bit 15 for A, bit 16 for B).  Consecutive 16-byte
-// vectors of a stage are consecutive copies of consecutive threads, so the stores into shared
+// vectors of a stage are copies of consecutive threads, so the stores into shared
 // memory are conflict-free.
 #pragma once
 

@@ -25,7 +25,8 @@ namespace nedf {
 using tcg::Operand;
 
 constexpr int kTcSplitRows = 1024;       // batch rows per weight-gradient split (a multiple of 64)
-constexpr int kTcStages = 3;
+constexpr int kTcStagesRow = 2;          // row GEMMs (K = 80 or W: at most two 64-deep blocks)
+constexpr int kTcStagesWgrad = 3;        // weight gradients (K = the split's rows)
 
 // ---- scratch ----------------------------------------------------------------------------------
 struct TcTrainScratch {
@@ -202,7 +203,7 @@ template <int BN, class Epi>
 __global__ void __launch_bounds__(tcg::kThreads) k_tc_gemm(Operand A, Operand B, long long k_total, Epi epi,
                                                            uint32_t *status)
 {
-    tcg::gemm_tile<BN, kTcStages>(A, B, blockIdx.x * tcg::kBM, 0, 0, k_total, epi, status, kStatusTimeout);
+    tcg::gemm_tile<BN, kTcStagesRow>(A, B, blockIdx.x * tcg::kBM, 0, 0, k_total, epi, status, kStatusTimeout);
 }
 
 // The weight and bias gradients of every hidden layer in one launch: blockIdx.y = layer,
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(tcg::kThreads) k_tc_wgrad(WgradLayers P, long 
     const int l = blockIdx.y;
     const long long kb = (long long)blockIdx.z * split_rows;
     const long long ke = kb + split_rows < k_total ? kb + split_rows : k_total;
-    tcg::gemm_tile<BN, kTcStages>(P.a[l], P.b[l], 0, 0, kb, ke, P.epi[l], status, kStatusTimeout);
+    tcg::gemm_tile<BN, kTcStagesWgrad>(P.a[l], P.b[l], 0, 0, kb, ke, P.epi[l], status, kStatusTimeout);
 }
 
 // ---- loss, output layer, first error signal ----------------------------------------------------
@@ -293,25 +294,42 @@ __global__ void k_tc_loss(const __nv_bfloat16 *hL, const __nv_bfloat16 *wout, co
     }
 }
 
-// Output-layer gradient of one split (blockIdx.x): dW_out[o][k] = sum_b dy[b][o] h_L[b][k] and
-// db_out[o] = sum_b dy[b][o] over the split's rows, in row order, into the split's partial.
+// Output-layer gradient of one split (blockIdx.x) and 32 of the W columns (blockIdx.y):
+// dW_out[o][k] = sum_b dy[b][o] h_L[b][k] and (column block 0) db_out[o] = sum_b dy[b][o] over the
+// split's rows into the split's partial.  Warp w sums rows w, w + 8, ... of the split (lane = column),
+// then the eight warps are added in order: a fixed summation order, deterministic.
 template <int W>
-__global__ void k_tc_out_grad(const __nv_bfloat16 *hL, const float *dy, int B, int rows_per_split, float *partial,
-                              long long split_stride, long long off)
+__global__ void __launch_bounds__(256) k_tc_out_grad(const __nv_bfloat16 *hL, const float *dy, int B, int rows_per_split,
+                                                     float *partial, long long split_stride, long long off)
 {
+    __shared__ float red[8][2][33];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = blockIdx.x * rows_per_split, r1 = min(B, r0 + rows_per_split);
+    const int c = blockIdx.y * 32 + lane;
+    float a0 = 0.0f, a1 = 0.0f, s0 = 0.0f, s1 = 0.0f;
+    for (int b = r0 + warp; b < r1; b += 8) {
+        const float2 g = *reinterpret_cast<const float2 *>(dy + 2 * (size_t)b);
+        const float h = __bfloat162float(hL[(size_t)b * W + c]);
+        a0 = fmaf(g.x, h, a0);
+        a1 = fmaf(g.y, h, a1);
+        s0 += g.x;
+        s1 += g.y;
+    }
+    red[warp][0][lane] = a0;
+    red[warp][1][lane] = a1;
+    if (lane == 0) { red[warp][0][32] = s0; red[warp][1][32] = s1; }
+    __syncthreads();
     float *p = partial + blockIdx.x * split_stride + off;
-    for (int j = threadIdx.x; j < 2 * W + 2; j += blockDim.x) {
+    if (threadIdx.x < 64) {
+        const int o = threadIdx.x >> 5, l = threadIdx.x & 31;
         float acc = 0.0f;
-        if (j < 2 * W) {
-            const int o = j / W, k = j % W;
-            for (int b = r0; b < r1; ++b) acc = fmaf(dy[2 * b + o], __bfloat162float(hL[(size_t)b * W + k]), acc);
-            p[(long long)o * W + k] = acc;
-        } else {
-            const int o = j - 2 * W;
-            for (int b = r0; b < r1; ++b) acc += dy[2 * b + o];
-            p[2LL * W + o] = acc;
-        }
+        for (int w = 0; w < 8; ++w) acc += red[w][o][l];
+        p[(long long)o * W + blockIdx.y * 32 + l] = acc;
+    } else if (threadIdx.x < 66 && blockIdx.y == 0) {
+        const int o = threadIdx.x - 64;
+        float acc = 0.0f;
+        for (int w = 0; w < 8; ++w) acc += red[w][o][32];
+        p[2LL * W + o] = acc;
     }
 }
 
@@ -329,7 +347,7 @@ template <int BN, class Epi>
 static cudaError_t gemm(const Operand &A, const Operand &B, int m_blocks, long long k_total, const Epi &epi,
                         uint32_t *status, cudaStream_t st)
 {
-    using SM = tcg::GemmSmem<BN, kTcStages>;
+    using SM = tcg::GemmSmem<BN, kTcStagesRow>;
     cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::BYTES);
     if (e != cudaSuccess) return e;
     k_tc_gemm<BN, Epi><<<m_blocks, tcg::kThreads, SM::BYTES, st>>>(A, B, k_total, epi, status);
@@ -376,14 +394,16 @@ static cudaError_t run_tc(const TrainLaunch &L, const float *o, const float *d, 
         P.epi[l] = EpiWeightGrad{s.partial + packed_off(l, W), L.n_params, W, fi, fip};
     }
     {
-        constexpr int BN = W + 16;
-        using SM = tcg::GemmSmem<BN, kTcStages>;
+        // the widest B operand: 80 inputs of layer 0 or W, then the 8-row group of the ones row
+        constexpr int BN = (W > kNedfInPad ? W : kNedfInPad) + 16;
+        using SM = tcg::GemmSmem<BN, kTcStagesWgrad>;
         if ((e = cudaFuncSetAttribute(k_tc_wgrad<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::BYTES)) !=
             cudaSuccess)
             return e;
         k_tc_wgrad<BN><<<dim3(1, nl, splits), tcg::kThreads, SM::BYTES, st>>>(P, B, kTcSplitRows, L.status);
     }
-    k_tc_out_grad<W><<<splits, 256, 0, st>>>(s.h[nl], s.dy, B, kTcSplitRows, s.partial, L.n_params, packed_off(nl, W));
+    k_tc_out_grad<W><<<dim3(splits, W / 32), 256, 0, st>>>(s.h[nl], s.dy, B, kTcSplitRows, s.partial, L.n_params,
+                                                            packed_off(nl, W));
     k_tc_sum_splits<<<(int)std::min<long long>((L.n_params + 255) / 256, (long long)L.num_sms * 8), 256, 0, st>>>(
         s.partial, splits, L.n_params, s.grad);
     return cudaGetLastError();

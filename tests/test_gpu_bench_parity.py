@@ -91,4 +91,4 @@ def test_stress_kind_frame_bf16_nedf_matches_oracle(orc):
     px = sg.pixel_subset(sc.W, sc.H, 2000, 10)
     rep, o = frame_vs_oracle(g, orc.OracleScene(sc, nedf_override=w), px=px, quant=orc.QUANT_BF16, march_n=128,
                              march_b=4, n_threads=16, max_excluded=0.1, **FRAME_OPTS)
-    assert rep["hit"] > 300 and g["stats"].status == 0
+    assert rep["hit"] > 200 and g["stats"].status == 0

@@ -87,9 +87,11 @@ def test_loss_and_gradient_match_oracle(lib, orc):
                                            (sg.tiny_sphere_scene, 0, 777)])
 def test_bf16_loss_and_gradient_match_oracle(lib, orc, scene_fn, t, n):
     """The tensor-core training path (BF16 operands, FP32 accumulation; BF16 handles) against the
-    oracle's BF16-training gradient (reading 29): the loss to 1e-5 relative, every gradient element
-    within 2e-4 of the largest plus 2e-3 of its own size.  Widths 128 and 64; ragged row counts
-    (300: two 128-row tiles and a tail; 3000: three batch splits of 1024, the last ragged)."""
+    oracle's BF16-training gradient (reading 29).  The loss agrees to 1e-5 relative.  The gradient
+    of each layer agrees in norm to a fifth of the layer's own BF16 rounding effect (the gap between
+    the oracle's BF16 and FP64 gradients) and to 5e-4 of the largest element: the remaining
+    differences are values an FP32 sum rounds to the other BF16 neighbour.  Widths 128 and 64;
+    ragged row counts (300: two 128-row tiles and a tail; 3000: three batch splits of 1024)."""
     import torch
     sc = scene_fn()
     osc = orc.OracleScene(sc)
@@ -98,19 +100,23 @@ def test_bf16_loss_and_gradient_match_oracle(lib, orc, scene_fn, t, n):
     r = lib.renderer_for(sc, precision=lib.PREC_BF16)
     g = torch.zeros(sc.types[t].nedf_w.shape[0], device="cuda")
     loss = r.loss_grad(t, o, d, m, h, g)
-    ol, og = orc.nedf_loss_grad(osc, t, o.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.float64),
-                                m.cpu().numpy().astype(np.float64), (h.cpu().numpy() > 0.5).astype(np.int32),
-                                quant=orc.QUANT_BF16)
+    args = (o.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.float64),
+            m.cpu().numpy().astype(np.float64), (h.cpu().numpy() > 0.5).astype(np.int32))
+    ol, og = orc.nedf_loss_grad(osc, t, *args, quant=orc.QUANT_BF16)
+    _, og64 = orc.nedf_loss_grad(osc, t, *args)
     gg = g.cpu().numpy().astype(np.float64)
-    scale = np.abs(og).max()
-    err = np.abs(gg - og)
-    print(f"loss gpu {loss:.6f} oracle {ol:.6f}; max |g - g_orc| / max |g_orc| = {err.max() / scale:.2e}")
     assert abs(loss - ol) <= 1e-5 * abs(ol)
-    assert np.all(err <= 2e-4 * scale + 2e-3 * np.abs(og))
-    # the FP64 gradient (no rounding) is further away: the comparison sees the BF16 rounding points
-    _, og64 = orc.nedf_loss_grad(osc, t, o.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.float64),
-                                 m.cpu().numpy().astype(np.float64), (h.cpu().numpy() > 0.5).astype(np.int32))
-    print(f"max |g_bf16 orc - g_fp64| / max = {np.abs(og - og64).max() / scale:.2e}")
+    scale = np.abs(og).max()
+    dims = sc.types[t].nedf_dims
+    off = 0
+    for l in range(len(dims) - 1):
+        k = dims[l] * dims[l + 1] + dims[l + 1]
+        e = np.linalg.norm(gg[off:off + k] - og[off:off + k])
+        gap = np.linalg.norm(og[off:off + k] - og64[off:off + k])
+        print(f"layer {l}: |g - g_bf16| {e:.3e}  |g_bf16 - g_fp64| {gap:.3e}  |g_bf16| {np.linalg.norm(og[off:off + k]):.3e}")
+        assert e <= 0.2 * gap + 5e-4 * scale, (l, e, gap)
+        off += k
+    print(f"loss gpu {loss:.6f} oracle {ol:.6f}; max |g - g_bf16| / max |g_bf16| = {np.abs(gg - og).max() / scale:.2e}")
     r.close()
 
 

@@ -539,3 +539,25 @@ def test_bf16_training_gradient_matches_torch_autograd(orc):
     # the unrounded oracle differs from it: the rounding points are real
     _, g_n = orc.nedf_loss_grad(osc, 0, o, d, m_star, h_star)
     assert np.abs(g_n - g_o).max() > 1e-6
+
+
+def test_mlp_flip2_rounds_two_values_the_other_way(orc):
+    """Two hidden units placed just off BF16 rounding boundaries (1 + 2^-8 - 3e-7 rounds to 1, else
+    1 + 2^-7; 2 + 2^-7 + 5e-7 rounds to 2 + 2^-6, else 2) feeding m = h0 / 2 + h1 / 4: each flip
+    and both together give the closed-form outputs."""
+    dims = sg.mlp_dims(sg.NEDF_IN, 1, 8, 2)
+    w = np.zeros(sg.mlp_param_count(dims))
+    off = sg.NEDF_IN * 8
+    w[off] = 1.0 + 2.0 ** -8 - 3e-7
+    w[off + 1] = 2.0 + 2.0 ** -7 + 5e-7
+    w[off + 8] = 0.5                                             # W_out[0][0]
+    w[off + 8 + 1] = 0.25                                        # W_out[0][1]
+    x = np.zeros(sg.NEDF_IN)
+    y0, ci, _ = orc.mlp_flip(w, dims, x, orc.QUANT_BF16, -1, 2)
+    h0, h1 = sg.NEDF_IN, sg.NEDF_IN + 1                          # value indices of the two units
+    assert set(ci.tolist()) == {h0, h1}
+    assert y0[0] == 0.5 * 1.0 + 0.25 * (2.0 + 2.0 ** -6)
+    assert orc.mlp_flip(w, dims, x, orc.QUANT_BF16, h0, 0)[0][0] == 0.5 * (1.0 + 2.0 ** -7) + 0.25 * (2.0 + 2.0 ** -6)
+    assert orc.mlp_flip(w, dims, x, orc.QUANT_BF16, h1, 0)[0][0] == 0.5 * 1.0 + 0.25 * 2.0
+    assert orc.mlp_flip2(w, dims, x, orc.QUANT_BF16, h0, h1)[0] == 0.5 * (1.0 + 2.0 ** -7) + 0.25 * 2.0
+    assert orc.mlp_flip2(w, dims, x, orc.QUANT_BF16, h0, h0)[0] == orc.mlp_flip(w, dims, x, orc.QUANT_BF16, h0, 0)[0][0]
