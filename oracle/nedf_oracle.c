@@ -319,8 +319,17 @@ static void mlp_core2(const double *w, int n_layers, const int *dims, const doub
                 acc += wv * av;
                 mag += fabs(wv * av);
             }
-            acc += bias[o];
-            mag += fabs(bias[o]);
+            /* reading 20: a layer whose products take BF16 operands (every hidden layer in the BF16
+             * mode, the first in the FP8 mode) takes its bias as the sum of two BF16 values, the
+             * rounded bias and the rounded remainder (16 significant bits); the output layer and
+             * the E4M3 layers add it in full */
+            double bv = bias[o];
+            if (l + 1 < n_layers && (quant == ORC_QUANT_BF16 || (quant == ORC_QUANT_FP8 && l == 0))) {
+                const double hi = orc_round_bf16(bv);
+                bv = hi + orc_round_bf16(bv - hi);
+            }
+            acc += bv;
+            mag += fabs(bv);
             b[o] = (l + 1 < n_layers) ? dmax(acc, 0.0) : acc;
             if (quant != ORC_QUANT_NONE && l + 1 < n_layers) {
                 /* hidden activations: BF16, or E4M3 in the FP8 mode (they feed E4M3 layers) */
@@ -776,7 +785,7 @@ double orc_march_depth(const orc_scene *sc, int type, const double ol[3], const 
 #define ORC_FLIP_CAND 16
 /* BF16: FP32 sums plus a bias carried to ~16 significant bits (relative 2^-17 of |b|); E4M3: the
  * accumulation of E4M3 products, coarser than FP32 (flips measured at relative margins to ~1e-4) */
-#define ORC_FLIP_MARGIN_BF16 1e-5
+#define ORC_FLIP_MARGIN_BF16 2e-5
 #define ORC_FLIP_MARGIN_FP8 2e-5
 static void nedf_spread(const orc_type *t, const int *dims, int nl, const double *feat, const double y[2],
                         int quant, double spread[2])

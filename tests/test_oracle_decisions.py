@@ -305,10 +305,11 @@ def test_mlp_qmargin_reports_the_tightest_rounded_value(orc):
     x = np.zeros(78)
     x[0] = 1.0                                                   # an exactly representable input
     w[0] = 1.0                                                   # W0[0][0]
-    boundary = 1.0 + 2.0 ** -8                                   # midpoint of 1 and 1 + 2^-7
-    w[78] = boundary - 1.0 - 3e-5                                # bias: pre-activation 3e-5 below it
+    # midpoint of 1 and 1 + 2^-7 is 1 + 2^-8; the bias 2^-8 - 2^-15 (exact in BF16, so its two-part
+    # BF16 form is itself) puts the pre-activation 2^-15 below it
+    w[78] = 2.0 ** -8 - 2.0 ** -15
     y, m = orc.mlp_qmargin(w, dims, x, orc.QUANT_BF16)
-    assert abs(m - 3e-5 / (1.0 + abs(w[78]))) < 1e-12
+    assert abs(m - 2.0 ** -15 / (1.0 + abs(w[78]))) < 1e-15
     _, m_none = orc.mlp_qmargin(w, dims, x, orc.QUANT_NONE)
     assert m_none == math.inf
 
@@ -331,12 +332,12 @@ def _flip_net(pre, w_out, b_m=0.0, a=5.0, width=8):
 
 
 def test_mlp_flip_rounds_one_value_the_other_way(orc):
-    pre = 1.0 + 2.0 ** -8 - 3e-7                                 # just below the 1 | 1+2^-7 midpoint
+    pre = 1.0 + 2.0 ** -8 - 2.0 ** -16                                 # just below the 1 | 1+2^-7 midpoint
     w, dims = _flip_net(pre, 0.5)
     x = np.zeros(sg.NEDF_IN)
     y, ci, cm = orc.mlp_flip(w, dims, x, orc.QUANT_BF16, -1, 3)
     assert abs(y[0] - 0.5 * 1.0) < 1e-15                         # rounds down to 1
-    assert ci[0] == sg.NEDF_IN and cm[0] < 1e-6                  # unit 0 of layer 0 is the knife edge
+    assert ci[0] == sg.NEDF_IN and abs(cm[0] - 2.0 ** -16 / pre) < 1e-12   # unit 0 of layer 0: the knife edge
     yf, _, _ = orc.mlp_flip(w, dims, x, orc.QUANT_BF16, int(ci[0]), 0)
     assert abs(yf[0] - 0.5 * (1.0 + 2.0 ** -7)) < 1e-15          # ... and up when flipped
     assert np.all(np.diff(cm[np.isfinite(cm)]) >= 0)
@@ -348,10 +349,10 @@ def test_mlp_flip_rounds_one_value_the_other_way(orc):
 
 
 def test_query_spread_is_the_depth_change_of_one_flip(orc):
-    """A row with one activation 3e-7 below a BF16 boundary: its depth may move by rb * w_out *
+    """A row with one activation 2^-16 below a BF16 boundary: its depth may move by rb * w_out *
     2^-7; the FP32 mode has no spread."""
     for rb in (1.0, 2.0):
-        w, dims = _flip_net(1.0 + 2.0 ** -8 - 3e-7, 0.25, b_m=0.1)
+        w, dims = _flip_net(1.0 + 2.0 ** -8 - 2.0 ** -16, 0.25, b_m=0.1)
         sc = one_instance_scene(sg.SDF_SPHERE, nedf_w=w, hidden=1, width=8, rb=rb)
         osc = orc.OracleScene(sc)
         _, _, (mg, dm, dsp) = orc.query_diag(osc, 0, EYE, DIR, quant=orc.QUANT_BF16)
@@ -440,7 +441,7 @@ def test_query_dmargin_of_the_plain_method(orc, n):
 def test_frame_gap_is_reduced_by_both_depth_spreads(orc):
     """Two instances with the same knife-edge network one behind the other: the reported gap is
     the depth difference less both instances' flip shifts (BF16), the plain difference in FP32."""
-    w, dims = _flip_net(1.0 + 2.0 ** -8 - 3e-7, 0.25, b_m=0.1)
+    w, dims = _flip_net(1.0 + 2.0 ** -8 - 2.0 ** -16, 0.25, b_m=0.1)
     t = sg.make_type(sg.SDF_SPHERE, 0, 0, 1, 8, nedf_seed=1)
     t.nedf_w = w.astype(np.float32)
     sc = sg.Scene("two", 33, 33, sg.f32([0, 0, 4]), sg.f32([0, 0, 0]), 40.0, sg.f32([[2, 3, 2]]), [t],
@@ -542,14 +543,14 @@ def test_bf16_training_gradient_matches_torch_autograd(orc):
 
 
 def test_mlp_flip2_rounds_two_values_the_other_way(orc):
-    """Two hidden units placed just off BF16 rounding boundaries (1 + 2^-8 - 3e-7 rounds to 1, else
-    1 + 2^-7; 2 + 2^-7 + 5e-7 rounds to 2 + 2^-6, else 2) feeding m = h0 / 2 + h1 / 4: each flip
-    and both together give the closed-form outputs."""
+    """Two hidden units placed just off BF16 rounding boundaries (1 + 2^-8 - 2^-16 rounds to 1, else
+    1 + 2^-7; 2 + 2^-7 + 2^-15 rounds to 2 + 2^-6, else 2; both biases exact as two BF16 parts)
+    feeding m = h0 / 2 + h1 / 4: each flip and both together give the closed-form outputs."""
     dims = sg.mlp_dims(sg.NEDF_IN, 1, 8, 2)
     w = np.zeros(sg.mlp_param_count(dims))
     off = sg.NEDF_IN * 8
-    w[off] = 1.0 + 2.0 ** -8 - 3e-7
-    w[off + 1] = 2.0 + 2.0 ** -7 + 5e-7
+    w[off] = 1.0 + 2.0 ** -8 - 2.0 ** -16
+    w[off + 1] = 2.0 + 2.0 ** -7 + 2.0 ** -15
     w[off + 8] = 0.5                                             # W_out[0][0]
     w[off + 8 + 1] = 0.25                                        # W_out[0][1]
     x = np.zeros(sg.NEDF_IN)

@@ -198,6 +198,8 @@ def test_mlp_fp8_mode_matches_torch_float8(orc):
         fi, fo = dims[l], dims[l + 1]
         W = w[off: off + fi * fo].reshape(fo, fi); off += fi * fo
         b = t(w[off: off + fo]); off += fo
+        if l == 0:                               # the BF16 first layer: the bias as two BF16 parts
+            b = bf(b.numpy()) + bf((b - bf(b.numpy())).numpy())
         if 0 < l < n - 1:
             s = 2.0 ** np.ceil(np.log2(np.abs(W).max() / 448.0))
             Wq = s * f8(W / s)
@@ -223,6 +225,8 @@ def test_mlp_bf16_mode_matches_torch_rounded_operands(orc):
         fi, fo = dims[l], dims[l + 1]
         W = bf(w[off: off + fi * fo].reshape(fo, fi)); off += fi * fo
         b = torch.tensor(w[off: off + fo]); off += fo
+        if l + 1 < len(dims) - 1:                # hidden layers: the bias as two BF16 parts
+            b = bf(b.numpy()) + bf((b - bf(b.numpy())).numpy())
         hq = bf(h.numpy()) if l else bf(x)
         h = hq @ W.T + b
         if l + 1 < len(dims) - 1:
