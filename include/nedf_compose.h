@@ -78,7 +78,8 @@ enum nedf_arch {            /* the NeDF network of every type                   
                                Eq. 4.  Packed weights W[out][in] then b[out]: head, per block W1,
                                b1, W2, b2, tail A, tail B (2,413,249 floats).  BF16 precision only
                                for rendering; training (loss_grad, train_step) uses the BCE loss of
-                               Eq. 6 in FP32 with the dense products in cuBLAS */
+                               Eq. 6 with every dense product a BF16 tensor-core GEMM (FP32
+                               accumulation, FP32 master weights) */
 };
 enum nedf_depth_source {    /* what answers the (ray, instance) depth queries of Steps 1 and 3 */
     NEDF_DEPTH_NEDF = 0,    /* the Neural Depth Field (the method)                             */
@@ -421,8 +422,10 @@ int nedf_compose_make_labels_density(nedf_handle *h, int type, int64_t n_rays, u
  * (m - m*)^2 plus 0.1 * mean BCE(a, hit*).  NEDF_ARCH_CLASSIFIER (Eq. 6 itself): mean over
  * labelled hits of BCE(coarse logits, one-hot S_c(m*)) + BCE(fine logits, one-hot S_f(m*)), each
  * the mean over its bins, plus 0.1 * mean BCE(hit logit, hit*); the segment operator S takes
- * u = (m* + 1) 32 to c = floor(u), f = floor((u - c) 128); dense products in cuBLAS.  FP32 master
- * weights and moments; the rendering copy is refreshed.  loss_host (host float, may be NULL)
+ * u = (m* + 1) 32 to c = floor(u), f = floor((u - c) 128).  Products: FP32 on CUDA cores for an
+ * FP32 handle's regression NeDF; otherwise BF16 operands on the tensor cores with FP32 accumulation
+ * (activations and error signals rounded to BF16 between products).  FP32 master weights and
+ * moments; the rendering copy is refreshed.  loss_host (host float, may be NULL)
  * receives the loss of this batch; giving it synchronises.  Errors: NEDF_ERR_STATE (no training
  * set for the type), NEDF_ERR_ARG, NEDF_ERR_CUDA. */
 int nedf_compose_train_step(nedf_handle *h, int type, int batch, float lr, float *loss_host);

@@ -3,7 +3,6 @@
 // Host side of the renderer: argument checks, ownership of device workspace, weight layout
 // conversion, and the launch sequence of each call.  All arithmetic of the method runs in the
 // kernels; this file only moves and validates data.
-#include <cublas_v2.h>
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
@@ -67,7 +66,6 @@ struct nedf_handle {
     Counters *d_cnt = nullptr;
     float *d_train_scratch = nullptr;
     size_t train_scratch_bytes = 0;
-    cublasHandle_t cublas = nullptr;             // classifier training's dense products (created on first use)
     float *d_loss = nullptr;
     std::vector<TrainState> train;
     std::vector<DevType> types_host;
@@ -391,7 +389,6 @@ void nedf_compose_destroy(nedf_handle *h)
         for (void *p : tp)
             if (p) cudaFree(p);
     }
-    if (h->cublas) cublasDestroy(h->cublas);
     if (h->h_frame) cudaFreeHost(h->h_frame);
     if (h->h_cam) cudaFreeHost(h->h_cam);
     for (cudaEvent_t e : h->ev)
@@ -1178,13 +1175,6 @@ static bool train_on_tensor_cores(const nedf_handle *h)
 static int ensure_train_scratch(nedf_handle *h, int batch)
 {
     const bool cls = h->cfg.nedf_arch == NEDF_ARCH_CLASSIFIER;
-    if (cls && !h->cublas) {
-        if (cublasCreate(&h->cublas) != CUBLAS_STATUS_SUCCESS) {
-            h->cublas = nullptr;
-            return fail(h, NEDF_ERR_CUDA, "cublasCreate");
-        }
-    }
-    if (cls && cublasSetStream(h->cublas, h->stream) != CUBLAS_STATUS_SUCCESS) return fail(h, NEDF_ERR_CUDA, "cublasSetStream");
     size_t need = cls ? cls_train_scratch_bytes(batch)
                   : train_on_tensor_cores(h) ? train_tc_scratch_bytes(batch, h->cfg.nedf_hidden, h->cfg.nedf_width, h->nedf_params)
                                              : train_scratch_bytes(batch, h->cfg.nedf_hidden, h->cfg.nedf_width, h->nedf_params);
@@ -1205,7 +1195,7 @@ static ClsTrainLaunch make_cls_train_launch(nedf_handle *h, int type)
     L.master = h->train[type].master;
     L.scratch = h->d_train_scratch;
     L.loss = h->d_loss;
-    L.cublas = h->cublas;
+    L.status = h->d_status;
     L.num_sms = h->num_sms;
     L.stream = h->stream;
     return L;

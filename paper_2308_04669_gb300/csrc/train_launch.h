@@ -56,14 +56,15 @@ cudaError_t launch_train_step(const TrainLaunch &L, const float *o, const float 
                               const float *hit_star, long long n_rays, long long start, int batch,
                               float *adam_m, float *adam_v, int step, float lr);
 
-// The paper's classifier network (train_cls.cu): Eq. 6 and its gradient by hand, dense products
-// in cuBLAS, Adam; the scratch holds a batch's activations (cls_train_scratch_bytes).
+// The paper's classifier network (train_cls.cu): Eq. 6 and its gradient by hand, the dense
+// products as BF16 tcgen05 GEMMs with FP32 accumulation, Adam; the scratch holds a batch's
+// activations (cls_train_scratch_bytes).
 struct ClsTrainLaunch {
     float rb;
     float *master;           // packed FP32 weights (head, 16 x (W1, b1, W2, b2), tail A, tail B)
     float *scratch;
     float *loss;             // device float[4]: loss, hit rows
-    void *cublas;            // cublasHandle_t bound to stream
+    uint32_t *status;        // device status word (bounded waits)
     int num_sms;
     cudaStream_t stream;
 };

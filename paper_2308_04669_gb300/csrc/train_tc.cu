@@ -19,6 +19,7 @@
 #include "mlp_f32.cuh"
 #include "tc_gemm.cuh"
 #include "train_launch.h"
+#include "train_tc.cuh"
 
 namespace nedf {
 
@@ -333,7 +334,8 @@ __global__ void __launch_bounds__(256) k_tc_out_grad(const __nv_bfloat16 *hL, co
     }
 }
 
-__global__ void k_tc_sum_splits(const float *partial, int splits, long long n, float *grad)
+namespace trn {
+__global__ void k_sum_splits(const float *partial, int splits, long long n, float *grad)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         float acc = 0.0f;
@@ -341,6 +343,7 @@ __global__ void k_tc_sum_splits(const float *partial, int splits, long long n, f
         grad[i] = acc;
     }
 }
+}  // namespace trn
 
 // ---- one forward / backward pass ----------------------------------------------------------------
 template <int BN, class Epi>
@@ -404,7 +407,7 @@ static cudaError_t run_tc(const TrainLaunch &L, const float *o, const float *d, 
     }
     k_tc_out_grad<W><<<dim3(splits, W / 32), 256, 0, st>>>(s.h[nl], s.dy, B, kTcSplitRows, s.partial, L.n_params,
                                                             packed_off(nl, W));
-    k_tc_sum_splits<<<(int)std::min<long long>((L.n_params + 255) / 256, (long long)L.num_sms * 8), 256, 0, st>>>(
+    trn::k_sum_splits<<<(int)std::min<long long>((L.n_params + 255) / 256, (long long)L.num_sms * 8), 256, 0, st>>>(
         s.partial, splits, L.n_params, s.grad);
     return cudaGetLastError();
 }

@@ -124,8 +124,11 @@ def _fine_centres(m):
 
 
 def test_classifier_loss_and_gradient_match_oracle(orc):
-    """Eq. 6 and its gradient on the GPU (FP32, dense products in cuBLAS) against the oracle's
-    hand-written FP64 backward pass, on march labels of a sphere."""
+    """Eq. 6 and its gradient on the GPU (every dense product a BF16 tensor-core GEMM with FP32
+    accumulation, the residual stream and error signals BF16 between products) against the
+    oracle's hand-written FP64 backward pass, on march labels of a sphere.  The BF16 bound: the loss
+    within 1 %, the whole gradient within 5 % in norm and every layer within 15 % of its norm (34
+    layers of BF16 rounding; the measured figures are printed)."""
     import torch
     from paper_2308_04669_gb300 import native
     sc = sg.classifier_scene(16, 16)
@@ -148,12 +151,15 @@ def test_classifier_loss_and_gradient_match_oracle(orc):
     assert 5 < hit.sum() < n - 5
     ol, og = orc.cls_loss_grad(sc.types[0].nedf_w.astype(np.float64), np.array(X), ms.cpu().numpy().astype(np.float64), hit)
     gg = g.cpu().numpy().astype(np.float64)
-    assert abs(loss - ol) <= 1e-4 * abs(ol), (loss, ol)
-    assert np.linalg.norm(gg - og) <= 1e-3 * np.linalg.norm(og)
+    rel = np.linalg.norm(gg - og) / np.linalg.norm(og)
     offs = np.cumsum([0] + [fi * fo + fo for fi, fo in sg.cls_layers()])
-    for li in range(len(offs) - 1):                      # every layer, not only the largest terms
-        a, b = gg[offs[li]:offs[li + 1]], og[offs[li]:offs[li + 1]]
-        assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b) + 1e-9, li
+    per_layer = [float(np.linalg.norm(gg[offs[li]:offs[li + 1]] - og[offs[li]:offs[li + 1]]) /
+                       (np.linalg.norm(og[offs[li]:offs[li + 1]]) + 1e-30)) for li in range(len(offs) - 1)]
+    print(f"loss gpu {loss:.6f} oracle {ol:.6f}; |g - g_fp64| / |g_fp64| = {rel:.3e}; "
+          f"per layer max {max(per_layer):.3e} median {np.median(per_layer):.3e}")
+    assert abs(loss - ol) <= 1e-2 * abs(ol), (loss, ol)
+    assert rel <= 5e-2
+    assert max(per_layer) <= 0.15, per_layer
     r.close()
 
 
