@@ -37,6 +37,7 @@ struct TcTrainScratch {
     __nv_bfloat16 *wb;           // BF16 weights: layer 0 [W][80], layers 1 .. L-1 [W][W], output [2][W]
     float *dy;                   // [B][2]
     float *grad;                 // [n_params]
+    trn::WgradJob *jobs;         // the weight-gradient tiles (device copy)
     float *partial;              // [splits][n_params]
 };
 
@@ -49,7 +50,7 @@ size_t train_tc_scratch_bytes(int batch, int hidden, int width, long long n_para
     const size_t B = (size_t)batch, splits = (B + kTcSplitRows - 1) / kTcSplitRows;
     size_t bytes = align256(B * kNedfInPad * 2) + 2 * (size_t)hidden * align256(B * width * 2) +
                    align256((size_t)wb_elems(hidden, width) * 2) + align256(B * 2 * 4) + align256(n_params * 4) +
-                   splits * (size_t)n_params * 4;
+                   align256(sizeof(trn::WgradJob) * 16) + splits * (size_t)n_params * 4;
     return bytes + 256;
 }
 
@@ -63,6 +64,7 @@ static TcTrainScratch carve_tc(void *base, int B, int L, int W, long long n_para
     s.wb = reinterpret_cast<__nv_bfloat16 *>(p); p += align256((size_t)wb_elems(L, W) * 2);
     s.dy = reinterpret_cast<float *>(p); p += align256((size_t)B * 2 * 4);
     s.grad = reinterpret_cast<float *>(p); p += align256((size_t)n_params * 4);
+    s.jobs = reinterpret_cast<trn::WgradJob *>(p); p += align256(sizeof(trn::WgradJob) * 16);
     s.partial = reinterpret_cast<float *>(p);
     return s;
 }
@@ -128,100 +130,6 @@ __global__ void k_tc_encode(float rb, const float *o, const float *d, long long 
     }
     for (int off = 16; off; off >>= 1) hits += __shfl_down_sync(0xffffffffu, hits, off);
     if ((threadIdx.x & 31) == 0 && hits != 0.0f) atomicAdd(loss_hits, hits);
-}
-
-// ---- GEMM epilogues --------------------------------------------------------------------------------
-// forward: out[row][n] = BF16(ReLU(acc + bias[n]))
-struct EpiForward {
-    __nv_bfloat16 *out;
-    const float *bias;
-    int M, W;
-    __device__ __forceinline__ void operator()(int row, int c0, const uint32_t (&v)[32]) const
-    {
-        if (row >= M || c0 >= W) return;
-        uint32_t pk[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-            pk[i] = tc::pack_bf16_relu(__uint_as_float(v[2 * i]) + __ldg(bias + c0 + 2 * i),
-                                       __uint_as_float(v[2 * i + 1]) + __ldg(bias + c0 + 2 * i + 1));
-        uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)row * W + c0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-    }
-};
-
-// backward: out[row][n] = BF16(acc * [h[row][n] > 0])
-struct EpiBackward {
-    __nv_bfloat16 *out;
-    const __nv_bfloat16 *h;
-    int M, W;
-    __device__ __forceinline__ void operator()(int row, int c0, const uint32_t (&v)[32]) const
-    {
-        if (row >= M || c0 >= W) return;
-        const uint4 *hs = reinterpret_cast<const uint4 *>(h + (size_t)row * W + c0);
-        uint32_t pk[16];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint4 hv = hs[q];
-            const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int i = 4 * q + j;
-                // a BF16 activation is positive iff its low and high halves have sign 0 and are nonzero
-                const float m0 = ((hw[j] & 0xFFFFu) != 0u && !(hw[j] & 0x8000u)) ? 1.0f : 0.0f;
-                const float m1 = ((hw[j] >> 16) != 0u && !(hw[j] & 0x80000000u)) ? 1.0f : 0.0f;
-                pk[i] = tc::pack_bf16(__uint_as_float(v[2 * i]) * m0, __uint_as_float(v[2 * i + 1]) * m1);
-            }
-        }
-        uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)row * W + c0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-    }
-};
-
-// weight gradient of one layer, one split: row = output feature, column n < fi: dW[row][n],
-// column n == ones (the synthesized column of ones): db[row]; written into the split's partial
-// gradient in the packed layout
-struct EpiWeightGrad {
-    float *partial;              // this layer's block of split 0
-    long long split_stride;
-    int fo, fi, ones;
-    __device__ __forceinline__ void operator()(int row, int c0, const uint32_t (&v)[32]) const
-    {
-        if (row >= fo) return;
-        float *p = partial + blockIdx.z * split_stride;       // blockIdx.z: the split
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int n = c0 + i;
-            if (n < fi) p[(long long)row * fi + n] = __uint_as_float(v[i]);
-            else if (n == ones) p[(long long)fo * fi + row] = __uint_as_float(v[i]);
-        }
-    }
-};
-
-// One 128 x BN tile per CTA: blockIdx.x = 128-row block of M (N fits one block).
-template <int BN, class Epi>
-__global__ void __launch_bounds__(tcg::kThreads) k_tc_gemm(Operand A, Operand B, long long k_total, Epi epi,
-                                                           uint32_t *status)
-{
-    tcg::gemm_tile<BN, kTcStagesRow>(A, B, blockIdx.x * tcg::kBM, 0, 0, k_total, epi, status, kStatusTimeout);
-}
-
-// The weight and bias gradients of every hidden layer in one launch: blockIdx.y = layer,
-// blockIdx.z = split of the batch (rows z * split_rows .. ), each layer's [dW | db] one tile.
-struct WgradLayers {
-    Operand a[16], b[16];
-    EpiWeightGrad epi[16];
-};
-
-template <int BN>
-__global__ void __launch_bounds__(tcg::kThreads) k_tc_wgrad(WgradLayers P, long long k_total, int split_rows,
-                                                            uint32_t *status)
-{
-    const int l = blockIdx.y;
-    const long long kb = (long long)blockIdx.z * split_rows;
-    const long long ke = kb + split_rows < k_total ? kb + split_rows : k_total;
-    tcg::gemm_tile<BN, kTcStagesWgrad>(P.a[l], P.b[l], 0, 0, kb, ke, P.epi[l], status, kStatusTimeout);
 }
 
 // ---- loss, output layer, first error signal ----------------------------------------------------
@@ -346,69 +254,61 @@ __global__ void k_sum_splits(const float *partial, int splits, long long n, floa
 }  // namespace trn
 
 // ---- one forward / backward pass ----------------------------------------------------------------
-template <int BN, class Epi>
-static cudaError_t gemm(const Operand &A, const Operand &B, int m_blocks, long long k_total, const Epi &epi,
-                        uint32_t *status, cudaStream_t st)
-{
-    using SM = tcg::GemmSmem<BN, kTcStagesRow>;
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::BYTES);
-    if (e != cudaSuccess) return e;
-    k_tc_gemm<BN, Epi><<<m_blocks, tcg::kThreads, SM::BYTES, st>>>(A, B, k_total, epi, status);
-    return cudaGetLastError();
-}
-
 template <int W>
 static cudaError_t run_tc(const TrainLaunch &L, const float *o, const float *d, const float *m_star,
                           const float *hit_star, long long start, long long n, int B, TcTrainScratch s)
 {
     cudaStream_t st = L.stream;
     const int nl = L.hidden;
+    uint32_t *status = L.status;
+    const uint32_t flag = kStatusTimeout;
     cudaError_t e = cudaMemsetAsync(L.loss, 0, sizeof(float) * 4, st);
     if (e != cudaSuccess) return e;
+#define CK_(x) do { if ((e = (x)) != cudaSuccess) return e; } while (0)
     k_tc_pack_weights<<<L.num_sms * 2, 256, 0, st>>>(L.master, s.wb, nl, W);
     const int eb = (int)std::min<long long>((B + 255) / 256, (long long)L.num_sms * 8);
     k_tc_encode<<<eb, 256, 0, st>>>(L.rb, o, d, start, n, B, s.x0, L.loss + 1, hit_star);
-    const int mb = (B + tcg::kBM - 1) / tcg::kBM;
-    // forward
+    // forward: H_{l+1} = BF16(ReLU(H_l Wb_l^T + b_l))
     for (int l = 0; l < nl; ++l) {
         const int fi = l == 0 ? kNedfInPad : W;
         const Operand A{l == 0 ? s.x0 : s.h[l], fi, B, fi, tcg::kKMajor, -1};
         const Operand Bw{s.wb + wb_off(l, W), fi, W, fi, tcg::kKMajor, -1};
-        const EpiForward epi{s.h[l + 1], L.master + packed_off(l, W) + (long long)(l == 0 ? kNedfIn : W) * W, B, W};
-        if ((e = gemm<W>(A, Bw, mb, fi, epi, L.status, st)) != cudaSuccess) return e;
+        const float *bias = L.master + packed_off(l, W) + (long long)(l == 0 ? kNedfIn : W) * W;
+        CK_((trn::rows_gemm<W, kTcStagesRow>(A, Bw, B, fi, trn::EpiForward<true, false>{s.h[l + 1], bias, nullptr, B, W, W},
+                                             status, flag, st)));
     }
     // loss, dy, first error signal
     k_tc_loss<W><<<eb, 256, 0, st>>>(s.h[nl], s.wb + wb_off(nl, W), L.master + packed_off(nl, W) + 2LL * W, o, d, m_star,
                                      hit_star, L.rb, start, n, B, s.dy, s.dz[nl - 1], L.loss);
-    // backward through the hidden layers
+    // backward through the hidden layers: dZ_{l-1} = BF16((dZ_l Wb_l) * [H_l > 0])
     for (int l = nl - 1; l >= 1; --l) {
         const Operand A{s.dz[l], W, B, W, tcg::kKMajor, -1};
         const Operand Bw{s.wb + wb_off(l, W), W, W, W, tcg::kMNMajor, -1};       // element (i, o) = W_l[o][i]
-        const EpiBackward epi{s.dz[l - 1], s.h[l], B, W};
-        if ((e = gemm<W>(A, Bw, mb, W, epi, L.status, st)) != cudaSuccess) return e;
+        CK_((trn::rows_gemm<W, kTcStagesRow>(A, Bw, B, W, trn::EpiBackward<false>{s.dz[l - 1], s.h[l], nullptr, B, W, W},
+                                             status, flag, st)));
     }
-    // weight and bias gradients of every hidden layer, split over the batch, one launch
-    const int splits = (B + kTcSplitRows - 1) / kTcSplitRows;
-    WgradLayers P{};
+    // weight and bias gradients of every hidden layer, split over the batch, one launch: per layer
+    // one tile [dW | db] = dZ^T [H | 1], the ones row after the layer's inputs
+    trn::WgradJob jobs[16];
     for (int l = 0; l < nl; ++l) {
         const int fi = l == 0 ? kNedfIn : W, fip = l == 0 ? kNedfInPad : W;
-        P.a[l] = Operand{s.dz[l], W, W, B, tcg::kMNMajor, -1};                    // (o, b) = dZ_l[b][o]
-        P.b[l] = Operand{l == 0 ? s.x0 : s.h[l], fip, fip, B, tcg::kMNMajor, fip}; // (i, b) = H_l[b][i]; row fip = 1
-        P.epi[l] = EpiWeightGrad{s.partial + packed_off(l, W), L.n_params, W, fi, fip};
+        trn::WgradJob j{};
+        j.a = Operand{s.dz[l], W, W, B, tcg::kMNMajor, -1};                      // (o, b) = dZ_l[b][o]
+        j.b = Operand{l == 0 ? s.x0 : s.h[l], fip, fip, B, tcg::kMNMajor, fip};  // (i, b) = H_l[b][i]; row fip = 1
+        j.m0 = 0; j.n0 = 0; j.c_lo = 0; j.c_hi = fi; j.fo = W; j.fi = fi; j.ones = fip; j.seg_split = W;
+        j.w_off[0] = packed_off(l, W); j.b_off[0] = packed_off(l, W) + (long long)fi * W;
+        jobs[l] = j;
     }
-    {
-        // the widest B operand: 80 inputs of layer 0 or W, then the 8-row group of the ones row
-        constexpr int BN = (W > kNedfInPad ? W : kNedfInPad) + 16;
-        using SM = tcg::GemmSmem<BN, kTcStagesWgrad>;
-        if ((e = cudaFuncSetAttribute(k_tc_wgrad<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::BYTES)) !=
-            cudaSuccess)
-            return e;
-        k_tc_wgrad<BN><<<dim3(1, nl, splits), tcg::kThreads, SM::BYTES, st>>>(P, B, kTcSplitRows, L.status);
-    }
+    CK_(cudaMemcpyAsync(s.jobs, jobs, sizeof(trn::WgradJob) * nl, cudaMemcpyHostToDevice, st));
+    // the widest B operand: 80 inputs of layer 0 or W, then the 8-row group of the ones row
+    constexpr int BN = (W > kNedfInPad ? W : kNedfInPad) + 16;
+    CK_((trn::wgrad<BN, kTcStagesWgrad>(s.jobs, nl, B, kTcSplitRows, s.partial, L.n_params, status, flag, st)));
+    const int splits = (B + kTcSplitRows - 1) / kTcSplitRows;
     k_tc_out_grad<W><<<dim3(splits, W / 32), 256, 0, st>>>(s.h[nl], s.dy, B, kTcSplitRows, s.partial, L.n_params,
                                                             packed_off(nl, W));
     trn::k_sum_splits<<<(int)std::min<long long>((L.n_params + 255) / 256, (long long)L.num_sms * 8), 256, 0, st>>>(
         s.partial, splits, L.n_params, s.grad);
+#undef CK_
     return cudaGetLastError();
 }
 
