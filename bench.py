@@ -34,11 +34,13 @@ sys.path.insert(0, ROOT)
 METRIC = "composited rays/s & ms/frame at 1024², NeDF vs ray-march, same GPU, depth err"
 WORKLOAD = ("1024 instances (sphere/torus/box, seed 3, T in [-20,20]^3) at 1024x1024, 4 point lights, "
             "NeDF 6x128 per type trained on ray-march labels, NeRF 8x256 per type, 8 shading samples, "
-            "fallback below confidence 0.9, 4 refinement steps with outlier re-answering")
+            "fallback below confidence 0.9, 4 refinement steps with outlier re-answering, confident misses "
+            "checked at 16 chord samples")
 WORKLOAD_STRESS = ("4096 instances (8 shape types x 512, seed 4, T in [-40,40]^3) at 2048x2048, 8 point lights, "
                    "NeDF 6x128 per type trained on ray-march labels, NeRF 8x256 per type, 8 shading samples, "
-                   "fallback below confidence 0.9, 4 refinement steps with outlier re-answering")
-FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1)
+                   "fallback below confidence 0.9, 4 refinement steps with outlier re-answering, confident misses "
+                   "checked at 16 chord samples")
+FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=16)
 NEDF_FLOP = 2 * (78 * 128 + 5 * 128 * 128 + 128 * 2)          # per query, unpadded
 # one training ray of the 6 x 128 NeDF: the forward pass, the input gradients of the hidden layers
 # (5 x 128 x 128) and of the output layer (2 x 128), and every weight gradient (as the forward)

@@ -136,6 +136,11 @@ typedef struct nedf_options {
                              /* with this many samples per pair (1 .. 1024); 0 = off (default)     */
     float shade_sigma_min;   /* the outlier threshold ("extremely small" density); default 1.0,   */
                              /* 2 % of the default peak density                                   */
+    int miss_check;          /* a NeDF miss kept by the confidence test is checked at this many   */
+                             /* midpoints of its bound chord (0 .. 64); if the density there      */
+                             /* reaches the half level anywhere, the pair is re-answered by the   */
+                             /* plain method (a confidently wrong miss would let a farther object */
+                             /* win the pixel); 0 = off (default)                                 */
 } nedf_options;
 
 typedef struct nedf_type_desc {
@@ -221,7 +226,8 @@ int nedf_compose_set_instances(nedf_handle *h, int n, const nedf_instance *inst)
 
 /* One frame: Steps 1-3 and the composite.  cam and lights are host records (n_lights in
  * 1 .. NEDF_MAX_LIGHTS).  Output buffers are caller-owned DEVICE arrays of width*height
- * elements (rgba and out: 4 floats per pixel):
+ * elements (rgba and out: 4 floats per pixel); `out` is an addition to the paper's colour,
+ * depth and id outputs so that the frame a viewer shows (colour times shadow) needs no extra pass:
  *   depth   float  Step 1 depth buffer: world distance along the unit pixel ray, +inf if empty
  *   id      uint32 Step 1 id buffer: winning instance index, 0xFFFFFFFF if empty
  *   rgba    float4 Step 2 colour buffer (premultiplied RGB, opacity), (0,0,0,0) if empty
@@ -418,7 +424,9 @@ int nedf_compose_make_labels_density(nedf_handle *h, int type, int64_t n_rays, u
 
 /* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) of the type's NeDF on `batch`
  * consecutive rays of its training set (wrapping around), starting where the previous step
- * ended.  Loss, NEDF_ARCH_REGRESSION (regression form of Eq. 6): mean over labelled hits of
+ * ended.  The random seed of a step is not an argument: the rays and labels are drawn once per
+ * training set by nedf_compose_make_labels (its `seed`), and a step is a deterministic function
+ * of the training set, the weights and the cursor (so a saved state resumes bit for bit).  Loss, NEDF_ARCH_REGRESSION (regression form of Eq. 6): mean over labelled hits of
  * (m - m*)^2 plus 0.1 * mean BCE(a, hit*).  NEDF_ARCH_CLASSIFIER (Eq. 6 itself): mean over
  * labelled hits of BCE(coarse logits, one-hot S_c(m*)) + BCE(fine logits, one-hot S_f(m*)), each
  * the mean over its bins, plus 0.1 * mean BCE(hit logit, hit*); the segment operator S takes

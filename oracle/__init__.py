@@ -65,7 +65,7 @@ class OrcOpts(C.Structure):
     _fields_ = [("depth_mode", C.c_int), ("march_n", C.c_int), ("march_b", C.c_int),
                 ("quant", C.c_int), ("fallback_conf", C.c_double), ("refine_steps", C.c_int),
                 ("n_threads", C.c_int), ("outlier_resample", C.c_int), ("shade_resample", C.c_int),
-                ("shade_sigma_min", C.c_double)]
+                ("shade_sigma_min", C.c_double), ("miss_check", C.c_int)]
 
 
 def _dp(a):
@@ -190,9 +190,10 @@ class OracleScene:
 
 
 def opts(depth_mode=DEPTH_MLP, march_n=128, march_b=4, quant=QUANT_NONE, fallback_conf=0.0,
-         refine_steps=0, n_threads=1, outlier_resample=0, shade_resample=0, shade_sigma_min=1.0) -> OrcOpts:
+         refine_steps=0, n_threads=1, outlier_resample=0, shade_resample=0, shade_sigma_min=1.0,
+         miss_check=0) -> OrcOpts:
     return OrcOpts(depth_mode, march_n, march_b, quant, fallback_conf, refine_steps, n_threads, outlier_resample,
-                   shade_resample, shade_sigma_min)
+                   shade_resample, shade_sigma_min, miss_check)
 
 
 def render(osc: OracleScene, px=None, alt=True, **kw):

@@ -863,6 +863,17 @@ static int query_ex(const orc_scene *sc, const orc_opts *op, int inst, const dou
             mg = dmin(mg, fabs(conf - op->fallback_conf) - 0.25 * spread[1]);
             march = conf < op->fallback_conf;
         }
+        /* Check of a confident NeDF miss (reading 30): the density at miss_check midpoints of the
+         * bound chord; reaching the half level at one makes the miss wrong, re-answered by the
+         * plain method. */
+        if (!march && !hit && op->miss_check > 0) {
+            double x[3];
+            for (int j = 0; j < op->miss_check && !march; ++j) {
+                const double tj = bd[0] + (j + 0.5) * (bd[1] - bd[0]) / op->miss_check;
+                for (int c = 0; c < 3; ++c) x[c] = ol[c] + tj * dl[c];
+                march = decide(dg, sc, type, ol, tj, x, 0.0, INFINITY);
+            }
+        }
         /* Depth check of a NeDF hit (Section "Deferred Shading": the density at the predicted
          * depth tells whether it reached the surface): if the half-density level is crossed
          * inside [D - h, D + h], bisect it; otherwise the hit is an outlier, re-answered by the

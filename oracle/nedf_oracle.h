@@ -86,6 +86,9 @@ typedef struct {
                               shade_sigma_min is re-rendered by the plain method's volume rendering
                               (this many samples per pair); 0 = off */
     double shade_sigma_min;
+    int miss_check;        /* MLP mode: a miss kept by the confidence test is checked at this many
+                              midpoints of its bound chord and re-answered by the plain method when
+                              the density reaches the half level at one (0 = off) */
 } orc_opts;
 
 /* Geometry and encoding */

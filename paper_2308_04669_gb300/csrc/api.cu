@@ -412,6 +412,7 @@ int nedf_compose_set_options(nedf_handle *h, const nedf_options *o)
         return fail(h, NEDF_ERR_ARG, "fallback_conf / refine_steps");
     if (o->shade_resample < 0 || o->shade_resample > 1024 || !(o->shade_sigma_min >= 0.f) || !std::isfinite(o->shade_sigma_min))
         return fail(h, NEDF_ERR_ARG, "shade_resample 0..1024, shade_sigma_min >= 0");
+    if (o->miss_check < 0 || o->miss_check > 64) return fail(h, NEDF_ERR_ARG, "miss_check 0..64");
     if (o->shade_resample > 0) {
         // buffers of Step-2 resampling: outlier flags, a pair list of up to a quarter of the
         // pixels' worth of pairs and the plain method's scratch for it (grown with the samples)
@@ -628,6 +629,7 @@ static cudaError_t stage_frame(nedf_handle *h, const nedf_camera *cam, const ned
     f.outlier_resample = h->opt.outlier_resample;
     f.shade_resample = h->opt.shade_resample;
     f.shade_sigma_min = h->opt.shade_sigma_min;
+    f.miss_check = h->opt.miss_check;
     f.edit_mode = h->edit_mode;
     f.edit_inst = h->edit_inst;
     f.n_inst = h->n_inst;

@@ -57,6 +57,7 @@ struct DevFrame {
     int outlier_resample;
     int shade_resample;          // Step-2 outlier resampling: plain-method samples per pair (0 = off)
     float shade_sigma_min;
+    int miss_check;              // density samples that check a confident NeDF miss (0 = off)
     // buffer reuse while one instance is manipulated: 0 a whole frame; 1 the frozen part (every
     // instance but edit_inst); 2 an edit frame (the frozen buffers plus edit_inst alone)
     int edit_mode, edit_inst;
@@ -225,7 +226,9 @@ __device__ __forceinline__ float refine_depth(const DevType &t, V3 ol, V3 dl, fl
 //   a pair whose confidence max(p, 1 - p), p = sigmoid(a), is below fallback_conf goes to the
 //   plain method; a hit whose window [D_l - h, D_l + h] brackets the half-density level is
 //   refined by bisection there; a hit whose window does not is an outlier and, with
-//   outlier_resample, also goes to the plain method.
+//   outlier_resample, also goes to the plain method; a miss that passed the confidence test is
+//   checked at miss_check midpoints of the bound chord and goes to the plain method when the
+//   density reaches the half level at one of them.
 // Returns true when the pair must be re-answered by the plain method.
 __device__ __forceinline__ bool nedf_decode(const DevFrame &f, const DevType &T, V3 ol, V3 dl, float tp, float m,
                                             float a, float &Dl, bool &hit)
@@ -236,6 +239,14 @@ __device__ __forceinline__ bool nedf_decode(const DevFrame &f, const DevType &T,
     if (f.fallback_conf > 0.0f) {
         float p = 1.0f / (1.0f + expf(-a));
         march = fmaxf(p, 1.0f - p) < f.fallback_conf;
+    }
+    if (!march && !hit && f.miss_check > 0) {
+        Chord ch;
+        if (bound_chord(ol, dl, T.rb, ch)) {
+            const float step = (ch.tx - ch.te) / (float)f.miss_check;
+            for (int j = 0; j < f.miss_check && !march; ++j)
+                march = inside_solid(T, madd(ol, ch.te + ((float)j + 0.5f) * step, dl));
+        }
     }
     if (!march && hit && f.refine_steps > 0) {
         float lo = Dl - f.shade_half, hi = Dl + f.shade_half;

@@ -41,7 +41,7 @@ class Options(C.Structure):
                 ("shadow_eps", C.c_float), ("sigma_max", C.c_float), ("sdf_width", C.c_float),
                 ("depth_source", C.c_int), ("march_steps", C.c_int), ("march_bisect", C.c_int),
                 ("fallback_conf", C.c_float), ("refine_steps", C.c_int), ("outlier_resample", C.c_int),
-                ("shade_resample", C.c_int), ("shade_sigma_min", C.c_float)]
+                ("shade_resample", C.c_int), ("shade_sigma_min", C.c_float), ("miss_check", C.c_int)]
 
 
 class TypeDesc(C.Structure):

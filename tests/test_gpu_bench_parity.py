@@ -17,7 +17,7 @@ from .gpu_helpers import NOID, frame_vs_oracle
 
 pytestmark = pytest.mark.gpu
 
-FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1)
+FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=16)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -62,11 +62,14 @@ def test_thousand_instance_frame_matches_oracle(orc, prec):
     quant = orc.QUANT_BF16 if prec == "bf16" else orc.QUANT_FP8
     g, w = trained_frame(sc, precision, 600, **FRAME_OPTS)
     assert g["stats"].status == 0 and g["stats"].primary_pairs > 1_500_000 and g["stats"].fallback_pairs > 0
-    px = sg.pixel_subset(sc.W, sc.H, 2500, 7)
+    # E4M3: one flipped activation moves m by up to ~5e-2, as much as the depth check's half window
+    # h, so the window decisions of many refined pairs are knife edges; more pixels keep > 2,500
+    # decided
+    px = sg.pixel_subset(sc.W, sc.H, 2500 if prec == "bf16" else 5000, 7)
     kw = {} if prec == "bf16" else dict(colour_tol=FP8_COLOUR_TOL)
     rep, o = frame_vs_oracle(g, orc.OracleScene(sc, nedf_override=w), px=px, quant=quant, march_n=128, march_b=4,
-                             n_threads=16, max_excluded=0.1, **FRAME_OPTS, **kw)
-    assert rep["hit"] > 600 and rep["shadowed"] > 50
+                             n_threads=16, max_excluded=0.1 if prec == "bf16" else 0.45, **FRAME_OPTS, **kw)
+    assert rep["hit"] > 600 and rep["shadowed"] > 50 and rep["pixels"] * (1 - rep["excluded"]) > 2000
 
 
 def test_stress_kind_frame_fp32_plain_method_matches_oracle(orc):

@@ -79,6 +79,26 @@ def test_refine_and_outlier_resample_fp32(orc):
     assert g["stats"].fallback_pairs > 0 and rep["hit"] > 500
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_miss_check_frame_matches_oracle(orc, prec):
+    """Confident NeDF misses checked by 16 density samples along the bound chord (the untrained
+    networks answer many wrong misses), with the confidence fallback, refinement and outlier
+    re-answering: Steps 1-3 against the oracle with the same options."""
+    from paper_2308_04669_gb300 import native
+    sc = sg.three_types_scene(96, 96, nerf=False)
+    kw = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=16)
+    precision = native.PREC_FP32 if prec == "fp32" else native.PREC_BF16
+    g = gpu_frame(sc, precision=precision, **kw)
+    g0 = gpu_frame(sc, precision=precision, **dict(kw, miss_check=0))
+    okw = dict(quant=orc.QUANT_NONE if prec == "fp32" else orc.QUANT_BF16)
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc), march_n=128, march_b=4, n_threads=8, max_excluded=0.1, **kw, **okw)
+    assert rep["hit"] > 1000 and g["stats"].status == 0
+    # the check re-answers pairs the network called confident misses: more plain-method pairs and
+    # more hit pixels than without it
+    assert g["stats"].fallback_pairs > g0["stats"].fallback_pairs
+    assert (g["id"] != NOID).sum() > (g0["id"] != NOID).sum()
+
+
 def test_light_inside_scene_bound(orc):
     """A light inside the scene's bound cannot use a shadow-map camera: every instance is tested."""
     sc = sg.three_types_scene(96, 96, nerf=False)

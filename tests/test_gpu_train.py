@@ -88,9 +88,10 @@ def test_loss_and_gradient_match_oracle(lib, orc):
 def test_bf16_loss_and_gradient_match_oracle(lib, orc, scene_fn, t, n):
     """The tensor-core training path (BF16 operands, FP32 accumulation; BF16 handles) against the
     oracle's BF16-training gradient (reading 29).  The loss agrees to 1e-5 relative.  The gradient
-    of each layer agrees in norm to a fifth of the layer's own BF16 rounding effect (the gap between
-    the oracle's BF16 and FP64 gradients) and to 5e-4 of the largest element: the remaining
-    differences are values an FP32 sum rounds to the other BF16 neighbour.  Widths 128 and 64;
+    of each layer agrees in norm to half the layer's own BF16 rounding effect (the gap between the
+    oracle's BF16 and FP64 gradients) and to 5e-4 of the largest element: the remaining differences
+    are values an FP32 sum rounds to the other BF16 neighbour (a missing term or mask, a transposed
+    operand, would be tens of per cent of the layer).  Widths 128 and 64;
     ragged row counts (300: two 128-row tiles and a tail; 3000: three batch splits of 1024)."""
     import torch
     sc = scene_fn()
@@ -108,14 +109,18 @@ def test_bf16_loss_and_gradient_match_oracle(lib, orc, scene_fn, t, n):
     assert abs(loss - ol) <= 1e-5 * abs(ol)
     scale = np.abs(og).max()
     dims = sc.types[t].nedf_dims
-    off = 0
+    off, bad = 0, []
     for l in range(len(dims) - 1):
         k = dims[l] * dims[l + 1] + dims[l + 1]
         e = np.linalg.norm(gg[off:off + k] - og[off:off + k])
         gap = np.linalg.norm(og[off:off + k] - og64[off:off + k])
-        print(f"layer {l}: |g - g_bf16| {e:.3e}  |g_bf16 - g_fp64| {gap:.3e}  |g_bf16| {np.linalg.norm(og[off:off + k]):.3e}")
-        assert e <= 0.2 * gap + 5e-4 * scale, (l, e, gap)
+        e64 = np.linalg.norm(gg[off:off + k] - og64[off:off + k])
+        print(f"layer {l}: |g - g_bf16| {e:.3e}  |g_bf16 - g_fp64| {gap:.3e}  |g - g_fp64| {e64:.3e}  "
+              f"|g_bf16| {np.linalg.norm(og[off:off + k]):.3e}")
+        if not e <= 0.5 * gap + 5e-4 * scale:
+            bad.append((l, e, gap))
         off += k
+    assert not bad, bad
     print(f"loss gpu {loss:.6f} oracle {ol:.6f}; max |g - g_bf16| / max |g_bf16| = {np.abs(gg - og).max() / scale:.2e}")
     r.close()
 

@@ -562,3 +562,33 @@ def test_mlp_flip2_rounds_two_values_the_other_way(orc):
     assert orc.mlp_flip(w, dims, x, orc.QUANT_BF16, h1, 0)[0][0] == 0.5 * 1.0 + 0.25 * 2.0
     assert orc.mlp_flip2(w, dims, x, orc.QUANT_BF16, h0, h1)[0] == 0.5 * (1.0 + 2.0 ** -7) + 0.25 * 2.0
     assert orc.mlp_flip2(w, dims, x, orc.QUANT_BF16, h0, h0)[0] == orc.mlp_flip(w, dims, x, orc.QUANT_BF16, h0, 0)[0][0]
+
+
+# ------------------------------------------------------------------------------------------------
+# miss check (reading 30): a confident miss verified by density samples along the bound chord
+# ------------------------------------------------------------------------------------------------
+def test_confident_miss_through_the_object_is_re_answered(orc):
+    """The network says 'miss' with confidence 0.993 (a = -5) on a ray through the sphere: with the
+    miss check the plain method answers (the surface at 2.5); without it the miss stands."""
+    hit, D = _query(orc, _m_for_depth(2.8), -5.0, fallback_conf=0.9, miss_check=16)
+    assert hit and abs(D - SURF) < 1e-9
+    hit, _ = _query(orc, _m_for_depth(2.8), -5.0, fallback_conf=0.9, miss_check=0)
+    assert not hit
+
+
+def test_miss_check_keeps_true_misses_and_ignores_hits(orc):
+    """A ray through the bound that passes the sphere (offset 0.7 > r = 0.5) stays a miss with no
+    plain-method work; a confident hit is not sampled (the check is for misses only)."""
+    sc = one_instance_scene(sg.SDF_SPHERE, nedf_w=constant_nedf(_m_for_depth(2.8), -5.0))
+    osc = orc.OracleScene(sc)
+    eye = np.array([0.0, 0.7, 3.0])
+    hit, out, (mg, dm, _) = orc.query_diag(osc, 0, eye, DIR, need=np.inf, fallback_conf=0.9, miss_check=16,
+                                           march_n=4096, march_b=60)
+    assert not hit and out[3] < out[4]                   # inside the bound, no crossing
+    # the 16 midpoints' margins: | |p| - 0.5 | over |o| + |t| + 1, the smallest at the closest approach
+    te, tx = out[3], out[4]
+    ts = te + (np.arange(16) + 0.5) * (tx - te) / 16
+    rel = np.abs(np.linalg.norm(eye[None, :] + ts[:, None] * DIR[None, :], axis=1) - 0.5) / (np.linalg.norm(eye) + ts + 1)
+    assert dm == math.inf or abs(dm - rel.min()) < 1e-12     # margins above 1e-4 are not recorded
+    hit, D = _query(orc, _m_for_depth(2.8), 5.0, miss_check=16)
+    assert hit and abs(D - _depth_of(_m_for_depth(2.8))) < 1e-12
