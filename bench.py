@@ -361,6 +361,11 @@ def run_ours(args):
     log = {}
     if args.train_steps > 0:
         train_types(r, sc, args.train_steps, args.train_batch, args.label_rays, log, stream, peaks()[0]["bf16_tflops"])
+        if args.train_only:                 # the learned part alone (profiling)
+            r.close()
+            if rank == 0:
+                print(json.dumps({"train_only": True, **log}), flush=True)
+            return
         ref_w = reference_weights(sc) if args.scene == "thousand" else None
         if ref_w is not None:
             log["train"]["same_weights_as_reference_arm"] = all(
@@ -694,6 +699,8 @@ def main():
                     "Step-1 NeDF, Step-3 NeDF, query), comma-separated; skips the autotuner")
     ap.add_argument("--no-march-dense", dest="march_dense", action="store_false",
                     help="skip the dense 128-sample ray-march frame (timed by default beside the early-stop one)")
+    ap.add_argument("--train-only", action="store_true",
+                    help="only the labels and training steps of the learned part (profiling runs)")
     ap.add_argument("--frames-only", action="store_true",
                     help="timed frames only: no judge, ray-march, FP32, e2e or CPU legs (profiling runs)")
     args = ap.parse_args()

@@ -103,6 +103,7 @@ def lib():
             l.orc_query_diag.argtypes = [sp, op, C.c_int, d, d, d, d, C.c_double]; l.orc_query_diag.restype = C.c_int
             l.orc_mlp_flip.argtypes = [d, C.c_int, i, d, d, C.c_int, C.c_int, C.c_int, i, d]
             l.orc_mlp_flip2.argtypes = [d, C.c_int, i, d, d, C.c_int, C.c_int, C.c_int]
+            l.orc_mlp_flipset.argtypes = [d, C.c_int, i, d, d, C.c_int, C.c_int, i]
             l.orc_volume_render.argtypes = [sp, op, C.c_int, C.c_int64, i64, d, d]
             l.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]; l.orc_splitmix64.restype = C.c_uint64
             l.orc_train_rays.argtypes = [C.c_double, C.c_uint64, C.c_int64, C.c_int, d, d]
@@ -335,6 +336,17 @@ def mlp_flip2(w, dims, x, quant, flip_a, flip_b):
     x = np.ascontiguousarray(x, np.float64)
     y = np.empty(dims[-1])
     lib().orc_mlp_flip2(_dp(w), len(dims) - 1, dims_c, _dp(x), _dp(y), int(quant), int(flip_a), int(flip_b))
+    return y
+
+
+def mlp_flipset(w, dims, x, quant, flips):
+    """The MLP with every rounded value listed in flips taken the other way (see orc_mlp_flipset)."""
+    w = np.ascontiguousarray(w, np.float64)
+    dims_c = (C.c_int * len(dims))(*dims)
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.empty(dims[-1])
+    f = (C.c_int * max(len(flips), 1))(*[int(v) for v in flips])
+    lib().orc_mlp_flipset(_dp(w), len(dims) - 1, dims_c, _dp(x), _dp(y), int(quant), len(flips), f)
     return y
 
 

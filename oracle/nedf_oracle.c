@@ -264,11 +264,18 @@ static double round_fmt(double v, int fmt, int flip)
  *   qmargin   (may be NULL) the row's smallest distance of a rounded value to its rounding
  *             boundary, relative to the scale that bounds another implementation's error there
  *             (sum of |w a| plus |b| for a layer's output, max(|v|, 1/4) for an input feature);
- *   flip_idx  index of one value rounded to its other neighbour (-1: none; flip_idx2 a second);
+ *   flips     the indices of the n_flips values rounded to their other neighbour;
  *   n_cand    the n_cand values of smallest relative margin are listed in cand_idx / cand_margin
  *             (ascending; unused entries get index -1). */
-static void mlp_core2(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
-                      double *qmargin, int flip_idx, int flip_idx2, int n_cand, int *cand_idx, double *cand_margin)
+static int in_flips(int vidx, int n_flips, const int *flips)
+{
+    for (int k = 0; k < n_flips; ++k)
+        if (flips[k] == vidx) return 1;
+    return 0;
+}
+
+static void mlp_core_set(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
+                         double *qmargin, int n_flips, const int *flips, int n_cand, int *cand_idx, double *cand_margin)
 {
     int maxd = 0;
     for (int l = 0; l <= n_layers; ++l) maxd = dims[l] > maxd ? dims[l] : maxd;
@@ -296,7 +303,7 @@ static void mlp_core2(const double *w, int n_layers, const int *dims, const doub
          * an absolute error from the coordinates: its margin is measured against |v| but no less
          * than 1/4 */
         NOTE_MARGIN(orc_round_margin(x[i], 0) / dmax(fabs(x[i]), 0.25));
-        a[i] = round_fmt(x[i], 0, vidx == flip_idx || vidx == flip_idx2);
+        a[i] = round_fmt(x[i], 0, in_flips(vidx, n_flips, flips));
     }
     const double *p = w;
     for (int l = 0; l < n_layers; ++l) {
@@ -335,7 +342,7 @@ static void mlp_core2(const double *w, int n_layers, const int *dims, const doub
                 /* hidden activations: BF16, or E4M3 in the FP8 mode (they feed E4M3 layers) */
                 int fmt = quant == ORC_QUANT_FP8 ? 1 : 0;
                 NOTE_MARGIN(orc_round_margin(b[o], fmt) / dmax(mag, 1e-300));
-                b[o] = round_fmt(b[o], fmt, vidx == flip_idx || vidx == flip_idx2);
+                b[o] = round_fmt(b[o], fmt, in_flips(vidx, n_flips, flips));
                 ++vidx;
             }
         }
@@ -347,6 +354,13 @@ static void mlp_core2(const double *w, int n_layers, const int *dims, const doub
     if (qmargin) *qmargin = qm;
     free(a);
     free(b);
+}
+
+static void mlp_core2(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
+                      double *qmargin, int flip_idx, int flip_idx2, int n_cand, int *cand_idx, double *cand_margin)
+{
+    const int flips[2] = {flip_idx, flip_idx2};
+    mlp_core_set(w, n_layers, dims, x, y, quant, qmargin, 2, flips, n_cand, cand_idx, cand_margin);
 }
 
 static void mlp_core(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
@@ -377,6 +391,12 @@ void orc_mlp_flip2(const double *w, int n_layers, const int *dims, const double 
                    int flip_b)
 {
     mlp_core2(w, n_layers, dims, x, y, quant, NULL, flip_a, flip_b, 0, NULL, NULL);
+}
+
+void orc_mlp_flipset(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
+                     int n_flips, const int *flips)
+{
+    mlp_core_set(w, n_layers, dims, x, y, quant, NULL, n_flips, flips, 0, NULL, NULL);
 }
 
 static int nedf_dims(const orc_type *t, int *dims)

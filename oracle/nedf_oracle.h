@@ -118,6 +118,10 @@ void orc_mlp_flip(const double *w, int n_layers, const int *dims, const double *
 /* orc_mlp with two values (flip_a, flip_b) rounded to their other neighbours. */
 void orc_mlp_flip2(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant, int flip_a,
                    int flip_b);
+/* orc_mlp with the n_flips values whose indices are listed in flips rounded to their other
+ * neighbours (several near-ties of one row may each fall on either side). */
+void orc_mlp_flipset(const double *w, int n_layers, const int *dims, const double *x, double *y, int quant,
+                     int n_flips, const int *flips);
 double orc_round_bf16(double x);
 double orc_round_e4m3(double x);
 double orc_fp8_scale(double max_abs);

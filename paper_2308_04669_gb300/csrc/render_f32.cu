@@ -312,46 +312,78 @@ __global__ void __launch_bounds__(kThreads) k_nedf_tiles(Workspace ws, int shado
 // ---------------------------------------------------------------------------------------------
 // Step 1 resolve: packed keys -> depth / id buffers, per-type lists of pixels to shade
 // ---------------------------------------------------------------------------------------------
-__global__ void k_resolve(Workspace ws, int npix)
+// Each block resolves kResolvePix x 256 pixels at a time: every thread takes kResolvePix pixels
+// 256 apart (coalesced key reads and depth / id writes), ranks its listed pixels inside the
+// block's per-type counts with shared-memory atomics (one per warp and type), and the block then
+// reserves its range of each type's shading list and adds its hit count with one global atomic
+// each, so the frame's few per-type counters see a few hundred atomics instead of one per warp.
+constexpr int kResolvePix = 8;
+
+__global__ void __launch_bounds__(256) k_resolve(Workspace ws, int npix)
 {
+    __shared__ unsigned s_cnt[kMaxTypes];
+    __shared__ unsigned long long s_base[kMaxTypes];
+    __shared__ unsigned s_hits;
     const DevFrame &f = *ws.frame;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
-        unsigned long long k = ws.keys[p];
-        float D = __int_as_float(0x7f800000);
-        uint32_t id = kNoId;
-        const bool hit = k != ~0ull;
-        uint32_t t = 0xFFFFFFFFu;
-        if (hit) {
-            D = __uint_as_float((uint32_t)(k >> 32));
-            id = (uint32_t)(k & 0xffffffffu);
-            t = ws.inst[id].type;
+    const int lane = threadIdx.x & 31;
+    const int n_types = f.n_types;
+    const long long per_block = (long long)kResolvePix * blockDim.x;
+    for (long long b0 = (long long)blockIdx.x * per_block; b0 < npix; b0 += (long long)gridDim.x * per_block) {
+        if (threadIdx.x < kMaxTypes) s_cnt[threadIdx.x] = 0u;
+        if (threadIdx.x == 0) s_hits = 0u;
+        __syncthreads();
+        uint32_t ty[kResolvePix], pos[kResolvePix];
+#pragma unroll
+        for (int i = 0; i < kResolvePix; ++i) {
+            const long long p = b0 + (long long)i * blockDim.x + threadIdx.x;
+            const bool in = p < npix;
+            const unsigned long long k = in ? ws.keys[p] : ~0ull;
+            float D = __int_as_float(0x7f800000);
+            uint32_t id = kNoId;
+            const bool hit = k != ~0ull;
+            uint32_t t = 0xFFFFFFFFu;
+            if (hit) {
+                D = __uint_as_float((uint32_t)(k >> 32));
+                id = (uint32_t)(k & 0xffffffffu);
+                t = ws.inst[id].type;
+            }
+            // an edit frame shades and fully re-shadows only the pixels the manipulated instance
+            // wins; every other pixel keeps the frozen part's colour and occlusion bits
+            if (f.edit_mode == 2 && hit) {
+                const bool listed = id == (uint32_t)f.edit_inst;
+                if (listed) ws.occl[p] = 0u;
+                else ws.rgba[p] = ws.edit_rgba[p];
+                if (!listed) t = 0xFFFFFFFFu;
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, t);
+            const unsigned hits = __ballot_sync(0xffffffffu, hit);
+            uint32_t r = 0u;
+            if (t != 0xFFFFFFFFu) {
+                const int leader = __ffs(peers) - 1;
+                if (lane == leader) r = atomicAdd(&s_cnt[t], (unsigned)__popc(peers));
+                r = __shfl_sync(peers, r, leader) + __popc(peers & ((1u << lane) - 1u));
+            }
+            if (lane == 0 && hits) atomicAdd(&s_hits, (unsigned)__popc(hits));
+            ty[i] = t;
+            pos[i] = r;
+            if (in) {
+                ws.depth[p] = D;
+                ws.id[p] = id;
+                if (!hit) ws.rgba[p] = make_float4(0.f, 0.f, 0.f, 0.f);   // hit pixels are written by Step 2
+            }
         }
-        // an edit frame shades and fully re-shadows only the pixels the manipulated instance
-        // wins; every other pixel keeps the frozen part's colour and occlusion bits
-        bool listed = hit;
-        if (f.edit_mode == 2 && hit) {
-            listed = id == (uint32_t)f.edit_inst;
-            if (listed) ws.occl[p] = 0u;
-            else ws.rgba[p] = ws.edit_rgba[p];
-            if (!listed) t = 0xFFFFFFFFu;
+        __syncthreads();
+        if (threadIdx.x < n_types) {
+            const unsigned c = s_cnt[threadIdx.x];
+            s_base[threadIdx.x] = c ? atomicAdd(&ws.cnt->h_count[threadIdx.x], (unsigned long long)c) : 0ull;
         }
-        // one atomic per (warp, type) and one per warp for the hit count: a few types share
-        // their counters across the whole frame
-        const unsigned act = __activemask();
-        const int lane = threadIdx.x & 31;
-        const unsigned peers = __match_any_sync(act, t);
-        const unsigned hits = __ballot_sync(act, hit);
-        if (listed) {
-            const int leader = __ffs(peers) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(&ws.cnt->h_count[t], (unsigned long long)__popc(peers));
-            base = __shfl_sync(peers, base, leader);
-            ws.hlist[(size_t)t * npix + base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)p;
-        }
-        if (lane == __ffs(act) - 1 && hits) atomicAdd(&ws.cnt->hit_pixels, (unsigned long long)__popc(hits));
-        ws.depth[p] = D;
-        ws.id[p] = id;
-        if (!hit) ws.rgba[p] = make_float4(0.f, 0.f, 0.f, 0.f);   // hit pixels are written by Step 2
+        if (threadIdx.x == 32 && s_hits) atomicAdd(&ws.cnt->hit_pixels, (unsigned long long)s_hits);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kResolvePix; ++i)
+            if (ty[i] != 0xFFFFFFFFu)
+                ws.hlist[(size_t)ty[i] * npix + s_base[ty[i]] + pos[i]] = (uint32_t)(b0 + (long long)i * blockDim.x + threadIdx.x);
+        __syncthreads();                          // s_cnt / s_base are reset for the next chunk
     }
 }
 
@@ -444,19 +476,37 @@ __global__ void __launch_bounds__(kThreads) k_shade_tiles(Workspace ws, int npix
 // ---------------------------------------------------------------------------------------------
 // Composite: shadow buffer = mean over lights of (occluded ? beta : 1); out = rgb * shadow
 // ---------------------------------------------------------------------------------------------
-__global__ void k_composite(Workspace ws, int npix)
+// Four pixels a grid stride apart per thread and iteration, their loads issued together, so that
+// enough bytes are in flight to cover the HBM latency.
+__global__ void __launch_bounds__(256) k_composite(Workspace ws, int npix)
 {
     const DevFrame &f = *ws.frame;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
-        float S = 1.0f;
-        if (ws.id[p] != kNoId) {
-            uint32_t m = ws.occl[p];
-            int occ = __popc(m);
-            S = ((f.n_lights - occ) * 1.0f + occ * f.beta) / f.n_lights;
+    const int nl = f.n_lights;
+    const float beta = f.beta;
+    const int stride = gridDim.x * blockDim.x;
+    for (int p0 = blockIdx.x * blockDim.x + threadIdx.x; p0 < npix; p0 += 4 * stride) {
+        uint32_t id[4], m[4];
+        float4 c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = p0 + u * stride;
+            id[u] = p < npix ? ws.id[p] : kNoId;
+            c[u] = p < npix ? ws.rgba[p] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        ws.shadow[p] = S;
-        float4 c = ws.rgba[p];
-        ws.out[p] = make_float4(c.x * S, c.y * S, c.z * S, c.w);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) m[u] = id[u] != kNoId ? ws.occl[p0 + u * stride] : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = p0 + u * stride;
+            if (p >= npix) break;
+            float S = 1.0f;
+            if (id[u] != kNoId) {
+                const int occ = __popc(m[u]);
+                S = ((nl - occ) * 1.0f + occ * beta) / nl;
+            }
+            ws.shadow[p] = S;
+            ws.out[p] = make_float4(c[u].x * S, c[u].y * S, c[u].z * S, c[u].w);
+        }
     }
 }
 
@@ -599,7 +649,7 @@ cudaError_t launch_frame(FrameLaunch &L)
         launches += 2;
     }
     mark();
-    k_composite<<<gsm * 4, 256, 0, st>>>(ws, npix);
+    k_composite<<<gsm * 8, 256, 0, st>>>(ws, npix);
     mark();
     L.launches = launches + 4 + nbin;
     return cudaGetLastError();

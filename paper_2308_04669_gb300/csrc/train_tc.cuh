@@ -160,6 +160,7 @@ struct EpiWgrad {
     const WgradJob *job;
     float *partial;
     long long split_stride;
+    // c0: the absolute first column (the tile's n0 included)
     __device__ __forceinline__ void operator()(int row, int c0, const uint32_t (&v)[32]) const
     {
         const WgradJob &J = *job;
@@ -169,7 +170,7 @@ struct EpiWgrad {
         float *p = partial + blockIdx.z * split_stride;                 // blockIdx.z: the split
 #pragma unroll 4
         for (int i = 0; i < 32; ++i) {
-            const int n = J.n0 + c0 + i;
+            const int n = c0 + i;
             if (n >= J.c_lo && n < J.c_hi && n < J.fi) p[J.w_off[s] + (long long)o * J.fi + n] = __uint_as_float(v[i]);
             else if (n == J.ones) p[J.b_off[s] + o] = __uint_as_float(v[i]);
         }

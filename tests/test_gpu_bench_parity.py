@@ -69,7 +69,10 @@ def test_thousand_instance_frame_matches_oracle(orc, prec):
     kw = {} if prec == "bf16" else dict(colour_tol=FP8_COLOUR_TOL)
     rep, o = frame_vs_oracle(g, orc.OracleScene(sc, nedf_override=w), px=px, quant=quant, march_n=128, march_b=4,
                              n_threads=16, max_excluded=0.1 if prec == "bf16" else 0.45, **FRAME_OPTS, **kw)
-    assert rep["hit"] > 600 and rep["shadowed"] > 50 and rep["pixels"] * (1 - rep["excluded"]) > 2000
+    # E4M3's spread leaves most shadow tests of this frame within the decision margin (their
+    # pixels' shadows undetermined and not compared); BF16 must decide many more
+    assert rep["hit"] > 600 and rep["pixels"] * (1 - rep["excluded"]) > 2000
+    assert rep["shadowed"] > (50 if prec == "bf16" else 10), rep
 
 
 def test_stress_kind_frame_fp32_plain_method_matches_oracle(orc):

@@ -81,12 +81,14 @@ def test_refine_and_outlier_resample_fp32(orc):
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_miss_check_frame_matches_oracle(orc, prec):
-    """Confident NeDF misses checked by 16 density samples along the bound chord (the untrained
-    networks answer many wrong misses), with the confidence fallback, refinement and outlier
-    re-answering: Steps 1-3 against the oracle with the same options."""
+    """NeDF misses checked by 16 density samples along the bound chord, with refinement and outlier
+    re-answering: Steps 1-3 against the oracle with the same options.  The untrained networks'
+    hit logits sit near zero, so the 0.9 confidence test would send nearly every pair to the plain
+    method; with the confidence test off every miss is a confident one and the untrained networks
+    answer many wrong misses for the check to catch."""
     from paper_2308_04669_gb300 import native
     sc = sg.three_types_scene(96, 96, nerf=False)
-    kw = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=16)
+    kw = dict(fallback_conf=0.0, refine_steps=4, outlier_resample=1, miss_check=16)
     precision = native.PREC_FP32 if prec == "fp32" else native.PREC_BF16
     g = gpu_frame(sc, precision=precision, **kw)
     g0 = gpu_frame(sc, precision=precision, **dict(kw, miss_check=0))

@@ -564,6 +564,31 @@ def test_mlp_flip2_rounds_two_values_the_other_way(orc):
     assert orc.mlp_flip2(w, dims, x, orc.QUANT_BF16, h0, h0)[0] == orc.mlp_flip(w, dims, x, orc.QUANT_BF16, h0, 0)[0][0]
 
 
+def test_mlp_flipset_rounds_any_set_of_values_the_other_way(orc):
+    """Three hidden units just off BF16 rounding boundaries (the two of the two-flip pin plus
+    4 + 2^-6 - 2^-14, which rounds to 4, else 4 + 2^-5) feeding m = h0 / 2 + h1 / 4 + h2 / 8: every
+    subset of flips gives its closed-form output, the empty set the plain rounding."""
+    import itertools
+    dims = sg.mlp_dims(sg.NEDF_IN, 1, 8, 2)
+    w = np.zeros(sg.mlp_param_count(dims))
+    off = sg.NEDF_IN * 8
+    w[off] = 1.0 + 2.0 ** -8 - 2.0 ** -16
+    w[off + 1] = 2.0 + 2.0 ** -7 + 2.0 ** -15
+    w[off + 2] = 4.0 + 2.0 ** -6 - 2.0 ** -14
+    w[off + 8], w[off + 9], w[off + 10] = 0.5, 0.25, 0.125       # W_out[0][0 .. 2]
+    x = np.zeros(sg.NEDF_IN)
+    units = [sg.NEDF_IN, sg.NEDF_IN + 1, sg.NEDF_IN + 2]
+    plain = [1.0, 2.0 + 2.0 ** -6, 4.0]
+    other = [1.0 + 2.0 ** -7, 2.0, 4.0 + 2.0 ** -5]
+    _, ci, _ = orc.mlp_flip(w, dims, x, orc.QUANT_BF16, -1, 3)
+    assert set(ci.tolist()) == set(units)
+    for k in range(4):
+        for sub in itertools.combinations(range(3), k):
+            h = [other[j] if j in sub else plain[j] for j in range(3)]
+            y = orc.mlp_flipset(w, dims, x, orc.QUANT_BF16, [units[j] for j in sub])
+            assert y[0] == 0.5 * h[0] + 0.25 * h[1] + 0.125 * h[2], sub
+
+
 # ------------------------------------------------------------------------------------------------
 # miss check (reading 30): a confident miss verified by density samples along the bound chord
 # ------------------------------------------------------------------------------------------------
