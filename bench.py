@@ -39,8 +39,11 @@ WORKLOAD = ("1024 instances (sphere/torus/box, seed 3, T in [-20,20]^3) at 1024x
 WORKLOAD_STRESS = ("4096 instances (8 shape types x 512, seed 4, T in [-40,40]^3) at 2048x2048, 8 point lights, "
                    "NeDF 6x128 per type trained on ray-march labels, NeRF 8x256 per type, 8 shading samples, "
                    "fallback below confidence 0.9, 4 refinement steps with outlier re-answering, confident misses "
-                   "checked at 16 chord samples")
-FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=16)
+                   "checked at 32 chord samples, plain-method re-answers at the labels' 256 steps + 8 bisections")
+# the frame's options (the C ABI's nedf_options) and the same options in the oracle's names
+FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=32, march_steps=256,
+                  march_bisect=8)
+ORACLE_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=32, march_n=256, march_b=8)
 NEDF_FLOP = 2 * (78 * 128 + 5 * 128 * 128 + 128 * 2)          # per query, unpadded
 # one training ray of the 6 x 128 NeDF: the forward pass, the input gradients of the hidden layers
 # (5 x 128 x 128) and of the output layer (2 x 128), and every weight gradient (as the forward)
@@ -175,7 +178,7 @@ def oracle_rate(scene, nedf_weights, target_s, threads, seed=11):
     while secs < target_s and done < scene.W * scene.H:
         px = sg.pixel_subset(scene.W, scene.H, batch, seed + n)
         t0 = time.perf_counter()
-        oracle.render(osc, px=px, alt=False, march_n=128, march_b=4, n_threads=threads, **FRAME_OPTS)
+        oracle.render(osc, px=px, alt=False, n_threads=threads, **ORACLE_OPTS)
         secs += time.perf_counter() - t0
         done += len(px)
         n += 1
@@ -197,13 +200,13 @@ def run_reference(args):
     osc = oracle.OracleScene(sc, nedf_override=w_ref)
     # calibrate a per-step pixel sample that takes about per_step_s on the host cores
     t0 = time.perf_counter()
-    oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, 256, 99), alt=False, n_threads=threads, **FRAME_OPTS)
+    oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, 256, 99), alt=False, n_threads=threads, **ORACLE_OPTS)
     n = int(max(64, 256 * per_step_s / max(time.perf_counter() - t0, 1e-3)))
     for w in range(args.warmup):
-        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 200 + w), alt=False, n_threads=threads, **FRAME_OPTS)
+        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 200 + w), alt=False, n_threads=threads, **ORACLE_OPTS)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 300 + k), alt=False, n_threads=threads, **FRAME_OPTS)
+        oracle.render(osc, px=sg.pixel_subset(sc.W, sc.H, n, 300 + k), alt=False, n_threads=threads, **ORACLE_OPTS)
     dt = time.perf_counter() - t0
     value = n * args.steps / dt
     ms_frame = 1000.0 * sc.W * sc.H / value
@@ -293,7 +296,8 @@ def classifier_frame(sc, stream, cam, lights, args, frames=5):
     oc = rc.get_options()
     for k, v in FRAME_OPTS.items():
         setattr(oc, k, v)
-    oc.fallback_conf, oc.outlier_resample = 0.0, 0          # untrained weights: their confidence means nothing
+    # untrained weights: their confidence means nothing, and most of their misses are wrong
+    oc.fallback_conf, oc.outlier_resample, oc.miss_check = 0.0, 0, 0
     rc.set_options(oc)
     cam, lights = rc.camera(sc.eye, sc.target, sc.fov_deg), rc.lights(sc.lights)
     cls_sched = rc.autotune(cam, lights, reps=2) if not args.no_autotune else None

@@ -76,8 +76,9 @@ enum nedf_arch {            /* the NeDF network of every type                   
                                h' = ReLU(h + W2 ReLU(W1 h + b1) + b2), tails 256 -> 1 + 64 (hit
                                logit, coarse bins) and 256 -> 128 (fine bins), argmax decode of
                                Eq. 4.  Packed weights W[out][in] then b[out]: head, per block W1,
-                               b1, W2, b2, tail A, tail B (2,413,249 floats).  BF16 precision only
-                               for rendering; training (loss_grad, train_step) uses the BCE loss of
+                               b1, W2, b2, tail A, tail B (2,413,249 floats).  Renders in BF16
+                               (tensor cores) or FP32 (CUDA cores, the reference precision; FP8
+                               is refused); training (loss_grad, train_step) uses the BCE loss of
                                Eq. 6 with every dense product a BF16 tensor-core GEMM (FP32
                                accumulation, FP32 master weights) */
 };

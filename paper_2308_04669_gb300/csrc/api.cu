@@ -74,6 +74,7 @@ struct nedf_handle {
     LightCam *d_lcam = nullptr;
     uint32_t *d_lg_count = nullptr, *d_lg_off = nullptr, *d_lg_cursor = nullptr, *d_lg_items = nullptr;
     uint32_t *d_lg_big = nullptr, *d_lg_big_count = nullptr, *d_scan_tmp = nullptr;
+    unsigned long long *d_sblk = nullptr;
     long long lg_cap = 0;
     size_t nedf_tc_stride = 0, nerf_tc_stride = 0;
     void *d_march_scratch = nullptr;
@@ -214,6 +215,7 @@ static Workspace make_ws(nedf_handle *h)
     ws.nedf_hidden = h->cfg.nedf_hidden;
     ws.nedf_width = h->cfg.nedf_width;
     ws.nedf_arch = h->cfg.nedf_arch;
+    ws.pair_geo = h->cfg.precision != NEDF_PREC_FP32 || h->cfg.nedf_arch == NEDF_ARCH_CLASSIFIER;
     ws.nerf_hidden = h->cfg.nerf_hidden;
     ws.nerf_width = h->cfg.nerf_width;
     ws.precision = h->cfg.precision;
@@ -236,6 +238,8 @@ static Workspace make_ws(nedf_handle *h)
     ws.lg_G = kLightGridSize;
     ws.max_inst = h->cfg.max_instances;
     ws.scan_tmp = h->d_scan_tmp;
+    ws.sblk = h->d_sblk;
+    ws.sblk_nb = shadow_bin_blocks(h->num_sms);
     return ws;
 }
 
@@ -264,8 +268,8 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
         return fail(nullptr, NEDF_ERR_ARG, "max_instances/max_types out of range");
     if (c.nedf_arch != NEDF_ARCH_REGRESSION && c.nedf_arch != NEDF_ARCH_CLASSIFIER)
         return fail(nullptr, NEDF_ERR_UNSUPPORTED, "nedf_arch");
-    if (c.nedf_arch == NEDF_ARCH_CLASSIFIER && c.precision != NEDF_PREC_BF16)
-        return fail(nullptr, NEDF_ERR_UNSUPPORTED, "the classifier network runs in BF16 precision only");
+    if (c.nedf_arch == NEDF_ARCH_CLASSIFIER && c.precision == NEDF_PREC_FP8)
+        return fail(nullptr, NEDF_ERR_UNSUPPORTED, "the classifier network runs in BF16 or FP32 precision");
     if (c.nedf_arch == NEDF_ARCH_REGRESSION &&
         (c.nedf_hidden < 1 || c.nedf_hidden > 16 || (c.nedf_width != 64 && c.nedf_width != 128 && c.nedf_width != 256)))
         return fail(nullptr, NEDF_ERR_UNSUPPORTED, "NeDF shape: hidden 1..16, width 64/128/256");
@@ -286,7 +290,7 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
     if (h->cfg.shadow_pair_capacity == 0) h->cfg.shadow_pair_capacity = 4 * npix * NEDF_MAX_LIGHTS / 8;
     h->stream = (cudaStream_t)cuda_stream;
     h->opt = nedf_options{8, 0.05f, 0.5f, 0.02f, 50.0f, 0.01f, NEDF_DEPTH_NEDF, 128, 4, 0.0f, 0, 0, 0, 1.0f};
-    if (c.nedf_arch == NEDF_ARCH_CLASSIFIER) {     // the fixed shape; the CUDA-core NeDF is unused
+    if (c.nedf_arch == NEDF_ARCH_CLASSIFIER) {     // the fixed shape; the regression kernels are unused
         h->cfg.nedf_hidden = 1;
         h->cfg.nedf_width = 64;
     }
@@ -352,6 +356,11 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
         CA(h->d_lg_big, sizeof(uint32_t) * (size_t)NEDF_MAX_LIGHTS * c.max_instances);
         CA(h->d_lg_big_count, sizeof(uint32_t) * NEDF_MAX_LIGHTS);
         CA(h->d_scan_tmp, sizeof(uint32_t) * 1024);
+        CA(h->d_sblk, sizeof(unsigned long long) * kMaxTypes * (shadow_bin_blocks(h->num_sms) + 1));
+    }
+    if (c.precision == NEDF_PREC_FP32 && c.nedf_arch == NEDF_ARCH_CLASSIFIER) {
+        h->nedf_tc_stride = cls_f32_blob_size();          // the CUDA-core classifier's FP32 weights
+        CA(h->d_nedf_tc, h->nedf_tc_stride * c.max_types);
     }
     if (c.precision != NEDF_PREC_FP32) {
         const bool f8 = c.precision == NEDF_PREC_FP8;
@@ -381,7 +390,7 @@ void nedf_compose_destroy(nedf_handle *h)
                    h->d_ppairs, h->d_spairs, h->d_pgeo, h->d_sgeo, h->d_sell, h->d_nout[0], h->d_nout[1], h->d_rs_mask, h->d_rs_pairs, h->d_rs_cnt, h->d_rs_scratch, h->d_edit_keys, h->d_edit_rgba, h->d_edit_occl, h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch,
                    h->d_march_scratch, h->d_nedf_tc, h->d_nerf_tc, h->d_fb[0], h->d_fb[1], h->d_lcam,
                    h->d_lg_count, h->d_lg_off, h->d_lg_cursor, h->d_lg_items, h->d_lg_big,
-                   h->d_lg_big_count, h->d_scan_tmp};
+                   h->d_lg_big_count, h->d_scan_tmp, h->d_sblk};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (TrainState &t : h->train) {
@@ -468,7 +477,9 @@ int nedf_compose_sync(nedf_handle *h)
 // Packs one type's FP32 master weights (device) into its tensor-core blob.
 static cudaError_t pack_nedf(nedf_handle *h, const float *master, uint8_t *blob)
 {
-    if (h->cfg.nedf_arch == NEDF_ARCH_CLASSIFIER) return launch_pack_cls(master, blob, h->stream);
+    if (h->cfg.nedf_arch == NEDF_ARCH_CLASSIFIER)
+        return h->cfg.precision == NEDF_PREC_FP32 ? launch_pack_cls_f32(master, blob, h->stream)
+                                                  : launch_pack_cls(master, blob, h->stream);
     return launch_pack_pipe(master, blob, kNedfIn, kNedfInPad, h->cfg.nedf_width, h->cfg.nedf_hidden, 2,
                             h->cfg.precision == NEDF_PREC_FP8, h->stream);
 }
@@ -929,7 +940,8 @@ int nedf_compose_validate(nedf_handle *h)
     CK(h, cudaMemcpy(&st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost));
     if (st) return NEDF_OK;      // an overflow or timeout is reported by sync; the lists are then partial
     const int T = h->n_types;
-    const bool tc_nedf = h->cfg.precision != NEDF_PREC_FP32 && h->opt.depth_source == NEDF_DEPTH_NEDF;
+    const bool tc_nedf = (h->cfg.precision != NEDF_PREC_FP32 || h->cfg.nedf_arch == NEDF_ARCH_CLASSIFIER) &&
+                         h->opt.depth_source == NEDF_DEPTH_NEDF;      // listed pairs, decode and fallback
     const bool tc_shade = h->cfg.precision != NEDF_PREC_FP32 && h->cfg.nerf_hidden > 0;
     const unsigned long long rows = tc_nedf ? kPipeTileRows : 64;
     const unsigned long long ppt = tc_shade ? 2 * (128 / h->opt.n_shade) : 64 / h->opt.n_shade;
@@ -1077,6 +1089,8 @@ int nedf_compose_nedf_query(nedf_handle *h, int type, int n, const float *o, con
     if (n < 0) return fail(h, NEDF_ERR_ARG, "n < 0");
     if (h->cfg.precision != NEDF_PREC_FP32)
         CK(h, launch_nedf_pipe(make_ws(h), 2, type, o, d, out, n, h->num_sms, h->stream));
+    else if (h->cfg.nedf_arch == NEDF_ARCH_CLASSIFIER)
+        CK(h, launch_cls_f32(make_ws(h), 2, type, o, d, out, n, h->num_sms, h->stream));
     else
         CK(h, launch_nedf_query_f32(make_ws(h), type, o, d, out, n, h->num_sms, h->stream));
     return NEDF_OK;

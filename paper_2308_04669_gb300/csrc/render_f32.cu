@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_bin_primary(Workspace ws)
         } else {
             warp_append(keep, make_uint2((uint32_t)(j * f.W + i), (uint32_t)inst), &ws.cnt->p_cursor[I.type],
                         &ws.cnt->p_off[I.type + 1], ws.ppairs, ws.status, kStatusPrimaryOverflow,
-                        ws.precision >= 1 ? ws.pgeo : nullptr, make_float4(ol.x, ol.y, ol.z, c.te),
+                        ws.pair_geo ? ws.pgeo : nullptr, make_float4(ol.x, ol.y, ol.z, c.te),
                         make_float4(dl.x, dl.y, dl.z, c.tp));
         }
     }
@@ -332,20 +332,29 @@ __global__ void __launch_bounds__(256) k_resolve(Workspace ws, int npix)
         if (threadIdx.x < kMaxTypes) s_cnt[threadIdx.x] = 0u;
         if (threadIdx.x == 0) s_hits = 0u;
         __syncthreads();
+        // every load first (the keys, then their instances' types), so that each thread has
+        // kResolvePix independent loads in flight instead of a chain per pixel
+        unsigned long long key[kResolvePix];
         uint32_t ty[kResolvePix], pos[kResolvePix];
 #pragma unroll
         for (int i = 0; i < kResolvePix; ++i) {
             const long long p = b0 + (long long)i * blockDim.x + threadIdx.x;
+            key[i] = p < npix ? ws.keys[p] : ~0ull;
+        }
+#pragma unroll
+        for (int i = 0; i < kResolvePix; ++i) ty[i] = key[i] != ~0ull ? ws.inst[(uint32_t)key[i]].type : 0xFFFFFFFFu;
+#pragma unroll
+        for (int i = 0; i < kResolvePix; ++i) {
+            const long long p = b0 + (long long)i * blockDim.x + threadIdx.x;
             const bool in = p < npix;
-            const unsigned long long k = in ? ws.keys[p] : ~0ull;
+            const unsigned long long k = key[i];
             float D = __int_as_float(0x7f800000);
             uint32_t id = kNoId;
             const bool hit = k != ~0ull;
-            uint32_t t = 0xFFFFFFFFu;
+            uint32_t t = ty[i];
             if (hit) {
                 D = __uint_as_float((uint32_t)(k >> 32));
                 id = (uint32_t)(k & 0xffffffffu);
-                t = ws.inst[id].type;
             }
             // an edit frame shades and fully re-shadows only the pixels the manipulated instance
             // wins; every other pixel keeps the frozen part's colour and occlusion bits
@@ -584,7 +593,10 @@ cudaError_t launch_frame(FrameLaunch &L)
     // the kernel that consumes the list
     const bool tc_nedf = ws.precision >= 1 && ws.depth_source == 0;      // BF16 or E4M3 tensor-core layers
     const bool tc_shade = ws.precision >= 1 && ws.nerf_hidden > 0;
-    const int nedf_rows = tc_nedf ? kPipeTileRows : kTileRows;
+    // the classifier network in FP32 on CUDA cores: the engines' tiles, decode and fallback
+    const bool cls_f32 = ws.precision == 0 && ws.nedf_arch == 1 && ws.depth_source == 0;
+    const bool listed_nedf = tc_nedf || cls_f32;                         // (m, a) per pair, then decode
+    const int nedf_rows = listed_nedf ? kPipeTileRows : kTileRows;
     // the engine shades (128 / n_shade) pixels per 128-row half, two halves per tile
     const int shade_ppt = tc_shade ? 2 * (kTcTileRows / L.n_shade) : kTileRows / L.n_shade;
     // inside a captured graph the records are external (they still mark the stage boundaries for
@@ -607,19 +619,20 @@ cudaError_t launch_frame(FrameLaunch &L)
     k_bin_primary<1><<<L.n_inst, kThreads, 0, st>>>(ws);
     // the engine launch alone, inside its stage (the stage also holds the decode and fallback)
     auto mark_engine = [&](int k) {
-        if (!L.events || !L.engine_events || !tc_nedf) return;
+        if (!L.events || !L.engine_events || !listed_nedf) return;
         if (cap == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(L.engine_events[k], st, cudaEventRecordExternal);
         else cudaEventRecord(L.engine_events[k], st);
         L.engines_timed = true;
     };
     mark();
     mark_engine(0);
-    cudaError_t e = tc_nedf ? launch_nedf_pipe(ws, 0, 0, nullptr, nullptr, nullptr, 0, gsm, st)
-                            : nedf_dispatch(ws, gsm * 4, 0, st);
+    cudaError_t e = tc_nedf   ? launch_nedf_pipe(ws, 0, 0, nullptr, nullptr, nullptr, 0, gsm, st)
+                    : cls_f32 ? launch_cls_f32(ws, 0, 0, nullptr, nullptr, nullptr, 0, gsm, st)
+                              : nedf_dispatch(ws, gsm * 4, 0, st);
     mark_engine(1);
     if (e != cudaSuccess) return e;
     int launches = 6;
-    if (tc_nedf) {                        // decode, then the pairs deferred to the plain method
+    if (listed_nedf) {                    // decode, then the pairs deferred to the plain method
         if ((e = launch_nedf_decode(ws, 0, gsm, st)) != cudaSuccess) return e;
         if ((e = launch_fallback(ws, 0, gsm, st)) != cudaSuccess) return e;
         launches += 2;
@@ -640,10 +653,12 @@ cudaError_t launch_frame(FrameLaunch &L)
     if (e != cudaSuccess) return e;
     mark();
     mark_engine(2);
-    e = tc_nedf ? launch_nedf_pipe(ws, 1, 0, nullptr, nullptr, nullptr, 0, gsm, st) : nedf_dispatch(ws, gsm * 4, 1, st);
+    e = tc_nedf   ? launch_nedf_pipe(ws, 1, 0, nullptr, nullptr, nullptr, 0, gsm, st)
+        : cls_f32 ? launch_cls_f32(ws, 1, 0, nullptr, nullptr, nullptr, 0, gsm, st)
+                  : nedf_dispatch(ws, gsm * 4, 1, st);
     mark_engine(3);
     if (e != cudaSuccess) return e;
-    if (tc_nedf) {
+    if (listed_nedf) {
         if ((e = launch_nedf_decode(ws, 1, gsm, st)) != cudaSuccess) return e;
         if ((e = launch_fallback(ws, 1, gsm, st)) != cudaSuccess) return e;
         launches += 2;

@@ -53,7 +53,7 @@ struct Workspace {
     long long pcap;
     uint2 *spairs;               // shadow (pixel * n_lights + light, instance)
     long long scap;
-    // pair geometry from the binning passes, for the tensor-core NeDF engine (precision >= 1): per
+    // pair geometry from the binning passes, for the NeDF engines that read it (pair_geo): per
     // pair (local origin, t_entry) and (local direction, t_perp); per shadow pair the world length
     // from the light to the lit point
     float4 *pgeo;                // [2 * pcap]
@@ -82,6 +82,7 @@ struct Workspace {
     long long nerf_stride;
     int nedf_hidden, nedf_width, nerf_hidden, nerf_width;
     int nedf_arch;               // 0: regression MLP, 1: the paper's classifier network (nedf_tc only)
+    int pair_geo;                // the binning passes store each pair's local ray (pgeo / sgeo)
     // BF16 tensor-core weight blobs (per type, fixed stride); precision 1 selects them
     int precision;
     int depth_source;            // host copy of the frame option (selects kernels)
@@ -103,6 +104,10 @@ struct Workspace {
     int lg_G;
     int max_inst;
     uint32_t *scan_tmp;          // block sums of the grid scan
+    // shadow-ray binning: per type t and block b of the binning grid, the block's pair count (count
+    // pass), then the first index of its range ([t][nb] = the end of the type's grid pairs)
+    unsigned long long *sblk;    // [kMaxTypes][sblk_nb + 1]
+    int sblk_nb;                 // blocks of the shadow-ray binning grid
     // tensor-core schedule: weight bytes per bulk copy of each engine mode (shade, march colour,
     // primary NeDF, shadow NeDF, NeDF query); picked by the autotuner or set by the caller
     int pipe_stage_bytes[5];

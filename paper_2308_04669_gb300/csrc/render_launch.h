@@ -46,6 +46,12 @@ size_t cls_blob_size();
 cudaError_t launch_pack_cls(const float *master, void *blob, cudaStream_t st);
 cudaError_t launch_cls_pipe(const Workspace &ws, int mode, int type, const float *o, const float *d, float *out,
                             int n, int num_sms, cudaStream_t st);
+// The same network on CUDA cores in FP32 (render_cls_f32.cu): per-type transposed FP32 blob, the
+// same three modes and (m, a) outputs
+size_t cls_f32_blob_size();
+cudaError_t launch_pack_cls_f32(const float *master, void *blob, cudaStream_t st);
+cudaError_t launch_cls_f32(const Workspace &ws, int mode, int type, const float *o, const float *d, float *out,
+                           int n, int num_sms, cudaStream_t st);
 cudaError_t launch_march_colour_pipe(const Workspace &ws, const MarchBuffers &mb, int n_samples, int num_sms,
                                      cudaStream_t st);
 cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStream_t st);
@@ -56,7 +62,9 @@ cudaError_t launch_nedf_decode(const Workspace &ws, int mode, int num_sms, cudaS
 // one bounded mbarrier wait that nothing completes (sets the timeout status after its limit)
 cudaError_t launch_wait_check(uint32_t *status, cudaStream_t st);
 
-// Step-3 binning through per-light shadow-map cameras (shadow_bin.cu)
+// Step-3 binning through per-light shadow-map cameras (shadow_bin.cu); its shadow-ray passes run
+// shadow_bin_blocks(num_sms) blocks (Workspace::sblk holds a range per type and block)
+inline int shadow_bin_blocks(int num_sms) { return num_sms * 8; }
 // edit_frame: buffer reuse's edit frame (the frozen pixels' shadow rays against the manipulated instance too)
 cudaError_t launch_shadow_binning(const Workspace &ws, int npix, int n_lights, int n_inst, int rows_per_tile,
                                   int num_sms, cudaStream_t st, int *launches, bool edit_frame = false);

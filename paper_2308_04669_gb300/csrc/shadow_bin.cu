@@ -10,7 +10,8 @@
 // cell of margin).  A shadow ray then looks up the single cell its direction falls in, and the
 // exact bound-sphere test decides.  Instances whose rectangle is too large (close to the
 // light) go to a per-light list every ray checks; a light inside the scene bound uses all
-// instances.  The per-type pair lists are then built exactly as in Step 1 (count, scan, fill).
+// instances.  The per-type pair lists are then built by a count pass, a scan and a fill pass
+// over the same rays, each block placing its pairs in its own range.
 #include "render_kernels.cuh"
 #include "render_launch.h"
 
@@ -139,39 +140,43 @@ __global__ void k_zero_u32(uint32_t *p, long long n)
         p[i] = 0u;
 }
 
+// One warp per (light, instance): the lanes share the instance's cell rectangle, one cell each,
+// so an instance covering tens of cells costs one round of atomics instead of a serial loop.
 template <int PASS>
-__global__ void k_light_bin(Workspace ws, int n_lights)
+__global__ void __launch_bounds__(256) k_light_bin(Workspace ws, int n_lights)
 {
     const DevFrame &f = *ws.frame;
-    const int G = ws.lg_G, n_inst = f.n_inst;
+    const int G = ws.lg_G, n_inst = f.n_inst, lane = threadIdx.x & 31;
     const long long total = (long long)n_lights * n_inst;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        int l = (int)(e / n_inst), i = (int)(e - (long long)l * n_inst);
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < total; e += warps) {
+        const int l = (int)(e / n_inst), i = (int)(e - (long long)l * n_inst);
         const LightCam cam = ws.lcam[l];
         if (!cam.valid) continue;
         if (f.edit_mode == 1 && i == f.edit_inst) continue;     // the frozen part has no manipulated instance
-        DevInst I = ws.inst[i];
-        float r = I.s * ws.types[I.type].rb;
+        const DevInst I = ws.inst[i];
+        const float r = I.s * ws.types[I.type].rb;
         int i0, i1, j0, j1;
-        bool ok = light_rect(cam, G, v3(I.T[0], I.T[1], I.T[2]), r, i0, i1, j0, j1);
+        const bool ok = light_rect(cam, G, v3(I.T[0], I.T[1], I.T[2]), r, i0, i1, j0, j1);
         if (!ok || (i1 - i0 + 1) * (j1 - j0 + 1) > kMaxCellsPerInstance) {
-            if (PASS == 1) {
-                uint32_t pos = atomicAdd(&ws.lg_big_count[l], 1u);
+            if (PASS == 1 && lane == 0) {
+                const uint32_t pos = atomicAdd(&ws.lg_big_count[l], 1u);
                 ws.lg_big[(size_t)l * ws.max_inst + pos] = (uint32_t)i;
             }
             continue;
         }
-        for (int j = j0; j <= j1; ++j)
-            for (int ii = i0; ii <= i1; ++ii) {
-                size_t cell = ((size_t)l * G + j) * G + ii;
-                if (PASS == 0) {
-                    atomicAdd(&ws.lg_count[cell], 1u);
-                } else {
-                    uint32_t pos = atomicAdd(&ws.lg_cursor[cell], 1u);
-                    if ((long long)pos < ws.lg_cap) ws.lg_items[pos] = (uint32_t)i;
-                    else atomicOr(ws.status, kStatusShadowOverflow);
-                }
+        const int wdt = i1 - i0 + 1, n_cells = wdt * (j1 - j0 + 1);
+        for (int c = lane; c < n_cells; c += 32) {
+            const int jr = c / wdt;
+            const size_t cell = ((size_t)l * G + (j0 + jr)) * G + (i0 + c - jr * wdt);
+            if (PASS == 0) {
+                atomicAdd(&ws.lg_count[cell], 1u);
+            } else {
+                const uint32_t pos = atomicAdd(&ws.lg_cursor[cell], 1u);
+                if ((long long)pos < ws.lg_cap) ws.lg_items[pos] = (uint32_t)i;
+                else atomicOr(ws.status, kStatusShadowOverflow);
             }
+        }
     }
 }
 
@@ -252,16 +257,34 @@ __device__ __forceinline__ unsigned lane_lt()
     return m;
 }
 
+// The shadow rays of the hit pixels (the per-type hit lists of the resolve, one after another),
+// lane-coherent: the 32 lanes of a warp take 32 consecutive hit pixels (neighbours on screen)
+// for one light, so that they mostly fall in the same light-grid cell, read the same candidate
+// instances (broadcast loads) and run the same number of candidate tests.  Flat index rr ->
+// q = rr / 32, light l = q % n_lights, hit h = (q / n_lights) * 32 + rr % 32.
+//
+// PASS 0 counts each block's kept pairs per type (shared-memory atomics) into sblk; after the
+// scan, PASS 1 runs the same rays in the same blocks and places each block's pairs in its own
+// range of each type's list with shared-memory cursors, so no global counter is contended.
 template <int PASS>
 __global__ void __launch_bounds__(256) k_bin_shadow_grid(Workspace ws, int npix)
 {
-    __shared__ unsigned long long cnt_t[kMaxTypes];
     __shared__ unsigned long long hit_pre[kMaxTypes + 1];   // first flat hit index of each type's list
+    __shared__ unsigned long long s_cur[kMaxTypes];         // PASS 0: count; PASS 1: cursor
+    __shared__ unsigned long long s_beg[kMaxTypes], s_end[kMaxTypes], s_lim[kMaxTypes];
     const DevFrame &f = *ws.frame;
     const int nl = f.n_lights, n_inst = f.n_inst, G = ws.lg_G, n_types = f.n_types;
-    const int lane = threadIdx.x & 31;
-    if (PASS == 0)
-        for (int k = threadIdx.x; k < kMaxTypes; k += blockDim.x) cnt_t[k] = 0;
+    const int lane = threadIdx.x & 31, nb = ws.sblk_nb;
+    if (threadIdx.x < n_types) {
+        const int t = threadIdx.x;
+        if (PASS == 0) {
+            s_cur[t] = 0;
+        } else {
+            s_beg[t] = s_cur[t] = ws.sblk[(size_t)t * (nb + 1) + blockIdx.x];
+            s_end[t] = ws.sblk[(size_t)t * (nb + 1) + blockIdx.x + 1];
+            s_lim[t] = ws.cnt->s_off[t + 1];
+        }
+    }
     if (threadIdx.x == 0) {
         unsigned long long acc = 0;
         for (int t = 0; t < n_types; ++t) {
@@ -271,26 +294,24 @@ __global__ void __launch_bounds__(256) k_bin_shadow_grid(Workspace ws, int npix)
         hit_pre[n_types] = acc;
     }
     __syncthreads();
-    // shadow rays only for pixels with a hit: the per-type hit lists of the resolve, one after
-    // another, each pixel's lights adjacent
-    const long long n_rays = (long long)hit_pre[n_types] * nl;
+    const unsigned long long n_hit = hit_pre[n_types];
+    const long long n_rays = (long long)((n_hit + 31) / 32) * 32 * nl;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < n_rays; base += (long long)gridDim.x * blockDim.x) {
         const long long rr = base + threadIdx.x;
-        bool valid = rr < n_rays;
-        uint32_t pix = 0, l = 0;
+        const long long q = rr >> 5;
+        const uint32_t l = (uint32_t)(q % nl);
+        const unsigned long long h = (unsigned long long)(q / nl) * 32 + (unsigned long long)(rr & 31);
+        const bool valid = h < n_hit;
+        uint32_t pix = 0;
         V3 o = v3(0, 0, 0), d = v3(0, 0, 1);
         float ell = 0.0f;
         int count = 0, nc = 0;
         uint32_t c0 = 0;
         bool grid = false;
         if (valid) {
-            const unsigned long long h = (unsigned long long)(rr / nl);
-            l = (uint32_t)(rr - (long long)h * nl);
             int t = 0;
             while (t + 1 < n_types && hit_pre[t + 1] <= h) ++t;
             pix = ws.hlist[(size_t)t * npix + (h - hit_pre[t])];
-        }
-        if (valid) {
             V3 oc, dc;
             camera_ray(f, pix % f.W, pix / f.W, oc, dc);
             V3 x = madd(oc, ws.depth[pix], dc);
@@ -331,39 +352,39 @@ __global__ void __launch_bounds__(256) k_bin_shadow_grid(Workspace ws, int npix)
                 keep = bound_chord(ol, dl, ws.types[ty].rb, ch) && (ch.te * I.s < ell) &&
                        !(f.edit_mode == 1 && inst == (uint32_t)f.edit_inst);
             }
+            const unsigned active = __ballot_sync(0xffffffffu, keep);
+            if (!keep) continue;
+            const unsigned peers = __match_any_sync(active, ty);
+            const int leader = __ffs(peers) - 1;
             if (PASS == 0) {
-                const unsigned active = __ballot_sync(0xffffffffu, keep);
-                if (keep) {
-                    const unsigned peers = __match_any_sync(active, ty);
-                    if (lane == __ffs(peers) - 1) atomicAdd(&cnt_t[ty], (unsigned long long)__popc(peers));
+                if (lane == leader) atomicAdd(&s_cur[ty], (unsigned long long)__popc(peers));
+                continue;
+            }
+            unsigned long long start = 0;
+            if (lane == leader) start = atomicAdd(&s_cur[ty], (unsigned long long)__popc(peers));
+            start = __shfl_sync(peers, start, leader);
+            const unsigned long long idx = start + __popc(peers & lane_lt());
+            if (idx < s_end[ty] && idx < s_lim[ty]) {
+                ws.spairs[idx] = make_uint2(pix * nl + l, inst);
+                if (ws.pair_geo) {
+                    ws.sgeo[2 * idx] = make_float4(ol.x, ol.y, ol.z, ch.te);
+                    ws.sgeo[2 * idx + 1] = make_float4(dl.x, dl.y, dl.z, ch.tp);
+                    ws.sell[idx] = ell;
                 }
             } else {
-                unsigned active = __ballot_sync(0xffffffffu, keep);
-                if (keep) {
-                    unsigned peers = __match_any_sync(active, ty);
-                    int leader = __ffs(peers) - 1;
-                    unsigned long long start = 0;
-                    if (lane == leader) start = atomicAdd(&ws.cnt->s_cursor[ty], (unsigned long long)__popc(peers));
-                    start = __shfl_sync(peers, start, leader);
-                    unsigned long long idx = start + __popc(peers & lane_lt());
-                    if (idx < ws.cnt->s_off[ty + 1]) {
-                        ws.spairs[idx] = make_uint2(pix * nl + l, inst);
-                        if (ws.precision >= 1) {
-                            ws.sgeo[2 * idx] = make_float4(ol.x, ol.y, ol.z, ch.te);
-                            ws.sgeo[2 * idx + 1] = make_float4(dl.x, dl.y, dl.z, ch.tp);
-                            ws.sell[idx] = ell;
-                        }
-                    } else {
-                        atomicOr(ws.status, kStatusShadowOverflow);
-                    }
-                }
+                atomicOr(ws.status, kStatusShadowOverflow);    // the list's capacity (or a count/fill mismatch)
             }
         }
     }
-    if (PASS == 0) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < f.n_types; k += blockDim.x)
-            if (cnt_t[k]) atomicAdd(&ws.cnt->s_count[k], cnt_t[k]);
+    __syncthreads();
+    if (threadIdx.x < n_types) {
+        const int t = threadIdx.x;
+        if (PASS == 0) {
+            ws.sblk[(size_t)t * (nb + 1) + blockIdx.x] = s_cur[t];
+        } else {
+            const unsigned long long filled = min(s_cur[t], min(s_end[t], s_lim[t]));
+            if (filled > s_beg[t]) atomicAdd(&ws.cnt->s_cursor[t], filled - s_beg[t]);
+        }
     }
 }
 
@@ -415,7 +436,7 @@ __global__ void __launch_bounds__(256) k_edit_shadow(Workspace ws, int npix)
             const unsigned long long idx = start + __popc(m & lane_lt());
             if (idx < ws.cnt->s_off[ty + 1]) {
                 ws.spairs[idx] = make_uint2(pix * nl + l, e);
-                if (ws.precision >= 1) {
+                if (ws.pair_geo) {
                     ws.sgeo[2 * idx] = make_float4(ol.x, ol.y, ol.z, ch.te);
                     ws.sgeo[2 * idx + 1] = make_float4(dl.x, dl.y, dl.z, ch.tp);
                     ws.sell[idx] = ell;
@@ -427,28 +448,62 @@ __global__ void __launch_bounds__(256) k_edit_shadow(Workspace ws, int npix)
     }
 }
 
-__global__ void k_scan_shadow_pairs(Workspace ws, int rows_per_tile)
+// The per-type shadow lists: type t holds its grid pairs (block after block) and then its edit
+// frame's pairs.  One warp per type sums the blocks' counts; thread 0 lays out the segments (the
+// capacity clamps the last ones) and their tiles; one warp per type then scans the blocks' counts
+// into their first indices.  s_cursor[t] starts at the segment: the fill pass adds each block's
+// pairs to it, the edit frame's appends continue from there, so a segment filled exactly ends at
+// the next segment.
+__global__ void __launch_bounds__(1024) k_scan_shadow_pairs(Workspace ws, int rows_per_tile)
 {
+    __shared__ unsigned long long s_grid[kMaxTypes];
     const DevFrame &f = *ws.frame;
     Counters &C = *ws.cnt;
-    unsigned long long o = 0, t = 0, req = 0;
-    for (int k = 0; k < f.n_types; ++k) {
-        unsigned long long c = C.s_count[k];
-        req += c;
-        if (o + c > (unsigned long long)ws.scap) {
-            c = (unsigned long long)ws.scap - o;
-            *ws.status |= kStatusShadowOverflow;
-        }
-        C.s_count[k] = c;
-        C.s_off[k] = o;
-        C.s_cursor[k] = o;
-        C.s_tile[k] = t;
-        o += c;
-        t += (c + rows_per_tile - 1) / rows_per_tile;
+    const int nb = ws.sblk_nb, T = f.n_types;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = warp; t < T; t += nw) {
+        unsigned long long s = 0;
+        for (int b = lane; b < nb; b += 32) s += ws.sblk[(size_t)t * (nb + 1) + b];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) s_grid[t] = s;
     }
-    C.s_off[f.n_types] = o;
-    C.s_tile[f.n_types] = t;
-    C.s_total_requested = req;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long o = 0, tl = 0, req = 0;
+        for (int k = 0; k < T; ++k) {
+            unsigned long long c = s_grid[k] + C.s_count[k];       // grid pairs + edit-frame pairs
+            req += c;
+            if (o + c > (unsigned long long)ws.scap) {
+                c = (unsigned long long)ws.scap - o;
+                *ws.status |= kStatusShadowOverflow;
+            }
+            C.s_count[k] = c;
+            C.s_off[k] = o;
+            C.s_cursor[k] = o;
+            C.s_tile[k] = tl;
+            o += c;
+            tl += (c + rows_per_tile - 1) / rows_per_tile;
+        }
+        C.s_off[T] = o;
+        C.s_tile[T] = tl;
+        C.s_total_requested = req;
+    }
+    __syncthreads();
+    for (int t = warp; t < T; t += nw) {
+        unsigned long long run = C.s_off[t];
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int b = b0 + lane;
+            const unsigned long long v = b < nb ? ws.sblk[(size_t)t * (nb + 1) + b] : 0ull;
+            unsigned long long incl = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (b < nb) ws.sblk[(size_t)t * (nb + 1) + b] = run + incl - v;
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) ws.sblk[(size_t)t * (nb + 1) + nb] = run;      // the end of the grid pairs
+    }
 }
 
 cudaError_t launch_shadow_binning(const Workspace &ws, int npix, int n_lights, int n_inst, int rows_per_tile,
@@ -459,7 +514,7 @@ cudaError_t launch_shadow_binning(const Workspace &ws, int npix, int n_lights, i
     const int nb = (int)((cells + kScanBlock - 1) / kScanBlock);
     if (nb > 1024) return cudaErrorInvalidValue;
     const long long pairs = (long long)n_lights * n_inst;
-    const int gb = (int)std::min<long long>((pairs + 255) / 256, (long long)num_sms * 8);
+    const int gb = (int)std::min<long long>((pairs + 7) / 8, (long long)num_sms * 8);     // a warp per pair
     k_light_setup<<<1, 256, 0, st>>>(ws);
     k_zero_u32<<<num_sms * 2, 256, 0, st>>>(ws.lg_count, cells);
     k_light_bin<0><<<gb, 256, 0, st>>>(ws, n_lights);
@@ -467,10 +522,10 @@ cudaError_t launch_shadow_binning(const Workspace &ws, int npix, int n_lights, i
     k_scan_sums<<<1, 1024, 0, st>>>(ws.scan_tmp, nb, ws.lg_off + cells);
     k_scan_add<<<num_sms * 2, 256, 0, st>>>(ws.lg_off, ws.lg_cursor, ws.scan_tmp, cells);
     k_light_bin<1><<<gb, 256, 0, st>>>(ws, n_lights);
-    k_bin_shadow_grid<0><<<num_sms * 8, 256, 0, st>>>(ws, npix);
+    k_bin_shadow_grid<0><<<ws.sblk_nb, 256, 0, st>>>(ws, npix);
     if (edit_frame) k_edit_shadow<0><<<num_sms * 8, 256, 0, st>>>(ws, npix);
-    k_scan_shadow_pairs<<<1, 1, 0, st>>>(ws, rows_per_tile);
-    k_bin_shadow_grid<1><<<num_sms * 8, 256, 0, st>>>(ws, npix);
+    k_scan_shadow_pairs<<<1, 1024, 0, st>>>(ws, rows_per_tile);
+    k_bin_shadow_grid<1><<<ws.sblk_nb, 256, 0, st>>>(ws, npix);
     if (edit_frame) k_edit_shadow<1><<<num_sms * 8, 256, 0, st>>>(ws, npix);
     *launches = edit_frame ? 12 : 10;
     return cudaGetLastError();

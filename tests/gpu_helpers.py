@@ -174,7 +174,8 @@ def check_network_rows(orc, g, w, dims, feats, quant, max_flip_rows):
     either agrees within ROW_ABS / ROW_REL, or some of its rounded values that lie within
     FLIP_LIMIT of a rounding boundary, rounded the other way, make the oracle agree with it within
     the same bound: an FP32 sum on the GPU fell on the other side of each such boundary.  Tried in
-    order: one value; two of the sixteen nearest; three or four of the eight nearest (a row with
+    order: one value; two of the sixteen nearest; one of the sixteen nearest and then a near-tie of
+    the trajectory that flip produces (a cascade); three or four of the eight nearest (a row with
     several near-ties).  Rows of the second kind are counted and bounded by max_flip_rows (a
     fraction)."""
     import itertools
@@ -194,6 +195,18 @@ def check_network_rows(orc, g, w, dims, feats, quant, max_flip_rows):
             pairs = [(a, b) for k, a in enumerate(cand[:16]) for b in cand[k + 1:16]]
             explained = any(close(g[i], orc.mlp_flip2(w, dims, f, quant, a, b), ROW_ABS, ROW_REL).all() for a, b in pairs)
             n_pair += explained
+        if not explained:
+            # a cascade: one flip moves a later value onto its own rounding boundary, which then
+            # rounds the other way too (a near-tie of the flipped trajectory, not of the original)
+            for a in cand[:16]:
+                _, ci2, cm2 = orc.mlp_flip(w, dims, f, quant, a, 32)
+                for b in (int(c) for c, m in zip(ci2, cm2) if c >= 0 and c != a and m < FLIP_LIMIT[quant]):
+                    if close(g[i], orc.mlp_flipset(w, dims, f, quant, [a, b]), ROW_ABS, ROW_REL).all():
+                        explained = True
+                        break
+                if explained:
+                    n_pair += 1
+                    break
         if not explained:
             sets = [c for k in (3, 4) for c in itertools.combinations(cand[:8], k)]
             explained = any(close(g[i], orc.mlp_flipset(w, dims, f, quant, c), ROW_ABS, ROW_REL).all() for c in sets)

@@ -17,7 +17,10 @@ from .gpu_helpers import NOID, frame_vs_oracle
 
 pytestmark = pytest.mark.gpu
 
-FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=16)
+# the bench frame's options (bench.py), on the device and in the oracle's names
+FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=32)
+GPU_MARCH = dict(march_steps=256, march_bisect=8)
+ORC_MARCH = dict(march_n=256, march_b=8)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -60,15 +63,15 @@ def test_thousand_instance_frame_matches_oracle(orc, prec):
     sc = sg.thousand_scene()
     precision = native.PREC_BF16 if prec == "bf16" else native.PREC_FP8
     quant = orc.QUANT_BF16 if prec == "bf16" else orc.QUANT_FP8
-    g, w = trained_frame(sc, precision, 600, **FRAME_OPTS)
+    g, w = trained_frame(sc, precision, 600, **FRAME_OPTS, **GPU_MARCH)
     assert g["stats"].status == 0 and g["stats"].primary_pairs > 1_500_000 and g["stats"].fallback_pairs > 0
     # E4M3: one flipped activation moves m by up to ~5e-2, as much as the depth check's half window
     # h, so the window decisions of many refined pairs are knife edges; more pixels keep > 2,500
     # decided
     px = sg.pixel_subset(sc.W, sc.H, 2500 if prec == "bf16" else 5000, 7)
     kw = {} if prec == "bf16" else dict(colour_tol=FP8_COLOUR_TOL)
-    rep, o = frame_vs_oracle(g, orc.OracleScene(sc, nedf_override=w), px=px, quant=quant, march_n=128, march_b=4,
-                             n_threads=16, max_excluded=0.1 if prec == "bf16" else 0.45, **FRAME_OPTS, **kw)
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc, nedf_override=w), px=px, quant=quant, n_threads=16,
+                             max_excluded=0.1 if prec == "bf16" else 0.45, **FRAME_OPTS, **ORC_MARCH, **kw)
     # E4M3's spread leaves most shadow tests of this frame within the decision margin (their
     # pixels' shadows undetermined and not compared); BF16 must decide many more
     assert rep["hit"] > 600 and rep["pixels"] * (1 - rep["excluded"]) > 2000
@@ -93,8 +96,8 @@ def test_stress_kind_frame_fp32_plain_method_matches_oracle(orc):
 def test_stress_kind_frame_bf16_nedf_matches_oracle(orc):
     from paper_2308_04669_gb300 import native
     sc = sg.stress_scene(256, 256, n_inst=512)
-    g, w = trained_frame(sc, native.PREC_BF16, 300, **FRAME_OPTS)
+    g, w = trained_frame(sc, native.PREC_BF16, 300, **FRAME_OPTS, **GPU_MARCH)
     px = sg.pixel_subset(sc.W, sc.H, 2000, 10)
-    rep, o = frame_vs_oracle(g, orc.OracleScene(sc, nedf_override=w), px=px, quant=orc.QUANT_BF16, march_n=128,
-                             march_b=4, n_threads=16, max_excluded=0.1, **FRAME_OPTS)
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc, nedf_override=w), px=px, quant=orc.QUANT_BF16, n_threads=16,
+                             max_excluded=0.1, **FRAME_OPTS, **ORC_MARCH)
     assert rep["hit"] > 200 and g["stats"].status == 0

@@ -1,4 +1,5 @@
-"""The paper's intersection network on the tensor cores (render_cls.cu) against the oracle.
+"""The paper's intersection network on the tensor cores (render_cls.cu) and on CUDA cores in FP32
+(render_cls_f32.cu) against the oracle.
 
 Tolerance, from the arithmetic: the network is 34 BF16 layers deep with a BF16 residual stream.
 A BF16 rounding that lands on the other side of a boundary (FP32 sums on the GPU, double sums in
@@ -16,7 +17,7 @@ import pytest
 
 from paper_2308_04669_gb300 import scenegen as sg
 
-from .gpu_helpers import NOID, MARGIN, close, gpu_frame
+from .gpu_helpers import NOID, MARGIN, close, frame_vs_oracle, gpu_frame
 
 pytestmark = pytest.mark.gpu
 
@@ -107,12 +108,73 @@ def test_classifier_frame_matches_oracle(orc):
     print(dict(pixels=len(px), hit=int(hit.sum()), same=float(same.sum() / decided.sum())))
 
 
-def test_classifier_renders_in_bf16_only():
+def test_classifier_refuses_fp8():
     from paper_2308_04669_gb300 import native
     sc = sg.classifier_scene(16, 16)
     with pytest.raises(native.NedfError) as e:
-        native.renderer_for(sc, precision=native.PREC_FP32)
+        native.renderer_for(sc, precision=native.PREC_FP8)
     assert e.value.code == native.NEDF_ERR_UNSUPPORTED
+
+
+# FP32 on CUDA cores (render_cls_f32.cu) against the FP64 network: the 34 layers' FP32 sums keep the
+# logits within about 1e-5 of their magnitude, so the argmax bins agree exactly wherever the top-2
+# gap exceeds GAP_F32, and the hit logit within LOGIT_TOL.
+GAP_F32 = 1e-3
+LOGIT_TOL = 1e-4
+
+
+def test_classifier_fp32_query_matches_fp64_oracle(orc):
+    import torch
+    from paper_2308_04669_gb300 import native
+    sc = sg.classifier_scene(8, 8)
+    rng = np.random.default_rng(11)
+    n = 700                       # two full 256-row tiles, a ragged one, several 64-row sub-tiles
+    o32 = rng.normal(size=(n, 3))
+    o32 = (2.5 * o32 / np.linalg.norm(o32, axis=1, keepdims=True)).astype(np.float32)
+    d32 = (-o32 + rng.normal(size=(n, 3)) * 0.8).astype(np.float32)
+    r = native.renderer_for(sc, precision=native.PREC_FP32)
+    for t in (0, 1, 2):
+        out = torch.empty(n, 4, device="cuda")
+        r.nedf_query(t, torch.tensor(o32, device="cuda"), torch.tensor(d32, device="cuda"), out)
+        torch.cuda.synchronize()
+        g = out.cpu().numpy().astype(np.float64)
+        w = sc.types[t].nedf_w.astype(np.float64)
+        rows, X, misses = [], [], 0
+        for i in range(n):
+            dd = d32[i].astype(np.float64); dd /= np.linalg.norm(dd)
+            feat, bd = orc.cls_features(o32[i].astype(np.float64), dd, float(sc.types[t].rb))
+            if feat is None:
+                if abs(bd[3]) > 1e-4:
+                    assert g[i, 3] == 0 and np.isinf(g[i, 2]) and g[i, 0] == 0
+                    misses += 1
+                continue
+            rows.append(i)
+            X.append(feat)
+        assert len(rows) > 300 and misses > 20
+        df = [orc.cls_decode(y) for y in orc.cls_logits(w, np.array(X))]
+        mf, af, gap = (np.array([d[k] for d in df]) for k in (0, 1, 4))
+        gm, ga = g[rows, 0], g[rows, 1]
+        assert close(ga, af, LOGIT_TOL, LOGIT_TOL).all(), np.abs(ga - af).max()
+        sel = gap > GAP_F32
+        assert sel.mean() > 0.95 and np.array_equal(gm[sel], mf[sel]), (sel.mean(), (gm[sel] != mf[sel]).sum())
+        Dl = g[rows, 2]
+        assert np.array_equal(g[rows, 3] == 1, (ga > 0) & (Dl > 0))
+        print(f"type {t}: {len(rows)} rays; |logit - fp64| max {np.abs(ga - af).max():.2e}; "
+              f"bins exact on {sel.mean():.4f} of rows")
+    r.close()
+
+
+def test_classifier_fp32_frame_matches_fp64_oracle(orc):
+    """Steps 1-3 with the classifier on every pair in FP32, against the oracle's FP64 frame,
+    element by element: ids bit-exact and depths, colours and shadow factors within the FP32
+    tolerance on the decided pixels (an argmax whose top-2 logit gap is under 1e-3, a depth tie or
+    a bound graze is a knife edge and is counted)."""
+    from paper_2308_04669_gb300 import native
+    sc = sg.classifier_scene(48, 48)
+    g = gpu_frame(sc, precision=native.PREC_FP32)
+    assert g["stats"].status == 0
+    rep, o = frame_vs_oracle(g, orc.OracleScene(sc), n_threads=16, max_excluded=0.05)
+    assert rep["hit"] > 300 and rep["shadowed"] > 50, rep
 
 
 def _fine_centres(m):
