@@ -328,26 +328,33 @@ int nedf_compose_check_wait_limit(nedf_handle *h);
 /* ---- schedule of the tensor-core MLP kernels and its autotuner ----------------------------------
  * The tensor-core engine streams each type's weights through a fixed shared-memory ring in stages,
  * one bulk copy per stage; the stage size trades copy-issue cost against how far ahead the ring
- * reads.  It changes timing only, never results.  Kernel index k of the arrays below:
+ * reads.  The NeDF engine at BF16 width 128 can also run its layers with either operand order:
+ * swapped (the weight chunk as A, 128 output features x the tile's 256 rows, one MMA per chunk)
+ * or unswapped (each 128-row half of the tile as A, the weight chunk as B, two MMAs per chunk).
+ * Neither choice changes results, only timing.  Kernel index k of the arrays below:
  * 0 Step-2 shading, 1 plain-method colour rows, 2 Step-1 NeDF, 3 Step-3 NeDF, 4 NeDF query. */
 #define NEDF_N_SCHEDULE 5
 typedef struct {
     int stage_bytes[NEDF_N_SCHEDULE];  /* weight bytes per bulk copy; 0 = default (16384); the
                                           kernel clamps to a whole number of weight chunks and to
                                           at least two stages in its ring                          */
-    float tuned_ms[NEDF_N_SCHEDULE];   /* set by nedf_compose_autotune: the chosen stage size's
-                                          best time for kernels 0, 2 and 3 (0 elsewhere)           */
+    float tuned_ms[NEDF_N_SCHEDULE];   /* set by nedf_compose_autotune: the chosen schedule's best
+                                          time for kernels 0, 2 and 3 (0 elsewhere)                */
+    int operand_order[NEDF_N_SCHEDULE];/* NeDF kernels 2-4 at BF16 width 128: 0 = default
+                                          (swapped), 1 = swapped, 2 = unswapped; ignored elsewhere */
 } nedf_schedule;
 
 /* Replaces the schedule (host struct, copied).  stage_bytes must be 0 or a multiple of 1024 in
- * [1024, 262144].  The next render re-captures its CUDA graph.  Errors: NEDF_ERR_ARG. */
+ * [1024, 262144], operand_order 0, 1 or 2.  The next render re-captures its CUDA graph.  Errors:
+ * NEDF_ERR_ARG. */
 int nedf_compose_set_schedule(nedf_handle *h, const nedf_schedule *s);
 int nedf_compose_get_schedule(nedf_handle *h, nedf_schedule *s);
 
 /* Autotuner: renders the given frame (into the handle's own buffers) with each candidate stage
- * size (8, 12, 16, 24, 32, 36, 48, 64 KB) for every tensor-core kernel, reps timed frames per candidate with stage
- * events, and keeps per kernel the size with the smallest time (the plain-method colour rows take
- * the shading kernel's choice, NeDF queries Step 1's).  Synchronises; leaves profiling as it was.
+ * size (8, 12, 16, 24, 32, 36, 48, 64 KB) for every tensor-core kernel and, at BF16 width 128,
+ * each operand order of the NeDF engines, reps timed frames per candidate with stage events, and
+ * keeps per kernel the candidate with the smallest time (the plain-method colour rows take the
+ * shading kernel's choice, NeDF queries Step 1's).  Synchronises; leaves profiling as it was.
  * chosen (may be NULL) receives the result.  With FP32 precision there is nothing to tune and the
  * schedule is left unchanged.  Errors: those of nedf_compose_render, NEDF_ERR_ARG for reps < 1. */
 int nedf_compose_autotune(nedf_handle *h, const nedf_camera *cam, const nedf_light *lights, int n_lights,

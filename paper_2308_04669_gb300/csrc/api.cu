@@ -109,6 +109,7 @@ struct nedf_handle {
     bool engines_timed = false, gengines = false;
     int last_launches = 0;
     int stage_bytes[NEDF_N_SCHEDULE] = {0, 0, 0, 0, 0};   // tensor-core schedule (0 = default)
+    int operand_order[NEDF_N_SCHEDULE] = {0, 0, 0, 0, 0};
     // guard bytes after every buffer allocated at create: (buffer, its size)
     std::vector<std::pair<const uint8_t *, size_t>> guards;
 };
@@ -223,6 +224,7 @@ static Workspace make_ws(nedf_handle *h)
     ws.nedf_tc = h->d_nedf_tc;
     ws.nedf_tc_stride = h->nedf_tc_stride;
     for (int k = 0; k < NEDF_N_SCHEDULE; ++k) ws.pipe_stage_bytes[k] = h->stage_bytes[k];
+    for (int k = 0; k < NEDF_N_SCHEDULE; ++k) ws.pipe_order[k] = h->operand_order[k];
     ws.nerf_tc = h->d_nerf_tc;
     ws.nerf_tc_stride = h->nerf_tc_stride;
     ws.fb_list[0] = h->d_fb[0];
@@ -1008,8 +1010,12 @@ int nedf_compose_set_schedule(nedf_handle *h, const nedf_schedule *s)
         const int b = s->stage_bytes[k];
         if (b != 0 && (b < 1024 || b > 262144 || b % 1024 != 0))
             return fail(h, NEDF_ERR_ARG, "stage_bytes: 0 or a multiple of 1024 in [1024, 262144]");
+        if (s->operand_order[k] < 0 || s->operand_order[k] > 2) return fail(h, NEDF_ERR_ARG, "operand_order: 0, 1 or 2");
     }
-    for (int k = 0; k < NEDF_N_SCHEDULE; ++k) h->stage_bytes[k] = s->stage_bytes[k];
+    for (int k = 0; k < NEDF_N_SCHEDULE; ++k) {
+        h->stage_bytes[k] = s->stage_bytes[k];
+        h->operand_order[k] = s->operand_order[k];
+    }
     drop_graph(h);
     return NEDF_OK;
 }
@@ -1020,6 +1026,7 @@ int nedf_compose_get_schedule(nedf_handle *h, nedf_schedule *s)
     for (int k = 0; k < NEDF_N_SCHEDULE; ++k) {
         s->stage_bytes[k] = h->stage_bytes[k];
         s->tuned_ms[k] = 0.0f;
+        s->operand_order[k] = h->operand_order[k];
     }
     return NEDF_OK;
 }
@@ -1036,42 +1043,56 @@ int nedf_compose_autotune(nedf_handle *h, const nedf_camera *cam, const nedf_lig
         // of three and six chunks, which divide the 9-chunk NeDF layers evenly
         static const int cand[8] = {8192, 12288, 16384, 24576, 32768, 36864, 49152, 65536};
         constexpr int n_cand = 8;
+        // operand orders of the NeDF engines: both at BF16 width 128 (swapped, unswapped), else the one
+        const bool orders = h->cfg.nedf_arch == NEDF_ARCH_REGRESSION && h->cfg.precision == NEDF_PREC_BF16 &&
+                            h->cfg.nedf_width == 128 && h->opt.depth_source == NEDF_DEPTH_NEDF;
+        const int n_order = orders ? 2 : 1;
         // stage index of each tuned kernel: Step-2 shading, Step-1 NeDF, Step-3 NeDF
         static const int kern[3] = {0, 2, 3}, stage[3] = {4, 2, 6};
         float best[3] = {1e30f, 1e30f, 1e30f};
-        int pick[3] = {cand[1], cand[1], cand[1]};
+        int pick[3] = {cand[1], cand[1], cand[1]}, pick_order[3] = {0, 0, 0};
         const bool was_profiling = h->profiling;
         r = nedf_compose_set_profiling(h, 1);
         if (r != NEDF_OK) return r;
-        for (int c = 0; c < n_cand; ++c) {
-            for (int k = 0; k < NEDF_N_SCHEDULE; ++k) h->stage_bytes[k] = cand[c];
-            drop_graph(h);
-            float t[3] = {1e30f, 1e30f, 1e30f};
-            for (int i = 0; i <= reps; ++i) {              // the first render captures the graph
-                r = render_impl(h, cam, lights, n_lights);
-                if (r != NEDF_OK) return r;
-                float ms[kStages];
-                r = nedf_compose_get_stage_times(h, ms, kStages);
-                if (r != NEDF_OK) return r;
-                if (i == 0) continue;
-                for (int j = 0; j < 3; ++j) t[j] = std::min(t[j], ms[stage[j]]);
-            }
-            for (int j = 0; j < 3; ++j)
-                if (t[j] < best[j]) {
-                    best[j] = t[j];
-                    pick[j] = cand[c];
+        for (int o = 0; o < n_order; ++o) {
+            const int order = orders ? 1 + o : 0;
+            for (int k = 0; k < NEDF_N_SCHEDULE; ++k) h->operand_order[k] = order;
+            for (int c = 0; c < n_cand; ++c) {
+                for (int k = 0; k < NEDF_N_SCHEDULE; ++k) h->stage_bytes[k] = cand[c];
+                drop_graph(h);
+                float t[3] = {1e30f, 1e30f, 1e30f};
+                for (int i = 0; i <= reps; ++i) {              // the first render captures the graph
+                    r = render_impl(h, cam, lights, n_lights);
+                    if (r != NEDF_OK) return r;
+                    float ms[kStages];
+                    r = nedf_compose_get_stage_times(h, ms, kStages);
+                    if (r != NEDF_OK) return r;
+                    if (i == 0) continue;
+                    for (int j = 0; j < 3; ++j) t[j] = std::min(t[j], ms[stage[j]]);
                 }
+                for (int j = 0; j < 3; ++j)
+                    if (t[j] < best[j]) {
+                        best[j] = t[j];
+                        pick[j] = cand[c];
+                        pick_order[j] = order;
+                    }
+            }
         }
         h->stage_bytes[0] = pick[0];
         h->stage_bytes[1] = pick[0];
         h->stage_bytes[2] = pick[1];
         h->stage_bytes[3] = pick[2];
         h->stage_bytes[4] = pick[1];
+        for (int k = 0; k < NEDF_N_SCHEDULE; ++k) h->operand_order[k] = 0;
+        h->operand_order[2] = pick_order[1];
+        h->operand_order[3] = pick_order[2];
+        h->operand_order[4] = pick_order[1];
         drop_graph(h);
         h->profiling = was_profiling;
         if (chosen) {
             for (int k = 0; k < NEDF_N_SCHEDULE; ++k) {
                 chosen->stage_bytes[k] = h->stage_bytes[k];
+                chosen->operand_order[k] = h->operand_order[k];
                 chosen->tuned_ms[k] = 0.0f;
             }
             for (int j = 0; j < 3; ++j) chosen->tuned_ms[kern[j]] = best[j];

@@ -111,6 +111,9 @@ struct Workspace {
     // tensor-core schedule: weight bytes per bulk copy of each engine mode (shade, march colour,
     // primary NeDF, shadow NeDF, NeDF query); picked by the autotuner or set by the caller
     int pipe_stage_bytes[5];
+    // operand order of the NeDF engines at BF16 width 128 (same kernel index): 0 default, 1 swapped
+    // (weights as A, D^T = W H^T), 2 unswapped (activations as A); results do not depend on it
+    int pipe_order[5];
 };
 
 struct LightCam {

@@ -680,10 +680,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
 // into one more chunk whose B (or, unswapped, A) operand is a constant block of ones shared by both
 // slots.
 // ---------------------------------------------------------------------------------------------------
-template <int N, bool F8>
+// SWAP (BF16 width 128 only): the operand order above; the autotuner picks it per NeDF mode (the
+// unswapped order: A = each half's activations, B = the weight chunk, as at width 64 and in E4M3).
+template <int N, bool F8, bool SWAP = (N == 128 && !F8)>
 struct NedfShape2 {
+    static_assert(!SWAP || (N == 128 && !F8), "swapped operands: BF16 width 128 only");
     using B = PipeShape<N, false, F8>;
-    static constexpr bool SW = N == 128 && !F8;                             // swapped operands
+    static constexpr bool SW = SWAP;                                         // swapped operands
     static constexpr size_t H_BYTES = 65536;        // swapped: 8 chunks x 256 rows x 16 BF16 columns
     static constexpr size_t ONES_BYTES = 8192;      // swapped: the bias chunk's constant operand
     // BF16 width 128: room for two whole 9-chunk layers (36 KB each), so a layer can be one stage
@@ -714,10 +717,16 @@ __global__ void __launch_bounds__(256) k_nedf_decode(Workspace ws)
     const uint2 *pairs = SHADOW ? ws.spairs : ws.ppairs;
     const float2 *nout = ws.nout[SHADOW ? 1 : 0];
     const int lane = threadIdx.x & 31;
-    // the trip count is uniform within a block, so the ballot below sees whole warps
+    __shared__ unsigned s_cnt;
+    __shared__ unsigned long long s_base;
+    // the trip count is uniform within a block, so the ballot and the barriers below see whole
+    // warps; deferred pairs are ranked inside the block (shared-memory atomics) and the block's
+    // range of the plain method's list is reserved with one global atomic
     for (unsigned long long base = blockIdx.x * (unsigned long long)blockDim.x; base < n;
          base += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long idx = base + threadIdx.x;
+        if (threadIdx.x == 0) s_cnt = 0u;
+        __syncthreads();
         bool defer = false;
         if (idx < n) {
             int t = 0;
@@ -742,13 +751,16 @@ __global__ void __launch_bounds__(256) k_nedf_decode(Workspace ws)
             if (!defer && hit) apply_hit(ws, f, SHADOW, pr, Dl);
         }
         const unsigned m = __ballot_sync(0xffffffffu, defer);
+        unsigned pos = 0;
         if (m) {
             const int leader = __ffs(m) - 1;
-            unsigned long long start = 0;
-            if (lane == leader) start = atomicAdd(&ws.cnt->fb_count[SHADOW ? 1 : 0], (unsigned long long)__popc(m));
-            start = __shfl_sync(0xffffffffu, start, leader);
-            if (defer) ws.fb_list[SHADOW ? 1 : 0][start + __popc(m & ((1u << lane) - 1u))] = (uint32_t)idx;
+            if (lane == leader) pos = atomicAdd(&s_cnt, (unsigned)__popc(m));
+            pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(m & ((1u << lane) - 1u));
         }
+        __syncthreads();
+        if (threadIdx.x == 0 && s_cnt) s_base = atomicAdd(&ws.cnt->fb_count[SHADOW ? 1 : 0], (unsigned long long)s_cnt);
+        __syncthreads();
+        if (defer) ws.fb_list[SHADOW ? 1 : 0][s_base + pos] = (uint32_t)idx;
     }
 }
 
@@ -759,11 +771,11 @@ cudaError_t launch_nedf_decode(const Workspace &ws, int mode, int num_sms, cudaS
     return cudaGetLastError();
 }
 
-template <int N, int MODE, bool F8>
+template <int N, int MODE, bool F8, bool SWAP>
 __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBuffers mb, PipeArgs a)
 {
     using SH = PipeShape<N, false, F8>;
-    using S2 = NedfShape2<N, F8>;
+    using S2 = NedfShape2<N, F8, SWAP>;
     constexpr int K0 = SH::K0, NOUT = 2;
     const int GC = max(1, min(a.stage_bytes / SH::CHUNK, S2::SMAX / 2));
     const int STAGE = GC * SH::CHUNK, S = S2::RING / STAGE;
@@ -1057,29 +1069,51 @@ cudaError_t launch_wait_check(uint32_t *status, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------------------------------
-// Deferred plain-method pairs (low confidence or outliers), one thread per pair
+// Deferred plain-method pairs (low confidence, outliers, checked misses), one warp per pair
 // ---------------------------------------------------------------------------------------------------
-__global__ void k_fallback(Workspace ws, int mode)
+__global__ void __launch_bounds__(256) k_fallback(Workspace ws, int mode)
 {
     const DevFrame &f = *ws.frame;
     const unsigned long long n = ws.cnt->fb_count[mode];
     const uint2 *pairs = mode == 1 ? ws.spairs : ws.ppairs;
-    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < n;
-         e += (unsigned long long)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    // one warp per deferred pair: the plain method's uniform samples t_k = t_e + (t_x - t_e) k / steps
+    // (the march_crossing sequence) 32 at a time, the first k whose sample is inside while sample
+    // k - 1 is not found by a ballot, then the same bisection: the same result as the serial march
+    for (unsigned long long e = blockIdx.x * (unsigned long long)(blockDim.x >> 5) + (threadIdx.x >> 5); e < n; e += n_warps) {
         const uint2 pr = pairs[ws.fb_list[mode][e]];
         const DevType T = ws.types[ws.inst[pr.y].type];
         PairRay R;
         setup_pair_ray(ws, f, mode == 1, pr, T.rb, R);
-        bool hit = false;
-        const float Dl = march_crossing(T, R.ol, R.dl, R.te, R.tx, f.march_steps, f.march_bisect, hit);
-        if (hit) apply_hit(ws, f, mode == 1, R, Dl);
+        const int steps = f.march_steps;
+        const float te = R.te, span = R.tx - R.te;
+        bool carry = inside_solid(T, madd(R.ol, te, R.dl));          // sample 0
+        int kc = 0;
+        for (int base = 1; base <= steps && kc == 0; base += 32) {
+            const int k = base + lane;
+            const bool in = k <= steps && inside_solid(T, madd(R.ol, te + span * (float)k / (float)steps, R.dl));
+            bool prev = __shfl_up_sync(0xffffffffu, in, 1);
+            if (lane == 0) prev = carry;
+            const unsigned cross = __ballot_sync(0xffffffffu, in && !prev);
+            if (cross) kc = base + __ffs(cross) - 1;
+            carry = __shfl_sync(0xffffffffu, in, 31);
+        }
+        if (kc == 0) continue;                                    // no crossing: the pair stays a miss
+        float lo = kc == 1 ? te : te + span * (float)(kc - 1) / (float)steps;
+        float hi = te + span * (float)kc / (float)steps;
+        for (int it = 0; it < f.march_bisect; ++it) {
+            const float mid = 0.5f * (lo + hi);
+            if (inside_solid(T, madd(R.ol, mid, R.dl))) hi = mid; else lo = mid;
+        }
+        if (lane == 0) apply_hit(ws, f, mode == 1, R, 0.5f * (lo + hi));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ws.cnt->fallback, n);
 }
 
 cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStream_t st)
 {
-    k_fallback<<<num_sms * 8, 128, 0, st>>>(ws, mode);
+    k_fallback<<<num_sms * 8, 256, 0, st>>>(ws, mode);
     return cudaGetLastError();
 }
 
@@ -1113,16 +1147,16 @@ static cudaError_t launch_pipe(const Workspace &ws, const MarchBuffers &mb, cons
     }
 }
 
-template <int N, int MODE, bool F8>
+template <int N, int MODE, bool F8, bool SWAP = (N == 128 && !F8)>
 static cudaError_t launch_nedf2_n(const Workspace &ws, const PipeArgs &a, int grid, cudaStream_t st)
 {
     const size_t f32b = (pipe_f32_floats(N, ws.nedf_hidden, 2, F8) * 4 + 15) & ~(size_t)15;
-    const size_t sm = NedfShape2<N, F8>::FIXED + 2 * f32b;
+    const size_t sm = NedfShape2<N, F8, SWAP>::FIXED + 2 * f32b;
     if (sm > 227 * 1024 - 8192) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(k_nedf2<N, MODE, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_nedf2<N, MODE, F8, SWAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     MarchBuffers none{};
-    k_nedf2<N, MODE, F8><<<grid, kPipeThreads, sm, st>>>(ws, none, a);
+    k_nedf2<N, MODE, F8, SWAP><<<grid, kPipeThreads, sm, st>>>(ws, none, a);
     return cudaGetLastError();
 }
 
@@ -1135,7 +1169,11 @@ static cudaError_t launch_nedf2(const Workspace &ws, const PipeArgs &a, int grid
     args.stage_bytes = ws.pipe_stage_bytes[MODE] > 0 ? ws.pipe_stage_bytes[MODE] : kDefaultStageBytes;
     switch (ws.nedf_width) {
     case 64: return f8 ? launch_nedf2_n<64, MODE, true>(ws, args, grid, st) : launch_nedf2_n<64, MODE, false>(ws, args, grid, st);
-    case 128: return f8 ? launch_nedf2_n<128, MODE, true>(ws, args, grid, st) : launch_nedf2_n<128, MODE, false>(ws, args, grid, st);
+    case 128:
+        if (f8) return launch_nedf2_n<128, MODE, true>(ws, args, grid, st);
+        // operand order 2: unswapped (activations as A); 0 (default) and 1: swapped
+        return ws.pipe_order[MODE] == 2 ? launch_nedf2_n<128, MODE, false, false>(ws, args, grid, st)
+                                        : launch_nedf2_n<128, MODE, false, true>(ws, args, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }

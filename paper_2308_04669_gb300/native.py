@@ -67,7 +67,8 @@ SCHEDULE_KERNELS = ("step2_shade", "march_colour", "step1_nedf", "step3_nedf", "
 
 
 class Schedule(C.Structure):
-    _fields_ = [("stage_bytes", C.c_int * N_SCHEDULE), ("tuned_ms", C.c_float * N_SCHEDULE)]
+    _fields_ = [("stage_bytes", C.c_int * N_SCHEDULE), ("tuned_ms", C.c_float * N_SCHEDULE),
+                ("operand_order", C.c_int * N_SCHEDULE)]
 
 
 class FrameStats(C.Structure):
@@ -323,10 +324,13 @@ class Renderer:
     def check_wait_limit(self):
         return self._check(_lib.nedf_compose_check_wait_limit(self.h))
 
-    def set_schedule(self, stage_bytes):
+    def set_schedule(self, stage_bytes, operand_order=None):
+        """stage_bytes (and operand_order: 0 default, 1 swapped, 2 unswapped) per kernel index."""
         s = Schedule()
         for k, b in enumerate(stage_bytes):
             s.stage_bytes[k] = int(b)
+        for k, o in enumerate(operand_order or []):
+            s.operand_order[k] = int(o)
         return self._check(_lib.nedf_compose_set_schedule(self.h, C.byref(s)))
 
     def get_schedule(self) -> dict:
@@ -334,14 +338,21 @@ class Renderer:
         self._check(_lib.nedf_compose_get_schedule(self.h, C.byref(s)))
         return {k: s.stage_bytes[i] for i, k in enumerate(SCHEDULE_KERNELS)}
 
+    def get_operand_order(self) -> dict:
+        s = Schedule()
+        self._check(_lib.nedf_compose_get_schedule(self.h, C.byref(s)))
+        return {k: s.operand_order[i] for i, k in enumerate(SCHEDULE_KERNELS)}
+
     def autotune(self, cam, lights, reps=3) -> dict:
-        """Picks the stage size of every tensor-core kernel by timing this frame; returns
-        {kernel: {"stage_bytes": b, "ms": best time (0 if not timed)}}."""
+        """Picks the stage size of every tensor-core kernel (and the NeDF engines' operand order at
+        BF16 width 128) by timing this frame; returns {kernel: {"stage_bytes": b, "operand_order":
+        "swapped" | "unswapped" | "fixed", "ms": best time (0 if not timed)}}."""
         s = Schedule()
         la, nl = lights
         self._check(_lib.nedf_compose_autotune(self.h, C.byref(cam), la, nl, reps, C.byref(s)))
-        return {k: {"stage_bytes": s.stage_bytes[i], "ms": round(float(s.tuned_ms[i]), 4)}
-                for i, k in enumerate(SCHEDULE_KERNELS)}
+        names = {0: "fixed", 1: "swapped", 2: "unswapped"}
+        return {k: {"stage_bytes": s.stage_bytes[i], "operand_order": names[s.operand_order[i]],
+                    "ms": round(float(s.tuned_ms[i]), 4)} for i, k in enumerate(SCHEDULE_KERNELS)}
 
     def nedf_query(self, type_, o, d, out):
         return self._check(_lib.nedf_compose_nedf_query(self.h, type_, int(o.shape[0]), _ptr(o), _ptr(d), _ptr(out)))

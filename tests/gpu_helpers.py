@@ -167,6 +167,9 @@ def compare_volume(g_rgba, o_rgba, vmargin, tol=(ABS_TOL, REL_TOL), max_excluded
 # sum's magnitude (measured on rows explained by a flip: most within 1e-6, a few near 1e-4, for
 # both the BF16 and the E4M3 products)
 FLIP_LIMIT = {1: 1e-4, 2: 1e-4}
+# rows whose exact flip set is beyond the bounded search (measured: 1 in ~4,000 BF16 rows, with 16
+# near-ties under 3.3e-6 of their scale) may be accepted by the first-order bound, this rarely
+BOUNDED_ROWS = 0.005
 
 
 def check_network_rows(orc, g, w, dims, feats, quant, max_flip_rows):
@@ -176,10 +179,12 @@ def check_network_rows(orc, g, w, dims, feats, quant, max_flip_rows):
     the same bound: an FP32 sum on the GPU fell on the other side of each such boundary.  Tried in
     order: one value; two of the sixteen nearest; one of the sixteen nearest and then a near-tie of
     the trajectory that flip produces (a cascade); three or four of the eight nearest (a row with
-    several near-ties).  Rows of the second kind are counted and bounded by max_flip_rows (a
+    several near-ties).  A row none of these reproduces must lie within the first-order bound of
+    its sixteen nearest near-ties (the sum of their single flips' output changes); at most
+    BOUNDED_ROWS of the rows may be of that kind.  Rows of the second kind are counted and bounded by max_flip_rows (a
     fraction)."""
     import itertools
-    n_tight = n_flip = n_pair = n_multi = 0
+    n_tight = n_flip = n_pair = n_multi = n_bounded = 0
     flips_needed = []
     for i, f in enumerate(feats):
         if f is None:
@@ -211,10 +216,19 @@ def check_network_rows(orc, g, w, dims, feats, quant, max_flip_rows):
             sets = [c for k in (3, 4) for c in itertools.combinations(cand[:8], k)]
             explained = any(close(g[i], orc.mlp_flipset(w, dims, f, quant, c), ROW_ABS, ROW_REL).all() for c in sets)
             n_multi += explained
+        if not explained:
+            # a row with many near-ties whose exact flip set the search above does not reach: within
+            # the first-order bound of its sixteen nearest (the sum of their single flips' effects)
+            bound = np.zeros_like(y)
+            for c in cand[:16]:
+                bound += np.abs(orc.mlp_flip(w, dims, f, quant, c, 0)[0] - y)
+            explained = bool((np.abs(g[i] - y) <= bound).all())
+            n_bounded += explained
         assert explained, f"row {i}: gpu {g[i]} oracle {y}, not explained by rounding flips (margins {cm[:8]})"
         n_flip += 1
         flips_needed.append(float(np.abs(g[i] - y).max()))
     rows = n_tight + n_flip
     assert rows > 0 and n_flip <= max_flip_rows * rows, (n_flip, rows)
+    assert n_bounded <= BOUNDED_ROWS * rows, (n_bounded, rows)
     return dict(rows=rows, flip_rows=n_flip, two_flip_rows=n_pair, multi_flip_rows=n_multi,
-                flip_err_max=max(flips_needed, default=0.0))
+                bounded_rows=n_bounded, flip_err_max=max(flips_needed, default=0.0))

@@ -116,11 +116,13 @@ def test_classifier_refuses_fp8():
     assert e.value.code == native.NEDF_ERR_UNSUPPORTED
 
 
-# FP32 on CUDA cores (render_cls_f32.cu) against the FP64 network: the 34 layers' FP32 sums keep the
-# logits within about 1e-5 of their magnitude, so the argmax bins agree exactly wherever the top-2
-# gap exceeds GAP_F32, and the hit logit within LOGIT_TOL.
+# FP32 on CUDA cores (render_cls_f32.cu) against the FP64 network.  The 16 chord points are FP32
+# coordinates (relative error ~6e-8) whose highest encoding frequency multiplies them by 2^9, so a
+# feature carries up to ~3e-5 of absolute error, which the 34 layers carry into the logits: measured
+# up to 1.2e-4.  The hit logit must agree within LOGIT_TOL, the argmax bins exactly wherever the
+# top-2 gap exceeds GAP_F32 (several times twice the largest logit error).
 GAP_F32 = 1e-3
-LOGIT_TOL = 1e-4
+LOGIT_TOL = 5e-4
 
 
 def test_classifier_fp32_query_matches_fp64_oracle(orc):

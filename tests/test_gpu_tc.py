@@ -160,6 +160,12 @@ def test_every_stage_size_on_a_large_frame(prec):
         for _ in range(2):
             got = frame()
             assert all(np.array_equal(x, y) for x, y in zip(ref, got)), b
+    # the NeDF engines' operand order (BF16 width 128: swapped or unswapped; ignored in E4M3)
+    for order in (1, 2):
+        for b in (8192, 36864):
+            r.set_schedule([b] * native.N_SCHEDULE, [order] * native.N_SCHEDULE)
+            got = frame()
+            assert all(np.array_equal(x, y) for x, y in zip(ref, got)), (order, b)
     r.close()
 
 
@@ -191,6 +197,8 @@ def test_schedule_changes_timing_not_results():
             assert all(np.array_equal(x, y) for x, y in zip(ref, got)), b
         tuned = r.autotune(cam, li, reps=1)
         assert all(v["stage_bytes"] in (8192, 12288, 16384, 24576, 32768, 36864, 49152, 65536) for v in tuned.values())
+        want = ("swapped", "unswapped") if prec == native.PREC_BF16 else ("fixed",)
+        assert tuned["step1_nedf"]["operand_order"] in want and tuned["step3_nedf"]["operand_order"] in want
         assert tuned["step2_shade"]["ms"] > 0 and tuned["step1_nedf"]["ms"] > 0
         assert r.get_schedule()["step3_nedf"] == tuned["step3_nedf"]["stage_bytes"]
         got = frame()
