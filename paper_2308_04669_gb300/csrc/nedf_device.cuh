@@ -184,14 +184,17 @@ __device__ __forceinline__ float density(const DevType &t, V3 x, float sigma_max
 }
 
 // Plain method: steps uniform steps over [te, tx]; first outside -> inside step; bisection.
-// Returns the crossing (local) or +inf.
+// Returns the crossing (local) or +inf.  Sample k is t_e + k (t_x - t_e) / steps, the step divided
+// once (a division per sample would cost more than the density test it places).
 __device__ __forceinline__ float march_crossing(const DevType &t, V3 ol, V3 dl, float te, float tx,
                                                 int steps, int bisect, bool &hit)
 {
-    float prev_t = te;
+    const float step = (tx - te) / (float)steps;
+    float prev_t = te, kf = 0.0f;
     bool prev_in = inside_solid(t, madd(ol, te, dl));
     for (int k = 1; k <= steps; ++k) {
-        float tk = te + (tx - te) * (float)k / (float)steps;
+        kf += 1.0f;
+        float tk = fmaf(kf, step, te);
         bool in = inside_solid(t, madd(ol, tk, dl));
         if (in && !prev_in) {
             float lo = prev_t, hi = tk;

@@ -82,34 +82,10 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
-// Appends (a, b) for every lane with keep set to segment `type` of a list (and, when geo is not
-// null, the pair's two geometry vectors at the same index); a pair beyond the segment is dropped
-// and the status word flagged.
-__device__ __forceinline__ void warp_append(bool keep, uint2 val, unsigned long long *cursor,
-                                            const unsigned long long *seg_end, uint2 *list,
-                                            uint32_t *status, uint32_t flag, float4 *geo = nullptr,
-                                            float4 g0 = float4{}, float4 g1 = float4{})
-{
-    unsigned mask = __ballot_sync(0xffffffffu, keep);
-    if (!mask) return;
-    int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
-    unsigned long long start = 0;
-    if (lane == leader) start = atomicAdd(cursor, (unsigned long long)__popc(mask));
-    start = __shfl_sync(0xffffffffu, start, leader);
-    if (keep) {
-        unsigned long long idx = start + __popc(mask & lanemask_lt());
-        if (idx < *seg_end) {
-            list[idx] = val;
-            if (geo) {
-                geo[2 * idx] = g0;
-                geo[2 * idx + 1] = g1;
-            }
-        } else {
-            atomicOr(status, flag);
-        }
-    }
-}
-
+// One block per instance: the pixels of the conservative screen rectangle of its bound sphere,
+// each culled exactly.  PASS 0 counts the kept pairs (pinst[2 i], and the type's total); after the
+// scan (pinst[2 i + 1] = the first index of the instance's range in its type's segment) PASS 1
+// writes them there with a shared-memory cursor, so no global counter is contended.
 template <int PASS>
 __global__ void __launch_bounds__(kThreads) k_bin_primary(Workspace ws)
 {
@@ -117,15 +93,26 @@ __global__ void __launch_bounds__(kThreads) k_bin_primary(Workspace ws)
     int inst = blockIdx.x;
     if (inst >= f.n_inst) return;
     // buffer reuse: the frozen part leaves the manipulated instance out, an edit frame has only it
-    if ((f.edit_mode == 1 && inst == f.edit_inst) || (f.edit_mode == 2 && inst != f.edit_inst)) return;
+    const bool skip = (f.edit_mode == 1 && inst == f.edit_inst) || (f.edit_mode == 2 && inst != f.edit_inst);
     DevInst I = ws.inst[inst];
     DevType T = ws.types[I.type];
-    int i0, i1, j0, j1;
-    if (!screen_rect(f, v3(I.T[0], I.T[1], I.T[2]), T.rb * I.s, i0, i1, j0, j1)) return;
+    int i0 = 0, i1 = -1, j0 = 0, j1 = -1;
+    if (skip || !screen_rect(f, v3(I.T[0], I.T[1], I.T[2]), T.rb * I.s, i0, i1, j0, j1)) {
+        if (PASS == 0 && threadIdx.x == 0) ws.pinst[2 * inst] = 0;
+        return;
+    }
     int bw = i1 - i0 + 1, npx = bw * (j1 - j0 + 1);
-    __shared__ unsigned long long blk_count;
-    if (PASS == 0 && threadIdx.x == 0) blk_count = 0;
-    if (PASS == 0) __syncthreads();
+    __shared__ unsigned long long blk_count, s_cur, s_beg, s_end;
+    if (threadIdx.x == 0) {
+        if (PASS == 0) {
+            blk_count = 0;
+        } else {
+            s_beg = s_cur = ws.pinst[2 * inst + 1];
+            s_end = min(s_beg + ws.pinst[2 * inst], ws.cnt->p_off[I.type + 1]);
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
     unsigned local = 0;
     for (int base = 0; base < npx; base += blockDim.x) {
         int p = base + threadIdx.x;
@@ -143,17 +130,37 @@ __global__ void __launch_bounds__(kThreads) k_bin_primary(Workspace ws)
         if (PASS == 0) {
             local += keep;
         } else {
-            warp_append(keep, make_uint2((uint32_t)(j * f.W + i), (uint32_t)inst), &ws.cnt->p_cursor[I.type],
-                        &ws.cnt->p_off[I.type + 1], ws.ppairs, ws.status, kStatusPrimaryOverflow,
-                        ws.pair_geo ? ws.pgeo : nullptr, make_float4(ol.x, ol.y, ol.z, c.te),
-                        make_float4(dl.x, dl.y, dl.z, c.tp));
+            const unsigned mask = __ballot_sync(0xffffffffu, keep);
+            if (!mask) continue;
+            const int leader = __ffs(mask) - 1;
+            unsigned long long start = 0;
+            if (lane == leader) start = atomicAdd(&s_cur, (unsigned long long)__popc(mask));
+            start = __shfl_sync(0xffffffffu, start, leader);
+            if (keep) {
+                const unsigned long long idx = start + __popc(mask & lanemask_lt());
+                if (idx < s_end) {
+                    ws.ppairs[idx] = make_uint2((uint32_t)(j * f.W + i), (uint32_t)inst);
+                    if (ws.pair_geo) {
+                        ws.pgeo[2 * idx] = make_float4(ol.x, ol.y, ol.z, c.te);
+                        ws.pgeo[2 * idx + 1] = make_float4(dl.x, dl.y, dl.z, c.tp);
+                    }
+                } else {
+                    atomicOr(ws.status, kStatusPrimaryOverflow);
+                }
+            }
         }
     }
     if (PASS == 0) {
         for (int o = 16; o; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
-        if ((threadIdx.x & 31) == 0 && local) atomicAdd(&blk_count, (unsigned long long)local);
+        if (lane == 0 && local) atomicAdd(&blk_count, (unsigned long long)local);
         __syncthreads();
-        if (threadIdx.x == 0 && blk_count) atomicAdd(&ws.cnt->p_count[I.type], blk_count);
+        if (threadIdx.x == 0) {
+            ws.pinst[2 * inst] = blk_count;
+            if (blk_count) atomicAdd(&ws.cnt->p_count[I.type], blk_count);
+        }
+    } else {
+        __syncthreads();
+        if (threadIdx.x == 0 && s_end > s_beg) atomicAdd(&ws.cnt->p_cursor[I.type], min(s_cur, s_end) - s_beg);
     }
 }
 
@@ -182,11 +189,22 @@ __device__ void scan_list(unsigned long long *count, unsigned long long *cursor,
     if (requested) *requested = req;
 }
 
-__global__ void k_scan_primary(Workspace ws, int rows_per_tile)
+// The type segments (thread 0), then each instance's range inside its type's segment (any
+// disjoint order: a shared-memory running offset per type).
+__global__ void __launch_bounds__(1024) k_scan_primary(Workspace ws, int rows_per_tile)
 {
+    __shared__ unsigned long long s_run[kMaxTypes];
     const DevFrame &f = *ws.frame;
-    scan_list(ws.cnt->p_count, ws.cnt->p_cursor, ws.cnt->p_off, ws.cnt->p_tile, f.n_types, ws.pcap,
-              rows_per_tile, ws.status, kStatusPrimaryOverflow, &ws.cnt->p_total_requested);
+    if (threadIdx.x == 0)
+        scan_list(ws.cnt->p_count, ws.cnt->p_cursor, ws.cnt->p_off, ws.cnt->p_tile, f.n_types, ws.pcap,
+                  rows_per_tile, ws.status, kStatusPrimaryOverflow, &ws.cnt->p_total_requested);
+    __syncthreads();
+    if (threadIdx.x < f.n_types) s_run[threadIdx.x] = ws.cnt->p_off[threadIdx.x];
+    __syncthreads();
+    for (int i = threadIdx.x; i < f.n_inst; i += blockDim.x) {
+        const unsigned long long c = ws.pinst[2 * i];
+        ws.pinst[2 * i + 1] = c ? atomicAdd(&s_run[ws.inst[i].type], c) : 0ull;
+    }
 }
 
 __global__ void k_scan_shade(Workspace ws, int pixels_per_tile)
@@ -576,7 +594,7 @@ cudaError_t launch_primary_binning(FrameLaunch &L)
     k_setup<<<1, 256, 0, st>>>(ws, L.cam);
     k_clear<<<L.num_sms * 4, 256, 0, st>>>(ws, npix);
     k_bin_primary<0><<<L.n_inst, kThreads, 0, st>>>(ws);
-    k_scan_primary<<<1, 1, 0, st>>>(ws, kTileRows);
+    k_scan_primary<<<1, 1024, 0, st>>>(ws, kTileRows);
     k_bin_primary<1><<<L.n_inst, kThreads, 0, st>>>(ws);
     return cudaGetLastError();
 }
@@ -615,7 +633,7 @@ cudaError_t launch_frame(FrameLaunch &L)
     k_clear<<<gsm * 4, 256, 0, st>>>(ws, npix);
     mark();
     k_bin_primary<0><<<L.n_inst, kThreads, 0, st>>>(ws);
-    k_scan_primary<<<1, 1, 0, st>>>(ws, nedf_rows);
+    k_scan_primary<<<1, 1024, 0, st>>>(ws, nedf_rows);
     k_bin_primary<1><<<L.n_inst, kThreads, 0, st>>>(ws);
     // the engine launch alone, inside its stage (the stage also holds the decode and fallback)
     auto mark_engine = [&](int k) {

@@ -107,6 +107,8 @@ struct Workspace {
     // shadow-ray binning: per type t and block b of the binning grid, the block's pair count (count
     // pass), then the first index of its range ([t][nb] = the end of the type's grid pairs)
     unsigned long long *sblk;    // [kMaxTypes][sblk_nb + 1]
+    // primary binning: per instance its pair count (count pass) and the first index of its range
+    unsigned long long *pinst;   // [max_instances][2]
     int sblk_nb;                 // blocks of the shadow-ray binning grid
     // tensor-core schedule: weight bytes per bulk copy of each engine mode (shade, march colour,
     // primary NeDF, shadow NeDF, NeDF query); picked by the autotuner or set by the caller

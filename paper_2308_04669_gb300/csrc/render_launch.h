@@ -64,7 +64,7 @@ cudaError_t launch_wait_check(uint32_t *status, cudaStream_t st);
 
 // Step-3 binning through per-light shadow-map cameras (shadow_bin.cu); its shadow-ray passes run
 // shadow_bin_blocks(num_sms) blocks (Workspace::sblk holds a range per type and block)
-inline int shadow_bin_blocks(int num_sms) { return num_sms * 8; }
+inline int shadow_bin_blocks(int num_sms) { return num_sms * 6; }   // one wave at 6 blocks per SM
 // edit_frame: buffer reuse's edit frame (the frozen pixels' shadow rays against the manipulated instance too)
 cudaError_t launch_shadow_binning(const Workspace &ws, int npix, int n_lights, int n_inst, int rows_per_tile,
                                   int num_sms, cudaStream_t st, int *launches, bool edit_frame = false);

@@ -1069,51 +1069,29 @@ cudaError_t launch_wait_check(uint32_t *status, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------------------------------
-// Deferred plain-method pairs (low confidence, outliers, checked misses), one warp per pair
+// Deferred plain-method pairs (low confidence, outliers, checked misses), one thread per pair
 // ---------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_fallback(Workspace ws, int mode)
+__global__ void k_fallback(Workspace ws, int mode)
 {
     const DevFrame &f = *ws.frame;
     const unsigned long long n = ws.cnt->fb_count[mode];
     const uint2 *pairs = mode == 1 ? ws.spairs : ws.ppairs;
-    const int lane = threadIdx.x & 31;
-    const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-    // one warp per deferred pair: the plain method's uniform samples t_k = t_e + (t_x - t_e) k / steps
-    // (the march_crossing sequence) 32 at a time, the first k whose sample is inside while sample
-    // k - 1 is not found by a ballot, then the same bisection: the same result as the serial march
-    for (unsigned long long e = blockIdx.x * (unsigned long long)(blockDim.x >> 5) + (threadIdx.x >> 5); e < n; e += n_warps) {
+    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < n;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
         const uint2 pr = pairs[ws.fb_list[mode][e]];
         const DevType T = ws.types[ws.inst[pr.y].type];
         PairRay R;
         setup_pair_ray(ws, f, mode == 1, pr, T.rb, R);
-        const int steps = f.march_steps;
-        const float te = R.te, span = R.tx - R.te;
-        bool carry = inside_solid(T, madd(R.ol, te, R.dl));          // sample 0
-        int kc = 0;
-        for (int base = 1; base <= steps && kc == 0; base += 32) {
-            const int k = base + lane;
-            const bool in = k <= steps && inside_solid(T, madd(R.ol, te + span * (float)k / (float)steps, R.dl));
-            bool prev = __shfl_up_sync(0xffffffffu, in, 1);
-            if (lane == 0) prev = carry;
-            const unsigned cross = __ballot_sync(0xffffffffu, in && !prev);
-            if (cross) kc = base + __ffs(cross) - 1;
-            carry = __shfl_sync(0xffffffffu, in, 31);
-        }
-        if (kc == 0) continue;                                    // no crossing: the pair stays a miss
-        float lo = kc == 1 ? te : te + span * (float)(kc - 1) / (float)steps;
-        float hi = te + span * (float)kc / (float)steps;
-        for (int it = 0; it < f.march_bisect; ++it) {
-            const float mid = 0.5f * (lo + hi);
-            if (inside_solid(T, madd(R.ol, mid, R.dl))) hi = mid; else lo = mid;
-        }
-        if (lane == 0) apply_hit(ws, f, mode == 1, R, 0.5f * (lo + hi));
+        bool hit = false;
+        const float Dl = march_crossing(T, R.ol, R.dl, R.te, R.tx, f.march_steps, f.march_bisect, hit);
+        if (hit) apply_hit(ws, f, mode == 1, R, Dl);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ws.cnt->fallback, n);
 }
 
 cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStream_t st)
 {
-    k_fallback<<<num_sms * 8, 256, 0, st>>>(ws, mode);
+    k_fallback<<<num_sms * 8, 128, 0, st>>>(ws, mode);
     return cudaGetLastError();
 }
 

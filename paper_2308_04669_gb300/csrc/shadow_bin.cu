@@ -267,7 +267,7 @@ __device__ __forceinline__ unsigned lane_lt()
 // scan, PASS 1 runs the same rays in the same blocks and places each block's pairs in its own
 // range of each type's list with shared-memory cursors, so no global counter is contended.
 template <int PASS>
-__global__ void __launch_bounds__(256) k_bin_shadow_grid(Workspace ws, int npix)
+__global__ void __launch_bounds__(256, 6) k_bin_shadow_grid(Workspace ws, int npix)
 {
     __shared__ unsigned long long hit_pre[kMaxTypes + 1];   // first flat hit index of each type's list
     __shared__ unsigned long long s_cur[kMaxTypes];         // PASS 0: count; PASS 1: cursor
