@@ -1069,29 +1069,57 @@ cudaError_t launch_wait_check(uint32_t *status, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------------------------------
-// Deferred plain-method pairs (low confidence, outliers, checked misses), one thread per pair
+// Deferred plain-method pairs (low confidence, outliers, checked misses), 1 to 32 lanes per pair
 // ---------------------------------------------------------------------------------------------------
-__global__ void k_fallback(Workspace ws, int mode)
+__global__ void __launch_bounds__(256) k_fallback(Workspace ws, int mode)
 {
     const DevFrame &f = *ws.frame;
     const unsigned long long n = ws.cnt->fb_count[mode];
     const uint2 *pairs = mode == 1 ? ws.spairs : ws.ppairs;
-    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < n;
-         e += (unsigned long long)gridDim.x * blockDim.x) {
+    // G lanes per pair: the largest power of two up to 32 that the launch's threads can give every
+    // pair.  A group takes G consecutive uniform samples at a time (the march_crossing sequence),
+    // finds the first one inside whose predecessor is outside by a ballot, then runs the same
+    // bisection: the result equals the serial march's for every G.  Few deferred pairs get many
+    // lanes each (latency hidden); many pairs get one (no lane repeats another's set-up).
+    const unsigned long long threads = (unsigned long long)gridDim.x * blockDim.x;
+    int G = 1;
+    while (G < 32 && n * (unsigned long long)(2 * G) <= threads) G *= 2;
+    const int lane = threadIdx.x & 31, sub = lane & (G - 1), gbase = lane & ~(G - 1);
+    const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << gbase;
+    const int steps = f.march_steps;
+    const unsigned long long groups = threads / (unsigned long long)G;
+    for (unsigned long long e = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) / (unsigned long long)G; e < n;
+         e += groups) {
         const uint2 pr = pairs[ws.fb_list[mode][e]];
         const DevType T = ws.types[ws.inst[pr.y].type];
         PairRay R;
         setup_pair_ray(ws, f, mode == 1, pr, T.rb, R);
-        bool hit = false;
-        const float Dl = march_crossing(T, R.ol, R.dl, R.te, R.tx, f.march_steps, f.march_bisect, hit);
-        if (hit) apply_hit(ws, f, mode == 1, R, Dl);
+        const float te = R.te, step = (R.tx - R.te) / (float)steps;
+        bool carry = inside_solid(T, madd(R.ol, te, R.dl));          // sample 0
+        int kc = 0;
+        for (int base = 1; base <= steps && kc == 0; base += G) {
+            const int k = base + sub;
+            const bool in = k <= steps && inside_solid(T, madd(R.ol, fmaf((float)k, step, te), R.dl));
+            bool prev = __shfl_up_sync(gmask, in, 1, G);
+            if (sub == 0) prev = carry;
+            const unsigned cross = (__ballot_sync(gmask, in && !prev) & gmask) >> gbase;
+            if (cross) kc = base + __ffs(cross) - 1;
+            carry = __shfl_sync(gmask, in, G - 1, G);
+        }
+        if (kc == 0) continue;                                    // no crossing: the pair stays a miss
+        float lo = kc == 1 ? te : fmaf((float)(kc - 1), step, te), hi = fmaf((float)kc, step, te);
+        for (int it = 0; it < f.march_bisect; ++it) {
+            const float mid = 0.5f * (lo + hi);
+            if (inside_solid(T, madd(R.ol, mid, R.dl))) hi = mid; else lo = mid;
+        }
+        if (sub == 0) apply_hit(ws, f, mode == 1, R, 0.5f * (lo + hi));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ws.cnt->fallback, n);
 }
 
 cudaError_t launch_fallback(const Workspace &ws, int mode, int num_sms, cudaStream_t st)
 {
-    k_fallback<<<num_sms * 8, 128, 0, st>>>(ws, mode);
+    k_fallback<<<num_sms * 8, 256, 0, st>>>(ws, mode);
     return cudaGetLastError();
 }
 
