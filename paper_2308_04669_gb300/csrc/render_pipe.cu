@@ -1069,50 +1069,68 @@ cudaError_t launch_wait_check(uint32_t *status, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------------------------------
-// Deferred plain-method pairs (low confidence, outliers, checked misses), 1 to 32 lanes per pair
+// Deferred plain-method pairs (low confidence, outliers, checked misses), G = 1 .. 32 lanes per pair
 // ---------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_fallback(Workspace ws, int mode)
 {
     const DevFrame &f = *ws.frame;
     const unsigned long long n = ws.cnt->fb_count[mode];
     const uint2 *pairs = mode == 1 ? ws.spairs : ws.ppairs;
-    // G lanes per pair: the largest power of two up to 32 that the launch's threads can give every
-    // pair.  A group takes G consecutive uniform samples at a time (the march_crossing sequence),
-    // finds the first one inside whose predecessor is outside by a ballot, then runs the same
-    // bisection: the result equals the serial march's for every G.  Few deferred pairs get many
-    // lanes each (latency hidden); many pairs get one (no lane repeats another's set-up).
+    // G lanes per pair: the largest power of two up to 32 such that every pair gets its lanes in
+    // one pass of the launch's threads.  Few deferred pairs get many lanes each (the march's
+    // dependent steps run G at a time); many pairs get few (no lane repeats another's set-up and
+    // bisection).  A warp holds 32 / G pairs and walks them in lockstep: the sample loop runs
+    // until every pair of the warp has its crossing or has passed the last sample, so every
+    // shuffle and ballot sees the whole warp.  A group takes G consecutive uniform samples per
+    // round (the march_crossing sequence), finds the first sample inside whose predecessor is
+    // outside, then runs the same bisection: the result equals the serial march's for every G.
     const unsigned long long threads = (unsigned long long)gridDim.x * blockDim.x;
     int G = 1;
     while (G < 32 && n * (unsigned long long)(2 * G) <= threads) G *= 2;
     const int lane = threadIdx.x & 31, sub = lane & (G - 1), gbase = lane & ~(G - 1);
-    const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << gbase;
+    const unsigned gbits = G == 32 ? 0xffffffffu : (1u << G) - 1u;
     const int steps = f.march_steps;
-    const unsigned long long groups = threads / (unsigned long long)G;
-    for (unsigned long long e = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) / (unsigned long long)G; e < n;
-         e += groups) {
-        const uint2 pr = pairs[ws.fb_list[mode][e]];
-        const DevType T = ws.types[ws.inst[pr.y].type];
+    const int P = 32 / G;                                            // pairs per warp
+    const unsigned long long warp_id = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long n_warps = threads >> 5;
+    for (unsigned long long e0 = warp_id * P; e0 < n; e0 += n_warps * P) {   // warp-uniform
+        const unsigned long long e = e0 + (unsigned long long)(lane / G);
+        const bool active = e < n;
         PairRay R;
-        setup_pair_ray(ws, f, mode == 1, pr, T.rb, R);
-        const float te = R.te, step = (R.tx - R.te) / (float)steps;
-        bool carry = inside_solid(T, madd(R.ol, te, R.dl));          // sample 0
+        DevType T;
+        float te = 0.0f, step = 0.0f;
+        bool carry = false;
+        if (active) {
+            const uint2 pr = pairs[ws.fb_list[mode][e]];
+            T = ws.types[ws.inst[pr.y].type];
+            setup_pair_ray(ws, f, mode == 1, pr, T.rb, R);
+            te = R.te;
+            step = (R.tx - R.te) / (float)steps;
+            carry = inside_solid(T, madd(R.ol, te, R.dl));           // sample 0
+        }
         int kc = 0;
-        for (int base = 1; base <= steps && kc == 0; base += G) {
+        bool done = !active;
+        for (int base = 1; base <= steps; base += G) {
             const int k = base + sub;
-            const bool in = k <= steps && inside_solid(T, madd(R.ol, fmaf((float)k, step, te), R.dl));
-            bool prev = __shfl_up_sync(gmask, in, 1, G);
+            const bool in = !done && k <= steps && inside_solid(T, madd(R.ol, fmaf((float)k, step, te), R.dl));
+            bool prev = __shfl_up_sync(0xffffffffu, in, 1, G);
             if (sub == 0) prev = carry;
-            const unsigned cross = (__ballot_sync(gmask, in && !prev) & gmask) >> gbase;
-            if (cross) kc = base + __ffs(cross) - 1;
-            carry = __shfl_sync(gmask, in, G - 1, G);
+            const unsigned cross = (__ballot_sync(0xffffffffu, in && !prev) >> gbase) & gbits;
+            if (!done && cross) {
+                kc = base + __ffs(cross) - 1;
+                done = true;
+            }
+            carry = __shfl_sync(0xffffffffu, in, G - 1, G);
+            if (__all_sync(0xffffffffu, done)) break;
         }
-        if (kc == 0) continue;                                    // no crossing: the pair stays a miss
-        float lo = kc == 1 ? te : fmaf((float)(kc - 1), step, te), hi = fmaf((float)kc, step, te);
-        for (int it = 0; it < f.march_bisect; ++it) {
-            const float mid = 0.5f * (lo + hi);
-            if (inside_solid(T, madd(R.ol, mid, R.dl))) hi = mid; else lo = mid;
+        if (kc != 0) {                                          // no crossing: the pair stays a miss
+            float lo = kc == 1 ? te : fmaf((float)(kc - 1), step, te), hi = fmaf((float)kc, step, te);
+            for (int it = 0; it < f.march_bisect; ++it) {
+                const float mid = 0.5f * (lo + hi);
+                if (inside_solid(T, madd(R.ol, mid, R.dl))) hi = mid; else lo = mid;
+            }
+            if (sub == 0) apply_hit(ws, f, mode == 1, R, 0.5f * (lo + hi));
         }
-        if (sub == 0) apply_hit(ws, f, mode == 1, R, 0.5f * (lo + hi));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ws.cnt->fallback, n);
 }

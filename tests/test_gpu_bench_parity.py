@@ -66,9 +66,10 @@ def test_thousand_instance_frame_matches_oracle(orc, prec):
     g, w = trained_frame(sc, precision, 600, **FRAME_OPTS, **GPU_MARCH)
     assert g["stats"].status == 0 and g["stats"].primary_pairs > 1_500_000 and g["stats"].fallback_pairs > 0
     # E4M3: one flipped activation moves m by up to ~5e-2, as much as the depth check's half window
-    # h, so the window decisions of many refined pairs are knife edges; more pixels keep > 2,500
-    # decided
-    px = sg.pixel_subset(sc.W, sc.H, 2500 if prec == "bf16" else 5000, 7)
+    # h, so the window decisions of many refined pairs are knife edges (about a third of the
+    # pixels), and most shadow tests sit inside their decision margin; four times the pixels keep
+    # enough of both decided
+    px = sg.pixel_subset(sc.W, sc.H, 2500 if prec == "bf16" else 10000, 7)
     kw = {} if prec == "bf16" else dict(colour_tol=FP8_COLOUR_TOL)
     rep, o = frame_vs_oracle(g, orc.OracleScene(sc, nedf_override=w), px=px, quant=quant, n_threads=16,
                              max_excluded=0.1 if prec == "bf16" else 0.45, **FRAME_OPTS, **ORC_MARCH, **kw)
