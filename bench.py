@@ -35,11 +35,11 @@ METRIC = "composited rays/s & ms/frame at 1024², NeDF vs ray-march, same GPU, d
 WORKLOAD = ("1024 instances (sphere/torus/box, seed 3, T in [-20,20]^3) at 1024x1024, 4 point lights, "
             "NeDF 6x128 per type trained on ray-march labels, NeRF 8x256 per type, 8 shading samples, "
             "fallback below confidence 0.9, 4 refinement steps with outlier re-answering, confident misses "
-            "checked at 16 chord samples")
+            "checked at {mc} chord samples, plain-method re-answers at the labels' 256 steps + 8 bisections")
 WORKLOAD_STRESS = ("4096 instances (8 shape types x 512, seed 4, T in [-40,40]^3) at 2048x2048, 8 point lights, "
                    "NeDF 6x128 per type trained on ray-march labels, NeRF 8x256 per type, 8 shading samples, "
                    "fallback below confidence 0.9, 4 refinement steps with outlier re-answering, confident misses "
-                   "checked at 32 chord samples, plain-method re-answers at the labels' 256 steps + 8 bisections")
+                   "checked at {mc} chord samples, plain-method re-answers at the labels' 256 steps + 8 bisections")
 # the frame's options (the C ABI's nedf_options) and the same options in the oracle's names
 FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=32, march_steps=256,
                   march_bisect=8)
@@ -213,7 +213,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_frame, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORLOAD_REF, "sample_px_per_step": n},
+            "config": {"workload": WORKLOAD.format(mc=args.miss_check), "W": sc.W, "H": sc.H,
+                       "instances": sc.n_inst, "lights": len(sc.lights), "sample_px_per_step": n,
+                       "oracle": "FP64, same scene, options and trained NeDF weights"},
             "cpu_baseline": {"value": value, "unit": "rays/s", "cores": threads, "kind": "oracle",
                              "sample": f"{n} seeded pixels of the 1024x1024 frame per step, all 1024 instances, "
                                        + ("the trained NeDF weights of the bench's schedule" if w_ref else
@@ -223,7 +225,6 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-WORLOAD_REF = WORKLOAD.replace("trained on ray-march labels", "trained on ray-march labels (oracle: FP64, same scene and weights)")
 
 
 def reference_weights(sc):
@@ -351,7 +352,7 @@ def run_ours(args):
     from paper_2308_04669_gb300 import scenegen as sg
 
     sc = sg.thousand_scene() if args.scene == "thousand" else sg.stress_scene()
-    workload = WORKLOAD if args.scene == "thousand" else WORKLOAD_STRESS
+    workload = WORKLOAD.format(mc=args.miss_check) if args.scene == "thousand" else WORKLOAD_STRESS
     n_li = len(sc.lights)
     stream = torch.cuda.Stream()            # a non-default stream: frames are CUDA-graph captured
     torch.cuda.set_stream(stream)
@@ -691,6 +692,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=20000, help="Adam steps per type (the workload's 20k)")
     ap.add_argument("--train-batch", type=int, default=65536)
     ap.add_argument("--label-rays", type=int, default=1 << 22, help="plain-method labelled rays per type (2^22)")
+    ap.add_argument("--miss-check", type=int, default=32, help="chord samples that verify a confident NeDF miss")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
@@ -710,6 +712,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    FRAME_OPTS["miss_check"] = ORACLE_OPTS["miss_check"] = args.miss_check
     if args.impl == "reference":
         run_reference(args)
     else:

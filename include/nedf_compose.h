@@ -331,7 +331,10 @@ int nedf_compose_check_wait_limit(nedf_handle *h);
  * reads.  The NeDF engine at BF16 width 128 can also run its layers with either operand order:
  * swapped (the weight chunk as A, 128 output features x the tile's 256 rows, one MMA per chunk)
  * or unswapped (each 128-row half of the tile as A, the weight chunk as B, two MMAs per chunk).
- * Neither choice changes results, only timing.  Kernel index k of the arrays below:
+ * The NeRF kernels at width 256 can also run on SM pairs (operand order 1: clusters of two CTAs
+ * whose MMAs span both SMs, M = 256 rows), whose colours differ from the one-SM engine's only by
+ * the FP32 order of the output layer's sum.  The stage size and the NeDF operand order change
+ * timing, not results.  Kernel index k of the arrays below:
  * 0 Step-2 shading, 1 plain-method colour rows, 2 Step-1 NeDF, 3 Step-3 NeDF, 4 NeDF query. */
 #define NEDF_N_SCHEDULE 5
 typedef struct {
@@ -341,7 +344,9 @@ typedef struct {
     float tuned_ms[NEDF_N_SCHEDULE];   /* set by nedf_compose_autotune: the chosen schedule's best
                                           time for kernels 0, 2 and 3 (0 elsewhere)                */
     int operand_order[NEDF_N_SCHEDULE];/* NeDF kernels 2-4 at BF16 width 128: 0 = default
-                                          (swapped), 1 = swapped, 2 = unswapped; ignored elsewhere */
+                                          (swapped), 1 = swapped, 2 = unswapped; NeRF kernels 0-1
+                                          at width 256: 0 = default (one SM), 1 = SM pair, 2 = one
+                                          SM; ignored elsewhere                                    */
 } nedf_schedule;
 
 /* Replaces the schedule (host struct, copied).  stage_bytes must be 0 or a multiple of 1024 in

@@ -76,7 +76,7 @@ struct nedf_handle {
     uint32_t *d_lg_big = nullptr, *d_lg_big_count = nullptr, *d_scan_tmp = nullptr;
     unsigned long long *d_sblk = nullptr, *d_pinst = nullptr;
     long long lg_cap = 0;
-    size_t nedf_tc_stride = 0, nerf_tc_stride = 0;
+    size_t nedf_tc_stride = 0, nerf_tc_stride = 0, nerf_pair_off = 0;
     void *d_march_scratch = nullptr;
     size_t march_scratch_bytes = 0;
     uint32_t *d_rs_mask = nullptr;
@@ -227,6 +227,7 @@ static Workspace make_ws(nedf_handle *h)
     for (int k = 0; k < NEDF_N_SCHEDULE; ++k) ws.pipe_order[k] = h->operand_order[k];
     ws.nerf_tc = h->d_nerf_tc;
     ws.nerf_tc_stride = h->nerf_tc_stride;
+    ws.nerf_pair_off = h->nerf_pair_off;
     ws.fb_list[0] = h->d_fb[0];
     ws.fb_list[1] = h->d_fb[1];
     ws.lcam = h->d_lcam;
@@ -372,7 +373,9 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
                                                                 : pipe_blob_size(kNedfInPad, c.nedf_width, c.nedf_hidden, 2, f8);
         CA(h->d_nedf_tc, h->nedf_tc_stride * c.max_types);
         if (c.nerf_hidden > 0) {
-            h->nerf_tc_stride = pipe_blob_size(kNerfInPad, c.nerf_width, c.nerf_hidden, 3, f8);
+            // width 256: each type's blob holds the one-SM layout, then the SM-pair layout
+            h->nerf_pair_off = c.nerf_width == 256 ? pipe_blob_size(kNerfInPad, c.nerf_width, c.nerf_hidden, 3, f8) : 0;
+            h->nerf_tc_stride = pipe_blob_size(kNerfInPad, c.nerf_width, c.nerf_hidden, 3, f8) + h->nerf_pair_off;
             CA(h->d_nerf_tc, h->nerf_tc_stride * c.max_types);
         }
     }
@@ -485,7 +488,7 @@ static cudaError_t pack_nedf(nedf_handle *h, const float *master, uint8_t *blob)
         return h->cfg.precision == NEDF_PREC_FP32 ? launch_pack_cls_f32(master, blob, h->stream)
                                                   : launch_pack_cls(master, blob, h->stream);
     return launch_pack_pipe(master, blob, kNedfIn, kNedfInPad, h->cfg.nedf_width, h->cfg.nedf_hidden, 2,
-                            h->cfg.precision == NEDF_PREC_FP8, h->stream);
+                            h->cfg.precision == NEDF_PREC_FP8, false, h->stream);
 }
 
 int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *types)
@@ -550,7 +553,12 @@ int nedf_compose_set_types(nedf_handle *h, int n_types, const nedf_type_desc *ty
                                        cudaMemcpyHostToDevice);
             if (e == cudaSuccess)
                 e = launch_pack_pipe(tmp, h->d_nerf_tc + (size_t)k * h->nerf_tc_stride, kNerfIn, kNerfInPad,
-                                   h->cfg.nerf_width, h->cfg.nerf_hidden, 3, h->cfg.precision == NEDF_PREC_FP8, h->stream);
+                                   h->cfg.nerf_width, h->cfg.nerf_hidden, 3, h->cfg.precision == NEDF_PREC_FP8, false,
+                                   h->stream);
+            if (e == cudaSuccess && h->nerf_pair_off)
+                e = launch_pack_pipe(tmp, h->d_nerf_tc + (size_t)k * h->nerf_tc_stride + h->nerf_pair_off, kNerfIn,
+                                     kNerfInPad, h->cfg.nerf_width, h->cfg.nerf_hidden, 3,
+                                     h->cfg.precision == NEDF_PREC_FP8, true, h->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
             if (e != cudaSuccess) {
                 cudaFree(tmp);
@@ -1058,7 +1066,7 @@ int nedf_compose_autotune(nedf_handle *h, const nedf_camera *cam, const nedf_lig
         if (r != NEDF_OK) return r;
         for (int o = 0; o < n_order; ++o) {
             const int order = orders ? 1 + o : 0;
-            for (int k = 0; k < NEDF_N_SCHEDULE; ++k) h->operand_order[k] = order;
+            for (int k = 2; k < NEDF_N_SCHEDULE; ++k) h->operand_order[k] = order;
             for (int c = 0; c < n_cand; ++c) {
                 for (int k = 0; k < NEDF_N_SCHEDULE; ++k) h->stage_bytes[k] = cand[c];
                 drop_graph(h);
@@ -1085,7 +1093,6 @@ int nedf_compose_autotune(nedf_handle *h, const nedf_camera *cam, const nedf_lig
         h->stage_bytes[2] = pick[1];
         h->stage_bytes[3] = pick[2];
         h->stage_bytes[4] = pick[1];
-        for (int k = 0; k < NEDF_N_SCHEDULE; ++k) h->operand_order[k] = 0;
         h->operand_order[2] = pick_order[1];
         h->operand_order[3] = pick_order[2];
         h->operand_order[4] = pick_order[1];

@@ -178,6 +178,20 @@ __device__ __forceinline__ float sdf_eval(const DevType &t, V3 x)
 // Inside the solid <=> density >= sigma_max / 2 <=> sdf <= 0 (sigmoid(0) = 1/2).
 __device__ __forceinline__ bool inside_solid(const DevType &t, V3 x) { return sdf_eval(t, x) <= 0.0f; }
 
+// A Lipschitz bound of sdf_eval inside the bound sphere (|x| <= rb): the exact distances (sphere,
+// torus, box, capsule, rounded cone), their minimum (two-sphere union) and the octahedron's lower
+// bound have gradients of length <= 1; the twist by angle k y about the y axis stretches distances
+// by at most sqrt(1 + (k rho)^2) <= 1 + |k| rb (rho: distance to the axis).
+__device__ __forceinline__ float sdf_lipschitz(const DevType &t)
+{
+    return t.kind == 6 ? 1.0f + fabsf(t.p[2]) * t.rb : 1.0f;
+}
+
+// Samples within (|sdf(x)| - kSkipMargin) / Lipschitz of x along the ray lie on x's side of the
+// surface.  The margin (local units) covers the FP32 error of the sample positions and of the SDF,
+// so a skipped sample's own inside test could not have come out the other way.
+constexpr float kSkipMargin = 1e-3f;
+
 __device__ __forceinline__ float density(const DevType &t, V3 x, float sigma_max, float w)
 {
     return sigma_max / (1.0f + expf(sdf_eval(t, x) / w));
@@ -207,6 +221,41 @@ __device__ __forceinline__ float march_crossing(const DevType &t, V3 ol, V3 dl, 
         }
         prev_in = in;
         prev_t = tk;
+    }
+    hit = false;
+    return __int_as_float(0x7f800000);
+}
+
+// march_crossing with the samples that the SDF proves to lie on the side of the last evaluated one
+// skipped: the same first outside -> inside sample k, the same bracket [t_{k-1}, t_k] and the same
+// bisection, so the same result, with a few SDF evaluations where a ray passes far from the surface
+// instead of `steps`.
+__device__ __forceinline__ float march_crossing_skip(const DevType &t, V3 ol, V3 dl, float te, float tx,
+                                                     int steps, int bisect, bool &hit)
+{
+    const float step = (tx - te) / (float)steps;
+    const float inv = 1.0f / (step * sdf_lipschitz(t));
+    float sd = sdf_eval(t, madd(ol, te, dl));
+    bool prev_in = sd <= 0.0f;
+    int k = 0;
+    while (true) {
+        const float room = (fabsf(sd) - kSkipMargin) * inv;      // samples k+1 .. k+m keep k's side
+        const int m = room > 0.0f ? (int)fminf(room, (float)steps) : 0;
+        k += m + 1;
+        if (k > steps) break;
+        const float tk = fmaf((float)k, step, te);
+        sd = sdf_eval(t, madd(ol, tk, dl));
+        const bool in = sd <= 0.0f;
+        if (in && !prev_in) {
+            float lo = fmaf((float)(k - 1), step, te), hi = tk;
+            for (int it = 0; it < bisect; ++it) {
+                float mid = 0.5f * (lo + hi);
+                if (inside_solid(t, madd(ol, mid, dl))) hi = mid; else lo = mid;
+            }
+            hit = true;
+            return 0.5f * (lo + hi);
+        }
+        prev_in = in;
     }
     hit = false;
     return __int_as_float(0x7f800000);
@@ -246,9 +295,18 @@ __device__ __forceinline__ bool nedf_decode(const DevFrame &f, const DevType &T,
     if (!march && !hit && f.miss_check > 0) {
         Chord ch;
         if (bound_chord(ol, dl, T.rb, ch)) {
+            // the midpoints in order; samples the SDF proves outside are skipped (same answer)
             const float step = (ch.tx - ch.te) / (float)f.miss_check;
-            for (int j = 0; j < f.miss_check && !march; ++j)
-                march = inside_solid(T, madd(ol, ch.te + ((float)j + 0.5f) * step, dl));
+            const float inv = 1.0f / (step * sdf_lipschitz(T));
+            for (int j = 0; j < f.miss_check;) {
+                const float sd = sdf_eval(T, madd(ol, ch.te + ((float)j + 0.5f) * step, dl));
+                if (sd <= 0.0f) {
+                    march = true;
+                    break;
+                }
+                const float room = (sd - kSkipMargin) * inv;
+                j += 1 + (room > 0.0f ? (int)fminf(room, (float)f.miss_check) : 0);
+            }
         }
     }
     if (!march && hit && f.refine_steps > 0) {

@@ -305,10 +305,10 @@ __global__ void __launch_bounds__(kThreads) k_nedf_tiles(Workspace ws, int shado
             float Dl;
             bool hit;
             if (use_march) {
-                Dl = march_crossing(T, ol, dl, ri.te, ri.tx, f.march_steps, f.march_bisect, hit);
+                Dl = march_crossing_skip(T, ol, dl, ri.te, ri.tx, f.march_steps, f.march_bisect, hit);
             } else {
                 if (nedf_decode(f, T, ol, dl, ri.tp, y[threadIdx.x][0], y[threadIdx.x][1], Dl, hit)) {
-                    Dl = march_crossing(T, ol, dl, ri.te, ri.tx, f.march_steps, f.march_bisect, hit);
+                    Dl = march_crossing_skip(T, ol, dl, ri.te, ri.tx, f.march_steps, f.march_bisect, hit);
                     atomicAdd(&ws.cnt->fallback, 1ull);
                 }
             }

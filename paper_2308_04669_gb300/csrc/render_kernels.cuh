@@ -90,6 +90,7 @@ struct Workspace {
     size_t nedf_tc_stride;
     const uint8_t *nerf_tc;
     size_t nerf_tc_stride;
+    size_t nerf_pair_off;        // width 256: offset of the SM-pair layout inside each type's blob (0: none)
     // pairs deferred to the plain method by the tensor-core NeDF kernels (indices into the lists)
     uint32_t *fb_list[2];
     // shadow-map cameras: per light a G x G grid of direction cells with instance lists
@@ -114,7 +115,8 @@ struct Workspace {
     // primary NeDF, shadow NeDF, NeDF query); picked by the autotuner or set by the caller
     int pipe_stage_bytes[5];
     // operand order of the NeDF engines at BF16 width 128 (same kernel index): 0 default, 1 swapped
-    // (weights as A, D^T = W H^T), 2 unswapped (activations as A); results do not depend on it
+    // (weights as A, D^T = W H^T), 2 unswapped (activations as A); results do not depend on it.
+    // NeRF kernels (0, 1) at width 256: 1 the SM-pair engine, 0 (default) and 2 the one-SM engine
     int pipe_order[5];
 };
 

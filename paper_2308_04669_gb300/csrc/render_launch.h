@@ -31,12 +31,18 @@ cudaError_t launch_frame(FrameLaunch &L);
 // hidden layers after the first in E4M3 with per-layer scales
 constexpr int kPipeTileRows = 256;
 size_t pipe_blob_size(int K0, int N, int L, int n_out, bool f8);
+// pair: the SM-pair engine's layout (width 256 only; see k_pack_pipe)
 cudaError_t launch_pack_pipe(const float *master, void *blob, int K_in, int K0, int N, int L, int n_out, bool f8,
-                             cudaStream_t st);
+                             bool pair, cudaStream_t st);
 // mode 0: Step-1 pairs, 1: Step-3 pairs, 2: n caller rays (o, d) of `type` -> out float4[n]
 cudaError_t launch_nedf_pipe(const Workspace &ws, int mode, int type, const float *o, const float *d, float *out,
                              int n, int num_sms, cudaStream_t st);
 cudaError_t launch_shade_pipe(const Workspace &ws, int npix, int num_sms, cudaStream_t st);
+// The SM-pair NeRF engine (render_pair.cu), width 256: mode kModeShade or kModeMarch (pipe_common.cuh);
+// cudaErrorInvalidConfiguration (nothing launched) when its shape does not fit
+struct PipeArgs;
+cudaError_t launch_pair_pipe(const Workspace &ws, const MarchBuffers &mb, const PipeArgs &a, int mode, int num_sms,
+                             cudaStream_t st);
 // The paper's classifier intersection network (render_cls.cu): packed FP32 master weights (head
 // 1008 -> 256, 16 residual blocks, tails 256 -> 65 and 256 -> 128) -> per-type BF16 blob; the
 // engine in the same three modes as launch_nedf_pipe, writing the same (m, a) outputs

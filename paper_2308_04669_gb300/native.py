@@ -325,7 +325,9 @@ class Renderer:
         return self._check(_lib.nedf_compose_check_wait_limit(self.h))
 
     def set_schedule(self, stage_bytes, operand_order=None):
-        """stage_bytes (and operand_order: 0 default, 1 swapped, 2 unswapped) per kernel index."""
+        """stage_bytes and operand_order per kernel index (NeDF kernels: 0 default, 1 swapped, 2
+        unswapped; NeRF kernels at width 256: 1 the SM-pair engine, 0 default and 2 the one-SM
+        engine)."""
         s = Schedule()
         for k, b in enumerate(stage_bytes):
             s.stage_bytes[k] = int(b)
@@ -346,12 +348,18 @@ class Renderer:
     def autotune(self, cam, lights, reps=3) -> dict:
         """Picks the stage size of every tensor-core kernel (and the NeDF engines' operand order at
         BF16 width 128) by timing this frame; returns {kernel: {"stage_bytes": b, "operand_order":
-        "swapped" | "unswapped" | "fixed", "ms": best time (0 if not timed)}}."""
+        "swapped" | "unswapped" | "fixed" | "sm_pair" | "one_sm", "ms": best time (0 if not
+        timed)}}.  The NeRF kernels keep the engine they were set to."""
         s = Schedule()
         la, nl = lights
         self._check(_lib.nedf_compose_autotune(self.h, C.byref(cam), la, nl, reps, C.byref(s)))
         names = {0: "fixed", 1: "swapped", 2: "unswapped"}
-        return {k: {"stage_bytes": s.stage_bytes[i], "operand_order": names[s.operand_order[i]],
+        nerf = {0: "one_sm", 1: "sm_pair", 2: "one_sm"} if self.cfg.nerf_width == 256 and \
+            self.cfg.precision != PREC_FP32 else None
+
+        def order(i):
+            return nerf[s.operand_order[i]] if nerf and i < 2 else names[s.operand_order[i]]
+        return {k: {"stage_bytes": s.stage_bytes[i], "operand_order": order(i),
                     "ms": round(float(s.tuned_ms[i]), 4)} for i, k in enumerate(SCHEDULE_KERNELS)}
 
     def nedf_query(self, type_, o, d, out):

@@ -163,7 +163,7 @@ def test_every_stage_size_on_a_large_frame(prec):
     # the NeDF engines' operand order (BF16 width 128: swapped or unswapped; ignored in E4M3)
     for order in (1, 2):
         for b in (8192, 36864):
-            r.set_schedule([b] * native.N_SCHEDULE, [order] * native.N_SCHEDULE)
+            r.set_schedule([b] * native.N_SCHEDULE, [0, 0, order, order, order])
             got = frame()
             assert all(np.array_equal(x, y) for x, y in zip(ref, got)), (order, b)
     r.close()
@@ -206,3 +206,48 @@ def test_schedule_changes_timing_not_results():
         with pytest.raises(native.NedfError):
             r.set_schedule([1000] * native.N_SCHEDULE)
         r.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_sm_pair_engine_matches_one_sm_engine(prec):
+    """The NeRF at width 256 runs on SM pairs (tcgen05 MMAs of cta_group::2, M = 256 across two
+    SMs) with operand order 1 of the shading and plain-method kernels, on one SM by default (0)
+    and with order 2.  On the 1024-instance scene (every SM pair walks many tiles of both slots and every
+    type) at every stage size: depth and id bitwise equal, colours element-wise within 2e-6 (the
+    two engines fold the last layer's two column halves in a different FP32 order), the
+    plain-method colour frame likewise, and clean status words."""
+    import torch
+    from paper_2308_04669_gb300 import native
+    sc = sg.thousand_scene(512, 512)
+    r = native.renderer_for(sc, precision=native.PREC_BF16 if prec == "bf16" else native.PREC_FP8)
+    cam, li = r.camera(sc.eye, sc.target, sc.fov_deg), r.lights(sc.lights)
+    n = sc.W * sc.H
+
+    def frame():
+        d = torch.empty(n, device="cuda"); i = torch.empty(n, dtype=torch.int32, device="cuda")
+        c = torch.empty(n, 4, device="cuda")
+        st = r.render(cam, li, d, i, c, None, None, stats=True)
+        torch.cuda.synchronize()
+        assert st.status == 0 and st.hit_pixels > 10000
+        return d.cpu().numpy(), i.cpu().numpy(), c.cpu().numpy().astype(np.float64)
+
+    def march():
+        c = torch.empty(n, 4, device="cuda")
+        r.render_march(cam, 64, 0, c)
+        torch.cuda.synchronize()
+        return c.cpu().numpy().astype(np.float64)
+
+    r.set_schedule([0] * native.N_SCHEDULE, [2, 2, 0, 0, 0])
+    one_sm, one_sm_march = frame(), march()
+    for b in (4096, 8192, 12288, 24576, 36864, 65536):
+        r.set_schedule([b] * native.N_SCHEDULE, [1, 1, 0, 0, 0])
+        got = frame()
+        assert np.array_equal(got[0], one_sm[0]) and np.array_equal(got[1], one_sm[1]), b
+        err = np.abs(got[2] - one_sm[2]).max()
+        print(f"{prec} stage {b}: max |pair - one SM| colour {err:.2e}")
+        assert err <= 2e-6, (b, err)
+    got_march = march()
+    err = np.abs(got_march - one_sm_march).max()
+    print(f"{prec} plain-method colour: max |pair - one SM| {err:.2e}")
+    assert (one_sm_march[:, 3] > 0.1).sum() > 10000 and err <= 2e-6
+    r.close()
