@@ -75,7 +75,8 @@ struct nedf_handle {
     uint32_t *d_lg_count = nullptr, *d_lg_off = nullptr, *d_lg_cursor = nullptr, *d_lg_items = nullptr;
     uint32_t *d_lg_big = nullptr, *d_lg_big_count = nullptr, *d_scan_tmp = nullptr;
     unsigned long long *d_sblk = nullptr, *d_pinst = nullptr;
-    long long lg_cap = 0;
+    uint32_t *d_smask = nullptr;
+    long long lg_cap = 0, smask_cap = 0;
     size_t nedf_tc_stride = 0, nerf_tc_stride = 0, nerf_pair_off = 0;
     void *d_march_scratch = nullptr;
     size_t march_scratch_bytes = 0;
@@ -242,6 +243,8 @@ static Workspace make_ws(nedf_handle *h)
     ws.max_inst = h->cfg.max_instances;
     ws.scan_tmp = h->d_scan_tmp;
     ws.sblk = h->d_sblk;
+    ws.smask = h->d_smask;
+    ws.smask_cap = h->smask_cap;
     ws.pinst = h->d_pinst;
     ws.sblk_nb = shadow_bin_blocks(h->num_sms);
     return ws;
@@ -362,6 +365,10 @@ int nedf_compose_create(const nedf_config *cfg, void *cuda_stream, nedf_handle *
         CA(h->d_scan_tmp, sizeof(uint32_t) * 1024);
         CA(h->d_sblk, sizeof(unsigned long long) * kMaxTypes * (shadow_bin_blocks(h->num_sms) + 1));
         CA(h->d_pinst, sizeof(unsigned long long) * 2 * c.max_instances);
+        // shadow rays' kept-candidate masks (count pass -> fill pass), for up to 8 lights per pixel;
+        // frames with more shadow rays fill without them
+        h->smask_cap = (npix + 32) * 8;
+        CA(h->d_smask, sizeof(uint32_t) * h->smask_cap);
     }
     if (c.precision == NEDF_PREC_FP32 && c.nedf_arch == NEDF_ARCH_CLASSIFIER) {
         h->nedf_tc_stride = cls_f32_blob_size();          // the CUDA-core classifier's FP32 weights
@@ -397,7 +404,7 @@ void nedf_compose_destroy(nedf_handle *h)
                    h->d_ppairs, h->d_spairs, h->d_pgeo, h->d_sgeo, h->d_sell, h->d_nout[0], h->d_nout[1], h->d_rs_mask, h->d_rs_pairs, h->d_rs_cnt, h->d_rs_scratch, h->d_edit_keys, h->d_edit_rgba, h->d_edit_occl, h->d_cnt, h->d_status, h->d_loss, h->d_train_scratch,
                    h->d_march_scratch, h->d_nedf_tc, h->d_nerf_tc, h->d_fb[0], h->d_fb[1], h->d_lcam,
                    h->d_lg_count, h->d_lg_off, h->d_lg_cursor, h->d_lg_items, h->d_lg_big,
-                   h->d_lg_big_count, h->d_scan_tmp, h->d_sblk, h->d_pinst};
+                   h->d_lg_big_count, h->d_scan_tmp, h->d_sblk, h->d_pinst, h->d_smask};
     for (void *p : dev)
         if (p) cudaFree(p);
     for (TrainState &t : h->train) {

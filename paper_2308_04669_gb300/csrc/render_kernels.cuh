@@ -108,6 +108,10 @@ struct Workspace {
     // shadow-ray binning: per type t and block b of the binning grid, the block's pair count (count
     // pass), then the first index of its range ([t][nb] = the end of the type's grid pairs)
     unsigned long long *sblk;    // [kMaxTypes][sblk_nb + 1]
+    // shadow-ray binning: per shadow ray (of at most 32 candidates) the candidates the count pass
+    // kept, bit k = candidate k, so the fill pass tests only those
+    uint32_t *smask;
+    long long smask_cap;
     // primary binning: per instance its pair count (count pass) and the first index of its range
     unsigned long long *pinst;   // [max_instances][2]
     int sblk_nb;                 // blocks of the shadow-ray binning grid

@@ -338,13 +338,25 @@ __global__ void __launch_bounds__(256, 6) k_bin_shadow_grid(Workspace ws, int np
                 count = n_inst;
             }
         }
-        const int maxc = __reduce_max_sync(0xffffffffu, count);
-        for (int k = 0; k < maxc; ++k) {
+        // the fill pass walks only the candidates the count pass kept (their bits in the ray's
+        // mask, lowest first), re-testing each exactly as the count pass did; rays of more than 32
+        // candidates (or frames beyond the mask buffer) walk all of them again
+        const bool masked = PASS == 1 && count <= 32 && n_rays <= ws.smask_cap;
+        uint32_t kmask = masked && valid ? ws.smask[rr] : 0u;
+        const int items = masked ? __popc(kmask) : count;
+        const int maxc = __reduce_max_sync(0xffffffffu, items);
+        uint32_t kept_bits = 0u;
+        for (int j = 0; j < maxc; ++j) {
             bool keep = false;
             uint32_t inst = 0, ty = 0;
             V3 ol = v3(0, 0, 0), dl = v3(0, 0, 0);
             Chord ch{};
-            if (k < count) {
+            int k = j;
+            if (masked && j < items) {
+                k = __ffs(kmask) - 1;
+                kmask &= kmask - 1u;
+            }
+            if (j < items) {
                 inst = grid ? (k < nc ? ws.lg_items[c0 + k] : ws.lg_big[(size_t)l * ws.max_inst + (k - nc)]) : (uint32_t)k;
                 DevInst I = ws.inst[inst];
                 ty = I.type;
@@ -352,6 +364,7 @@ __global__ void __launch_bounds__(256, 6) k_bin_shadow_grid(Workspace ws, int np
                 keep = bound_chord(ol, dl, ws.types[ty].rb, ch) && (ch.te * I.s < ell) &&
                        !(f.edit_mode == 1 && inst == (uint32_t)f.edit_inst);
             }
+            if (PASS == 0 && keep && k < 32) kept_bits |= 1u << k;
             const unsigned active = __ballot_sync(0xffffffffu, keep);
             if (!keep) continue;
             const unsigned peers = __match_any_sync(active, ty);
@@ -375,6 +388,7 @@ __global__ void __launch_bounds__(256, 6) k_bin_shadow_grid(Workspace ws, int np
                 atomicOr(ws.status, kStatusShadowOverflow);    // the list's capacity (or a count/fill mismatch)
             }
         }
+        if (PASS == 0 && valid && count <= 32 && n_rays <= ws.smask_cap) ws.smask[rr] = kept_bits;
     }
     __syncthreads();
     if (threadIdx.x < n_types) {
