@@ -41,9 +41,9 @@ WORKLOAD_STRESS = ("4096 instances (8 shape types x 512, seed 4, T in [-40,40]^3
                    "fallback below confidence 0.9, 4 refinement steps with outlier re-answering, confident misses "
                    "checked at {mc} chord samples, plain-method re-answers at the labels' 256 steps + 8 bisections")
 # the frame's options (the C ABI's nedf_options) and the same options in the oracle's names
-FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=32, march_steps=256,
+FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=64, march_steps=256,
                   march_bisect=8)
-ORACLE_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=32, march_n=256, march_b=8)
+ORACLE_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=64, march_n=256, march_b=8)
 NEDF_FLOP = 2 * (78 * 128 + 5 * 128 * 128 + 128 * 2)          # per query, unpadded
 # one training ray of the 6 x 128 NeDF: the forward pass, the input gradients of the hidden layers
 # (5 x 128 x 128) and of the output layer (2 x 128), and every weight gradient (as the forward)
@@ -279,6 +279,71 @@ def train_types(r, scene, steps, batch, n_rays, log, stream, peak_tflops):
                     "weights_sha256": hashlib.sha256(w.astype(np.float32).tobytes()).hexdigest()}
 
 
+def fp8_frame(sc, r, stream, jdepth, jids, peak_bf16, args, frames=20):
+    """The same frame with every hidden layer but the first in E4M3 (per-layer scales), rendered
+    with the trained weights of `r` (BF16 training) and the same options: frame time, stages, the
+    engines against the FP8 peak, and the all-pixel depth error against the same judge."""
+    import copy
+    import torch
+    from paper_2308_04669_gb300 import native
+    n = sc.W * sc.H
+    w_tr = [r.get_nedf_weights(t, sc.types[t].nedf_w.shape[0]) for t in range(len(sc.types))]
+    sc8 = copy.copy(sc)
+    sc8.types = [copy.copy(t) for t in sc.types]
+    for t, w in zip(sc8.types, w_tr):
+        t.nedf_w = w
+    r8 = native.renderer_for(sc8, precision=native.PREC_FP8, stream=stream)
+    o8 = r8.get_options()
+    for k, v in FRAME_OPTS.items():
+        setattr(o8, k, v)
+    r8.set_options(o8)
+    cam, lights = r8.camera(sc.eye, sc.target, sc.fov_deg), r8.lights(sc.lights)
+    sched = r8.autotune(cam, lights, reps=2) if not args.no_autotune else None
+    depth = torch.empty(n, device="cuda")
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    out = torch.empty(n, 4, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    r8.set_profiling(True)
+    for _ in range(3):
+        r8.render(cam, lights, depth, ids, None, None, out)
+    st = r8.render(cam, lights, depth, ids, None, None, out, stats=True)
+    torch.cuda.synchronize()
+    tot, stages, engines = 0.0, {}, {}
+    for _ in range(frames):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r8.render(cam, lights, depth, ids, None, None, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+        for k, v in r8.stage_times().items():
+            stages[k] = stages.get(k, 0.0) + v / frames
+        for k, v in r8.engine_times().items():
+            engines[k] = engines.get(k, 0.0) + v / frames
+    ms = tot / frames
+    both = (ids != -1) & (jids != -1)
+    err = (depth.double() - jdepth.double()).abs()[both]
+    peak8 = 2.0 * peak_bf16
+    eng = {}
+    for k, pairs in (("step1_nedf", st.primary_pairs), ("step3_nedf", st.shadow_pairs)):
+        if engines.get(k, 0) > 0:
+            tf = pairs * NEDF_FLOP / (engines[k] * 1e-3) / 1e12
+            eng[k] = {"engine_ms": round(engines[k], 4), "engine_tflops": round(tf, 1), "engine_frac_fp8": round(tf / peak8, 3)}
+    shade_tf = st.hit_pixels * 8 * NERF_FLOP / (stages["step2_shade"] * 1e-3) / 1e12
+    r8.close()
+    return {"ms_per_frame": ms, "rays_per_s": n / (ms * 1e-3),
+            "stage_ms": {k: round(v, 4) for k, v in stages.items()}, "engines": eng,
+            "step2_shade": {"tflops": round(shade_tf, 1), "frac_fp8": round(shade_tf / peak8, 3)},
+            "fallback_pairs": st.fallback_pairs,
+            "depth_err": {"mean_over_rb": float(err.mean()), "p99_over_rb": float(torch.quantile(err.float(), 0.99)),
+                          "id_agreement": float((ids == jids)[both].double().mean()),
+                          "pixels_both_hit": int(both.sum())},
+            "schedule": sched,
+            "peak_basis": "fp8 dense = bf16 dense measured (burst) x 2 (nominal 4.5 / 2.25 PFLOP/s)",
+            "note": "hidden layers after the first in E4M3 with per-layer scales, FP32 accumulation; the BF16 frame's trained weights and options; same judge"}
+
+
 def classifier_frame(sc, stream, cam, lights, args, frames=5):
     """The workload's instances, lights and NeRF colour networks with every type's NeDF replaced
     by the paper's classifier network (seeded weights): frame time and the NeDF engines alone."""
@@ -352,7 +417,7 @@ def run_ours(args):
     from paper_2308_04669_gb300 import scenegen as sg
 
     sc = sg.thousand_scene() if args.scene == "thousand" else sg.stress_scene()
-    workload = WORKLOAD.format(mc=args.miss_check) if args.scene == "thousand" else WORKLOAD_STRESS
+    workload = (WORKLOAD if args.scene == "thousand" else WORKLOAD_STRESS).format(mc=args.miss_check)
     n_li = len(sc.lights)
     stream = torch.cuda.Stream()            # a non-default stream: frames are CUDA-graph captured
     torch.cuda.set_stream(stream)
@@ -587,6 +652,11 @@ def run_ours(args):
         fp32 = {"ms_per_frame": e0.elapsed_time(e1) / 3, "rays_per_s": n / (e0.elapsed_time(e1) / 3 * 1e-3)}
         r32.close()
 
+    # ---- the same frame with E4M3 hidden layers (the precision ladder's next rung) ------------
+    fp8 = None
+    if prec == native.PREC_BF16 and not args.no_fp8:
+        fp8 = fp8_frame(sc, r, stream, jdepth, jids, peaks()[0]["bf16_tflops"], args)
+
     # ---- end to end through the public API with host buffers ---------------------------------
     host_out = torch.empty(n, 4, dtype=torch.float32, pin_memory=True)
     inst_args = (sc.inst_type, sc.inst_R, sc.inst_T, sc.inst_s)
@@ -667,6 +737,7 @@ def run_ours(args):
                       "fallback_rate": st.fallback_pairs / max(1, P1 + P3), "mlp_stages": mlp_stages,
                       "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "wall_s": t_wall},
             "fp32_frame": fp32,
+            "fp8_frame": fp8,
             "rs_frame": rs,
             "edit_frame": edit,
             "classifier_frame": cls,
@@ -692,10 +763,11 @@ def main():
     ap.add_argument("--train-steps", type=int, default=20000, help="Adam steps per type (the workload's 20k)")
     ap.add_argument("--train-batch", type=int, default=65536)
     ap.add_argument("--label-rays", type=int, default=1 << 22, help="plain-method labelled rays per type (2^22)")
-    ap.add_argument("--miss-check", type=int, default=32, help="chord samples that verify a confident NeDF miss")
+    ap.add_argument("--miss-check", type=int, default=64, help="chord samples that verify a confident NeDF miss")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-fp8", action="store_true", help="skip the E4M3 frame beside the BF16 one")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tensor-core schedule")
     ap.add_argument("--no-resample", action="store_true", help="skip the frame with Step-2 outlier resampling")
     ap.add_argument("--no-edit", action="store_true", help="skip the buffer-reuse (edit) frames")

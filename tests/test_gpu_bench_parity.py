@@ -18,7 +18,7 @@ from .gpu_helpers import NOID, frame_vs_oracle
 pytestmark = pytest.mark.gpu
 
 # the bench frame's options (bench.py), on the device and in the oracle's names
-FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=32)
+FRAME_OPTS = dict(fallback_conf=0.9, refine_steps=4, outlier_resample=1, miss_check=64)
 GPU_MARCH = dict(march_steps=256, march_bisect=8)
 ORC_MARCH = dict(march_n=256, march_b=8)
 
