@@ -439,7 +439,8 @@ int nedf_compose_make_labels_density(nedf_handle *h, int type, int64_t n_rays, u
  * consecutive rays of its training set (wrapping around), starting where the previous step
  * ended.  The random seed of a step is not an argument: the rays and labels are drawn once per
  * training set by nedf_compose_make_labels (its `seed`), and a step is a deterministic function
- * of the training set, the weights and the cursor (so a saved state resumes bit for bit).  Loss, NEDF_ARCH_REGRESSION (regression form of Eq. 6): mean over labelled hits of
+ * of the training set, the weights and the cursor (so a saved state resumes bit for bit).
+ * Loss, NEDF_ARCH_REGRESSION (regression form of Eq. 6): mean over labelled hits of
  * (m - m*)^2 plus 0.1 * mean BCE(a, hit*).  NEDF_ARCH_CLASSIFIER (Eq. 6 itself): mean over
  * labelled hits of BCE(coarse logits, one-hot S_c(m*)) + BCE(fine logits, one-hot S_f(m*)), each
  * the mean over its bins, plus 0.1 * mean BCE(hit logit, hit*); the segment operator S takes

@@ -559,6 +559,64 @@ cudaError_t launch_nedf_decode(const Workspace &ws, int mode, int num_sms, cudaS
     return cudaGetLastError();
 }
 
+// A whole NeDF layer (one weight stage holds it) issued as a straight run of MMAs: descriptors
+// advance by constant steps of their start-address field, with no per-MMA address selection (a
+// per-chunk branch and descriptor rebuild in the issuing thread cost ≈ 40 cycles per MMA, enough
+// to starve the tensor pipe).  Swapped operands: D^T (dx, 128 features x 256 rows) += W_c H_c^T with
+// weight chunk c of the stage (A, 4 KB apart) and the slot's activation chunk c (B, 8 KB apart);
+// BIAS: the last chunk reads the constant-one block instead.
+template <int NK, bool BIAS>
+__device__ __forceinline__ void issue_layer_swapped(uint32_t dx, uint64_t wd, uint32_t hs, uint32_t ones, uint32_t id)
+{
+    const uint64_t bd = smem_desc(hs, 4096, 128);
+#pragma unroll
+    for (int c = 0; c < (BIAS ? NK - 1 : NK); ++c)
+        mma_bf16(dx, wd + (uint64_t)(c * (4096 >> 4)), bd + (uint64_t)(c * (8192 >> 4)), id, c > 0 ? 1u : 0u);
+    if (BIAS) mma_bf16(dx, wd + (uint64_t)((NK - 1) * (4096 >> 4)), smem_desc(ones, 4096, 128), id, 1u);
+}
+
+// The same for the unswapped last hidden layer: each 128-row half (A: the MN-major activations,
+// halves 2 KB apart) against weight chunk c (B), into dx and dy; the last chunk is the bias chunk.
+template <int NK>
+__device__ __forceinline__ void issue_layer_unswapped(uint32_t dx, uint32_t dy, uint64_t wd, uint32_t hs, uint32_t ones,
+                                                      uint32_t id)
+{
+    const uint64_t ax = smem_desc(hs, 4096, 128), ay = smem_desc(hs + 2048u, 4096, 128);
+#pragma unroll
+    for (int c = 0; c < NK - 1; ++c) {
+        mma_bf16(dx, ax + (uint64_t)(c * (8192 >> 4)), wd + (uint64_t)(c * (4096 >> 4)), id, c > 0 ? 1u : 0u);
+        mma_bf16(dy, ay + (uint64_t)(c * (8192 >> 4)), wd + (uint64_t)(c * (4096 >> 4)), id, c > 0 ? 1u : 0u);
+    }
+    const uint64_t wl = wd + (uint64_t)((NK - 1) * (4096 >> 4));
+    mma_bf16(dx, smem_desc(ones, 4096, 128), wl, id, 1u);
+    mma_bf16(dy, smem_desc(ones + 2048u, 4096, 128), wl, id, 1u);
+}
+
+// The same straight run for the unswapped engine (128-row halves as A, weight chunks as B; E4M3
+// hidden layers or width 64): NK chunks of chunk_bytes each; BIAS: the last chunk reads A from the
+// constant-one columns at ones_off.
+template <bool E4M3, int NK, bool BIAS>
+__device__ __forceinline__ void issue_layer_halves(uint32_t dx, uint32_t dy, uint32_t ax, uint32_t ay, uint32_t stage,
+                                                   uint32_t chunk_bytes, uint32_t idesc, uint32_t ones_off)
+{
+    const uint64_t bd = smem_desc(stage, 128, 256), adx = smem_desc(ax, 2048, 128), ady = smem_desc(ay, 2048, 128);
+    const uint64_t bstep = (uint64_t)(chunk_bytes >> 4);
+#pragma unroll
+    for (int c = 0; c < NK; ++c) {
+        const bool bias = BIAS && c == NK - 1;
+        const uint64_t a0 = bias ? smem_desc(ax + ones_off, 2048, 128) : adx + (uint64_t)(c * (4096 >> 4));
+        const uint64_t a1 = bias ? smem_desc(ay + ones_off, 2048, 128) : ady + (uint64_t)(c * (4096 >> 4));
+        const uint32_t acc = c > 0 ? 1u : 0u;
+        if (E4M3) {
+            mma_e4m3(dx, a0, bd + (uint64_t)c * bstep, idesc, acc);
+            mma_e4m3(dy, a1, bd + (uint64_t)c * bstep, idesc, acc);
+        } else {
+            mma_bf16(dx, a0, bd + (uint64_t)c * bstep, idesc, acc);
+            mma_bf16(dy, a1, bd + (uint64_t)c * bstep, idesc, acc);
+        }
+    }
+}
+
 template <int N, int MODE, bool F8, bool SWAP>
 __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBuffers mb, PipeArgs a)
 {
@@ -678,6 +736,14 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                                 // activations (8-column groups 4 KB apart, 8-row groups 128 bytes
                                 // apart); a hidden layer's bias chunk reads the ones block
                                 uint64_t wd = smem_desc(stage, 128, 256);
+                                if (c0 == 0 && c1 == nk && (swapped || l > 0)) {
+                                    // the whole layer in this stage (the autotuner's stages of >= 36 KB)
+                                    if constexpr (SW) {
+                                        if (!swapped) issue_layer_unswapped<N / kKC + 1>(dx, dy, wd, hs, ones, id_sw);
+                                        else if (l == 0) issue_layer_swapped<K0 / kKC, false>(dx, wd, hs, ones, id_sw);
+                                        else issue_layer_swapped<N / kKC + 1, true>(dx, wd, hs, ones, id_sw);
+                                    }
+                                } else
                                 for (int c = c0; c < c1; ++c) {
                                     const uint32_t src = (l > 0 && c == N / kKC) ? ones : hs + (uint32_t)c * 8192u;
                                     const uint32_t acc = c > 0 ? 1u : 0u;
@@ -689,6 +755,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_nedf2(Workspace ws, MarchBu
                                     }
                                     wd += (uint64_t)(SH::CHUNK >> 4);
                                 }
+                            } else if (c0 == 0 && c1 == nk) {
+                                // the whole layer in this stage: a straight run
+                                if (l == 0) issue_layer_halves<false, K0 / kKC, false>(dx, dy, ax, ay, stage, SH::CHUNK, idesc, 0u);
+                                else if (e4m3) issue_layer_halves<true, N / 32, false>(dx, dy, ax, ay, stage, SH::CHUNK, idesc8, 0u);
+                                else issue_layer_halves<false, N / kKC + 1, true>(dx, dy, ax, ay, stage, SH::CHUNK, idesc,
+                                                                                  (uint32_t)(SH::ONES / kKC) * 4096u);
                             } else if (e4m3) {
                                 issue_chunks<true>(dx, dy, ax, ay, stage, c0, c1, SH::CHUNK, idesc8, -1, 0u);
                             } else {
