@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pair(Workspace ws, MarchBuf
                         for (int c0 = 0; c0 < nk; c0 += GC, ++q, rp.next(S)) {
                             const int st = rp.st;
                             const uint32_t bytes = (uint32_t)(min(GC, nk - c0) * SH::HCHUNK);
-                            if (!pair_wait(&w_empty[st], rp.ph ^ 1u, abort, ws.status)) break;
+                            if (!pipe_wait(&w_empty[st], rp.ph ^ 1u, abort, ws.status)) break;
                             mbar_arrive_expect_tx(&w_full[st], bytes);
                             bulk_g2s(ring + (size_t)st * STAGE, src + (size_t)c0 * SH::HCHUNK, bytes, &w_full[st]);
                         }
@@ -258,11 +258,21 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pair(Workspace ws, MarchBuf
                             // chunk c reads A columns [16c, 16c + 16) (BF16) or [32c, 32c + 32)
                             // (E4M3): 4 KB at c * 4096; a BF16 hidden layer's chunk 16 is its bias,
                             // against the constant-one columns at 256 = the same offset
-                            for (int c = c0; c < c1; ++c) {
-                                const uint64_t ad = smem_desc(ax + (uint32_t)c * 4096u, 2048, 128);
-                                if (e4m3) mma_e4m3_pair(d, ad, bd, id8, c > 0 ? 1u : 0u);
-                                else mma_bf16_pair(d, ad, bd, idb, c > 0 ? 1u : 0u);
-                                bd += (uint64_t)(SH::HCHUNK >> 4);
+                            // descriptors advance by constant steps of their start-address field (a
+                            // per-MMA rebuild in the issuing thread starves the pipe)
+                            uint64_t ad = smem_desc(ax + (uint32_t)c0 * 4096u, 2048, 128);
+                            if (e4m3) {
+                                for (int c = c0; c < c1; ++c) {
+                                    mma_e4m3_pair(d, ad, bd, id8, c > 0 ? 1u : 0u);
+                                    ad += (uint64_t)(4096 >> 4);
+                                    bd += (uint64_t)(SH::HCHUNK >> 4);
+                                }
+                            } else {
+                                for (int c = c0; c < c1; ++c) {
+                                    mma_bf16_pair(d, ad, bd, idb, c > 0 ? 1u : 0u);
+                                    ad += (uint64_t)(4096 >> 4);
+                                    bd += (uint64_t)(SH::HCHUNK >> 4);
+                                }
                             }
                             if (release) {
                                 mma_commit_pair(smem_addr(&w_empty[st]));
@@ -300,7 +310,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pair(Workspace ws, MarchBuf
         }
         // this warp's A writes are done: one arrival per warp on the even CTA's a_ready
         auto arrive_a = [&](int s) {
-            fence_proxy_async_all();
+            fence_proxy_async_smem();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(a_ready_even[s]);
@@ -434,7 +444,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pair(Workspace ws, MarchBuf
                     // tcgen05.ld is warp-collective: a warp-uniform outcome; the last layer's step
                     // (tail, set-up: named barriers) decides for all 256 epilogue threads
                     const bool last = l + 1 == L;
-                    const bool okw = __all_sync(0xffffffffu, pair_wait(&acc_full[s], (uint32_t)(jb[s]++ & 1u), abort, ws.status));
+                    const bool okw = __all_sync(0xffffffffu, pipe_wait(&acc_full[s], (uint32_t)(jb[s]++ & 1u), abort, ws.status));
                     const bool ok = last ? !epilogue_any(!okw) : okw;
                     if (ok) {
                         tc_fence_after();

@@ -258,10 +258,6 @@ __device__ __forceinline__ void cluster_sync()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// Orders this thread's generic-proxy writes before later async-proxy accesses in every state space
-// (the SM-pair MMAs read both CTAs' shared memory).
-__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
-
 // TMEM of a CTA pair: one warp of each CTA of the pair executes these (the same column count).
 __device__ __forceinline__ void tmem_alloc_pair(uint32_t *dst_smem, uint32_t ncols)
 {
