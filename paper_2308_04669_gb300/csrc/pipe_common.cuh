@@ -13,6 +13,7 @@ using namespace tc;
 constexpr int kPipeRows = 256;              // rows per tile (two MMA halves of 128)
 constexpr int kHalf = 128;
 constexpr int kPipeThreads = 320;           // 8 epilogue warps, producer, MMA issuer
+constexpr int kPipeThreadsPf = 384;         // the NeRF engine: + 2 warps preparing the next tile's rows
 constexpr int kKC = 16;                     // K columns per weight chunk (one MMA K step)
 // A bulk copy costs its issuing thread a few hundred cycles whatever its size, so weights move in
 // stages of several chunks (one copy, one full and one empty barrier phase each).  The stage size

@@ -180,8 +180,64 @@ __device__ __forceinline__ void issue_chunks(uint32_t dx, uint32_t dy, uint32_t 
 }
 
 
+// Inputs of row R of a NeRF tile: the sample's local position and direction (x6), its density
+// (shade) or sample weight (march), and the keys the tail needs: for shading, the pixel and its
+// sample length at slot [half * 128 + pixel-in-half] (written by the pixel's first sample row);
+// for the plain method's colour rows, the row's pair (0xFFFFFFFF: none).  Invalid rows get zeros.
+template <int MODE>
+__device__ __forceinline__ void pipe_row_inputs(const Workspace &ws, const MarchBuffers &mb, const PipeArgs &a,
+                                                const DevFrame &f, const DevType &T, int t, unsigned long long tile,
+                                                int R, float *x6, float &sig, uint32_t *key, float *wd)
+{
+    for (int c = 0; c < 6; ++c) x6[c] = 0.f;
+    sig = 0.f;
+    const int g = R / kHalf, r = R - g * kHalf;
+    if (MODE == kModeShade) {
+        const int ns = f.n_shade;
+        const int ppg = kHalf / ns;           // pixels per half
+        const unsigned long long first = (tile - ws.cnt->h_tile[t]) * (unsigned long long)(2 * ppg) + g * ppg;
+        const int q = r / ns, j = r - q * ns;
+        if (q < ppg && first + q < ws.cnt->h_count[t]) {
+            const uint32_t p = ws.hlist[(size_t)t * a.npix + first + q];
+            const DevInst I = ws.inst[ws.id[p]];
+            V3 o, d, ol, dl;
+            camera_ray(f, p % f.W, p / f.W, o, d);
+            to_local(I, o, d, ol, dl);
+            const float Dl = ws.depth[p] / I.s;
+            const float delta = 2.0f * f.shade_half / ns;
+            const V3 x = madd(ol, Dl - f.shade_half + (j + 0.5f) * delta, dl);
+            x6[0] = x.x; x6[1] = x.y; x6[2] = x.z; x6[3] = dl.x; x6[4] = dl.y; x6[5] = dl.z;
+            sig = density(T, x, f.sigma_max, f.sdf_width);
+            if (j == 0) { key[g * kHalf + q] = p; wd[g * kHalf + q] = I.s * delta; }
+        }
+    } else {
+        const unsigned long long end = min(mb.row_cursor[t], mb.row_off[t + 1]);
+        const unsigned long long idx = mb.row_off[t] + (tile - mb.row_tile[t]) * kPipeRows + R;
+        uint32_t pair = 0xFFFFFFFFu;
+        if (idx < end) {
+            const uint2 row = mb.rows[idx];
+            const uint2 pp = ws.ppairs[row.x];
+            const DevInst I = ws.inst[pp.y];
+            V3 o, d, ol, dl;
+            camera_ray(f, pp.x % f.W, pp.x / f.W, o, d);
+            to_local(I, o, d, ol, dl);
+            Chord ch;
+            bound_chord(ol, dl, T.rb, ch);
+            const float dt = (ch.tx - ch.te) / a.n_samples;
+            float Tr = mb.T_first[row.x];
+            for (int jj = mb.k_first[row.x]; jj < (int)row.y; ++jj)
+                Tr *= expf(-density(T, madd(ol, ch.te + (jj + 0.5f) * dt, dl), f.sigma_max, f.sdf_width) * I.s * dt);
+            const V3 x = madd(ol, ch.te + (row.y + 0.5f) * dt, dl);
+            x6[0] = x.x; x6[1] = x.y; x6[2] = x.z; x6[3] = dl.x; x6[4] = dl.y; x6[5] = dl.z;
+            sig = Tr * (1.0f - expf(-density(T, x, f.sigma_max, f.sdf_width) * I.s * dt));
+            pair = row.x;
+        }
+        key[R] = pair;
+    }
+}
+
 template <int N, int MODE, bool F8>
-__global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuffers mb, PipeArgs a)
+__global__ void __launch_bounds__(kPipeThreadsPf, 1) k_pipe(Workspace ws, MarchBuffers mb, PipeArgs a)
 {
     static_assert(MODE == kModeShade || MODE == kModeMarch, "the NeDF modes run in k_nedf2");
     constexpr bool NERF = true;
@@ -197,6 +253,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
     __shared__ float t_sig[kPipeRows], t_rgb[kPipeRows][3];
     __shared__ uint32_t t_key[kPipeRows];
     __shared__ float t_wd[kPipeRows];
+    // the next tile's row inputs, computed by the prefetch warps while this tile's layers run
+    __shared__ float pf_x[kPipeRows][6], pf_sig[kPipeRows], pf_wd[kPipeRows];
+    __shared__ uint32_t pf_key[kPipeRows];
+    __shared__ uint64_t pf_full, pf_empty;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = NERF ? ws.nerf_hidden : ws.nedf_hidden;
@@ -211,6 +271,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
         mbar_init(&P.a_ready, 2 * kHalf);
         mbar_init(&P.acc_full, 1);
         mbar_init(&P.fin, 1);
+        mbar_init(&pf_full, kPipeThreadsPf - kPipeThreads);
+        mbar_init(&pf_empty, 2 * kHalf);
         for (int s = 0; s < S; ++s) {
             mbar_init(&w_full[s], 1);
             mbar_init(&w_empty[s], 1);
@@ -282,6 +344,23 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                 pipe_drain(&P.fin, 0u, ws.status);
             }
         }
+    } else if (warp >= 10) {
+        // ------------------------------ prefetch warps ------------------------------------------
+        // each tile's row inputs (the global-load chain pixel -> instance -> depth, the sample
+        // geometry and density) one tile ahead of the epilogue, into pf_*: 4 rows per thread
+        const int pt = threadIdx.x - kPipeThreads;
+        uint32_t ph = 0;
+        for (unsigned long long tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x, ph ^= 1u) {
+            if (!pipe_wait(&pf_empty, ph ^ 1u, abort, ws.status)) break;
+            const int t = pipe_tile_type<MODE>(ws, mb, a, tile);
+            const DevType T = ws.types[t];
+#pragma unroll
+            for (int k = 0; k < kPipeRows / (kPipeThreadsPf - kPipeThreads); ++k) {
+                const int R = pt + k * (kPipeThreadsPf - kPipeThreads);
+                pipe_row_inputs<MODE>(ws, mb, a, f, T, t, tile, R, pf_x[R], pf_sig[R], pf_key, pf_wd);
+            }
+            mbar_arrive(&pf_full);
+        }
     } else {
         // ------------------------------ epilogue groups -----------------------------------------
         const int g = warp >> 2;                      // 0: rows 0..127 (X), 1: rows 128..255 (Y)
@@ -294,7 +373,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
             *reinterpret_cast<uint4 *>(Ag + a_offset(r, SH::ONES)) = make_uint4(pack_bf16(1.0f, 1.0f), 0u, 0u, 0u);
             *reinterpret_cast<uint4 *>(Ag + a_offset(r, SH::ONES + 8)) = make_uint4(0u, 0u, 0u, 0u);
         }
-        unsigned long long jb = 0;
+        unsigned long long jb = 0, pf_ph = 0;
         const int ns = f.n_shade;
         int f32_type = -1;
         const float *f32 = f32s;
@@ -312,54 +391,22 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pipe(Workspace ws, MarchBuf
                 asm volatile("bar.sync 3, 256;" ::: "memory");
                 f32_type = t;
             }
-            // ---- row set-up ---------------------------------------------------------------------
-            float x6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            bool valid = false;
-            unsigned long long idx = 0;
-            float sig = 0.f;                          // shade: density; march: sample weight
-            if (MODE == kModeShade) {
-                const int ppg = kHalf / ns;           // pixels per half
-                const unsigned long long first = (tile - ws.cnt->h_tile[t]) * (unsigned long long)(2 * ppg) + g * ppg;
-                const unsigned long long cnt = ws.cnt->h_count[t];
-                const int q = r / ns, j = r - q * ns;
-                valid = q < ppg && first + q < cnt;
-                if (valid) {
-                    const uint32_t p = ws.hlist[(size_t)t * a.npix + first + q];
-                    const DevInst I = ws.inst[ws.id[p]];
-                    V3 o, d, ol, dl;
-                    camera_ray(f, p % f.W, p / f.W, o, d);
-                    to_local(I, o, d, ol, dl);
-                    const float Dl = ws.depth[p] / I.s;
-                    const float delta = 2.0f * f.shade_half / ns;
-                    const V3 x = madd(ol, Dl - f.shade_half + (j + 0.5f) * delta, dl);
-                    x6[0] = x.x; x6[1] = x.y; x6[2] = x.z; x6[3] = dl.x; x6[4] = dl.y; x6[5] = dl.z;
-                    sig = density(T, x, f.sigma_max, f.sdf_width);
-                    if (j == 0) { t_key[g * kHalf + q] = p; t_wd[g * kHalf + q] = I.s * delta; }
+            // ---- row set-up: the prefetch warps' inputs for this tile ----------------------------
+            float x6[6];
+            float sig;                                // shade: density; march: sample weight
+            {
+                const bool okp = pipe_wait(&pf_full, (uint32_t)(pf_ph & 1u), abort, ws.status);
+                ++pf_ph;
+                if (epilogue_any(!okp)) {
+                    *abort = 1;
+                    break;
                 }
-            } else if (MODE == kModeMarch) {
-                const unsigned long long end = min(mb.row_cursor[t], mb.row_off[t + 1]);
-                idx = mb.row_off[t] + (tile - mb.row_tile[t]) * kPipeRows + R;
-                valid = idx < end;
-                uint32_t pair = 0xFFFFFFFFu;
-                if (valid) {
-                    const uint2 row = mb.rows[idx];
-                    const uint2 pp = ws.ppairs[row.x];
-                    const DevInst I = ws.inst[pp.y];
-                    V3 o, d, ol, dl;
-                    camera_ray(f, pp.x % f.W, pp.x / f.W, o, d);
-                    to_local(I, o, d, ol, dl);
-                    Chord ch;
-                    bound_chord(ol, dl, T.rb, ch);
-                    const float dt = (ch.tx - ch.te) / a.n_samples;
-                    float Tr = mb.T_first[row.x];
-                    for (int jj = mb.k_first[row.x]; jj < (int)row.y; ++jj)
-                        Tr *= expf(-density(T, madd(ol, ch.te + (jj + 0.5f) * dt, dl), f.sigma_max, f.sdf_width) * I.s * dt);
-                    const V3 x = madd(ol, ch.te + (row.y + 0.5f) * dt, dl);
-                    x6[0] = x.x; x6[1] = x.y; x6[2] = x.z; x6[3] = dl.x; x6[4] = dl.y; x6[5] = dl.z;
-                    sig = Tr * (1.0f - expf(-density(T, x, f.sigma_max, f.sdf_width) * I.s * dt));
-                    pair = row.x;
-                }
-                t_key[R] = pair;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) x6[c] = pf_x[R][c];
+                sig = pf_sig[R];
+                t_key[R] = pf_key[R];
+                t_wd[R] = pf_wd[R];
+                mbar_arrive(&pf_empty);               // this thread is done with the buffer
             }
             {
                 float feat[K0];
@@ -966,7 +1013,7 @@ static cudaError_t launch_pipe_n(const Workspace &ws, const MarchBuffers &mb, co
     if (sm > 227 * 1024 - 8192) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(k_pipe<N, MODE, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_pipe<N, MODE, F8><<<grid, kPipeThreads, sm, st>>>(ws, mb, a);
+    k_pipe<N, MODE, F8><<<grid, kPipeThreadsPf, sm, st>>>(ws, mb, a);
     return cudaGetLastError();
 }
 
