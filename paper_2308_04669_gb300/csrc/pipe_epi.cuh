@@ -136,29 +136,51 @@ __device__ __forceinline__ void epi_convert8(const uint32_t (&v)[32], const floa
 }
 
 // Last hidden layer: ReLU and BF16 rounding of 32 columns, folded into the NOUT outputs (w_out
-// rows of length N).
+// rows of length N; 16-byte aligned at every multiple of 4 columns).  The weights are read four
+// columns per load; the FMAs run in column order, so the sums are those of a column-by-column loop.
 template <int NOUT, int N>
 __device__ __forceinline__ void epi_output(const uint32_t (&v)[32], const float *wout, float *out)
 {
 #pragma unroll
-    for (int jj = 0; jj < 32; jj += 2) {
-        const uint32_t p = pack_bf16_relu(__uint_as_float(v[jj]), __uint_as_float(v[jj + 1]));
-        const float h0 = __uint_as_float(p << 16), h1 = __uint_as_float(p & 0xFFFF0000u);
+    for (int jj = 0; jj < 32; jj += 4) {
+        float4 w[NOUT];
 #pragma unroll
-        for (int o = 0; o < NOUT; ++o) out[o] = fmaf(h1, wout[o * N + jj + 1], fmaf(h0, wout[o * N + jj], out[o]));
+        for (int o = 0; o < NOUT; ++o) w[o] = *reinterpret_cast<const float4 *>(wout + o * N + jj);
+        const uint32_t p0 = pack_bf16_relu(__uint_as_float(v[jj]), __uint_as_float(v[jj + 1]));
+        const uint32_t p1 = pack_bf16_relu(__uint_as_float(v[jj + 2]), __uint_as_float(v[jj + 3]));
+        const float h0 = __uint_as_float(p0 << 16), h1 = __uint_as_float(p0 & 0xFFFF0000u);
+        const float h2 = __uint_as_float(p1 << 16), h3 = __uint_as_float(p1 & 0xFFFF0000u);
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) {
+            out[o] = fmaf(h1, w[o].y, fmaf(h0, w[o].x, out[o]));
+            out[o] = fmaf(h3, w[o].w, fmaf(h2, w[o].z, out[o]));
+        }
     }
 }
 
-// The same with E4M3 rounding of the last hidden activation.
+// The same with E4M3 rounding of the last hidden activation (bias and weights four columns per
+// load).
 template <int NOUT, int N, bool AFF>
 __device__ __forceinline__ void epi_output8(const uint32_t (&v)[32], const float *bias, float s, const float *wout, float *out)
 {
 #pragma unroll
-    for (int jj = 0; jj < 32; jj += 2) {
-        float h0, h1;
-        unpack_e4m3(pack_e4m3_relu(epi_affine<AFF>(v[jj], bias, jj, s), epi_affine<AFF>(v[jj + 1], bias, jj + 1, s)), h0, h1);
+    for (int jj = 0; jj < 32; jj += 4) {
+        float4 w[NOUT];
 #pragma unroll
-        for (int o = 0; o < NOUT; ++o) out[o] = fmaf(h1, wout[o * N + jj + 1], fmaf(h0, wout[o * N + jj], out[o]));
+        for (int o = 0; o < NOUT; ++o) w[o] = *reinterpret_cast<const float4 *>(wout + o * N + jj);
+        const float4 b = AFF ? *reinterpret_cast<const float4 *>(bias + jj) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float x0 = AFF ? fmaf(__uint_as_float(v[jj]), s, b.x) : __uint_as_float(v[jj]);
+        const float x1 = AFF ? fmaf(__uint_as_float(v[jj + 1]), s, b.y) : __uint_as_float(v[jj + 1]);
+        const float x2 = AFF ? fmaf(__uint_as_float(v[jj + 2]), s, b.z) : __uint_as_float(v[jj + 2]);
+        const float x3 = AFF ? fmaf(__uint_as_float(v[jj + 3]), s, b.w) : __uint_as_float(v[jj + 3]);
+        float h0, h1, h2, h3;
+        unpack_e4m3(pack_e4m3_relu(x0, x1), h0, h1);
+        unpack_e4m3(pack_e4m3_relu(x2, x3), h2, h3);
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) {
+            out[o] = fmaf(h1, w[o].y, fmaf(h0, w[o].x, out[o]));
+            out[o] = fmaf(h3, w[o].w, fmaf(h2, w[o].z, out[o]));
+        }
     }
 }
 
