@@ -346,11 +346,14 @@ __global__ void __launch_bounds__(kPipeThreadsPf, 1) k_pipe(Workspace ws, MarchB
         }
     } else if (warp >= 10) {
         // ------------------------------ prefetch warps ------------------------------------------
-        // each tile's row inputs (the global-load chain pixel -> instance -> depth, the sample
-        // geometry and density) one tile ahead of the epilogue, into pf_*: 4 rows per thread
+        // shading: each tile's row inputs (the global-load chain pixel -> instance -> depth, the
+        // sample geometry and density) one tile ahead of the epilogue, into pf_*: 4 rows per thread.
+        // The plain method's colour rows carry a transmittance loop over their earlier samples, too
+        // much for 64 threads: their epilogue threads compute their own rows.
         const int pt = threadIdx.x - kPipeThreads;
         uint32_t ph = 0;
-        for (unsigned long long tile = blockIdx.x; tile < n_tiles && !*abort; tile += gridDim.x, ph ^= 1u) {
+        for (unsigned long long tile = blockIdx.x; MODE == kModeShade && tile < n_tiles && !*abort;
+             tile += gridDim.x, ph ^= 1u) {
             if (!pipe_wait(&pf_empty, ph ^ 1u, abort, ws.status)) break;
             const int t = pipe_tile_type<MODE>(ws, mb, a, tile);
             const DevType T = ws.types[t];
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(kPipeThreadsPf, 1) k_pipe(Workspace ws, MarchB
             // ---- row set-up: the prefetch warps' inputs for this tile ----------------------------
             float x6[6];
             float sig;                                // shade: density; march: sample weight
-            {
+            if (MODE == kModeShade) {
                 const bool okp = pipe_wait(&pf_full, (uint32_t)(pf_ph & 1u), abort, ws.status);
                 ++pf_ph;
                 if (epilogue_any(!okp)) {
@@ -407,6 +410,8 @@ __global__ void __launch_bounds__(kPipeThreadsPf, 1) k_pipe(Workspace ws, MarchB
                 t_key[R] = pf_key[R];
                 t_wd[R] = pf_wd[R];
                 mbar_arrive(&pf_empty);               // this thread is done with the buffer
+            } else {
+                pipe_row_inputs<MODE>(ws, mb, a, f, T, t, tile, R, x6, sig, t_key, t_wd);
             }
             {
                 float feat[K0];
