@@ -56,7 +56,7 @@ TRAINED_WEIGHTS = os.path.join(ROOT, "paper_2308_04669_gb300", "data", "nedf_tho
 # kernel source (profiles/); a stage is absent here once its kernel changed after the capture.
 # DRAM bytes per launch of the dominant kernel from an ncu capture of the current kernel (None until
 # the kernel's counters have been taken again after a change)
-PROFILED_TRAFFIC = {"step2_shade": 9.53e6}    # k_pipe<256,0>, profiles/k_pipe_1024inst_1024px_bf16.md
+PROFILED_TRAFFIC = {"step2_shade": 9.60e6}    # k_pipe<256,0>, profiles/k_pipe_1024inst_1024px_bf16.md
 NERF_FLOP = 2 * (90 * 256 + 7 * 256 * 256 + 256 * 3)          # per sample, unpadded
 # the paper's intersection network: head 1008 -> 256, 16 residual blocks of two 256 x 256 layers,
 # tails 256 -> 65 and 256 -> 128; per query, unpadded
