@@ -53,10 +53,9 @@ TRAIN_FLOP = NEDF_FLOP + 2 * (5 * 128 * 128 + 2 * 128) + NEDF_FLOP
 # time the same frame
 TRAINED_WEIGHTS = os.path.join(ROOT, "paper_2308_04669_gb300", "data", "nedf_thousand_trained.npz")
 # DRAM bytes (read + write) per launch of a stage's kernel from an ncu capture of the current
-# kernel source (profiles/); a stage is absent here once its kernel changed after the capture.
-# DRAM bytes per launch of the dominant kernel from an ncu capture of the current kernel (None until
-# the kernel's counters have been taken again after a change)
-PROFILED_TRAFFIC = {"step2_shade": 9.60e6}    # k_pipe<256,0>, profiles/k_pipe_1024inst_1024px_bf16.md
+# kernel source on this frame (k_pipe<256, 0, 0>: 9.61 MB for 320,817 hit pixels, scaled to the
+# bench frame's); a stage is absent here once its kernel changed after the capture.
+PROFILED_TRAFFIC = {"step2_shade": 9.60e6}
 NERF_FLOP = 2 * (90 * 256 + 7 * 256 * 256 + 256 * 3)          # per sample, unpadded
 # the paper's intersection network: head 1008 -> 256, 16 residual blocks of two 256 x 256 layers,
 # tails 256 -> 65 and 256 -> 128; per query, unpadded
