@@ -15,7 +15,9 @@
 //   warp 8      producer: streams the weight chunks of every layer of every tile, in MMA order,
 //               through a ring of shared-memory stages (one bulk asynchronous copy each: a copy
 //               costs its issuing thread a few hundred cycles whatever its size);
-//   warp 9      MMA issuer (and TMEM owner).
+//   warp 9      MMA issuer (and TMEM owner);
+//   warps 10-11 (shading) prefetch: the next tile's row inputs (pixel, instance, depth, sample
+//               position and density) into shared memory while the current tile's layers run.
 // k_nedf2 (the NeDF, widths up to 128) keeps two such tiles in flight (see its own comment).
 // The producer only waits for free stages, so while the epilogue warps work on layer l it is
 // already loading layer l+1.  Every wait is bounded: a timeout sets the status word and an abort
